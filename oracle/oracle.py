@@ -1,0 +1,242 @@
+"""ctypes front end of the FP64 oracle (test infrastructure only).
+
+Every function takes a workload object with the attributes of
+`paper_2603_24027_gb300.inputs.Workload` (duck-typed; this module imports
+nothing from the CUDA package) and numpy arrays, and returns numpy arrays.
+State blocks are float64 [18][nz][ny][nx]: Ex Ey Ez Hx Hy Hz psi0..psi11.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+C0 = 299792458.0
+NF = 18
+FMT = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "none": -1}
+
+
+class OCfg(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("P", C.c_int),
+        ("periodic", C.c_int), ("n_steps", C.c_int),
+        ("S", C.c_double), ("dx", C.c_double),
+        ("pml_m", C.c_int), ("sigma_factor", C.c_double), ("kappa_max", C.c_double),
+        ("alpha_factor", C.c_double),
+        ("src_kind", C.c_int), ("src_comp", C.c_int), ("src_axis", C.c_int),
+        ("src_pos", C.c_int * 3), ("src_sigma", C.c_double * 2),
+        ("lambda0", C.c_double), ("rel_bw", C.c_double), ("t0_over_tau", C.c_double),
+        ("amplitude", C.c_double),
+        ("det_kind", C.c_int), ("det_axis", C.c_int), ("det_index", C.c_int),
+        ("det_lo", C.c_int * 2), ("det_hi", C.c_int * 2),
+        ("dlo", C.c_int * 3), ("dhi", C.c_int * 3),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        cp = C.POINTER(OCfg)
+        L.oracle_profiles.argtypes = [cp, C.c_int, dp]
+        L.oracle_waveform.argtypes = [cp, dp]
+        L.oracle_source_weight.argtypes = [cp, dp]
+        L.oracle_step.argtypes = [cp, dp, dp, C.c_int, dp]
+        L.oracle_run.argtypes = [cp, dp, dp, C.c_int, C.c_int, dp]
+        L.oracle_step_adjoint.argtypes = [cp, dp, dp]
+        L.oracle_unstep.argtypes = [cp, dp, dp, C.c_int]
+        L.oracle_gradient.argtypes = [cp, dp, C.c_double, dp, dp, dp]
+        L.oracle_reverse.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                     dp, dp, dp]
+        L.oracle_quantize_array.argtypes = [C.c_int, dp, dp, C.c_long]
+        L.oracle_format_max.argtypes = [C.c_int]
+        L.oracle_format_max.restype = C.c_double
+        L.oracle_interp_series.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, dp, dp]
+        L.oracle_sample_values.argtypes = [cp]
+        L.oracle_sample_values.restype = C.c_size_t
+        L.oracle_num_threads.restype = C.c_int
+        L.oracle_set_num_threads.argtypes = [C.c_int]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_cfg(w, periodic: int = 0, pml=None, n_steps=None) -> OCfg:
+    c = OCfg()
+    c.nx, c.ny, c.nz = w.nx, w.ny, w.nz
+    c.P = w.pml_thickness if pml is None else pml
+    c.periodic = periodic
+    c.n_steps = w.n_steps if n_steps is None else n_steps
+    c.S = C0 * w.dt / w.dx
+    c.dx = w.dx
+    c.pml_m = w.pml_order
+    c.sigma_factor = w.pml_sigma_factor
+    c.kappa_max = w.pml_kappa_max
+    c.alpha_factor = w.pml_alpha_factor
+    c.src_kind = w.src_kind
+    c.src_comp = w.src_component
+    c.src_axis = w.src_axis
+    c.src_pos[:] = list(w.src_pos)
+    c.src_sigma[:] = list(w.src_sigma_uv)
+    c.lambda0 = w.lambda0
+    c.rel_bw = w.rel_bandwidth
+    c.t0_over_tau = w.t0_over_tau
+    c.amplitude = w.amplitude
+    c.det_kind = w.det_kind
+    c.det_axis = w.det_axis
+    c.det_index = w.det_index
+    c.det_lo[:] = list(w.det_lo)
+    c.det_hi[:] = list(w.det_hi)
+    c.dlo[:] = list(w.design_lo)
+    c.dhi[:] = list(w.design_hi)
+    return c
+
+
+def _eps(w) -> np.ndarray:
+    return np.ascontiguousarray(w.eps, dtype=np.float64)
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError(f"oracle call failed with status {rc}")
+
+
+def profiles(w, axis: int, **kw) -> dict:
+    """CPML profile arrays along `axis` (b/a/kinv at E and H positions)."""
+    c = make_cfg(w, **kw)
+    n = (w.nx, w.ny, w.nz)[axis]
+    out = np.zeros(6 * n)
+    _check(lib().oracle_profiles(C.byref(c), axis, _dp(out)))
+    out = out.reshape(6, n)
+    return dict(b_e=out[0], a_e=out[1], kinv_e=out[2], b_h=out[3], a_h=out[4], kinv_h=out[5])
+
+
+def waveform(w, **kw) -> np.ndarray:
+    c = make_cfg(w, **kw)
+    out = np.zeros(c.n_steps)
+    _check(lib().oracle_waveform(C.byref(c), _dp(out)))
+    return out
+
+
+def source_weight(w, **kw) -> np.ndarray:
+    c = make_cfg(w, **kw)
+    out = np.zeros((w.nz, w.ny, w.nx))
+    _check(lib().oracle_source_weight(C.byref(c), _dp(out)))
+    return out
+
+
+def zero_state(w) -> np.ndarray:
+    return np.zeros((NF, w.nz, w.ny, w.nx))
+
+
+def step(w, state: np.ndarray, n: int, **kw) -> float:
+    """One forward step in place; returns l_n."""
+    c = make_cfg(w, **kw)
+    obj = np.zeros(1)
+    _check(lib().oracle_step(C.byref(c), _dp(_eps(w)), _dp(state), n, _dp(obj)))
+    return float(obj[0])
+
+
+def run(w, state: np.ndarray, n0: int = 0, count=None, **kw) -> np.ndarray:
+    """count forward steps in place from step n0; returns per-step l_n."""
+    c = make_cfg(w, **kw)
+    count = c.n_steps if count is None else count
+    obj = np.zeros(max(count, 1))
+    _check(lib().oracle_run(C.byref(c), _dp(_eps(w)), _dp(state), n0, count, _dp(obj)))
+    return obj[:count]
+
+
+def forward(w, **kw):
+    """Forward run from the zero state: (final state, per-step objective)."""
+    st = zero_state(w)
+    obj = run(w, st, **kw)
+    return st, obj
+
+
+def step_adjoint(w, lam: np.ndarray, **kw) -> None:
+    c = make_cfg(w, **kw)
+    _check(lib().oracle_step_adjoint(C.byref(c), _dp(_eps(w)), _dp(lam)))
+
+
+def unstep(w, state: np.ndarray, n: int, **kw) -> None:
+    c = make_cfg(w, **kw)
+    _check(lib().oracle_unstep(C.byref(c), _dp(_eps(w)), _dp(state), n))
+
+
+def gradient(w, seed: float = 1.0, want_state: bool = False, **kw):
+    """Exact discrete gradient dL/d(eps) over the design box (stored history).
+    Returns (L, grad[dz][dy][dx]) or (L, grad, final_state)."""
+    c = make_cfg(w, **kw)
+    g = np.zeros(w.design_shape)
+    obj = np.zeros(1)
+    fs = zero_state(w) if want_state else None
+    _check(lib().oracle_gradient(C.byref(c), _dp(_eps(w)), seed, _dp(g), _dp(obj),
+                                 _dp(fs) if want_state else None))
+    return (float(obj[0]), g, fs) if want_state else (float(obj[0]), g)
+
+
+def n_samples(n_steps: int, k: int) -> int:
+    r = (n_steps - 1) % k
+    return (n_steps - 1 - r) // k + 1
+
+
+def sample_values(w, **kw) -> int:
+    c = make_cfg(w, **kw)
+    return int(lib().oracle_sample_values(C.byref(c)))
+
+
+def reverse(w, fmt: str = "none", scaled: bool = False, k: int = 1, interp: str = "linear",
+            seed: float = 1.0, want_tape: bool = False, **kw):
+    """The method in FP64: recorded + compressed interface slices, then the
+    time-reversed simulation with the adjoint.  Returns (L, grad[, tape])."""
+    c = make_cfg(w, **kw)
+    g = np.zeros(w.design_shape)
+    obj = np.zeros(1)
+    tape = None
+    if want_tape:
+        tape = np.zeros((n_samples(c.n_steps, k), sample_values(w, **kw)))
+    _check(lib().oracle_reverse(C.byref(c), _dp(_eps(w)), FMT[fmt], int(scaled), k,
+                                0 if interp == "linear" else 1, seed, _dp(g), _dp(obj),
+                                _dp(tape) if want_tape else None))
+    return (float(obj[0]), g, tape) if want_tape else (float(obj[0]), g)
+
+
+def quantize(fmt: str, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.zeros_like(x)
+    _check(lib().oracle_quantize_array(FMT[fmt], _dp(x), _dp(out), x.size))
+    return out
+
+
+def format_max(fmt: str) -> float:
+    return float(lib().oracle_format_max(FMT[fmt]))
+
+
+def interp_series(kind: str, t, p, q) -> np.ndarray:
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros_like(q)
+    _check(lib().oracle_interp_series(0 if kind == "linear" else 1, t.size, _dp(t), _dp(p),
+                                      q.size, _dp(q), _dp(out)))
+    return out
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().oracle_set_num_threads(int(n))

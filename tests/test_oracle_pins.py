@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test ties one part of the oracle to something the paper or the
+mathematics fixes: the paper's printed numbers (Eq. 1 and the text after it),
+the Yee dispersion relation (closed form), the discrete leapfrog energy
+(invariant), exact time reversal, the transpose identity <v, F u> = <F^T v, u>,
+brute-force central differences, library float casts and polynomial
+exactness of the interpolants.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import golden
+from oracle import oracle as O
+from paper_2603_24027_gb300 import inputs as I
+
+C0 = 299792458.0
+
+
+def box(nx, ny, nz, P=0, n_steps=10, eps=None, **kw):
+    eps = np.ones((nz, ny, nx), np.float32) if eps is None else eps
+    base = dict(name="t", nx=nx, ny=ny, nz=nz, dx=20e-9, dt=I.cfl_dt(20e-9), n_steps=n_steps,
+                pml_thickness=P, eps=eps, design_lo=(P, P, P), design_hi=(nx - P, ny - P, nz - P),
+                src_kind=I.SRC_NONE, det_kind=0)
+    base.update(kw)
+    return I.Workload(**base)
+
+
+# ------------------------------------------------------------ Eq. 1 -------
+
+def test_eq1_numbers_from_the_paper():
+    g = golden("paper_numbers.txt")
+    assert I.COURANT == g["courant_factor"][0]
+    assert I.C0 == g["speed_of_light_m_s"][0]
+    dt = I.cfl_dt(20e-9)
+    v, tol = g["dt_at_dx20nm_s"]
+    assert abs(dt - v) / v < tol
+    v, tol = g["period_1550nm_s"]
+    period = 1550e-9 / C0
+    assert abs(period - v) / v < tol
+    v, tol = g["steps_per_period_1550nm"]
+    assert abs(period / dt - v) / v < tol
+
+
+def test_waveform_carrier_period_matches_paper():
+    """Zero crossings of the oracle's source waveform at dx = 20 nm are spaced
+    by half of ~136 steps (Sec. 2: 1550 nm ~ 136 time steps)."""
+    w = box(8, 8, 8, n_steps=4000, src_kind=I.SRC_POINT, src_pos=(4, 4, 4), t0_over_tau=3.0)
+    g = O.waveform(w)
+    s = np.sign(g)
+    idx = np.nonzero((s[:-1] * s[1:]) < 0)[0]
+    # keep crossings where the envelope is well above rounding
+    env = np.abs(g).max()
+    good = [i for i in idx if max(abs(g[i - 30:i + 30]).max(), 0) > 1e-3 * env]
+    # sub-step crossing positions by linear interpolation
+    xs = np.array([i + g[i] / (g[i] - g[i + 1]) for i in good])
+    half = np.diff(xs).mean()
+    steps_per_period = golden("paper_numbers.txt")["steps_per_period_1550nm"][0]
+    assert abs(2 * half - steps_per_period) / steps_per_period < 1e-2
+    # closed form lambda0 / (S dx) with S = 0.99/sqrt(3)
+    S = C0 * w.dt / w.dx
+    assert abs(2 * half - 1550e-9 / (S * 20e-9)) < 0.05
+
+
+def test_waveform_bandwidth_is_30_percent_fwhm():
+    """Power-spectrum FWHM of the pulse equals rel_bandwidth * w0."""
+    w = box(8, 8, 8, n_steps=20000, src_kind=I.SRC_POINT, src_pos=(4, 4, 4), t0_over_tau=6.0)
+    g = O.waveform(w)
+    n = 1 << 18
+    spec = np.abs(np.fft.rfft(g, n)) ** 2
+    f = np.fft.rfftfreq(n)               # cycles per step
+    k = spec.argmax()
+    half = spec[k] / 2
+    lo = np.nonzero(spec[:k] < half)[0][-1]
+    hi = k + np.nonzero(spec[k:] < half)[0][0]
+    fwhm = f[hi] - f[lo]
+    S = C0 * w.dt / w.dx
+    f0 = S * w.dx / w.lambda0            # cycles per step
+    assert abs(f[k] - f0) / f0 < 2e-3
+    assert abs(fwhm / f0 - 0.3) < 5e-3
+
+
+# ------------------------------------------------ Yee dispersion ----------
+
+@pytest.mark.parametrize("mode", ["Ez_xy", "Ex_yz", "Ey_zx"])
+@pytest.mark.parametrize("eps_r", [1.0, 2.25])
+def test_yee_dispersion_closed_form(mode, eps_r):
+    """A transverse standing mode cos(k.r) on a periodic grid obeys
+    E^{n+1} + E^{n-1} = (2 - 4 (S^2/eps) sum_i sin^2(k_i/2)) E^n exactly
+    (discrete curl-curl eigenvalue); a sign or index error in any of the
+    curl terms used by the mode breaks it."""
+    nx, ny, nz = 16, 12, 10
+    eps = np.full((nz, ny, nx), eps_r, np.float32)
+    w = box(nx, ny, nz, eps=eps, n_steps=60)
+    kx, ky, kz = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny, 2 * np.pi * 1 / nz
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    st = O.zero_state(w)
+    comp, ks = {"Ez_xy": (2, (kx, ky)), "Ex_yz": (0, (ky, kz)), "Ey_zx": (1, (kz, kx))}[mode]
+    phase = {"Ez_xy": kx * x + ky * y, "Ex_yz": ky * y + kz * z, "Ey_zx": kz * z + kx * x}[mode]
+    st[comp] = np.cos(phase)
+    S = C0 * w.dt / w.dx
+    coef = 2 - 4 * S * S / eps_r * sum(math.sin(kk / 2) ** 2 for kk in ks)
+    hist = [st[comp].copy()]
+    for n in range(40):
+        O.step(w, st, n, periodic=1)
+        hist.append(st[comp].copy())
+        others = [c for c in range(3) if c != comp]
+        assert np.abs(st[others]).max() < 1e-12
+    for n in range(1, 40):
+        np.testing.assert_allclose(hist[n + 1] + hist[n - 1], coef * hist[n], atol=1e-12, rtol=0)
+
+
+# ------------------------------------------------------ energy -------------
+
+def test_leapfrog_energy_is_conserved_in_a_zero_padded_box():
+    """W^n = sum eps E^n.E^n + sum Ht^{n-1/2}.Ht^{n+1/2} is invariant for the
+    lossless update when curlH is the transpose of curlE (zero padding)."""
+    nx, ny, nz = 10, 9, 8
+    rng = np.random.default_rng(1)
+    eps = rng.uniform(1.0, 12.25, (nz, ny, nx)).astype(np.float32)
+    w = box(nx, ny, nz, eps=eps, n_steps=2000)
+    st = O.zero_state(w)
+    st[:6] = I.random_state((nz, ny, nx), 7, 6)
+    e64 = eps.astype(np.float64)
+    W = []
+    for n in range(2000):
+        E = st[:3].copy()
+        Hm = st[3:6].copy()
+        O.step(w, st, n)
+        W.append(np.sum(e64 * E * E) + np.sum(Hm * st[3:6]))
+    W = np.array(W)
+    assert W[0] > 0
+    assert np.abs(W / W[0] - 1).max() < 1e-12
+
+
+# ----------------------------------------------------- reversal -----------
+
+def test_exact_time_reversal_without_pml():
+    """N steps forward then N inverse steps recover (E^0, Ht^{-1/2}) to FP64
+    rounding (the premise of time-reversible gradients, Sec. 1)."""
+    nx, ny, nz = 12, 11, 9
+    rng = np.random.default_rng(2)
+    eps = rng.uniform(1.0, 12.25, (nz, ny, nx)).astype(np.float32)
+    w = box(nx, ny, nz, eps=eps, n_steps=300, src_kind=I.SRC_POINT, src_component=1,
+            src_pos=(5, 4, 3), t0_over_tau=0.3)
+    st = O.zero_state(w)
+    st[:6] = I.random_state((nz, ny, nx), 3, 6)
+    init = st[:6].copy()
+    O.run(w, st, 0, 300)
+    assert np.abs(st[:6] - init).max() > 0.1
+    for n in range(299, -1, -1):
+        O.unstep(w, st, n)
+    assert np.abs(st[:6] - init).max() < 1e-11 * np.abs(init).max()
+
+
+# -------------------------------------------------- CPML structure ---------
+
+def test_cpml_profiles_vanish_exactly_on_the_lossless_interior():
+    """Interior cells [P, N-P) must see b = a = 0 and 1/kappa = 1 at both the
+    E and H positions, and every PML cell must be lossy, so the interior
+    update is exactly invertible and the layer absorbs."""
+    w = I.small_dipole()
+    P = w.pml_thickness
+    for ax, n in enumerate((w.nx, w.ny, w.nz)):
+        pr = O.profiles(w, ax)
+        inner = slice(P, n - P)
+        for key in ("b_e", "a_e", "b_h", "a_h"):
+            assert np.all(pr[key][inner] == 0.0)
+        assert np.all(pr["kinv_e"] == 1.0) and np.all(pr["kinv_h"] == 1.0)
+        for key in ("a_e", "a_h"):
+            assert np.all(pr[key][:P] < 0) and np.all(pr[key][n - P:] < 0)
+        for key in ("b_e", "b_h"):
+            assert np.all((pr[key][:P] > 0) & (pr[key][:P] < 1))
+        # grading deepens toward the outer faces on both sides
+        assert np.all(np.diff(pr["b_e"][:P]) > 0) and np.all(np.diff(pr["b_h"][n - P:]) < 0)
+        # mirror symmetry of the Yee grid: E positions on the low side match
+        # H positions on the high side
+        np.testing.assert_allclose(pr["b_e"][:P], pr["b_h"][n - P:][::-1], rtol=1e-15)
+        np.testing.assert_allclose(pr["b_h"][:P], pr["b_e"][n - P:][::-1], rtol=1e-15)
+
+
+def test_cpml_absorbs_an_outgoing_pulse():
+    """A dipole pulse radiating in vacuum leaves the box through the CPML: the
+    field energy left in the interior long after the pulse is below 1e-9 of
+    its peak, while with the absorbing profiles switched off the radiated
+    share (~1e-4 of the peak) stays in the box."""
+    n, P, T = 40, 10, 1500
+    # t0 = 4 tau: the pulse starts from ~0 and carries no DC current, which
+    # would otherwise leave a static dipole field behind.
+    w = box(n, n, n, P=P, n_steps=T, src_kind=I.SRC_POINT, src_component=2,
+            src_pos=(20, 20, 20), t0_over_tau=4.0, dx=25e-9, dt=I.cfl_dt(25e-9))
+    inner = (slice(P, n - P),) * 3
+
+    def energy_trace(wl):
+        st = O.zero_state(wl)
+        out = []
+        for s in range(0, T, 100):
+            O.run(wl, st, s, 100)
+            out.append(sum(np.sum(st[c][inner] ** 2) for c in range(6)))
+        return np.array(out)
+
+    e_pml = energy_trace(w)
+    e_off = energy_trace(w.replace(pml_sigma_factor=0.0, pml_alpha_factor=0.0))
+    # The peak is dominated by the dipole's reactive near field; what radiates
+    # is ~1e-4 of it.  Lossless layers keep that share, the CPML removes it.
+    assert e_pml[-1] < 1e-9 * e_pml.max()
+    assert e_off[-1] > 1e-5 * e_off.max()
+
+
+# -------------------------------------------------- transpose ---------------
+
+@pytest.mark.parametrize("kappa", [1.0, 3.0])
+def test_adjoint_step_is_the_transpose(kappa):
+    """<v, F u> = <F^T v, u> for one step on the full state (fields and all 12
+    psi arrays) with CPML on every face, random eps and kappa grading."""
+    nx, ny, nz, P = 14, 12, 11, 3
+    rng = np.random.default_rng(4)
+    eps = rng.uniform(1.0, 12.25, (nz, ny, nx)).astype(np.float32)
+    w = box(nx, ny, nz, P=P, eps=eps, pml_kappa_max=kappa)
+    u = I.random_state((nz, ny, nx), 11, O.NF)
+    v = I.random_state((nz, ny, nx), 12, O.NF)
+    Fu = u.copy()
+    O.step(w, Fu, 0)
+    Ftv = v.copy()
+    O.step_adjoint(w, Ftv)
+    lhs, rhs = np.sum(v * Fu), np.sum(Ftv * u)
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(v * Fu).sum())
+
+
+def test_adjoint_of_three_steps_composes():
+    nx, ny, nz, P = 11, 10, 9, 2
+    rng = np.random.default_rng(5)
+    eps = rng.uniform(1.0, 12.25, (nz, ny, nx)).astype(np.float32)
+    w = box(nx, ny, nz, P=P, eps=eps)
+    u = I.random_state((nz, ny, nx), 21, O.NF)
+    v = I.random_state((nz, ny, nx), 22, O.NF)
+    Fu = u.copy()
+    for n in range(3):
+        O.step(w, Fu, n)
+    Ftv = v.copy()
+    for n in range(3):
+        O.step_adjoint(w, Ftv)
+    assert abs(np.sum(v * Fu) - np.sum(Ftv * u)) <= 1e-13 * np.abs(v * Fu).sum()
+
+
+# ------------------------------------------------ finite differences --------
+
+def _fd_check(w, cells, h, rtol):
+    L0, g = O.gradient(w)
+    gmax = np.abs(g).max()
+    for (z, y, x) in cells:
+        e = w.eps.astype(np.float64)
+        c = (z + w.design_lo[2], y + w.design_lo[1], x + w.design_lo[0])
+        ep, em = e.copy(), e.copy()
+        ep[c] += h
+        em[c] -= h
+        Lp = O.forward(w.replace(eps=ep))[1].sum()
+        Lm = O.forward(w.replace(eps=em))[1].sum()
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g[z, y, x]) <= rtol * gmax, (c, fd, g[z, y, x])
+    return L0, g
+
+
+def test_gradient_matches_central_differences_on_every_design_cell():
+    """Brute force on an 8^3 grid (2-cell CPML, 4^3 design = interior,
+    |E|^2 objective, point source): all 64 cells."""
+    w = I.fd_cube()
+    cells = [(z, y, x) for z in range(4) for y in range(4) for x in range(4)]
+    L0, g = _fd_check(w, cells, 1e-5, 1e-7)
+    assert L0 > 0 and np.abs(g).max() > 0
+
+
+def test_gradient_matches_central_differences_poynting_plane_source():
+    """Poynting objective and Gaussian plane source on an odd-sized grid."""
+    w = I.ragged_box(nx=13, ny=11, nz=10, P=2, n_steps=50)
+    rng = np.random.default_rng(6)
+    shp = w.design_shape
+    cells = [tuple(int(rng.integers(0, s)) for s in shp) for _ in range(12)]
+    L0, g = _fd_check(w, cells, 1e-5, 1e-7)
+    assert np.abs(g).max() > 0
+
+
+# ----------------------------------------- the method vs the definition -----
+
+@pytest.mark.parametrize("maker", [I.fd_cube, lambda: I.ragged_box(nx=15, ny=12, nz=11, P=3, n_steps=70)])
+def test_time_reversed_gradient_with_exact_samples_equals_stored_history(maker):
+    """With unquantised samples at every step (k = 1) the time-reversed
+    simulation reproduces the exact discrete gradient (Sec. 1-2): this pins the
+    choice of recorded layers and their half-step alignment.  The oracle sets
+    every value outside the interior and the recorded layers to NaN first."""
+    w = maker()
+    L, g = O.gradient(w)
+    L2, g2 = O.reverse(w, "none", k=1)
+    assert L2 == pytest.approx(L, rel=1e-14)
+    assert np.isfinite(g2).all()
+    assert np.linalg.norm(g2 - g) <= 1e-11 * np.linalg.norm(g)
+
+
+def test_subsampled_exact_samples_converge_with_k():
+    """Linear interpolation of exact samples: the gradient error shrinks as k
+    decreases (Sec. 2, Fig. 1b)."""
+    w = I.ragged_box(nx=15, ny=12, nz=11, P=3, n_steps=120)
+    _, g = O.gradient(w)
+    errs = []
+    for k in (8, 4, 2):
+        _, gk = O.reverse(w, "none", k=k)
+        errs.append(np.linalg.norm(gk - g) / np.linalg.norm(g))
+    assert errs[0] > errs[1] > errs[2] > 0
+
+
+# --------------------------------------------------------- codecs ------------
+
+TORCH_DT = {"bf16": "bfloat16", "f16": "float16", "e4m3": "float8_e4m3fn"}
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16", "e4m3"])
+def test_quantizer_matches_library_casts(fmt):
+    """RNE onto bf16 / fp16 / e4m3fn equals torch's float32 casts bit for bit
+    on float32 inputs spanning normals, subnormals and exact ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    fmax = O.format_max(fmt)
+    mags = np.exp(rng.uniform(np.log(fmax) - 40, np.log(fmax), 20000))
+    x = (mags * rng.choice([-1, 1], mags.size)).astype(np.float32)
+    # exact ties halfway between neighbours of the target format
+    t = torch.from_numpy(x).to(getattr(torch, TORCH_DT[fmt])).to(torch.float64).numpy()
+    up = np.nextafter(np.abs(t).astype(np.float32), np.float32(np.inf))
+    nxt = torch.from_numpy(up).to(getattr(torch, TORCH_DT[fmt])).to(torch.float64).numpy()
+    ties = (np.abs(t) + (np.abs(nxt) - np.abs(t)) / 2).astype(np.float32)
+    ties = ties[np.abs(ties) <= fmax]
+    xs = np.concatenate([x, ties, -ties, np.float32([0.0, fmax, -fmax])])
+    ref = torch.from_numpy(xs).to(getattr(torch, TORCH_DT[fmt])).to(torch.float64).numpy()
+    got = O.quantize(fmt, xs.astype(np.float64))
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_quantizer_fp32_and_saturation():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(5000) * 10.0 ** rng.uniform(-40, 30, 5000)
+    np.testing.assert_array_equal(O.quantize("f32", x), x.astype(np.float32).astype(np.float64))
+    assert O.quantize("e4m3", [1e6])[0] == 448.0 and O.quantize("e4m3", [-1e6])[0] == -448.0
+    assert O.quantize("f16", [1e9])[0] == 65504.0
+
+
+def test_compression_factor_of_the_paper():
+    """(32 / bits) x k: float8 with k = 16 gives the paper's 64x."""
+    v = golden("paper_numbers.txt")["compression_e4m3b11fnuz_k16"][0]
+    assert (32 // 8) * 16 == v
+
+
+# --------------------------------------------------- interpolation -----------
+
+def test_linear_interpolation_is_exact_on_affine_series():
+    t = np.array([-1.0, 2, 6, 10, 14])
+    p = 0.25 - 1.5 * t
+    q = np.linspace(-1, 14, 61)
+    np.testing.assert_allclose(O.interp_series("linear", t, p, q), 0.25 - 1.5 * q, atol=1e-13)
+
+
+def test_cubic_interpolation_is_exact_on_quadratics_with_uneven_knots():
+    t = np.array([-1.0, 3, 7, 11, 15, 19])           # first gap 4, like the zero knot
+    t2 = np.array([0.0, 2, 7, 12, 17])               # first gap 2
+    for tt in (t, t2):
+        p = 0.5 + 0.3 * tt - 0.07 * tt * tt
+        q = np.linspace(tt[0], tt[-1], 97)
+        np.testing.assert_allclose(O.interp_series("cubic", tt, p, q),
+                                   0.5 + 0.3 * q - 0.07 * q * q, atol=1e-12)
+
+
+def test_cubic_on_uniform_knots_is_catmull_rom():
+    t = np.arange(0.0, 40.0, 4.0)
+    rng = np.random.default_rng(9)
+    p = rng.standard_normal(t.size)
+    q = 13.0                      # between t[3] = 12 and t[4] = 16
+    s = 0.25
+    cr = 0.5 * ((2 * p[4 - 1]) + (-p[2] + p[4]) * s + (2 * p[2] - 5 * p[3] + 4 * p[4] - p[5]) * s * s
+                + (-p[2] + 3 * p[3] - 3 * p[4] + p[5]) * s ** 3)
+    assert O.interp_series("cubic", t, p, [q])[0] == pytest.approx(cr, rel=1e-13)
+
+
+@pytest.mark.parametrize("k", [2, 4, 8, 16, 32])
+def test_sine_at_136_steps_per_period(k):
+    """Fig. 1b analogue: a sine at 136 steps per period sampled every k steps.
+    Linear interpolation error is at most h^2 w^2 / 8 (h = k steps) and
+    reaches at least 70% of it; cubic is well below linear."""
+    w = 2 * np.pi / 136.0
+    t = np.arange(0.0, 1000.0, k)
+    p = np.sin(w * t)
+    q = np.arange(0.0, t[-1] + 1, 1.0)
+    lin = np.abs(O.interp_series("linear", t, p, q) - np.sin(w * q)).max()
+    bound = (k * w) ** 2 / 8
+    assert lin <= bound * (1 + 1e-9)
+    if k >= 4:
+        assert lin >= 0.7 * bound
+    inner = (q > t[1]) & (q < t[-2])
+    cub = np.abs(O.interp_series("cubic", t, p, q) - np.sin(w * q))[inner].max()
+    # cubic's edge shrinks as sampling approaches Nyquist (4.25 samples/period at k = 32)
+    assert cub < (0.2 if k <= 16 else 0.5) * lin
