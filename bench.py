@@ -1,0 +1,444 @@
+"""Benchmark: gradient throughput of the time-reversible FDTD on one or more GPUs.
+
+One step = one forward run (n_steps leapfrog steps recording the compressed
+boundary tape) plus one backward run (time-reversed interior, tape restore,
+adjoint, dL/d(eps)) of the waveguide workload: 200 x 200 x 100 cells at
+20 nm, 12-cell CPML, 2000 steps, BF16 tape every 4th step with linear
+interpolation.  Metric: cell-updates per second of the whole gradient,
+nx*ny*nz*n_steps / (T_forward + T_backward), cells including the CPML.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank computes its own design (independent
+problems, no data-path collective) and rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+reverse grad Gcell-updates/s & HBM roofline %; tape bytes at stated grad err"
+UNIT = "Gcell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--tape", default="bf16:4:linear")
+    p.add_argument("--compare-tape", default="f32:1:linear")
+    p.add_argument("--kernel", type=int, default=-1, help="0 split, 1 fused, -1 library default")
+    p.add_argument("--sample-every", type=int, default=50)
+    p.add_argument("--cpu-sample-steps", type=int, default=24)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank: int, n_steps=None):
+    from paper_2603_24027_gb300 import inputs as I
+    w = I.waveguide_mid(seed=rank)
+    return w if n_steps is None else w.replace(n_steps=n_steps)
+
+
+# ------------------------------------------------------------ roofline ---
+
+def cell_classes(w):
+    """Counts of cells by (interior?, number of CPML slab axes, in design box?)."""
+    P = w.pml_thickness
+    ax = []
+    for n in (w.nx, w.ny, w.nz):
+        s = np.zeros(n, np.int64)
+        s[:P] = 1
+        s[n - P:] = 1
+        ax.append(s)
+    slabs = ax[2][:, None, None] + ax[1][None, :, None] + ax[0][None, None, :]
+    design = np.zeros(w.shape, bool)
+    design[w.design_slice()] = True
+    interior = slabs == 0
+    return dict(interior=int(interior.sum()), design=int(design.sum()),
+                slab_axes=int(slabs.sum()), cells=w.n_cells)
+
+
+def algorithmic_bytes(w):
+    """Minimum HBM bytes per launch of each kernel kind (FP32 = 4 B, FP64 accumulator 8 B).
+    Split kernels move one field family per launch; fused kernels read the
+    state once and write it once (ping-pong)."""
+    c = cell_classes(w)
+    n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
+    npml = n - ni
+    return {
+        # read E,H; write H (36 B); CPML: 2 psi read + 2 written per slab axis
+        "fwd_h": 36 * n + 16 * sa,
+        # read H,E,cb; write E (40 B); CPML as above
+        "fwd_e": 40 * n + 16 * sa,
+        # interior: read H,E,cb,lamE,lamH, write E,lamH (76 B); others 40 B; design 16 B
+        "rev_e": 76 * ni + 40 * npml + 16 * nd + 16 * sa,
+        # interior: read E,H,lamH,lamE, write H,lamE (72 B); others 36 B
+        "rev_h": 72 * ni + 36 * npml + 16 * sa,
+        # read E,H,cb, write E,H (52 B); 4 psi read + 4 written per slab axis
+        "fused_fwd": 52 * n + 32 * sa,
+        # interior: primal 12+12... read E,H,lamE,lamH,cb, write E,H,lamE,lamH (100 B);
+        # CPML-side cells adjoint only (52 B); design +16 B; psi 32 B per slab axis
+        "fused_rev": 100 * ni + 52 * npml + 16 * nd + 32 * sa,
+    }
+
+
+def record_bytes(w, dtype_bytes):
+    P = w.pml_thickness
+    a, b, c = w.nx - 2 * P, w.ny - 2 * P, w.nz - 2 * P
+    vals = 4 * (b * c + a * c + a * b)
+    return vals * (4 + dtype_bytes)
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic(kernel: str, digest: str):
+    """ncu DRAM bytes per launch recorded for this kernel build, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split("#", 1)[0].split()
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest and parts[2] == "waveguide200":
+                return float(parts[3])
+    return None
+
+
+# -------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.err = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception as e:  # nvidia-smi missing
+            self.err = str(e)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if self.err or not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "note": self.err or "no nvidia-smi samples"}
+        sm, mx, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for_smi(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts):
+            return parts[local_rank].strip()
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------- ours ---
+
+def tape_cfg(A, spec: str):
+    dt, k, interp = spec.split(":")
+    return A.record_cfg(dt, int(k), interp)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2603_24027_gb300 import build as B
+    B.build()
+    from paper_2603_24027_gb300 import _capi as A
+    from paper_2603_24027_gb300 import fdtd
+
+    w = workload(rank)
+    rec = tape_cfg(A, args.tape)
+    sim = fdtd.Simulation(w, device=dev)
+    if args.kernel >= 0:
+        sim.set_option(A.OPT_KERNEL, args.kernel)
+    sim.set_option(A.OPT_SAMPLE_EVERY, args.sample_every)
+    eps = torch.from_numpy(w.eps).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def step(s, r):
+        s.forward(eps, r)
+        return s.backward(1.0)
+
+    for _ in range(max(3, args.warmup)):
+        step(sim, rec)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    fwd_ms, bwd_ms, ktimes = [], [], {}
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(gpu_index_for_smi(local)) as clk:
+        for i in range(args.steps):
+            flush.random_(0, 255)              # evict L2 (129 MB) before each timed step
+            starts[i].record()
+            g = step(sim, rec)
+            ends[i].record()
+            t = sim.last_timing()
+            fwd_ms.append(t["fwd_ms"])
+            bwd_ms.append(t["bwd_ms"])
+            for name, (ms, n) in sim.kernel_timing().items():
+                ktimes.setdefault(name, []).append((ms, n))
+        torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = sim.last_timing()
+    gpu_launches = (launches["fwd_launches"] + launches["bwd_launches"] + 2) * args.steps
+    cell_updates = w.n_cells * w.n_steps
+    value = ws * cell_updates * args.steps / (total_ms / 1e3) / 1e9
+
+    # per-kernel live timing (sampled launches, CUDA events on the library stream)
+    algo = algorithmic_bytes(w)
+    peak, peak_kind = read_peaks()
+    per_step = {"fwd_h": w.n_steps, "fwd_e": w.n_steps, "rev_e": w.n_steps, "rev_h": w.n_steps,
+                "fused_fwd": w.n_steps, "fused_rev": w.n_steps,
+                "record": -(-w.n_steps // rec.k), "restore_seed": w.n_steps}
+    kern = {}
+    for name, lst in ktimes.items():
+        n = sum(c for _, c in lst)
+        avg = sum(ms * c for ms, c in lst) / max(n, 1)
+        share = avg * per_step[name] / (total_ms / args.steps)
+        d = {"avg_ms": avg, "sampled_launches": n, "share_of_step": share}
+        if name in algo:
+            d["algorithmic_bytes"] = algo[name]
+            d["achieved_gbs"] = algo[name] / (avg / 1e3) / 1e9
+        kern[name] = d
+    dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["share_of_step"])
+    digest = B._digest()
+    traffic = read_traffic(dom, digest)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"],
+                "peak": peak, "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
+                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": algo[dom]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded waveguide: Si strip in SiO2, smoothed random design)",
+        "config": {"workload": w.name, "cells": w.n_cells, "n_steps": w.n_steps,
+                   "pml": w.pml_thickness, "tape": args.tape,
+                   "design_box": list(w.design_shape[::-1]),
+                   "parallelism": f"replicas x{ws}", "l2": "flushed before every timed step",
+                   "fwd_ms": statistics.median(fwd_ms), "bwd_ms": statistics.median(bwd_ms),
+                   "wall_s": wall},
+        "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "kernels": kern,
+        "clocks": clk.summary(),
+        "tape_bytes": sim.tape_bytes(rec),
+    }
+
+    # the same code with the uncompressed FP32 tape, and gradient agreement
+    if not args.no_compare:
+        rec32 = tape_cfg(A, args.compare_tape)
+        sim32 = fdtd.Simulation(w, device=dev)
+        if args.kernel >= 0:
+            sim32.set_option(A.OPT_KERNEL, args.kernel)
+        for _ in range(2):
+            g32 = step(sim32, rec32)
+        torch.cuda.synchronize()
+        ts = []
+        for i in range(args.steps):
+            flush.random_(0, 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g32 = step(sim32, rec32)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        v32 = cell_updates / (sum(ts) / args.steps / 1e3) / 1e9
+        g64, g3264 = g.double(), g32.double()
+        cosv = float((g64 * g3264).sum() / (g64.norm() * g3264.norm()))
+        relv = float((g64 - g3264).norm() / g3264.norm())
+        out["compare"] = {"tape": args.compare_tape, "value": v32,
+                          "tape_bytes": sim32.tape_bytes(rec32),
+                          "tape_reduction": sim32.tape_bytes(rec32) / sim.tape_bytes(rec),
+                          "speedup_vs_compare": value / ws / v32,
+                          "grad_cosine": cosv, "grad_rel_err": relv}
+        del sim32
+
+    # end to end through the public host-buffer call
+    eps_h = torch.from_numpy(w.eps).pin_memory()
+    grad_h = torch.empty(w.design_shape, dtype=torch.float32).pin_memory()
+    sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
+    barrier()
+    torch.cuda.synchronize()
+    te = []
+    for i in range(args.steps):
+        flush.random_(0, 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
+        te.append(time.perf_counter() - t0)
+    e2e_t = sum(te)
+    if ws > 1:
+        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    nd = int(np.prod(w.design_shape))
+    out["e2e"] = {"value": ws * cell_updates * args.steps / e2e_t / 1e9, "unit": UNIT,
+                  "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- oracle ---
+
+def oracle_step(n_steps: int):
+    from oracle import oracle as O
+    w = workload(0, n_steps=n_steps)
+    t0 = time.perf_counter()
+    O.gradient(w)
+    return time.perf_counter() - t0, w
+
+
+def cpu_baseline(n_steps: int):
+    from oracle import build as ob
+    from oracle import oracle as O
+    ob.build()
+    dt, w = oracle_step(n_steps)
+    return {"value": w.n_cells * w.n_steps / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle gradient (forward + stored-history adjoint) of the same "
+                      f"200x200x100 workload truncated to {n_steps} steps; {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as ob
+    from oracle import oracle as O
+    ob.build()
+    n = args.cpu_sample_steps
+    for _ in range(max(3, args.warmup)):
+        oracle_step(max(2, n // 4))
+    ts = []
+    for _ in range(args.steps):
+        dt, w = oracle_step(n)
+        ts.append(dt)
+    value = w.n_cells * n * len(ts) / sum(ts) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": 1e3 * sum(ts) / len(ts),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "cells": w.n_cells, "n_steps_sample": n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"each step: FP64 oracle gradient of the 200x200x100 "
+                                      f"workload over {n} steps"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

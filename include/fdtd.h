@@ -1,0 +1,227 @@
+/*
+ * fdtd.h -- C ABI of the GB300 time-reversible FDTD gradient library.
+ *
+ * The library computes L(eps) = sum_n l_n and dL/d(eps_r) for a 3D Yee FDTD
+ * with a convolutional PML, using the time-reversible gradient of the paper
+ * (Sec. 1-2): the forward run records only the fields on the interface
+ * slices between the simulation volume and the PML, compressed by reduced
+ * bit-width and by keeping every k-th step; the backward run reverses the
+ * lossless interior in time, injects the recorded slices back (interpolated
+ * in time) and runs the adjoint alongside.
+ *
+ * Units: normalised fields E and Ht = eta0 H; S = c dt / dx (Eq. 1 with
+ * C = 0.99 gives S = 0.99/sqrt(3)).  Arrays are float32 [nz][ny][nx], x
+ * fastest, contiguous.  Grid cells [P, N-P) along every axis form the
+ * interior; the design box must lie inside it.
+ *
+ * Memory: the caller owns every device buffer (eps, gradient, workspace) and
+ * the CUDA stream; the library never calls cudaMalloc.  Calls return an
+ * fdtd_status and never throw; fdtd_last_error() gives a message.  One
+ * handle must not be used from two threads at once.
+ */
+#ifndef FDTD_GB300_H
+#define FDTD_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_ABI_VERSION 1
+
+typedef enum {
+  FDTD_OK = 0,
+  FDTD_EINVAL = -1,     /* bad argument (message in fdtd_last_error) */
+  FDTD_ENOMEM = -2,     /* workspace missing or too small; host allocation failed */
+  FDTD_ECUDA = -3,      /* a CUDA runtime call failed */
+  FDTD_ESTATE = -4,     /* call out of order (e.g. backward without forward) */
+  FDTD_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  FDTD_ENONFINITE = -6  /* eps < 1 or non-finite, or a non-finite result */
+} fdtd_status;
+
+typedef struct fdtd_handle fdtd_handle;
+
+typedef struct { int nx, ny, nz; } fdtd_grid;
+
+/* Convolutional PML (Roden & Gedney, cited in Sec. 1) on all six faces.
+ * Grading over the depth d in (0,1] from the interface:
+ *   sigma dt/eps0 = sigma_factor (order+1) S d^order,
+ *   kappa = 1 + (kappa_max-1) d^order,
+ *   alpha dt/eps0 = alpha_factor 2 pi f0 dt (1-d),  f0 = c / lambda0.
+ * Zero or negative fields select the defaults 3 / 0.8 / 1 / 0.05. */
+typedef struct {
+  int thickness;          /* P >= 1 cells */
+  int order;
+  double sigma_factor;
+  double kappa_max;
+  double alpha_factor;
+} fdtd_pml;
+
+enum { FDTD_SRC_NONE = 0, FDTD_SRC_POINT = 1, FDTD_SRC_PLANE_GAUSS = 2 };
+
+/* Current source J entering E += (S/eps)(curl Ht - J).
+ * J^{n+1/2} = amplitude w(u,v) g((n+1/2) dt),
+ * g(t) = exp(-((t-t0)/tau)^2) sin(w0 (t-t0)), w0 = 2 pi c / lambda0,
+ * tau = 2 sqrt(2 ln 2) / (rel_bandwidth w0) (power-spectrum FWHM),
+ * t0 = t0_over_tau tau.
+ * POINT: w = 1 at pos.  PLANE_GAUSS: plane normal `axis` at pos[axis];
+ * w = exp(-(u-pos_u)^2/(2 su^2) - (v-pos_v)^2/(2 sv^2)) over the interior
+ * cross-section, (u,v) the other two axes in increasing order. */
+typedef struct {
+  int kind;
+  int component;          /* 0..2 = Ex, Ey, Ez */
+  int pos[3];
+  int axis;
+  double sigma_uv[2];
+  double lambda0;         /* metres */
+  double rel_bandwidth;
+  double t0_over_tau;
+  double amplitude;
+} fdtd_source;
+
+enum { FDTD_OBJ_E2_PLANE = 1, FDTD_OBJ_POYNTING_PLANE = 2 };
+
+/* Objective l_n on the plane normal `axis` at `index`, cells (u,v) in
+ * [lo,hi) with (u,v) the other two axes in increasing order:
+ *   E2_PLANE:       l_n = sum |E^{n+1}|^2
+ *   POYNTING_PLANE: l_n = sum (E^{n+1} x Ht^{n+1/2}) . axis
+ * (components co-indexed at each cell; the Poynting detector stands for
+ * the paper's flux detectors, Sec. 3). */
+typedef struct {
+  int kind;
+  int axis;
+  int index;
+  int lo[2];
+  int hi[2];
+} fdtd_detector;
+
+enum { FDTD_TAPE_F32 = 0, FDTD_TAPE_BF16 = 1, FDTD_TAPE_F16 = 2, FDTD_TAPE_E4M3 = 3 };
+enum { FDTD_INTERP_LINEAR = 0, FDTD_INTERP_CUBIC = 1 };
+
+/* Boundary-tape compression (Sec. 2): storage type of the recorded slices,
+ * k = keep every k-th step (the last step is always kept), and the time
+ * interpolation used to restore the steps in between.  scaled = 1 stores a
+ * per-face, per-sample FP32 scale absmax/format_max (F16 and E4M3 only);
+ * values are converted back to FP32 before any arithmetic. */
+typedef struct {
+  int dtype;
+  int k;
+  int interp;
+  int scaled;
+} fdtd_record_cfg;
+
+/* Plan a problem.  Host only: touches no device.  dx in metres, dt in
+ * seconds with c dt / dx <= 1/sqrt(3).  n_steps >= 1.  design box
+ * [lo, hi) inside the interior.  cuda_stream: the caller's stream (NULL =
+ * legacy default stream); all work is ordered after work already queued
+ * there, and later work queued there sees the results.
+ * Errors: FDTD_EINVAL (message in fdtd_last_error(NULL)), FDTD_ENOMEM. */
+int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fdtd_pml* pml,
+                const fdtd_source* source, const fdtd_detector* detector, int n_steps,
+                const int design_lo[3], const int design_hi[3], void* cuda_stream,
+                fdtd_handle** out);
+
+/* Bytes of device workspace needed for forward + backward with `rec`. */
+int fdtd_workspace_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned) as the workspace.
+ * It must stay valid until the handle is destroyed or rebound. */
+int fdtd_bind_workspace(fdtd_handle* h, void* dptr, size_t bytes);
+
+/* Bytes of the compressed boundary tape alone (samples + scales). */
+int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes);
+
+/* Forward run: n_steps leapfrog steps from zero fields with eps (device,
+ * float32 [nz][ny][nx], every value finite and >= 1), recording the
+ * boundary tape; writes L to *objective (host).  Blocks until done.
+ * Keeps the final state for fdtd_backward. */
+int fdtd_forward(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec,
+                 double* objective);
+
+/* Backward run: seed * dL/d(eps) over the design box into d_grad_eps
+ * (device, float32 [dz][dy][dx]).  Needs a preceding fdtd_forward; consumes
+ * its state (FDTD_ESTATE otherwise).  Blocks until done. */
+int fdtd_backward(fdtd_handle* h, double seed, float* d_grad_eps);
+
+/* Both directions with HOST buffers (end-to-end path): copies h_eps to the
+ * device, runs forward and backward, copies seed * dL/d(eps) over the
+ * design box to h_grad.  Pinned host memory makes the copies asynchronous. */
+int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps, const fdtd_record_cfg* rec,
+                             double seed, double* objective, float* h_grad);
+
+/* Batched designs: n independent handles (each with its own workspace)
+ * processed together; objs[i] / d_grads[i] as in fdtd_forward/backward. */
+int fdtd_group_forward(fdtd_handle* const* hs, int n, const float* const* d_eps,
+                       const fdtd_record_cfg* rec, double* objs);
+int fdtd_group_backward(fdtd_handle* const* hs, int n, const double* seeds,
+                        float* const* d_grads);
+
+/* Last error message of h, or of the last failed fdtd_create when h is NULL. */
+const char* fdtd_last_error(const fdtd_handle* h);
+
+/* Release host resources and CUDA objects (not the caller's memory). */
+int fdtd_destroy(fdtd_handle* h);
+
+/* ------------------------------------------------ tuning and timing --- */
+
+enum {
+  FDTD_OPT_USE_GRAPHS = 0,    /* 1 (default): replay the time loop as a CUDA graph */
+  FDTD_OPT_KERNEL = 1,        /* 0: split half-step kernels, 1: fused 2.5D kernels */
+  FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8); width is 32 */
+  FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
+  FDTD_OPT_SAMPLE_EVERY = 4   /* m > 0: time every m-th launch of each kernel kind with
+                                 CUDA events on the library's stream (0 = off) */
+};
+int fdtd_set_option(fdtd_handle* h, int option, int value);
+int fdtd_get_option(const fdtd_handle* h, int option, int* value);
+
+/* Kernel kinds for fdtd_kernel_timing. */
+enum {
+  FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
+  FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_FUSED_FWD = 6, FDTD_K_FUSED_REV = 7,
+  FDTD_K_KINDS = 8
+};
+/* Average device duration (ms) of the sampled launches of one kernel kind
+ * in the last forward + backward, and how many launches were sampled
+ * (FDTD_OPT_SAMPLE_EVERY must be > 0). */
+int fdtd_kernel_timing(const fdtd_handle* h, int kind, float* avg_ms, int* samples);
+
+/* Device time (CUDA events on the library's stream) of the last forward
+ * time loop and backward time loop, in milliseconds, and the number of
+ * kernel launches each issued. */
+int fdtd_last_timing(const fdtd_handle* h, float* fwd_ms, float* bwd_ms, int* fwd_launches,
+                     int* bwd_launches);
+
+/* ------------------------------------------------ introspection --------- */
+
+/* Host copies of the plan's tables (no device needed).  which: 0 b_E,
+ * 1 a_E, 2 1/kappa_E (integer positions), 3 b_H, 4 a_H, 5 1/kappa_H
+ * (half-integer positions); out has the axis length. */
+int fdtd_pml_profile(const fdtd_handle* h, int axis, int which, float* out);
+/* J waveform amplitude * g((n+1/2) dt) for n = 0..n_steps-1. */
+int fdtd_source_waveform(const fdtd_handle* h, float* out);
+/* Interpolation of reverse step `step`: field 0 = Ht^{step+1/2} on the low
+ * faces, 1 = E^{step} on the high faces.  Writes 4 (slot, weight) pairs;
+ * slot -1 marks an unused entry (or the known zero initial state). */
+int fdtd_interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int step, int field,
+                        int* slot, float* weight);
+
+/* Copy the current E, Ht (6 x [nz][ny][nx] float32) into d_out (device). */
+int fdtd_read_fields(fdtd_handle* h, float* d_out);
+/* Per-step objective l_n of the last forward (host, n_steps doubles). */
+int fdtd_objective_history(fdtd_handle* h, double* out);
+
+/* Tape codec on raw device arrays, for tests: encode n float32 values with
+ * one scale (absmax/format_max when scaled, else 1) written to *d_scale,
+ * and decode them back.  d_code holds n elements of the tape type. */
+int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code, float* d_scale,
+                void* cuda_stream);
+int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale, float* d_out,
+                void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_GB300_H */

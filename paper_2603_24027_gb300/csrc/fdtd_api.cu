@@ -1,0 +1,1054 @@
+// fdtd_api.cu -- host side of the library: plan, workspace, orchestration, C ABI.
+//
+// A handle holds the plan of one problem (grid, CPML tables, source, detector,
+// design box, step count) and, after fdtd_forward, the state the backward run
+// starts from.  Device memory is the caller's workspace; the library creates
+// only its own stream, events and CUDA graphs.  The time loops (hundreds to
+// thousands of launches) are captured once per record configuration and
+// replayed as CUDA graphs.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "fdtd_internal.cuh"
+
+using namespace fdtd;
+
+namespace {
+
+const double kC0 = 299792458.0;
+
+struct Layout {
+  size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, prof, srcw, tape, scales, err;
+  size_t total;
+  long long stride;   // tape elements per sample
+  int J;              // samples
+};
+
+struct GraphKey {
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample;
+  bool operator<(const GraphKey& o) const {
+    return memcmp(this, &o, sizeof(GraphKey)) < 0;
+  }
+};
+
+}  // namespace
+
+struct fdtd_handle {
+  int nx, ny, nz, px, P, N, nmax;
+  double S, dx, dt;
+  fdtd_pml pml;
+  fdtd_source src;
+  fdtd_detector det;
+  int dlo[3], dhi[3];
+  cudaStream_t user_stream;
+
+  std::vector<float> prof;    // [3][6][nmax]
+  std::vector<float> wave;    // [N]
+  std::vector<float> srcw;    // source weights over its region
+  int src_u0, src_u1, src_v0, src_v1, src_axis, src_index;
+  Faces faces;
+
+  char* ws;
+  size_t ws_bytes;
+  bool tables_uploaded;
+  bool have_forward;
+  int fwd_buf;                // field buffer holding the state after forward
+  fdtd_record_cfg fwd_rec;
+
+  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample;
+  // sampled kernel timing: event pairs per kernel kind
+  std::vector<cudaEvent_t> sev[FDTD_K_KINDS][2];
+  int sused[FDTD_K_KINDS];
+  int gsused[2][FDTD_K_KINDS];   // sample counts of the captured graphs (one sampling per key)
+  float savg[FDTD_K_KINDS];
+  int scount[FDTD_K_KINDS];
+
+  cudaStream_t stream;
+  cudaEvent_t ev_in, ev_out, t0, t1, t2, t3;
+  bool cuda_ready;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  int launches_fwd, launches_bwd;
+  float fwd_ms, bwd_ms;
+  std::vector<double> obj_hist;
+  std::string err;
+};
+
+static std::string g_create_error;
+
+static int fail(fdtd_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+static int cuda_fail(fdtd_handle* h, const char* what, cudaError_t e) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  return fail(h, FDTD_ECUDA, buf);
+}
+
+#define CK(h, x)                                   \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, #x, e_); \
+  } while (0)
+
+// ------------------------------------------------------------ CPML plan ---
+// Depth into the absorbing layer of a derivative at coordinate x (cells; E
+// derivatives at integers, H derivatives at half-integers).  The lossless
+// span [P, N-P-1/2] holds every E and H position of the interior cells, so
+// the interior update has no CPML terms and can be inverted exactly.
+static double layer_depth(int n, int P, double x) {
+  double lo = (double)P, hi = (double)(n - P) - 0.5;
+  double cells = 0.0;
+  if (x < lo) cells = lo - x;
+  else if (x > hi) cells = x - hi;
+  return cells / P;
+}
+
+static void cpml_coeffs(const fdtd_handle* h, double d, float out[3]) {
+  if (d <= 0.0) {
+    out[0] = 0.f;
+    out[1] = 0.f;
+    out[2] = 1.f;
+    return;
+  }
+  const double m = h->pml.order;
+  const double grade = pow(d, m);
+  const double sigma = h->pml.sigma_factor * (m + 1.0) * h->S * grade;  // sigma dt / eps0
+  const double kappa = 1.0 + (h->pml.kappa_max - 1.0) * grade;
+  const double w0dt = 2.0 * M_PI * h->S * h->dx / h->src.lambda0;      // 2 pi f0 dt
+  const double alpha = h->pml.alpha_factor * w0dt * (1.0 - d);          // alpha dt / eps0
+  const double b = exp(-(sigma / kappa + alpha));
+  const double a = sigma * (b - 1.0) / (kappa * (sigma + kappa * alpha));
+  out[0] = (float)b;
+  out[1] = (float)a;
+  out[2] = (float)(1.0 / kappa);
+}
+
+static void build_profiles(fdtd_handle* h) {
+  int dims[3] = {h->nx, h->ny, h->nz};
+  h->prof.assign(3 * 6 * h->nmax, 0.f);
+  for (int ax = 0; ax < 3; ++ax) {
+    for (int i = 0; i < dims[ax]; ++i) {
+      float e[3], hh[3];
+      cpml_coeffs(h, layer_depth(dims[ax], h->P, (double)i), e);
+      cpml_coeffs(h, layer_depth(dims[ax], h->P, (double)i + 0.5), hh);
+      for (int w = 0; w < 3; ++w) {
+        h->prof[(ax * 6 + w) * h->nmax + i] = e[w];
+        h->prof[(ax * 6 + 3 + w) * h->nmax + i] = hh[w];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- source ---
+// Gaussian-modulated carrier sampled at the half steps; times in units of dt.
+static void build_source(fdtd_handle* h) {
+  h->wave.assign(h->N, 0.f);
+  h->srcw.clear();
+  const fdtd_source& s = h->src;
+  if (s.kind == FDTD_SRC_NONE) return;
+  const double w0 = 2.0 * M_PI * h->S * h->dx / s.lambda0;  // rad per step
+  const double tau = 2.0 * sqrt(2.0 * M_LN2) / (s.rel_bandwidth * w0);
+  const double t0 = s.t0_over_tau * tau;
+  for (int n = 0; n < h->N; ++n) {
+    double t = (n + 0.5) - t0;
+    double env = exp(-(t * t) / (tau * tau));
+    h->wave[n] = (float)(s.amplitude * env * sin(w0 * t));
+  }
+  int dims[3] = {h->nx, h->ny, h->nz};
+  if (s.kind == FDTD_SRC_POINT) {
+    h->src_axis = 2;
+    h->src_index = s.pos[2];
+    h->src_u0 = s.pos[0];
+    h->src_u1 = s.pos[0] + 1;
+    h->src_v0 = s.pos[1];
+    h->src_v1 = s.pos[1] + 1;
+    h->srcw.assign(1, 1.f);
+  } else {
+    int a = s.axis, ua = a == 0 ? 1 : 0, va = a == 2 ? 1 : 2;
+    h->src_axis = a;
+    h->src_index = s.pos[a];
+    h->src_u0 = h->P;
+    h->src_u1 = dims[ua] - h->P;
+    h->src_v0 = h->P;
+    h->src_v1 = dims[va] - h->P;
+    int nu = h->src_u1 - h->src_u0, nv = h->src_v1 - h->src_v0;
+    h->srcw.resize((size_t)nu * nv);
+    for (int v = 0; v < nv; ++v)
+      for (int u = 0; u < nu; ++u) {
+        double ru = (h->src_u0 + u - s.pos[ua]) / s.sigma_uv[0];
+        double rv = (h->src_v0 + v - s.pos[va]) / s.sigma_uv[1];
+        h->srcw[(size_t)v * nu + u] = (float)exp(-0.5 * (ru * ru + rv * rv));
+      }
+  }
+}
+
+// ----------------------------------------------------------------- faces ---
+static void build_faces(fdtd_handle* h) {
+  int dims[3] = {h->nx, h->ny, h->nz};
+  int start = 0;
+  h->faces.start[0] = 0;
+  for (int f = 0; f < 6; ++f) {
+    FaceDesc& d = h->faces.f[f];
+    int a = f / 2, high = f & 1;
+    d.axis = a;
+    d.ua = a == 0 ? 1 : 0;
+    d.va = a == 2 ? 1 : 2;
+    d.nu = dims[d.ua] - 2 * h->P;
+    d.nv = dims[d.va] - 2 * h->P;
+    d.layer = high ? dims[a] - h->P : h->P - 1;
+    int base = high ? 0 : 3;  // E on high faces, Ht on low faces
+    d.comp0 = base + d.ua;
+    d.comp1 = base + d.va;
+    d.off = start;
+    start += 2 * d.nu * d.nv;
+    h->faces.start[f + 1] = start;
+  }
+}
+
+static long long sample_elems(const fdtd_handle* h) { return h->faces.start[6]; }
+
+static int n_samples(int N, int k) {
+  int r = (N - 1) % k;
+  return (N - 1 - r) / k + 1;
+}
+
+// ---------------------------------------------------------- interpolation ---
+// Knots of the recorded series in step units: samples at r + j k and the
+// known zero initial state (Ht^{-1/2} at -1; E^0 at 0 unless 0 is a sample).
+// The value at step n is sum_m weight_m * sample(slot_m): linear uses the two
+// bracketing knots; cubic is a cubic Hermite whose knot slopes are those of
+// the Lagrange quadratic through the knot and its neighbours (one-sided at
+// the ends), i.e. Catmull-Rom on evenly spaced knots.
+struct Knots {
+  std::vector<double> t;
+  std::vector<int> slot;  // -1 for the zero knot
+};
+
+static Knots make_knots(int N, int k, int field) {
+  Knots K;
+  int r = (N - 1) % k;
+  int J = n_samples(N, k);
+  if (field == 0) {
+    K.t.push_back(-1.0);
+    K.slot.push_back(-1);
+  } else if (r > 0) {
+    K.t.push_back(0.0);
+    K.slot.push_back(-1);
+  }
+  for (int j = 0; j < J; ++j) {
+    K.t.push_back((double)(r + j * k));
+    K.slot.push_back(j);
+  }
+  return K;
+}
+
+// Derivative weights at node x of the quadratic through nodes (a, b, c):
+// d/dx of the Lagrange basis polynomials.
+static void lagrange_slope(double a, double b, double c, double x, double w[3]) {
+  w[0] = ((x - b) + (x - c)) / ((a - b) * (a - c));
+  w[1] = ((x - a) + (x - c)) / ((b - a) * (b - c));
+  w[2] = ((x - a) + (x - b)) / ((c - a) * (c - b));
+}
+
+// Slope at knot j as weights over knot indices idx[0..2].
+static void knot_slope(const Knots& K, int j, int idx[3], double w[3]) {
+  int n = (int)K.t.size();
+  if (n == 2) {
+    idx[0] = 0; idx[1] = 1; idx[2] = 1;
+    double h = K.t[1] - K.t[0];
+    w[0] = -1.0 / h; w[1] = 1.0 / h; w[2] = 0.0;
+    return;
+  }
+  int c = j;
+  if (c < 1) c = 1;
+  if (c > n - 2) c = n - 2;
+  idx[0] = c - 1; idx[1] = c; idx[2] = c + 1;
+  lagrange_slope(K.t[c - 1], K.t[c], K.t[c + 1], K.t[j], w);
+}
+
+static void interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int n, int field,
+                           int slot[4], float wt[4]) {
+  for (int m = 0; m < 4; ++m) { slot[m] = -1; wt[m] = 0.f; }
+  Knots K = make_knots(h->N, rec->k, field);
+  int nk = (int)K.t.size();
+  double q = (double)n;
+  int a = 0;
+  while (a + 1 < nk && K.t[a + 1] < q) ++a;
+  // exact knot hit
+  for (int j = 0; j < nk; ++j)
+    if (K.t[j] == q) {
+      slot[0] = K.slot[j];
+      wt[0] = 1.f;
+      return;
+    }
+  if (a + 1 >= nk) { slot[0] = K.slot[nk - 1]; wt[0] = 1.f; return; }
+  int b = a + 1;
+  double hh = K.t[b] - K.t[a];
+  double s = (q - K.t[a]) / hh;
+  std::map<int, double> acc;  // knot index -> weight
+  if (rec->interp == FDTD_INTERP_LINEAR || nk < 2) {
+    acc[a] += 1.0 - s;
+    acc[b] += s;
+  } else {
+    double h00 = (1 + 2 * s) * (1 - s) * (1 - s), h10 = s * (1 - s) * (1 - s);
+    double h01 = s * s * (3 - 2 * s), h11 = -s * s * (1 - s);
+    acc[a] += h00;
+    acc[b] += h01;
+    int ia[3], ib[3];
+    double wa[3], wb[3];
+    knot_slope(K, a, ia, wa);
+    knot_slope(K, b, ib, wb);
+    for (int m = 0; m < 3; ++m) {
+      acc[ia[m]] += h10 * hh * wa[m];
+      acc[ib[m]] += h11 * hh * wb[m];
+    }
+  }
+  int m = 0;
+  for (auto& kv : acc) {
+    if (K.slot[kv.first] < 0 || kv.second == 0.0) continue;  // zero knot contributes nothing
+    if (m < 4) {
+      slot[m] = K.slot[kv.first];
+      wt[m] = (float)kv.second;
+      ++m;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- layout ---
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
+  Layout L;
+  size_t nc = (size_t)h->nz * h->ny * h->px;
+  size_t f6 = al(6 * nc * sizeof(float));
+  size_t P2 = 2 * (size_t)h->P;
+  size_t ps = 4 * ((size_t)h->nz * h->ny * P2 + (size_t)h->nz * P2 * h->px +
+                   P2 * h->ny * h->px);
+  size_t psb = al(ps * sizeof(float));
+  size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
+  size_t off = 0;
+  L.F[0] = off; off += f6;
+  L.F[1] = off; off += f6;
+  L.L[0] = off; off += f6;
+  L.L[1] = off; off += f6;
+  L.cb = off; off += al(nc * sizeof(float));
+  L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
+  L.psiF[0] = off; off += psb;
+  L.psiF[1] = off; off += psb;
+  L.psiL[0] = off; off += psb;
+  L.psiL[1] = off; off += psb;
+  L.gacc = off; off += al(nd * sizeof(double));
+  L.gout = off; off += al(nd * sizeof(float));
+  L.obj = off; off += al((size_t)h->N * sizeof(double));
+  L.prof = off; off += al(h->prof.size() * sizeof(float));
+  L.srcw = off; off += al((h->srcw.size() + 1) * sizeof(float));
+  L.err = off; off += 256;
+  int dt = rec ? rec->dtype : 0;
+  int k = rec ? rec->k : 1;
+  int eb = code_bytes(dt);
+  long long se = sample_elems(h);
+  long long stride = ((se * eb + 15) / 16) * 16 / eb;
+  L.stride = stride;
+  L.J = n_samples(h->N, k);
+  L.tape = off; off += al((size_t)L.J * stride * eb);
+  L.scales = off; off += al((size_t)L.J * 6 * sizeof(float));
+  L.total = off;
+  return L;
+}
+
+static Geo geo_of(const fdtd_handle* h) {
+  Geo g;
+  g.nx = h->nx; g.ny = h->ny; g.nz = h->nz; g.px = h->px; g.P = h->P; g.nmax = h->nmax;
+  g.plane = (long long)h->ny * h->px;
+  g.nc = (long long)h->nz * g.plane;
+  g.S = (float)h->S;
+  long long P2 = 2LL * h->P;
+  g.psx = 0;
+  g.psy = 4LL * h->nz * h->ny * P2;
+  g.psz = g.psy + 4LL * h->nz * P2 * h->px;
+  g.ps_total = g.psz + 4LL * P2 * h->ny * h->px;
+  g.prof = nullptr;
+  return g;
+}
+
+static int check_rec(fdtd_handle* h, const fdtd_record_cfg* rec) {
+  if (!rec) return fail(h, FDTD_EINVAL, "record config is NULL");
+  if (rec->dtype < 0 || rec->dtype > 3) return fail(h, FDTD_EINVAL, "unknown tape dtype");
+  if (rec->k < 1) return fail(h, FDTD_EINVAL, "k must be >= 1");
+  if (rec->interp != FDTD_INTERP_LINEAR && rec->interp != FDTD_INTERP_CUBIC)
+    return fail(h, FDTD_EINVAL, "unknown interpolation");
+  if (rec->scaled && rec->dtype < 2)
+    return fail(h, FDTD_EINVAL, "per-face scale applies to F16 and E4M3 only");
+  return FDTD_OK;
+}
+
+// ------------------------------------------------------------- create ---
+extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fdtd_pml* pml,
+                           const fdtd_source* source, const fdtd_detector* detector, int n_steps,
+                           const int design_lo[3], const int design_hi[3], void* cuda_stream,
+                           fdtd_handle** out) {
+  if (!out) return fail(nullptr, FDTD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !pml || !design_lo || !design_hi)
+    return fail(nullptr, FDTD_EINVAL, "NULL argument");
+  int P = pml->thickness;
+  int dims[3] = {grid->nx, grid->ny, grid->nz};
+  if (P < 1) return fail(nullptr, FDTD_EINVAL, "PML thickness must be >= 1");
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 2 * P + 2 || dims[a] > (1 << 20))
+      return fail(nullptr, FDTD_EINVAL, "each grid size must be >= 2*P+2");
+  if (!(dx > 0) || !(dt > 0)) return fail(nullptr, FDTD_EINVAL, "dx and dt must be > 0");
+  double S = kC0 * dt / dx;
+  if (S > 1.0 / sqrt(3.0) * (1.0 + 1e-12))
+    return fail(nullptr, FDTD_EINVAL, "c dt / dx exceeds the 3D CFL limit 1/sqrt(3) (Eq. 1)");
+  if (n_steps < 1) return fail(nullptr, FDTD_EINVAL, "n_steps must be >= 1");
+  for (int a = 0; a < 3; ++a)
+    if (design_lo[a] < P || design_hi[a] > dims[a] - P || design_lo[a] >= design_hi[a])
+      return fail(nullptr, FDTD_EINVAL, "design box must be non-empty and inside the interior");
+  fdtd_source src = {};
+  if (source) src = *source;
+  if (src.kind != FDTD_SRC_NONE) {
+    if (src.kind != FDTD_SRC_POINT && src.kind != FDTD_SRC_PLANE_GAUSS)
+      return fail(nullptr, FDTD_EINVAL, "unknown source kind");
+    if (src.component < 0 || src.component > 2)
+      return fail(nullptr, FDTD_EINVAL, "source component must be 0..2");
+    if (!(src.lambda0 > 0) || !(src.rel_bandwidth > 0))
+      return fail(nullptr, FDTD_EINVAL, "source lambda0 and bandwidth must be > 0");
+    if (src.kind == FDTD_SRC_POINT) {
+      for (int a = 0; a < 3; ++a)
+        if (src.pos[a] < P || src.pos[a] >= dims[a] - P)
+          return fail(nullptr, FDTD_EINVAL, "point source must be inside the interior");
+    } else {
+      if (src.axis < 0 || src.axis > 2)
+        return fail(nullptr, FDTD_EINVAL, "source axis must be 0..2");
+      if (src.pos[src.axis] < P || src.pos[src.axis] >= dims[src.axis] - P)
+        return fail(nullptr, FDTD_EINVAL, "source plane must be inside the interior");
+      if (!(src.sigma_uv[0] > 0) || !(src.sigma_uv[1] > 0))
+        return fail(nullptr, FDTD_EINVAL, "source widths must be > 0");
+    }
+  } else {
+    src.lambda0 = 1550e-9;  // sets alpha of the CPML only
+  }
+  fdtd_detector det = {};
+  if (detector) det = *detector;
+  if (det.kind != 0) {
+    if (det.kind != FDTD_OBJ_E2_PLANE && det.kind != FDTD_OBJ_POYNTING_PLANE)
+      return fail(nullptr, FDTD_EINVAL, "unknown detector kind");
+    if (det.axis < 0 || det.axis > 2) return fail(nullptr, FDTD_EINVAL, "detector axis 0..2");
+    int ua = det.axis == 0 ? 1 : 0, va = det.axis == 2 ? 1 : 2;
+    if (det.index < P || det.index >= dims[det.axis] - P)
+      return fail(nullptr, FDTD_EINVAL, "detector plane must be inside the interior");
+    if (det.lo[0] < P || det.hi[0] > dims[ua] - P || det.lo[0] >= det.hi[0] || det.lo[1] < P ||
+        det.hi[1] > dims[va] - P || det.lo[1] >= det.hi[1])
+      return fail(nullptr, FDTD_EINVAL, "detector window must be non-empty and inside the interior");
+  }
+  fdtd_handle* h = new (std::nothrow) fdtd_handle();
+  if (!h) return fail(nullptr, FDTD_ENOMEM, "host allocation failed");
+  h->nx = dims[0]; h->ny = dims[1]; h->nz = dims[2];
+  h->px = (h->nx + 7) & ~7;
+  h->P = P;
+  h->N = n_steps;
+  h->nmax = std::max(h->nx, std::max(h->ny, h->nz));
+  h->S = S; h->dx = dx; h->dt = dt;
+  h->pml = *pml;
+  if (h->pml.order <= 0) h->pml.order = 3;
+  if (h->pml.sigma_factor < 0) h->pml.sigma_factor = 0.8;
+  if (h->pml.kappa_max <= 0) h->pml.kappa_max = 1.0;
+  if (h->pml.alpha_factor < 0) h->pml.alpha_factor = 0.05;
+  h->src = src;
+  h->det = det;
+  for (int a = 0; a < 3; ++a) { h->dlo[a] = design_lo[a]; h->dhi[a] = design_hi[a]; }
+  h->user_stream = (cudaStream_t)cuda_stream;
+  h->ws = nullptr; h->ws_bytes = 0;
+  h->tables_uploaded = false;
+  h->have_forward = false;
+  h->fwd_buf = 0;
+  h->opt_graphs = 1;
+  h->opt_kernel = 0;
+  h->opt_tile_y = 8;
+  h->opt_zchunk = 8;
+  h->opt_sample = 0;
+  for (int q = 0; q < FDTD_K_KINDS; ++q) {
+    h->sused[q] = 0; h->savg[q] = 0.f; h->scount[q] = 0;
+    h->gsused[0][q] = h->gsused[1][q] = 0;
+  }
+  h->cuda_ready = false;
+  h->launches_fwd = h->launches_bwd = 0;
+  h->fwd_ms = h->bwd_ms = 0.f;
+  build_profiles(h);
+  build_source(h);
+  build_faces(h);
+  *out = h;
+  return FDTD_OK;
+}
+
+extern "C" const char* fdtd_last_error(const fdtd_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+static void drop_graphs(fdtd_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+}
+
+extern "C" int fdtd_destroy(fdtd_handle* h) {
+  if (!h) return FDTD_OK;
+  if (h->cuda_ready) {
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    for (int q = 0; q < FDTD_K_KINDS; ++q)
+      for (int e = 0; e < 2; ++e)
+        for (cudaEvent_t ev : h->sev[q][e]) cudaEventDestroy(ev);
+    cudaEventDestroy(h->ev_in); cudaEventDestroy(h->ev_out);
+    cudaEventDestroy(h->t0); cudaEventDestroy(h->t1);
+    cudaEventDestroy(h->t2); cudaEventDestroy(h->t3);
+    cudaStreamDestroy(h->stream);
+  }
+  delete h;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_workspace_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec,
+                                    size_t* bytes) {
+  if (!h || !bytes) return FDTD_EINVAL;
+  if (rec && (rec->k < 1 || rec->dtype < 0 || rec->dtype > 3)) return FDTD_EINVAL;
+  *bytes = layout_of(h, rec).total;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes) {
+  if (!h || !bytes || !rec || rec->k < 1 || rec->dtype < 0 || rec->dtype > 3) return FDTD_EINVAL;
+  size_t J = n_samples(h->N, rec->k);
+  size_t b = J * (size_t)sample_elems(h) * code_bytes(rec->dtype);
+  if (rec->scaled) b += J * 6 * sizeof(float);
+  *bytes = b;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_bind_workspace(fdtd_handle* h, void* dptr, size_t bytes) {
+  if (!h) return FDTD_EINVAL;
+  if (!dptr || ((uintptr_t)dptr & 255)) return fail(h, FDTD_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < layout_of(h, nullptr).total) return fail(h, FDTD_ENOMEM, "workspace too small");
+  if (h->cuda_ready) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  h->ws = (char*)dptr;
+  h->ws_bytes = bytes;
+  h->tables_uploaded = false;
+  h->have_forward = false;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
+  if (!h) return FDTD_EINVAL;
+  switch (option) {
+    case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
+    case FDTD_OPT_KERNEL:
+      if (value != 0 && value != 1) return fail(h, FDTD_EINVAL, "kernel must be 0 or 1");
+      h->opt_kernel = value;
+      break;
+    case FDTD_OPT_TILE_Y:
+      if (value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(h, FDTD_EINVAL, "tile_y must be 1, 2, 4 or 8");
+      h->opt_tile_y = value;
+      break;
+    case FDTD_OPT_ZCHUNK:
+      if (value < 0) return fail(h, FDTD_EINVAL, "zchunk must be >= 0");
+      h->opt_zchunk = value;
+      break;
+    case FDTD_OPT_SAMPLE_EVERY:
+      if (value < 0) return fail(h, FDTD_EINVAL, "sample interval must be >= 0");
+      h->opt_sample = value;
+      break;
+    default: return fail(h, FDTD_EINVAL, "unknown option");
+  }
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
+  if (!h || !value) return FDTD_EINVAL;
+  switch (option) {
+    case FDTD_OPT_USE_GRAPHS: *value = h->opt_graphs; break;
+    case FDTD_OPT_KERNEL: *value = h->opt_kernel; break;
+    case FDTD_OPT_TILE_Y: *value = h->opt_tile_y; break;
+    case FDTD_OPT_ZCHUNK: *value = h->opt_zchunk; break;
+    case FDTD_OPT_SAMPLE_EVERY: *value = h->opt_sample; break;
+    default: return FDTD_EINVAL;
+  }
+  return FDTD_OK;
+}
+
+// ------------------------------------------------------ introspection ---
+extern "C" int fdtd_pml_profile(const fdtd_handle* h, int axis, int which, float* out) {
+  if (!h || !out || axis < 0 || axis > 2 || which < 0 || which > 5) return FDTD_EINVAL;
+  int n = axis == 0 ? h->nx : (axis == 1 ? h->ny : h->nz);
+  memcpy(out, &h->prof[(axis * 6 + which) * h->nmax], n * sizeof(float));
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_source_waveform(const fdtd_handle* h, float* out) {
+  if (!h || !out) return FDTD_EINVAL;
+  memcpy(out, h->wave.data(), h->N * sizeof(float));
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int step,
+                                   int field, int* slot, float* weight) {
+  if (!h || !rec || !slot || !weight || rec->k < 1 || step < 0 || step >= h->N ||
+      (field != 0 && field != 1))
+    return FDTD_EINVAL;
+  interp_weights(h, rec, step, field, slot, weight);
+  return FDTD_OK;
+}
+
+// --------------------------------------------------------- orchestration ---
+static int ensure_cuda(fdtd_handle* h) {
+  if (h->cuda_ready) return FDTD_OK;
+  CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  CK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CK(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  CK(h, cudaEventCreate(&h->t0));
+  CK(h, cudaEventCreate(&h->t1));
+  CK(h, cudaEventCreate(&h->t2));
+  CK(h, cudaEventCreate(&h->t3));
+  h->cuda_ready = true;
+  return FDTD_OK;
+}
+
+static int begin(fdtd_handle* h) {
+  if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+  int rc = ensure_cuda(h);
+  if (rc) return rc;
+  CK(h, cudaEventRecord(h->ev_in, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  if (!h->tables_uploaded) {
+    Layout L = layout_of(h, nullptr);
+    CK(h, cudaMemcpyAsync(h->ws + L.prof, h->prof.data(), h->prof.size() * sizeof(float),
+                          cudaMemcpyHostToDevice, h->stream));
+    if (!h->srcw.empty())
+      CK(h, cudaMemcpyAsync(h->ws + L.srcw, h->srcw.data(), h->srcw.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));  // host vectors may be pageable
+    h->tables_uploaded = true;
+  }
+  return FDTD_OK;
+}
+
+static int finish(fdtd_handle* h) {
+  CK(h, cudaEventRecord(h->ev_out, h->stream));
+  CK(h, cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+  return FDTD_OK;
+}
+
+static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
+  StepArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = geo_of(h);
+  a.g.prof = (const float*)(h->ws + L.prof);
+  a.cb = (float*)(h->ws + L.cb);
+  a.gacc = (double*)(h->ws + L.gacc);
+  for (int i = 0; i < 3; ++i) { a.dlo[i] = h->dlo[i]; a.dhi[i] = h->dhi[i]; }
+  a.src.kind = h->src.kind;
+  a.src.comp = h->src.component;
+  a.src.axis = h->src_axis;
+  a.src.index = h->src_index;
+  a.src.u0 = h->src_u0; a.src.u1 = h->src_u1; a.src.v0 = h->src_v0; a.src.v1 = h->src_v1;
+  a.src.w = (const float*)(h->ws + L.srcw);
+  a.det.kind = h->det.kind;
+  a.det.axis = h->det.axis;
+  a.det.index = h->det.index;
+  a.det.u0 = h->det.lo[0]; a.det.u1 = h->det.hi[0];
+  a.det.v0 = h->det.lo[1]; a.det.v1 = h->det.hi[1];
+  a.tile_y = h->opt_tile_y;
+  a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
+  return a;
+}
+
+// Sampled kernel timing: event pairs recorded on h->stream around every
+// opt_sample-th launch of a kernel kind (external event nodes when captured).
+static bool sampled(const fdtd_handle* h, int n) { return h->opt_sample > 0 && n % h->opt_sample == 0; }
+
+static int ensure_sample_events(fdtd_handle* h) {
+  if (h->opt_sample <= 0) return FDTD_OK;
+  size_t need = (size_t)h->N / h->opt_sample + 2;
+  for (int q = 0; q < FDTD_K_KINDS; ++q)
+    for (int e = 0; e < 2; ++e)
+      while (h->sev[q][e].size() < need) {
+        cudaEvent_t ev;
+        CK(h, cudaEventCreate(&ev));
+        h->sev[q][e].push_back(ev);
+      }
+  return FDTD_OK;
+}
+
+static cudaError_t mark(fdtd_handle* h, int kind, int which, bool on) {
+  if (!on) return cudaSuccess;
+  int i = h->sused[kind];
+  if (i >= (int)h->sev[kind][which].size()) return cudaSuccess;
+  if (which == 1) h->sused[kind] = i + 1;
+  return cudaEventRecordWithFlags(h->sev[kind][which][i], h->stream, cudaEventRecordExternal);
+}
+
+static void reset_samples(fdtd_handle* h, const int* kinds, int nk) {
+  for (int q = 0; q < nk; ++q) h->sused[kinds[q]] = 0;
+}
+
+static void collect_samples(fdtd_handle* h, const int* kinds, int nk) {
+  for (int q = 0; q < nk; ++q) {
+    int kd = kinds[q];
+    double tot = 0.0;
+    int cnt = 0;
+    for (int i = 0; i < h->sused[kd]; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->sev[kd][0][i], h->sev[kd][1][i]) == cudaSuccess) {
+        tot += ms;
+        ++cnt;
+      }
+    }
+    h->savg[kd] = cnt ? (float)(tot / cnt) : 0.f;
+    h->scount[kd] = cnt;
+  }
+}
+
+static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_FUSED_FWD};
+static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_FUSED_REV};
+
+// Enqueue the forward time loop on h->stream (capturable).
+static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
+  Layout L = layout_of(h, rec);
+  StepArgs a = step_args(h, L);
+  size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
+  size_t psb = (size_t)a.g.ps_total * sizeof(float);
+  cudaError_t e;
+  int nl = 0;
+  if ((e = cudaMemsetAsync(h->ws + L.F[0], 0, nc6, h->stream))) return e;
+  if ((e = cudaMemsetAsync(h->ws + L.psiF[0], 0, psb, h->stream))) return e;
+  if ((e = cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream))) return e;
+  int r = (h->N - 1) % rec->k;
+  a.F = (float*)(h->ws + L.F[0]);
+  a.psiA = (float*)(h->ws + L.psiF[0]);
+  char* tape = h->ws + L.tape;
+  float* scales = (float*)(h->ws + L.scales);
+  int eb = code_bytes(rec->dtype);
+  reset_samples(h, kFwdKinds, 4);
+  int nrec = 0;
+  for (int n = 0; n < h->N; ++n) {
+    bool sm = sampled(h, n);
+    a.jn = h->wave[n];
+    a.obj = (double*)(h->ws + L.obj) + n;
+    if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
+    if ((e = launch_fwd_h(a, h->stream))) return e;
+    if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
+    ++nl;
+    if (n >= r && (n - r) % rec->k == 0) {
+      int j = (n - r) / rec->k;
+      bool sr = sampled(h, nrec++);
+      if ((e = mark(h, FDTD_K_RECORD, 0, sr))) return e;
+      if ((e = launch_record(rec->dtype, rec->scaled, a.F, a.g, h->faces,
+                             tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
+                             h->stream)))
+        return e;
+      if ((e = mark(h, FDTD_K_RECORD, 1, sr))) return e;
+      ++nl;
+    }
+    if ((e = mark(h, FDTD_K_FWD_E, 0, sm))) return e;
+    if ((e = launch_fwd_e(a, h->stream))) return e;
+    if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
+    ++nl;
+  }
+  *launches = nl;
+  return cudaSuccess;
+}
+
+static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
+  Layout L = layout_of(h, rec);
+  StepArgs a = step_args(h, L);
+  size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
+  size_t psb = (size_t)a.g.ps_total * sizeof(float);
+  size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
+  cudaError_t e;
+  int nl = 0;
+  if ((e = cudaMemsetAsync(h->ws + L.L[0], 0, nc6, h->stream))) return e;
+  if ((e = cudaMemsetAsync(h->ws + L.psiL[0], 0, psb, h->stream))) return e;
+  if ((e = cudaMemsetAsync(h->ws + L.psiL[1], 0, psb, h->stream))) return e;
+  if ((e = cudaMemsetAsync(h->ws + L.gacc, 0, nd * sizeof(double), h->stream))) return e;
+  a.F = (float*)(h->ws + L.F[h->fwd_buf]);
+  a.L = (float*)(h->ws + L.L[0]);
+  Det det = a.det;
+  int cur = 0;
+  reset_samples(h, kBwdKinds, 4);
+  for (int n = h->N - 1; n >= 0; --n) {
+    bool sm = sampled(h, n);
+    Interp ip;
+    interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
+    interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
+    if ((e = mark(h, FDTD_K_RESTORE, 0, sm))) return e;
+    if ((e = launch_restore_seed(rec->dtype, a.F, a.L, a.g, h->faces, h->ws + L.tape, L.stride,
+                                 (const float*)(h->ws + L.scales), ip, det, h->stream)))
+      return e;
+    if ((e = mark(h, FDTD_K_RESTORE, 1, sm))) return e;
+    a.jn = h->wave[n];
+    a.psiA = (float*)(h->ws + L.psiL[cur]);
+    a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
+    if ((e = mark(h, FDTD_K_REV_E, 0, sm))) return e;
+    if ((e = launch_rev_e(a, h->stream))) return e;
+    if ((e = mark(h, FDTD_K_REV_E, 1, sm))) return e;
+    if ((e = mark(h, FDTD_K_REV_H, 0, sm))) return e;
+    if ((e = launch_rev_h(a, h->stream))) return e;
+    if ((e = mark(h, FDTD_K_REV_H, 1, sm))) return e;
+    cur ^= 1;
+    nl += 3;
+  }
+  *launches = nl;
+  return cudaSuccess;
+}
+
+typedef cudaError_t (*EnqueueFn)(fdtd_handle*, const fdtd_record_cfg*, int*);
+
+// Run a time loop, through a cached CUDA graph when enabled.
+static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, EnqueueFn fn,
+                    int* launches, cudaEvent_t ta, cudaEvent_t tb) {
+  int rc = ensure_sample_events(h);
+  if (rc) return rc;
+  if (!h->opt_graphs) {
+    CK(h, cudaEventRecord(ta, h->stream));
+    cudaError_t e = fn(h, rec, launches);
+    if (e) return cuda_fail(h, "time loop launch", e);
+    CK(h, cudaEventRecord(tb, h->stream));
+    return FDTD_OK;
+  }
+  GraphKey key;
+  memset(&key, 0, sizeof key);
+  key.dir = dir; key.dtype = rec->dtype; key.k = rec->k; key.interp = rec->interp;
+  key.scaled = rec->scaled; key.kernel = h->opt_kernel; key.tile_y = h->opt_tile_y;
+  key.zchunk = h->opt_zchunk;
+  key.sample = h->opt_sample;
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraph_t graph;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    cudaError_t e = fn(h, rec, &nl);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    if (e) return cuda_fail(h, "time loop capture", e);
+    if (e2) return cuda_fail(h, "cudaStreamEndCapture", e2);
+    cudaGraphExec_t exec;
+    cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3) return cuda_fail(h, "cudaGraphInstantiate", e3);
+    if (h->graphs.size() >= 8) drop_graphs(h);
+    it = h->graphs.insert(std::make_pair(key, exec)).first;
+    for (int q = 0; q < FDTD_K_KINDS; ++q) h->gsused[dir][q] = h->sused[q];
+    if (dir == 0) h->launches_fwd = nl; else h->launches_bwd = nl;
+  }
+  const int* kinds = dir == 0 ? kFwdKinds : kBwdKinds;
+  for (int q = 0; q < 4; ++q) h->sused[kinds[q]] = h->gsused[dir][kinds[q]];
+  CK(h, cudaEventRecord(ta, h->stream));
+  CK(h, cudaGraphLaunch(it->second, h->stream));
+  CK(h, cudaEventRecord(tb, h->stream));
+  *launches = dir == 0 ? h->launches_fwd : h->launches_bwd;
+  return FDTD_OK;
+}
+
+static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec) {
+  int rc = check_rec(h, rec);
+  if (rc) return rc;
+  if (!d_eps) return fail(h, FDTD_EINVAL, "eps is NULL");
+  Layout L = layout_of(h, rec);
+  if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+  if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this record config");
+  rc = begin(h);
+  if (rc) return rc;
+  h->have_forward = false;
+  CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, h->stream));
+  Geo g = geo_of(h);
+  CK(h, launch_prep(d_eps, (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), h->stream));
+  int nl = 0;
+  rc = run_loop(h, rec, 0, enqueue_forward, &nl, h->t0, h->t1);
+  if (rc) return rc;
+  h->launches_fwd = nl;
+  h->fwd_buf = 0;
+  h->fwd_rec = *rec;
+  return FDTD_OK;
+}
+
+static int forward_finish(fdtd_handle* h, double* objective) {
+  Layout L = layout_of(h, &h->fwd_rec);
+  h->obj_hist.assign(h->N, 0.0);
+  unsigned err = 0;
+  CK(h, cudaMemcpyAsync(h->obj_hist.data(), h->ws + L.obj, h->N * sizeof(double),
+                        cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
+  collect_samples(h, kFwdKinds, 4);
+  int rc = finish(h);
+  if (rc) return rc;
+  if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
+  double s = 0.0;
+  for (double v : h->obj_hist) s += v;
+  if (!isfinite(s)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
+  if (objective) *objective = s;
+  h->have_forward = true;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_forward(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec,
+                            double* objective) {
+  if (!h) return FDTD_EINVAL;
+  int rc = forward_async(h, d_eps, rec);
+  if (rc) return rc;
+  return forward_finish(h, objective);
+}
+
+static int backward_async(fdtd_handle* h) {
+  if (!h->have_forward) return fail(h, FDTD_ESTATE, "backward needs a preceding forward");
+  int rc = begin(h);
+  if (rc) return rc;
+  int nl = 0;
+  rc = run_loop(h, &h->fwd_rec, 1, enqueue_backward, &nl, h->t2, h->t3);
+  if (rc) return rc;
+  h->launches_bwd = nl;
+  h->have_forward = false;
+  return FDTD_OK;
+}
+
+static int backward_finish(fdtd_handle* h, double seed, float* d_grad) {
+  Layout L = layout_of(h, &h->fwd_rec);
+  Geo g = geo_of(h);
+  CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g, h->dlo,
+                        h->dhi, seed, d_grad, (unsigned*)(h->ws + L.err), h->stream));
+  unsigned err = 0;
+  CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaEventElapsedTime(&h->bwd_ms, h->t2, h->t3));
+  collect_samples(h, kBwdKinds, 4);
+  int rc = finish(h);
+  if (rc) return rc;
+  if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_backward(fdtd_handle* h, double seed, float* d_grad_eps) {
+  if (!h) return FDTD_EINVAL;
+  if (!d_grad_eps) return fail(h, FDTD_EINVAL, "gradient buffer is NULL");
+  int rc = backward_async(h);
+  if (rc) return rc;
+  return backward_finish(h, seed, d_grad_eps);
+}
+
+extern "C" int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps,
+                                        const fdtd_record_cfg* rec, double seed,
+                                        double* objective, float* h_grad) {
+  if (!h) return FDTD_EINVAL;
+  if (!h_eps || !h_grad) return fail(h, FDTD_EINVAL, "NULL host buffer");
+  if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+  int rc = ensure_cuda(h);
+  if (rc) return rc;
+  Layout L = layout_of(h, rec ? rec : &h->fwd_rec);
+  size_t n = (size_t)h->nx * h->ny * h->nz;
+  size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
+  CK(h, cudaEventRecord(h->ev_in, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  CK(h, cudaMemcpyAsync(h->ws + L.eps, h_eps, n * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream));
+  rc = fdtd_forward(h, (const float*)(h->ws + L.eps), rec, objective);
+  if (rc) return rc;
+  rc = backward_async(h);
+  if (rc) return rc;
+  rc = backward_finish(h, seed, (float*)(h->ws + L.gout));
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(h_grad, h->ws + L.gout, nd * sizeof(float), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_group_forward(fdtd_handle* const* hs, int n, const float* const* d_eps,
+                                  const fdtd_record_cfg* rec, double* objs) {
+  if (!hs || n < 0 || (n > 0 && (!d_eps || !objs))) return FDTD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    int rc = forward_async(hs[i], d_eps[i], rec);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = forward_finish(hs[i], &objs[i]);
+    if (rc) return rc;
+  }
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_group_backward(fdtd_handle* const* hs, int n, const double* seeds,
+                                   float* const* d_grads) {
+  if (!hs || n < 0 || (n > 0 && (!seeds || !d_grads))) return FDTD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!d_grads[i]) return fail(hs[i], FDTD_EINVAL, "gradient buffer is NULL");
+    int rc = backward_async(hs[i]);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = backward_finish(hs[i], seeds[i], d_grads[i]);
+    if (rc) return rc;
+  }
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_last_timing(const fdtd_handle* h, float* fwd_ms, float* bwd_ms,
+                                int* fwd_launches, int* bwd_launches) {
+  if (!h) return FDTD_EINVAL;
+  if (fwd_ms) *fwd_ms = h->fwd_ms;
+  if (bwd_ms) *bwd_ms = h->bwd_ms;
+  if (fwd_launches) *fwd_launches = h->launches_fwd;
+  if (bwd_launches) *bwd_launches = h->launches_bwd;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_kernel_timing(const fdtd_handle* h, int kind, float* avg_ms, int* samples) {
+  if (!h || kind < 0 || kind >= FDTD_K_KINDS) return FDTD_EINVAL;
+  if (avg_ms) *avg_ms = h->savg[kind];
+  if (samples) *samples = h->scount[kind];
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_read_fields(fdtd_handle* h, float* d_out) {
+  if (!h || !d_out) return FDTD_EINVAL;
+  if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+  int rc = begin(h);
+  if (rc) return rc;
+  Layout L = layout_of(h, nullptr);
+  CK(h, launch_gather((const float*)(h->ws + L.F[h->fwd_buf]), geo_of(h), d_out, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return finish(h);
+}
+
+extern "C" int fdtd_objective_history(fdtd_handle* h, double* out) {
+  if (!h || !out) return FDTD_EINVAL;
+  if ((int)h->obj_hist.size() != h->N) return fail(h, FDTD_ESTATE, "no forward run yet");
+  memcpy(out, h->obj_hist.data(), h->N * sizeof(double));
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code,
+                           float* d_scale, void* cuda_stream) {
+  if (dtype < 0 || dtype > 3 || !d_in || !d_code || !d_scale) return FDTD_EINVAL;
+  if (scaled && dtype < 2) return FDTD_EINVAL;
+  cudaError_t e = launch_encode(dtype, scaled, d_in, n, d_code, d_scale, (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
+}
+
+extern "C" int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale,
+                           float* d_out, void* cuda_stream) {
+  if (dtype < 0 || dtype > 3 || !d_code || !d_scale || !d_out) return FDTD_EINVAL;
+  cudaError_t e = launch_decode(dtype, d_code, n, d_scale, d_out, (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
+}

@@ -1,0 +1,168 @@
+// fdtd_internal.cuh -- device data layout and helpers shared by the kernels.
+//
+// Layout in HBM (all float32 unless noted, x fastest, rows padded to px):
+//   fields   F[6][nz][ny][px]       Ex Ey Ez Hx Hy Hz   (E, Ht = eta0 H)
+//   cb       [nz][ny][px]           S / eps_r
+//   psi set  x-slab [4][nz][ny][2P], y-slab [4][nz][2P][px], z-slab [4][2P][ny][px]
+//            (convolutional-PML auxiliaries only where they are non-zero)
+//   profiles [3 axes][6][nmax]      b_E a_E 1/kappa_E b_H a_H 1/kappa_H
+// psi components per axis slab (curl term, sign):
+//   x: 0 (Hy, -dEz/dx) 1 (Hz, +dEy/dx) 2 (Ey, -dHz/dx) 3 (Ez, +dHy/dx)
+//   y: 0 (Hx, +dEz/dy) 1 (Hz, -dEx/dy) 2 (Ex, +dHz/dy) 3 (Ez, -dHx/dy)
+//   z: 0 (Hx, -dEy/dz) 1 (Hy, +dEx/dz) 2 (Ex, -dHy/dz) 3 (Ey, +dHx/dz)
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+enum { PR_BE = 0, PR_AE = 1, PR_KE = 2, PR_BH = 3, PR_AH = 4, PR_KH = 5 };
+enum { ERR_EPS = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u, ERR_LAUNCH = 8u };
+
+struct Geo {
+  int nx, ny, nz, px, P, nmax;
+  long long plane;  // ny * px
+  long long nc;     // nz * plane (one component)
+  float S;
+  const float* prof;
+  long long psx, psy, psz;  // element offsets of the y and z slabs inside a psi set (psx = 0)
+  long long ps_total;       // elements per psi set
+};
+
+// Source region: plane normal `axis` at `index`, cells (u,v) in [u0,u1)x[v0,v1),
+// weights w[(v-v0)*(u1-u0) + (u-u0)] for field component `comp`.
+struct Src {
+  int kind, comp, axis, index, u0, u1, v0, v1;
+  const float* w;
+};
+
+struct Det {
+  int kind, axis, index, u0, u1, v0, v1;
+};
+
+struct FaceDesc {
+  int axis, ua, va, nu, nv, layer;
+  int comp0, comp1;          // field component index (0..5) of the two tangential values
+  long long off;             // element offset of the face inside one tape sample
+};
+
+struct Faces {
+  FaceDesc f[6];
+  int start[7];              // prefix sums of the value counts (2 nu nv)
+};
+
+struct Interp {
+  int slot[2][4];            // tape slot per term (-1: unused)
+  float w[2][4];
+};
+
+__device__ __forceinline__ float prof(const Geo& g, int axis, int which, int i) {
+  return __ldg(g.prof + ((long long)(axis * 6 + which)) * g.nmax + i);
+}
+
+__device__ __forceinline__ bool in_slab(int pos, int n, int P) { return pos < P || pos >= n - P; }
+
+__device__ __forceinline__ long long psi_x(const Geo& g, int c, int i, int j, int k) {
+  int s = i < g.P ? i : i - (g.nx - 2 * g.P);
+  return (((long long)c * g.nz + k) * g.ny + j) * (2 * g.P) + s;
+}
+__device__ __forceinline__ long long psi_y(const Geo& g, int c, int i, int j, int k) {
+  int s = j < g.P ? j : j - (g.ny - 2 * g.P);
+  return g.psy + (((long long)c * g.nz + k) * (2 * g.P) + s) * g.px + i;
+}
+__device__ __forceinline__ long long psi_z(const Geo& g, int c, int i, int j, int k) {
+  int s = k < g.P ? k : k - (g.nz - 2 * g.P);
+  return g.psz + (((long long)c * (2 * g.P) + s) * g.ny + j) * g.px + i;
+}
+
+// Plane membership: p = (i, j, k); (u, v) = the two other axes in increasing order.
+__device__ __forceinline__ bool on_plane(int axis, int index, int u0, int u1, int v0, int v1, int i,
+                                         int j, int k, int* u, int* v) {
+  int p0 = axis == 0 ? i : (axis == 1 ? j : k);
+  if (p0 != index) return false;
+  int uu = axis == 0 ? j : i;
+  int vv = axis == 2 ? j : k;
+  *u = uu;
+  *v = vv;
+  return uu >= u0 && uu < u1 && vv >= v0 && vv < v1;
+}
+
+// ---------------------------------------------------------------- codec ----
+// Tape element types: 0 f32, 1 bf16, 2 f16, 3 e4m3 (OCP e4m3fn).  Encoding is
+// round-to-nearest-even with saturation to the largest finite value.
+template <int DT> struct Code;
+template <> struct Code<0> {
+  typedef float T;
+  static constexpr float fmax = 3.4028234663852886e38f;
+  __device__ static T enc(float x) { return x; }
+  __device__ static float dec(T c) { return c; }
+};
+template <> struct Code<1> {
+  typedef __nv_bfloat16 T;
+  static constexpr float fmax = 3.3895313892515355e38f;
+  __device__ static T enc(float x) { return __float2bfloat16_rn(x); }
+  __device__ static float dec(T c) { return __bfloat162float(c); }
+};
+template <> struct Code<2> {
+  typedef __half T;
+  static constexpr float fmax = 65504.0f;
+  __device__ static T enc(float x) { return __float2half_rn(fminf(fmaxf(x, -65504.0f), 65504.0f)); }
+  __device__ static float dec(T c) { return __half2float(c); }
+};
+template <> struct Code<3> {
+  typedef __nv_fp8_storage_t T;
+  static constexpr float fmax = 448.0f;
+  __device__ static T enc(float x) { return __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3); }
+  __device__ static float dec(T c) {
+    __half_raw h = __nv_cvt_fp8_to_halfraw(c, __NV_E4M3);
+    return __half2float(__half(h));
+  }
+};
+
+inline int code_bytes(int dt) { return dt == 0 ? 4 : (dt == 3 ? 1 : 2); }
+
+// ------------------------------------------------------------ launchers ----
+// Implemented in kernels_step.cu / kernels_tape.cu; return cudaGetLastError().
+struct StepArgs {
+  Geo g;
+  float* F;        // fields
+  float* cb;
+  float* psiA;     // psi set read (and written in place by the split forward)
+  float* psiB;     // psi set written (ping-pong)
+  float* L;        // adjoint fields (6 components, same layout as F)
+  double* gacc;    // FP64 design-box accumulator [dz][dy][dx]
+  int dlo[3], dhi[3];
+  Src src;
+  Det det;
+  double* obj;     // per-step objective slot
+  float jn;        // J waveform value of this step
+  int zchunk;
+  int tile_y;
+};
+
+cudaError_t launch_prep(const float* eps, float* cb, Geo g, unsigned* err, cudaStream_t s);
+cudaError_t launch_fwd_h(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_fwd_e(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_fused_fwd(const StepArgs& a, float* Fout, cudaStream_t s);
+cudaError_t launch_fused_rev(const StepArgs& a, float* Fout, float* Lout, cudaStream_t s);
+cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
+                            const int* dhi, double scale, float* out, unsigned* err,
+                            cudaStream_t s);
+cudaError_t launch_gather(const float* F, Geo g, float* out, cudaStream_t s);
+cudaError_t launch_record(int dtype, int scaled, const float* F, Geo g, const Faces& fc,
+                          void* tape_sample, float* scale_slot, cudaStream_t s);
+cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
+                                const void* tape, long long sample_stride, const float* scales,
+                                const Interp& ip, const Det& det, cudaStream_t s);
+cudaError_t launch_encode(int dtype, int scaled, const float* in, size_t n, void* code,
+                          float* scale, cudaStream_t s);
+cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* scale, float* out,
+                          cudaStream_t s);
+
+}  // namespace fdtd

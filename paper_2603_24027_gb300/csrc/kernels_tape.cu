@@ -1,0 +1,286 @@
+// kernels_tape.cu -- boundary tape: record (compress) and restore (decompress).
+//
+// Sec. 2: the fields on the interface slices between the simulation volume
+// and the PML are recorded in the forward run and injected back in the
+// time-reversed run; they are stored at reduced bit-width (converted back to
+// FP32 before use) and only every k-th step, with interpolation in time.
+//
+// Recorded layers (the values the interior inverse reads from outside the
+// interior): low faces (x-, y-, z-) at index P-1 hold the two tangential Ht
+// components at n+1/2; high faces (x+, y+, z+) at index N-P hold the two
+// tangential E components at n.  One sample = 6 faces x 2 components x the
+// interior cross-section, [face][comp][v][u].
+//
+// k_record runs one thread-block cluster per face: every CTA takes a share of
+// the face, the per-face absmax is reduced across the cluster through
+// distributed shared memory, then each CTA encodes its share with the common
+// scale.  No global atomics and no second launch.
+#include <cooperative_groups.h>
+
+#include "fdtd_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fdtd {
+
+static constexpr int REC_CLUSTER = 8;
+static constexpr int REC_THREADS = 512;
+
+__device__ __forceinline__ long long face_cell(const Geo& g, const FaceDesc& f, int r,
+                                               int* comp) {
+  int per = f.nu * f.nv;
+  int t = r / per;
+  int rem = r - t * per;
+  int v = rem / f.nu;
+  int u = rem - v * f.nu;
+  int p[3];
+  p[f.axis] = f.layer;
+  p[f.ua] = g.P + u;
+  p[f.va] = g.P + v;
+  *comp = t == 0 ? f.comp0 : f.comp1;
+  return (long long)p[2] * g.plane + (long long)p[1] * g.px + p[0];
+}
+
+template <int DT>
+__global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict__ F, Geo g,
+                                                        Faces fc, void* tape_sample,
+                                                        float* scale_slot, int scaled) {
+  typedef typename Code<DT>::T T;
+  __shared__ float red[REC_THREADS / 32];
+  __shared__ float cl_amax;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int f = blockIdx.y;
+  const FaceDesc fd = fc.f[f];
+  const int n = 2 * fd.nu * fd.nv;
+  const int rank = (int)cluster.block_rank();
+  const int nr = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  float scale = 1.0f;
+  if (scaled) {
+    float m = 0.f;
+    for (int r = rank * REC_THREADS + tid; r < n; r += nr * REC_THREADS) {
+      int comp;
+      long long q = face_cell(g, fd, r, &comp);
+      m = fmaxf(m, fabsf(F[comp * g.nc + q]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    if (tid < 32) {
+      float t = tid < REC_THREADS / 32 ? red[tid] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+      if (tid == 0) cl_amax = t;
+    }
+    cluster.sync();
+    float amax = 0.f;
+    for (int b = 0; b < nr; ++b) amax = fmaxf(amax, *cluster.map_shared_rank(&cl_amax, b));
+    cluster.sync();  // peers may still be reading this CTA's cl_amax
+    scale = amax > 0.f ? __fdiv_rn(amax, Code<DT>::fmax) : 1.0f;
+  }
+  if (rank == 0 && tid == 0) scale_slot[f] = scale;
+  T* out = reinterpret_cast<T*>(tape_sample) + fd.off;
+  for (int r = rank * REC_THREADS + tid; r < n; r += nr * REC_THREADS) {
+    int comp;
+    long long q = face_cell(g, fd, r, &comp);
+    float x = F[comp * g.nc + q];
+    out[r] = Code<DT>::enc(scaled ? __fdiv_rn(x, scale) : x);
+  }
+}
+
+template <int DT>
+static cudaError_t launch_record_t(int scaled, const float* F, Geo g, const Faces& fc,
+                                   void* tape_sample, float* scale_slot, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(REC_CLUSTER, 6, 1);
+  cfg.blockDim = dim3(REC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = REC_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_record<DT>, F, g, fc, tape_sample, scale_slot, scaled);
+}
+
+cudaError_t launch_record(int dtype, int scaled, const float* F, Geo g, const Faces& fc,
+                          void* tape_sample, float* scale_slot, cudaStream_t s) {
+  switch (dtype) {
+    case 0: return launch_record_t<0>(0, F, g, fc, tape_sample, scale_slot, s);
+    case 1: return launch_record_t<1>(0, F, g, fc, tape_sample, scale_slot, s);
+    case 2: return launch_record_t<2>(scaled, F, g, fc, tape_sample, scale_slot, s);
+    case 3: return launch_record_t<3>(scaled, F, g, fc, tape_sample, scale_slot, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// -------------------------------------------------------------- restore ---
+// One thread per recorded value: the interpolated value at this reverse step
+// is sum_m w[m] * decode(sample slot[m]) * scale[slot[m]] (slot -1 = the known
+// zero initial state, or an unused term).  Threads past the faces add the
+// objective seed dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector plane.
+template <int DT>
+__global__ void k_restore_seed(float* __restrict__ F, float* __restrict__ L, Geo g, Faces fc,
+                               const void* __restrict__ tape, long long stride,
+                               const float* __restrict__ scales, Interp ip, Det det) {
+  typedef typename Code<DT>::T T;
+  const int total = fc.start[6];
+  const int du = det.u1 - det.u0, dv = det.v1 - det.v0;
+  const int nd = det.kind ? du * dv : 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total + nd;
+       t += gridDim.x * blockDim.x) {
+    if (t < total) {
+      int f = 0;
+      while (t >= fc.start[f + 1]) ++f;
+      const FaceDesc& fd = fc.f[f];
+      int r = t - fc.start[f];
+      int comp;
+      long long q = face_cell(g, fd, r, &comp);
+      int fld = f & 1;  // 0: Ht on low faces, 1: E on high faces
+      float v = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int s = ip.slot[fld][m];
+        if (s >= 0) {
+          const T* src = reinterpret_cast<const T*>(tape) + (long long)s * stride + fd.off;
+          float x = Code<DT>::dec(src[r]);
+          if (DT >= 2) x = x * scales[s * 6 + f];
+          v += ip.w[fld][m] * x;
+        }
+      }
+      F[comp * g.nc + q] = v;
+    } else {
+      int e = t - total;
+      int v = det.v0 + e / du, u = det.u0 + e % du;
+      int p[3];
+      int ua = det.axis == 0 ? 1 : 0, va = det.axis == 2 ? 1 : 2;
+      p[det.axis] = det.index;
+      p[ua] = u;
+      p[va] = v;
+      long long q = (long long)p[2] * g.plane + (long long)p[1] * g.px + p[0];
+      if (det.kind == 1) {
+        for (int c = 0; c < 3; ++c) L[c * g.nc + q] += 2.0f * F[c * g.nc + q];
+      } else {
+        int b = (det.axis + 1) % 3, c = (det.axis + 2) % 3;
+        float Eb = F[b * g.nc + q], Ec = F[c * g.nc + q];
+        float Hb = F[(3 + b) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
+        L[b * g.nc + q] += Hc;
+        L[c * g.nc + q] -= Hb;
+        L[(3 + c) * g.nc + q] += Eb;
+        L[(3 + b) * g.nc + q] -= Ec;
+      }
+    }
+  }
+}
+
+cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
+                                const void* tape, long long stride, const float* scales,
+                                const Interp& ip, const Det& det, cudaStream_t s) {
+  int n = fc.start[6] + (det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 0);
+  int blocks = (n + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks < 1) blocks = 1;
+  switch (dtype) {
+    case 0: k_restore_seed<0><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 1: k_restore_seed<1><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 2: k_restore_seed<2><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 3: k_restore_seed<3><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------- raw codec ------
+// One cluster of CTAs reduces the absmax of the whole array (test entry).
+template <int DT>
+__global__ void __launch_bounds__(REC_THREADS) k_encode(const float* __restrict__ in, size_t n,
+                                                        void* code, float* scale_out,
+                                                        int scaled) {
+  typedef typename Code<DT>::T T;
+  __shared__ float red[REC_THREADS / 32];
+  __shared__ float cl_amax;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int nr = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  float scale = 1.0f;
+  if (scaled) {
+    float m = 0.f;
+    for (size_t r = (size_t)rank * REC_THREADS + tid; r < n; r += (size_t)nr * REC_THREADS)
+      m = fmaxf(m, fabsf(in[r]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) red[tid >> 5] = m;
+    __syncthreads();
+    if (tid < 32) {
+      float t = tid < REC_THREADS / 32 ? red[tid] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+      if (tid == 0) cl_amax = t;
+    }
+    cluster.sync();
+    float amax = 0.f;
+    for (int b = 0; b < nr; ++b) amax = fmaxf(amax, *cluster.map_shared_rank(&cl_amax, b));
+    cluster.sync();
+    scale = amax > 0.f ? __fdiv_rn(amax, Code<DT>::fmax) : 1.0f;
+  }
+  if (rank == 0 && tid == 0) *scale_out = scale;
+  T* out = reinterpret_cast<T*>(code);
+  for (size_t r = (size_t)rank * REC_THREADS + tid; r < n; r += (size_t)nr * REC_THREADS)
+    out[r] = Code<DT>::enc(scaled ? __fdiv_rn(in[r], scale) : in[r]);
+}
+
+template <int DT>
+__global__ void k_decode(const void* code, size_t n, const float* scale, float* out) {
+  typedef typename Code<DT>::T T;
+  const T* c = reinterpret_cast<const T*>(code);
+  float s = *scale;
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < n;
+       r += (size_t)gridDim.x * blockDim.x)
+    out[r] = Code<DT>::dec(c[r]) * s;
+}
+
+template <int DT>
+static cudaError_t launch_encode_t(int scaled, const float* in, size_t n, void* code, float* scale,
+                                   cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(REC_CLUSTER, 1, 1);
+  cfg.blockDim = dim3(REC_THREADS, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = REC_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_encode<DT>, in, n, code, scale, scaled);
+}
+
+cudaError_t launch_encode(int dtype, int scaled, const float* in, size_t n, void* code,
+                          float* scale, cudaStream_t s) {
+  switch (dtype) {
+    case 0: return launch_encode_t<0>(0, in, n, code, scale, s);
+    case 1: return launch_encode_t<1>(0, in, n, code, scale, s);
+    case 2: return launch_encode_t<2>(scaled, in, n, code, scale, s);
+    case 3: return launch_encode_t<3>(scaled, in, n, code, scale, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* scale, float* out,
+                          cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  switch (dtype) {
+    case 0: k_decode<0><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
+    case 1: k_decode<1><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
+    case 2: k_decode<2><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
+    case 3: k_decode<3><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fdtd

@@ -1,0 +1,162 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library loads, exports every entry point include/fdtd.h declares, and
+its host-computed plan (CPML tables, source waveform, tape interpolation
+weights, argument validation, tape sizes) agrees with the independent FP64
+oracle.  No compute kernel is called here.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2603_24027_gb300 import build as B
+from paper_2603_24027_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    B.build()
+    from paper_2603_24027_gb300 import _capi
+    return _capi
+
+
+@pytest.fixture(scope="module")
+def fdtd(capi):
+    from paper_2603_24027_gb300 import fdtd
+    return fdtd
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fdtd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdtd_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(capi):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = C.CDLL(capi.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding knows the prototype of each one
+    assert set(names) <= set(capi._PROTOS)
+
+
+def test_library_is_built_for_sm103a_only():
+    flags = B.ARCH
+    assert flags == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+WORKLOADS = [I.small_dipole, lambda: I.waveguide_sweep(n_steps=50), I.fd_cube, I.ragged_box]
+
+
+@pytest.mark.parametrize("make", WORKLOADS)
+def test_cpml_tables_match_oracle(fdtd, make):
+    w = make()
+    sim = fdtd.Simulation(w)
+    for ax in range(3):
+        ref = O.profiles(w, ax)
+        for which, key in enumerate(("b_e", "a_e", "kinv_e", "b_h", "a_h", "kinv_h")):
+            got = sim.pml_profile(ax, which).astype(np.float64)
+            np.testing.assert_allclose(got, ref[key], rtol=1.2e-7, atol=1e-30)
+
+
+def test_cpml_tables_with_kappa_grading(fdtd):
+    w = I.ragged_box().replace(pml_kappa_max=5.0, pml_alpha_factor=0.2)
+    sim = fdtd.Simulation(w)
+    for ax in range(3):
+        ref = O.profiles(w, ax)
+        for which, key in enumerate(("b_e", "a_e", "kinv_e", "b_h", "a_h", "kinv_h")):
+            np.testing.assert_allclose(sim.pml_profile(ax, which), ref[key], rtol=1.2e-7, atol=1e-30)
+
+
+@pytest.mark.parametrize("make", WORKLOADS)
+def test_source_waveform_matches_oracle(fdtd, make):
+    w = make()
+    sim = fdtd.Simulation(w)
+    got = sim.source_waveform().astype(np.float64)
+    ref = O.waveform(w)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-7 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("N,k", [(40, 1), (40, 3), (41, 4), (37, 8), (16, 16), (5, 7), (2000, 16)])
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+@pytest.mark.parametrize("field", [0, 1])
+def test_interpolation_weights_match_oracle(capi, fdtd, N, k, interp, field):
+    """The library's per-step weights applied to a random recorded series
+    equal the oracle's interpolation of that series, zero knot included."""
+    w = I.fd_cube(n_steps=N)
+    sim = fdtd.Simulation(w)
+    rec = capi.record_cfg("f32", k, interp)
+    r = (N - 1) % k
+    J = O.n_samples(N, k)
+    rng = np.random.default_rng(N * 100 + k)
+    vals = rng.standard_normal(J)
+    t = [r + j * k for j in range(J)]
+    p = list(vals)
+    if field == 0:
+        t, p = [-1] + t, [0.0] + p
+    elif r > 0:
+        t, p = [0] + t, [0.0] + p
+    steps = list(range(0, N, max(1, N // 60)))
+    ref = O.interp_series(interp, np.array(t, float), np.array(p), np.array(steps, float))
+    for s, rv in zip(steps, ref):
+        slot, wt = sim.interp_weights(rec, s, field)
+        got = sum(wt[m] * vals[slot[m]] for m in range(4) if slot[m] >= 0)
+        assert got == pytest.approx(rv, abs=2e-6 * (1 + np.abs(vals).max()))
+
+
+def test_create_rejects_bad_arguments(capi, fdtd):
+    good = I.fd_cube()
+    bad = [
+        good.replace(pml_thickness=0),
+        good.replace(dt=good.dt * 1.02),                    # beyond the 3D CFL limit
+        good.replace(n_steps=0),
+        good.replace(design_lo=(1, 2, 2)),                   # design box in the PML
+        good.replace(design_hi=(2, 6, 6)),                   # empty design box
+        good.replace(src_pos=(0, 3, 3)),                     # source in the PML
+        good.replace(src_component=3),
+        good.replace(det_index=1),                           # detector in the PML
+        good.replace(det_hi=(7, 6)),
+        good.replace(nx=5),                                  # interior too small
+    ]
+    for w in bad:
+        with pytest.raises(capi.FdtdError) as e:
+            fdtd.Simulation(w)
+        assert e.value.status == capi.FDTD_EINVAL
+
+
+def test_forward_without_workspace_is_a_state_error(capi, fdtd):
+    sim = fdtd.Simulation(I.fd_cube())
+    out = C.c_double()
+    rc = capi.lib().fdtd_forward(sim.h, C.c_void_p(1), C.byref(capi.record_cfg()), C.byref(out))
+    assert rc == capi.FDTD_ESTATE
+    rc = capi.lib().fdtd_backward(sim.h, 1.0, C.c_void_p(1))
+    assert rc == capi.FDTD_ESTATE
+
+
+def test_tape_sizes_and_compression_factors(capi, fdtd):
+    """Bytes per sample = 2 tangential values x 6 interior cross-sections x
+    dtype bytes; factor = (32/bits) x k relative to FP32 every step (Sec. 3)
+    plus 24 bytes of scales per sample for scaled formats."""
+    w = I.waveguide_mid()
+    sim = fdtd.Simulation(w)
+    n = [w.nx - 24, w.ny - 24, w.nz - 24]
+    per_sample = 2 * 2 * (n[1] * n[2] + n[0] * n[2] + n[0] * n[1])
+    assert per_sample == 230912                      # 200x200x100, P = 12
+    f32 = sim.tape_bytes(capi.record_cfg("f32", 1))
+    assert f32 == 2000 * per_sample * 4
+    bf16k4 = sim.tape_bytes(capi.record_cfg("bf16", 4))
+    assert bf16k4 == 500 * per_sample * 2
+    assert f32 / bf16k4 == 8.0
+    e4k8 = sim.tape_bytes(capi.record_cfg("e4m3", 8))
+    assert e4k8 == 250 * (per_sample + 24)
+    assert f32 / e4k8 > 31.99
+    e4k16 = sim.tape_bytes(capi.record_cfg("e4m3", 16, scaled=True))
+    assert f32 / e4k16 > 63.9                        # the paper's 64x at 8 bits, k = 16

@@ -1,0 +1,245 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated targets): forward fields 1e-5 relative L2 (FP32 fields),
+uncompressed-tape (FP32, k = 1) gradient 1e-4 relative L2 against the exact
+discrete gradient.  Compressed tapes are compared with the oracle's own FP64
+run of the method (same quantiser, same interpolation): their difference is
+FP32-vs-FP64 field rounding amplified by the quantiser's rounding decisions,
+so the bar there is a relative L2 of 2e-2 and a cosine of 0.999.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2603_24027_gb300 import build as B
+from paper_2603_24027_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    B.build()
+    from paper_2603_24027_gb300 import fdtd
+    return fdtd
+
+
+@pytest.fixture(scope="module")
+def A(F):
+    from paper_2603_24027_gb300 import _capi
+    return _capi
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def cos(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def gpu_run(F, A, w, rec=None, seed=1.0, options=None):
+    rec = rec or A.record_cfg("f32", 1)
+    sim = F.Simulation(w)
+    for k, v in (options or {}).items():
+        sim.set_option(k, v)
+    eps = torch.from_numpy(np.ascontiguousarray(w.eps)).cuda()
+    L = sim.forward(eps, rec)
+    fields = sim.read_fields().cpu().numpy()
+    hist = sim.objective_history()
+    g = sim.backward(seed).cpu().numpy()
+    return dict(L=L, fields=fields, hist=hist, g=g, sim=sim)
+
+
+SMALL = {
+    "ragged_poynting": lambda: I.ragged_box(),
+    "ragged_e2_point": lambda: I.ragged_box(nx=45, ny=27, nz=23, P=5, n_steps=90,
+                                            det_kind=I.OBJ_E2_PLANE, src_kind=I.SRC_POINT),
+    "fd_cube": lambda: I.fd_cube(),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_forward_fields_and_objective(F, A, name, kernel):
+    w = SMALL[name]()
+    r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel})
+    st, obj = O.forward(w)
+    for c in range(6):
+        assert rel(r["fields"][c], st[c]) < 1e-5, c
+    np.testing.assert_allclose(r["hist"], obj, rtol=0, atol=1e-5 * np.abs(obj).max())
+    assert r["L"] == pytest.approx(obj.sum(), rel=1e-5)
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_uncompressed_gradient_matches_exact_gradient(F, A, name, kernel):
+    w = SMALL[name]()
+    r = gpu_run(F, A, w, seed=1.0, options={A.OPT_KERNEL: kernel})
+    L, g = O.gradient(w)
+    assert r["L"] == pytest.approx(L, rel=1e-5)
+    assert rel(r["g"], g) < 1e-4
+
+
+def test_seed_scales_the_gradient(F, A):
+    w = SMALL["ragged_poynting"]()
+    r1 = gpu_run(F, A, w, seed=1.0)
+    r2 = gpu_run(F, A, w, seed=-2.5)
+    np.testing.assert_allclose(r2["g"], -2.5 * r1["g"], rtol=1e-6, atol=1e-30)
+
+
+def test_dipole48_config(F, A):
+    """48^3 at 25 nm, 8-cell CPML, 400 steps, 16^3 random design (FP32 k=1)."""
+    w = I.small_dipole()
+    r = gpu_run(F, A, w)
+    L, g, st = O.gradient(w, want_state=True)
+    for c in range(6):
+        assert rel(r["fields"][c], st[c]) < 1e-5
+    assert r["L"] == pytest.approx(L, rel=1e-5)
+    assert rel(r["g"], g) < 1e-4
+
+
+@pytest.mark.parametrize("dtype,k,interp", [("bf16", 4, "linear"), ("f16", 2, "cubic"),
+                                            ("e4m3", 1, "linear"), ("e4m3", 4, "cubic"),
+                                            ("f32", 3, "linear"), ("f32", 5, "cubic")])
+def test_compressed_tape_matches_oracle_method(F, A, dtype, k, interp):
+    w = I.ragged_box(n_steps=120)
+    rec = A.record_cfg(dtype, k, interp)
+    r = gpu_run(F, A, w, rec=rec)
+    L, g = O.reverse(w, dtype, scaled=bool(rec.scaled), k=k, interp=interp)
+    assert r["L"] == pytest.approx(L, rel=1e-5)
+    assert rel(r["g"], g) < 2e-2
+    assert cos(r["g"], g) > 0.999
+
+
+def test_graphs_and_direct_launches_agree(F, A):
+    w = SMALL["ragged_e2_point"]()
+    rec = A.record_cfg("bf16", 2, "linear")
+    a = gpu_run(F, A, w, rec=rec, options={A.OPT_USE_GRAPHS: 1})
+    b = gpu_run(F, A, w, rec=rec, options={A.OPT_USE_GRAPHS: 0})
+    np.testing.assert_array_equal(a["fields"], b["fields"])
+    np.testing.assert_allclose(a["g"], b["g"], rtol=1e-12, atol=1e-30)
+
+
+@pytest.mark.parametrize("zchunk,tile_y", [(1, 4), (3, 8), (0, 2), (16, 1)])
+def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y):
+    w = SMALL["ragged_poynting"]()
+    base = gpu_run(F, A, w)
+    for kernel in (0, 1):
+        r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel, A.OPT_ZCHUNK: zchunk,
+                                      A.OPT_TILE_Y: tile_y})
+        np.testing.assert_array_equal(r["fields"], base["fields"])
+        np.testing.assert_allclose(r["g"], base["g"], rtol=1e-6, atol=1e-12 * np.abs(base["g"]).max())
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "e4m3"])
+@pytest.mark.parametrize("scaled", [False, True])
+def test_codec_is_bit_exact_against_torch_casts(F, A, dtype, scaled):
+    import ctypes as C
+    if scaled and dtype == "bf16":
+        pytest.skip("bf16 shares FP32's exponent range: no scale")
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "e4m3": torch.float8_e4m3fn}[dtype]
+    rng = np.random.default_rng(3)
+    n = 100003
+    x = (rng.standard_normal(n) * np.exp(rng.uniform(-12, 6, n))).astype(np.float32)
+    if not scaled and dtype == "e4m3":
+        x = np.clip(x, -448, 448)
+    if not scaled and dtype == "f16":
+        x = np.clip(x, -65504, 65504)
+    xd = torch.from_numpy(x).cuda()
+    code = torch.empty(n, dtype=tdt, device="cuda")
+    scale = torch.zeros(1, dtype=torch.float32, device="cuda")
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    code_id = A.TAPE[dtype]
+    A.check(A.lib().fdtd_encode(code_id, int(scaled), C.c_void_p(xd.data_ptr()), n,
+                                C.c_void_p(code.data_ptr()), C.c_void_p(scale.data_ptr()), None))
+    A.check(A.lib().fdtd_decode(code_id, C.c_void_p(code.data_ptr()), n,
+                                C.c_void_p(scale.data_ptr()), C.c_void_p(out.data_ptr()), None))
+    s = np.float32(1.0)
+    if scaled:
+        fmax = {"f16": 65504.0, "e4m3": 448.0}[dtype]
+        s = np.float32(np.abs(x).max()) / np.float32(fmax)
+        assert scale.item() == s
+    ref_code = torch.from_numpy((x / s).astype(np.float32)).to(tdt)
+    assert torch.equal(code.cpu().view(torch.uint8 if dtype == "e4m3" else torch.int16),
+                       ref_code.view(torch.uint8 if dtype == "e4m3" else torch.int16))
+    ref = (ref_code.to(torch.float32) * torch.tensor(s)).numpy()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+
+
+def test_autograd_function_against_central_differences(F, A):
+    """FDTDGrad's backward vs a directional central difference of its own
+    forward (FP32 fields, FP64 objective), random direction over the box."""
+    w = I.ragged_box(n_steps=100)
+    sim = F.Simulation(w)
+    rec = A.record_cfg("f32", 1)
+    eps_bg = torch.from_numpy(w.eps).cuda()
+    d = torch.from_numpy(w.eps[w.design_slice()].copy()).cuda().requires_grad_(True)
+    L = F.objective(d, eps_bg, sim, rec)
+    L.backward()
+    g = d.grad.double()
+    v = torch.from_numpy(np.random.default_rng(5).standard_normal(w.design_shape)).cuda()
+    v = v / v.norm()
+    h = 1e-2
+    Lp = F.objective((d.detach().double() + h * v).float(), eps_bg, sim, rec).item()
+    Lm = F.objective((d.detach().double() - h * v).float(), eps_bg, sim, rec).item()
+    fd = (Lp - Lm) / (2 * h)
+    an = float((g * v).sum())
+    assert abs(fd - an) <= 2e-3 * abs(an) + 1e-9 * abs(L.item())
+
+
+def test_host_buffer_path_matches_device_path(F, A):
+    w = SMALL["ragged_poynting"]()
+    rec = A.record_cfg("bf16", 2, "cubic")
+    r = gpu_run(F, A, w, rec=rec, seed=0.75)
+    sim = F.Simulation(w)
+    eps_h = torch.from_numpy(w.eps).pin_memory()
+    L, gh = sim.value_and_grad_host(eps_h, rec, seed=0.75)
+    assert L == pytest.approx(r["L"], rel=1e-12)
+    np.testing.assert_allclose(gh.numpy(), r["g"], rtol=1e-12, atol=1e-30)
+
+
+def test_group_calls_match_single_calls(F, A):
+    ws = I.batched_cubes(n_sims=3, sizes=(20, 24, 28), steps=(60, 90))
+    rec = A.record_cfg("bf16", 4, "linear")
+    sims = [F.Simulation(w) for w in ws]
+    eps = [torch.from_numpy(w.eps).cuda() for w in ws]
+    objs = F.group_forward(sims, eps, rec)
+    grads = F.group_backward(sims, seeds=[1.0, 2.0, -1.0])
+    for w, o, g, s in zip(ws, objs, grads, [1.0, 2.0, -1.0]):
+        r = gpu_run(F, A, w, rec=rec, seed=s)
+        assert o == pytest.approx(r["L"], rel=1e-12)
+        np.testing.assert_allclose(g.cpu().numpy(), r["g"], rtol=1e-10, atol=1e-30)
+
+
+def test_error_statuses(F, A):
+    import ctypes as C
+    w = SMALL["fd_cube"]()
+    sim = F.Simulation(w)
+    rec = A.record_cfg("f32", 1)
+    sim.ensure_workspace(rec)
+    g = torch.empty(w.design_shape, device="cuda")
+    rc = A.lib().fdtd_backward(sim.h, 1.0, C.c_void_p(g.data_ptr()))
+    assert rc == A.FDTD_ESTATE
+    bad = torch.from_numpy(w.eps).cuda()
+    bad[4, 4, 4] = 0.5
+    with pytest.raises(A.FdtdError) as e:
+        sim.forward(bad, rec)
+    assert e.value.status == A.FDTD_ENONFINITE
+    bad[4, 4, 4] = float("nan")
+    with pytest.raises(A.FdtdError) as e:
+        sim.forward(bad, rec)
+    assert e.value.status == A.FDTD_ENONFINITE
+    # a valid run afterwards still works and a second backward is refused
+    sim.forward(torch.from_numpy(w.eps).cuda(), rec)
+    sim.backward()
+    rc = A.lib().fdtd_backward(sim.h, 1.0, C.c_void_p(g.data_ptr()))
+    assert rc == A.FDTD_ESTATE
