@@ -537,7 +537,7 @@ extern "C" int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec,
 extern "C" int fdtd_bind_workspace(fdtd_handle* h, void* dptr, size_t bytes) {
   if (!h) return FDTD_EINVAL;
   if (!dptr || ((uintptr_t)dptr & 255)) return fail(h, FDTD_EINVAL, "workspace must be 256-byte aligned");
-  if (bytes < layout_of(h, nullptr).total) return fail(h, FDTD_ENOMEM, "workspace too small");
+  if (bytes < layout_of(h, nullptr).tape) return fail(h, FDTD_ENOMEM, "workspace too small");
   if (h->cuda_ready) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   h->ws = (char*)dptr;
@@ -556,8 +556,8 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
-      if (value != 1 && value != 2 && value != 4 && value != 8)
-        return fail(h, FDTD_EINVAL, "tile_y must be 1, 2, 4 or 8");
+      if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+        return fail(h, FDTD_EINVAL, "tile_y must be 1, 2, 4, 8 or 16");
       h->opt_tile_y = value;
       break;
     case FDTD_OPT_ZCHUNK:
@@ -733,6 +733,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if ((e = cudaMemsetAsync(h->ws + L.psiF[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream))) return e;
   int r = (h->N - 1) % rec->k;
+  const bool fused = h->opt_kernel == 1;
+  int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
   char* tape = h->ws + L.tape;
@@ -744,15 +746,39 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     bool sm = sampled(h, n);
     a.jn = h->wave[n];
     a.obj = (double*)(h->ws + L.obj) + n;
+    const bool rec_now = n >= r && (n - r) % rec->k == 0;
+    const int j = rec_now ? (n - r) / rec->k : 0;
+    if (fused) {
+      // one pass: (E^n, Ht^{n-1/2}) in F[cur] -> (E^{n+1}, Ht^{n+1/2}) in F[cur^1]
+      float* Fo = (float*)(h->ws + L.F[cur ^ 1]);
+      float* po = (float*)(h->ws + L.psiF[cur ^ 1]);
+      a.F = (float*)(h->ws + L.F[cur]);
+      a.psiA = (float*)(h->ws + L.psiF[cur]);
+      if ((e = mark(h, FDTD_K_FUSED_FWD, 0, sm))) return e;
+      if ((e = launch_fused_fwd(a, Fo, po, h->stream))) return e;
+      if ((e = mark(h, FDTD_K_FUSED_FWD, 1, sm))) return e;
+      ++nl;
+      if (rec_now) {
+        bool sr = sampled(h, nrec++);
+        if ((e = mark(h, FDTD_K_RECORD, 0, sr))) return e;
+        if ((e = launch_record(rec->dtype, rec->scaled, Fo, a.F, a.g, h->faces,
+                               tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
+                               h->stream)))
+          return e;
+        if ((e = mark(h, FDTD_K_RECORD, 1, sr))) return e;
+        ++nl;
+      }
+      cur ^= 1;
+      continue;
+    }
     if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
     if ((e = launch_fwd_h(a, h->stream))) return e;
     if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
     ++nl;
-    if (n >= r && (n - r) % rec->k == 0) {
-      int j = (n - r) / rec->k;
+    if (rec_now) {
       bool sr = sampled(h, nrec++);
       if ((e = mark(h, FDTD_K_RECORD, 0, sr))) return e;
-      if ((e = launch_record(rec->dtype, rec->scaled, a.F, a.g, h->faces,
+      if ((e = launch_record(rec->dtype, rec->scaled, a.F, a.F, a.g, h->faces,
                              tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
                              h->stream)))
         return e;
@@ -764,6 +790,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
     ++nl;
   }
+  h->fwd_buf = cur;
   *launches = nl;
   return cudaSuccess;
 }
@@ -875,7 +902,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   rc = run_loop(h, rec, 0, enqueue_forward, &nl, h->t0, h->t1);
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = 0;
+  h->fwd_buf = (h->opt_kernel == 1) ? (h->N & 1) : 0;
   h->fwd_rec = *rec;
   return FDTD_OK;
 }

@@ -149,14 +149,15 @@ cudaError_t launch_fwd_h(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
-cudaError_t launch_fused_fwd(const StepArgs& a, float* Fout, cudaStream_t s);
+cudaError_t launch_fused_fwd(const StepArgs& a, float* Fout, float* psiOut, cudaStream_t s);
 cudaError_t launch_fused_rev(const StepArgs& a, float* Fout, float* Lout, cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);
 cudaError_t launch_gather(const float* F, Geo g, float* out, cudaStream_t s);
-cudaError_t launch_record(int dtype, int scaled, const float* F, Geo g, const Faces& fc,
-                          void* tape_sample, float* scale_slot, cudaStream_t s);
+// FH holds Ht^{n+1/2} (low faces), FE holds E^n (high faces).
+cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* FE, Geo g,
+                          const Faces& fc, void* tape_sample, float* scale_slot, cudaStream_t s);
 cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
                                 const void* tape, long long sample_stride, const float* scales,
                                 const Interp& ip, const Det& det, cudaStream_t s);

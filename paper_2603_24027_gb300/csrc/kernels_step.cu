@@ -36,9 +36,9 @@ __device__ __forceinline__ float cpml_fwd(float d, float* psi, long long pi, con
                                           int pos, int side) {
   float b = prof(g, ax, side + 0, pos), a = prof(g, ax, side + 1, pos),
         kv = prof(g, ax, side + 2, pos);
-  float s = b * psi[pi] + a * d;
+  float s = __fmaf_rn(b, psi[pi], __fmul_rn(a, d));  // same rounding sequence as the fused kernel
   psi[pi] = s;
-  return kv * d + s;
+  return __fmaf_rn(kv, d, s);
 }
 
 // ------------------------------------------------------------------ prep ---
@@ -127,14 +127,17 @@ __global__ void __launch_bounds__(256) k_fwd_h(StepArgs a) {
   }
 }
 
+// Split kernels are built for at most 256 threads: tile heights above 8 run as 8.
+static int split_ty(const StepArgs& a) { return a.tile_y > 8 ? 8 : a.tile_y; }
+
 static dim3 step_grid(const StepArgs& a) {
-  int ty = a.tile_y;
+  int ty = split_ty(a);
   int zc = a.zchunk;
   return dim3((a.g.nx + 31) / 32, (a.g.ny + ty - 1) / ty, (a.g.nz + zc - 1) / zc);
 }
 
 cudaError_t launch_fwd_h(const StepArgs& a, cudaStream_t s) {
-  k_fwd_h<<<step_grid(a), dim3(32, a.tile_y), 0, s>>>(a);
+  k_fwd_h<<<step_grid(a), dim3(32, split_ty(a)), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(256) k_fwd_e(StepArgs a) {
 }
 
 cudaError_t launch_fwd_e(const StepArgs& a, cudaStream_t s) {
-  k_fwd_e<<<step_grid(a), dim3(32, a.tile_y), 0, s>>>(a);
+  k_fwd_e<<<step_grid(a), dim3(32, split_ty(a)), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(256) k_rev_e(StepArgs a) {
 }
 
 cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s) {
-  k_rev_e<<<step_grid(a), dim3(32, a.tile_y), 0, s>>>(a);
+  k_rev_e<<<step_grid(a), dim3(32, split_ty(a)), 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(256) k_rev_h(StepArgs a) {
 }
 
 cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s) {
-  k_rev_h<<<step_grid(a), dim3(32, a.tile_y), 0, s>>>(a);
+  k_rev_h<<<step_grid(a), dim3(32, split_ty(a)), 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -42,7 +42,8 @@ __device__ __forceinline__ long long face_cell(const Geo& g, const FaceDesc& f, 
 }
 
 template <int DT>
-__global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict__ F, Geo g,
+__global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict__ FH,
+                                                        const float* __restrict__ FE, Geo g,
                                                         Faces fc, void* tape_sample,
                                                         float* scale_slot, int scaled) {
   typedef typename Code<DT>::T T;
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict_
   cg::cluster_group cluster = cg::this_cluster();
   const int f = blockIdx.y;
   const FaceDesc fd = fc.f[f];
+  const float* __restrict__ F = (f & 1) ? FE : FH;
   const int n = 2 * fd.nu * fd.nv;
   const int rank = (int)cluster.block_rank();
   const int nr = (int)cluster.num_blocks();
@@ -88,8 +90,9 @@ __global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict_
 }
 
 template <int DT>
-static cudaError_t launch_record_t(int scaled, const float* F, Geo g, const Faces& fc,
-                                   void* tape_sample, float* scale_slot, cudaStream_t s) {
+static cudaError_t launch_record_t(int scaled, const float* FH, const float* FE, Geo g,
+                                   const Faces& fc, void* tape_sample, float* scale_slot,
+                                   cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(REC_CLUSTER, 6, 1);
   cfg.blockDim = dim3(REC_THREADS, 1, 1);
@@ -102,16 +105,16 @@ static cudaError_t launch_record_t(int scaled, const float* F, Geo g, const Face
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_record<DT>, F, g, fc, tape_sample, scale_slot, scaled);
+  return cudaLaunchKernelEx(&cfg, k_record<DT>, FH, FE, g, fc, tape_sample, scale_slot, scaled);
 }
 
-cudaError_t launch_record(int dtype, int scaled, const float* F, Geo g, const Faces& fc,
-                          void* tape_sample, float* scale_slot, cudaStream_t s) {
+cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* FE, Geo g,
+                          const Faces& fc, void* tape_sample, float* scale_slot, cudaStream_t s) {
   switch (dtype) {
-    case 0: return launch_record_t<0>(0, F, g, fc, tape_sample, scale_slot, s);
-    case 1: return launch_record_t<1>(0, F, g, fc, tape_sample, scale_slot, s);
-    case 2: return launch_record_t<2>(scaled, F, g, fc, tape_sample, scale_slot, s);
-    case 3: return launch_record_t<3>(scaled, F, g, fc, tape_sample, scale_slot, s);
+    case 0: return launch_record_t<0>(0, FH, FE, g, fc, tape_sample, scale_slot, s);
+    case 1: return launch_record_t<1>(0, FH, FE, g, fc, tape_sample, scale_slot, s);
+    case 2: return launch_record_t<2>(scaled, FH, FE, g, fc, tape_sample, scale_slot, s);
+    case 3: return launch_record_t<3>(scaled, FH, FE, g, fc, tape_sample, scale_slot, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -249,17 +249,21 @@ def ragged_box(nx=70, ny=21, nz=19, P=6, n_steps=80, seed: int = 0,
     dx = 25e-9
     kw = dict(det_kind=det_kind)
     if det_kind == OBJ_POYNTING_PLANE:
-        kw.update(det_axis=0, det_index=nx - P - 2, det_lo=(P, P), det_hi=(ny - P, nz - P))
+        kw.update(det_axis=0, det_index=min(nx - P - 2, P + 11), det_lo=(P, P),
+                  det_hi=(ny - P, nz - P))
     else:
-        kw.update(det_axis=2, det_index=nz - P - 2, det_lo=(P + 1, P + 1), det_hi=(nx - P - 1, ny - P - 1))
+        kw.update(det_axis=2, det_index=min(nz - P - 2, P + 9), det_lo=(P + 1, P + 1),
+                  det_hi=(nx - P - 1, ny - P - 1))
     if src_kind == SRC_PLANE_GAUSS:
         kw.update(src_kind=src_kind, src_component=1, src_axis=0, src_pos=(P + 1, ny // 2, nz // 2),
                   src_sigma_uv=(2.5, 2.0))
     else:
         kw.update(src_kind=src_kind, src_component=2, src_pos=(nx // 3, ny // 2, P + 1))
+    # broadband pulse (rel. bandwidth 1, ~41-step envelope) so that it reaches
+    # the detector within a short run
     return Workload(name=f"ragged{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dt=cfl_dt(dx),
                     n_steps=n_steps, pml_thickness=P, eps=eps, design_lo=lo, design_hi=hi,
-                    t0_over_tau=0.7, **kw)
+                    rel_bandwidth=1.0, t0_over_tau=1.2, **kw)
 
 
 def fd_cube(seed: int = 0, n_steps: int = 60) -> Workload:
