@@ -220,6 +220,38 @@ int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code
 int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale, float* d_out,
                 void* cuda_stream);
 
+/* ------------------------------------------------ no-allocation variant --- */
+
+/* Largest workspace (bytes) fdtd_value_and_grad_noalloc can hold. */
+#define FDTD_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* Forward + backward without any device allocation, for callers that cannot
+ * allocate device memory themselves: code that runs while someone else's
+ * CUDA-graph capture is active (cudaMalloc is not permitted then), or
+ * deployments whose device memory budget is fixed up front.  The paper has no
+ * counterpart; this is a library convenience.
+ *
+ * Instead of a caller-bound workspace it uses one scratch array compiled into
+ * the library: FDTD_NOALLOC_SCRATCH_BYTES (64 MiB) per GPU, reserved on every
+ * GPU that loads the library and held until the process exits.  Problems
+ * whose workspace (fdtd_workspace_bytes with the same rec) exceeds it are
+ * rejected with FDTD_ENOMEM and a message giving both sizes.
+ *
+ * Arguments and results are those of fdtd_forward followed by fdtd_backward:
+ * d_eps (device, float32 [nz][ny][nx]), seed, *objective (host), d_grad
+ * (device, float32 design box).  Work is queued on the handle's stream and
+ * the call blocks until done.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.  The call
+ * itself calls no cudaMalloc / cudaFree, creates no stream, event or graph,
+ * and clears every part of the scratch it reads before using it.  All calls
+ * on a device share the one array, so calls that overlap on the GPU (from
+ * several threads or streams) race: serialise them.  The handle's own
+ * workspace binding, if any, is left untouched; after this call
+ * fdtd_backward needs a new fdtd_forward. */
+int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec,
+                                double seed, double* objective, float* d_grad);
+
 #ifdef __cplusplus
 }
 #endif

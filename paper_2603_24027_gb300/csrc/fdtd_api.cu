@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1078,4 +1079,112 @@ extern "C" int fdtd_decode(int dtype, const void* d_code, size_t n, const float*
   cudaError_t e = launch_decode(dtype, d_code, n, d_scale, d_out, (cudaStream_t)cuda_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
+}
+
+// ------------------------------------------------ no-allocation variant ---
+// A fixed scratch area compiled into the library stands in for the caller's
+// workspace.  Host code must not use g_noalloc_scratch's name as a device
+// address (it is a host-side stand-in); the address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FDTD_NOALLOC_SCRATCH_BYTES];
+
+static void* g_noalloc_ptr[256];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(fdtd_handle* h, void** out) {
+  int dev = 0;
+  CK(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(h, FDTD_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(h, "cudaGetSymbolAddress(noalloc scratch)", e);
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
+                                           const fdtd_record_cfg* rec, double seed,
+                                           double* objective, float* d_grad) {
+  if (!h) return FDTD_EINVAL;
+  int rc = check_rec(h, rec);
+  if (rc) return rc;
+  if (!d_eps || !d_grad) return fail(h, FDTD_EINVAL, "NULL device buffer");
+  Layout L = layout_of(h, rec);
+  if (L.total > FDTD_NOALLOC_SCRATCH_BYTES) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "problem needs a %zu-byte workspace; the fixed no-allocation scratch holds %llu bytes",
+             L.total, (unsigned long long)FDTD_NOALLOC_SCRATCH_BYTES);
+    return fail(h, FDTD_ENOMEM, buf);
+  }
+  void* scratch = nullptr;
+  rc = noalloc_scratch(h, &scratch);
+  if (rc) return rc;
+
+  // Run the usual time loops on the caller's stream with the scratch as the
+  // workspace: direct launches (no graph), no sampling events.
+  char* ws0 = h->ws;
+  size_t b0 = h->ws_bytes;
+  bool up0 = h->tables_uploaded;
+  cudaStream_t s0 = h->stream;
+  int samp0 = h->opt_sample;
+  h->ws = (char*)scratch;
+  h->ws_bytes = FDTD_NOALLOC_SCRATCH_BYTES;
+  h->stream = h->user_stream;
+  h->opt_sample = 0;
+  h->have_forward = false;
+  auto restore = [&]() {
+    h->ws = ws0;
+    h->ws_bytes = b0;
+    h->tables_uploaded = up0;
+    h->stream = s0;
+    h->opt_sample = samp0;
+    h->have_forward = false;
+  };
+  auto run = [&]() -> int {
+    cudaStream_t s = h->stream;
+    Layout L0 = layout_of(h, nullptr);
+    CK(h, cudaMemcpyAsync(h->ws + L0.prof, h->prof.data(), h->prof.size() * sizeof(float),
+                          cudaMemcpyHostToDevice, s));
+    if (!h->srcw.empty())
+      CK(h, cudaMemcpyAsync(h->ws + L0.srcw, h->srcw.data(), h->srcw.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, s));
+    Geo g = geo_of(h);
+    CK(h, launch_prep(d_eps, (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), s));
+    int nl = 0;
+    cudaError_t e = enqueue_forward(h, rec, &nl);
+    if (e) return cuda_fail(h, "forward launch", e);
+    h->fwd_buf = (h->opt_kernel == 1) ? (h->N & 1) : 0;
+    // objective: per-step slots summed on the host in chunks
+    double sum = 0.0, chunk[256];
+    for (int n0 = 0; n0 < h->N; n0 += 256) {
+      int m = h->N - n0 < 256 ? h->N - n0 : 256;
+      CK(h, cudaMemcpyAsync(chunk, h->ws + L.obj + (size_t)n0 * sizeof(double),
+                            m * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaStreamSynchronize(s));
+      for (int i = 0; i < m; ++i) sum += chunk[i];
+    }
+    unsigned err = 0;
+    CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
+    if (!isfinite(sum)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
+    e = enqueue_backward(h, rec, &nl);
+    if (e) return cuda_fail(h, "backward launch", e);
+    CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g,
+                          h->dlo, h->dhi, seed, d_grad, (unsigned*)(h->ws + L.err), s));
+    CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
+    if (objective) *objective = sum;
+    return FDTD_OK;
+  };
+  rc = run();
+  restore();
+  return rc;
 }
