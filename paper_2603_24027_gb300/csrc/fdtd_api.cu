@@ -63,6 +63,10 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample;
+  // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
+  FwdMaps fmaps[2];
+  char* maps_ws;
+  int maps_ty;
   // sampled kernel timing: event pairs per kernel kind
   std::vector<cudaEvent_t> sev[FDTD_K_KINDS][2];
   int sused[FDTD_K_KINDS];
@@ -331,10 +335,7 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   Layout L;
   size_t nc = (size_t)h->nz * h->ny * h->px;
   size_t f6 = al(6 * nc * sizeof(float));
-  size_t P2 = 2 * (size_t)h->P;
-  size_t ps = 4 * ((size_t)h->nz * h->ny * P2 + (size_t)h->nz * P2 * h->px +
-                   P2 * h->ny * h->px);
-  size_t psb = al(ps * sizeof(float));
+  size_t psb = al(12 * nc * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
   size_t off = 0;
   L.F[0] = off; off += f6;
@@ -372,11 +373,7 @@ static Geo geo_of(const fdtd_handle* h) {
   g.plane = (long long)h->ny * h->px;
   g.nc = (long long)h->nz * g.plane;
   g.S = (float)h->S;
-  long long P2 = 2LL * h->P;
-  g.psx = 0;
-  g.psy = 4LL * h->nz * h->ny * P2;
-  g.psz = g.psy + 4LL * h->nz * P2 * h->px;
-  g.ps_total = g.psz + 4LL * P2 * h->ny * h->px;
+  g.ps_total = 12LL * g.nc;
   g.prof = nullptr;
   return g;
 }
@@ -478,6 +475,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_sample = 0;
+  h->maps_ws = nullptr;
+  h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
     h->sused[q] = 0; h->savg[q] = 0.f; h->scount[q] = 0;
     h->gsused[0][q] = h->gsused[1][q] = 0;
@@ -553,7 +552,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
   switch (option) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
-      if (value != 0 && value != 1) return fail(h, FDTD_EINVAL, "kernel must be 0 or 1");
+      if (value < 0 || value > 3) return fail(h, FDTD_EINVAL, "kernel must be 0..3");
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
@@ -670,6 +669,7 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.det.v0 = h->det.lo[1]; a.det.v1 = h->det.hi[1];
   a.tile_y = h->opt_tile_y;
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
+  a.err = (unsigned*)(h->ws + L.err);
   return a;
 }
 
@@ -734,7 +734,23 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if ((e = cudaMemsetAsync(h->ws + L.psiF[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream))) return e;
   int r = (h->N - 1) % rec->k;
-  const bool fused = h->opt_kernel == 1;
+  const bool fused = h->opt_kernel == 1 || h->opt_kernel == 2;
+  const bool tma = h->opt_kernel == 2;
+  const bool split_tma = h->opt_kernel == 3;
+  SplitMaps smaps;
+  if (split_tma &&
+      (e = encode_split_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
+                             (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
+                             h->opt_tile_y, &smaps)))
+    return e;
+  if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
+    for (int b = 0; b < 2; ++b)
+      if ((e = encode_fwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb), a.g,
+                               h->opt_tile_y, &h->fmaps[b])))
+        return e;
+    h->maps_ws = h->ws;
+    h->maps_ty = h->opt_tile_y;
+  }
   int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
@@ -756,7 +772,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       a.F = (float*)(h->ws + L.F[cur]);
       a.psiA = (float*)(h->ws + L.psiF[cur]);
       if ((e = mark(h, FDTD_K_FUSED_FWD, 0, sm))) return e;
-      if ((e = launch_fused_fwd(a, Fo, po, h->stream))) return e;
+      if ((e = tma ? launch_fwd_tma(h->fmaps[cur], a, Fo, po, h->stream)
+                   : launch_fused_fwd(a, Fo, po, h->stream)))
+        return e;
       if ((e = mark(h, FDTD_K_FUSED_FWD, 1, sm))) return e;
       ++nl;
       if (rec_now) {
@@ -773,7 +791,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
-    if ((e = launch_fwd_h(a, h->stream))) return e;
+    if ((e = split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
+      return e;
     if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
     ++nl;
     if (rec_now) {
@@ -787,7 +806,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
     }
     if ((e = mark(h, FDTD_K_FWD_E, 0, sm))) return e;
-    if ((e = launch_fwd_e(a, h->stream))) return e;
+    if ((e = split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
+      return e;
     if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
     ++nl;
   }
@@ -812,6 +832,14 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
   int cur = 0;
+  const bool rtma = h->opt_kernel >= 2;
+  SplitMaps rmaps[2];
+  if (rtma)
+    for (int b = 0; b < 2; ++b)
+      if ((e = encode_split_maps(a.F, a.L, (const float*)(h->ws + L.cb),
+                                 (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
+                                 &rmaps[b])))
+        return e;
   reset_samples(h, kBwdKinds, 4);
   for (int n = h->N - 1; n >= 0; --n) {
     bool sm = sampled(h, n);
@@ -827,10 +855,12 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = mark(h, FDTD_K_REV_E, 0, sm))) return e;
-    if ((e = launch_rev_e(a, h->stream))) return e;
+    if ((e = rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
+      return e;
     if ((e = mark(h, FDTD_K_REV_E, 1, sm))) return e;
     if ((e = mark(h, FDTD_K_REV_H, 0, sm))) return e;
-    if ((e = launch_rev_h(a, h->stream))) return e;
+    if ((e = rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
+      return e;
     if ((e = mark(h, FDTD_K_REV_H, 1, sm))) return e;
     cur ^= 1;
     nl += 3;
@@ -903,7 +933,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   rc = run_loop(h, rec, 0, enqueue_forward, &nl, h->t0, h->t1);
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = (h->opt_kernel == 1) ? (h->N & 1) : 0;
+  h->fwd_buf = (h->opt_kernel == 1 || h->opt_kernel == 2) ? (h->N & 1) : 0;
   h->fwd_rec = *rec;
   return FDTD_OK;
 }
@@ -921,6 +951,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
+  if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
   double s = 0.0;
   for (double v : h->obj_hist) s += v;
   if (!isfinite(s)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
@@ -961,6 +992,7 @@ static int backward_finish(fdtd_handle* h, double seed, float* d_grad) {
   collect_samples(h, kBwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
+  if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
   if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
   return FDTD_OK;
 }
@@ -1159,7 +1191,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
     if (e) return cuda_fail(h, "forward launch", e);
-    h->fwd_buf = (h->opt_kernel == 1) ? (h->N & 1) : 0;
+    h->fwd_buf = (h->opt_kernel == 1 || h->opt_kernel == 2) ? (h->N & 1) : 0;
     // objective: per-step slots summed on the host in chunks
     double sum = 0.0, chunk[256];
     for (int n0 = 0; n0 < h->N; n0 += 256) {

@@ -3,8 +3,9 @@
 // Layout in HBM (all float32 unless noted, x fastest, rows padded to px):
 //   fields   F[6][nz][ny][px]       Ex Ey Ez Hx Hy Hz   (E, Ht = eta0 H)
 //   cb       [nz][ny][px]           S / eps_r
-//   psi set  x-slab [4][nz][ny][2P], y-slab [4][nz][2P][px], z-slab [4][2P][ny][px]
-//            (convolutional-PML auxiliaries only where they are non-zero)
+//   psi set  [3 axes][4][nz][ny][px] (convolutional-PML auxiliaries; only the
+//            cells of each axis' absorbing slabs are ever read or written, the
+//            full-grid layout lets the TMA stage them with the field boxes)
 //   profiles [3 axes][6][nmax]      b_E a_E 1/kappa_E b_H a_H 1/kappa_H
 // psi components per axis slab (curl term, sign):
 //   x: 0 (Hy, -dEz/dx) 1 (Hz, +dEy/dx) 2 (Ey, -dHz/dx) 3 (Ez, +dHy/dx)
@@ -12,6 +13,7 @@
 //   z: 0 (Hx, -dEy/dz) 1 (Hy, +dEx/dz) 2 (Ex, -dHy/dz) 3 (Ey, +dHx/dz)
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -29,8 +31,7 @@ struct Geo {
   long long nc;     // nz * plane (one component)
   float S;
   const float* prof;
-  long long psx, psy, psz;  // element offsets of the y and z slabs inside a psi set (psx = 0)
-  long long ps_total;       // elements per psi set
+  long long ps_total;       // elements per psi set (12 * nc)
 };
 
 // Source region: plane normal `axis` at `index`, cells (u,v) in [u0,u1)x[v0,v1),
@@ -66,17 +67,18 @@ __device__ __forceinline__ float prof(const Geo& g, int axis, int which, int i) 
 
 __device__ __forceinline__ bool in_slab(int pos, int n, int P) { return pos < P || pos >= n - P; }
 
+// psi component c (0..3) of axis a at cell (i, j, k): full-grid layout.
+__device__ __forceinline__ long long psi_at(const Geo& g, int a, int c, int i, int j, int k) {
+  return (long long)(a * 4 + c) * g.nc + (long long)k * g.plane + (long long)j * g.px + i;
+}
 __device__ __forceinline__ long long psi_x(const Geo& g, int c, int i, int j, int k) {
-  int s = i < g.P ? i : i - (g.nx - 2 * g.P);
-  return (((long long)c * g.nz + k) * g.ny + j) * (2 * g.P) + s;
+  return psi_at(g, 0, c, i, j, k);
 }
 __device__ __forceinline__ long long psi_y(const Geo& g, int c, int i, int j, int k) {
-  int s = j < g.P ? j : j - (g.ny - 2 * g.P);
-  return g.psy + (((long long)c * g.nz + k) * (2 * g.P) + s) * g.px + i;
+  return psi_at(g, 1, c, i, j, k);
 }
 __device__ __forceinline__ long long psi_z(const Geo& g, int c, int i, int j, int k) {
-  int s = k < g.P ? k : k - (g.nz - 2 * g.P);
-  return g.psz + (((long long)c * (2 * g.P) + s) * g.ny + j) * g.px + i;
+  return psi_at(g, 2, c, i, j, k);
 }
 
 // Plane membership: p = (i, j, k); (u, v) = the two other axes in increasing order.
@@ -142,6 +144,13 @@ struct StepArgs {
   float jn;        // J waveform value of this step
   int zchunk;
   int tile_y;
+  unsigned* err;   // device error word (ERR_*)
+};
+
+// Tensor maps of the TMA kernels: E and Ht boxes of one field buffer and the
+// cb box, each a 4D (x, y, z, component) view.
+struct alignas(64) FwdMaps {
+  CUtensorMap E, H, cb;
 };
 
 cudaError_t launch_prep(const float* eps, float* cb, Geo g, unsigned* err, cudaStream_t s);
@@ -151,6 +160,20 @@ cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fused_fwd(const StepArgs& a, float* Fout, float* psiOut, cudaStream_t s);
 cudaError_t launch_fused_rev(const StepArgs& a, float* Fout, float* Lout, cudaStream_t s);
+cudaError_t encode_fwd_maps(const float* F, const float* cb, const Geo& g, int ty, FwdMaps* m);
+
+// Tensor maps of the TMA half-step kernels: "h" = halo box {40, ty+2} at
+// (x0-4, y0-1), "o" = own box {32, ty} at (x0, y0), over the field buffer F,
+// the adjoint buffer L, cb and the psi set read by the kernel.
+struct alignas(64) SplitMaps {
+  CUtensorMap Fh, Fo, Lh, Lo, cbh, cbo, Ph, Po;
+};
+cudaError_t encode_split_maps(const float* F, const float* L, const float* cb, const float* psiA,
+                              const Geo& g, int ty, SplitMaps* m);
+// which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
+cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
+                           cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);

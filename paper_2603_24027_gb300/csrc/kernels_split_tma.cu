@@ -1,0 +1,774 @@
+// kernels_split_tma.cu -- half-step kernels with TMA-staged planes.
+//
+// The four half-steps of the method, each an in-place update of one family
+// of arrays that reads only arrays it does not write (as in kernels_step.cu):
+//   k_sfwd_h  Ht^{n+1/2} = Ht^{n-1/2} - S curlE(E^n)            (+ psi_H)
+//   k_sfwd_e  E^{n+1} = E^n + cb (curlH(Ht^{n+1/2}) - J)         (+ psi_E, objective)
+//   k_srev_e  E^n = E^{n+1} - cb (curlH Ht^{n+1/2} - J) on the interior, dL/dcb,
+//             lam_H += transpose of the E half-step               (+ lam_psi_E)
+//   k_srev_h  Ht^{n-1/2} = Ht^{n+1/2} + S curlE E^n on the interior,
+//             lam_E += transpose of the H half-step               (+ lam_psi_H)
+// A CTA owns a 32 x TY column tile and a z chunk [k0, k1).  The planes it
+// reads (k0-1 .. k1 at most) stream through an S-stage ring: "halo" boxes cover x in [x0-4, x0+36),
+// y in [y0-1, y0+TY+1) (neighbours at +-1), "own" boxes the tile itself.
+// Out-of-grid box elements arrive as zeros (the zero-padding boundary).  The
+// CPML auxiliaries are staged only for tiles/planes inside an absorbing slab.
+// Per-cell arithmetic matches kernels_step.cu operation for operation.
+#include <cudaTypedefs.h>
+
+#include "fdtd_internal.cuh"
+#include "tma.cuh"
+
+namespace fdtd {
+
+template <int TY>
+struct SL {
+  static constexpr int HW = 40, HR = TY + 2, HP = HW * HR;   // halo box plane (floats)
+  static constexpr int OW = 32, OR = TY, OP = OW * OR;       // own box plane
+  static constexpr int r128(int b) { return (b + 127) / 128 * 128; }
+};
+
+__device__ __forceinline__ float cpml_s(float d, float psi_old, float* pout, long long pi, float b,
+                                        float a, float kv) {
+  float s = __fmaf_rn(b, psi_old, __fmul_rn(a, d));
+  pout[pi] = s;
+  return __fmaf_rn(kv, d, s);
+}
+
+__device__ __forceinline__ float adj_s(float v, float lpsi, float* pout, long long pi, bool own,
+                                       float b, float a, float kv) {
+  float mu = lpsi + v;
+  if (own) pout[pi] = b * mu;
+  return kv * v + a * mu;
+}
+
+__device__ __forceinline__ float src_wt(const Src& s, int i, int j, int k) {
+  int u, v;
+  if (s.kind == 0 || !on_plane(s.axis, s.index, s.u0, s.u1, s.v0, s.v1, i, j, k, &u, &v))
+    return 0.f;
+  return __ldg(s.w + (long long)(v - s.v0) * (s.u1 - s.u0) + (u - s.u0));
+}
+
+// ------------------------------------------------------------ pipeline ---
+// Ring over planes p0..p1.  Plane p lives in stage (p - p0) % S; its barrier
+// completes once per use, parity ((p - p0) / S) & 1.  Every issued plane must
+// be waited for before its stage is re-armed and before the CTA exits (a bulk
+// copy still landing in shared memory of a finished CTA is not allowed), so
+// each kernel's ring spans exactly the planes it reads.
+template <int S>
+struct Ring {
+  unsigned char* base;
+  uint64_t* bars;
+  int stage_bytes, p0, p1;
+  __device__ unsigned char* at(int p) const { return base + ((p - p0) % S) * stage_bytes; }
+  __device__ uint64_t* bar(int p) const { return &bars[(p - p0) % S]; }
+  __device__ uint32_t parity(int p) const { return ((p - p0) / S) & 1; }
+  __device__ bool wait(int p) const { return mbar_wait(bar(p), parity(p), kWaitCycles); }
+};
+
+// Common CTA prologue: barrier setup.  Returns the ring.
+template <int S>
+__device__ __forceinline__ Ring<S> ring_setup(unsigned char* dsm, int stage_bytes, int p0, int p1) {
+  Ring<S> r;
+  r.base = dsm;
+  r.bars = reinterpret_cast<uint64_t*>(dsm + S * stage_bytes);
+  r.stage_bytes = stage_bytes;
+  r.p0 = p0;
+  r.p1 = p1;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&r.bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  return r;
+}
+
+template <int S>
+__device__ void ring_drain(const Ring<S>& r, unsigned* err) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    atomicOr(err, ERR_TIMEOUT);
+    for (int p = r.p1; p >= r.p0 && p > r.p1 - S; --p) r.wait(p);
+  }
+}
+
+__device__ __forceinline__ bool tile_in_slab(int lo, int hi_incl, int n, int P) {
+  return lo < P || hi_incl >= n - P;
+}
+
+// =================================================== forward H half-step ===
+template <int TY, int S>
+struct FH {
+  typedef SL<TY> L;
+  static constexpr int E = 0;                                   // E halo, 3 comps
+  static constexpr int H = L::r128(3 * L::HP * 4);              // H own, 3 comps
+  static constexpr int PX = H + L::r128(3 * L::OP * 4);         // psi own 2 comps, x/y/z
+  static constexpr int PY = PX + L::r128(2 * L::OP * 4);
+  static constexpr int PZ = PY + L::r128(2 * L::OP * 4);
+  static constexpr int STAGE = PZ + L::r128(2 * L::OP * 4);
+  static int smem() { return S * STAGE + 8 * S; }
+};
+
+template <int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_sfwd_h(const __grid_constant__ SplitMaps m,
+                                                   StepArgs a) {
+  typedef SL<TY> L;
+  typedef FH<TY, S> Y;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const Geo& g = a.g;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool valid = x < g.nx && y < g.ny;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  // planes k0 .. k1 (E at k+1 for the last plane), each waited before reuse
+  Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0, k1);
+  auto issue = [&](int p) {
+    unsigned char* st = R.at(p);
+    uint64_t* bar = R.bar(p);
+    const bool body = p >= k0 && p < k1;
+    const bool zs = body && in_slab(p, g.nz, g.P);
+    uint32_t tx_bytes = 3 * L::HP * 4 + (body ? 3 * L::OP * 4 : 0) +
+                        (body && txs ? 2 * L::OP * 4 : 0) + (body && tys ? 2 * L::OP * 4 : 0) +
+                        (zs ? 2 * L::OP * 4 : 0);
+    mbar_expect_tx(bar, tx_bytes);
+    tma_load_4d(st + Y::E, &m.Fh, bar, x0 - 4, y0 - 1, p, 0);
+    if (body) tma_load_4d(st + Y::H, &m.Fo, bar, x0, y0, p, 3);
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 0);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 4);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 8);
+  };
+  if (tid == 0)
+    for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
+  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f, by = 0.f, ay = 0.f, ky = 1.f;
+  if (valid && sx) { bx = prof(g, 0, PR_BH, x); ax = prof(g, 0, PR_AH, x); kx = prof(g, 0, PR_KH, x); }
+  if (valid && sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
+  const int hi = (ty + 1) * L::HW + tx + 4;   // own cell in a halo box
+  const int oi = ty * L::OW + tx;             // own cell in an own box
+  float* F = a.F;
+  float* psi = a.psiA;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  bool ok = true;
+  for (int k = k0; k < k1; ++k, q += g.plane) {
+    if (!R.wait(k) || !R.wait(k + 1)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
+    if (valid) {
+      const float* Ec = reinterpret_cast<const float*>(R.at(k) + Y::E);
+      const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
+      const float* Ho = reinterpret_cast<const float*>(R.at(k) + Y::H);
+      const float ex = Ec[hi], ey = Ec[L::HP + hi], ez = Ec[2 * L::HP + hi];
+      const float d0 = Ec[2 * L::HP + hi + L::HW] - ez;   // dEz/dy
+      const float d1 = En[L::HP + hi] - ey;               // dEy/dz
+      const float d2 = En[hi] - ex;                       // dEx/dz
+      const float d3 = Ec[2 * L::HP + hi + 1] - ez;       // dEz/dx
+      const float d4 = Ec[L::HP + hi + 1] - ey;           // dEy/dx
+      const float d5 = Ec[hi + L::HW] - ex;               // dEx/dy
+      const bool sz = in_slab(k, g.nz, g.P);
+      float cx, cy, cz;
+      if (!(sx || sy || sz)) {
+        cx = d0 - d1;
+        cy = d2 - d3;
+        cz = d4 - d5;
+      } else {
+        float t0 = d0, t1 = d1, t2 = d2, t3 = d3, t4 = d4, t5 = d5;
+        if (sx) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PX);
+          t3 = cpml_s(d3, P[oi], psi, psi_at(g, 0, 0, x, y, k), bx, ax, kx);
+          t4 = cpml_s(d4, P[L::OP + oi], psi, psi_at(g, 0, 1, x, y, k), bx, ax, kx);
+        }
+        if (sy) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PY);
+          t0 = cpml_s(d0, P[oi], psi, psi_at(g, 1, 0, x, y, k), by, ay, ky);
+          t5 = cpml_s(d5, P[L::OP + oi], psi, psi_at(g, 1, 1, x, y, k), by, ay, ky);
+        }
+        if (sz) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PZ);
+          const float bz = prof(g, 2, PR_BH, k), az = prof(g, 2, PR_AH, k), kz = prof(g, 2, PR_KH, k);
+          t1 = cpml_s(d1, P[oi], psi, psi_at(g, 2, 0, x, y, k), bz, az, kz);
+          t2 = cpml_s(d2, P[L::OP + oi], psi, psi_at(g, 2, 1, x, y, k), bz, az, kz);
+        }
+        cx = t0 - t1;
+        cy = t2 - t3;
+        cz = t4 - t5;
+      }
+      F[3 * g.nc + q] = __fsub_rn(Ho[oi], __fmul_rn(g.S, cx));
+      F[4 * g.nc + q] = __fsub_rn(Ho[L::OP + oi], __fmul_rn(g.S, cy));
+      F[5 * g.nc + q] = __fsub_rn(Ho[2 * L::OP + oi], __fmul_rn(g.S, cz));
+    }
+    __syncthreads();
+    if (tid == 0 && k + S <= R.p1) issue(k + S);   // plane k is no longer read
+  }
+}
+
+// =================================================== forward E half-step ===
+template <int TY, int S>
+struct FE {
+  typedef SL<TY> L;
+  static constexpr int H = 0;                                   // H halo, 3 comps
+  static constexpr int E = L::r128(3 * L::HP * 4);              // E own
+  static constexpr int CB = E + L::r128(3 * L::OP * 4);         // cb own
+  static constexpr int PX = CB + L::r128(L::OP * 4);
+  static constexpr int PY = PX + L::r128(2 * L::OP * 4);
+  static constexpr int PZ = PY + L::r128(2 * L::OP * 4);
+  static constexpr int STAGE = PZ + L::r128(2 * L::OP * 4);
+  static int smem() { return S * STAGE + 8 * S + 256; }
+};
+
+template <int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_sfwd_e(const __grid_constant__ SplitMaps m,
+                                                   StepArgs a) {
+  typedef SL<TY> L;
+  typedef FE<TY, S> Y;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const Geo& g = a.g;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool valid = x < g.nx && y < g.ny;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  // planes k0-1 .. k1-1 (Ht at k-1 for the first plane), each waited before reuse
+  Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0 - 1, k1 - 1);
+  double* red = reinterpret_cast<double*>(dsm + S * Y::STAGE + 8 * S + 64);
+  auto issue = [&](int p) {
+    unsigned char* st = R.at(p);
+    uint64_t* bar = R.bar(p);
+    const bool body = p >= k0 && p < k1;
+    const bool zs = body && in_slab(p, g.nz, g.P);
+    uint32_t tx_bytes = 3 * L::HP * 4 + (body ? 4 * L::OP * 4 : 0) +
+                        (body && txs ? 2 * L::OP * 4 : 0) + (body && tys ? 2 * L::OP * 4 : 0) +
+                        (zs ? 2 * L::OP * 4 : 0);
+    mbar_expect_tx(bar, tx_bytes);
+    tma_load_4d(st + Y::H, &m.Fh, bar, x0 - 4, y0 - 1, p, 3);
+    if (body) {
+      tma_load_4d(st + Y::E, &m.Fo, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::CB, &m.cbo, bar, x0, y0, p, 0);
+    }
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 2);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 6);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 10);
+  };
+  if (tid == 0)
+    for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
+  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f, by = 0.f, ay = 0.f, ky = 1.f;
+  if (valid && sx) { bx = prof(g, 0, PR_BE, x); ax = prof(g, 0, PR_AE, x); kx = prof(g, 0, PR_KE, x); }
+  if (valid && sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
+  const int hi = (ty + 1) * L::HW + tx + 4;
+  const int oi = ty * L::OW + tx;
+  float* F = a.F;
+  float* psi = a.psiA;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  double lsum = 0.0;
+  bool ok = true;
+  for (int k = k0; k < k1; ++k, q += g.plane) {
+    if (!R.wait(k - 1) || !R.wait(k)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
+    if (valid) {
+      const float* Hc = reinterpret_cast<const float*>(R.at(k) + Y::H);
+      const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
+      const float* Eo = reinterpret_cast<const float*>(R.at(k) + Y::E);
+      const float* CB = reinterpret_cast<const float*>(R.at(k) + Y::CB);
+      const float hx = Hc[hi], hy = Hc[L::HP + hi], hz = Hc[2 * L::HP + hi];
+      const float d6 = hz - Hc[2 * L::HP + hi - L::HW];   // dHz/dy
+      const float d7 = hy - Hm[L::HP + hi];               // dHy/dz
+      const float d8 = hx - Hm[hi];                       // dHx/dz
+      const float d9 = hz - Hc[2 * L::HP + hi - 1];       // dHz/dx
+      const float d10 = hy - Hc[L::HP + hi - 1];          // dHy/dx
+      const float d11 = hx - Hc[hi - L::HW];              // dHx/dy
+      const bool sz = in_slab(k, g.nz, g.P);
+      float c0, c1, c2;
+      if (!(sx || sy || sz)) {
+        c0 = d6 - d7;
+        c1 = d8 - d9;
+        c2 = d10 - d11;
+      } else {
+        float t6 = d6, t7 = d7, t8 = d8, t9 = d9, t10 = d10, t11 = d11;
+        if (sx) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PX);
+          t9 = cpml_s(d9, P[oi], psi, psi_at(g, 0, 2, x, y, k), bx, ax, kx);
+          t10 = cpml_s(d10, P[L::OP + oi], psi, psi_at(g, 0, 3, x, y, k), bx, ax, kx);
+        }
+        if (sy) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PY);
+          t6 = cpml_s(d6, P[oi], psi, psi_at(g, 1, 2, x, y, k), by, ay, ky);
+          t11 = cpml_s(d11, P[L::OP + oi], psi, psi_at(g, 1, 3, x, y, k), by, ay, ky);
+        }
+        if (sz) {
+          const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PZ);
+          const float bz = prof(g, 2, PR_BE, k), az = prof(g, 2, PR_AE, k), kz = prof(g, 2, PR_KE, k);
+          t7 = cpml_s(d7, P[oi], psi, psi_at(g, 2, 2, x, y, k), bz, az, kz);
+          t8 = cpml_s(d8, P[L::OP + oi], psi, psi_at(g, 2, 3, x, y, k), bz, az, kz);
+        }
+        c0 = t6 - t7;
+        c1 = t8 - t9;
+        c2 = t10 - t11;
+      }
+      const float w = src_wt(a.src, x, y, k);
+      if (w != 0.f) {
+        const float wj = __fmul_rn(w, a.jn);
+        if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
+        else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
+        else c2 = __fsub_rn(c2, wj);
+      }
+      const float cbv = CB[oi];
+      const float ex = __fadd_rn(Eo[oi], __fmul_rn(cbv, c0));
+      const float ey = __fadd_rn(Eo[L::OP + oi], __fmul_rn(cbv, c1));
+      const float ez = __fadd_rn(Eo[2 * L::OP + oi], __fmul_rn(cbv, c2));
+      F[q] = ex;
+      F[g.nc + q] = ey;
+      F[2 * g.nc + q] = ez;
+      int u, v;
+      if (a.det.kind && on_plane(a.det.axis, a.det.index, a.det.u0, a.det.u1, a.det.v0,
+                                 a.det.v1, x, y, k, &u, &v)) {
+        if (a.det.kind == 1) {
+          lsum += (double)ex * ex + (double)ey * ey + (double)ez * ez;
+        } else {
+          const float E3[3] = {ex, ey, ez}, H3[3] = {hx, hy, hz};
+          const int b = (a.det.axis + 1) % 3, cc = (a.det.axis + 2) % 3;
+          lsum += (double)E3[b] * H3[cc] - (double)E3[cc] * H3[b];
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
+  }
+  if (a.det.kind) {
+    double v = lsum;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int wv = 0; wv < TY; ++wv) t += red[wv];
+      if (t != 0.0) atomicAdd(a.obj, t);
+    }
+  }
+}
+
+// ======================================== reverse E phase (+ adjoint H) ===
+template <int TY, int S>
+struct RE {
+  typedef SL<TY> L;
+  static constexpr int H = 0;                                   // H halo
+  static constexpr int E = L::r128(3 * L::HP * 4);              // E own
+  static constexpr int CB = E + L::r128(3 * L::OP * 4);         // cb halo
+  static constexpr int LE = CB + L::r128(L::HP * 4);            // lam_E halo
+  static constexpr int LH = LE + L::r128(3 * L::HP * 4);        // lam_H own
+  static constexpr int PX = LH + L::r128(3 * L::OP * 4);        // lam_psi_E halo, 2 comps
+  static constexpr int PY = PX + L::r128(2 * L::HP * 4);
+  static constexpr int PZ = PY + L::r128(2 * L::HP * 4);
+  static constexpr int STAGE = PZ + L::r128(2 * L::HP * 4);
+  static int smem() { return S * STAGE + 8 * S; }
+};
+
+template <int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_srev_e(const __grid_constant__ SplitMaps m,
+                                                   StepArgs a) {
+  typedef SL<TY> L;
+  typedef RE<TY, S> Y;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const Geo& g = a.g;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool valid = x < g.nx && y < g.ny;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  // slab flags include the +1 neighbours the adjoint reads
+  const bool txs = tile_in_slab(x0, min(x0 + 32, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
+  const bool tint = x0 + 31 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0 - 1, k1);
+  auto issue = [&](int p) {
+    unsigned char* st = R.at(p);
+    uint64_t* bar = R.bar(p);
+    const bool body = p >= k0 && p < k1;
+    const bool zs = p >= k0 && in_slab(p, g.nz, g.P) && p < g.nz;
+    uint32_t tx_bytes = 3 * L::HP * 4 + L::HP * 4 + 3 * L::HP * 4 +
+                        (body ? 6 * L::OP * 4 : 0) + (body && txs ? 2 * L::HP * 4 : 0) +
+                        (body && tys ? 2 * L::HP * 4 : 0) + (zs ? 2 * L::HP * 4 : 0);
+    mbar_expect_tx(bar, tx_bytes);
+    tma_load_4d(st + Y::H, &m.Fh, bar, x0 - 4, y0 - 1, p, 3);
+    tma_load_4d(st + Y::CB, &m.cbh, bar, x0 - 4, y0 - 1, p, 0);
+    tma_load_4d(st + Y::LE, &m.Lh, bar, x0 - 4, y0 - 1, p, 0);
+    if (body) {
+      tma_load_4d(st + Y::E, &m.Fo, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::LH, &m.Lo, bar, x0, y0, p, 3);
+    }
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Ph, bar, x0 - 4, y0 - 1, p, 2);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Ph, bar, x0 - 4, y0 - 1, p, 6);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Ph, bar, x0 - 4, y0 - 1, p, 10);
+  };
+  if (tid == 0)
+    for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
+  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
+  const bool sx1 = in_slab(x + 1, g.nx, g.P), sy1 = in_slab(y + 1, g.ny, g.P);
+  const bool inxy = x >= g.P && x < g.nx - g.P && y >= g.P && y < g.ny - g.P;
+  const bool dxy = x >= a.dlo[0] && x < a.dhi[0] && y >= a.dlo[1] && y < a.dhi[1];
+  const int dX = a.dhi[0] - a.dlo[0], dY = a.dhi[1] - a.dlo[1];
+  const int hi = (ty + 1) * L::HW + tx + 4;
+  const int oi = ty * L::OW + tx;
+  float* F = a.F;
+  float* LL = a.L;
+  float* lpB = a.psiB;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  bool ok = true;
+  for (int k = k0; k < k1; ++k, q += g.plane) {
+    if (!R.wait(k - 1) || !R.wait(k) || !R.wait(k + 1)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
+    if (valid) {
+      const unsigned char* sc = R.at(k);
+      const unsigned char* sn = R.at(k + 1);
+      const float* LEc = reinterpret_cast<const float*>(sc + Y::LE);
+      const float* CBc = reinterpret_cast<const float*>(sc + Y::CB);
+      const float cbv = CBc[hi];
+      const float lex = LEc[hi], ley = LEc[L::HP + hi], lez = LEc[2 * L::HP + hi];
+      // primal inverse E update on the interior, dL/dcb on the design box
+      if (tint && inxy && k >= g.P && k < g.nz - g.P) {
+        const float* Hc = reinterpret_cast<const float*>(sc + Y::H);
+        const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
+        const float* Eo = reinterpret_cast<const float*>(sc + Y::E);
+        const float hx = Hc[hi], hy = Hc[L::HP + hi], hz = Hc[2 * L::HP + hi];
+        const float d6 = hz - Hc[2 * L::HP + hi - L::HW], d7 = hy - Hm[L::HP + hi];
+        const float d8 = hx - Hm[hi], d9 = hz - Hc[2 * L::HP + hi - 1];
+        const float d10 = hy - Hc[L::HP + hi - 1], d11 = hx - Hc[hi - L::HW];
+        float c0 = d6 - d7, c1 = d8 - d9, c2 = d10 - d11;
+        const float w = src_wt(a.src, x, y, k);
+        if (w != 0.f) {
+          const float wj = __fmul_rn(w, a.jn);
+          if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
+          else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
+          else c2 = __fsub_rn(c2, wj);
+        }
+        F[q] = __fsub_rn(Eo[oi], __fmul_rn(cbv, c0));
+        F[g.nc + q] = __fsub_rn(Eo[L::OP + oi], __fmul_rn(cbv, c1));
+        F[2 * g.nc + q] = __fsub_rn(Eo[2 * L::OP + oi], __fmul_rn(cbv, c2));
+        if (dxy && k >= a.dlo[2] && k < a.dhi[2]) {
+          const float s = lex * c0 + ley * c1 + lez * c2;
+          const long long qd = ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (x - a.dlo[0]);
+          a.gacc[qd] += (double)s;
+        }
+      }
+      // adjoint of the E half-step: lam_H += D'^T lam_delta'
+      const float wx = cbv * lex, wy = cbv * ley, wz = cbv * lez;
+      float o6 = wx, o11 = -wz, o7 = -wx, o8 = wy, o9 = -wy, o10 = wz;
+      float n6, n11, n7, n8, n9, n10;
+      {  // +y neighbour (terms t6: Ex,y,+ and t11: Ez,y,-)
+        const int r = hi + L::HW;
+        const float c2 = CBc[r];
+        n6 = c2 * LEc[r];
+        n11 = -c2 * LEc[2 * L::HP + r];
+      }
+      {  // +x neighbour (t9: Ey,x,- and t10: Ez,x,+)
+        const int r = hi + 1;
+        const float c2 = CBc[r];
+        n9 = -c2 * LEc[L::HP + r];
+        n10 = c2 * LEc[2 * L::HP + r];
+      }
+      {  // +z neighbour (t7: Ex,z,- and t8: Ey,z,+)
+        const float* LEn = reinterpret_cast<const float*>(sn + Y::LE);
+        const float c2 = reinterpret_cast<const float*>(sn + Y::CB)[hi];
+        n7 = -c2 * LEn[hi];
+        n8 = c2 * LEn[L::HP + hi];
+      }
+      if (y + 1 >= g.ny) { n6 = 0.f; n11 = 0.f; }
+      if (x + 1 >= g.nx) { n9 = 0.f; n10 = 0.f; }
+      if (k + 1 >= g.nz) { n7 = 0.f; n8 = 0.f; }
+      if (sy || (sy1 && y + 1 < g.ny)) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PY);
+        const float b = prof(g, 1, PR_BE, y), aa = prof(g, 1, PR_AE, y), kv = prof(g, 1, PR_KE, y);
+        if (sy) {
+          o6 = adj_s(o6, P[hi], lpB, psi_at(g, 1, 2, x, y, k), true, b, aa, kv);
+          o11 = adj_s(o11, P[L::HP + hi], lpB, psi_at(g, 1, 3, x, y, k), true, b, aa, kv);
+        }
+        if (sy1 && y + 1 < g.ny) {
+          const float b1 = prof(g, 1, PR_BE, y + 1), a1 = prof(g, 1, PR_AE, y + 1),
+                      k1v = prof(g, 1, PR_KE, y + 1);
+          n6 = adj_s(n6, P[hi + L::HW], lpB, 0, false, b1, a1, k1v);
+          n11 = adj_s(n11, P[L::HP + hi + L::HW], lpB, 0, false, b1, a1, k1v);
+        }
+      }
+      if (sx || (sx1 && x + 1 < g.nx)) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PX);
+        if (sx) {
+          const float b = prof(g, 0, PR_BE, x), aa = prof(g, 0, PR_AE, x), kv = prof(g, 0, PR_KE, x);
+          o9 = adj_s(o9, P[hi], lpB, psi_at(g, 0, 2, x, y, k), true, b, aa, kv);
+          o10 = adj_s(o10, P[L::HP + hi], lpB, psi_at(g, 0, 3, x, y, k), true, b, aa, kv);
+        }
+        if (sx1 && x + 1 < g.nx) {
+          const float b1 = prof(g, 0, PR_BE, x + 1), a1 = prof(g, 0, PR_AE, x + 1),
+                      k1v = prof(g, 0, PR_KE, x + 1);
+          n9 = adj_s(n9, P[hi + 1], lpB, 0, false, b1, a1, k1v);
+          n10 = adj_s(n10, P[L::HP + hi + 1], lpB, 0, false, b1, a1, k1v);
+        }
+      }
+      const bool sz = in_slab(k, g.nz, g.P), sz1 = k + 1 < g.nz && in_slab(k + 1, g.nz, g.P);
+      if (sz) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PZ);
+        const float b = prof(g, 2, PR_BE, k), aa = prof(g, 2, PR_AE, k), kv = prof(g, 2, PR_KE, k);
+        o7 = adj_s(o7, P[hi], lpB, psi_at(g, 2, 2, x, y, k), true, b, aa, kv);
+        o8 = adj_s(o8, P[L::HP + hi], lpB, psi_at(g, 2, 3, x, y, k), true, b, aa, kv);
+      }
+      if (sz1) {
+        const float* P = reinterpret_cast<const float*>(sn + Y::PZ);
+        const float b1 = prof(g, 2, PR_BE, k + 1), a1 = prof(g, 2, PR_AE, k + 1),
+                    k1v = prof(g, 2, PR_KE, k + 1);
+        n7 = adj_s(n7, P[hi], lpB, 0, false, b1, a1, k1v);
+        n8 = adj_s(n8, P[L::HP + hi], lpB, 0, false, b1, a1, k1v);
+      }
+      const float* LHo = reinterpret_cast<const float*>(sc + Y::LH);
+      LL[3 * g.nc + q] = LHo[oi] + ((o8 - n8) + (o11 - n11));
+      LL[4 * g.nc + q] = LHo[L::OP + oi] + ((o7 - n7) + (o10 - n10));
+      LL[5 * g.nc + q] = LHo[2 * L::OP + oi] + ((o6 - n6) + (o9 - n9));
+    }
+    __syncthreads();
+    if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
+  }
+}
+
+// ======================================== reverse H phase (+ adjoint E) ===
+template <int TY, int S>
+struct RH {
+  typedef SL<TY> L;
+  static constexpr int E = 0;                                   // E halo
+  static constexpr int H = L::r128(3 * L::HP * 4);              // H own
+  static constexpr int LH = H + L::r128(3 * L::OP * 4);         // lam_H halo
+  static constexpr int LE = LH + L::r128(3 * L::HP * 4);        // lam_E own
+  static constexpr int PX = LE + L::r128(3 * L::OP * 4);        // lam_psi_H halo, 2 comps
+  static constexpr int PY = PX + L::r128(2 * L::HP * 4);
+  static constexpr int PZ = PY + L::r128(2 * L::HP * 4);
+  static constexpr int STAGE = PZ + L::r128(2 * L::HP * 4);
+  static int smem() { return S * STAGE + 8 * S; }
+};
+
+template <int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ SplitMaps m,
+                                                   StepArgs a) {
+  typedef SL<TY> L;
+  typedef RH<TY, S> Y;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const Geo& g = a.g;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool valid = x < g.nx && y < g.ny;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  // slab flags include the -1 neighbours the adjoint reads
+  const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  const bool tint = x0 + 31 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0 - 1, k1);
+  auto issue = [&](int p) {
+    unsigned char* st = R.at(p);
+    uint64_t* bar = R.bar(p);
+    const bool body = p >= k0 && p < k1;
+    const bool zs = p >= 0 && p < k1 && in_slab(p, g.nz, g.P);
+    uint32_t tx_bytes = 3 * L::HP * 4 + 3 * L::HP * 4 + (body ? 6 * L::OP * 4 : 0) +
+                        (body && txs ? 2 * L::HP * 4 : 0) + (body && tys ? 2 * L::HP * 4 : 0) +
+                        (zs ? 2 * L::HP * 4 : 0);
+    mbar_expect_tx(bar, tx_bytes);
+    tma_load_4d(st + Y::E, &m.Fh, bar, x0 - 4, y0 - 1, p, 0);
+    tma_load_4d(st + Y::LH, &m.Lh, bar, x0 - 4, y0 - 1, p, 3);
+    if (body) {
+      tma_load_4d(st + Y::H, &m.Fo, bar, x0, y0, p, 3);
+      tma_load_4d(st + Y::LE, &m.Lo, bar, x0, y0, p, 0);
+    }
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Ph, bar, x0 - 4, y0 - 1, p, 0);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Ph, bar, x0 - 4, y0 - 1, p, 4);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Ph, bar, x0 - 4, y0 - 1, p, 8);
+  };
+  if (tid == 0)
+    for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
+  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
+  const bool sxm = x > 0 && in_slab(x - 1, g.nx, g.P), sym = y > 0 && in_slab(y - 1, g.ny, g.P);
+  const bool inxy = x >= g.P && x < g.nx - g.P && y >= g.P && y < g.ny - g.P;
+  const int hi = (ty + 1) * L::HW + tx + 4;
+  const int oi = ty * L::OW + tx;
+  const float S_ = g.S;
+  float* F = a.F;
+  float* LL = a.L;
+  float* lpB = a.psiB;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  bool ok = true;
+  for (int k = k0; k < k1; ++k, q += g.plane) {
+    if (!R.wait(k - 1) || !R.wait(k) || !R.wait(k + 1)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
+    if (valid) {
+      const unsigned char* sc = R.at(k);
+      const unsigned char* sp = R.at(k - 1);
+      // primal inverse H update on the interior
+      if (tint && inxy && k >= g.P && k < g.nz - g.P) {
+        const float* Ec = reinterpret_cast<const float*>(sc + Y::E);
+        const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
+        const float* Ho = reinterpret_cast<const float*>(sc + Y::H);
+        const float ex = Ec[hi], ey = Ec[L::HP + hi], ez = Ec[2 * L::HP + hi];
+        const float d0 = Ec[2 * L::HP + hi + L::HW] - ez, d1 = En[L::HP + hi] - ey;
+        const float d2 = En[hi] - ex, d3 = Ec[2 * L::HP + hi + 1] - ez;
+        const float d4 = Ec[L::HP + hi + 1] - ey, d5 = Ec[hi + L::HW] - ex;
+        F[3 * g.nc + q] = __fadd_rn(Ho[oi], __fmul_rn(S_, d0 - d1));
+        F[4 * g.nc + q] = __fadd_rn(Ho[L::OP + oi], __fmul_rn(S_, d2 - d3));
+        F[5 * g.nc + q] = __fadd_rn(Ho[2 * L::OP + oi], __fmul_rn(S_, d4 - d5));
+      }
+      // adjoint of the H half-step: lam_E += D^T lam_delta, v = -S s lam_H
+      const float* LHc = reinterpret_cast<const float*>(sc + Y::LH);
+      const float* LHp = reinterpret_cast<const float*>(sp + Y::LH);
+      const float lhx = LHc[hi], lhy = LHc[L::HP + hi], lhz = LHc[2 * L::HP + hi];
+      float o0 = -S_ * lhx, o5 = S_ * lhz, o1 = S_ * lhx, o2 = -S_ * lhy, o3 = S_ * lhy,
+            o4 = -S_ * lhz;
+      float m0 = -S_ * LHc[hi - L::HW], m5 = S_ * LHc[2 * L::HP + hi - L::HW];   // -y
+      float m3 = S_ * LHc[L::HP + hi - 1], m4 = -S_ * LHc[2 * L::HP + hi - 1];   // -x
+      float m1 = S_ * LHp[hi], m2 = -S_ * LHp[L::HP + hi];                       // -z
+      if (y == 0) { m0 = 0.f; m5 = 0.f; }
+      if (x == 0) { m3 = 0.f; m4 = 0.f; }
+      if (k == 0) { m1 = 0.f; m2 = 0.f; }
+      if (sy || sym) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PY);
+        if (sy) {
+          const float b = prof(g, 1, PR_BH, y), aa = prof(g, 1, PR_AH, y), kv = prof(g, 1, PR_KH, y);
+          o0 = adj_s(o0, P[hi], lpB, psi_at(g, 1, 0, x, y, k), true, b, aa, kv);
+          o5 = adj_s(o5, P[L::HP + hi], lpB, psi_at(g, 1, 1, x, y, k), true, b, aa, kv);
+        }
+        if (sym) {
+          const float b1 = prof(g, 1, PR_BH, y - 1), a1 = prof(g, 1, PR_AH, y - 1),
+                      k1v = prof(g, 1, PR_KH, y - 1);
+          m0 = adj_s(m0, P[hi - L::HW], lpB, 0, false, b1, a1, k1v);
+          m5 = adj_s(m5, P[L::HP + hi - L::HW], lpB, 0, false, b1, a1, k1v);
+        }
+      }
+      if (sx || sxm) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PX);
+        if (sx) {
+          const float b = prof(g, 0, PR_BH, x), aa = prof(g, 0, PR_AH, x), kv = prof(g, 0, PR_KH, x);
+          o3 = adj_s(o3, P[hi], lpB, psi_at(g, 0, 0, x, y, k), true, b, aa, kv);
+          o4 = adj_s(o4, P[L::HP + hi], lpB, psi_at(g, 0, 1, x, y, k), true, b, aa, kv);
+        }
+        if (sxm) {
+          const float b1 = prof(g, 0, PR_BH, x - 1), a1 = prof(g, 0, PR_AH, x - 1),
+                      k1v = prof(g, 0, PR_KH, x - 1);
+          m3 = adj_s(m3, P[hi - 1], lpB, 0, false, b1, a1, k1v);
+          m4 = adj_s(m4, P[L::HP + hi - 1], lpB, 0, false, b1, a1, k1v);
+        }
+      }
+      const bool sz = in_slab(k, g.nz, g.P), szm = k > 0 && in_slab(k - 1, g.nz, g.P);
+      if (sz) {
+        const float* P = reinterpret_cast<const float*>(sc + Y::PZ);
+        const float b = prof(g, 2, PR_BH, k), aa = prof(g, 2, PR_AH, k), kv = prof(g, 2, PR_KH, k);
+        o1 = adj_s(o1, P[hi], lpB, psi_at(g, 2, 0, x, y, k), true, b, aa, kv);
+        o2 = adj_s(o2, P[L::HP + hi], lpB, psi_at(g, 2, 1, x, y, k), true, b, aa, kv);
+      }
+      if (szm) {
+        const float* P = reinterpret_cast<const float*>(sp + Y::PZ);
+        const float b1 = prof(g, 2, PR_BH, k - 1), a1 = prof(g, 2, PR_AH, k - 1),
+                    k1v = prof(g, 2, PR_KH, k - 1);
+        m1 = adj_s(m1, P[hi], lpB, 0, false, b1, a1, k1v);
+        m2 = adj_s(m2, P[L::HP + hi], lpB, 0, false, b1, a1, k1v);
+      }
+      const float* LEo = reinterpret_cast<const float*>(sc + Y::LE);
+      LL[q] = LEo[oi] + ((m2 - o2) + (m5 - o5));
+      LL[g.nc + q] = LEo[L::OP + oi] + ((m1 - o1) + (m4 - o4));
+      LL[2 * g.nc + q] = LEo[2 * L::OP + oi] + ((m0 - o0) + (m3 - o3));
+    }
+    __syncthreads();
+    if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
+  }
+}
+
+// ------------------------------------------------------------ launchers ---
+template <class KT>
+static cudaError_t set_smem(KT kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int TY, int S>
+static cudaError_t launch_split_t(int which, const SplitMaps& m, const StepArgs& a,
+                                  cudaStream_t s) {
+  dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
+  dim3 block(32, TY);
+  cudaError_t e = cudaSuccess;
+  switch (which) {
+    case 0: {
+      int sm = FH<TY, S>::smem();
+      if ((e = set_smem(k_sfwd_h<TY, S>, sm))) return e;
+      k_sfwd_h<TY, S><<<grid, block, sm, s>>>(m, a);
+      break;
+    }
+    case 1: {
+      int sm = FE<TY, S>::smem();
+      if ((e = set_smem(k_sfwd_e<TY, S>, sm))) return e;
+      k_sfwd_e<TY, S><<<grid, block, sm, s>>>(m, a);
+      break;
+    }
+    case 2: {
+      int sm = RE<TY, S>::smem();
+      if ((e = set_smem(k_srev_e<TY, S>, sm))) return e;
+      k_srev_e<TY, S><<<grid, block, sm, s>>>(m, a);
+      break;
+    }
+    case 3: {
+      int sm = RH<TY, S>::smem();
+      if ((e = set_smem(k_srev_h<TY, S>, sm))) return e;
+      k_srev_h<TY, S><<<grid, block, sm, s>>>(m, a);
+      break;
+    }
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
+cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s) {
+  switch (a.tile_y) {
+    case 1: return launch_split_t<1, 4>(which, m, a, s);
+    case 2: return launch_split_t<2, 4>(which, m, a, s);
+    case 4: return launch_split_t<4, 4>(which, m, a, s);
+    case 8: return launch_split_t<8, 4>(which, m, a, s);
+    case 16: return launch_split_t<16, 3>(which, m, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// -------------------------------------------------------- tensor maps ---
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn2() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static cudaError_t enc(CUtensorMap* m, const float* base, const Geo& g, int ncomp, int bx, int by,
+                       int bc) {
+  auto fn = encode_fn2();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)ncomp};
+  cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.nc * 4};
+  cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)bc};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_split_maps(const float* F, const float* Lm, const float* cb, const float* psiA,
+                              const Geo& g, int ty, SplitMaps* m) {
+  cudaError_t e;
+  if ((e = enc(&m->Fh, F, g, 6, 40, ty + 2, 3))) return e;
+  if ((e = enc(&m->Fo, F, g, 6, 32, ty, 3))) return e;
+  if ((e = enc(&m->Lh, Lm, g, 6, 40, ty + 2, 3))) return e;
+  if ((e = enc(&m->Lo, Lm, g, 6, 32, ty, 3))) return e;
+  if ((e = enc(&m->cbh, cb, g, 1, 40, ty + 2, 1))) return e;
+  if ((e = enc(&m->cbo, cb, g, 1, 32, ty, 1))) return e;
+  if ((e = enc(&m->Ph, psiA, g, 12, 40, ty + 2, 2))) return e;
+  return enc(&m->Po, psiA, g, 12, 32, ty, 2);
+}
+
+}  // namespace fdtd

@@ -1,0 +1,67 @@
+"""Short, self-contained run of the library for profilers (ncu launch lists,
+single-kernel captures) and launch-shape sweeps.
+
+  python -m paper_2603_24027_gb300.ncu_driver --workload waveguide200 --steps 12 \
+      --kernel 2 --tile-y 4 --zchunk 8 --tape bf16:4:linear [--no-graphs] [--sweep]
+
+Runs one forward + backward (after one warm-up pair when --warmup 1) and
+prints the objective and per-kernel sampled timings.  --pml overrides the
+CPML thickness, to separate interior and absorbing-layer cost.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="waveguide200")
+    p.add_argument("--steps", type=int, default=12)
+    p.add_argument("--kernel", type=int, default=2)
+    p.add_argument("--tile-y", type=int, default=4)
+    p.add_argument("--zchunk", type=int, default=8)
+    p.add_argument("--tape", default="bf16:4:linear")
+    p.add_argument("--pml", type=int, default=0)
+    p.add_argument("--warmup", type=int, default=0)
+    p.add_argument("--sample-every", type=int, default=0)
+    p.add_argument("--no-graphs", action="store_true")
+    a = p.parse_args(argv)
+
+    import torch
+    from paper_2603_24027_gb300 import _capi as A
+    from paper_2603_24027_gb300 import build as B
+    from paper_2603_24027_gb300 import fdtd
+    from paper_2603_24027_gb300 import inputs as I
+
+    B.build()
+    w = I.CONFIGS[a.workload]().replace(n_steps=a.steps)
+    if a.pml:
+        w = w.replace(pml_thickness=a.pml)
+    dt, k, interp = a.tape.split(":")
+    rec = A.record_cfg(dt, int(k), interp)
+    sim = fdtd.Simulation(w)
+    sim.set_option(A.OPT_KERNEL, a.kernel)
+    sim.set_option(A.OPT_TILE_Y, a.tile_y)
+    sim.set_option(A.OPT_ZCHUNK, a.zchunk)
+    sim.set_option(A.OPT_SAMPLE_EVERY, a.sample_every)
+    sim.set_option(A.OPT_USE_GRAPHS, 0 if a.no_graphs else 1)
+    eps = torch.from_numpy(w.eps).cuda()
+    for _ in range(a.warmup + 1):
+        L = sim.forward(eps, rec)
+        g = sim.backward(1.0)
+    torch.cuda.synchronize()
+    out = dict(workload=w.name, steps=w.n_steps, pml=w.pml_thickness, kernel=a.kernel,
+               tile_y=a.tile_y, zchunk=a.zchunk, L=L, grad_l1=float(g.abs().sum()),
+               timing=sim.last_timing(), kernels=sim.kernel_timing())
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -74,8 +74,11 @@ SMALL = {
 }
 
 
+KERNELS = [0, 1, 2, 3]   # split plain, fused plain, fused TMA (+TMA reverse), split TMA
+
+
 @pytest.mark.parametrize("name", list(SMALL))
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_forward_fields_and_objective(F, A, name, kernel):
     w = SMALL[name]()
     r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel})
@@ -87,7 +90,7 @@ def test_forward_fields_and_objective(F, A, name, kernel):
 
 
 @pytest.mark.parametrize("name", list(SMALL))
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_uncompressed_gradient_matches_exact_gradient(F, A, name, kernel):
     w = SMALL[name]()
     r = gpu_run(F, A, w, seed=1.0, options={A.OPT_KERNEL: kernel})
@@ -136,11 +139,11 @@ def test_graphs_and_direct_launches_agree(F, A):
     np.testing.assert_allclose(a["g"], b["g"], rtol=1e-12, atol=1e-30)
 
 
-@pytest.mark.parametrize("zchunk,tile_y", [(1, 4), (3, 8), (0, 2), (16, 1)])
+@pytest.mark.parametrize("zchunk,tile_y", [(1, 4), (3, 8), (0, 2), (16, 1), (5, 16)])
 def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y):
     w = SMALL["ragged_poynting"]()
     base = gpu_run(F, A, w)
-    for kernel in (0, 1):
+    for kernel in KERNELS:
         r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel, A.OPT_ZCHUNK: zchunk,
                                       A.OPT_TILE_Y: tile_y})
         np.testing.assert_array_equal(r["fields"], base["fields"])
