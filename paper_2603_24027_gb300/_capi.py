@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_ENOMEM", -3: "FDTD_EC
                 -4: "FDTD_ESTATE", -5: "FDTD_ETIMEOUT", -6: "FDTD_ENONFINITE"}
 TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3}
 INTERP = {"linear": 0, "cubic": 1}
-OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY = 0, 1, 2, 3, 4
+OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS = 0, 1, 2, 3, 4, 5
 K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV = range(8)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "fused_fwd",
                 "fused_rev"]

@@ -32,7 +32,7 @@ struct Layout {
 };
 
 struct GraphKey {
-  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample;
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -62,7 +62,7 @@ struct fdtd_handle {
   int fwd_buf;                // field buffer holding the state after forward
   fdtd_record_cfg fwd_rec;
 
-  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample;
+  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -471,10 +471,11 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->have_forward = false;
   h->fwd_buf = 0;
   h->opt_graphs = 1;
-  h->opt_kernel = 0;
+  h->opt_kernel = 3;
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_sample = 0;
+  h->opt_rows = 1;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -568,6 +569,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < 0) return fail(h, FDTD_EINVAL, "sample interval must be >= 0");
       h->opt_sample = value;
       break;
+    case FDTD_OPT_ROWS_PER_THREAD:
+      if (value != 1 && value != 2) return fail(h, FDTD_EINVAL, "rows per thread must be 1 or 2");
+      h->opt_rows = value;
+      break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -581,6 +586,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_TILE_Y: *value = h->opt_tile_y; break;
     case FDTD_OPT_ZCHUNK: *value = h->opt_zchunk; break;
     case FDTD_OPT_SAMPLE_EVERY: *value = h->opt_sample; break;
+    case FDTD_OPT_ROWS_PER_THREAD: *value = h->opt_rows; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -668,6 +674,7 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.det.u0 = h->det.lo[0]; a.det.u1 = h->det.hi[0];
   a.det.v0 = h->det.lo[1]; a.det.v1 = h->det.hi[1];
   a.tile_y = h->opt_tile_y;
+  a.rows = h->opt_rows;
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
   a.err = (unsigned*)(h->ws + L.err);
   return a;
@@ -889,6 +896,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.scaled = rec->scaled; key.kernel = h->opt_kernel; key.tile_y = h->opt_tile_y;
   key.zchunk = h->opt_zchunk;
   key.sample = h->opt_sample;
+  key.rows = h->opt_rows;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;

@@ -144,6 +144,7 @@ struct StepArgs {
   float jn;        // J waveform value of this step
   int zchunk;
   int tile_y;
+  int rows;        // tile rows per thread (TMA half-step kernels)
   unsigned* err;   // device error word (ERR_*)
 };
 

@@ -95,6 +95,16 @@ __device__ __forceinline__ bool tile_in_slab(int lo, int hi_incl, int n, int P) 
   return lo < P || hi_incl >= n - P;
 }
 
+
+// Per-row state of a thread: a thread handles rows ty + r * (TY / RPT),
+// r = 0 .. RPT-1, of its 32 x TY tile.
+#define ROWS_SETUP()                                                                  \
+  constexpr int TYT = TY / RPT;                                                        \
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;                    \
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;                                \
+  const int x = x0 + tx;                                                               \
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+
 // =================================================== forward H half-step ===
 template <int TY, int S>
 struct FH {
@@ -108,18 +118,14 @@ struct FH {
   static int smem() { return S * STAGE + 8 * S; }
 };
 
-template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY) k_sfwd_h(const __grid_constant__ SplitMaps m,
-                                                   StepArgs a) {
+template <int TY, int RPT, int S>
+__global__ void __launch_bounds__(32 * TY / RPT) k_sfwd_h(const __grid_constant__ SplitMaps m,
+                                                         StepArgs a) {
   typedef SL<TY> L;
   typedef FH<TY, S> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool valid = x < g.nx && y < g.ny;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  ROWS_SETUP();
   const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // planes k0 .. k1 (E at k+1 for the last plane), each waited before reuse
@@ -141,23 +147,42 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_h(const __grid_constant__ Spli
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
-  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
-  float bx = 0.f, ax = 0.f, kx = 1.f, by = 0.f, ay = 0.f, ky = 1.f;
-  if (valid && sx) { bx = prof(g, 0, PR_BH, x); ax = prof(g, 0, PR_AH, x); kx = prof(g, 0, PR_KH, x); }
-  if (valid && sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
-  const int hi = (ty + 1) * L::HW + tx + 4;   // own cell in a halo box
-  const int oi = ty * L::OW + tx;             // own cell in an own box
+  const bool sx = x < g.nx && in_slab(x, g.nx, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f;
+  if (sx) { bx = prof(g, 0, PR_BH, x); ax = prof(g, 0, PR_AH, x); kx = prof(g, 0, PR_KH, x); }
+  bool valid[RPT], sy[RPT];
+  float by[RPT], ay[RPT], ky[RPT];
+  long long q[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int y = y0 + ty + r * TYT;
+    valid[r] = x < g.nx && y < g.ny;
+    sy[r] = valid[r] && in_slab(y, g.ny, g.P);
+    by[r] = sy[r] ? prof(g, 1, PR_BH, y) : 0.f;
+    ay[r] = sy[r] ? prof(g, 1, PR_AH, y) : 0.f;
+    ky[r] = sy[r] ? prof(g, 1, PR_KH, y) : 1.f;
+    q[r] = (long long)k0 * g.plane + (long long)y * g.px + x;
+  }
   float* F = a.F;
   float* psi = a.psiA;
-  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  const long long nc = g.nc;
   bool ok = true;
-  for (int k = k0; k < k1; ++k, q += g.plane) {
+  for (int k = k0; k < k1; ++k) {
     if (!R.wait(k) || !R.wait(k + 1)) ok = false;
     if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
-    if (valid) {
-      const float* Ec = reinterpret_cast<const float*>(R.at(k) + Y::E);
-      const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
-      const float* Ho = reinterpret_cast<const float*>(R.at(k) + Y::H);
+    const float* Ec = reinterpret_cast<const float*>(R.at(k) + Y::E);
+    const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
+    const float* Ho = reinterpret_cast<const float*>(R.at(k) + Y::H);
+    const bool sz = in_slab(k, g.nz, g.P);
+    float bz = 0.f, az = 0.f, kz = 1.f;
+    if (sz) { bz = prof(g, 2, PR_BH, k); az = prof(g, 2, PR_AH, k); kz = prof(g, 2, PR_KH, k); }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!valid[r]) continue;
+      const int ty_r = ty + r * TYT;
+      const int hi = (ty_r + 1) * L::HW + tx + 4;   // own cell in a halo box
+      const int oi = ty_r * L::OW + tx;             // own cell in an own box
+      const long long qq = q[r];
       const float ex = Ec[hi], ey = Ec[L::HP + hi], ez = Ec[2 * L::HP + hi];
       const float d0 = Ec[2 * L::HP + hi + L::HW] - ez;   // dEz/dy
       const float d1 = En[L::HP + hi] - ey;               // dEy/dz
@@ -165,9 +190,8 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_h(const __grid_constant__ Spli
       const float d3 = Ec[2 * L::HP + hi + 1] - ez;       // dEz/dx
       const float d4 = Ec[L::HP + hi + 1] - ey;           // dEy/dx
       const float d5 = Ec[hi + L::HW] - ex;               // dEx/dy
-      const bool sz = in_slab(k, g.nz, g.P);
       float cx, cy, cz;
-      if (!(sx || sy || sz)) {
+      if (!(sx || sy[r] || sz)) {
         cx = d0 - d1;
         cy = d2 - d3;
         cz = d4 - d5;
@@ -175,28 +199,29 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_h(const __grid_constant__ Spli
         float t0 = d0, t1 = d1, t2 = d2, t3 = d3, t4 = d4, t5 = d5;
         if (sx) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PX);
-          t3 = cpml_s(d3, P[oi], psi, psi_at(g, 0, 0, x, y, k), bx, ax, kx);
-          t4 = cpml_s(d4, P[L::OP + oi], psi, psi_at(g, 0, 1, x, y, k), bx, ax, kx);
+          t3 = cpml_s(d3, P[oi], psi, 0 * nc + qq, bx, ax, kx);
+          t4 = cpml_s(d4, P[L::OP + oi], psi, 1 * nc + qq, bx, ax, kx);
         }
-        if (sy) {
+        if (sy[r]) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PY);
-          t0 = cpml_s(d0, P[oi], psi, psi_at(g, 1, 0, x, y, k), by, ay, ky);
-          t5 = cpml_s(d5, P[L::OP + oi], psi, psi_at(g, 1, 1, x, y, k), by, ay, ky);
+          t0 = cpml_s(d0, P[oi], psi, 4 * nc + qq, by[r], ay[r], ky[r]);
+          t5 = cpml_s(d5, P[L::OP + oi], psi, 5 * nc + qq, by[r], ay[r], ky[r]);
         }
         if (sz) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PZ);
-          const float bz = prof(g, 2, PR_BH, k), az = prof(g, 2, PR_AH, k), kz = prof(g, 2, PR_KH, k);
-          t1 = cpml_s(d1, P[oi], psi, psi_at(g, 2, 0, x, y, k), bz, az, kz);
-          t2 = cpml_s(d2, P[L::OP + oi], psi, psi_at(g, 2, 1, x, y, k), bz, az, kz);
+          t1 = cpml_s(d1, P[oi], psi, 8 * nc + qq, bz, az, kz);
+          t2 = cpml_s(d2, P[L::OP + oi], psi, 9 * nc + qq, bz, az, kz);
         }
         cx = t0 - t1;
         cy = t2 - t3;
         cz = t4 - t5;
       }
-      F[3 * g.nc + q] = __fsub_rn(Ho[oi], __fmul_rn(g.S, cx));
-      F[4 * g.nc + q] = __fsub_rn(Ho[L::OP + oi], __fmul_rn(g.S, cy));
-      F[5 * g.nc + q] = __fsub_rn(Ho[2 * L::OP + oi], __fmul_rn(g.S, cz));
+      F[3 * nc + qq] = __fsub_rn(Ho[oi], __fmul_rn(g.S, cx));
+      F[4 * nc + qq] = __fsub_rn(Ho[L::OP + oi], __fmul_rn(g.S, cy));
+      F[5 * nc + qq] = __fsub_rn(Ho[2 * L::OP + oi], __fmul_rn(g.S, cz));
     }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) q[r] += g.plane;
     __syncthreads();
     if (tid == 0 && k + S <= R.p1) issue(k + S);   // plane k is no longer read
   }
@@ -216,18 +241,14 @@ struct FE {
   static int smem() { return S * STAGE + 8 * S + 256; }
 };
 
-template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY) k_sfwd_e(const __grid_constant__ SplitMaps m,
-                                                   StepArgs a) {
+template <int TY, int RPT, int S>
+__global__ void __launch_bounds__(32 * TY / RPT) k_sfwd_e(const __grid_constant__ SplitMaps m,
+                                                         StepArgs a) {
   typedef SL<TY> L;
   typedef FE<TY, S> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool valid = x < g.nx && y < g.ny;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  ROWS_SETUP();
   const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // planes k0-1 .. k1-1 (Ht at k-1 for the first plane), each waited before reuse
@@ -253,25 +274,48 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_e(const __grid_constant__ Spli
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
-  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
-  float bx = 0.f, ax = 0.f, kx = 1.f, by = 0.f, ay = 0.f, ky = 1.f;
-  if (valid && sx) { bx = prof(g, 0, PR_BE, x); ax = prof(g, 0, PR_AE, x); kx = prof(g, 0, PR_KE, x); }
-  if (valid && sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
-  const int hi = (ty + 1) * L::HW + tx + 4;
-  const int oi = ty * L::OW + tx;
+  const bool sx = x < g.nx && in_slab(x, g.nx, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f;
+  if (sx) { bx = prof(g, 0, PR_BE, x); ax = prof(g, 0, PR_AE, x); kx = prof(g, 0, PR_KE, x); }
+  bool valid[RPT], sy[RPT];
+  float by[RPT], ay[RPT], ky[RPT];
+  long long q[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int y = y0 + ty + r * TYT;
+    valid[r] = x < g.nx && y < g.ny;
+    sy[r] = valid[r] && in_slab(y, g.ny, g.P);
+    by[r] = sy[r] ? prof(g, 1, PR_BE, y) : 0.f;
+    ay[r] = sy[r] ? prof(g, 1, PR_AE, y) : 0.f;
+    ky[r] = sy[r] ? prof(g, 1, PR_KE, y) : 1.f;
+    q[r] = (long long)k0 * g.plane + (long long)y * g.px + x;
+  }
+  // source and detector planes this thread's columns can cross
+  const bool src_on = a.src.kind != 0;
+  const bool det_on = a.det.kind != 0;
   float* F = a.F;
   float* psi = a.psiA;
-  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  const long long nc = g.nc;
   double lsum = 0.0;
   bool ok = true;
-  for (int k = k0; k < k1; ++k, q += g.plane) {
+  for (int k = k0; k < k1; ++k) {
     if (!R.wait(k - 1) || !R.wait(k)) ok = false;
     if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
-    if (valid) {
-      const float* Hc = reinterpret_cast<const float*>(R.at(k) + Y::H);
-      const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
-      const float* Eo = reinterpret_cast<const float*>(R.at(k) + Y::E);
-      const float* CB = reinterpret_cast<const float*>(R.at(k) + Y::CB);
+    const float* Hc = reinterpret_cast<const float*>(R.at(k) + Y::H);
+    const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
+    const float* Eo = reinterpret_cast<const float*>(R.at(k) + Y::E);
+    const float* CB = reinterpret_cast<const float*>(R.at(k) + Y::CB);
+    const bool sz = in_slab(k, g.nz, g.P);
+    float bz = 0.f, az = 0.f, kz = 1.f;
+    if (sz) { bz = prof(g, 2, PR_BE, k); az = prof(g, 2, PR_AE, k); kz = prof(g, 2, PR_KE, k); }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!valid[r]) continue;
+      const int ty_r = ty + r * TYT;
+      const int y = y0 + ty_r;
+      const int hi = (ty_r + 1) * L::HW + tx + 4;
+      const int oi = ty_r * L::OW + tx;
+      const long long qq = q[r];
       const float hx = Hc[hi], hy = Hc[L::HP + hi], hz = Hc[2 * L::HP + hi];
       const float d6 = hz - Hc[2 * L::HP + hi - L::HW];   // dHz/dy
       const float d7 = hy - Hm[L::HP + hi];               // dHy/dz
@@ -279,9 +323,8 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_e(const __grid_constant__ Spli
       const float d9 = hz - Hc[2 * L::HP + hi - 1];       // dHz/dx
       const float d10 = hy - Hc[L::HP + hi - 1];          // dHy/dx
       const float d11 = hx - Hc[hi - L::HW];              // dHx/dy
-      const bool sz = in_slab(k, g.nz, g.P);
       float c0, c1, c2;
-      if (!(sx || sy || sz)) {
+      if (!(sx || sy[r] || sz)) {
         c0 = d6 - d7;
         c1 = d8 - d9;
         c2 = d10 - d11;
@@ -289,61 +332,67 @@ __global__ void __launch_bounds__(32 * TY) k_sfwd_e(const __grid_constant__ Spli
         float t6 = d6, t7 = d7, t8 = d8, t9 = d9, t10 = d10, t11 = d11;
         if (sx) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PX);
-          t9 = cpml_s(d9, P[oi], psi, psi_at(g, 0, 2, x, y, k), bx, ax, kx);
-          t10 = cpml_s(d10, P[L::OP + oi], psi, psi_at(g, 0, 3, x, y, k), bx, ax, kx);
+          t9 = cpml_s(d9, P[oi], psi, 2 * nc + qq, bx, ax, kx);
+          t10 = cpml_s(d10, P[L::OP + oi], psi, 3 * nc + qq, bx, ax, kx);
         }
-        if (sy) {
+        if (sy[r]) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PY);
-          t6 = cpml_s(d6, P[oi], psi, psi_at(g, 1, 2, x, y, k), by, ay, ky);
-          t11 = cpml_s(d11, P[L::OP + oi], psi, psi_at(g, 1, 3, x, y, k), by, ay, ky);
+          t6 = cpml_s(d6, P[oi], psi, 6 * nc + qq, by[r], ay[r], ky[r]);
+          t11 = cpml_s(d11, P[L::OP + oi], psi, 7 * nc + qq, by[r], ay[r], ky[r]);
         }
         if (sz) {
           const float* P = reinterpret_cast<const float*>(R.at(k) + Y::PZ);
-          const float bz = prof(g, 2, PR_BE, k), az = prof(g, 2, PR_AE, k), kz = prof(g, 2, PR_KE, k);
-          t7 = cpml_s(d7, P[oi], psi, psi_at(g, 2, 2, x, y, k), bz, az, kz);
-          t8 = cpml_s(d8, P[L::OP + oi], psi, psi_at(g, 2, 3, x, y, k), bz, az, kz);
+          t7 = cpml_s(d7, P[oi], psi, 10 * nc + qq, bz, az, kz);
+          t8 = cpml_s(d8, P[L::OP + oi], psi, 11 * nc + qq, bz, az, kz);
         }
         c0 = t6 - t7;
         c1 = t8 - t9;
         c2 = t10 - t11;
       }
-      const float w = src_wt(a.src, x, y, k);
-      if (w != 0.f) {
-        const float wj = __fmul_rn(w, a.jn);
-        if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
-        else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
-        else c2 = __fsub_rn(c2, wj);
+      if (src_on) {
+        const float w = src_wt(a.src, x, y, k);
+        if (w != 0.f) {
+          const float wj = __fmul_rn(w, a.jn);
+          if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
+          else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
+          else c2 = __fsub_rn(c2, wj);
+        }
       }
       const float cbv = CB[oi];
       const float ex = __fadd_rn(Eo[oi], __fmul_rn(cbv, c0));
       const float ey = __fadd_rn(Eo[L::OP + oi], __fmul_rn(cbv, c1));
       const float ez = __fadd_rn(Eo[2 * L::OP + oi], __fmul_rn(cbv, c2));
-      F[q] = ex;
-      F[g.nc + q] = ey;
-      F[2 * g.nc + q] = ez;
+      F[qq] = ex;
+      F[nc + qq] = ey;
+      F[2 * nc + qq] = ez;
       int u, v;
-      if (a.det.kind && on_plane(a.det.axis, a.det.index, a.det.u0, a.det.u1, a.det.v0,
-                                 a.det.v1, x, y, k, &u, &v)) {
+      if (det_on && on_plane(a.det.axis, a.det.index, a.det.u0, a.det.u1, a.det.v0, a.det.v1,
+                             x, y, k, &u, &v)) {
         if (a.det.kind == 1) {
           lsum += (double)ex * ex + (double)ey * ey + (double)ez * ez;
         } else {
-          const float E3[3] = {ex, ey, ez}, H3[3] = {hx, hy, hz};
-          const int b = (a.det.axis + 1) % 3, cc = (a.det.axis + 2) % 3;
-          lsum += (double)E3[b] * H3[cc] - (double)E3[cc] * H3[b];
+          const int ax_ = a.det.axis;
+          const float Eb = ax_ == 0 ? ey : (ax_ == 1 ? ez : ex);
+          const float Ec2 = ax_ == 0 ? ez : (ax_ == 1 ? ex : ey);
+          const float Hb = ax_ == 0 ? hy : (ax_ == 1 ? hz : hx);
+          const float Hc2 = ax_ == 0 ? hz : (ax_ == 1 ? hx : hy);
+          lsum += (double)Eb * Hc2 - (double)Ec2 * Hb;
         }
       }
     }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) q[r] += g.plane;
     __syncthreads();
     if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
   }
-  if (a.det.kind) {
+  if (det_on) {
     double v = lsum;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((tid & 31) == 0) red[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
-      for (int wv = 0; wv < TY; ++wv) t += red[wv];
+      for (int wv = 0; wv < TYT; ++wv) t += red[wv];
       if (t != 0.0) atomicAdd(a.obj, t);
     }
   }
@@ -365,18 +414,14 @@ struct RE {
   static int smem() { return S * STAGE + 8 * S; }
 };
 
-template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY) k_srev_e(const __grid_constant__ SplitMaps m,
-                                                   StepArgs a) {
+template <int TY, int RPT, int S>
+__global__ void __launch_bounds__(32 * TY / RPT) k_srev_e(const __grid_constant__ SplitMaps m,
+                                                         StepArgs a) {
   typedef SL<TY> L;
   typedef RE<TY, S> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool valid = x < g.nx && y < g.ny;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  ROWS_SETUP();
   // slab flags include the +1 neighbours the adjoint reads
   const bool txs = tile_in_slab(x0, min(x0 + 32, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
@@ -404,49 +449,75 @@ __global__ void __launch_bounds__(32 * TY) k_srev_e(const __grid_constant__ Spli
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
-  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
-  const bool sx1 = in_slab(x + 1, g.nx, g.P), sy1 = in_slab(y + 1, g.ny, g.P);
-  const bool inxy = x >= g.P && x < g.nx - g.P && y >= g.P && y < g.ny - g.P;
-  const bool dxy = x >= a.dlo[0] && x < a.dhi[0] && y >= a.dlo[1] && y < a.dhi[1];
+  const bool xv = x < g.nx;
+  const bool sx = xv && in_slab(x, g.nx, g.P), sx1 = x + 1 < g.nx && in_slab(x + 1, g.nx, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f;
+  if (sx) { bx = prof(g, 0, PR_BE, x); ax = prof(g, 0, PR_AE, x); kx = prof(g, 0, PR_KE, x); }
+  if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
+  const bool xin = x >= g.P && x < g.nx - g.P;
+  const bool dx_in = x >= a.dlo[0] && x < a.dhi[0];
   const int dX = a.dhi[0] - a.dlo[0], dY = a.dhi[1] - a.dlo[1];
-  const int hi = (ty + 1) * L::HW + tx + 4;
-  const int oi = ty * L::OW + tx;
+  bool valid[RPT];
+  long long q[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int y = y0 + ty + r * TYT;
+    valid[r] = xv && y < g.ny;
+    q[r] = (long long)k0 * g.plane + (long long)y * g.px + x;
+  }
   float* F = a.F;
   float* LL = a.L;
   float* lpB = a.psiB;
-  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  const long long nc = g.nc;
+  const bool src_on = a.src.kind != 0;
   bool ok = true;
-  for (int k = k0; k < k1; ++k, q += g.plane) {
+  for (int k = k0; k < k1; ++k) {
     if (!R.wait(k - 1) || !R.wait(k) || !R.wait(k + 1)) ok = false;
     if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
-    if (valid) {
-      const unsigned char* sc = R.at(k);
-      const unsigned char* sn = R.at(k + 1);
-      const float* LEc = reinterpret_cast<const float*>(sc + Y::LE);
-      const float* CBc = reinterpret_cast<const float*>(sc + Y::CB);
+    const unsigned char* sc = R.at(k);
+    const unsigned char* sn = R.at(k + 1);
+    const float* LEc = reinterpret_cast<const float*>(sc + Y::LE);
+    const float* CBc = reinterpret_cast<const float*>(sc + Y::CB);
+    const float* LEn = reinterpret_cast<const float*>(sn + Y::LE);
+    const float* CBn = reinterpret_cast<const float*>(sn + Y::CB);
+    const float* Hc = reinterpret_cast<const float*>(sc + Y::H);
+    const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
+    const float* Eo = reinterpret_cast<const float*>(sc + Y::E);
+    const float* LHo = reinterpret_cast<const float*>(sc + Y::LH);
+    const bool kin = k >= g.P && k < g.nz - g.P;
+    const bool dk_in = k >= a.dlo[2] && k < a.dhi[2];
+    const bool sz = in_slab(k, g.nz, g.P), sz1 = k + 1 < g.nz && in_slab(k + 1, g.nz, g.P);
+    const bool zlast = k + 1 >= g.nz;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!valid[r]) continue;
+      const int ty_r = ty + r * TYT;
+      const int y = y0 + ty_r;
+      const int hi = (ty_r + 1) * L::HW + tx + 4;
+      const int oi = ty_r * L::OW + tx;
+      const long long qq = q[r];
       const float cbv = CBc[hi];
       const float lex = LEc[hi], ley = LEc[L::HP + hi], lez = LEc[2 * L::HP + hi];
       // primal inverse E update on the interior, dL/dcb on the design box
-      if (tint && inxy && k >= g.P && k < g.nz - g.P) {
-        const float* Hc = reinterpret_cast<const float*>(sc + Y::H);
-        const float* Hm = reinterpret_cast<const float*>(R.at(k - 1) + Y::H);
-        const float* Eo = reinterpret_cast<const float*>(sc + Y::E);
+      if (tint && xin && kin && y >= g.P && y < g.ny - g.P) {
         const float hx = Hc[hi], hy = Hc[L::HP + hi], hz = Hc[2 * L::HP + hi];
         const float d6 = hz - Hc[2 * L::HP + hi - L::HW], d7 = hy - Hm[L::HP + hi];
         const float d8 = hx - Hm[hi], d9 = hz - Hc[2 * L::HP + hi - 1];
         const float d10 = hy - Hc[L::HP + hi - 1], d11 = hx - Hc[hi - L::HW];
         float c0 = d6 - d7, c1 = d8 - d9, c2 = d10 - d11;
-        const float w = src_wt(a.src, x, y, k);
-        if (w != 0.f) {
-          const float wj = __fmul_rn(w, a.jn);
-          if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
-          else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
-          else c2 = __fsub_rn(c2, wj);
+        if (src_on) {
+          const float w = src_wt(a.src, x, y, k);
+          if (w != 0.f) {
+            const float wj = __fmul_rn(w, a.jn);
+            if (a.src.comp == 0) c0 = __fsub_rn(c0, wj);
+            else if (a.src.comp == 1) c1 = __fsub_rn(c1, wj);
+            else c2 = __fsub_rn(c2, wj);
+          }
         }
-        F[q] = __fsub_rn(Eo[oi], __fmul_rn(cbv, c0));
-        F[g.nc + q] = __fsub_rn(Eo[L::OP + oi], __fmul_rn(cbv, c1));
-        F[2 * g.nc + q] = __fsub_rn(Eo[2 * L::OP + oi], __fmul_rn(cbv, c2));
-        if (dxy && k >= a.dlo[2] && k < a.dhi[2]) {
+        F[qq] = __fsub_rn(Eo[oi], __fmul_rn(cbv, c0));
+        F[nc + qq] = __fsub_rn(Eo[L::OP + oi], __fmul_rn(cbv, c1));
+        F[2 * nc + qq] = __fsub_rn(Eo[2 * L::OP + oi], __fmul_rn(cbv, c2));
+        if (dx_in && dk_in && y >= a.dlo[1] && y < a.dhi[1]) {
           const float s = lex * c0 + ley * c1 + lez * c2;
           const long long qd = ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (x - a.dlo[0]);
           a.gacc[qd] += (double)s;
@@ -457,60 +528,56 @@ __global__ void __launch_bounds__(32 * TY) k_srev_e(const __grid_constant__ Spli
       float o6 = wx, o11 = -wz, o7 = -wx, o8 = wy, o9 = -wy, o10 = wz;
       float n6, n11, n7, n8, n9, n10;
       {  // +y neighbour (terms t6: Ex,y,+ and t11: Ez,y,-)
-        const int r = hi + L::HW;
-        const float c2 = CBc[r];
-        n6 = c2 * LEc[r];
-        n11 = -c2 * LEc[2 * L::HP + r];
+        const int rr = hi + L::HW;
+        const float c2 = CBc[rr];
+        n6 = c2 * LEc[rr];
+        n11 = -c2 * LEc[2 * L::HP + rr];
       }
       {  // +x neighbour (t9: Ey,x,- and t10: Ez,x,+)
-        const int r = hi + 1;
-        const float c2 = CBc[r];
-        n9 = -c2 * LEc[L::HP + r];
-        n10 = c2 * LEc[2 * L::HP + r];
+        const int rr = hi + 1;
+        const float c2 = CBc[rr];
+        n9 = -c2 * LEc[L::HP + rr];
+        n10 = c2 * LEc[2 * L::HP + rr];
       }
       {  // +z neighbour (t7: Ex,z,- and t8: Ey,z,+)
-        const float* LEn = reinterpret_cast<const float*>(sn + Y::LE);
-        const float c2 = reinterpret_cast<const float*>(sn + Y::CB)[hi];
+        const float c2 = CBn[hi];
         n7 = -c2 * LEn[hi];
         n8 = c2 * LEn[L::HP + hi];
       }
       if (y + 1 >= g.ny) { n6 = 0.f; n11 = 0.f; }
       if (x + 1 >= g.nx) { n9 = 0.f; n10 = 0.f; }
-      if (k + 1 >= g.nz) { n7 = 0.f; n8 = 0.f; }
-      if (sy || (sy1 && y + 1 < g.ny)) {
+      if (zlast) { n7 = 0.f; n8 = 0.f; }
+      const bool sy = in_slab(y, g.ny, g.P), sy1 = y + 1 < g.ny && in_slab(y + 1, g.ny, g.P);
+      if (sy || sy1) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PY);
-        const float b = prof(g, 1, PR_BE, y), aa = prof(g, 1, PR_AE, y), kv = prof(g, 1, PR_KE, y);
         if (sy) {
-          o6 = adj_s(o6, P[hi], lpB, psi_at(g, 1, 2, x, y, k), true, b, aa, kv);
-          o11 = adj_s(o11, P[L::HP + hi], lpB, psi_at(g, 1, 3, x, y, k), true, b, aa, kv);
+          const float b = prof(g, 1, PR_BE, y), aa = prof(g, 1, PR_AE, y), kv = prof(g, 1, PR_KE, y);
+          o6 = adj_s(o6, P[hi], lpB, 6 * nc + qq, true, b, aa, kv);
+          o11 = adj_s(o11, P[L::HP + hi], lpB, 7 * nc + qq, true, b, aa, kv);
         }
-        if (sy1 && y + 1 < g.ny) {
+        if (sy1) {
           const float b1 = prof(g, 1, PR_BE, y + 1), a1 = prof(g, 1, PR_AE, y + 1),
                       k1v = prof(g, 1, PR_KE, y + 1);
           n6 = adj_s(n6, P[hi + L::HW], lpB, 0, false, b1, a1, k1v);
           n11 = adj_s(n11, P[L::HP + hi + L::HW], lpB, 0, false, b1, a1, k1v);
         }
       }
-      if (sx || (sx1 && x + 1 < g.nx)) {
+      if (sx || sx1) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PX);
         if (sx) {
-          const float b = prof(g, 0, PR_BE, x), aa = prof(g, 0, PR_AE, x), kv = prof(g, 0, PR_KE, x);
-          o9 = adj_s(o9, P[hi], lpB, psi_at(g, 0, 2, x, y, k), true, b, aa, kv);
-          o10 = adj_s(o10, P[L::HP + hi], lpB, psi_at(g, 0, 3, x, y, k), true, b, aa, kv);
+          o9 = adj_s(o9, P[hi], lpB, 2 * nc + qq, true, bx, ax, kx);
+          o10 = adj_s(o10, P[L::HP + hi], lpB, 3 * nc + qq, true, bx, ax, kx);
         }
-        if (sx1 && x + 1 < g.nx) {
-          const float b1 = prof(g, 0, PR_BE, x + 1), a1 = prof(g, 0, PR_AE, x + 1),
-                      k1v = prof(g, 0, PR_KE, x + 1);
-          n9 = adj_s(n9, P[hi + 1], lpB, 0, false, b1, a1, k1v);
-          n10 = adj_s(n10, P[L::HP + hi + 1], lpB, 0, false, b1, a1, k1v);
+        if (sx1) {
+          n9 = adj_s(n9, P[hi + 1], lpB, 0, false, bx1, ax1, kx1);
+          n10 = adj_s(n10, P[L::HP + hi + 1], lpB, 0, false, bx1, ax1, kx1);
         }
       }
-      const bool sz = in_slab(k, g.nz, g.P), sz1 = k + 1 < g.nz && in_slab(k + 1, g.nz, g.P);
       if (sz) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PZ);
         const float b = prof(g, 2, PR_BE, k), aa = prof(g, 2, PR_AE, k), kv = prof(g, 2, PR_KE, k);
-        o7 = adj_s(o7, P[hi], lpB, psi_at(g, 2, 2, x, y, k), true, b, aa, kv);
-        o8 = adj_s(o8, P[L::HP + hi], lpB, psi_at(g, 2, 3, x, y, k), true, b, aa, kv);
+        o7 = adj_s(o7, P[hi], lpB, 10 * nc + qq, true, b, aa, kv);
+        o8 = adj_s(o8, P[L::HP + hi], lpB, 11 * nc + qq, true, b, aa, kv);
       }
       if (sz1) {
         const float* P = reinterpret_cast<const float*>(sn + Y::PZ);
@@ -519,11 +586,12 @@ __global__ void __launch_bounds__(32 * TY) k_srev_e(const __grid_constant__ Spli
         n7 = adj_s(n7, P[hi], lpB, 0, false, b1, a1, k1v);
         n8 = adj_s(n8, P[L::HP + hi], lpB, 0, false, b1, a1, k1v);
       }
-      const float* LHo = reinterpret_cast<const float*>(sc + Y::LH);
-      LL[3 * g.nc + q] = LHo[oi] + ((o8 - n8) + (o11 - n11));
-      LL[4 * g.nc + q] = LHo[L::OP + oi] + ((o7 - n7) + (o10 - n10));
-      LL[5 * g.nc + q] = LHo[2 * L::OP + oi] + ((o6 - n6) + (o9 - n9));
+      LL[3 * nc + qq] = LHo[oi] + ((o8 - n8) + (o11 - n11));
+      LL[4 * nc + qq] = LHo[L::OP + oi] + ((o7 - n7) + (o10 - n10));
+      LL[5 * nc + qq] = LHo[2 * L::OP + oi] + ((o6 - n6) + (o9 - n9));
     }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) q[r] += g.plane;
     __syncthreads();
     if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
   }
@@ -544,18 +612,14 @@ struct RH {
   static int smem() { return S * STAGE + 8 * S; }
 };
 
-template <int TY, int S>
-__global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ SplitMaps m,
-                                                   StepArgs a) {
+template <int TY, int RPT, int S>
+__global__ void __launch_bounds__(32 * TY / RPT) k_srev_h(const __grid_constant__ SplitMaps m,
+                                                         StepArgs a) {
   typedef SL<TY> L;
   typedef RH<TY, S> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool valid = x < g.nx && y < g.ny;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  ROWS_SETUP();
   // slab flags include the -1 neighbours the adjoint reads
   const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + 31, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
@@ -582,39 +646,58 @@ __global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ Spli
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
-  const bool sx = in_slab(x, g.nx, g.P), sy = in_slab(y, g.ny, g.P);
-  const bool sxm = x > 0 && in_slab(x - 1, g.nx, g.P), sym = y > 0 && in_slab(y - 1, g.ny, g.P);
-  const bool inxy = x >= g.P && x < g.nx - g.P && y >= g.P && y < g.ny - g.P;
-  const int hi = (ty + 1) * L::HW + tx + 4;
-  const int oi = ty * L::OW + tx;
+  const bool xv = x < g.nx;
+  const bool sx = xv && in_slab(x, g.nx, g.P), sxm = xv && x > 0 && in_slab(x - 1, g.nx, g.P);
+  float bx = 0.f, ax = 0.f, kx = 1.f, bxm = 0.f, axm = 0.f, kxm = 1.f;
+  if (sx) { bx = prof(g, 0, PR_BH, x); ax = prof(g, 0, PR_AH, x); kx = prof(g, 0, PR_KH, x); }
+  if (sxm) { bxm = prof(g, 0, PR_BH, x - 1); axm = prof(g, 0, PR_AH, x - 1); kxm = prof(g, 0, PR_KH, x - 1); }
+  const bool xin = x >= g.P && x < g.nx - g.P;
+  bool valid[RPT];
+  long long q[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int y = y0 + ty + r * TYT;
+    valid[r] = xv && y < g.ny;
+    q[r] = (long long)k0 * g.plane + (long long)y * g.px + x;
+  }
   const float S_ = g.S;
   float* F = a.F;
   float* LL = a.L;
   float* lpB = a.psiB;
-  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  const long long nc = g.nc;
   bool ok = true;
-  for (int k = k0; k < k1; ++k, q += g.plane) {
+  for (int k = k0; k < k1; ++k) {
     if (!R.wait(k - 1) || !R.wait(k) || !R.wait(k + 1)) ok = false;
     if (!__syncthreads_and(ok)) { ring_drain<S>(R, a.err); return; }
-    if (valid) {
-      const unsigned char* sc = R.at(k);
-      const unsigned char* sp = R.at(k - 1);
+    const unsigned char* sc = R.at(k);
+    const unsigned char* sp = R.at(k - 1);
+    const float* Ec = reinterpret_cast<const float*>(sc + Y::E);
+    const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
+    const float* Ho = reinterpret_cast<const float*>(sc + Y::H);
+    const float* LHc = reinterpret_cast<const float*>(sc + Y::LH);
+    const float* LHp = reinterpret_cast<const float*>(sp + Y::LH);
+    const float* LEo = reinterpret_cast<const float*>(sc + Y::LE);
+    const bool kin = k >= g.P && k < g.nz - g.P;
+    const bool sz = in_slab(k, g.nz, g.P), szm = k > 0 && in_slab(k - 1, g.nz, g.P);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!valid[r]) continue;
+      const int ty_r = ty + r * TYT;
+      const int y = y0 + ty_r;
+      const int hi = (ty_r + 1) * L::HW + tx + 4;
+      const int oi = ty_r * L::OW + tx;
+      const long long qq = q[r];
       // primal inverse H update on the interior
-      if (tint && inxy && k >= g.P && k < g.nz - g.P) {
-        const float* Ec = reinterpret_cast<const float*>(sc + Y::E);
-        const float* En = reinterpret_cast<const float*>(R.at(k + 1) + Y::E);
-        const float* Ho = reinterpret_cast<const float*>(sc + Y::H);
+      if (tint && xin && kin && y >= g.P && y < g.ny - g.P) {
         const float ex = Ec[hi], ey = Ec[L::HP + hi], ez = Ec[2 * L::HP + hi];
         const float d0 = Ec[2 * L::HP + hi + L::HW] - ez, d1 = En[L::HP + hi] - ey;
         const float d2 = En[hi] - ex, d3 = Ec[2 * L::HP + hi + 1] - ez;
         const float d4 = Ec[L::HP + hi + 1] - ey, d5 = Ec[hi + L::HW] - ex;
-        F[3 * g.nc + q] = __fadd_rn(Ho[oi], __fmul_rn(S_, d0 - d1));
-        F[4 * g.nc + q] = __fadd_rn(Ho[L::OP + oi], __fmul_rn(S_, d2 - d3));
-        F[5 * g.nc + q] = __fadd_rn(Ho[2 * L::OP + oi], __fmul_rn(S_, d4 - d5));
+        F[3 * nc + qq] = __fadd_rn(Ho[oi], __fmul_rn(S_, d0 - d1));
+        F[4 * nc + qq] = __fadd_rn(Ho[L::OP + oi], __fmul_rn(S_, d2 - d3));
+        F[5 * nc + qq] = __fadd_rn(Ho[2 * L::OP + oi], __fmul_rn(S_, d4 - d5));
       }
       // adjoint of the H half-step: lam_E += D^T lam_delta, v = -S s lam_H
-      const float* LHc = reinterpret_cast<const float*>(sc + Y::LH);
-      const float* LHp = reinterpret_cast<const float*>(sp + Y::LH);
       const float lhx = LHc[hi], lhy = LHc[L::HP + hi], lhz = LHc[2 * L::HP + hi];
       float o0 = -S_ * lhx, o5 = S_ * lhz, o1 = S_ * lhx, o2 = -S_ * lhy, o3 = S_ * lhy,
             o4 = -S_ * lhz;
@@ -624,12 +707,13 @@ __global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ Spli
       if (y == 0) { m0 = 0.f; m5 = 0.f; }
       if (x == 0) { m3 = 0.f; m4 = 0.f; }
       if (k == 0) { m1 = 0.f; m2 = 0.f; }
+      const bool sy = in_slab(y, g.ny, g.P), sym = y > 0 && in_slab(y - 1, g.ny, g.P);
       if (sy || sym) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PY);
         if (sy) {
           const float b = prof(g, 1, PR_BH, y), aa = prof(g, 1, PR_AH, y), kv = prof(g, 1, PR_KH, y);
-          o0 = adj_s(o0, P[hi], lpB, psi_at(g, 1, 0, x, y, k), true, b, aa, kv);
-          o5 = adj_s(o5, P[L::HP + hi], lpB, psi_at(g, 1, 1, x, y, k), true, b, aa, kv);
+          o0 = adj_s(o0, P[hi], lpB, 4 * nc + qq, true, b, aa, kv);
+          o5 = adj_s(o5, P[L::HP + hi], lpB, 5 * nc + qq, true, b, aa, kv);
         }
         if (sym) {
           const float b1 = prof(g, 1, PR_BH, y - 1), a1 = prof(g, 1, PR_AH, y - 1),
@@ -641,23 +725,19 @@ __global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ Spli
       if (sx || sxm) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PX);
         if (sx) {
-          const float b = prof(g, 0, PR_BH, x), aa = prof(g, 0, PR_AH, x), kv = prof(g, 0, PR_KH, x);
-          o3 = adj_s(o3, P[hi], lpB, psi_at(g, 0, 0, x, y, k), true, b, aa, kv);
-          o4 = adj_s(o4, P[L::HP + hi], lpB, psi_at(g, 0, 1, x, y, k), true, b, aa, kv);
+          o3 = adj_s(o3, P[hi], lpB, 0 * nc + qq, true, bx, ax, kx);
+          o4 = adj_s(o4, P[L::HP + hi], lpB, 1 * nc + qq, true, bx, ax, kx);
         }
         if (sxm) {
-          const float b1 = prof(g, 0, PR_BH, x - 1), a1 = prof(g, 0, PR_AH, x - 1),
-                      k1v = prof(g, 0, PR_KH, x - 1);
-          m3 = adj_s(m3, P[hi - 1], lpB, 0, false, b1, a1, k1v);
-          m4 = adj_s(m4, P[L::HP + hi - 1], lpB, 0, false, b1, a1, k1v);
+          m3 = adj_s(m3, P[hi - 1], lpB, 0, false, bxm, axm, kxm);
+          m4 = adj_s(m4, P[L::HP + hi - 1], lpB, 0, false, bxm, axm, kxm);
         }
       }
-      const bool sz = in_slab(k, g.nz, g.P), szm = k > 0 && in_slab(k - 1, g.nz, g.P);
       if (sz) {
         const float* P = reinterpret_cast<const float*>(sc + Y::PZ);
         const float b = prof(g, 2, PR_BH, k), aa = prof(g, 2, PR_AH, k), kv = prof(g, 2, PR_KH, k);
-        o1 = adj_s(o1, P[hi], lpB, psi_at(g, 2, 0, x, y, k), true, b, aa, kv);
-        o2 = adj_s(o2, P[L::HP + hi], lpB, psi_at(g, 2, 1, x, y, k), true, b, aa, kv);
+        o1 = adj_s(o1, P[hi], lpB, 8 * nc + qq, true, b, aa, kv);
+        o2 = adj_s(o2, P[L::HP + hi], lpB, 9 * nc + qq, true, b, aa, kv);
       }
       if (szm) {
         const float* P = reinterpret_cast<const float*>(sp + Y::PZ);
@@ -666,11 +746,12 @@ __global__ void __launch_bounds__(32 * TY) k_srev_h(const __grid_constant__ Spli
         m1 = adj_s(m1, P[hi], lpB, 0, false, b1, a1, k1v);
         m2 = adj_s(m2, P[L::HP + hi], lpB, 0, false, b1, a1, k1v);
       }
-      const float* LEo = reinterpret_cast<const float*>(sc + Y::LE);
-      LL[q] = LEo[oi] + ((m2 - o2) + (m5 - o5));
-      LL[g.nc + q] = LEo[L::OP + oi] + ((m1 - o1) + (m4 - o4));
-      LL[2 * g.nc + q] = LEo[2 * L::OP + oi] + ((m0 - o0) + (m3 - o3));
+      LL[qq] = LEo[oi] + ((m2 - o2) + (m5 - o5));
+      LL[nc + qq] = LEo[L::OP + oi] + ((m1 - o1) + (m4 - o4));
+      LL[2 * nc + qq] = LEo[2 * L::OP + oi] + ((m0 - o0) + (m3 - o3));
     }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) q[r] += g.plane;
     __syncthreads();
     if (tid == 0 && k - 1 + S <= R.p1) issue(k - 1 + S);
   }
@@ -682,35 +763,35 @@ static cudaError_t set_smem(KT kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int TY, int S>
+template <int TY, int RPT, int S>
 static cudaError_t launch_split_t(int which, const SplitMaps& m, const StepArgs& a,
                                   cudaStream_t s) {
   dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
-  dim3 block(32, TY);
+  dim3 block(32, TY / RPT);
   cudaError_t e = cudaSuccess;
   switch (which) {
     case 0: {
       int sm = FH<TY, S>::smem();
-      if ((e = set_smem(k_sfwd_h<TY, S>, sm))) return e;
-      k_sfwd_h<TY, S><<<grid, block, sm, s>>>(m, a);
+      if ((e = set_smem(k_sfwd_h<TY, RPT, S>, sm))) return e;
+      k_sfwd_h<TY, RPT, S><<<grid, block, sm, s>>>(m, a);
       break;
     }
     case 1: {
       int sm = FE<TY, S>::smem();
-      if ((e = set_smem(k_sfwd_e<TY, S>, sm))) return e;
-      k_sfwd_e<TY, S><<<grid, block, sm, s>>>(m, a);
+      if ((e = set_smem(k_sfwd_e<TY, RPT, S>, sm))) return e;
+      k_sfwd_e<TY, RPT, S><<<grid, block, sm, s>>>(m, a);
       break;
     }
     case 2: {
       int sm = RE<TY, S>::smem();
-      if ((e = set_smem(k_srev_e<TY, S>, sm))) return e;
-      k_srev_e<TY, S><<<grid, block, sm, s>>>(m, a);
+      if ((e = set_smem(k_srev_e<TY, RPT, S>, sm))) return e;
+      k_srev_e<TY, RPT, S><<<grid, block, sm, s>>>(m, a);
       break;
     }
     case 3: {
       int sm = RH<TY, S>::smem();
-      if ((e = set_smem(k_srev_h<TY, S>, sm))) return e;
-      k_srev_h<TY, S><<<grid, block, sm, s>>>(m, a);
+      if ((e = set_smem(k_srev_h<TY, RPT, S>, sm))) return e;
+      k_srev_h<TY, RPT, S><<<grid, block, sm, s>>>(m, a);
       break;
     }
     default: return cudaErrorInvalidValue;
@@ -719,13 +800,15 @@ static cudaError_t launch_split_t(int which, const SplitMaps& m, const StepArgs&
 }
 
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
+// a.rows: rows of the tile each thread handles (1 or 2; tile height 1 uses 1).
 cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s) {
+  const bool two = a.rows >= 2;
   switch (a.tile_y) {
-    case 1: return launch_split_t<1, 4>(which, m, a, s);
-    case 2: return launch_split_t<2, 4>(which, m, a, s);
-    case 4: return launch_split_t<4, 4>(which, m, a, s);
-    case 8: return launch_split_t<8, 4>(which, m, a, s);
-    case 16: return launch_split_t<16, 3>(which, m, a, s);
+    case 1: return launch_split_t<1, 1, 4>(which, m, a, s);
+    case 2: return two ? launch_split_t<2, 2, 4>(which, m, a, s) : launch_split_t<2, 1, 4>(which, m, a, s);
+    case 4: return two ? launch_split_t<4, 2, 4>(which, m, a, s) : launch_split_t<4, 1, 4>(which, m, a, s);
+    case 8: return two ? launch_split_t<8, 2, 4>(which, m, a, s) : launch_split_t<8, 1, 4>(which, m, a, s);
+    case 16: return two ? launch_split_t<16, 2, 3>(which, m, a, s) : launch_split_t<16, 1, 3>(which, m, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -139,13 +139,14 @@ def test_graphs_and_direct_launches_agree(F, A):
     np.testing.assert_allclose(a["g"], b["g"], rtol=1e-12, atol=1e-30)
 
 
-@pytest.mark.parametrize("zchunk,tile_y", [(1, 4), (3, 8), (0, 2), (16, 1), (5, 16)])
-def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y):
+@pytest.mark.parametrize("zchunk,tile_y,rows", [(1, 4, 2), (3, 8, 1), (0, 2, 2), (16, 1, 1),
+                                                (5, 16, 2), (2, 8, 2)])
+def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y, rows):
     w = SMALL["ragged_poynting"]()
     base = gpu_run(F, A, w)
     for kernel in KERNELS:
         r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel, A.OPT_ZCHUNK: zchunk,
-                                      A.OPT_TILE_Y: tile_y})
+                                      A.OPT_TILE_Y: tile_y, A.OPT_ROWS: rows})
         np.testing.assert_array_equal(r["fields"], base["fields"])
         np.testing.assert_allclose(r["g"], base["g"], rtol=1e-6, atol=1e-12 * np.abs(base["g"]).max())
 
