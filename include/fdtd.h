@@ -168,10 +168,11 @@ int fdtd_destroy(fdtd_handle* h);
 enum {
   FDTD_OPT_USE_GRAPHS = 0,    /* 1 (default): replay the time loop as a CUDA graph */
   FDTD_OPT_KERNEL = 1,        /* 0: split half-steps (plain loads), 1: fused 2.5D forward
-                                 (plain loads), 2: fused forward with TMA staging, 3 (default):
-                                 split half-steps with TMA staging; 2 and 3 use the
-                                 TMA-staged reverse kernels, 0 and 1 the plain ones */
-  FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8); width is 32 */
+                                 (plain loads), 2: fused forward with TMA staging, 3: split
+                                 half-steps with TMA staging, 4 (default): TMA half-steps that
+                                 read one plane per iteration; 2 and 3 use the TMA reverse of
+                                 3, 0 and 1 the plain reverse */
+  FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4 default, 8, 16); width 32 */
   FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
   FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: time every m-th launch of each kernel kind with
                                  CUDA events on the library's stream (0 = off) */

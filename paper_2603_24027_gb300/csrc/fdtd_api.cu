@@ -471,8 +471,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->have_forward = false;
   h->fwd_buf = 0;
   h->opt_graphs = 1;
-  h->opt_kernel = 3;
-  h->opt_tile_y = 8;
+  h->opt_kernel = 4;
+  h->opt_tile_y = 4;
   h->opt_zchunk = 8;
   h->opt_sample = 0;
   h->opt_rows = 1;
@@ -553,7 +553,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
   switch (option) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
-      if (value < 0 || value > 3) return fail(h, FDTD_EINVAL, "kernel must be 0..3");
+      if (value < 0 || value > 4) return fail(h, FDTD_EINVAL, "kernel must be 0..4");
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
@@ -744,11 +744,18 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   const bool fused = h->opt_kernel == 1 || h->opt_kernel == 2;
   const bool tma = h->opt_kernel == 2;
   const bool split_tma = h->opt_kernel == 3;
+  const bool lagk = h->opt_kernel == 4;
   SplitMaps smaps;
   if (split_tma &&
       (e = encode_split_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
                              (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
                              h->opt_tile_y, &smaps)))
+    return e;
+  LagMaps lmaps;
+  if (lagk &&
+      (e = encode_lag_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
+                           (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
+                           h->opt_tile_y, &lmaps)))
     return e;
   if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
     for (int b = 0; b < 2; ++b)
@@ -798,7 +805,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
-    if ((e = split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
+    if ((e = lagk ? launch_lag(0, lmaps, a, h->stream)
+                  : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
     ++nl;
@@ -813,7 +821,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
     }
     if ((e = mark(h, FDTD_K_FWD_E, 0, sm))) return e;
-    if ((e = split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
+    if ((e = lagk ? launch_lag(1, lmaps, a, h->stream)
+                  : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
     ++nl;
@@ -839,14 +848,20 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
   int cur = 0;
-  const bool rtma = h->opt_kernel >= 2;
+  const bool rlag = h->opt_kernel == 4;
+  const bool rtma = h->opt_kernel == 2 || h->opt_kernel == 3;
   SplitMaps rmaps[2];
-  if (rtma)
-    for (int b = 0; b < 2; ++b)
-      if ((e = encode_split_maps(a.F, a.L, (const float*)(h->ws + L.cb),
-                                 (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
-                                 &rmaps[b])))
-        return e;
+  LagMaps lrmaps[2];
+  for (int b = 0; b < 2; ++b) {
+    if (rtma && (e = encode_split_maps(a.F, a.L, (const float*)(h->ws + L.cb),
+                                       (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
+                                       &rmaps[b])))
+      return e;
+    if (rlag && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
+                                     (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
+                                     &lrmaps[b])))
+      return e;
+  }
   reset_samples(h, kBwdKinds, 4);
   for (int n = h->N - 1; n >= 0; --n) {
     bool sm = sampled(h, n);
@@ -862,11 +877,13 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = mark(h, FDTD_K_REV_E, 0, sm))) return e;
-    if ((e = rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
+    if ((e = rlag ? launch_lag(2, lrmaps[cur], a, h->stream)
+              : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_REV_E, 1, sm))) return e;
     if ((e = mark(h, FDTD_K_REV_H, 0, sm))) return e;
-    if ((e = rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
+    if ((e = rlag ? launch_lag(3, lrmaps[cur], a, h->stream)
+              : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_REV_H, 1, sm))) return e;
     cur ^= 1;

@@ -173,6 +173,16 @@ cudaError_t encode_split_maps(const float* F, const float* L, const float* cb, c
                               const Geo& g, int ty, SplitMaps* m);
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
 cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s);
+
+// Tensor maps of the one-plane-per-iteration kernels: 36 x (ty+1) boxes
+// (own and one neighbour side), own boxes, and the psi boxes 36 x ty,
+// 32 x (ty+1), 32 x ty.
+struct alignas(64) LagMaps {
+  CUtensorMap F36, F32, L36, L32, cb36, cb32, P36, P32y, P32;
+};
+cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
+                            const Geo& g, int ty, LagMaps* m);
+cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
                            cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,

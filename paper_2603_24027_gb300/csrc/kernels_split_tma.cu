@@ -144,6 +144,11 @@ __global__ void __launch_bounds__(32 * TY / RPT) k_sfwd_h(const __grid_constant_
     if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 0);
     if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 4);
     if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 8);
+    const int pf = p + S;   // warm L2 for the plane this stage will hold next
+    if (pf <= R.p1 && pf < g.nz) {
+      tma_prefetch_l2_4d(&m.Fh, x0 - 4, y0 - 1, pf, 0);
+      if (pf < k1) tma_prefetch_l2_4d(&m.Fo, x0, y0, pf, 3);
+    }
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -271,6 +276,12 @@ __global__ void __launch_bounds__(32 * TY / RPT) k_sfwd_e(const __grid_constant_
     if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 2);
     if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 6);
     if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 10);
+    const int pf = p + S;
+    if (pf <= R.p1 && pf >= 0 && pf < g.nz) {
+      tma_prefetch_l2_4d(&m.Fh, x0 - 4, y0 - 1, pf, 3);
+      tma_prefetch_l2_4d(&m.Fo, x0, y0, pf, 0);
+      tma_prefetch_l2_4d(&m.cbo, x0, y0, pf, 0);
+    }
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -442,6 +453,16 @@ __global__ void __launch_bounds__(32 * TY / RPT) k_srev_e(const __grid_constant_
     if (body) {
       tma_load_4d(st + Y::E, &m.Fo, bar, x0, y0, p, 0);
       tma_load_4d(st + Y::LH, &m.Lo, bar, x0, y0, p, 3);
+    }
+    const int pf = p + S;
+    if (pf <= R.p1 && pf >= 0 && pf < g.nz) {
+      tma_prefetch_l2_4d(&m.Fh, x0 - 4, y0 - 1, pf, 3);
+      tma_prefetch_l2_4d(&m.cbh, x0 - 4, y0 - 1, pf, 0);
+      tma_prefetch_l2_4d(&m.Lh, x0 - 4, y0 - 1, pf, 0);
+      if (pf < k1) {
+        tma_prefetch_l2_4d(&m.Fo, x0, y0, pf, 0);
+        tma_prefetch_l2_4d(&m.Lo, x0, y0, pf, 3);
+      }
     }
     if (body && txs) tma_load_4d(st + Y::PX, &m.Ph, bar, x0 - 4, y0 - 1, p, 2);
     if (body && tys) tma_load_4d(st + Y::PY, &m.Ph, bar, x0 - 4, y0 - 1, p, 6);
@@ -639,6 +660,15 @@ __global__ void __launch_bounds__(32 * TY / RPT) k_srev_h(const __grid_constant_
     if (body) {
       tma_load_4d(st + Y::H, &m.Fo, bar, x0, y0, p, 3);
       tma_load_4d(st + Y::LE, &m.Lo, bar, x0, y0, p, 0);
+    }
+    const int pf = p + S;
+    if (pf <= R.p1 && pf >= 0 && pf < g.nz) {
+      tma_prefetch_l2_4d(&m.Fh, x0 - 4, y0 - 1, pf, 0);
+      tma_prefetch_l2_4d(&m.Lh, x0 - 4, y0 - 1, pf, 3);
+      if (pf < k1) {
+        tma_prefetch_l2_4d(&m.Fo, x0, y0, pf, 3);
+        tma_prefetch_l2_4d(&m.Lo, x0, y0, pf, 0);
+      }
     }
     if (body && txs) tma_load_4d(st + Y::PX, &m.Ph, bar, x0 - 4, y0 - 1, p, 0);
     if (body && tys) tma_load_4d(st + Y::PY, &m.Ph, bar, x0 - 4, y0 - 1, p, 4);

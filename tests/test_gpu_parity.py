@@ -74,7 +74,7 @@ SMALL = {
 }
 
 
-KERNELS = [0, 1, 2, 3]   # split plain, fused plain, fused TMA (+TMA reverse), split TMA
+KERNELS = [0, 1, 2, 3, 4]   # split plain, fused plain, fused TMA, split TMA, one-plane TMA
 
 
 @pytest.mark.parametrize("name", list(SMALL))
