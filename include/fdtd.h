@@ -102,8 +102,9 @@ enum { FDTD_INTERP_LINEAR = 0, FDTD_INTERP_CUBIC = 1 };
 /* Boundary-tape compression (Sec. 2): storage type of the recorded slices,
  * k = keep every k-th step (the last step is always kept), and the time
  * interpolation used to restore the steps in between.  scaled = 1 stores a
- * per-face, per-sample FP32 scale absmax/format_max (F16 and E4M3 only);
- * values are converted back to FP32 before any arithmetic. */
+ * per-face, per-sample FP32 scale max(absmax/format_max, 2^-126) (1 when the
+ * face is all zero; F16 and E4M3 only); values are converted back to FP32
+ * before any arithmetic. */
 typedef struct {
   int dtype;
   int k;

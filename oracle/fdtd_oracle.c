@@ -712,7 +712,8 @@ static void encode_face(int fmt, int scaled, double* v, size_t n, double* scale_
   if (scaled) {
     double amax = 0.0;
     for (size_t i = 0; i < n; ++i) amax = fmax(amax, fabs(v[i]));
-    scale = amax > 0.0 ? amax / oracle_format_max(fmt) : 1.0;
+    /* at least the smallest normal FP32 number (2^-126), as stored scales are FP32 */
+    scale = amax > 0.0 ? fmax(amax / oracle_format_max(fmt), ldexp(1.0, -126)) : 1.0;
   }
   for (size_t i = 0; i < n; ++i) v[i] = oracle_quantize(fmt, v[i] / scale) * scale;
   if (scale_out) *scale_out = scale;

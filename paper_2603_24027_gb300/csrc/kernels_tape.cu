@@ -11,10 +11,11 @@
 // tangential E components at n.  One sample = 6 faces x 2 components x the
 // interior cross-section, [face][comp][v][u].
 //
-// k_record runs one thread-block cluster per face: every CTA takes a share of
-// the face, the per-face absmax is reduced across the cluster through
-// distributed shared memory, then each CTA encodes its share with the common
-// scale.  No global atomics and no second launch.
+// Scaled formats: k_record runs one thread-block cluster per face: every CTA
+// takes a share of the face, the per-face absmax is reduced across the
+// cluster through distributed shared memory, then each CTA encodes its share
+// with the common scale (no global atomics, no second launch).  Unscaled
+// formats use one thread per value.
 #include <cooperative_groups.h>
 
 #include "fdtd_internal.cuh"
@@ -23,69 +24,100 @@ namespace cg = cooperative_groups;
 
 namespace fdtd {
 
-static constexpr int REC_CLUSTER = 8;
-static constexpr int REC_THREADS = 512;
+// Smallest per-face scale: the smallest normal FP32 number, so that
+// amax / format_max never underflows to zero (0/0 would encode NaN).
+static constexpr float kMinScale = 1.17549435e-38f;
 
-__device__ __forceinline__ long long face_cell(const Geo& g, const FaceDesc& f, int r,
-                                               int* comp) {
-  int per = f.nu * f.nv;
-  int t = r / per;
-  int rem = r - t * per;
-  int v = rem / f.nu;
-  int u = rem - v * f.nu;
-  int p[3];
-  p[f.axis] = f.layer;
-  p[f.ua] = g.P + u;
-  p[f.va] = g.P + v;
-  *comp = t == 0 ? f.comp0 : f.comp1;
-  return (long long)p[2] * g.plane + (long long)p[1] * g.px + p[0];
+static constexpr int REC_CLUSTER = 8;     // raw codec entry points
+static constexpr int REC_THREADS = 512;
+static constexpr int FACE_CLUSTER = 16;   // CTAs per face when a face-wide absmax is needed
+static constexpr int FACE_THREADS = 1024;
+static constexpr int FLAT_THREADS = 256;  // one thread per value otherwise
+
+// Cell at (u, v) of the plane normal to `axis` at `index`; (u, v) are the
+// two other axes in increasing order.
+__device__ __forceinline__ long long cell_on_plane(const Geo& g, int axis, int index, int u,
+                                                   int v) {
+  const int x = axis == 0 ? index : u;
+  const int y = axis == 1 ? index : (axis == 0 ? u : v);
+  const int z = axis == 2 ? index : v;
+  return (long long)z * g.plane + (long long)y * g.px + x;
 }
 
+// Value r of face fd ([comp][v][u]): its field component and cell.
+__device__ __forceinline__ long long face_value_cell(const Geo& g, const FaceDesc& fd, int r,
+                                                    int* comp) {
+  const int row = r / fd.nu, u = r - row * fd.nu;
+  const int t = row >= fd.nv, v = row - t * fd.nv;
+  *comp = t ? fd.comp1 : fd.comp0;
+  return cell_on_plane(g, fd.axis, fd.layer, g.P + u, g.P + v);
+}
+
+// Unscaled formats: one thread per recorded value, grid (value blocks, face).
 template <int DT>
-__global__ void __launch_bounds__(REC_THREADS) k_record(const float* __restrict__ FH,
-                                                        const float* __restrict__ FE, Geo g,
-                                                        Faces fc, void* tape_sample,
-                                                        float* scale_slot, int scaled) {
+__global__ void __launch_bounds__(FLAT_THREADS) k_record_flat(const float* __restrict__ FH,
+                                                              const float* __restrict__ FE, Geo g,
+                                                              const __grid_constant__ Faces fc,
+                                                              void* __restrict__ tape_sample,
+                                                              float* scale_slot) {
   typedef typename Code<DT>::T T;
-  __shared__ float red[REC_THREADS / 32];
+  const int f = blockIdx.y;
+  const FaceDesc& fd = fc.f[f];
+  const int n = 2 * fd.nu * fd.nv;
+  const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale_slot[f] = 1.0f;
+  if (r >= n) return;
+  const float* __restrict__ F = (f & 1) ? FE : FH;
+  int comp;
+  const long long q = face_value_cell(g, fd, r, &comp);
+  reinterpret_cast<T*>(tape_sample)[fd.off + r] = Code<DT>::enc(F[comp * g.nc + q]);
+}
+
+// Scaled formats: one cluster of FACE_CLUSTER CTAs per face (blockIdx.y); the
+// face's absmax is reduced across the cluster through distributed shared
+// memory, then each CTA encodes its share with the common scale.
+template <int DT>
+__global__ void __launch_bounds__(FACE_THREADS) k_record(const float* __restrict__ FH,
+                                                         const float* __restrict__ FE, Geo g,
+                                                         const __grid_constant__ Faces fc,
+                                                         void* __restrict__ tape_sample,
+                                                         float* scale_slot) {
+  typedef typename Code<DT>::T T;
+  __shared__ float red[FACE_THREADS / 32];
   __shared__ float cl_amax;
   cg::cluster_group cluster = cg::this_cluster();
   const int f = blockIdx.y;
-  const FaceDesc fd = fc.f[f];
+  const FaceDesc& fd = fc.f[f];
   const float* __restrict__ F = (f & 1) ? FE : FH;
   const int n = 2 * fd.nu * fd.nv;
   const int rank = (int)cluster.block_rank();
   const int nr = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
-  float scale = 1.0f;
-  if (scaled) {
-    float m = 0.f;
-    for (int r = rank * REC_THREADS + tid; r < n; r += nr * REC_THREADS) {
-      int comp;
-      long long q = face_cell(g, fd, r, &comp);
-      m = fmaxf(m, fabsf(F[comp * g.nc + q]));
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((tid & 31) == 0) red[tid >> 5] = m;
-    __syncthreads();
-    if (tid < 32) {
-      float t = tid < REC_THREADS / 32 ? red[tid] : 0.f;
-      for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-      if (tid == 0) cl_amax = t;
-    }
-    cluster.sync();
-    float amax = 0.f;
-    for (int b = 0; b < nr; ++b) amax = fmaxf(amax, *cluster.map_shared_rank(&cl_amax, b));
-    cluster.sync();  // peers may still be reading this CTA's cl_amax
-    scale = amax > 0.f ? __fdiv_rn(amax, Code<DT>::fmax) : 1.0f;
+  float m = 0.f;
+  for (int r = rank * FACE_THREADS + tid; r < n; r += nr * FACE_THREADS) {
+    int comp;
+    const long long q = face_value_cell(g, fd, r, &comp);
+    m = fmaxf(m, fabsf(F[comp * g.nc + q]));
   }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  if (tid < 32) {
+    float t = red[tid];
+    for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (tid == 0) cl_amax = t;
+  }
+  cluster.sync();
+  float amax = 0.f;
+  for (int b = 0; b < nr; ++b) amax = fmaxf(amax, *cluster.map_shared_rank(&cl_amax, b));
+  cluster.sync();  // peers may still be reading this CTA's cl_amax
+  const float scale = amax > 0.f ? fmaxf(__fdiv_rn(amax, Code<DT>::fmax), kMinScale) : 1.0f;
   if (rank == 0 && tid == 0) scale_slot[f] = scale;
   T* out = reinterpret_cast<T*>(tape_sample) + fd.off;
-  for (int r = rank * REC_THREADS + tid; r < n; r += nr * REC_THREADS) {
+  for (int r = rank * FACE_THREADS + tid; r < n; r += nr * FACE_THREADS) {
     int comp;
-    long long q = face_cell(g, fd, r, &comp);
-    float x = F[comp * g.nc + q];
-    out[r] = Code<DT>::enc(scaled ? __fdiv_rn(x, scale) : x);
+    const long long q = face_value_cell(g, fd, r, &comp);
+    out[r] = Code<DT>::enc(__fdiv_rn(F[comp * g.nc + q], scale));
   }
 }
 
@@ -93,19 +125,33 @@ template <int DT>
 static cudaError_t launch_record_t(int scaled, const float* FH, const float* FE, Geo g,
                                    const Faces& fc, void* tape_sample, float* scale_slot,
                                    cudaStream_t s) {
+  if (!scaled) {
+    int nmax = 0;
+    for (int f = 0; f < 6; ++f) nmax = max(nmax, 2 * fc.f[f].nu * fc.f[f].nv);
+    dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, 6);
+    k_record_flat<DT><<<grid, FLAT_THREADS, 0, s>>>(FH, FE, g, fc, tape_sample, scale_slot);
+    return cudaGetLastError();
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_record<DT>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e) return e;
+    attr = true;
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(REC_CLUSTER, 6, 1);
-  cfg.blockDim = dim3(REC_THREADS, 1, 1);
+  cfg.gridDim = dim3(FACE_CLUSTER, 6, 1);
+  cfg.blockDim = dim3(FACE_THREADS, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = REC_CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = FACE_CLUSTER;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_record<DT>, FH, FE, g, fc, tape_sample, scale_slot, scaled);
+  return cudaLaunchKernelEx(&cfg, k_record<DT>, FH, FE, g, fc, tape_sample, scale_slot);
 }
 
 cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* FE, Geo g,
@@ -120,60 +166,56 @@ cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* F
 }
 
 // -------------------------------------------------------------- restore ---
-// One thread per recorded value: the interpolated value at this reverse step
-// is sum_m w[m] * decode(sample slot[m]) * scale[slot[m]] (slot -1 = the known
-// zero initial state, or an unused term).  Threads past the faces add the
-// objective seed dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector plane.
+// One thread per recorded value, grid (value blocks, face): the value at this
+// reverse step is sum_m w[m] * decode(sample slot[m]) * scale[slot[m]] (slot
+// -1 = the known zero initial state or an unused term).  blockIdx.y == 6 adds
+// the objective seed dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector plane.
 template <int DT>
-__global__ void k_restore_seed(float* __restrict__ F, float* __restrict__ L, Geo g, Faces fc,
-                               const void* __restrict__ tape, long long stride,
-                               const float* __restrict__ scales, Interp ip, Det det) {
+__global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict__ F,
+                                                               float* __restrict__ L, Geo g,
+                                                               const __grid_constant__ Faces fc,
+                                                               const void* __restrict__ tape,
+                                                               long long stride,
+                                                               const float* __restrict__ scales,
+                                                               const __grid_constant__ Interp ip,
+                                                               Det det) {
   typedef typename Code<DT>::T T;
-  const int total = fc.start[6];
-  const int du = det.u1 - det.u0, dv = det.v1 - det.v0;
-  const int nd = det.kind ? du * dv : 0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total + nd;
-       t += gridDim.x * blockDim.x) {
-    if (t < total) {
-      int f = 0;
-      while (t >= fc.start[f + 1]) ++f;
-      const FaceDesc& fd = fc.f[f];
-      int r = t - fc.start[f];
-      int comp;
-      long long q = face_cell(g, fd, r, &comp);
-      int fld = f & 1;  // 0: Ht on low faces, 1: E on high faces
-      float v = 0.f;
+  const int f = blockIdx.y;
+  const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
+  if (f < 6) {
+    const FaceDesc& fd = fc.f[f];
+    if (r >= 2 * fd.nu * fd.nv) return;
+    const int fld = f & 1;  // 0: Ht on low faces, 1: E on high faces
+    const T* tp = reinterpret_cast<const T*>(tape) + fd.off + r;
+    float val = 0.f;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int s = ip.slot[fld][m];
-        if (s >= 0) {
-          const T* src = reinterpret_cast<const T*>(tape) + (long long)s * stride + fd.off;
-          float x = Code<DT>::dec(src[r]);
-          if (DT >= 2) x = x * scales[s * 6 + f];
-          v += ip.w[fld][m] * x;
-        }
+    for (int m = 0; m < 4; ++m) {
+      const int s = ip.slot[fld][m];
+      if (s >= 0) {
+        float x = Code<DT>::dec(tp[(long long)s * stride]);
+        if (DT >= 2) x = x * scales[s * 6 + f];
+        val += ip.w[fld][m] * x;
       }
-      F[comp * g.nc + q] = v;
+    }
+    int comp;
+    const long long q = face_value_cell(g, fd, r, &comp);
+    F[comp * g.nc + q] = val;
+  } else {
+    if (!det.kind) return;
+    const int du = det.u1 - det.u0, dv = det.v1 - det.v0;
+    if (r >= du * dv) return;
+    const int v = r / du, e = r - v * du;
+    const long long q = cell_on_plane(g, det.axis, det.index, det.u0 + e, det.v0 + v);
+    if (det.kind == 1) {
+      for (int c = 0; c < 3; ++c) L[c * g.nc + q] += 2.0f * F[c * g.nc + q];
     } else {
-      int e = t - total;
-      int v = det.v0 + e / du, u = det.u0 + e % du;
-      int p[3];
-      int ua = det.axis == 0 ? 1 : 0, va = det.axis == 2 ? 1 : 2;
-      p[det.axis] = det.index;
-      p[ua] = u;
-      p[va] = v;
-      long long q = (long long)p[2] * g.plane + (long long)p[1] * g.px + p[0];
-      if (det.kind == 1) {
-        for (int c = 0; c < 3; ++c) L[c * g.nc + q] += 2.0f * F[c * g.nc + q];
-      } else {
-        int b = (det.axis + 1) % 3, c = (det.axis + 2) % 3;
-        float Eb = F[b * g.nc + q], Ec = F[c * g.nc + q];
-        float Hb = F[(3 + b) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
-        L[b * g.nc + q] += Hc;
-        L[c * g.nc + q] -= Hb;
-        L[(3 + c) * g.nc + q] += Eb;
-        L[(3 + b) * g.nc + q] -= Ec;
-      }
+      const int b = (det.axis + 1) % 3, c = (det.axis + 2) % 3;
+      const float Eb = F[b * g.nc + q], Ec = F[c * g.nc + q];
+      const float Hb = F[(3 + b) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
+      L[b * g.nc + q] += Hc;
+      L[c * g.nc + q] -= Hb;
+      L[(3 + c) * g.nc + q] += Eb;
+      L[(3 + b) * g.nc + q] -= Ec;
     }
   }
 }
@@ -181,15 +223,14 @@ __global__ void k_restore_seed(float* __restrict__ F, float* __restrict__ L, Geo
 cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
                                 const void* tape, long long stride, const float* scales,
                                 const Interp& ip, const Det& det, cudaStream_t s) {
-  int n = fc.start[6] + (det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 0);
-  int blocks = (n + 255) / 256;
-  if (blocks > 152 * 4) blocks = 152 * 4;
-  if (blocks < 1) blocks = 1;
+  int nmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 1;
+  for (int f = 0; f < 6; ++f) nmax = max(nmax, 2 * fc.f[f].nu * fc.f[f].nv);
+  dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, 7, 1);
   switch (dtype) {
-    case 0: k_restore_seed<0><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 1: k_restore_seed<1><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 2: k_restore_seed<2><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 3: k_restore_seed<3><<<blocks, 256, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 0: k_restore_seed<0><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 1: k_restore_seed<1><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 2: k_restore_seed<2><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
+    case 3: k_restore_seed<3><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -225,7 +266,7 @@ __global__ void __launch_bounds__(REC_THREADS) k_encode(const float* __restrict_
     float amax = 0.f;
     for (int b = 0; b < nr; ++b) amax = fmaxf(amax, *cluster.map_shared_rank(&cl_amax, b));
     cluster.sync();
-    scale = amax > 0.f ? __fdiv_rn(amax, Code<DT>::fmax) : 1.0f;
+    scale = amax > 0.f ? fmaxf(__fdiv_rn(amax, Code<DT>::fmax), kMinScale) : 1.0f;
   }
   if (rank == 0 && tid == 0) *scale_out = scale;
   T* out = reinterpret_cast<T*>(code);

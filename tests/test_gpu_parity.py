@@ -258,3 +258,35 @@ def test_error_statuses(F, A):
     sim.backward()
     rc = A.lib().fdtd_backward(sim.h, 1.0, C.c_void_p(g.data_ptr()))
     assert rc == A.FDTD_ESTATE
+
+
+@pytest.mark.parametrize("dtype", ["f16", "e4m3"])
+def test_scaled_codec_on_vanishing_faces_stays_finite(F, A, dtype):
+    """A face whose absmax is far below FP32's normal range must not produce a
+    zero scale (0/0 would encode NaN): the scale is at least 2^-126."""
+    import ctypes as C
+    x = np.array([1e-43, -5e-44, 0.0, 3e-45], np.float32)
+    xd = torch.from_numpy(x).cuda()
+    tdt = {"f16": torch.float16, "e4m3": torch.float8_e4m3fn}[dtype]
+    code = torch.empty(x.size, dtype=tdt, device="cuda")
+    scale = torch.zeros(1, dtype=torch.float32, device="cuda")
+    out = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    A.check(A.lib().fdtd_encode(A.TAPE[dtype], 1, C.c_void_p(xd.data_ptr()), x.size,
+                                C.c_void_p(code.data_ptr()), C.c_void_p(scale.data_ptr()), None))
+    A.check(A.lib().fdtd_decode(A.TAPE[dtype], C.c_void_p(code.data_ptr()), x.size,
+                                C.c_void_p(scale.data_ptr()), C.c_void_p(out.data_ptr()), None))
+    assert scale.item() == np.float32(2.0 ** -126)
+    o = out.cpu().numpy()
+    assert np.isfinite(o).all() and np.abs(o).max() <= 1e-37
+
+
+def test_compressed_tape_with_vanishing_boundary_fields(F, A):
+    """Early in a run most boundary faces carry only the tiny leading edge of
+    the field; the scaled FP8 tape must still give a finite gradient that
+    agrees with the oracle's run of the method."""
+    w = I.ragged_box(n_steps=24)
+    rec = A.record_cfg("e4m3", 1, "linear")
+    r = gpu_run(F, A, w, rec=rec)
+    L, g = O.reverse(w, "e4m3", scaled=True, k=1, interp="linear")
+    assert np.isfinite(r["g"]).all()
+    assert cos(r["g"], g) > 0.999
