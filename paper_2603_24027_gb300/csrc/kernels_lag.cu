@@ -404,25 +404,29 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagM
   // plane k0-1: Ht(k0-1) at the own cell; planes k0..k1-1: the step proper;
   // plane p > k0 also finishes lam_H(p-1) with its +z neighbour terms.
   Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0 - 1, k1);
+  // primal data only where the primal runs: interior tiles, planes P..nz-P-1
+  // (and plane P-1's Ht for the z difference of plane P)
+  auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
   auto issue = [&](int p) {
     unsigned char* st = R.at(p);
     uint64_t* bar = R.bar(p);
     const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (body || tail);
     const bool lam = body || tail;
-    uint32_t bytes = (head || body ? 3 * B::P * 4 : 0) + (lam ? 4 * B::P * 4 : 0) +
-                     (body ? 6 * B::OP * 4 : 0) + (body && txs ? 2 * B::XP * 4 : 0) +
-                     (body && tys ? 2 * B::YP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
+    const bool hbox = (head || body) && (primal_plane(p) || primal_plane(p + 1));
+    const bool ebox = body && primal_plane(p);
+    uint32_t bytes = (hbox ? 3 * B::P * 4 : 0) + (lam ? 4 * B::P * 4 : 0) +
+                     (body ? 3 * B::OP * 4 : 0) + (ebox ? 3 * B::OP * 4 : 0) +
+                     (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
+                     (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    if (head || body) tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
+    if (hbox) tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
     if (lam) {
       tma_load_4d(st + Y::CB, &m.cb36, bar, x0, y0, p, 0);
       tma_load_4d(st + Y::LE, &m.L36, bar, x0, y0, p, 0);
     }
-    if (body) {
-      tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
-      tma_load_4d(st + Y::LH, &m.L32, bar, x0, y0, p, 3);
-    }
+    if (ebox) tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
+    if (body) tma_load_4d(st + Y::LH, &m.L32, bar, x0, y0, p, 3);
     if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0, y0, p, 2);
     if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0, p, 6);
     if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 10);
@@ -478,9 +482,11 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagM
         const float* Hb = reinterpret_cast<const float*>(st + Y::H);
         const float cbv = CBb[hb];
         const float lex = LEb[hb], ley = LEb[B::P + hb], lez = LEb[2 * B::P + hb];
-        const float hx = Hb[lb], hy = Hb[B::P + lb], hz = Hb[2 * B::P + lb];
+        const bool hv = primal_plane(k) || primal_plane(k + 1);   // H box staged
+        const float hx = hv ? Hb[lb] : 0.f, hy = hv ? Hb[B::P + lb] : 0.f;
+        const float hz = hv ? Hb[2 * B::P + lb] : 0.f;
         // primal inverse E update on the interior, dL/dcb on the design box
-        if (tint && xyin && k >= g.P && k < g.nz - g.P) {
+        if (primal_plane(k) && xyin) {
           const float d6 = hz - Hb[2 * B::P + lb - B::W], d7 = hy - c_hy;
           const float d8 = hx - c_hx, d9 = hz - Hb[2 * B::P + lb - 1];
           const float d10 = hy - Hb[B::P + lb - 1], d11 = hx - Hb[lb - B::W];
@@ -564,8 +570,9 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagM
         q += g.plane;
       } else if (p < k0) {
         const float* Hb = reinterpret_cast<const float*>(st + Y::H);
-        c_hx = Hb[lb];
-        c_hy = Hb[B::P + lb];
+        const bool hv = primal_plane(p) || primal_plane(p + 1);
+        c_hx = hv ? Hb[lb] : 0.f;
+        c_hy = hv ? Hb[B::P + lb] : 0.f;
       }
     }
     __syncthreads();
@@ -606,21 +613,25 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_h(const __grid_constant__ LagM
   // plane k0-1: lam_H(k0-1) terms for the -z neighbour; planes k0..k1-1: the
   // step proper; plane p > k0 also finishes the primal Ht(p-1) with E(p).
   Ring<S> R = ring_setup<S>(dsm, Y::STAGE, k0 - 1, k1);
+  // primal data only where the primal runs: interior tiles, planes P..nz-P-1
+  // (and plane nz-P's E for the z difference of plane nz-P-1)
+  auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
   auto issue = [&](int p) {
     unsigned char* st = R.at(p);
     uint64_t* bar = R.bar(p);
     const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (head || body);
-    uint32_t bytes = (body || tail ? 3 * B::P * 4 : 0) + (head || body ? 3 * B::P * 4 : 0) +
-                     (body ? 6 * B::OP * 4 : 0) + (body && txs ? 2 * B::XP * 4 : 0) +
-                     (body && tys ? 2 * B::YP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
+    const bool ebox = (body && primal_plane(p)) || (tail && primal_plane(p - 1));
+    const bool hown = body && primal_plane(p);
+    uint32_t bytes = (ebox ? 3 * B::P * 4 : 0) + (head || body ? 3 * B::P * 4 : 0) +
+                     (hown ? 3 * B::OP * 4 : 0) + (body ? 3 * B::OP * 4 : 0) +
+                     (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
+                     (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    if (body || tail) tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
+    if (ebox) tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
     if (head || body) tma_load_4d(st + Y::LH, &m.L36, bar, x0 - 4, y0 - 1, p, 3);
-    if (body) {
-      tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
-      tma_load_4d(st + Y::LE, &m.L32, bar, x0, y0, p, 0);
-    }
+    if (hown) tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
+    if (body) tma_load_4d(st + Y::LE, &m.L32, bar, x0, y0, p, 0);
     if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0 - 4, y0, p, 0);
     if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0 - 1, p, 4);
     if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 8);
@@ -667,7 +678,7 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_h(const __grid_constant__ LagM
       const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
       if (p >= k0 && p < k1) {
         const int k = p;
-        c_pr = tint && xyin && k >= g.P && k < g.nz - g.P;
+        c_pr = primal_plane(k) && xyin;
         if (c_pr) {  // primal Ht(k): x and y derivatives now, z derivatives next plane
           const float ex = Eb[hb], ey = Eb[B::P + hb], ez = Eb[2 * B::P + hb];
           const float* Ho = reinterpret_cast<const float*>(st + Y::H);
