@@ -1,0 +1,40 @@
+"""Reduced precision sweep on the 100 x 100 x 50 waveguide (Fig. 3 analogue):
+one seed, a few tape configurations, checked against the FP64 oracle."""
+import os
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import precision_sweep as PS  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_sweep_waveguide_device():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2603_24027_gb300 import build as B
+    B.build()
+    rows, _ = PS.run_seed(0, 2000, dtypes=["f32", "bf16", "e4m3"], ks=[1, 4, 8, 16],
+                          interps=["linear", "cubic"])
+    by = {(r["dtype"], r["k"], r["interp"]): r for r in rows}
+    base = by[("f32", 1, "linear")]
+    assert base["grad_rel_err"] < 1e-4 and base["L_rel_err"] < 1e-5
+    # compressed tapes: cosine >= 0.999 up to k = 8, every dtype and interpolation
+    for (dt, k, interp), r in by.items():
+        if k <= 8:
+            assert r["cos_fp32_k1"] >= 0.999, (dt, k, interp, r["cos_fp32_k1"])
+    # >= 16x smaller tape at cosine >= 0.999 (FP8 k = 8, BF16 k = 8)
+    assert by[("e4m3", 8, "cubic")]["compression"] > 31.9
+    assert by[("e4m3", 8, "cubic")]["cos_fp32_k1"] > 0.999
+    assert by[("bf16", 8, "linear")]["compression"] == pytest.approx(16.0)
+    # Sec. 3: degradation grows with k for linear interpolation; bf16 ~ fp32
+    lin = [by[("f32", k, "linear")]["cos_fp32_k1"] for k in (4, 8, 16)]
+    assert lin[0] > lin[1] > lin[2]
+    assert abs(by[("bf16", 4, "linear")]["cos_fp32_k1"] - by[("f32", 4, "linear")]["cos_fp32_k1"]) < 1e-5
+    # cubic interpolation beats linear at every k > 1
+    for k in (4, 8, 16):
+        assert by[("f32", k, "cubic")]["grad_rel_err"] < by[("f32", k, "linear")]["grad_rel_err"]
