@@ -57,6 +57,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Largest value of x over all ranks (the slowest rank's time); the
+    process group must be initialised when ws > 1."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, cell_updates: int, steps: int, seconds: float) -> float:
+    """Whole-job Gcell-updates/s: every rank runs its own replica of the
+    workload (weak scaling), timed by the slowest rank."""
+    return ws * cell_updates * steps / seconds / 1e9
+
+
 def workload(rank: int, n_steps=None):
     from paper_2603_24027_gb300 import inputs as I
     w = I.waveguide_mid(seed=rank)
@@ -270,15 +288,11 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - wall0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     launches = sim.last_timing()
     gpu_launches = (launches["fwd_launches"] + launches["bwd_launches"] + 2) * args.steps
     cell_updates = w.n_cells * w.n_steps
-    value = ws * cell_updates * args.steps / (total_ms / 1e3) / 1e9
+    value = job_rate(ws, cell_updates, args.steps, total_ms / 1e3)
 
     # per-kernel live timing (sampled launches, CUDA events on the library stream)
     algo = algorithmic_bytes(w)
@@ -365,13 +379,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
         te.append(time.perf_counter() - t0)
-    e2e_t = sum(te)
-    if ws > 1:
-        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(sum(te), ws, dev)
     nd = int(np.prod(w.design_shape))
-    out["e2e"] = {"value": ws * cell_updates * args.steps / e2e_t / 1e9, "unit": UNIT,
+    out["e2e"] = {"value": job_rate(ws, cell_updates, args.steps, e2e_t), "unit": UNIT,
                   "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -96,15 +96,27 @@ typedef struct {
   int hi[2];
 } fdtd_detector;
 
-enum { FDTD_TAPE_F32 = 0, FDTD_TAPE_BF16 = 1, FDTD_TAPE_F16 = 2, FDTD_TAPE_E4M3 = 3 };
+/* Tape element types.  E4M3 is the OCP / hardware float8 e4m3fn (max 448).
+ * 4..8 are the 8-bit formats compared in Sec. 4 (Fig. 3), coded in software
+ * (exponent bits, mantissa bits, bias, largest finite value):
+ *   E4M3B11FNUZ 4,3,11, 30      E5M2FNUZ 5,2,16, 57344     E4M3FNUZ 4,3,8, 240
+ *   E4M3_IEEE   4,3,7,  240     E3M4     3,4,3,  15.5
+ * "fnuz": no infinities, no negative zero, NaN = 0x80; the IEEE-like ones
+ * reserve the all-ones exponent for infinities and NaNs.  All encodings round
+ * to nearest, ties to even, and saturate to the largest finite value. */
+enum {
+  FDTD_TAPE_F32 = 0, FDTD_TAPE_BF16 = 1, FDTD_TAPE_F16 = 2, FDTD_TAPE_E4M3 = 3,
+  FDTD_TAPE_E4M3B11FNUZ = 4, FDTD_TAPE_E5M2FNUZ = 5, FDTD_TAPE_E4M3FNUZ = 6,
+  FDTD_TAPE_E4M3_IEEE = 7, FDTD_TAPE_E3M4 = 8
+};
 enum { FDTD_INTERP_LINEAR = 0, FDTD_INTERP_CUBIC = 1 };
 
 /* Boundary-tape compression (Sec. 2): storage type of the recorded slices,
  * k = keep every k-th step (the last step is always kept), and the time
  * interpolation used to restore the steps in between.  scaled = 1 stores a
  * per-face, per-sample FP32 scale max(absmax/format_max, 2^-126) (1 when the
- * face is all zero; F16 and E4M3 only); values are converted back to FP32
- * before any arithmetic. */
+ * face is all zero; F16 and the 8-bit types only); values are converted back
+ * to FP32 before any arithmetic. */
 typedef struct {
   int dtype;
   int k;
@@ -170,14 +182,18 @@ enum {
   FDTD_OPT_USE_GRAPHS = 0,    /* 1 (default): replay the time loop as a CUDA graph */
   FDTD_OPT_KERNEL = 1,        /* 0: split half-steps (plain loads), 1: fused 2.5D forward
                                  (plain loads), 2: fused forward with TMA staging, 3: split
-                                 half-steps with TMA staging, 4 (default): TMA half-steps that
-                                 read one plane per iteration; 2 and 3 use the TMA reverse of
-                                 3, 0 and 1 the plain reverse */
-  FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4 default, 8, 16); width 32 */
+                                 half-steps with TMA staging, 4: TMA half-steps that read one
+                                 plane per iteration, 5 (default): the kernels of 4 with two
+                                 x-cells per thread (tile height at least 2); 2 and 3 use the
+                                 TMA reverse of 3, 0 and 1 the plain reverse */
+  FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8 default, 16); width 32 */
   FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
   FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: time every m-th launch of each kernel kind with
                                  CUDA events on the library's stream (0 = off) */
-  FDTD_OPT_ROWS_PER_THREAD = 5 /* TMA half-step kernels: tile rows per thread (1 default, 2) */
+  FDTD_OPT_ROWS_PER_THREAD = 5, /* TMA half-step kernels: tile rows per thread (1 default, 2) */
+  FDTD_OPT_STAGES = 6           /* one-plane kernels (4, 5): planes staged per CTA (2
+                                   default, 3, 4): stages - 1 planes are in flight while one
+                                   is computed */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -572,6 +572,18 @@ int oracle_gradient(const ocfg* c, const double* eps, double seed, double* grad,
  *   2 float16 : 10 mantissa bits, emin -14, max 65504
  *   3 float8 e4m3fn: 3 mantissa bits, emin -6, max 448
  *   0 float32 : 23 mantissa bits, emin -126 (the FP32 tape)
+ * The 8-bit formats the paper compares in Sec. 4 (Fig. 3); for an exponent
+ * field of E bits with bias B the smallest normal exponent is 1 - B.  "fnuz"
+ * formats have no infinities and one NaN code (0x80), so every other code,
+ * the all-ones exponent included, is finite; the IEEE-like formats reserve
+ * the all-ones exponent for infinities and NaNs:
+ *   4 float8 e4m3b11fnuz: 3 mantissa bits, bias 11, emin -10, max 1.875 * 2^4 = 30
+ *   5 float8 e5m2fnuz   : 2 mantissa bits, bias 16, emin -15, max 1.75 * 2^15 = 57344
+ *   6 float8 e4m3fnuz   : 3 mantissa bits, bias 8,  emin -7,  max 1.875 * 2^7 = 240
+ *   7 float8 e4m3 (IEEE): 3 mantissa bits, bias 7,  emin -6,  max 1.875 * 2^7 = 240
+ *   8 float8 e3m4 (IEEE): 4 mantissa bits, bias 3,  emin -2,  max 1.9375 * 2^3 = 15.5
+ * Saturation of out-of-range values is this implementation's reading (the
+ * paper does not say how values beyond the range are converted).
  */
 static double quant_generic(double x, int mbits, int emin, double fmax) {
   if (x == 0.0 || isnan(x)) return x;
@@ -592,6 +604,11 @@ double oracle_format_max(int fmt) {
     case 1: return ldexp(2.0 - ldexp(1.0, -7), 127);
     case 2: return 65504.0;
     case 3: return 448.0;
+    case 4: return 30.0;
+    case 5: return 57344.0;
+    case 6: return 240.0;
+    case 7: return 240.0;
+    case 8: return 15.5;
   }
   return 0.0;
 }
@@ -602,6 +619,11 @@ double oracle_quantize(int fmt, double x) {
     case 1: return quant_generic(x, 7, -126, oracle_format_max(1));
     case 2: return quant_generic(x, 10, -14, 65504.0);
     case 3: return quant_generic(x, 3, -6, 448.0);
+    case 4: return quant_generic(x, 3, -10, 30.0);
+    case 5: return quant_generic(x, 2, -15, 57344.0);
+    case 6: return quant_generic(x, 3, -7, 240.0);
+    case 7: return quant_generic(x, 3, -6, 240.0);
+    case 8: return quant_generic(x, 4, -2, 15.5);
   }
   return x;
 }

@@ -16,7 +16,11 @@ from . import build as _build
 
 C0 = 299792458.0
 NF = 18
-FMT = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "none": -1}
+# Tape formats.  "e4m3" is the OCP / hardware float8 e4m3fn (max 448); the
+# other 8-bit formats are the ones compared in Sec. 4 (Fig. 3); "e4m3ieee" is
+# the IEEE-style float8 e4m3 with infinities (max 240).
+FMT = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4, "e5m2fnuz": 5,
+       "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8, "none": -1}
 
 
 class OCfg(C.Structure):

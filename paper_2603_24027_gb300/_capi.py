@@ -16,9 +16,12 @@ FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ESTATE, FDTD_ETIMEOUT, FDTD_
     0, -1, -2, -3, -4, -5, -6)
 STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_ENOMEM", -3: "FDTD_ECUDA",
                 -4: "FDTD_ESTATE", -5: "FDTD_ETIMEOUT", -6: "FDTD_ENONFINITE"}
-TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3}
+# Tape element types: "e4m3" (alias "e4m3fn") is the hardware OCP float8; the
+# other 8-bit names are the formats of Sec. 4, "e4m3ieee" the IEEE-style e4m3.
+TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4, "e5m2fnuz": 5,
+        "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8}
 INTERP = {"linear": 0, "cubic": 1}
-OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS = 0, 1, 2, 3, 4, 5
+OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS, OPT_STAGES = range(7)
 K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV = range(8)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "fused_fwd",
                 "fused_rev"]
@@ -119,7 +122,8 @@ def check(status: int, handle=None) -> None:
 
 
 def record_cfg(dtype: str = "f32", k: int = 1, interp: str = "linear", scaled=None) -> RecordCfg:
-    """Tape configuration; scaled defaults to per-face scales for f16 / e4m3."""
+    """Tape configuration; scaled defaults to per-face scales for f16 and the
+    hardware e4m3 (the paper's 8-bit formats default to unscaled, as in Sec. 4)."""
     if scaled is None:
-        scaled = dtype in ("f16", "e4m3")
+        scaled = dtype in ("f16", "e4m3", "e4m3fn")
     return RecordCfg(TAPE[dtype], int(k), INTERP[interp], int(bool(scaled)))

@@ -32,7 +32,7 @@ struct Layout {
 };
 
 struct GraphKey {
-  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows;
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -62,7 +62,7 @@ struct fdtd_handle {
   int fwd_buf;                // field buffer holding the state after forward
   fdtd_record_cfg fwd_rec;
 
-  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows;
+  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -380,7 +380,7 @@ static Geo geo_of(const fdtd_handle* h) {
 
 static int check_rec(fdtd_handle* h, const fdtd_record_cfg* rec) {
   if (!rec) return fail(h, FDTD_EINVAL, "record config is NULL");
-  if (rec->dtype < 0 || rec->dtype > 3) return fail(h, FDTD_EINVAL, "unknown tape dtype");
+  if (rec->dtype < 0 || rec->dtype >= kTapeDtypes) return fail(h, FDTD_EINVAL, "unknown tape dtype");
   if (rec->k < 1) return fail(h, FDTD_EINVAL, "k must be >= 1");
   if (rec->interp != FDTD_INTERP_LINEAR && rec->interp != FDTD_INTERP_CUBIC)
     return fail(h, FDTD_EINVAL, "unknown interpolation");
@@ -471,11 +471,12 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->have_forward = false;
   h->fwd_buf = 0;
   h->opt_graphs = 1;
-  h->opt_kernel = 4;
-  h->opt_tile_y = 4;
+  h->opt_kernel = 5;
+  h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_sample = 0;
   h->opt_rows = 1;
+  h->opt_stages = 2;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -521,13 +522,14 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
 extern "C" int fdtd_workspace_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec,
                                     size_t* bytes) {
   if (!h || !bytes) return FDTD_EINVAL;
-  if (rec && (rec->k < 1 || rec->dtype < 0 || rec->dtype > 3)) return FDTD_EINVAL;
+  if (rec && (rec->k < 1 || rec->dtype < 0 || rec->dtype >= kTapeDtypes)) return FDTD_EINVAL;
   *bytes = layout_of(h, rec).total;
   return FDTD_OK;
 }
 
 extern "C" int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes) {
-  if (!h || !bytes || !rec || rec->k < 1 || rec->dtype < 0 || rec->dtype > 3) return FDTD_EINVAL;
+  if (!h || !bytes || !rec || rec->k < 1 || rec->dtype < 0 || rec->dtype >= kTapeDtypes)
+    return FDTD_EINVAL;
   size_t J = n_samples(h->N, rec->k);
   size_t b = J * (size_t)sample_elems(h) * code_bytes(rec->dtype);
   if (rec->scaled) b += J * 6 * sizeof(float);
@@ -553,7 +555,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
   switch (option) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
-      if (value < 0 || value > 4) return fail(h, FDTD_EINVAL, "kernel must be 0..4");
+      if (value < 0 || value > 5) return fail(h, FDTD_EINVAL, "kernel must be 0..5");
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
@@ -573,6 +575,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value != 1 && value != 2) return fail(h, FDTD_EINVAL, "rows per thread must be 1 or 2");
       h->opt_rows = value;
       break;
+    case FDTD_OPT_STAGES:
+      if (value < 2 || value > 4) return fail(h, FDTD_EINVAL, "stages must be 2, 3 or 4");
+      h->opt_stages = value;
+      break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -587,6 +593,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_ZCHUNK: *value = h->opt_zchunk; break;
     case FDTD_OPT_SAMPLE_EVERY: *value = h->opt_sample; break;
     case FDTD_OPT_ROWS_PER_THREAD: *value = h->opt_rows; break;
+    case FDTD_OPT_STAGES: *value = h->opt_stages; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -654,6 +661,12 @@ static int finish(fdtd_handle* h) {
   return FDTD_OK;
 }
 
+// Tile height the half-step kernels run with: the two-cells-per-thread
+// kernels cover two tile rows per warp, so their tiles are at least 2 high.
+static int lag_tile_y(const fdtd_handle* h) {
+  return (h->opt_kernel == 5 && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
+}
+
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   StepArgs a;
   memset(&a, 0, sizeof a);
@@ -673,8 +686,9 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.det.index = h->det.index;
   a.det.u0 = h->det.lo[0]; a.det.u1 = h->det.hi[0];
   a.det.v0 = h->det.lo[1]; a.det.v1 = h->det.hi[1];
-  a.tile_y = h->opt_tile_y;
+  a.tile_y = lag_tile_y(h);
   a.rows = h->opt_rows;
+  a.stages = h->opt_stages;
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
   a.err = (unsigned*)(h->ws + L.err);
   return a;
@@ -744,7 +758,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   const bool fused = h->opt_kernel == 1 || h->opt_kernel == 2;
   const bool tma = h->opt_kernel == 2;
   const bool split_tma = h->opt_kernel == 3;
-  const bool lagk = h->opt_kernel == 4;
+  const bool lagk = h->opt_kernel == 4 || h->opt_kernel == 5;
+  const bool pair = h->opt_kernel == 5;
   SplitMaps smaps;
   if (split_tma &&
       (e = encode_split_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
@@ -755,7 +770,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (lagk &&
       (e = encode_lag_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
                            (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
-                           h->opt_tile_y, &lmaps)))
+                           a.tile_y, &lmaps)))
     return e;
   if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
     for (int b = 0; b < 2; ++b)
@@ -805,7 +820,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
-    if ((e = lagk ? launch_lag(0, lmaps, a, h->stream)
+    if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream) : launch_lag(0, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
@@ -821,7 +836,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
     }
     if ((e = mark(h, FDTD_K_FWD_E, 0, sm))) return e;
-    if ((e = lagk ? launch_lag(1, lmaps, a, h->stream)
+    if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream) : launch_lag(1, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
@@ -848,7 +863,8 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
   int cur = 0;
-  const bool rlag = h->opt_kernel == 4;
+  const bool rlag = h->opt_kernel == 4 || h->opt_kernel == 5;
+  const bool rpair = h->opt_kernel == 5;
   const bool rtma = h->opt_kernel == 2 || h->opt_kernel == 3;
   SplitMaps rmaps[2];
   LagMaps lrmaps[2];
@@ -858,7 +874,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                        &rmaps[b])))
       return e;
     if (rlag && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
-                                     (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
+                                     (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y,
                                      &lrmaps[b])))
       return e;
   }
@@ -877,12 +893,14 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = mark(h, FDTD_K_REV_E, 0, sm))) return e;
-    if ((e = rlag ? launch_lag(2, lrmaps[cur], a, h->stream)
+    if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
+                         : launch_lag(2, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_REV_E, 1, sm))) return e;
     if ((e = mark(h, FDTD_K_REV_H, 0, sm))) return e;
-    if ((e = rlag ? launch_lag(3, lrmaps[cur], a, h->stream)
+    if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
+                         : launch_lag(3, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
       return e;
     if ((e = mark(h, FDTD_K_REV_H, 1, sm))) return e;
@@ -914,6 +932,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.zchunk = h->opt_zchunk;
   key.sample = h->opt_sample;
   key.rows = h->opt_rows;
+  key.stages = h->opt_stages;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1123,7 +1142,7 @@ extern "C" int fdtd_objective_history(fdtd_handle* h, double* out) {
 
 extern "C" int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code,
                            float* d_scale, void* cuda_stream) {
-  if (dtype < 0 || dtype > 3 || !d_in || !d_code || !d_scale) return FDTD_EINVAL;
+  if (dtype < 0 || dtype >= kTapeDtypes || !d_in || !d_code || !d_scale) return FDTD_EINVAL;
   if (scaled && dtype < 2) return FDTD_EINVAL;
   cudaError_t e = launch_encode(dtype, scaled, d_in, n, d_code, d_scale, (cudaStream_t)cuda_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
@@ -1132,7 +1151,7 @@ extern "C" int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, v
 
 extern "C" int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale,
                            float* d_out, void* cuda_stream) {
-  if (dtype < 0 || dtype > 3 || !d_code || !d_scale || !d_out) return FDTD_EINVAL;
+  if (dtype < 0 || dtype >= kTapeDtypes || !d_code || !d_scale || !d_out) return FDTD_EINVAL;
   cudaError_t e = launch_decode(dtype, d_code, n, d_scale, d_out, (cudaStream_t)cuda_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;

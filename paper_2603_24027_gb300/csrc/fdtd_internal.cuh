@@ -94,8 +94,9 @@ __device__ __forceinline__ bool on_plane(int axis, int index, int u0, int u1, in
 }
 
 // ---------------------------------------------------------------- codec ----
-// Tape element types: 0 f32, 1 bf16, 2 f16, 3 e4m3 (OCP e4m3fn).  Encoding is
-// round-to-nearest-even with saturation to the largest finite value.
+// Tape element types: 0 f32, 1 bf16, 2 f16, 3 e4m3 (OCP e4m3fn), 4..8 the
+// software-coded 8-bit formats below.  Encoding is round-to-nearest-even with
+// saturation to the largest finite value.
 template <int DT> struct Code;
 template <> struct Code<0> {
   typedef float T;
@@ -125,7 +126,60 @@ template <> struct Code<3> {
   }
 };
 
-inline int code_bytes(int dt) { return dt == 0 ? 4 : (dt == 3 ? 1 : 2); }
+// Software codec of the 8-bit formats compared in Sec. 4 (Fig. 3) that have
+// no hardware conversion: M stored mantissa bits, exponent bias BIAS, IEEE =
+// the all-ones exponent encodes infinities / NaNs (else "fnuz": one NaN code
+// 0x80, every other code finite, no negative zero).  Encoding saturates to
+// FMAX and rounds to nearest, ties to even: below the smallest normal 2^(1-B)
+// the value is an integer multiple of 2^(1-B-M) (exact power-of-two scaling,
+// then a round-to-nearest-even integer conversion); above it the FP32 bit
+// pattern (exponent and mantissa as one integer) is rounded at bit 23-M, a
+// mantissa carry moving into the exponent, and re-biased.
+__device__ __forceinline__ float pow2f(int e) {   // 2^e for normal-range e
+  return __uint_as_float((uint32_t)(127 + e) << 23);
+}
+template <int M, int BIAS, bool IEEE>
+__device__ __forceinline__ uint8_t soft8_enc(float x, float fmax) {
+  const uint32_t sgn = (__float_as_uint(x) >> 24) & 0x80u;
+  const float a = fminf(fabsf(x), fmax);
+  uint32_t code;
+  if (a < pow2f(1 - BIAS)) {
+    code = __float2uint_rn(a * pow2f(BIAS + M - 1));
+  } else {
+    uint32_t u = __float_as_uint(a);
+    constexpr int sh = 23 - M;
+    u += (1u << (sh - 1)) - 1u + ((u >> sh) & 1u);
+    code = (u >> sh) - ((uint32_t)(127 - BIAS) << M);
+  }
+  if (code == 0 && !IEEE) return 0;   // unsigned zero
+  return (uint8_t)(code | sgn);
+}
+template <int E, int M, int BIAS, bool IEEE>
+__device__ __forceinline__ float soft8_dec(uint8_t c) {
+  const uint32_t mag = c & 0x7fu;
+  const uint32_t ef = mag >> M, mf = mag & ((1u << M) - 1u);
+  float v;
+  if (ef == 0) v = (float)mf * pow2f(1 - BIAS - M);
+  else v = __uint_as_float(((ef + 127u - BIAS) << 23) | (mf << (23 - M)));
+  if (IEEE && ef == (1u << E) - 1u) v = mf ? __uint_as_float(0x7fc00000u) : __uint_as_float(0x7f800000u);
+  if (!IEEE && c == 0x80u) return __uint_as_float(0x7fc00000u);
+  return (c & 0x80u) ? -v : v;
+}
+template <int E, int M, int BIAS, bool IEEE, int FMAX_NUM, int FMAX_DEN>
+struct Soft8 {
+  typedef uint8_t T;
+  static constexpr float fmax = (float)FMAX_NUM / (float)FMAX_DEN;
+  __device__ static T enc(float x) { return soft8_enc<M, BIAS, IEEE>(x, fmax); }
+  __device__ static float dec(T c) { return soft8_dec<E, M, BIAS, IEEE>(c); }
+};
+template <> struct Code<4> : Soft8<4, 3, 11, false, 30, 1> {};     // e4m3b11fnuz, max 30
+template <> struct Code<5> : Soft8<5, 2, 16, false, 57344, 1> {};  // e5m2fnuz, max 57344
+template <> struct Code<6> : Soft8<4, 3, 8, false, 240, 1> {};     // e4m3fnuz, max 240
+template <> struct Code<7> : Soft8<4, 3, 7, true, 240, 1> {};      // e4m3 (IEEE-like), max 240
+template <> struct Code<8> : Soft8<3, 4, 3, true, 31, 2> {};       // e3m4 (IEEE-like), max 15.5
+
+constexpr int kTapeDtypes = 9;
+inline int code_bytes(int dt) { return dt == 0 ? 4 : (dt <= 2 ? 2 : 1); }
 
 // ------------------------------------------------------------ launchers ----
 // Implemented in kernels_step.cu / kernels_tape.cu; return cudaGetLastError().
@@ -145,6 +199,7 @@ struct StepArgs {
   int zchunk;
   int tile_y;
   int rows;        // tile rows per thread (TMA half-step kernels)
+  int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   unsigned* err;   // device error word (ERR_*)
 };
 
@@ -183,6 +238,8 @@ struct alignas(64) LagMaps {
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
                             const Geo& g, int ty, LagMaps* m);
 cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
+// The same half-steps with two x-cells per thread (tile height >= 2).
+cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
                            cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,

@@ -13,106 +13,11 @@
 // including the association of every sum, so results are bit-identical.
 #include <cudaTypedefs.h>
 
-#include "fdtd_internal.cuh"
-#include "tma.cuh"
+#include "lag_common.cuh"
 
 namespace fdtd {
 
-namespace lag {
-
-constexpr int r128(int b) { return (b + 127) / 128 * 128; }
-
-__device__ __forceinline__ float cpml_s(float d, float psi_old, float* pout, long long pi, float b,
-                                        float a, float kv) {
-  float s = __fmaf_rn(b, psi_old, __fmul_rn(a, d));
-  pout[pi] = s;
-  return __fmaf_rn(kv, d, s);
-}
-
-__device__ __forceinline__ float adj_s(float v, float lpsi, float* pout, long long pi, bool own,
-                                       float b, float a, float kv) {
-  float mu = lpsi + v;
-  if (own) pout[pi] = b * mu;
-  return kv * v + a * mu;
-}
-
-__device__ __forceinline__ float src_wt(const Src& s, int i, int j, int k) {
-  int u, v;
-  if (s.kind == 0 || !on_plane(s.axis, s.index, s.u0, s.u1, s.v0, s.v1, i, j, k, &u, &v))
-    return 0.f;
-  return __ldg(s.w + (long long)(v - s.v0) * (s.u1 - s.u0) + (u - s.u0));
-}
-
-__device__ __forceinline__ bool tile_in_slab(int lo, int hi_incl, int n, int P) {
-  return lo < P || hi_incl >= n - P;
-}
-
-// Ring over planes p0..p1 (see kernels_split_tma.cu): plane p in stage
-// (p - p0) % S, barrier parity ((p - p0) / S) & 1.  Here every plane is read
-// in exactly one iteration, after which its stage is re-armed for p + S.
-template <int S>
-struct Ring {
-  unsigned char* base;
-  uint64_t* bars;
-  int stage_bytes, p0, p1;
-  __device__ unsigned char* at(int p) const { return base + ((p - p0) % S) * stage_bytes; }
-  __device__ uint64_t* bar(int p) const { return &bars[(p - p0) % S]; }
-  __device__ bool wait(int p) const {
-    return mbar_wait(bar(p), ((p - p0) / S) & 1, kWaitCycles);
-  }
-};
-
-template <int S>
-__device__ __forceinline__ Ring<S> ring_setup(unsigned char* dsm, int stage_bytes, int p0, int p1) {
-  Ring<S> r;
-  r.base = dsm;
-  r.bars = reinterpret_cast<uint64_t*>(dsm + S * stage_bytes);
-  r.stage_bytes = stage_bytes;
-  r.p0 = p0;
-  r.p1 = p1;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&r.bars[s], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  return r;
-}
-
-template <int S>
-__device__ void ring_drain(const Ring<S>& r, int p_waited, unsigned* err) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    atomicOr(err, ERR_TIMEOUT);
-    for (int p = p_waited; p <= r.p1 && p < p_waited + S; ++p) r.wait(p);
-  }
-}
-
-// Box geometry: "lo" boxes start at (x0-4, y0-1) and cover own, -x, -y;
-// "hi" boxes start at (x0, y0) and cover own, +x, +y.  Both are 36 x (TY+1).
-template <int TY>
-struct G {
-  static constexpr int W = 36, R = TY + 1, P = W * R;   // 36-wide box plane
-  static constexpr int OP = 32 * TY;                     // own box plane
-  static constexpr int XP = 36 * TY;                     // 36 x TY psi box (x neighbour)
-  static constexpr int YP = 32 * (TY + 1);               // 32 x (TY+1) psi box (y neighbour)
-};
-
-}  // namespace lag
-
-using namespace lag;
-
 // =================================================== forward H half-step ===
-template <int TY, int S>
-struct LFH {
-  typedef G<TY> g_;
-  static constexpr int E = 0;                                  // E hi box, 3 comps
-  static constexpr int H = r128(3 * g_::P * 4);                // H own
-  static constexpr int PX = H + r128(3 * g_::OP * 4);          // psi_H own x/y/z, 2 comps
-  static constexpr int PY = PX + r128(2 * g_::OP * 4);
-  static constexpr int PZ = PY + r128(2 * g_::OP * 4);
-  static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 8 * S; }
-};
-
 template <int TY, int S>
 __global__ void __launch_bounds__(32 * TY) k_lfwd_h(const __grid_constant__ LagMaps m,
                                                    StepArgs a) {
@@ -213,18 +118,6 @@ __global__ void __launch_bounds__(32 * TY) k_lfwd_h(const __grid_constant__ LagM
 }
 
 // =================================================== forward E half-step ===
-template <int TY, int S>
-struct LFE {
-  typedef G<TY> g_;
-  static constexpr int H = 0;                                  // Ht lo box
-  static constexpr int E = r128(3 * g_::P * 4);                // E own
-  static constexpr int CB = E + r128(3 * g_::OP * 4);          // cb own
-  static constexpr int PX = CB + r128(g_::OP * 4);             // psi_E own x/y/z
-  static constexpr int PY = PX + r128(2 * g_::OP * 4);
-  static constexpr int PZ = PY + r128(2 * g_::OP * 4);
-  static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 8 * S + 256; }
-};
 
 template <int TY, int S>
 __global__ void __launch_bounds__(32 * TY) k_lfwd_e(const __grid_constant__ LagMaps m,
@@ -371,20 +264,6 @@ __global__ void __launch_bounds__(32 * TY) k_lfwd_e(const __grid_constant__ LagM
 }
 
 // ======================================== reverse E phase (+ adjoint H) ===
-template <int TY, int S>
-struct LRE {
-  typedef G<TY> g_;
-  static constexpr int H = 0;                                  // Ht lo box
-  static constexpr int E = r128(3 * g_::P * 4);                // E own
-  static constexpr int CB = E + r128(3 * g_::OP * 4);          // cb hi box
-  static constexpr int LE = CB + r128(g_::P * 4);              // lam_E hi box
-  static constexpr int LH = LE + r128(3 * g_::P * 4);          // lam_H own
-  static constexpr int PX = LH + r128(3 * g_::OP * 4);         // lam_psi_E x: 36 x TY at (x0, y0)
-  static constexpr int PY = PX + r128(2 * g_::XP * 4);         // lam_psi_E y: 32 x (TY+1) at (x0, y0)
-  static constexpr int PZ = PY + r128(2 * g_::YP * 4);         // lam_psi_E z: own
-  static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 8 * S; }
-};
 
 template <int TY, int S>
 __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagMaps m,
@@ -581,19 +460,6 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagM
 }
 
 // ======================================== reverse H phase (+ adjoint E) ===
-template <int TY, int S>
-struct LRH {
-  typedef G<TY> g_;
-  static constexpr int E = 0;                                  // E hi box
-  static constexpr int H = r128(3 * g_::P * 4);                // Ht own
-  static constexpr int LH = H + r128(3 * g_::OP * 4);          // lam_H lo box
-  static constexpr int LE = LH + r128(3 * g_::P * 4);          // lam_E own
-  static constexpr int PX = LE + r128(3 * g_::OP * 4);         // lam_psi_H x: 36 x TY at (x0-4, y0)
-  static constexpr int PY = PX + r128(2 * g_::XP * 4);         // lam_psi_H y: 32 x (TY+1) at (x0, y0-1)
-  static constexpr int PZ = PY + r128(2 * g_::YP * 4);         // lam_psi_H z: own
-  static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 8 * S; }
-};
 
 template <int TY, int S>
 __global__ void __launch_bounds__(32 * TY) k_lrev_h(const __grid_constant__ LagMaps m,
@@ -797,12 +663,18 @@ static cudaError_t launch_lag_t(int which, const LagMaps& m, const StepArgs& a, 
 }
 
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
+// Stage counts 2 and 4 are built for tile heights 2, 4 and 8; the other
+// heights run with 3.
 cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
+  const int S = a.stages;
   switch (a.tile_y) {
     case 1: return launch_lag_t<1, 3>(which, m, a, s);
-    case 2: return launch_lag_t<2, 3>(which, m, a, s);
-    case 4: return launch_lag_t<4, 3>(which, m, a, s);
-    case 8: return launch_lag_t<8, 3>(which, m, a, s);
+    case 2: return S == 2 ? launch_lag_t<2, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag_t<2, 4>(which, m, a, s) : launch_lag_t<2, 3>(which, m, a, s);
+    case 4: return S == 2 ? launch_lag_t<4, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag_t<4, 4>(which, m, a, s) : launch_lag_t<4, 3>(which, m, a, s);
+    case 8: return S == 2 ? launch_lag_t<8, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag_t<8, 4>(which, m, a, s) : launch_lag_t<8, 3>(which, m, a, s);
     case 16: return launch_lag_t<16, 3>(which, m, a, s);
   }
   return cudaErrorInvalidValue;

@@ -18,11 +18,30 @@
 // formats use one thread per value.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "fdtd_internal.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace fdtd {
+
+// Call fn(std::integral_constant<int, DT>) for the tape element type dtype.
+template <class Fn>
+static cudaError_t with_dtype(int dtype, Fn&& fn) {
+  switch (dtype) {
+    case 0: return fn(std::integral_constant<int, 0>{});
+    case 1: return fn(std::integral_constant<int, 1>{});
+    case 2: return fn(std::integral_constant<int, 2>{});
+    case 3: return fn(std::integral_constant<int, 3>{});
+    case 4: return fn(std::integral_constant<int, 4>{});
+    case 5: return fn(std::integral_constant<int, 5>{});
+    case 6: return fn(std::integral_constant<int, 6>{});
+    case 7: return fn(std::integral_constant<int, 7>{});
+    case 8: return fn(std::integral_constant<int, 8>{});
+  }
+  return cudaErrorInvalidValue;
+}
 
 // Smallest per-face scale: the smallest normal FP32 number, so that
 // amax / format_max never underflows to zero (0/0 would encode NaN).
@@ -156,13 +175,11 @@ static cudaError_t launch_record_t(int scaled, const float* FH, const float* FE,
 
 cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* FE, Geo g,
                           const Faces& fc, void* tape_sample, float* scale_slot, cudaStream_t s) {
-  switch (dtype) {
-    case 0: return launch_record_t<0>(0, FH, FE, g, fc, tape_sample, scale_slot, s);
-    case 1: return launch_record_t<1>(0, FH, FE, g, fc, tape_sample, scale_slot, s);
-    case 2: return launch_record_t<2>(scaled, FH, FE, g, fc, tape_sample, scale_slot, s);
-    case 3: return launch_record_t<3>(scaled, FH, FE, g, fc, tape_sample, scale_slot, s);
-  }
-  return cudaErrorInvalidValue;
+  // FP32 and BF16 are never scaled
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    return launch_record_t<DT>(DT >= 2 ? scaled : 0, FH, FE, g, fc, tape_sample, scale_slot, s);
+  });
 }
 
 // -------------------------------------------------------------- restore ---
@@ -226,14 +243,11 @@ cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Face
   int nmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 1;
   for (int f = 0; f < 6; ++f) nmax = max(nmax, 2 * fc.f[f].nu * fc.f[f].nv);
   dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, 7, 1);
-  switch (dtype) {
-    case 0: k_restore_seed<0><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 1: k_restore_seed<1><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 2: k_restore_seed<2><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    case 3: k_restore_seed<3><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    k_restore_seed<DT><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det);
+    return cudaGetLastError();
+  });
 }
 
 // -------------------------------------------------------- raw codec ------
@@ -303,13 +317,10 @@ static cudaError_t launch_encode_t(int scaled, const float* in, size_t n, void* 
 
 cudaError_t launch_encode(int dtype, int scaled, const float* in, size_t n, void* code,
                           float* scale, cudaStream_t s) {
-  switch (dtype) {
-    case 0: return launch_encode_t<0>(0, in, n, code, scale, s);
-    case 1: return launch_encode_t<1>(0, in, n, code, scale, s);
-    case 2: return launch_encode_t<2>(scaled, in, n, code, scale, s);
-    case 3: return launch_encode_t<3>(scaled, in, n, code, scale, s);
-  }
-  return cudaErrorInvalidValue;
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    return launch_encode_t<DT>(DT >= 2 ? scaled : 0, in, n, code, scale, s);
+  });
 }
 
 cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* scale, float* out,
@@ -317,14 +328,11 @@ cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* sc
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  switch (dtype) {
-    case 0: k_decode<0><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
-    case 1: k_decode<1><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
-    case 2: k_decode<2><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
-    case 3: k_decode<3><<<blocks, 256, 0, s>>>(code, n, scale, out); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    k_decode<DT><<<blocks, 256, 0, s>>>(code, n, scale, out);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace fdtd

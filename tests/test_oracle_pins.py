@@ -344,6 +344,90 @@ def test_quantizer_fp32_and_saturation():
     assert O.quantize("f16", [1e9])[0] == 65504.0
 
 
+# The 8-bit formats of Sec. 4 (Fig. 3), defined by their bit layout: E
+# exponent bits, M mantissa bits, exponent bias, and whether the all-ones
+# exponent is reserved (IEEE-like: infinities and NaNs) or finite ("fnuz": one
+# NaN code 0x80, no negative zero, no infinities).
+FP8_LAYOUT = {"e4m3b11fnuz": (4, 3, 11, "fnuz"), "e5m2fnuz": (5, 2, 16, "fnuz"),
+              "e4m3fnuz": (4, 3, 8, "fnuz"), "e4m3ieee": (4, 3, 7, "ieee"),
+              "e3m4": (3, 4, 3, "ieee")}
+
+
+def fp8_codes(layout):
+    """All finite non-negative values with their codes, by brute force over
+    the 128 non-negative bit patterns."""
+    E, M, bias, kind = layout
+    out = []
+    for code in range(128):
+        ef, mf = code >> M, code & ((1 << M) - 1)
+        if kind == "ieee" and ef == (1 << E) - 1:
+            continue                       # infinities and NaNs
+        if ef == 0:
+            v = mf * 2.0 ** (1 - bias - M)
+        else:
+            v = (1 + mf / 2.0 ** M) * 2.0 ** (ef - bias)
+        out.append((v, code))
+    return sorted(out)
+
+
+def fp8_round_brute(layout, x):
+    """Nearest representable value, ties to the even code, saturating at the
+    largest finite value."""
+    table = fp8_codes(layout)
+    vals = np.array([v for v, _ in table])
+    codes = np.array([c for _, c in table])
+    out = np.empty_like(x)
+    for i, xi in enumerate(x):
+        a = abs(xi)
+        if a >= vals[-1]:
+            out[i] = np.copysign(vals[-1], xi)
+            continue
+        j = np.searchsorted(vals, a)       # vals[j-1] < a <= vals[j]
+        if vals[j] == a:
+            q = a
+        else:
+            lo, hi = vals[j - 1], vals[j]
+            if a - lo < hi - a:
+                q = lo
+            elif hi - a < a - lo:
+                q = hi
+            else:
+                q = lo if codes[j - 1] % 2 == 0 else hi
+        out[i] = np.copysign(q, xi)
+    return out
+
+
+@pytest.mark.parametrize("fmt", sorted(FP8_LAYOUT))
+def test_paper_fp8_formats_against_brute_force(fmt):
+    """RNE with saturation onto the paper's 8-bit formats (Sec. 4) equals the
+    nearest value among all codes of the bit layout, ties to the even code, on
+    random magnitudes over the whole range, exact midpoints and out-of-range
+    values; the largest finite value is the layout's."""
+    layout = FP8_LAYOUT[fmt]
+    table = fp8_codes(layout)
+    vals = np.array([v for v, _ in table])
+    assert O.format_max(fmt) == vals[-1]
+    rng = np.random.default_rng(11)
+    mags = np.exp(rng.uniform(np.log(vals[1]) - 3, np.log(vals[-1]) + 2, 4000))
+    mids = (vals[:-1] + vals[1:]) / 2
+    x = np.concatenate([mags * rng.choice([-1, 1], mags.size), mids, -mids, vals, [0.0]])
+    np.testing.assert_array_equal(O.quantize(fmt, x), fp8_round_brute(layout, x))
+
+
+@pytest.mark.parametrize("fmt,tname", [("e4m3fnuz", "float8_e4m3fnuz"),
+                                       ("e5m2fnuz", "float8_e5m2fnuz")])
+def test_paper_fp8_formats_match_torch_casts_in_range(fmt, tname):
+    """Inside the finite range the fnuz quantisers equal torch's casts of the
+    same float32 values (torch does not saturate, so the range is clipped)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    fmax = O.format_max(fmt)
+    x = (np.exp(rng.uniform(np.log(fmax) - 25, np.log(fmax), 20000)) *
+         rng.choice([-1, 1], 20000)).astype(np.float32)
+    ref = torch.from_numpy(x).to(getattr(torch, tname)).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.quantize(fmt, x.astype(np.float64)), ref)
+
+
 def test_compression_factor_of_the_paper():
     """(32 / bits) x k: float8 with k = 16 gives the paper's 64x."""
     v = golden("paper_numbers.txt")["compression_e4m3b11fnuz_k16"][0]
