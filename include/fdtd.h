@@ -188,8 +188,9 @@ enum {
                                  TMA reverse of 3, 0 and 1 the plain reverse */
   FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8 default, 16); width 32 */
   FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
-  FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: time every m-th launch of each kernel kind with
-                                 CUDA events on the library's stream (0 = off) */
+  FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: every m-th launch of a time loop opens a timed
+                                 interval (CUDA events on the library's stream), see
+                                 fdtd_kernel_timing (0 = off) */
   FDTD_OPT_ROWS_PER_THREAD = 5, /* TMA half-step kernels: tile rows per thread (1 default, 2) */
   FDTD_OPT_STAGES = 6           /* one-plane kernels (4, 5): planes staged per CTA (2
                                    default, 3, 4): stages - 1 planes are in flight while one
@@ -204,9 +205,14 @@ enum {
   FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_FUSED_FWD = 6, FDTD_K_FUSED_REV = 7,
   FDTD_K_KINDS = 8
 };
-/* Average device duration (ms) of the sampled launches of one kernel kind
- * in the last forward + backward, and how many launches were sampled
- * (FDTD_OPT_SAMPLE_EVERY must be > 0). */
+/* Average in-loop cost (ms) per launch of one kernel kind in the last
+ * forward + backward, and the number of samples it rests on
+ * (FDTD_OPT_SAMPLE_EVERY = m must be > 0).  Every m-th launch opens an
+ * interval timed with CUDA events, alternately around one launch (kind p)
+ * and around two consecutive launches (kind p, then kind q); the cost of q is
+ * mean(pair p->q) - mean(single p), so the events' own overhead cancels and
+ * the result is q's duration plus its launch gap after p.  0 when a kind was
+ * not sampled. */
 int fdtd_kernel_timing(const fdtd_handle* h, int kind, float* avg_ms, int* samples);
 
 /* Device time (CUDA events on the library's stream) of the last forward

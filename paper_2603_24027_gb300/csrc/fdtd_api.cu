@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -40,6 +41,17 @@ struct GraphKey {
 
 }  // namespace
 
+// One sampled interval of a time loop: type 0 = a single launch of kind q,
+// type 1 = two consecutive launches, kind p then kind q; -1 = left open.
+struct SampleEntry {
+  int type, p, q;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec;
+  std::vector<SampleEntry> plan;   // intervals the graph's event nodes record
+};
+
 struct fdtd_handle {
   int nx, ny, nz, px, P, N, nmax;
   double S, dx, dt;
@@ -67,17 +79,17 @@ struct fdtd_handle {
   FwdMaps fmaps[2];
   char* maps_ws;
   int maps_ty;
-  // sampled kernel timing: event pairs per kernel kind
-  std::vector<cudaEvent_t> sev[FDTD_K_KINDS][2];
-  int sused[FDTD_K_KINDS];
-  int gsused[2][FDTD_K_KINDS];   // sample counts of the captured graphs (one sampling per key)
+  // sampled kernel timing (see Sampler): per direction a pool of start / end
+  // events and the intervals the last enqueued or replayed loop recorded
+  std::vector<cudaEvent_t> spool[2][2];
+  std::vector<SampleEntry> splan[2];
   float savg[FDTD_K_KINDS];
   int scount[FDTD_K_KINDS];
 
   cudaStream_t stream;
   cudaEvent_t ev_in, ev_out, t0, t1, t2, t3;
   bool cuda_ready;
-  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, GraphEntry> graphs;
   int launches_fwd, launches_bwd;
   float fwd_ms, bwd_ms;
   std::vector<double> obj_hist;
@@ -480,8 +492,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
-    h->sused[q] = 0; h->savg[q] = 0.f; h->scount[q] = 0;
-    h->gsused[0][q] = h->gsused[1][q] = 0;
+    h->savg[q] = 0.f;
+    h->scount[q] = 0;
   }
   h->cuda_ready = false;
   h->launches_fwd = h->launches_bwd = 0;
@@ -498,7 +510,7 @@ extern "C" const char* fdtd_last_error(const fdtd_handle* h) {
 }
 
 static void drop_graphs(fdtd_handle* h) {
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
 }
 
@@ -507,9 +519,9 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
   if (h->cuda_ready) {
     cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    for (int q = 0; q < FDTD_K_KINDS; ++q)
+    for (int d = 0; d < 2; ++d)
       for (int e = 0; e < 2; ++e)
-        for (cudaEvent_t ev : h->sev[q][e]) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : h->spool[d][e]) cudaEventDestroy(ev);
     cudaEventDestroy(h->ev_in); cudaEventDestroy(h->ev_out);
     cudaEventDestroy(h->t0); cudaEventDestroy(h->t1);
     cudaEventDestroy(h->t2); cudaEventDestroy(h->t3);
@@ -696,47 +708,85 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
 
 // Sampled kernel timing: event pairs recorded on h->stream around every
 // opt_sample-th launch of a kernel kind (external event nodes when captured).
-static bool sampled(const fdtd_handle* h, int n) { return h->opt_sample > 0 && n % h->opt_sample == 0; }
-
-static int ensure_sample_events(fdtd_handle* h) {
-  if (h->opt_sample <= 0) return FDTD_OK;
-  size_t need = (size_t)h->N / h->opt_sample + 2;
-  for (int q = 0; q < FDTD_K_KINDS; ++q)
-    for (int e = 0; e < 2; ++e)
-      while (h->sev[q][e].size() < need) {
-        cudaEvent_t ev;
-        CK(h, cudaEventCreate(&ev));
-        h->sev[q][e].push_back(ev);
-      }
-  return FDTD_OK;
-}
-
-static cudaError_t mark(fdtd_handle* h, int kind, int which, bool on) {
-  if (!on) return cudaSuccess;
-  int i = h->sused[kind];
-  if (i >= (int)h->sev[kind][which].size()) return cudaSuccess;
-  if (which == 1) h->sused[kind] = i + 1;
-  return cudaEventRecordWithFlags(h->sev[kind][which][i], h->stream, cudaEventRecordExternal);
-}
-
-static void reset_samples(fdtd_handle* h, const int* kinds, int nk) {
-  for (int q = 0; q < nk; ++q) h->sused[kinds[q]] = 0;
-}
-
-static void collect_samples(fdtd_handle* h, const int* kinds, int nk) {
-  for (int q = 0; q < nk; ++q) {
-    int kd = kinds[q];
-    double tot = 0.0;
-    int cnt = 0;
-    for (int i = 0; i < h->sused[kd]; ++i) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, h->sev[kd][0][i], h->sev[kd][1][i]) == cudaSuccess) {
-        tot += ms;
-        ++cnt;
-      }
+// Sampled kernel timing.  A CUDA event pair around a single launch inside the
+// time loop also measures the event nodes and the launch latency they expose
+// (several microseconds), so the per-launch cost is measured differentially:
+// every m-th launch opens an interval, alternately around one launch (kind p)
+// and around two consecutive launches (kind p, then kind q).  The in-loop
+// cost of kind q is mean(pair p->q) - mean(single p): both intervals carry the
+// same event overhead, which cancels, and what remains is q's duration plus
+// its launch gap after p, i.e. what q adds to the loop.
+struct Sampler {
+  fdtd_handle* h;
+  int dir;
+  long long m, i = 0;
+  int open = -1;        // plan entry of the open interval
+  int open_type = 0;
+  long long end_at = 0;  // launch index after which it closes
+  Sampler(fdtd_handle* h_, int dir_) : h(h_), dir(dir_), m(h_->opt_sample) {
+    h->splan[dir].clear();
+  }
+  cudaError_t record(int which, size_t slot) {
+    std::vector<cudaEvent_t>& pool = h->spool[dir][which];
+    while (pool.size() <= slot) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e) return e;
+      pool.push_back(ev);
     }
-    h->savg[kd] = cnt ? (float)(tot / cnt) : 0.f;
-    h->scount[kd] = cnt;
+    return cudaEventRecordWithFlags(pool[slot], h->stream, cudaEventRecordExternal);
+  }
+  cudaError_t before(int kind) {
+    if (m <= 0 || open >= 0 || i % m) return cudaSuccess;
+    open_type = (int)((i / m) & 1);
+    h->splan[dir].push_back(SampleEntry{-1, kind, kind});
+    open = (int)h->splan[dir].size() - 1;
+    end_at = i + open_type;
+    return record(0, (size_t)open);
+  }
+  cudaError_t after(int kind) {
+    cudaError_t e = cudaSuccess;
+    if (open >= 0 && i == end_at) {
+      SampleEntry& se = h->splan[dir][open];
+      se.type = open_type;
+      se.q = kind;
+      e = record(1, (size_t)open);
+      open = -1;
+    }
+    ++i;
+    return e;
+  }
+};
+
+static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
+  const std::vector<SampleEntry>& plan = h->splan[dir];
+  double ssum[FDTD_K_KINDS] = {0}, psum[FDTD_K_KINDS][FDTD_K_KINDS] = {{0}};
+  int sn[FDTD_K_KINDS] = {0}, pn[FDTD_K_KINDS][FDTD_K_KINDS] = {{0}};
+  for (size_t j = 0; j < plan.size(); ++j) {
+    const SampleEntry& se = plan[j];
+    if (se.type < 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->spool[dir][0][j], h->spool[dir][1][j]) != cudaSuccess) continue;
+    if (se.type == 0) {
+      ssum[se.p] += ms;
+      ++sn[se.p];
+    } else {
+      psum[se.p][se.q] += ms;
+      ++pn[se.p][se.q];
+    }
+  }
+  for (int t = 0; t < nk; ++t) {
+    const int q = kinds[t];
+    int best = -1;
+    for (int p = 0; p < FDTD_K_KINDS; ++p)
+      if (pn[p][q] > 0 && sn[p] > 0 && (best < 0 || pn[p][q] > pn[best][q])) best = p;
+    if (best >= 0) {
+      h->savg[q] = (float)(psum[best][q] / pn[best][q] - ssum[best] / sn[best]);
+      h->scount[q] = std::min(pn[best][q], sn[best]);
+    } else {
+      h->savg[q] = 0.f;
+      h->scount[q] = 0;
+    }
   }
 }
 
@@ -786,10 +836,8 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   char* tape = h->ws + L.tape;
   float* scales = (float*)(h->ws + L.scales);
   int eb = code_bytes(rec->dtype);
-  reset_samples(h, kFwdKinds, 4);
-  int nrec = 0;
+  Sampler smp(h, 0);
   for (int n = 0; n < h->N; ++n) {
-    bool sm = sampled(h, n);
     a.jn = h->wave[n];
     a.obj = (double*)(h->ws + L.obj) + n;
     const bool rec_now = n >= r && (n - r) % rec->k == 0;
@@ -800,46 +848,44 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       float* po = (float*)(h->ws + L.psiF[cur ^ 1]);
       a.F = (float*)(h->ws + L.F[cur]);
       a.psiA = (float*)(h->ws + L.psiF[cur]);
-      if ((e = mark(h, FDTD_K_FUSED_FWD, 0, sm))) return e;
+      if ((e = smp.before(FDTD_K_FUSED_FWD))) return e;
       if ((e = tma ? launch_fwd_tma(h->fmaps[cur], a, Fo, po, h->stream)
                    : launch_fused_fwd(a, Fo, po, h->stream)))
         return e;
-      if ((e = mark(h, FDTD_K_FUSED_FWD, 1, sm))) return e;
+      if ((e = smp.after(FDTD_K_FUSED_FWD))) return e;
       ++nl;
       if (rec_now) {
-        bool sr = sampled(h, nrec++);
-        if ((e = mark(h, FDTD_K_RECORD, 0, sr))) return e;
+        if ((e = smp.before(FDTD_K_RECORD))) return e;
         if ((e = launch_record(rec->dtype, rec->scaled, Fo, a.F, a.g, h->faces,
                                tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
                                h->stream)))
           return e;
-        if ((e = mark(h, FDTD_K_RECORD, 1, sr))) return e;
+        if ((e = smp.after(FDTD_K_RECORD))) return e;
         ++nl;
       }
       cur ^= 1;
       continue;
     }
-    if ((e = mark(h, FDTD_K_FWD_H, 0, sm))) return e;
+    if ((e = smp.before(FDTD_K_FWD_H))) return e;
     if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream) : launch_lag(0, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
       return e;
-    if ((e = mark(h, FDTD_K_FWD_H, 1, sm))) return e;
+    if ((e = smp.after(FDTD_K_FWD_H))) return e;
     ++nl;
     if (rec_now) {
-      bool sr = sampled(h, nrec++);
-      if ((e = mark(h, FDTD_K_RECORD, 0, sr))) return e;
+      if ((e = smp.before(FDTD_K_RECORD))) return e;
       if ((e = launch_record(rec->dtype, rec->scaled, a.F, a.F, a.g, h->faces,
                              tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
                              h->stream)))
         return e;
-      if ((e = mark(h, FDTD_K_RECORD, 1, sr))) return e;
+      if ((e = smp.after(FDTD_K_RECORD))) return e;
       ++nl;
     }
-    if ((e = mark(h, FDTD_K_FWD_E, 0, sm))) return e;
+    if ((e = smp.before(FDTD_K_FWD_E))) return e;
     if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream) : launch_lag(1, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
       return e;
-    if ((e = mark(h, FDTD_K_FWD_E, 1, sm))) return e;
+    if ((e = smp.after(FDTD_K_FWD_E))) return e;
     ++nl;
   }
   h->fwd_buf = cur;
@@ -878,32 +924,31 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                      &lrmaps[b])))
       return e;
   }
-  reset_samples(h, kBwdKinds, 4);
+  Sampler smp(h, 1);
   for (int n = h->N - 1; n >= 0; --n) {
-    bool sm = sampled(h, n);
     Interp ip;
     interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
-    if ((e = mark(h, FDTD_K_RESTORE, 0, sm))) return e;
+    if ((e = smp.before(FDTD_K_RESTORE))) return e;
     if ((e = launch_restore_seed(rec->dtype, a.F, a.L, a.g, h->faces, h->ws + L.tape, L.stride,
                                  (const float*)(h->ws + L.scales), ip, det, h->stream)))
       return e;
-    if ((e = mark(h, FDTD_K_RESTORE, 1, sm))) return e;
+    if ((e = smp.after(FDTD_K_RESTORE))) return e;
     a.jn = h->wave[n];
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
-    if ((e = mark(h, FDTD_K_REV_E, 0, sm))) return e;
+    if ((e = smp.before(FDTD_K_REV_E))) return e;
     if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
                          : launch_lag(2, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
-    if ((e = mark(h, FDTD_K_REV_E, 1, sm))) return e;
-    if ((e = mark(h, FDTD_K_REV_H, 0, sm))) return e;
+    if ((e = smp.after(FDTD_K_REV_E))) return e;
+    if ((e = smp.before(FDTD_K_REV_H))) return e;
     if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
                          : launch_lag(3, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
       return e;
-    if ((e = mark(h, FDTD_K_REV_H, 1, sm))) return e;
+    if ((e = smp.after(FDTD_K_REV_H))) return e;
     cur ^= 1;
     nl += 3;
   }
@@ -916,8 +961,16 @@ typedef cudaError_t (*EnqueueFn)(fdtd_handle*, const fdtd_record_cfg*, int*);
 // Run a time loop, through a cached CUDA graph when enabled.
 static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, EnqueueFn fn,
                     int* launches, cudaEvent_t ta, cudaEvent_t tb) {
-  int rc = ensure_sample_events(h);
-  if (rc) return rc;
+  // events for the sampled intervals exist before a capture starts
+  if (h->opt_sample > 0) {
+    const size_t need = (size_t)(3LL * h->N / h->opt_sample) + 4;
+    for (int e = 0; e < 2; ++e)
+      while (h->spool[dir][e].size() < need) {
+        cudaEvent_t ev;
+        CK(h, cudaEventCreate(&ev));
+        h->spool[dir][e].push_back(ev);
+      }
+  }
   if (!h->opt_graphs) {
     CK(h, cudaEventRecord(ta, h->stream));
     cudaError_t e = fn(h, rec, launches);
@@ -947,14 +1000,12 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
     cudaGraphDestroy(graph);
     if (e3) return cuda_fail(h, "cudaGraphInstantiate", e3);
     if (h->graphs.size() >= 8) drop_graphs(h);
-    it = h->graphs.insert(std::make_pair(key, exec)).first;
-    for (int q = 0; q < FDTD_K_KINDS; ++q) h->gsused[dir][q] = h->sused[q];
+    it = h->graphs.insert(std::make_pair(key, GraphEntry{exec, h->splan[dir]})).first;
     if (dir == 0) h->launches_fwd = nl; else h->launches_bwd = nl;
   }
-  const int* kinds = dir == 0 ? kFwdKinds : kBwdKinds;
-  for (int q = 0; q < 4; ++q) h->sused[kinds[q]] = h->gsused[dir][kinds[q]];
+  h->splan[dir] = it->second.plan;
   CK(h, cudaEventRecord(ta, h->stream));
-  CK(h, cudaGraphLaunch(it->second, h->stream));
+  CK(h, cudaGraphLaunch(it->second.exec, h->stream));
   CK(h, cudaEventRecord(tb, h->stream));
   *launches = dir == 0 ? h->launches_fwd : h->launches_bwd;
   return FDTD_OK;
@@ -991,7 +1042,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
-  collect_samples(h, kFwdKinds, 4);
+  collect_samples(h, 0, kFwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
@@ -1033,7 +1084,7 @@ static int backward_finish(fdtd_handle* h, double seed, float* d_grad) {
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaEventElapsedTime(&h->bwd_ms, h->t2, h->t3));
-  collect_samples(h, kBwdKinds, 4);
+  collect_samples(h, 1, kBwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");

@@ -11,6 +11,11 @@ oracle.  The forward fields' error against the oracle is reported once (the
 forward does not depend on the tape).
 
     python tests/precision_sweep.py --seeds 10 --out results.jsonl --md table.md
+
+--paper-formats runs the paper's own grid instead (Sec. 4, Fig. 3): every
+type unscaled (float32, float16, bfloat16 and the five 8-bit formats
+e4m3b11fnuz, e5m2fnuz, e4m3fnuz, e4m3 (IEEE-style) and e3m4) for k in
+{1, 2, 4, 8, 16, 32} with linear interpolation.
 """
 from __future__ import annotations
 
@@ -28,6 +33,8 @@ import numpy as np  # noqa: E402
 DTYPES = ["f32", "bf16", "f16", "e4m3"]
 KS = [1, 2, 4, 8, 16]
 INTERPS = ["linear", "cubic"]
+PAPER_DTYPES = ["f32", "f16", "bf16", "e4m3b11fnuz", "e5m2fnuz", "e4m3fnuz", "e4m3ieee", "e3m4"]
+PAPER_KS = [1, 2, 4, 8, 16, 32]
 
 
 def rel(a, b):
@@ -42,7 +49,11 @@ def cos(a, b):
     return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
-def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS):
+def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS, scaled=None,
+             oracle=True):
+    """One seed of the sweep.  scaled=None keeps each type's default (per-face
+    scales for f16 and the hardware e4m3); False stores every type unscaled.
+    oracle=False skips the FP64 reference (errors against it are then NaN)."""
     import torch
 
     from oracle import oracle as O
@@ -52,7 +63,10 @@ def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS):
 
     w = I.waveguide_sweep(seed=seed, n_steps=n_steps)
     t0 = time.perf_counter()
-    L_ref, g_ref, st_ref = O.gradient(w, want_state=True)
+    if oracle:
+        L_ref, g_ref, st_ref = O.gradient(w, want_state=True)
+    else:
+        L_ref, g_ref, st_ref = float("nan"), np.full(w.design_shape, np.nan), None
     t_oracle = time.perf_counter() - t0
     eps = torch.from_numpy(w.eps).cuda()
     sim = fdtd.Simulation(w)
@@ -63,7 +77,7 @@ def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS):
             for interp in interps:
                 if dt == "f32" and k == 1 and interp == "cubic":
                     continue
-                rec = A.record_cfg(dt, k, interp)
+                rec = A.record_cfg(dt, k, interp, scaled=scaled)
                 L = sim.forward(eps, rec)
                 fields = sim.read_fields().cpu().numpy() if base is None else None
                 g = sim.backward(1.0).cpu().numpy()
@@ -72,8 +86,8 @@ def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS):
                            cos_oracle=cos(g, g_ref))
                 if base is None:   # FP32 k = 1 first
                     base = dict(g=g, bytes=row["tape_bytes"])
-                    row["E_rel_err"] = rel(fields[:3], st_ref[:3])
-                    row["H_rel_err"] = rel(fields[3:6], st_ref[3:6])
+                    row["E_rel_err"] = rel(fields[:3], st_ref[:3]) if oracle else float("nan")
+                    row["H_rel_err"] = rel(fields[3:6], st_ref[3:6]) if oracle else float("nan")
                 row["compression"] = base["bytes"] / row["tape_bytes"]
                 row["cos_fp32_k1"] = cos(g, base["g"])
                 row["rel_fp32_k1"] = rel(g, base["g"])
@@ -103,6 +117,8 @@ def main():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--out", default=None)
     p.add_argument("--md", default=None)
+    p.add_argument("--paper-formats", action="store_true")
+    p.add_argument("--no-oracle", action="store_true")
     a = p.parse_args()
     from paper_2603_24027_gb300 import build as B
     from oracle import build as OB
@@ -110,7 +126,11 @@ def main():
     OB.build()
     rows = []
     for s in range(a.seeds):
-        r, t = run_seed(s, a.steps)
+        if a.paper_formats:
+            r, t = run_seed(s, a.steps, dtypes=PAPER_DTYPES, ks=PAPER_KS, interps=["linear"],
+                            scaled=False, oracle=not a.no_oracle)
+        else:
+            r, t = run_seed(s, a.steps, oracle=not a.no_oracle)
         base = r[0]
         print(f"seed {s}: oracle {t:.1f} s, fields E {base['E_rel_err']:.2e} H {base['H_rel_err']:.2e}, "
               f"L {base['L_rel_err']:.2e}, FP32 k=1 grad {base['grad_rel_err']:.2e}", flush=True)

@@ -197,6 +197,29 @@ def test_codec_is_bit_exact_against_torch_casts(F, A, dtype, scaled):
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
 
 
+def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
+    """Differential in-loop timing (pair of launches minus single launch):
+    every kernel kind gets a positive cost, the costs times the launch counts
+    add up to the measured loop times, and sampling does not change results."""
+    w = I.waveguide_sweep(n_steps=200)
+    rec = A.record_cfg("bf16", 4, "linear")
+    base = gpu_run(F, A, w, rec=rec)
+    r = gpu_run(F, A, w, rec=rec, options={A.OPT_SAMPLE_EVERY: 7})
+    np.testing.assert_array_equal(r["fields"], base["fields"])
+    np.testing.assert_array_equal(r["g"], base["g"])
+    sim = r["sim"]
+    sim.forward(torch.from_numpy(w.eps).cuda(), rec)   # warm graphs, then measure
+    sim.backward(1.0)
+    kt, t = sim.kernel_timing(), sim.last_timing()
+    for name in ("fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h"):
+        assert name in kt and kt[name][0] > 0 and kt[name][1] >= 1, (name, kt)
+    n, nrec = w.n_steps, -(-w.n_steps // 4)
+    fwd = n * (kt["fwd_h"][0] + kt["fwd_e"][0]) + nrec * kt["record"][0]
+    bwd = n * (kt["restore_seed"][0] + kt["rev_e"][0] + kt["rev_h"][0])
+    assert 0.7 < fwd / t["fwd_ms"] < 1.3, (fwd, t)
+    assert 0.7 < bwd / t["bwd_ms"] < 1.3, (bwd, t)
+
+
 PAPER_FP8 = ["e4m3b11fnuz", "e5m2fnuz", "e4m3fnuz", "e4m3ieee", "e3m4"]
 
 
