@@ -192,9 +192,14 @@ enum {
                                  interval (CUDA events on the library's stream), see
                                  fdtd_kernel_timing (0 = off) */
   FDTD_OPT_ROWS_PER_THREAD = 5, /* TMA half-step kernels: tile rows per thread (1 default, 2) */
-  FDTD_OPT_STAGES = 6           /* one-plane kernels (4, 5): planes staged per CTA (2
+  FDTD_OPT_STAGES = 6,          /* one-plane kernels (4, 5): planes staged per CTA (2
                                    default, 3, 4): stages - 1 planes are in flight while one
                                    is computed */
+  FDTD_OPT_PDL = 7,             /* 1 (default): kernel 5 launches as a programmatic dependent
+                                   of the previous kernel (its launch and prologue overlap
+                                   the previous kernel's tail); 0: plain stream order */
+  FDTD_OPT_PREFETCH = 8         /* kernel 5: 1 = when a plane is staged, warm L2 with the
+                                   next plane's boxes; 0 (default) = off */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -33,7 +33,7 @@ struct Layout {
 };
 
 struct GraphKey {
-  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages;
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -74,7 +74,8 @@ struct fdtd_handle {
   int fwd_buf;                // field buffer holding the state after forward
   fdtd_record_cfg fwd_rec;
 
-  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages;
+  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
+      opt_prefetch;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -489,6 +490,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
+  h->opt_pdl = 1;
+  h->opt_prefetch = 0;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -591,6 +594,8 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < 2 || value > 4) return fail(h, FDTD_EINVAL, "stages must be 2, 3 or 4");
       h->opt_stages = value;
       break;
+    case FDTD_OPT_PDL: h->opt_pdl = value ? 1 : 0; break;
+    case FDTD_OPT_PREFETCH: h->opt_prefetch = value ? 1 : 0; break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -606,6 +611,8 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_SAMPLE_EVERY: *value = h->opt_sample; break;
     case FDTD_OPT_ROWS_PER_THREAD: *value = h->opt_rows; break;
     case FDTD_OPT_STAGES: *value = h->opt_stages; break;
+    case FDTD_OPT_PDL: *value = h->opt_pdl; break;
+    case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -701,6 +708,8 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.tile_y = lag_tile_y(h);
   a.rows = h->opt_rows;
   a.stages = h->opt_stages;
+  a.pdl = h->opt_pdl;
+  a.prefetch = h->opt_prefetch;
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
   a.err = (unsigned*)(h->ws + L.err);
   return a;
@@ -986,6 +995,8 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.sample = h->opt_sample;
   key.rows = h->opt_rows;
   key.stages = h->opt_stages;
+  key.pdl = h->opt_pdl;
+  key.prefetch = h->opt_prefetch;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;

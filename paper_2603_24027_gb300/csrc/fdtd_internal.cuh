@@ -200,6 +200,8 @@ struct StepArgs {
   int tile_y;
   int rows;        // tile rows per thread (TMA half-step kernels)
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
+  int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
+  int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
   unsigned* err;   // device error word (ERR_*)
 };
 

@@ -54,6 +54,36 @@ __device__ __forceinline__ float adj(float v, float lpsi, float b, float a, floa
   return kv * v + a * mu;
 }
 
+// Programmatic dependent launch: wait until the previous kernel in the stream
+// has completed and its writes are visible (nothing before this point reads
+// or writes data another kernel touches), then allow the next kernel's CTAs
+// to start their own prologue as this grid's CTAs retire.  Without a
+// programmatic dependency both are no-ops.
+__device__ __forceinline__ void pdl_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Stage plane p: boxes(p, f) calls f(stage offset, tensor map, x, y, component,
+// bytes) for every box the kernel needs of plane p.  The barrier expects the
+// sum of the boxes' bytes, then every box is loaded; with prefetch, plane
+// p + 1's boxes are also warmed in L2 so that their own load, one iteration
+// later, finds them closer (only planes inside [0, nz) and the ring).
+template <class Boxes>
+__device__ __forceinline__ void stage_plane(const Boxes& boxes, int p, unsigned char* st,
+                                            uint64_t* bar, bool prefetch_next) {
+  uint32_t bytes = 0;
+  boxes(p, [&](int, const CUtensorMap*, int, int, int, uint32_t b) { bytes += b; });
+  mbar_expect_tx(bar, bytes);
+  boxes(p, [&](int off, const CUtensorMap* mp, int x, int y, int c, uint32_t) {
+    tma_load_4d(st + off, mp, bar, x, y, p, c);
+  });
+  if (prefetch_next)
+    boxes(p + 1, [&](int, const CUtensorMap* mp, int x, int y, int c, uint32_t) {
+      tma_prefetch_l2_4d(mp, x, y, p + 1, c);
+    });
+}
+
 template <int S>
 __device__ __forceinline__ uint64_t* ring_init(unsigned char* dsm, int stage_bytes) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + S * stage_bytes);
@@ -105,18 +135,19 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_h(const __grid_constant__ Lag
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
-  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+  auto boxes = [&](int p, auto&& f) {
     const bool body = p < k1;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    uint32_t bytes = 3 * B::P * 4 + (body ? 3 * B::OP * 4 : 0) + (body && txs ? 2 * B::OP * 4 : 0) +
-                     (body && tys ? 2 * B::OP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
-    mbar_expect_tx(bar, bytes);
-    tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
-    if (body) tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P32, bar, x0, y0, p, 0);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32, bar, x0, y0, p, 4);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 8);
+    f(Y::E, &m.F36, x0, y0, 0, 3 * B::P * 4);
+    if (body) f(Y::H, &m.F32, x0, y0, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.P32, x0, y0, 0, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.P32, x0, y0, 4, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.P32, x0, y0, 8, 2 * B::OP * 4);
   };
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= k1 && p + 1 < g.nz);
+  };
+  pdl_sync();
   if (tid == 0)
     for (int i = 0; i < S && k0 + i <= k1; ++i) issue(k0 + i, dsm + i * Y::STAGE, bars + i);
   const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
@@ -264,21 +295,22 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_e(const __grid_constant__ Lag
   const int p0_ = k0 - 1, p1_ = k1 - 1;
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
   double* red = reinterpret_cast<double*>(dsm + S * Y::STAGE + 8 * S + 64);
-  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+  auto boxes = [&](int p, auto&& f) {
     const bool body = p >= k0;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    uint32_t bytes = 3 * B::P * 4 + (body ? 4 * B::OP * 4 : 0) + (body && txs ? 2 * B::OP * 4 : 0) +
-                     (body && tys ? 2 * B::OP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
-    mbar_expect_tx(bar, bytes);
-    tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
+    f(Y::H, &m.F36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
     if (body) {
-      tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
-      tma_load_4d(st + Y::CB, &m.cb32, bar, x0, y0, p, 0);
+      f(Y::E, &m.F32, x0, y0, 0, 3 * B::OP * 4);
+      f(Y::CB, &m.cb32, x0, y0, 0, B::OP * 4);
     }
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P32, bar, x0, y0, p, 2);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32, bar, x0, y0, p, 6);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 10);
+    if (body && txs) f(Y::PX, &m.P32, x0, y0, 2, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.P32, x0, y0, 6, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.P32, x0, y0, 10, 2 * B::OP * 4);
   };
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
+  };
+  pdl_sync();
   if (tid == 0)
     for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
   const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
@@ -476,28 +508,27 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
   // primal data only where the primal runs: interior tiles, planes P..nz-P-1
   // (and plane P-1's Ht for the z difference of plane P)
   auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
-  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+  auto boxes = [&](int p, auto&& f) {
     const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (body || tail);
     const bool lam = body || tail;
     const bool hbox = (head || body) && (primal_plane(p) || primal_plane(p + 1));
     const bool ebox = body && primal_plane(p);
-    uint32_t bytes = (hbox ? 3 * B::P * 4 : 0) + (lam ? 4 * B::P * 4 : 0) +
-                     (body ? 3 * B::OP * 4 : 0) + (ebox ? 3 * B::OP * 4 : 0) +
-                     (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
-                     (zs ? 2 * B::OP * 4 : 0);
-    mbar_expect_tx(bar, bytes);
-    if (hbox) tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
+    if (hbox) f(Y::H, &m.F36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
     if (lam) {
-      tma_load_4d(st + Y::CB, &m.cb36, bar, x0, y0, p, 0);
-      tma_load_4d(st + Y::LE, &m.L36, bar, x0, y0, p, 0);
+      f(Y::CB, &m.cb36, x0, y0, 0, B::P * 4);
+      f(Y::LE, &m.L36, x0, y0, 0, 3 * B::P * 4);
     }
-    if (ebox) tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
-    if (body) tma_load_4d(st + Y::LH, &m.L32, bar, x0, y0, p, 3);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0, y0, p, 2);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0, p, 6);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 10);
+    if (ebox) f(Y::E, &m.F32, x0, y0, 0, 3 * B::OP * 4);
+    if (body) f(Y::LH, &m.L32, x0, y0, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.P36, x0, y0, 2, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.P32y, x0, y0, 6, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.P32, x0, y0, 10, 2 * B::OP * 4);
   };
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
+  };
+  pdl_sync();
   if (tid == 0)
     for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
   // x profiles at x, x+1 (cell 1, also cell 0's +x neighbour) and x+2
@@ -776,24 +807,23 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
   // primal data only where the primal runs: interior tiles, planes P..nz-P-1
   // (and plane nz-P's E for the z difference of plane nz-P-1)
   auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
-  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+  auto boxes = [&](int p, auto&& f) {
     const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (head || body);
     const bool ebox = (body && primal_plane(p)) || (tail && primal_plane(p - 1));
     const bool hown = body && primal_plane(p);
-    uint32_t bytes = (ebox ? 3 * B::P * 4 : 0) + (head || body ? 3 * B::P * 4 : 0) +
-                     (hown ? 3 * B::OP * 4 : 0) + (body ? 3 * B::OP * 4 : 0) +
-                     (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
-                     (zs ? 2 * B::OP * 4 : 0);
-    mbar_expect_tx(bar, bytes);
-    if (ebox) tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
-    if (head || body) tma_load_4d(st + Y::LH, &m.L36, bar, x0 - 4, y0 - 1, p, 3);
-    if (hown) tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
-    if (body) tma_load_4d(st + Y::LE, &m.L32, bar, x0, y0, p, 0);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0 - 4, y0, p, 0);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0 - 1, p, 4);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 8);
+    if (ebox) f(Y::E, &m.F36, x0, y0, 0, 3 * B::P * 4);
+    if (head || body) f(Y::LH, &m.L36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
+    if (hown) f(Y::H, &m.F32, x0, y0, 3, 3 * B::OP * 4);
+    if (body) f(Y::LE, &m.L32, x0, y0, 0, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.P36, x0 - 4, y0, 0, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.P32y, x0, y0 - 1, 4, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.P32, x0, y0, 8, 2 * B::OP * 4);
   };
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
+  };
+  pdl_sync();
   if (tid == 0)
     for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
   // x profiles at x-1 (cell 0's -x neighbour), x and x+1
@@ -1005,39 +1035,38 @@ static cudaError_t set_smem_l2(KT kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Launch with the programmatic-stream-serialization attribute when a.pdl is
+// set (the kernel then overlaps its launch and prologue with the tail of the
+// previous kernel and waits in pdl_sync()).
+template <class KT>
+static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStream_t s,
+                             const LagMaps& m, const StepArgs& a) {
+  cudaError_t e = set_smem_l2(kernel, smem);
+  if (e) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = a.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, m, a);
+}
+
 template <int TY, int S>
 static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
   dim3 block(16, TY);
-  cudaError_t e = cudaSuccess;
   switch (which) {
-    case 0: {
-      int sm = LFH<TY, S>::smem();
-      if ((e = set_smem_l2(k_l2fwd_h<TY, S>, sm))) return e;
-      k_l2fwd_h<TY, S><<<grid, block, sm, s>>>(m, a);
-      break;
-    }
-    case 1: {
-      int sm = LFE<TY, S>::smem();
-      if ((e = set_smem_l2(k_l2fwd_e<TY, S>, sm))) return e;
-      k_l2fwd_e<TY, S><<<grid, block, sm, s>>>(m, a);
-      break;
-    }
-    case 2: {
-      int sm = LRE<TY, S>::smem();
-      if ((e = set_smem_l2(k_l2rev_e<TY, S>, sm))) return e;
-      k_l2rev_e<TY, S><<<grid, block, sm, s>>>(m, a);
-      break;
-    }
-    case 3: {
-      int sm = LRH<TY, S>::smem();
-      if ((e = set_smem_l2(k_l2rev_h<TY, S>, sm))) return e;
-      k_l2rev_h<TY, S><<<grid, block, sm, s>>>(m, a);
-      break;
-    }
-    default: return cudaErrorInvalidValue;
+    case 0: return launch_ex(k_l2fwd_h<TY, S>, grid, block, LFH<TY, S>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S>, grid, block, LFE<TY, S>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S>, grid, block, LRE<TY, S>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S>, grid, block, LRH<TY, S>::smem(), s, m, a);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.

@@ -197,6 +197,18 @@ def test_codec_is_bit_exact_against_torch_casts(F, A, dtype, scaled):
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
+    w = SMALL["ragged_poynting"]()
+    rec = A.record_cfg("bf16", 2, "linear")
+    a = gpu_run(F, A, w, rec=rec, options={A.OPT_PDL: 1, A.OPT_USE_GRAPHS: graphs,
+                                           A.OPT_PREFETCH: 1})
+    b = gpu_run(F, A, w, rec=rec, options={A.OPT_PDL: 0, A.OPT_USE_GRAPHS: graphs})
+    np.testing.assert_array_equal(a["fields"], b["fields"])
+    np.testing.assert_array_equal(a["g"], b["g"])
+    assert a["L"] == b["L"]
+
+
 def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
     """Differential in-loop timing (pair of launches minus single launch):
     every kernel kind gets a positive cost, the costs times the launch counts
