@@ -8,10 +8,17 @@ interpolation.  Metric: cell-updates per second of the whole gradient,
 nx*ny*nz*n_steps / (T_forward + T_backward), cells including the CPML.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload waveguide200|waveguide600|batched64] [--n-steps N]
 
 N > 1 runs under torchrun: every rank computes its own design (independent
 problems, no data-path collective) and rank 0 prints one JSON line.
 --impl reference times the FP64 CPU oracle on the host cores instead.
+
+Other workloads (not the default line): waveguide600 = 600 x 600 x 300 cells
+at 10 nm, 16-cell CPML (10000 steps unless --n-steps); batched64 = 64
+independent vacuum cubes of 32..128 cells with 600..1500 steps each, run
+concurrently through the group calls (one step = one group forward + one
+group backward of all 64).
 """
 from __future__ import annotations
 
@@ -47,6 +54,9 @@ def parse():
     p.add_argument("--cpu-sample-steps", type=int, default=24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true")
+    p.add_argument("--workload", default="waveguide200",
+                   choices=["waveguide200", "waveguide600", "batched64"])
+    p.add_argument("--n-steps", type=int, default=0, help="override the workload's step count")
     return p.parse_args()
 
 
@@ -75,10 +85,10 @@ def job_rate(ws: int, cell_updates: int, steps: int, seconds: float) -> float:
     return ws * cell_updates * steps / seconds / 1e9
 
 
-def workload(rank: int, n_steps=None):
+def workload(rank: int, n_steps=None, name: str = "waveguide200"):
     from paper_2603_24027_gb300 import inputs as I
-    w = I.waveguide_mid(seed=rank)
-    return w if n_steps is None else w.replace(n_steps=n_steps)
+    w = I.waveguide_large(seed=rank) if name == "waveguide600" else I.waveguide_mid(seed=rank)
+    return w if not n_steps else w.replace(n_steps=n_steps)
 
 
 # ------------------------------------------------------------ roofline ---
@@ -141,7 +151,7 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def read_traffic(kernel: str, digest: str):
+def read_traffic(kernel: str, digest: str, workload: str = "waveguide200"):
     """ncu DRAM bytes per launch recorded for this kernel build, or None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -149,7 +159,7 @@ def read_traffic(kernel: str, digest: str):
     with open(path) as f:
         for line in f:
             parts = line.split("#", 1)[0].split()
-            if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest and parts[2] == "waveguide200":
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest and parts[2] == workload:
                 return float(parts[3])
     return None
 
@@ -246,7 +256,7 @@ def run_ours(args):
     from paper_2603_24027_gb300 import _capi as A
     from paper_2603_24027_gb300 import fdtd
 
-    w = workload(rank)
+    w = workload(rank, args.n_steps, args.workload)
     rec = tape_cfg(A, args.tape)
     sim = fdtd.Simulation(w, device=dev)
     if args.kernel >= 0:
@@ -312,7 +322,7 @@ def run_ours(args):
         kern[name] = d
     dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["share_of_step"])
     digest = B._digest()
-    traffic = read_traffic(dom, digest)
+    traffic = read_traffic(dom, digest, args.workload)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"],
                 "peak": peak, "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
@@ -385,7 +395,7 @@ def run_ours(args):
                   "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps, args.workload)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -394,23 +404,25 @@ def run_ours(args):
 
 # ------------------------------------------------------------- oracle ---
 
-def oracle_step(n_steps: int):
+def oracle_step(n_steps: int, name: str = "waveguide200"):
     from oracle import oracle as O
-    w = workload(0, n_steps=n_steps)
+    w = workload(0, n_steps=n_steps, name=name)
     t0 = time.perf_counter()
     O.gradient(w)
     return time.perf_counter() - t0, w
 
 
-def cpu_baseline(n_steps: int):
+def cpu_baseline(n_steps: int, name: str = "waveguide200"):
     from oracle import build as ob
     from oracle import oracle as O
     ob.build()
-    dt, w = oracle_step(n_steps)
+    if name == "waveguide600":          # 27x the cells: keep the sample at a similar CPU time
+        n_steps = max(2, n_steps // 12)
+    dt, w = oracle_step(n_steps, name)
     return {"value": w.n_cells * w.n_steps / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle",
             "sample": f"FP64 oracle gradient (forward + stored-history adjoint) of the same "
-                      f"200x200x100 workload truncated to {n_steps} steps; {dt:.1f} s"}
+                      f"{w.nx}x{w.ny}x{w.nz} workload truncated to {n_steps} steps; {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -442,10 +454,111 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """64 independent problems on one GPU through the group calls."""
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_24027_gb300 import build as B
+    B.build()
+    from paper_2603_24027_gb300 import _capi as A
+    from paper_2603_24027_gb300 import fdtd
+    from paper_2603_24027_gb300 import inputs as I
+
+    wl = I.batched_cubes(seed=rank)
+    rec = tape_cfg(A, args.tape)
+    sims = [fdtd.Simulation(w, device=dev) for w in wl]
+    eps = [torch.from_numpy(w.eps).to(dev) for w in wl]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        fdtd.group_forward(sims, eps, rec)
+        return fdtd.group_backward(sims)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ts = []
+    with ClockSampler(gpu_index_for_smi(local)) as clk:
+        for _ in range(args.steps):
+            flush.random_(0, 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+    total_ms = max_over_ranks(sum(ts), ws, dev)
+    cell_updates = sum(w.n_cells * w.n_steps for w in wl)
+    value = job_rate(ws, cell_updates, args.steps, total_ms / 1e3)
+    # aggregate algorithmic bytes of one step (all problems, all launches)
+    byts = 0
+    for w in wl:
+        ab = algorithmic_bytes(w)
+        byts += w.n_steps * (ab["fwd_h"] + ab["fwd_e"] + ab["rev_e"] + ab["rev_h"])
+    peak, peak_kind = read_peaks()
+    achieved = byts / (total_ms / args.steps / 1e3) / 1e9
+    launches = sum(s.last_timing()["fwd_launches"] + s.last_timing()["bwd_launches"] + 2
+                   for s in sims) * args.steps
+
+    # end to end: eps from pinned host memory in, gradients and objectives out
+    eps_h = [torch.from_numpy(w.eps).pin_memory() for w in wl]
+    grads_h = [torch.empty(w.design_shape, dtype=torch.float32).pin_memory() for w in wl]
+    te = []
+    for _ in range(args.steps):
+        flush.random_(0, 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, hsrc in zip(eps, eps_h):
+            d.copy_(hsrc, non_blocking=True)
+        objs = fdtd.group_forward(sims, eps, rec)
+        gs = fdtd.group_backward(sims)
+        for hdst, g in zip(grads_h, gs):
+            hdst.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+        te.append(time.perf_counter() - t0)
+    assert all(np.isfinite(objs))
+    e2e_t = max_over_ranks(sum(te), ws, dev)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (64 seeded vacuum cubes with random design boxes)",
+        "config": {"workload": "batched64", "problems": len(wl),
+                   "cells": sum(w.n_cells for w in wl), "cell_updates": cell_updates,
+                   "tape": args.tape, "parallelism": f"replicas x{ws}, 64 concurrent problems",
+                   "l2": "flushed before every timed step"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "all kernels, aggregate over 64 concurrent problems",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_step": byts},
+        "clocks": clk.summary(),
+        "e2e": {"value": job_rate(ws, cell_updates, args.steps, e2e_t), "unit": UNIT,
+                "h2d_bytes_per_step": sum(w.n_cells * 4 for w in wl),
+                "d2h_bytes_per_step": sum(int(np.prod(w.design_shape)) * 4 + 8 for w in wl)},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched(args)
     else:
         run_ours(args)
 

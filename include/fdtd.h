@@ -195,11 +195,14 @@ enum {
   FDTD_OPT_STAGES = 6,          /* one-plane kernels (4, 5): planes staged per CTA (2
                                    default, 3, 4): stages - 1 planes are in flight while one
                                    is computed */
-  FDTD_OPT_PDL = 7,             /* 1 (default): kernel 5 launches as a programmatic dependent
-                                   of the previous kernel (its launch and prologue overlap
-                                   the previous kernel's tail); 0: plain stream order */
-  FDTD_OPT_PREFETCH = 8         /* kernel 5: 1 = when a plane is staged, warm L2 with the
+  FDTD_OPT_PDL = 7,             /* kernel 5: 1 = launch as a programmatic dependent of the
+                                   previous kernel (its launch and prologue overlap the
+                                   previous kernel's tail); 0 (default) = plain stream order */
+  FDTD_OPT_PREFETCH = 8,        /* kernel 5: 1 = when a plane is staged, warm L2 with the
                                    next plane's boxes; 0 (default) = off */
+  FDTD_OPT_TILE_X = 9           /* kernel 5 with tile height 8 and 2 or 3 stages: tile width
+                                   32 or 40; 0 (default) = the width that leaves fewer idle
+                                   columns in the last tile along x (32 on a tie) */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -33,7 +33,8 @@ struct Layout {
 };
 
 struct GraphKey {
-  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch;
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
+      tile_x;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -75,7 +76,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch;
+      opt_prefetch, opt_tile_x;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -490,8 +491,9 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
-  h->opt_pdl = 1;
+  h->opt_pdl = 0;
   h->opt_prefetch = 0;
+  h->opt_tile_x = 0;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -596,6 +598,11 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       break;
     case FDTD_OPT_PDL: h->opt_pdl = value ? 1 : 0; break;
     case FDTD_OPT_PREFETCH: h->opt_prefetch = value ? 1 : 0; break;
+    case FDTD_OPT_TILE_X:
+      if (value != 0 && value != 32 && value != 40)
+        return fail(h, FDTD_EINVAL, "tile_x must be 0 (automatic), 32 or 40");
+      h->opt_tile_x = value;
+      break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -613,6 +620,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_STAGES: *value = h->opt_stages; break;
     case FDTD_OPT_PDL: *value = h->opt_pdl; break;
     case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
+    case FDTD_OPT_TILE_X: *value = h->opt_tile_x; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -686,6 +694,16 @@ static int lag_tile_y(const fdtd_handle* h) {
   return (h->opt_kernel == 5 && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
 }
 
+// Tile width of the two-cells-per-thread kernels: 40-wide tiles exist for a
+// tile height of 8 with 2 or 3 stages; automatic picks the width that wastes
+// fewer columns of the last tile (32 on a tie).
+static int lag_tile_x(const fdtd_handle* h) {
+  if (h->opt_kernel != 5 || lag_tile_y(h) != 8 || h->opt_stages > 3) return 32;
+  if (h->opt_tile_x) return h->opt_tile_x;
+  const int w32 = (h->nx + 31) / 32 * 32 - h->nx, w40 = (h->nx + 39) / 40 * 40 - h->nx;
+  return w40 < w32 ? 40 : 32;
+}
+
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   StepArgs a;
   memset(&a, 0, sizeof a);
@@ -710,6 +728,7 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.stages = h->opt_stages;
   a.pdl = h->opt_pdl;
   a.prefetch = h->opt_prefetch;
+  a.tile_x = lag_tile_x(h);
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
   a.err = (unsigned*)(h->ws + L.err);
   return a;
@@ -829,7 +848,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (lagk &&
       (e = encode_lag_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
                            (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
-                           a.tile_y, &lmaps)))
+                           a.tile_y, a.tile_x, &lmaps)))
     return e;
   if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
     for (int b = 0; b < 2; ++b)
@@ -929,7 +948,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                        &rmaps[b])))
       return e;
     if (rlag && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
-                                     (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y,
+                                     (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y, a.tile_x,
                                      &lrmaps[b])))
       return e;
   }
@@ -997,6 +1016,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.stages = h->opt_stages;
   key.pdl = h->opt_pdl;
   key.prefetch = h->opt_prefetch;
+  key.tile_x = h->opt_tile_x;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;

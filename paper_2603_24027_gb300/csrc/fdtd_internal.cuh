@@ -202,6 +202,7 @@ struct StepArgs {
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
   int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
+  int tile_x;      // two-cells-per-thread kernels: tile width (32 or 40 cells)
   unsigned* err;   // device error word (ERR_*)
 };
 
@@ -231,14 +232,14 @@ cudaError_t encode_split_maps(const float* F, const float* L, const float* cb, c
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
 cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s);
 
-// Tensor maps of the one-plane-per-iteration kernels: 36 x (ty+1) boxes
-// (own and one neighbour side), own boxes, and the psi boxes 36 x ty,
-// 32 x (ty+1), 32 x ty.
+// Tensor maps of the one-plane-per-iteration kernels for a tw x ty tile:
+// wide (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes,
+// and the psi boxes (tw+4) x ty, tw x (ty+1), tw x ty.
 struct alignas(64) LagMaps {
-  CUtensorMap F36, F32, L36, L32, cb36, cb32, P36, P32y, P32;
+  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Pxw, Pyw, Po;
 };
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
-                            const Geo& g, int ty, LagMaps* m);
+                            const Geo& g, int ty, int tw, LagMaps* m);
 cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 // The same half-steps with two x-cells per thread (tile height >= 2).
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);

@@ -42,11 +42,11 @@ __global__ void __launch_bounds__(32 * TY) k_lfwd_h(const __grid_constant__ LagM
     uint32_t bytes = 3 * B::P * 4 + (body ? 3 * B::OP * 4 : 0) + (body && txs ? 2 * B::OP * 4 : 0) +
                      (body && tys ? 2 * B::OP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
-    if (body) tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P32, bar, x0, y0, p, 0);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32, bar, x0, y0, p, 4);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 8);
+    tma_load_4d(st + Y::E, &m.Fw, bar, x0, y0, p, 0);
+    if (body) tma_load_4d(st + Y::H, &m.Fo, bar, x0, y0, p, 3);
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 0);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 4);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 8);
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -144,14 +144,14 @@ __global__ void __launch_bounds__(32 * TY) k_lfwd_e(const __grid_constant__ LagM
     uint32_t bytes = 3 * B::P * 4 + (body ? 4 * B::OP * 4 : 0) + (body && txs ? 2 * B::OP * 4 : 0) +
                      (body && tys ? 2 * B::OP * 4 : 0) + (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
+    tma_load_4d(st + Y::H, &m.Fw, bar, x0 - 4, y0 - 1, p, 3);
     if (body) {
-      tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
-      tma_load_4d(st + Y::CB, &m.cb32, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::E, &m.Fo, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::CB, &m.cbo, bar, x0, y0, p, 0);
     }
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P32, bar, x0, y0, p, 2);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32, bar, x0, y0, p, 6);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 10);
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Po, bar, x0, y0, p, 2);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Po, bar, x0, y0, p, 6);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 10);
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -299,16 +299,16 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_e(const __grid_constant__ LagM
                      (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
                      (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    if (hbox) tma_load_4d(st + Y::H, &m.F36, bar, x0 - 4, y0 - 1, p, 3);
+    if (hbox) tma_load_4d(st + Y::H, &m.Fw, bar, x0 - 4, y0 - 1, p, 3);
     if (lam) {
-      tma_load_4d(st + Y::CB, &m.cb36, bar, x0, y0, p, 0);
-      tma_load_4d(st + Y::LE, &m.L36, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::CB, &m.cbw, bar, x0, y0, p, 0);
+      tma_load_4d(st + Y::LE, &m.Lw, bar, x0, y0, p, 0);
     }
-    if (ebox) tma_load_4d(st + Y::E, &m.F32, bar, x0, y0, p, 0);
-    if (body) tma_load_4d(st + Y::LH, &m.L32, bar, x0, y0, p, 3);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0, y0, p, 2);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0, p, 6);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 10);
+    if (ebox) tma_load_4d(st + Y::E, &m.Fo, bar, x0, y0, p, 0);
+    if (body) tma_load_4d(st + Y::LH, &m.Lo, bar, x0, y0, p, 3);
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Pxw, bar, x0, y0, p, 2);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Pyw, bar, x0, y0, p, 6);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 10);
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -494,13 +494,13 @@ __global__ void __launch_bounds__(32 * TY) k_lrev_h(const __grid_constant__ LagM
                      (body && txs ? 2 * B::XP * 4 : 0) + (body && tys ? 2 * B::YP * 4 : 0) +
                      (zs ? 2 * B::OP * 4 : 0);
     mbar_expect_tx(bar, bytes);
-    if (ebox) tma_load_4d(st + Y::E, &m.F36, bar, x0, y0, p, 0);
-    if (head || body) tma_load_4d(st + Y::LH, &m.L36, bar, x0 - 4, y0 - 1, p, 3);
-    if (hown) tma_load_4d(st + Y::H, &m.F32, bar, x0, y0, p, 3);
-    if (body) tma_load_4d(st + Y::LE, &m.L32, bar, x0, y0, p, 0);
-    if (body && txs) tma_load_4d(st + Y::PX, &m.P36, bar, x0 - 4, y0, p, 0);
-    if (body && tys) tma_load_4d(st + Y::PY, &m.P32y, bar, x0, y0 - 1, p, 4);
-    if (zs) tma_load_4d(st + Y::PZ, &m.P32, bar, x0, y0, p, 8);
+    if (ebox) tma_load_4d(st + Y::E, &m.Fw, bar, x0, y0, p, 0);
+    if (head || body) tma_load_4d(st + Y::LH, &m.Lw, bar, x0 - 4, y0 - 1, p, 3);
+    if (hown) tma_load_4d(st + Y::H, &m.Fo, bar, x0, y0, p, 3);
+    if (body) tma_load_4d(st + Y::LE, &m.Lo, bar, x0, y0, p, 0);
+    if (body && txs) tma_load_4d(st + Y::PX, &m.Pxw, bar, x0 - 4, y0, p, 0);
+    if (body && tys) tma_load_4d(st + Y::PY, &m.Pyw, bar, x0, y0 - 1, p, 4);
+    if (zs) tma_load_4d(st + Y::PZ, &m.Po, bar, x0, y0, p, 8);
   };
   if (tid == 0)
     for (int p = R.p0; p <= R.p1 && p < R.p0 + S; ++p) issue(p);
@@ -709,17 +709,18 @@ static cudaError_t enc3(CUtensorMap* m, const float* base, const Geo& g, int nco
 }
 
 cudaError_t encode_lag_maps(const float* F, const float* Lm, const float* cb, const float* psiA,
-                            const Geo& g, int ty, LagMaps* m) {
+                            const Geo& g, int ty, int tw, LagMaps* m) {
   cudaError_t e;
-  if ((e = enc3(&m->F36, F, g, 6, 36, ty + 1, 3))) return e;
-  if ((e = enc3(&m->F32, F, g, 6, 32, ty, 3))) return e;
-  if ((e = enc3(&m->L36, Lm, g, 6, 36, ty + 1, 3))) return e;
-  if ((e = enc3(&m->L32, Lm, g, 6, 32, ty, 3))) return e;
-  if ((e = enc3(&m->cb36, cb, g, 1, 36, ty + 1, 1))) return e;
-  if ((e = enc3(&m->cb32, cb, g, 1, 32, ty, 1))) return e;
-  if ((e = enc3(&m->P36, psiA, g, 12, 36, ty, 2))) return e;
-  if ((e = enc3(&m->P32y, psiA, g, 12, 32, ty + 1, 2))) return e;
-  return enc3(&m->P32, psiA, g, 12, 32, ty, 2);
+  const int w = tw + 4;
+  if ((e = enc3(&m->Fw, F, g, 6, w, ty + 1, 3))) return e;
+  if ((e = enc3(&m->Fo, F, g, 6, tw, ty, 3))) return e;
+  if ((e = enc3(&m->Lw, Lm, g, 6, w, ty + 1, 3))) return e;
+  if ((e = enc3(&m->Lo, Lm, g, 6, tw, ty, 3))) return e;
+  if ((e = enc3(&m->cbw, cb, g, 1, w, ty + 1, 1))) return e;
+  if ((e = enc3(&m->cbo, cb, g, 1, tw, ty, 1))) return e;
+  if ((e = enc3(&m->Pxw, psiA, g, 12, w, ty, 2))) return e;
+  if ((e = enc3(&m->Pyw, psiA, g, 12, tw, ty + 1, 2))) return e;
+  return enc3(&m->Po, psiA, g, 12, tw, ty, 2);
 }
 
 }  // namespace fdtd

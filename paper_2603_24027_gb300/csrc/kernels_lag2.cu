@@ -119,30 +119,30 @@ __device__ void ring_abort(uint64_t* bars, int stg, uint32_t par, int p, int p1,
 using namespace lag2;
 
 // =================================================== forward H half-step ===
-template <int TY, int S>
-__global__ void __launch_bounds__(16 * TY) k_l2fwd_h(const __grid_constant__ LagMaps m,
+template <int TY, int S, int TW>
+__global__ void __launch_bounds__(TW / 2 * TY) k_l2fwd_h(const __grid_constant__ LagMaps m,
                                                     StepArgs a) {
-  typedef G<TY> B;
-  typedef LFH<TY, S> Y;
+  typedef G<TY, TW> B;
+  typedef LFH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
   const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
-  const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
   auto boxes = [&](int p, auto&& f) {
     const bool body = p < k1;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    f(Y::E, &m.F36, x0, y0, 0, 3 * B::P * 4);
-    if (body) f(Y::H, &m.F32, x0, y0, 3, 3 * B::OP * 4);
-    if (body && txs) f(Y::PX, &m.P32, x0, y0, 0, 2 * B::OP * 4);
-    if (body && tys) f(Y::PY, &m.P32, x0, y0, 4, 2 * B::OP * 4);
-    if (zs) f(Y::PZ, &m.P32, x0, y0, 8, 2 * B::OP * 4);
+    f(Y::E, &m.Fw, x0, y0, 0, 3 * B::P * 4);
+    if (body) f(Y::H, &m.Fo, x0, y0, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Po, x0, y0, 0, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.Po, x0, y0, 4, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.Po, x0, y0, 8, 2 * B::OP * 4);
   };
   auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
     stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= k1 && p + 1 < g.nz);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_h(const __grid_constant__ Lag
   if (sx1) { bx1 = prof(g, 0, PR_BH, x + 1); ax1 = prof(g, 0, PR_AH, x + 1); kx1 = prof(g, 0, PR_KH, x + 1); }
   if (sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
   const int hb = ty * B::W + 2 * tx;   // own pair in a hi box
-  const int ob = ty * 32 + 2 * tx;     // own pair in an own box
+  const int ob = ty * TW + 2 * tx;     // own pair in an own box
   const long long nc = g.nc;
   float* const Hx = a.F + 3 * nc;
   float* const Hy = Hx + nc;
@@ -277,19 +277,19 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_h(const __grid_constant__ Lag
 }
 
 // =================================================== forward E half-step ===
-template <int TY, int S>
-__global__ void __launch_bounds__(16 * TY) k_l2fwd_e(const __grid_constant__ LagMaps m,
+template <int TY, int S, int TW>
+__global__ void __launch_bounds__(TW / 2 * TY) k_l2fwd_e(const __grid_constant__ LagMaps m,
                                                     StepArgs a) {
-  typedef G<TY> B;
-  typedef LFE<TY, S> Y;
+  typedef G<TY, TW> B;
+  typedef LFE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
   const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
-  const bool txs = tile_in_slab(x0, min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane k0-1 only provides Ht(k0-1) at the own pair
   const int p0_ = k0 - 1, p1_ = k1 - 1;
@@ -298,14 +298,14 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_e(const __grid_constant__ Lag
   auto boxes = [&](int p, auto&& f) {
     const bool body = p >= k0;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    f(Y::H, &m.F36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
+    f(Y::H, &m.Fw, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
     if (body) {
-      f(Y::E, &m.F32, x0, y0, 0, 3 * B::OP * 4);
-      f(Y::CB, &m.cb32, x0, y0, 0, B::OP * 4);
+      f(Y::E, &m.Fo, x0, y0, 0, 3 * B::OP * 4);
+      f(Y::CB, &m.cbo, x0, y0, 0, B::OP * 4);
     }
-    if (body && txs) f(Y::PX, &m.P32, x0, y0, 2, 2 * B::OP * 4);
-    if (body && tys) f(Y::PY, &m.P32, x0, y0, 6, 2 * B::OP * 4);
-    if (zs) f(Y::PZ, &m.P32, x0, y0, 10, 2 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Po, x0, y0, 2, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.Po, x0, y0, 6, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.Po, x0, y0, 10, 2 * B::OP * 4);
   };
   auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
     stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_e(const __grid_constant__ Lag
   if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
   if (sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
   const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
-  const int ob = ty * 32 + 2 * tx;
+  const int ob = ty * TW + 2 * tx;
   const long long nc = g.nc;
   float* const Ex = a.F;
   float* const Ey = Ex + nc;
@@ -478,28 +478,28 @@ __global__ void __launch_bounds__(16 * TY) k_l2fwd_e(const __grid_constant__ Lag
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
-      for (int wv = 0; wv < (16 * TY) / 32; ++wv) t += red[wv];
+      for (int wv = 0; wv < (TW / 2 * TY) / 32; ++wv) t += red[wv];
       if (t != 0.0) atomicAdd(a.obj, t);
     }
   }
 }
 
 // ======================================== reverse E phase (+ adjoint H) ===
-template <int TY, int S>
-__global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ LagMaps m,
+template <int TY, int S, int TW>
+__global__ void __launch_bounds__(TW / 2 * TY) k_l2rev_e(const __grid_constant__ LagMaps m,
                                                     StepArgs a) {
-  typedef G<TY> B;
-  typedef LRE<TY, S> Y;
+  typedef G<TY, TW> B;
+  typedef LRE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
   const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
-  const bool txs = tile_in_slab(x0, min(x0 + 32, g.nx - 1), g.nx, g.P);
+  const bool txs = tile_in_slab(x0, min(x0 + TW, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
-  const bool tint = x0 + 31 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
   // plane k0-1: Ht(k0-1) at the own pair; planes k0..k1-1: the step proper,
   // each also finishing lam_H(p-1) with its own z-terms; plane k1 finishes
   // lam_H(k1-1).
@@ -514,16 +514,16 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
     const bool lam = body || tail;
     const bool hbox = (head || body) && (primal_plane(p) || primal_plane(p + 1));
     const bool ebox = body && primal_plane(p);
-    if (hbox) f(Y::H, &m.F36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
+    if (hbox) f(Y::H, &m.Fw, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
     if (lam) {
-      f(Y::CB, &m.cb36, x0, y0, 0, B::P * 4);
-      f(Y::LE, &m.L36, x0, y0, 0, 3 * B::P * 4);
+      f(Y::CB, &m.cbw, x0, y0, 0, B::P * 4);
+      f(Y::LE, &m.Lw, x0, y0, 0, 3 * B::P * 4);
     }
-    if (ebox) f(Y::E, &m.F32, x0, y0, 0, 3 * B::OP * 4);
-    if (body) f(Y::LH, &m.L32, x0, y0, 3, 3 * B::OP * 4);
-    if (body && txs) f(Y::PX, &m.P36, x0, y0, 2, 2 * B::XP * 4);
-    if (body && tys) f(Y::PY, &m.P32y, x0, y0, 6, 2 * B::YP * 4);
-    if (zs) f(Y::PZ, &m.P32, x0, y0, 10, 2 * B::OP * 4);
+    if (ebox) f(Y::E, &m.Fo, x0, y0, 0, 3 * B::OP * 4);
+    if (body) f(Y::LH, &m.Lo, x0, y0, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Pxw, x0, y0, 2, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.Pyw, x0, y0, 6, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.Po, x0, y0, 10, 2 * B::OP * 4);
   };
   auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
     stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
   const int dX = a.dhi[0] - a.dlo[0], dY = a.dhi[1] - a.dlo[1];
   const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
   const int hb = ty * B::W + 2 * tx;             // own pair in a hi box
-  const int ob = ty * 32 + 2 * tx;
+  const int ob = ty * TW + 2 * tx;
   const long long nc = g.nc;
   float* const Ex = a.F;
   float* const LHx = a.L + 3 * nc;
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
         }
         if (x + 2 >= g.nx) { n9x = 0.f; n10x = 0.f; }
         if (sy || sy1) {
-          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // 32 x (TY+1) at (x0, y0)
+          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0)
           if (sy) {
             const float2 p0 = ld2(P, ob), p1 = ld2(P + B::YP, ob);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
             st2(lpB + 7 * nc, q, s11[0], s11[1], true, v1);
           }
           if (sy1) {
-            const float2 p0 = ld2(P, ob + 32), p1 = ld2(P + B::YP, ob + 32);
+            const float2 p0 = ld2(P, ob + TW), p1 = ld2(P + B::YP, ob + TW);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
             float dummy;
 #pragma unroll
@@ -685,8 +685,8 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
           }
         }
         if (sx0 || sx1 || sx2) {
-          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // 36 x TY at (x0, y0)
-          const int xb = ty * 36 + 2 * tx;
+          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0, y0)
+          const int xb = ty * B::W + 2 * tx;
           const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
           float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
           if (sx0) {
@@ -785,21 +785,21 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_e(const __grid_constant__ Lag
 }
 
 // ======================================== reverse H phase (+ adjoint E) ===
-template <int TY, int S>
-__global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ LagMaps m,
+template <int TY, int S, int TW>
+__global__ void __launch_bounds__(TW / 2 * TY) k_l2rev_h(const __grid_constant__ LagMaps m,
                                                     StepArgs a) {
-  typedef G<TY> B;
-  typedef LRH<TY, S> Y;
+  typedef G<TY, TW> B;
+  typedef LRH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
   const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
-  const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + 31, g.nx - 1), g.nx, g.P);
+  const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
-  const bool tint = x0 + 31 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
   // plane k0-1: lam_H(k0-1) terms for the -z neighbour; planes k0..k1-1: the
   // step proper; plane p > k0 also finishes the primal Ht(p-1) with E(p).
   const int p0_ = k0 - 1, p1_ = k1;
@@ -812,13 +812,13 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (head || body);
     const bool ebox = (body && primal_plane(p)) || (tail && primal_plane(p - 1));
     const bool hown = body && primal_plane(p);
-    if (ebox) f(Y::E, &m.F36, x0, y0, 0, 3 * B::P * 4);
-    if (head || body) f(Y::LH, &m.L36, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
-    if (hown) f(Y::H, &m.F32, x0, y0, 3, 3 * B::OP * 4);
-    if (body) f(Y::LE, &m.L32, x0, y0, 0, 3 * B::OP * 4);
-    if (body && txs) f(Y::PX, &m.P36, x0 - 4, y0, 0, 2 * B::XP * 4);
-    if (body && tys) f(Y::PY, &m.P32y, x0, y0 - 1, 4, 2 * B::YP * 4);
-    if (zs) f(Y::PZ, &m.P32, x0, y0, 8, 2 * B::OP * 4);
+    if (ebox) f(Y::E, &m.Fw, x0, y0, 0, 3 * B::P * 4);
+    if (head || body) f(Y::LH, &m.Lw, x0 - 4, y0 - 1, 3, 3 * B::P * 4);
+    if (hown) f(Y::H, &m.Fo, x0, y0, 3, 3 * B::OP * 4);
+    if (body) f(Y::LE, &m.Lo, x0, y0, 0, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Pxw, x0 - 4, y0, 0, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.Pyw, x0, y0 - 1, 4, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.Po, x0, y0, 8, 2 * B::OP * 4);
   };
   auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
     stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
   const bool xyin1 = v1 && yin && x + 1 >= g.P && x + 1 < g.nx - g.P;
   const int lb = (ty + 1) * B::W + 2 * tx + 4;
   const int hb = ty * B::W + 2 * tx;
-  const int ob = ty * 32 + 2 * tx;
+  const int ob = ty * TW + 2 * tx;
   const float S_ = g.S;
   const long long nc = g.nc;
   float* const Hx = a.F + 3 * nc;
@@ -920,8 +920,8 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
         if (y == 0) { m0[0] = 0.f; m0[1] = 0.f; m5[0] = 0.f; m5[1] = 0.f; }
         if (x == 0) { m3x = 0.f; m4x = 0.f; }
         if (sy || sym) {
-          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // 32 x (TY+1) at (x0, y0-1)
-          const int yb = (ty + 1) * 32 + 2 * tx;
+          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0-1)
+          const int yb = (ty + 1) * TW + 2 * tx;
           if (sy) {
             const float2 p0 = ld2(P, yb), p1 = ld2(P + B::YP, yb);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
             st2(lpB + 5 * nc, q, s5[0], s5[1], true, v1);
           }
           if (sym) {
-            const float2 p0 = ld2(P, yb - 32), p1 = ld2(P + B::YP, yb - 32);
+            const float2 p0 = ld2(P, yb - TW), p1 = ld2(P + B::YP, yb - TW);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
             float dummy;
 #pragma unroll
@@ -946,8 +946,8 @@ __global__ void __launch_bounds__(16 * TY) k_l2rev_h(const __grid_constant__ Lag
           }
         }
         if (sx0 || sx1 || sxm) {
-          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // 36 x TY at (x0-4, y0)
-          const int xb = ty * 36 + 2 * tx + 4;
+          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0-4, y0)
+          const int xb = ty * B::W + 2 * tx + 4;
           const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
           float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
           if (sx0) {
@@ -1056,15 +1056,16 @@ static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStr
   return cudaLaunchKernelEx(&cfg, kernel, m, a);
 }
 
-template <int TY, int S>
+template <int TY, int S, int TW = 32>
 static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
-  dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
-  dim3 block(16, TY);
+  static_assert((TW / 2 * TY) % 32 == 0, "a CTA is a whole number of warps");
+  dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
+  dim3 block(TW / 2, TY);
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S>, grid, block, LFH<TY, S>::smem(), s, m, a);
-    case 1: return launch_ex(k_l2fwd_e<TY, S>, grid, block, LFE<TY, S>::smem(), s, m, a);
-    case 2: return launch_ex(k_l2rev_e<TY, S>, grid, block, LRE<TY, S>::smem(), s, m, a);
-    case 3: return launch_ex(k_l2rev_h<TY, S>, grid, block, LRH<TY, S>::smem(), s, m, a);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S, TW>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S, TW>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -1075,6 +1076,10 @@ static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
 // heights 2, 4 and 8; height 16 runs with 3.
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   const int S = a.stages;
+  if (a.tile_x == 40) {   // 40-wide tiles: tile height 8 only (whole warps), 2 or 3 stages
+    if (a.tile_y != 8) return cudaErrorInvalidValue;
+    return S == 3 ? launch_lag2_t<8, 3, 40>(which, m, a, s) : launch_lag2_t<8, 2, 40>(which, m, a, s);
+  }
   switch (a.tile_y) {
     case 2: return S == 2 ? launch_lag2_t<2, 2>(which, m, a, s)
                  : S == 4 ? launch_lag2_t<2, 4>(which, m, a, s) : launch_lag2_t<2, 3>(which, m, a, s);

@@ -76,14 +76,15 @@ __device__ void ring_drain(const Ring<S>& r, int p_waited, unsigned* err) {
   }
 }
 
-// Box geometry: "lo" boxes start at (x0-4, y0-1) and cover own, -x, -y;
-// "hi" boxes start at (x0, y0) and cover own, +x, +y.  Both are 36 x (TY+1).
-template <int TY>
+// Box geometry of a TW x TY tile: "lo" boxes start at (x0-4, y0-1) and cover
+// own, -x, -y; "hi" boxes start at (x0, y0) and cover own, +x, +y.  Both are
+// (TW+4) x (TY+1).
+template <int TY, int TW = 32>
 struct G {
-  static constexpr int W = 36, R = TY + 1, P = W * R;   // 36-wide box plane
-  static constexpr int OP = 32 * TY;                     // own box plane
-  static constexpr int XP = 36 * TY;                     // 36 x TY psi box (x neighbour)
-  static constexpr int YP = 32 * (TY + 1);               // 32 x (TY+1) psi box (y neighbour)
+  static constexpr int W = TW + 4, R = TY + 1, P = W * R;   // wide box plane
+  static constexpr int OP = TW * TY;                         // own box plane
+  static constexpr int XP = W * TY;                          // (TW+4) x TY psi box (x neighbour)
+  static constexpr int YP = TW * (TY + 1);                   // TW x (TY+1) psi box (y neighbour)
 };
 
 }  // namespace lag
@@ -92,9 +93,9 @@ using namespace lag;
 
 // Stage layouts (byte offsets of each box in one ring stage).
 // Forward H half-step: E hi box, Ht own, psi_H own boxes of the three axes.
-template <int TY, int S>
+template <int TY, int S, int TW = 32>
 struct LFH {
-  typedef G<TY> g_;
+  typedef G<TY, TW> g_;
   static constexpr int E = 0;                                  // E hi box, 3 comps
   static constexpr int H = r128(3 * g_::P * 4);                // H own
   static constexpr int PX = H + r128(3 * g_::OP * 4);          // psi_H own x/y/z, 2 comps
@@ -106,9 +107,9 @@ struct LFH {
 
 // Forward E half-step: Ht lo box, E and cb own, psi_E own boxes; a small
 // tail holds the per-warp objective partial sums.
-template <int TY, int S>
+template <int TY, int S, int TW = 32>
 struct LFE {
-  typedef G<TY> g_;
+  typedef G<TY, TW> g_;
   static constexpr int H = 0;                                  // Ht lo box
   static constexpr int E = r128(3 * g_::P * 4);                // E own
   static constexpr int CB = E + r128(3 * g_::OP * 4);          // cb own
@@ -121,9 +122,9 @@ struct LFE {
 
 // Reverse E phase: Ht lo box, E own, cb and lam_E hi boxes, lam_H own,
 // lam_psi_E boxes that reach the +x / +y neighbour.
-template <int TY, int S>
+template <int TY, int S, int TW = 32>
 struct LRE {
-  typedef G<TY> g_;
+  typedef G<TY, TW> g_;
   static constexpr int H = 0;                                  // Ht lo box
   static constexpr int E = r128(3 * g_::P * 4);                // E own
   static constexpr int CB = E + r128(3 * g_::OP * 4);          // cb hi box
@@ -138,9 +139,9 @@ struct LRE {
 
 // Reverse H phase: E hi box, Ht own, lam_H lo box, lam_E own, lam_psi_H
 // boxes that reach the -x / -y neighbour.
-template <int TY, int S>
+template <int TY, int S, int TW = 32>
 struct LRH {
-  typedef G<TY> g_;
+  typedef G<TY, TW> g_;
   static constexpr int E = 0;                                  // E hi box
   static constexpr int H = r128(3 * g_::P * 4);                // Ht own
   static constexpr int LH = H + r128(3 * g_::OP * 4);          // lam_H lo box

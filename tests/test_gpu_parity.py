@@ -197,6 +197,20 @@ def test_codec_is_bit_exact_against_torch_casts(F, A, dtype, scaled):
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("tile_x,stages", [(32, 2), (40, 2), (40, 3)])
+@pytest.mark.parametrize("name", ["ragged_poynting", "ragged_e2_point"])
+def test_tile_widths_do_not_change_results(F, A, tile_x, stages, name):
+    """Two-cells-per-thread kernels with 32- and 40-wide tiles (8 rows)
+    against the reference kernel variant."""
+    w = SMALL[name]()
+    rec = A.record_cfg("bf16", 2, "linear")
+    base = gpu_run(F, A, w, rec=rec, options={A.OPT_KERNEL: 0})
+    r = gpu_run(F, A, w, rec=rec, options={A.OPT_KERNEL: 5, A.OPT_TILE_Y: 8,
+                                           A.OPT_TILE_X: tile_x, A.OPT_STAGES: stages})
+    np.testing.assert_array_equal(r["fields"], base["fields"])
+    same_gradient(r["g"], base["g"])
+
+
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     w = SMALL["ragged_poynting"]()
