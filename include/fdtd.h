@@ -201,8 +201,7 @@ enum {
   FDTD_OPT_PREFETCH = 8,        /* kernel 5: 1 = when a plane is staged, warm L2 with the
                                    next plane's boxes; 0 (default) = off */
   FDTD_OPT_TILE_X = 9           /* kernel 5 with tile height 8 and 2 or 3 stages: tile width
-                                   32 or 40; 0 (default) = the width that leaves fewer idle
-                                   columns in the last tile along x (32 on a tie) */
+                                   32 (default) or 40 cells */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

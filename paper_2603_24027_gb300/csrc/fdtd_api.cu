@@ -493,7 +493,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_stages = 2;
   h->opt_pdl = 0;
   h->opt_prefetch = 0;
-  h->opt_tile_x = 0;
+  h->opt_tile_x = 32;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -599,8 +599,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
     case FDTD_OPT_PDL: h->opt_pdl = value ? 1 : 0; break;
     case FDTD_OPT_PREFETCH: h->opt_prefetch = value ? 1 : 0; break;
     case FDTD_OPT_TILE_X:
-      if (value != 0 && value != 32 && value != 40)
-        return fail(h, FDTD_EINVAL, "tile_x must be 0 (automatic), 32 or 40");
+      if (value != 32 && value != 40) return fail(h, FDTD_EINVAL, "tile_x must be 32 or 40");
       h->opt_tile_x = value;
       break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
@@ -695,13 +694,10 @@ static int lag_tile_y(const fdtd_handle* h) {
 }
 
 // Tile width of the two-cells-per-thread kernels: 40-wide tiles exist for a
-// tile height of 8 with 2 or 3 stages; automatic picks the width that wastes
-// fewer columns of the last tile (32 on a tie).
+// tile height of 8 with 2 or 3 stages, otherwise 32.
 static int lag_tile_x(const fdtd_handle* h) {
   if (h->opt_kernel != 5 || lag_tile_y(h) != 8 || h->opt_stages > 3) return 32;
-  if (h->opt_tile_x) return h->opt_tile_x;
-  const int w32 = (h->nx + 31) / 32 * 32 - h->nx, w40 = (h->nx + 39) / 40 * 40 - h->nx;
-  return w40 < w32 ? 40 : 32;
+  return h->opt_tile_x == 40 ? 40 : 32;
 }
 
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {

@@ -31,7 +31,7 @@ def main(argv=None):
     p.add_argument("--stages", type=int, default=2)
     p.add_argument("--pdl", type=int, default=0)
     p.add_argument("--prefetch", type=int, default=0)
-    p.add_argument("--tile-x", type=int, default=0)
+    p.add_argument("--tile-x", type=int, default=32)
     p.add_argument("--tape", default="bf16:4:linear")
     p.add_argument("--pml", type=int, default=0)
     p.add_argument("--warmup", type=int, default=0)

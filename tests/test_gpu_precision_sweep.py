@@ -38,3 +38,25 @@ def test_sweep_waveguide_device():
     # cubic interpolation beats linear at every k > 1
     for k in (4, 8, 16):
         assert by[("f32", k, "cubic")]["grad_rel_err"] < by[("f32", k, "linear")]["grad_rel_err"]
+
+
+def test_paper_format_grid_ordering():
+    """Sec. 4 (Fig. 3) with the paper's unscaled formats: float16, bfloat16
+    and e4m3b11fnuz stay with float32, e5m2fnuz close behind, and the formats
+    with coarse subnormals degrade in the order of their smallest subnormal
+    (e4m3fnuz 2^-10, IEEE e4m3 2^-9, e3m4 2^-6) already at k = 1."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2603_24027_gb300 import build as B
+    B.build()
+    rows, _ = PS.run_seed(0, 2000, dtypes=PS.PAPER_DTYPES, ks=[1, 16], interps=["linear"],
+                          scaled=False, oracle=False)
+    c = {(r["dtype"], r["k"]): r["cos_fp32_k1"] for r in rows}
+    for dt in ("f16", "bf16", "e4m3b11fnuz"):
+        assert c[(dt, 1)] > 0.99999, (dt, c[(dt, 1)])
+        assert abs(c[(dt, 16)] - c[("f32", 16)]) < 5e-4
+    assert c[("e5m2fnuz", 1)] > 0.99995
+    assert c[("e4m3b11fnuz", 1)] > c[("e4m3fnuz", 1)] > c[("e4m3ieee", 1)] > c[("e3m4", 1)]
+    assert c[("e3m4", 1)] < 0.99
+    comp = {(r["dtype"], r["k"]): r["compression"] for r in rows}
+    assert comp[("e4m3b11fnuz", 16)] == pytest.approx(64.0)
