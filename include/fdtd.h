@@ -58,7 +58,8 @@ typedef struct {
   double alpha_factor;
 } fdtd_pml;
 
-enum { FDTD_SRC_NONE = 0, FDTD_SRC_POINT = 1, FDTD_SRC_PLANE_GAUSS = 2 };
+enum { FDTD_SRC_NONE = 0, FDTD_SRC_POINT = 1, FDTD_SRC_PLANE_GAUSS = 2,
+       FDTD_SRC_PLANE_UNIFORM = 3 };
 
 /* Current source J entering E += (S/eps)(curl Ht - J).
  * J^{n+1/2} = amplitude w(u,v) g((n+1/2) dt),
@@ -67,7 +68,10 @@ enum { FDTD_SRC_NONE = 0, FDTD_SRC_POINT = 1, FDTD_SRC_PLANE_GAUSS = 2 };
  * t0 = t0_over_tau tau.
  * POINT: w = 1 at pos.  PLANE_GAUSS: plane normal `axis` at pos[axis];
  * w = exp(-(u-pos_u)^2/(2 su^2) - (v-pos_v)^2/(2 sv^2)) over the interior
- * cross-section, (u,v) the other two axes in increasing order. */
+ * cross-section, (u,v) the other two axes in increasing order.
+ * PLANE_UNIFORM: the same plane with w = 1 over the interior cross-section,
+ * a normally incident plane wave (the paper's coupler source, Sec. 4);
+ * sigma_uv is ignored. */
 typedef struct {
   int kind;
   int component;          /* 0..2 = Ex, Ey, Ez */
@@ -176,6 +180,24 @@ const char* fdtd_last_error(const fdtd_handle* h);
 /* Release host resources and CUDA objects (not the caller's memory). */
 int fdtd_destroy(fdtd_handle* h);
 
+/* ------------------------------------------------- second detector --- */
+
+/* Attach a second detector plane (NULL or kind 0 detaches it), e.g. the
+ * input-side flux of a transmission ratio (Sec. 4 measures the Poynting flux
+ * above the coupler and in its output waveguide).  Its objective
+ * M = sum_n m_n accumulates in each forward alongside L (one extra launch per
+ * step).  Same validation as the create detector (FDTD_EINVAL).  Host only;
+ * invalidates a pending forward. */
+int fdtd_set_detector2(fdtd_handle* h, const fdtd_detector* detector2);
+/* L and M of the last forward (M = 0 without a second detector).
+ * FDTD_ESTATE before the first forward. */
+int fdtd_objectives(const fdtd_handle* h, double* L, double* M);
+/* Backward for the objective seed * L + seed2 * M: d_grad_eps receives
+ * d(seed L + seed2 M)/d(eps) over the design box (one time-reversed run; the
+ * seeds enter as the detectors' adjoint sources).  seed2 != 0 without a
+ * second detector: FDTD_ESTATE.  Otherwise as fdtd_backward. */
+int fdtd_backward2(fdtd_handle* h, double seed, double seed2, float* d_grad_eps);
+
 /* ------------------------------------------------ tuning and timing --- */
 
 enum {
@@ -210,7 +232,7 @@ int fdtd_get_option(const fdtd_handle* h, int option, int* value);
 enum {
   FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
   FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_FUSED_FWD = 6, FDTD_K_FUSED_REV = 7,
-  FDTD_K_KINDS = 8
+  FDTD_K_MONITOR = 8, FDTD_K_KINDS = 9
 };
 /* Average in-loop cost (ms) per launch of one kernel kind in the last
  * forward + backward, and the number of samples it rests on

@@ -47,7 +47,7 @@ typedef struct {
   double sigma_factor;     /* sigma_max = sigma_factor*(m+1)/(eta0*dx) */
   double kappa_max;
   double alpha_factor;     /* alpha_max*dt/eps0 = alpha_factor * 2*pi*f0*dt */
-  int src_kind;            /* 0 none, 1 point, 2 Gaussian plane */
+  int src_kind;            /* 0 none, 1 point, 2 Gaussian plane, 3 uniform plane (plane wave) */
   int src_comp;            /* 0..2 = Ex..Ez */
   int src_axis;            /* plane normal for kind 2 */
   int src_pos[3];
@@ -56,6 +56,9 @@ typedef struct {
   int det_kind;            /* 1 |E|^2, 2 Poynting along the plane normal */
   int det_axis, det_index, det_lo[2], det_hi[2];
   int dlo[3], dhi[3];      /* design box, half-open */
+  /* optional second detector (kind 0 = none), e.g. the input-side flux of a
+   * transmission ratio; its objective is M = sum_n m_n */
+  int det2_kind, det2_axis, det2_index, det2_lo[2], det2_hi[2];
 } ocfg;
 
 /* ------------------------------------------------------------ helpers ---- */
@@ -184,7 +187,9 @@ int oracle_source_weight(const ocfg* c, double* w) {
   memset(w, 0, ncell(c) * sizeof(double));
   if (c->src_kind == 1) {
     w[idx(c, c->src_pos[0], c->src_pos[1], c->src_pos[2])] = 1.0;
-  } else if (c->src_kind == 2) {
+  } else if (c->src_kind == 2 || c->src_kind == 3) {
+    /* a sheet over the plane's interior cross-section: Gaussian profile
+     * (kind 2) or uniform, a normally incident plane wave (kind 3) */
     int a = c->src_axis;
     int ua = a == 0 ? 1 : 0, va = a == 2 ? 1 : 2;
     int P = c->P;
@@ -193,7 +198,7 @@ int oracle_source_weight(const ocfg* c, double* w) {
         double du = (u - c->src_pos[ua]) / c->src_sigma[0];
         double dv = (v - c->src_pos[va]) / c->src_sigma[1];
         int p[3]; p[a] = c->src_pos[a]; p[ua] = u; p[va] = v;
-        w[idx(c, p[0], p[1], p[2])] = exp(-0.5 * (du * du + dv * dv));
+        w[idx(c, p[0], p[1], p[2])] = c->src_kind == 3 ? 1.0 : exp(-0.5 * (du * du + dv * dv));
       }
   }
   return 0;
@@ -488,21 +493,43 @@ int oracle_step_adjoint(const ocfg* c, const double* eps, double* lam) {
  * because E^{n+1} = E^n + (S/eps) X and d(S/eps)/d(eps) = -(S/eps)/eps.
  * grad: design box [dz][dy][dx], multiplied by seed.  obj: L.
  */
-int oracle_gradient(const ocfg* c, const double* eps, double seed, double* grad, double* obj,
-                    double* final_state) {
+/* The second detector as a configuration of its own (same grid, det_* of
+ * the second detector), so the plane helpers above serve both. */
+static ocfg second_detector(const ocfg* c) {
+  ocfg d = *c;
+  d.det_kind = c->det2_kind;
+  d.det_axis = c->det2_axis;
+  d.det_index = c->det2_index;
+  d.det_lo[0] = c->det2_lo[0]; d.det_lo[1] = c->det2_lo[1];
+  d.det_hi[0] = c->det2_hi[0]; d.det_hi[1] = c->det2_hi[1];
+  return d;
+}
+
+/* Stored-history gradient of seed * L + seed2 * M (M from the second
+ * detector when det2_kind != 0).  obj2 (optional): {L, M}. */
+int oracle_gradient2(const ocfg* c, const double* eps, double seed, double seed2, double* grad,
+                     double* obj2, double* final_state) {
   size_t N = ncell(c);
   int dX = c->dhi[0] - c->dlo[0], dY = c->dhi[1] - c->dlo[1], dZ = c->dhi[2] - c->dlo[2];
   size_t nd = (size_t)dX * dY * dZ;
-  int nu = c->det_hi[0] - c->det_lo[0], nv = c->det_hi[1] - c->det_lo[1];
-  size_t np = (size_t)nu * nv;
   int T = c->n_steps;
+  const ocfg c2 = second_detector(c);
+  const int nd2 = c->det2_kind ? 2 : 1;
+  const ocfg* dc[2] = {c, &c2};
+  int nu[2], nv[2];
+  size_t np[2];
+  for (int t = 0; t < 2; ++t) {
+    nu[t] = dc[t]->det_hi[0] - dc[t]->det_lo[0];
+    nv[t] = dc[t]->det_hi[1] - dc[t]->det_lo[1];
+    np[t] = t < nd2 ? (size_t)nu[t] * nv[t] : 0;
+  }
   octx x;
   if (ctx_init(&x, c)) { ctx_free(&x); return -2; }
   double* st = (double*)calloc(NF * N, sizeof(double));
   double* lam = (double*)calloc(NF * N, sizeof(double));
   double* tmp = (double*)malloc(6 * N * sizeof(double));
   double* hist = (double*)malloc((size_t)(T + 1) * 3 * nd * sizeof(double));
-  double* dets = (double*)malloc((size_t)T * 6 * np * sizeof(double));
+  double* dets = (double*)malloc((size_t)T * 6 * (np[0] + np[1]) * sizeof(double));
   double* plane = (double*)calloc(NF * N, sizeof(double));   /* scratch for seeds */
   if (!st || !lam || !tmp || !hist || !dets || !plane) {
     free(st); free(lam); free(tmp); free(hist); free(dets); free(plane); ctx_free(&x);
@@ -515,31 +542,42 @@ int oracle_gradient(const ocfg* c, const double* eps, double seed, double* grad,
         for (int ii = 0; ii < dX; ++ii)                                          \
           hist[((size_t)(slot) * 3 + e) * nd + ((size_t)kk * dY + jj) * dX + ii] = \
               st[e * N + idx(c, c->dlo[0] + ii, c->dlo[1] + jj, c->dlo[2] + kk)];
-  double L = 0.0;
+  /* detector t's plane fields of step n live at dets + n*6*(np0+np1) + t*6*np0 */
+#define DET_AT(n, t, f, v, u) \
+  dets[(size_t)(n) * 6 * (np[0] + np[1]) + (size_t)(t) * 6 * np[0] + (size_t)(f) * np[t] + \
+       (size_t)(v) * nu[t] + (u)]
+  double Ls[2] = {0.0, 0.0};
   SAVE_DESIGN(0);
   for (int n = 0; n < T; ++n) {
     h_update(&x, st);
     e_update(&x, eps, st, n);
-    L += objective(c, st);
+    for (int t = 0; t < nd2; ++t) {
+      Ls[t] += objective(dc[t], st);
+      for (int f = 0; f < 6; ++f)
+        for (int v = 0; v < nv[t]; ++v)
+          for (int u = 0; u < nu[t]; ++u) {
+            int i, j, k;
+            det_cell(dc[t], dc[t]->det_lo[0] + u, dc[t]->det_lo[1] + v, &i, &j, &k);
+            DET_AT(n, t, f, v, u) = st[f * N + idx(c, i, j, k)];
+          }
+    }
     SAVE_DESIGN(n + 1);
-    for (int f = 0; f < 6; ++f)
-      for (int v = 0; v < nv; ++v)
-        for (int u = 0; u < nu; ++u) {
-          int i, j, k; det_cell(c, c->det_lo[0] + u, c->det_lo[1] + v, &i, &j, &k);
-          dets[((size_t)n * 6 + f) * np + (size_t)v * nu + u] = st[f * N + idx(c, i, j, k)];
-        }
   }
   if (final_state) memcpy(final_state, st, NF * N * sizeof(double));
   for (size_t q = 0; q < nd; ++q) grad[q] = 0.0;
+  const double seeds[2] = {seed, seed2};
   for (int n = T - 1; n >= 0; --n) {
-    /* seed from the stored plane fields (E^{n+1}, Ht^{n+1/2}) */
-    for (int f = 0; f < 6; ++f)
-      for (int v = 0; v < nv; ++v)
-        for (int u = 0; u < nu; ++u) {
-          int i, j, k; det_cell(c, c->det_lo[0] + u, c->det_lo[1] + v, &i, &j, &k);
-          plane[f * N + idx(c, i, j, k)] = dets[((size_t)n * 6 + f) * np + (size_t)v * nu + u];
-        }
-    objective_seed(c, plane, seed, lam);
+    /* seed from the stored plane fields (E^{n+1}, Ht^{n+1/2}) of each detector */
+    for (int t = 0; t < nd2; ++t) {
+      for (int f = 0; f < 6; ++f)
+        for (int v = 0; v < nv[t]; ++v)
+          for (int u = 0; u < nu[t]; ++u) {
+            int i, j, k;
+            det_cell(dc[t], dc[t]->det_lo[0] + u, dc[t]->det_lo[1] + v, &i, &j, &k);
+            plane[f * N + idx(c, i, j, k)] = DET_AT(n, t, f, v, u);
+          }
+      objective_seed(dc[t], plane, seeds[t], lam);
+    }
     /* gradient with lam_E^{n+1} (seeded, before this step's transposes) */
     for (int kk = 0; kk < dZ; ++kk)
       for (int jj = 0; jj < dY; ++jj)
@@ -557,10 +595,22 @@ int oracle_gradient(const ocfg* c, const double* eps, double seed, double* grad,
     adj_h_transpose(&x, lam, tmp);
   }
 #undef SAVE_DESIGN
-  if (obj) *obj = L;
+#undef DET_AT
+  if (obj2) { obj2[0] = Ls[0]; obj2[1] = Ls[1]; }
   free(st); free(lam); free(tmp); free(hist); free(dets); free(plane);
   ctx_free(&x);
   return 0;
+}
+
+/* The single-objective gradient: seed * dL/d(eps) (second detector ignored). */
+int oracle_gradient(const ocfg* c, const double* eps, double seed, double* grad, double* obj,
+                    double* final_state) {
+  ocfg one = *c;
+  one.det2_kind = 0;
+  double o2[2];
+  int rc = oracle_gradient2(&one, eps, seed, 0.0, grad, o2, final_state);
+  if (obj) *obj = o2[0];
+  return rc;
 }
 
 /* ----------------------------------------------------- quantisers ----

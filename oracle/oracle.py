@@ -37,6 +37,8 @@ class OCfg(C.Structure):
         ("det_kind", C.c_int), ("det_axis", C.c_int), ("det_index", C.c_int),
         ("det_lo", C.c_int * 2), ("det_hi", C.c_int * 2),
         ("dlo", C.c_int * 3), ("dhi", C.c_int * 3),
+        ("det2_kind", C.c_int), ("det2_axis", C.c_int), ("det2_index", C.c_int),
+        ("det2_lo", C.c_int * 2), ("det2_hi", C.c_int * 2),
     ]
 
 
@@ -58,6 +60,7 @@ def lib():
         L.oracle_step_adjoint.argtypes = [cp, dp, dp]
         L.oracle_unstep.argtypes = [cp, dp, dp, C.c_int]
         L.oracle_gradient.argtypes = [cp, dp, C.c_double, dp, dp, dp]
+        L.oracle_gradient2.argtypes = [cp, dp, C.c_double, C.c_double, dp, dp, dp]
         L.oracle_reverse.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      dp, dp, dp]
         L.oracle_quantize_array.argtypes = [C.c_int, dp, dp, C.c_long]
@@ -105,6 +108,11 @@ def make_cfg(w, periodic: int = 0, pml=None, n_steps=None) -> OCfg:
     c.det_hi[:] = list(w.det_hi)
     c.dlo[:] = list(w.design_lo)
     c.dhi[:] = list(w.design_hi)
+    c.det2_kind = w.det2_kind
+    c.det2_axis = w.det2_axis
+    c.det2_index = w.det2_index
+    c.det2_lo[:] = list(w.det2_lo)
+    c.det2_hi[:] = list(w.det2_hi)
     return c
 
 
@@ -189,6 +197,16 @@ def gradient(w, seed: float = 1.0, want_state: bool = False, **kw):
     _check(lib().oracle_gradient(C.byref(c), _dp(_eps(w)), seed, _dp(g), _dp(obj),
                                  _dp(fs) if want_state else None))
     return (float(obj[0]), g, fs) if want_state else (float(obj[0]), g)
+
+
+def gradient2(w, seed: float = 1.0, seed2: float = 0.0, **kw):
+    """Stored-history gradient of seed * L + seed2 * M, where M is the
+    objective of the workload's second detector.  Returns (L, M, grad)."""
+    c = make_cfg(w, **kw)
+    g = np.zeros(w.design_shape)
+    obj = np.zeros(2)
+    _check(lib().oracle_gradient2(C.byref(c), _dp(_eps(w)), seed, seed2, _dp(g), _dp(obj), None))
+    return float(obj[0]), float(obj[1]), g
 
 
 def n_samples(n_steps: int, k: int) -> int:

@@ -23,9 +23,10 @@ TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4,
 INTERP = {"linear": 0, "cubic": 1}
 OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS, OPT_STAGES, OPT_PDL, \
     OPT_PREFETCH, OPT_TILE_X = range(10)
-K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV = range(8)
+K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV, K_MONITOR = \
+    range(9)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "fused_fwd",
-                "fused_rev"]
+                "fused_rev", "monitor"]
 
 
 class Grid(C.Structure):
@@ -72,6 +73,9 @@ _PROTOS = {
     "fdtd_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                C.POINTER(C.c_double)]),
     "fdtd_backward": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
+    "fdtd_backward2": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p]),
+    "fdtd_set_detector2": (C.c_int, [C.c_void_p, C.POINTER(Detector)]),
+    "fdtd_objectives": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fdtd_value_and_grad_host": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                            C.c_double, C.POINTER(C.c_double), C.c_void_p]),
     "fdtd_group_forward": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),

@@ -26,7 +26,8 @@ namespace {
 const double kC0 = 299792458.0;
 
 struct Layout {
-  size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, prof, srcw, tape, scales, err;
+  size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, obj2, seeds, prof, srcw, tape,
+      scales, err;
   size_t total;
   long long stride;   // tape elements per sample
   int J;              // samples
@@ -59,6 +60,8 @@ struct fdtd_handle {
   fdtd_pml pml;
   fdtd_source src;
   fdtd_detector det;
+  fdtd_detector det2;         // optional second detector (kind 0 = none)
+  double seeds[2];            // backward seeds of the two detectors (host copy)
   int dlo[3], dhi[3];
   cudaStream_t user_stream;
 
@@ -95,6 +98,7 @@ struct fdtd_handle {
   int launches_fwd, launches_bwd;
   float fwd_ms, bwd_ms;
   std::vector<double> obj_hist;
+  double obj2_sum;            // second detector's objective of the last forward
   std::string err;
 };
 
@@ -205,7 +209,8 @@ static void build_source(fdtd_handle* h) {
       for (int u = 0; u < nu; ++u) {
         double ru = (h->src_u0 + u - s.pos[ua]) / s.sigma_uv[0];
         double rv = (h->src_v0 + v - s.pos[va]) / s.sigma_uv[1];
-        h->srcw[(size_t)v * nu + u] = (float)exp(-0.5 * (ru * ru + rv * rv));
+        h->srcw[(size_t)v * nu + u] =
+            s.kind == FDTD_SRC_PLANE_UNIFORM ? 1.f : (float)exp(-0.5 * (ru * ru + rv * rv));
       }
   }
 }
@@ -365,6 +370,8 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   L.gacc = off; off += al(nd * sizeof(double));
   L.gout = off; off += al(nd * sizeof(float));
   L.obj = off; off += al((size_t)h->N * sizeof(double));
+  L.obj2 = off; off += al((size_t)h->N * sizeof(double));
+  L.seeds = off; off += al(2 * sizeof(double));
   L.prof = off; off += al(h->prof.size() * sizeof(float));
   L.srcw = off; off += al((h->srcw.size() + 1) * sizeof(float));
   L.err = off; off += 256;
@@ -404,6 +411,20 @@ static int check_rec(fdtd_handle* h, const fdtd_record_cfg* rec) {
 }
 
 // ------------------------------------------------------------- create ---
+static const char* detector_error(const fdtd_detector& det, const int dims[3], int P) {
+  if (det.kind == 0) return nullptr;
+  if (det.kind != FDTD_OBJ_E2_PLANE && det.kind != FDTD_OBJ_POYNTING_PLANE)
+    return "unknown detector kind";
+  if (det.axis < 0 || det.axis > 2) return "detector axis 0..2";
+  int ua = det.axis == 0 ? 1 : 0, va = det.axis == 2 ? 1 : 2;
+  if (det.index < P || det.index >= dims[det.axis] - P)
+    return "detector plane must be inside the interior";
+  if (det.lo[0] < P || det.hi[0] > dims[ua] - P || det.lo[0] >= det.hi[0] || det.lo[1] < P ||
+      det.hi[1] > dims[va] - P || det.lo[1] >= det.hi[1])
+    return "detector window must be non-empty and inside the interior";
+  return nullptr;
+}
+
 extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fdtd_pml* pml,
                            const fdtd_source* source, const fdtd_detector* detector, int n_steps,
                            const int design_lo[3], const int design_hi[3], void* cuda_stream,
@@ -429,7 +450,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   fdtd_source src = {};
   if (source) src = *source;
   if (src.kind != FDTD_SRC_NONE) {
-    if (src.kind != FDTD_SRC_POINT && src.kind != FDTD_SRC_PLANE_GAUSS)
+    if (src.kind != FDTD_SRC_POINT && src.kind != FDTD_SRC_PLANE_GAUSS &&
+        src.kind != FDTD_SRC_PLANE_UNIFORM)
       return fail(nullptr, FDTD_EINVAL, "unknown source kind");
     if (src.component < 0 || src.component > 2)
       return fail(nullptr, FDTD_EINVAL, "source component must be 0..2");
@@ -444,7 +466,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
         return fail(nullptr, FDTD_EINVAL, "source axis must be 0..2");
       if (src.pos[src.axis] < P || src.pos[src.axis] >= dims[src.axis] - P)
         return fail(nullptr, FDTD_EINVAL, "source plane must be inside the interior");
-      if (!(src.sigma_uv[0] > 0) || !(src.sigma_uv[1] > 0))
+      if (src.kind == FDTD_SRC_PLANE_GAUSS && (!(src.sigma_uv[0] > 0) || !(src.sigma_uv[1] > 0)))
         return fail(nullptr, FDTD_EINVAL, "source widths must be > 0");
     }
   } else {
@@ -452,17 +474,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   }
   fdtd_detector det = {};
   if (detector) det = *detector;
-  if (det.kind != 0) {
-    if (det.kind != FDTD_OBJ_E2_PLANE && det.kind != FDTD_OBJ_POYNTING_PLANE)
-      return fail(nullptr, FDTD_EINVAL, "unknown detector kind");
-    if (det.axis < 0 || det.axis > 2) return fail(nullptr, FDTD_EINVAL, "detector axis 0..2");
-    int ua = det.axis == 0 ? 1 : 0, va = det.axis == 2 ? 1 : 2;
-    if (det.index < P || det.index >= dims[det.axis] - P)
-      return fail(nullptr, FDTD_EINVAL, "detector plane must be inside the interior");
-    if (det.lo[0] < P || det.hi[0] > dims[ua] - P || det.lo[0] >= det.hi[0] || det.lo[1] < P ||
-        det.hi[1] > dims[va] - P || det.lo[1] >= det.hi[1])
-      return fail(nullptr, FDTD_EINVAL, "detector window must be non-empty and inside the interior");
-  }
+  if (const char* msg = detector_error(det, dims, P)) return fail(nullptr, FDTD_EINVAL, msg);
   fdtd_handle* h = new (std::nothrow) fdtd_handle();
   if (!h) return fail(nullptr, FDTD_ENOMEM, "host allocation failed");
   h->nx = dims[0]; h->ny = dims[1]; h->nz = dims[2];
@@ -478,6 +490,10 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   if (h->pml.alpha_factor < 0) h->pml.alpha_factor = 0.05;
   h->src = src;
   h->det = det;
+  h->det2 = fdtd_detector{};
+  h->seeds[0] = 1.0;
+  h->seeds[1] = 0.0;
+  h->obj2_sum = 0.0;
   for (int a = 0; a < 3; ++a) { h->dlo[a] = design_lo[a]; h->dhi[a] = design_hi[a]; }
   h->user_stream = (cudaStream_t)cuda_stream;
   h->ws = nullptr; h->ws_bytes = 0;
@@ -700,6 +716,18 @@ static int lag_tile_x(const fdtd_handle* h) {
   return h->opt_tile_x == 40 ? 40 : 32;
 }
 
+static Det det_of(const fdtd_detector& d) {
+  Det o;
+  o.kind = d.kind;
+  o.axis = d.axis;
+  o.index = d.index;
+  o.u0 = d.lo[0]; o.u1 = d.hi[0];
+  o.v0 = d.lo[1]; o.v1 = d.hi[1];
+  return o;
+}
+
+static Det det2_of(const fdtd_handle* h) { return det_of(h->det2); }
+
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   StepArgs a;
   memset(&a, 0, sizeof a);
@@ -714,11 +742,7 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.src.index = h->src_index;
   a.src.u0 = h->src_u0; a.src.u1 = h->src_u1; a.src.v0 = h->src_v0; a.src.v1 = h->src_v1;
   a.src.w = (const float*)(h->ws + L.srcw);
-  a.det.kind = h->det.kind;
-  a.det.axis = h->det.axis;
-  a.det.index = h->det.index;
-  a.det.u0 = h->det.lo[0]; a.det.u1 = h->det.hi[0];
-  a.det.v0 = h->det.lo[1]; a.det.v1 = h->det.hi[1];
+  a.det = det_of(h->det);
   a.tile_y = lag_tile_y(h);
   a.rows = h->opt_rows;
   a.stages = h->opt_stages;
@@ -814,7 +838,8 @@ static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
   }
 }
 
-static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_FUSED_FWD};
+static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_FUSED_FWD,
+                                FDTD_K_MONITOR};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_FUSED_REV};
 
 // Enqueue the forward time loop on h->stream (capturable).
@@ -860,6 +885,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   char* tape = h->ws + L.tape;
   float* scales = (float*)(h->ws + L.scales);
   int eb = code_bytes(rec->dtype);
+  const Det det2 = det2_of(h);
+  if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
+    return e;
   Sampler smp(h, 0);
   for (int n = 0; n < h->N; ++n) {
     a.jn = h->wave[n];
@@ -887,6 +915,12 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
         if ((e = smp.after(FDTD_K_RECORD))) return e;
         ++nl;
       }
+      if (det2.kind) {
+        if ((e = smp.before(FDTD_K_MONITOR))) return e;
+        if ((e = launch_monitor(Fo, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream))) return e;
+        if ((e = smp.after(FDTD_K_MONITOR))) return e;
+        ++nl;
+      }
       cur ^= 1;
       continue;
     }
@@ -911,6 +945,12 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       return e;
     if ((e = smp.after(FDTD_K_FWD_E))) return e;
     ++nl;
+    if (det2.kind) {
+      if ((e = smp.before(FDTD_K_MONITOR))) return e;
+      if ((e = launch_monitor(a.F, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream))) return e;
+      if ((e = smp.after(FDTD_K_MONITOR))) return e;
+      ++nl;
+    }
   }
   h->fwd_buf = cur;
   *launches = nl;
@@ -932,6 +972,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   a.F = (float*)(h->ws + L.F[h->fwd_buf]);
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
+  const Det det2 = det2_of(h);
   int cur = 0;
   const bool rlag = h->opt_kernel == 4 || h->opt_kernel == 5;
   const bool rpair = h->opt_kernel == 5;
@@ -955,7 +996,8 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
     if ((e = smp.before(FDTD_K_RESTORE))) return e;
     if ((e = launch_restore_seed(rec->dtype, a.F, a.L, a.g, h->faces, h->ws + L.tape, L.stride,
-                                 (const float*)(h->ws + L.scales), ip, det, h->stream)))
+                                 (const float*)(h->ws + L.scales), ip, det, det2,
+                                 (const double*)(h->ws + L.seeds), h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_RESTORE))) return e;
     a.jn = h->wave[n];
@@ -1066,10 +1108,16 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   unsigned err = 0;
   CK(h, cudaMemcpyAsync(h->obj_hist.data(), h->ws + L.obj, h->N * sizeof(double),
                         cudaMemcpyDeviceToHost, h->stream));
+  std::vector<double> m(h->det2.kind ? h->N : 0);
+  if (h->det2.kind)
+    CK(h, cudaMemcpyAsync(m.data(), h->ws + L.obj2, h->N * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  h->obj2_sum = 0.0;
+  for (double v : m) h->obj2_sum += v;
   CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
-  collect_samples(h, 0, kFwdKinds, 4);
+  collect_samples(h, 0, kFwdKinds, 5);
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
@@ -1090,10 +1138,19 @@ extern "C" int fdtd_forward(fdtd_handle* h, const float* d_eps, const fdtd_recor
   return forward_finish(h, objective);
 }
 
-static int backward_async(fdtd_handle* h) {
+// Upload the detectors' seeds (read by the restore kernel of every step).
+static cudaError_t upload_seeds(fdtd_handle* h, const Layout& L, double seed, double seed2,
+                                cudaStream_t s) {
+  h->seeds[0] = seed;
+  h->seeds[1] = h->det2.kind ? seed2 : 0.0;
+  return cudaMemcpyAsync(h->ws + L.seeds, h->seeds, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+}
+
+static int backward_async(fdtd_handle* h, double seed, double seed2) {
   if (!h->have_forward) return fail(h, FDTD_ESTATE, "backward needs a preceding forward");
   int rc = begin(h);
   if (rc) return rc;
+  CK(h, upload_seeds(h, layout_of(h, &h->fwd_rec), seed, seed2, h->stream));
   int nl = 0;
   rc = run_loop(h, &h->fwd_rec, 1, enqueue_backward, &nl, h->t2, h->t3);
   if (rc) return rc;
@@ -1102,11 +1159,11 @@ static int backward_async(fdtd_handle* h) {
   return FDTD_OK;
 }
 
-static int backward_finish(fdtd_handle* h, double seed, float* d_grad) {
+static int backward_finish(fdtd_handle* h, float* d_grad) {
   Layout L = layout_of(h, &h->fwd_rec);
   Geo g = geo_of(h);
   CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g, h->dlo,
-                        h->dhi, seed, d_grad, (unsigned*)(h->ws + L.err), h->stream));
+                        h->dhi, 1.0, d_grad, (unsigned*)(h->ws + L.err), h->stream));
   unsigned err = 0;
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -1122,9 +1179,42 @@ static int backward_finish(fdtd_handle* h, double seed, float* d_grad) {
 extern "C" int fdtd_backward(fdtd_handle* h, double seed, float* d_grad_eps) {
   if (!h) return FDTD_EINVAL;
   if (!d_grad_eps) return fail(h, FDTD_EINVAL, "gradient buffer is NULL");
-  int rc = backward_async(h);
+  int rc = backward_async(h, seed, 0.0);
   if (rc) return rc;
-  return backward_finish(h, seed, d_grad_eps);
+  return backward_finish(h, d_grad_eps);
+}
+
+extern "C" int fdtd_backward2(fdtd_handle* h, double seed, double seed2, float* d_grad_eps) {
+  if (!h) return FDTD_EINVAL;
+  if (!d_grad_eps) return fail(h, FDTD_EINVAL, "gradient buffer is NULL");
+  if (!h->det2.kind && seed2 != 0.0) return fail(h, FDTD_ESTATE, "no second detector is set");
+  int rc = backward_async(h, seed, seed2);
+  if (rc) return rc;
+  return backward_finish(h, d_grad_eps);
+}
+
+extern "C" int fdtd_set_detector2(fdtd_handle* h, const fdtd_detector* d) {
+  if (!h) return FDTD_EINVAL;
+  fdtd_detector det = {};
+  if (d) det = *d;
+  int dims[3] = {h->nx, h->ny, h->nz};
+  if (const char* msg = detector_error(det, dims, h->P)) return fail(h, FDTD_EINVAL, msg);
+  h->det2 = det;
+  h->have_forward = false;
+  drop_graphs(h);
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_objectives(const fdtd_handle* h, double* L, double* M) {
+  if (!h) return FDTD_EINVAL;
+  if ((int)h->obj_hist.size() != h->N) return FDTD_ESTATE;
+  if (L) {
+    double s = 0.0;
+    for (double v : h->obj_hist) s += v;
+    *L = s;
+  }
+  if (M) *M = h->obj2_sum;
+  return FDTD_OK;
 }
 
 extern "C" int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps,
@@ -1144,9 +1234,9 @@ extern "C" int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps,
                         h->stream));
   rc = fdtd_forward(h, (const float*)(h->ws + L.eps), rec, objective);
   if (rc) return rc;
-  rc = backward_async(h);
+  rc = backward_async(h, seed, 0.0);
   if (rc) return rc;
-  rc = backward_finish(h, seed, (float*)(h->ws + L.gout));
+  rc = backward_finish(h, (float*)(h->ws + L.gout));
   if (rc) return rc;
   CK(h, cudaMemcpyAsync(h_grad, h->ws + L.gout, nd * sizeof(float), cudaMemcpyDeviceToHost,
                         h->stream));
@@ -1173,11 +1263,11 @@ extern "C" int fdtd_group_backward(fdtd_handle* const* hs, int n, const double* 
   if (!hs || n < 0 || (n > 0 && (!seeds || !d_grads))) return FDTD_EINVAL;
   for (int i = 0; i < n; ++i) {
     if (!d_grads[i]) return fail(hs[i], FDTD_EINVAL, "gradient buffer is NULL");
-    int rc = backward_async(hs[i]);
+    int rc = backward_async(hs[i], seeds[i], 0.0);
     if (rc) return rc;
   }
   for (int i = 0; i < n; ++i) {
-    int rc = backward_finish(hs[i], seeds[i], d_grads[i]);
+    int rc = backward_finish(hs[i], d_grads[i]);
     if (rc) return rc;
   }
   return FDTD_OK;
@@ -1328,10 +1418,11 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     CK(h, cudaStreamSynchronize(s));
     if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
     if (!isfinite(sum)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
+    CK(h, upload_seeds(h, L, seed, 0.0, s));
     e = enqueue_backward(h, rec, &nl);
     if (e) return cuda_fail(h, "backward launch", e);
     CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g,
-                          h->dlo, h->dhi, seed, d_grad, (unsigned*)(h->ws + L.err), s));
+                          h->dlo, h->dhi, 1.0, d_grad, (unsigned*)(h->ws + L.err), s));
     CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");

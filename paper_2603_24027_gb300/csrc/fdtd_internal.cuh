@@ -249,12 +249,16 @@ cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const in
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);
 cudaError_t launch_gather(const float* F, Geo g, float* out, cudaStream_t s);
+// Objective of one detector plane for one step, added to *out (FP64).
+cudaError_t launch_monitor(const float* F, Geo g, const Det& d, double* out, cudaStream_t s);
 // FH holds Ht^{n+1/2} (low faces), FE holds E^n (high faces).
 cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* FE, Geo g,
                           const Faces& fc, void* tape_sample, float* scale_slot, cudaStream_t s);
+// Seeds: det gets seeds[0], det2 (kind 0 = none) seeds[1] (device FP64).
 cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
                                 const void* tape, long long sample_stride, const float* scales,
-                                const Interp& ip, const Det& det, cudaStream_t s);
+                                const Interp& ip, const Det& det, const Det& det2,
+                                const double* seeds, cudaStream_t s);
 cudaError_t launch_encode(int dtype, int scaled, const float* in, size_t n, void* code,
                           float* scale, cudaStream_t s);
 cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* scale, float* out,

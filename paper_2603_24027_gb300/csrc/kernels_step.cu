@@ -437,6 +437,49 @@ cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const in
   return cudaGetLastError();
 }
 
+// -------------------------------------------------------------- monitor ---
+// Objective l_n of a detector plane from (E^{n+1}, Ht^{n+1/2}) in F: one
+// thread per plane cell, FP64 block sums, one atomic per block into *out.
+__global__ void __launch_bounds__(256) k_monitor(const float* __restrict__ F, Geo g, Det d,
+                                                 double* out) {
+  __shared__ double red[8];
+  const int du = d.u1 - d.u0, dv = d.v1 - d.v0;
+  const int r = blockIdx.x * 256 + threadIdx.x;
+  double v = 0.0;
+  if (r < du * dv) {
+    const int vv = r / du, uu = r - vv * du;
+    const int u = d.u0 + uu, w = d.v0 + vv;
+    const int x = d.axis == 0 ? d.index : u;
+    const int y = d.axis == 1 ? d.index : (d.axis == 0 ? u : w);
+    const int z = d.axis == 2 ? d.index : w;
+    const long long q = (long long)z * g.plane + (long long)y * g.px + x;
+    if (d.kind == 1) {
+      for (int c = 0; c < 3; ++c) {
+        const double e = F[c * g.nc + q];
+        v += e * e;
+      }
+    } else {
+      const int b = (d.axis + 1) % 3, c = (d.axis + 2) % 3;
+      v = (double)F[b * g.nc + q] * F[(3 + c) * g.nc + q] -
+          (double)F[c * g.nc + q] * F[(3 + b) * g.nc + q];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    if (t != 0.0) atomicAdd(out, t);
+  }
+}
+
+cudaError_t launch_monitor(const float* F, Geo g, const Det& d, double* out, cudaStream_t s) {
+  const int n = (d.u1 - d.u0) * (d.v1 - d.v0);
+  k_monitor<<<(n + 255) / 256, 256, 0, s>>>(F, g, d, out);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- gather ---
 __global__ void k_gather(const float* __restrict__ F, Geo g, float* __restrict__ out) {
   long long n = (long long)g.nx * g.ny * g.nz;

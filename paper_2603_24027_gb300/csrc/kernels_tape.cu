@@ -186,7 +186,8 @@ cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* F
 // One thread per recorded value, grid (value blocks, face): the value at this
 // reverse step is sum_m w[m] * decode(sample slot[m]) * scale[slot[m]] (slot
 // -1 = the known zero initial state or an unused term).  blockIdx.y == 6 adds
-// the objective seed dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector plane.
+// the objective seed seeds[0] * dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector
+// plane, blockIdx.y == 7 the second detector's seeds[1] * dm_n/d(...).
 template <int DT>
 __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict__ F,
                                                                float* __restrict__ L, Geo g,
@@ -195,7 +196,8 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict
                                                                long long stride,
                                                                const float* __restrict__ scales,
                                                                const __grid_constant__ Interp ip,
-                                                               Det det) {
+                                                               Det det, Det det2,
+                                                               const double* __restrict__ seeds) {
   typedef typename Code<DT>::T T;
   const int f = blockIdx.y;
   const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
@@ -218,34 +220,39 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict
     const long long q = face_value_cell(g, fd, r, &comp);
     F[comp * g.nc + q] = val;
   } else {
-    if (!det.kind) return;
-    const int du = det.u1 - det.u0, dv = det.v1 - det.v0;
+    const Det& d = f == 6 ? det : det2;
+    if (!d.kind) return;
+    const int du = d.u1 - d.u0, dv = d.v1 - d.v0;
     if (r >= du * dv) return;
+    const float s = (float)seeds[f - 6];
     const int v = r / du, e = r - v * du;
-    const long long q = cell_on_plane(g, det.axis, det.index, det.u0 + e, det.v0 + v);
-    if (det.kind == 1) {
-      for (int c = 0; c < 3; ++c) L[c * g.nc + q] += 2.0f * F[c * g.nc + q];
+    const long long q = cell_on_plane(g, d.axis, d.index, d.u0 + e, d.v0 + v);
+    if (d.kind == 1) {
+      for (int c = 0; c < 3; ++c) L[c * g.nc + q] += s * (2.0f * F[c * g.nc + q]);
     } else {
-      const int b = (det.axis + 1) % 3, c = (det.axis + 2) % 3;
+      const int b = (d.axis + 1) % 3, c = (d.axis + 2) % 3;
       const float Eb = F[b * g.nc + q], Ec = F[c * g.nc + q];
       const float Hb = F[(3 + b) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
-      L[b * g.nc + q] += Hc;
-      L[c * g.nc + q] -= Hb;
-      L[(3 + c) * g.nc + q] += Eb;
-      L[(3 + b) * g.nc + q] -= Ec;
+      L[b * g.nc + q] += s * Hc;
+      L[c * g.nc + q] -= s * Hb;
+      L[(3 + c) * g.nc + q] += s * Eb;
+      L[(3 + b) * g.nc + q] -= s * Ec;
     }
   }
 }
 
 cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
                                 const void* tape, long long stride, const float* scales,
-                                const Interp& ip, const Det& det, cudaStream_t s) {
+                                const Interp& ip, const Det& det, const Det& det2,
+                                const double* seeds, cudaStream_t s) {
   int nmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 1;
+  if (det2.kind) nmax = max(nmax, (det2.u1 - det2.u0) * (det2.v1 - det2.v0));
   for (int f = 0; f < 6; ++f) nmax = max(nmax, 2 * fc.f[f].nu * fc.f[f].nv);
-  dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, 7, 1);
+  dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, det2.kind ? 8 : 7, 1);
   return with_dtype(dtype, [&](auto dt) {
     constexpr int DT = decltype(dt)::value;
-    k_restore_seed<DT><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det);
+    k_restore_seed<DT><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det,
+                                                     det2, seeds);
     return cudaGetLastError();
   });
 }

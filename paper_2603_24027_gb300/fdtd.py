@@ -38,6 +38,16 @@ def _fill_structs(w):
     return grid, pml, src, det
 
 
+def _detector2(w):
+    d = A.Detector()
+    d.kind = w.det2_kind
+    d.axis = w.det2_axis
+    d.index = w.det2_index
+    d.lo[:] = list(w.det2_lo)
+    d.hi[:] = list(w.det2_hi)
+    return d
+
+
 class Simulation:
     """One FDTD gradient problem on one GPU.
 
@@ -61,6 +71,8 @@ class Simulation:
         self.h = h
         self._ws = None
         self._ws_bytes = 0
+        if workload.det2_kind:
+            self._check(A.lib().fdtd_set_detector2(self.h, C.byref(_detector2(workload))))
 
     # ------------------------------------------------------------ lifetime --
     def close(self):
@@ -121,12 +133,24 @@ class Simulation:
                                          C.byref(out)))
         return out.value
 
-    def backward(self, seed: float = 1.0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """seed * dL/d(eps) over the design box, float32 [dz][dy][dx]."""
+    def backward(self, seed: float = 1.0, out: Optional[torch.Tensor] = None,
+                 seed2: Optional[float] = None) -> torch.Tensor:
+        """d(seed L + seed2 M)/d(eps) over the design box, float32 [dz][dy][dx]
+        (M: the second detector's objective; seed2 only with one)."""
         if out is None:
             out = torch.empty(self.design_shape, dtype=torch.float32, device=self._ws.device)
-        self._check(A.lib().fdtd_backward(self.h, float(seed), C.c_void_p(out.data_ptr())))
+        if seed2 is None:
+            self._check(A.lib().fdtd_backward(self.h, float(seed), C.c_void_p(out.data_ptr())))
+        else:
+            self._check(A.lib().fdtd_backward2(self.h, float(seed), float(seed2),
+                                               C.c_void_p(out.data_ptr())))
         return out
+
+    def objectives(self):
+        """(L, M) of the last forward; M is 0 without a second detector."""
+        L, M = C.c_double(), C.c_double()
+        self._check(A.lib().fdtd_objectives(self.h, C.byref(L), C.byref(M)))
+        return L.value, M.value
 
     def value_and_grad_host(self, eps_host: torch.Tensor, rec, seed: float = 1.0,
                             grad_host: Optional[torch.Tensor] = None):
@@ -237,3 +261,33 @@ class FDTDGrad(torch.autograd.Function):
 
 def objective(eps_design, eps_background, sim, rec):
     return FDTDGrad.apply(eps_design, eps_background, sim, rec)
+
+
+class FDTDGrad2(torch.autograd.Function):
+    """(L, M)(eps_design) for a simulation with a second detector.
+
+    forward(eps_design, eps_background, sim, rec) -> float64 tensor [L, M]
+    backward: d(gL L + gM M)/d(eps_design) from one time-reversed run with the
+    two detectors' seeds (gL, gM) = the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, eps_design, eps_background, sim, rec):
+        eps = eps_background.detach().clone()
+        eps[sim.w.design_slice()] = eps_design.detach().to(torch.float32)
+        sim.forward(eps.contiguous(), rec)
+        L, M = sim.objectives()
+        ctx.sim = sim
+        ctx.dtype = eps_design.dtype
+        return torch.tensor([L, M], dtype=torch.float64, device=eps.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        gl, gm = (float(v) for v in g.detach().cpu())
+        grad = ctx.sim.backward(gl, seed2=gm)
+        return grad.to(ctx.dtype), None, None, None
+
+
+def objectives(eps_design, eps_background, sim, rec):
+    """Differentiable (L, M) of a simulation with a second detector."""
+    return FDTDGrad2.apply(eps_design, eps_background, sim, rec)

@@ -25,7 +25,7 @@ COURANT = 0.99            # Courant factor C of Eq. 1
 EPS_SIO2 = 2.085
 EPS_SI = 12.25
 
-SRC_NONE, SRC_POINT, SRC_PLANE_GAUSS = 0, 1, 2
+SRC_NONE, SRC_POINT, SRC_PLANE_GAUSS, SRC_PLANE_UNIFORM = 0, 1, 2, 3
 OBJ_E2_PLANE, OBJ_POYNTING_PLANE = 1, 2
 
 
@@ -68,6 +68,12 @@ class Workload:
     det_index: int = 0
     det_lo: tuple = (0, 0)
     det_hi: tuple = (0, 0)
+    # optional second detector (kind 0 = none): its objective M sits beside L
+    det2_kind: int = 0
+    det2_axis: int = 2
+    det2_index: int = 0
+    det2_lo: tuple = (0, 0)
+    det2_hi: tuple = (0, 0)
     pml_order: int = 3
     pml_sigma_factor: float = 0.8
     pml_kappa_max: float = 1.0
@@ -280,12 +286,68 @@ def fd_cube(seed: int = 0, n_steps: int = 60) -> Workload:
                     det_kind=OBJ_E2_PLANE, det_axis=2, det_index=4, det_lo=(2, 2), det_hi=(6, 6))
 
 
+def coupler(nx: int = 150, ny: int = 110, nz: int = 70, P: int = 12, n_steps: int = 2000,
+            dx: float = 20e-9, dev: int = 80, wg_w: int = 20, layer: int = 11,
+            src_dz: int = 14, det_dz: int = 8, rho=None, seed: int = 0) -> Workload:
+    """Grating-coupler analogue of the paper's optimisation benchmark (Sec. 4):
+    a dev x dev x layer design region (1.6 um x 1.6 um x 220 nm at 20 nm) in
+    SiO2 cladding feeding a wg_w-wide Si waveguide that runs along +x into the
+    CPML; a normally incident Ey plane wave from a z-plane src_dz cells above
+    the layer.  Objective L: Poynting flux along +x through the waveguide
+    cross-section near the far end; second detector M: Poynting flux along +z
+    through the plane det_dz cells above the device (the incident side).  The
+    transmission is -L/M (the incident flux points down).  rho (dev x dev in
+    [0, 1], or None for a seeded smooth random start) maps to eps = SiO2 +
+    (Si - SiO2) rho, extruded over the layer."""
+    eps = np.full((nz, ny, nx), EPS_SIO2, np.float32)
+    z0 = nz // 2 - layer // 2
+    z1 = z0 + layer
+    x0 = P + 6
+    x1 = x0 + dev
+    y0 = (ny - dev) // 2
+    y1 = y0 + dev
+    yw0 = (ny - wg_w) // 2
+    yw1 = yw0 + wg_w
+    eps[z0:z1, yw0:yw1, x1:] = EPS_SI
+    if rho is None:
+        rng = _rng(seed)
+        noise = rng.standard_normal((dev, dev))
+        k = _gaussian_kernel(3.0)
+        c = (len(k) - 1) // 2
+
+        def conv(r):   # zero-padded, centred, also for rows shorter than k
+            return np.convolve(r, k, mode="full")[c:c + len(r)]
+        sm = np.apply_along_axis(conv, 0, noise)
+        sm = np.apply_along_axis(conv, 1, sm)
+        sm = (sm - sm.mean()) / (sm.std() + 1e-12)
+        rho = 1.0 / (1.0 + np.exp(-sm))
+    rho = np.asarray(rho, np.float64)
+    eps[z0:z1, y0:y1, x0:x1] = (EPS_SIO2 + (EPS_SI - EPS_SIO2) * rho)[None].astype(np.float32)
+    m = 6 if wg_w >= 12 else 2
+    return Workload(
+        name=f"coupler{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dt=cfl_dt(dx),
+        n_steps=n_steps, pml_thickness=P, eps=eps, design_lo=(x0, y0, z0),
+        design_hi=(x1, y1, z1), src_kind=SRC_PLANE_UNIFORM, src_component=1, src_axis=2,
+        src_pos=(nx // 2, ny // 2, z1 + src_dz), t0_over_tau=3.0,
+        det_kind=OBJ_POYNTING_PLANE, det_axis=0, det_index=nx - P - 4,
+        det_lo=(max(P, yw0 - m), max(P, z0 - m)), det_hi=(min(ny - P, yw1 + m), min(nz - P, z1 + m)),
+        det2_kind=OBJ_POYNTING_PLANE, det2_axis=2, det2_index=z1 + det_dz,
+        det2_lo=(x0, y0), det2_hi=(x1, y1))
+
+
+def coupler_small(n_steps: int = 90, seed: int = 0) -> Workload:
+    """The coupler layout at oracle-test size: 36 x 28 x 26 cells, 5-cell CPML."""
+    return coupler(nx=36, ny=28, nz=26, P=5, n_steps=n_steps, dx=25e-9, dev=10, wg_w=4,
+                   layer=3, src_dz=4, det_dz=2, seed=seed)
+
+
 def random_state(shape, seed: int, n_arrays: int, scale: float = 1.0) -> np.ndarray:
     """Seeded float64 state block [n_arrays][nz][ny][nx] for operator tests."""
     return _rng(seed).standard_normal((n_arrays,) + tuple(shape)) * scale
 
 
 CONFIGS = {
+    "coupler150": coupler,
     "dipole48": small_dipole,
     "waveguide200": waveguide_mid,
     "waveguide100": waveguide_sweep,

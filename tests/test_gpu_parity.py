@@ -246,6 +246,42 @@ def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
     assert 0.7 < bwd / t["bwd_ms"] < 1.3, (bwd, t)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_two_detector_gradient_matches_oracle(F, A, kernel):
+    """Coupler layout (plane-wave source, flux through the output waveguide L
+    and above the device M): objectives and the gradient of s L + s2 M from
+    one time-reversed run against the oracle's stored-history gradient."""
+    w = I.coupler_small(n_steps=110)
+    s1, s2 = 0.7, -1.3
+    Lr, Mr, gr = O.gradient2(w, s1, s2)
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_KERNEL, kernel)
+    eps = torch.from_numpy(w.eps).cuda()
+    L = sim.forward(eps, A.record_cfg("f32", 1))
+    L2, M = sim.objectives()
+    assert L2 == L
+    assert L == pytest.approx(Lr, rel=1e-5) and M == pytest.approx(Mr, rel=1e-5)
+    g = sim.backward(s1, seed2=s2).cpu().numpy()
+    assert rel(g, gr) < 1e-4
+
+
+def test_two_detector_compressed_tape_and_seed_errors(F, A):
+    w = I.coupler_small(n_steps=110)
+    Lr, Mr, gr = O.gradient2(w, 1.0, -2.0)
+    sim = F.Simulation(w)
+    eps = torch.from_numpy(w.eps).cuda()
+    sim.forward(eps, A.record_cfg("e4m3b11fnuz", 4, "linear"))
+    g = sim.backward(1.0, seed2=-2.0).cpu().numpy()
+    assert cos(g, gr) > 0.999
+    # seed2 without a second detector is a state error
+    w1 = w.replace(det2_kind=0)
+    sim1 = F.Simulation(w1)
+    sim1.forward(eps, A.record_cfg("f32", 1))
+    with pytest.raises(A.FdtdError) as e:
+        sim1.backward(1.0, seed2=1.0)
+    assert e.value.status == A.FDTD_ESTATE
+
+
 PAPER_FP8 = ["e4m3b11fnuz", "e5m2fnuz", "e4m3fnuz", "e4m3ieee", "e3m4"]
 
 

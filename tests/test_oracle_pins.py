@@ -282,6 +282,58 @@ def test_gradient_matches_central_differences_poynting_plane_source():
     assert np.abs(g).max() > 0
 
 
+def _swap_detectors(w):
+    """The workload with its second detector as the objective detector."""
+    return w.replace(det_kind=w.det2_kind, det_axis=w.det2_axis, det_index=w.det2_index,
+                     det_lo=w.det2_lo, det_hi=w.det2_hi, det2_kind=0)
+
+
+def test_two_detector_gradient_matches_central_differences():
+    """Transmission-ratio ingredients (Sec. 4): the stored-history gradient of
+    s L + s2 M (L through the output waveguide, M above the coupler, plane-wave
+    source) against central differences of the same combination."""
+    w = I.coupler_small(n_steps=70)
+    s1, s2 = 0.7, -1.3
+    L, M, g = O.gradient2(w, s1, s2)
+    assert L != 0.0 and M != 0.0
+    # each objective on its own equals the single-detector path
+    L1, g1 = O.gradient(w)
+    M1, gm = O.gradient(_swap_detectors(w))
+    assert L1 == pytest.approx(L, rel=1e-14) and M1 == pytest.approx(M, rel=1e-14)
+    np.testing.assert_allclose(g, s1 * g1 + s2 * gm, rtol=0, atol=1e-12 * np.abs(g).max())
+    gmax = np.abs(g).max()
+    rng = np.random.default_rng(9)
+    h = 1e-3   # |M| >> |dM/d eps| here: smaller steps are dominated by the rounding of M
+    for _ in range(10):
+        z, y, x = (int(rng.integers(0, n)) for n in w.design_shape)
+        c = (z + w.design_lo[2], y + w.design_lo[1], x + w.design_lo[0])
+        ep, em = w.eps.astype(np.float64), w.eps.astype(np.float64)
+        ep[c] += h
+        em[c] -= h
+        f = []
+        for e in (ep, em):
+            we = w.replace(eps=e)
+            f.append(s1 * O.forward(we)[1].sum() + s2 * O.forward(_swap_detectors(we))[1].sum())
+        fd = (f[0] - f[1]) / (2 * h)
+        assert abs(fd - g[z, y, x]) <= 1e-7 * gmax, (c, fd, g[z, y, x])
+
+
+def test_plane_wave_source_is_transversely_uniform():
+    """A uniform sheet source (normally incident plane wave) on a periodic
+    grid without CPML drives fields that do not vary across the sheet's plane,
+    only along its normal, and only the source's component and the matching
+    magnetic component are excited."""
+    w = I.coupler_small(n_steps=40).replace(pml_thickness=0, eps=np.ones((26, 28, 36), np.float32))
+    st = O.zero_state(w)
+    O.run(w, st, periodic=1, pml=0, count=40)
+    Ey, Hx = st[1], st[3]
+    assert np.abs(Ey).max() > 0
+    for f in (Ey, Hx):
+        assert np.abs(f - f[:, :1, :1]).max() <= 1e-14 * np.abs(f).max()
+    for c in (0, 2, 4, 5):
+        assert np.abs(st[c]).max() == 0.0
+
+
 # ----------------------------------------- the method vs the definition -----
 
 @pytest.mark.parametrize("maker", [I.fd_cube, lambda: I.ragged_box(nx=15, ny=12, nz=11, P=3, n_steps=70)])
