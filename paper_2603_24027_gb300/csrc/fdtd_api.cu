@@ -61,7 +61,8 @@ struct fdtd_handle {
   fdtd_source src;
   fdtd_detector det;
   fdtd_detector det2;         // optional second detector (kind 0 = none)
-  double seeds[2];            // backward seeds of the two detectors (host copy)
+  double seeds[2];            // backward seeds of the two detectors over seed_scale (host copy)
+  double seed_scale;          // reference seed, applied when the gradient is finalised
   int dlo[3], dhi[3];
   cudaStream_t user_stream;
 
@@ -493,6 +494,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->det2 = fdtd_detector{};
   h->seeds[0] = 1.0;
   h->seeds[1] = 0.0;
+  h->seed_scale = 1.0;
   h->obj2_sum = 0.0;
   for (int a = 0; a < 3; ++a) { h->dlo[a] = design_lo[a]; h->dhi[a] = design_hi[a]; }
   h->user_stream = (cudaStream_t)cuda_stream;
@@ -1139,10 +1141,17 @@ extern "C" int fdtd_forward(fdtd_handle* h, const float* d_eps, const fdtd_recor
 }
 
 // Upload the detectors' seeds (read by the restore kernel of every step).
+// The adjoint runs with the seeds divided by a reference seed (the first
+// non-zero one), so one of them is exactly 1 and the single-detector run is
+// seeded exactly as without seeds; the reference multiplies the gradient in
+// FP64 when it is finalised, which keeps the result exactly linear in it.
 static cudaError_t upload_seeds(fdtd_handle* h, const Layout& L, double seed, double seed2,
                                 cudaStream_t s) {
-  h->seeds[0] = seed;
-  h->seeds[1] = h->det2.kind ? seed2 : 0.0;
+  if (!h->det2.kind) seed2 = 0.0;
+  const double ref = seed != 0.0 ? seed : (seed2 != 0.0 ? seed2 : 1.0);
+  h->seed_scale = ref;
+  h->seeds[0] = seed / ref;
+  h->seeds[1] = seed2 / ref;
   return cudaMemcpyAsync(h->ws + L.seeds, h->seeds, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
 }
 
@@ -1163,7 +1172,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   Layout L = layout_of(h, &h->fwd_rec);
   Geo g = geo_of(h);
   CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g, h->dlo,
-                        h->dhi, 1.0, d_grad, (unsigned*)(h->ws + L.err), h->stream));
+                        h->dhi, h->seed_scale, d_grad, (unsigned*)(h->ws + L.err), h->stream));
   unsigned err = 0;
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -1422,7 +1431,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     e = enqueue_backward(h, rec, &nl);
     if (e) return cuda_fail(h, "backward launch", e);
     CK(h, launch_finalize((const double*)(h->ws + L.gacc), (const float*)(h->ws + L.cb), g,
-                          h->dlo, h->dhi, 1.0, d_grad, (unsigned*)(h->ws + L.err), s));
+                          h->dlo, h->dhi, h->seed_scale, d_grad, (unsigned*)(h->ws + L.err), s));
     CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
