@@ -183,11 +183,13 @@ cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* F
 }
 
 // -------------------------------------------------------------- restore ---
-// One thread per recorded value, grid (value blocks, face): the value at this
+// One thread per recorded value over all six faces (value r of the sample
+// belongs to the face f with start[f] <= r < start[f+1]): the value at this
 // reverse step is sum_m w[m] * decode(sample slot[m]) * scale[slot[m]] (slot
-// -1 = the known zero initial state or an unused term).  blockIdx.y == 6 adds
-// the objective seed seeds[0] * dl_n/d(E^{n+1}, Ht^{n+1/2}) on the detector
-// plane, blockIdx.y == 7 the second detector's seeds[1] * dm_n/d(...).
+// -1 = the known zero initial state or an unused term).  The blocks after the
+// faces' add the objective seeds on the detector planes: seeds[0] *
+// dl_n/d(E^{n+1}, Ht^{n+1/2}) for the detector, seeds[1] * dm_n/d(...) for
+// the second one.
 template <int DT>
 __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict__ F,
                                                                float* __restrict__ L, Geo g,
@@ -197,47 +199,54 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict
                                                                const float* __restrict__ scales,
                                                                const __grid_constant__ Interp ip,
                                                                Det det, Det det2,
-                                                               const double* __restrict__ seeds) {
+                                                               const double* __restrict__ seeds,
+                                                               int face_blocks, int det_blocks) {
   typedef typename Code<DT>::T T;
-  const int f = blockIdx.y;
-  const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
-  if (f < 6) {
+  if ((int)blockIdx.x < face_blocks) {
+    const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
+    if (r >= fc.start[6]) return;
+    int f = 0;
+#pragma unroll
+    for (int t = 1; t < 6; ++t) f += r >= fc.start[t];
     const FaceDesc& fd = fc.f[f];
-    if (r >= 2 * fd.nu * fd.nv) return;
+    const int rr = r - fc.start[f];
     const int fld = f & 1;  // 0: Ht on low faces, 1: E on high faces
-    const T* tp = reinterpret_cast<const T*>(tape) + fd.off + r;
+    const T* tp = reinterpret_cast<const T*>(tape) + fd.off + rr;
     float val = 0.f;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const int s = ip.slot[fld][m];
       if (s >= 0) {
         float x = Code<DT>::dec(tp[(long long)s * stride]);
-        if (DT >= 2) x = x * scales[s * 6 + f];
+        if (DT >= 2) x = x * __ldg(scales + s * 6 + f);
         val += ip.w[fld][m] * x;
       }
     }
     int comp;
-    const long long q = face_value_cell(g, fd, r, &comp);
+    const long long q = face_value_cell(g, fd, rr, &comp);
     F[comp * g.nc + q] = val;
+    return;
+  }
+  const int b = blockIdx.x - face_blocks;
+  const int which = b >= det_blocks;
+  const Det& d = which ? det2 : det;
+  if (!d.kind) return;
+  const int du = d.u1 - d.u0, dv = d.v1 - d.v0;
+  const int r = (b - which * det_blocks) * FLAT_THREADS + threadIdx.x;
+  if (r >= du * dv) return;
+  const float s = (float)seeds[which];
+  const int v = r / du, e = r - v * du;
+  const long long q = cell_on_plane(g, d.axis, d.index, d.u0 + e, d.v0 + v);
+  if (d.kind == 1) {
+    for (int c = 0; c < 3; ++c) L[c * g.nc + q] += s * (2.0f * F[c * g.nc + q]);
   } else {
-    const Det& d = f == 6 ? det : det2;
-    if (!d.kind) return;
-    const int du = d.u1 - d.u0, dv = d.v1 - d.v0;
-    if (r >= du * dv) return;
-    const float s = (float)seeds[f - 6];
-    const int v = r / du, e = r - v * du;
-    const long long q = cell_on_plane(g, d.axis, d.index, d.u0 + e, d.v0 + v);
-    if (d.kind == 1) {
-      for (int c = 0; c < 3; ++c) L[c * g.nc + q] += s * (2.0f * F[c * g.nc + q]);
-    } else {
-      const int b = (d.axis + 1) % 3, c = (d.axis + 2) % 3;
-      const float Eb = F[b * g.nc + q], Ec = F[c * g.nc + q];
-      const float Hb = F[(3 + b) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
-      L[b * g.nc + q] += s * Hc;
-      L[c * g.nc + q] -= s * Hb;
-      L[(3 + c) * g.nc + q] += s * Eb;
-      L[(3 + b) * g.nc + q] -= s * Ec;
-    }
+    const int bb = (d.axis + 1) % 3, c = (d.axis + 2) % 3;
+    const float Eb = F[bb * g.nc + q], Ec = F[c * g.nc + q];
+    const float Hb = F[(3 + bb) * g.nc + q], Hc = F[(3 + c) * g.nc + q];
+    L[bb * g.nc + q] += s * Hc;
+    L[c * g.nc + q] -= s * Hb;
+    L[(3 + c) * g.nc + q] += s * Eb;
+    L[(3 + bb) * g.nc + q] -= s * Ec;
   }
 }
 
@@ -245,14 +254,16 @@ cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Face
                                 const void* tape, long long stride, const float* scales,
                                 const Interp& ip, const Det& det, const Det& det2,
                                 const double* seeds, cudaStream_t s) {
-  int nmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 1;
-  if (det2.kind) nmax = max(nmax, (det2.u1 - det2.u0) * (det2.v1 - det2.v0));
-  for (int f = 0; f < 6; ++f) nmax = max(nmax, 2 * fc.f[f].nu * fc.f[f].nv);
-  dim3 grid((nmax + FLAT_THREADS - 1) / FLAT_THREADS, det2.kind ? 8 : 7, 1);
+  const int face_blocks = (fc.start[6] + FLAT_THREADS - 1) / FLAT_THREADS;
+  int dmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 0;
+  if (det2.kind) dmax = max(dmax, (det2.u1 - det2.u0) * (det2.v1 - det2.v0));
+  const int det_blocks = (dmax + FLAT_THREADS - 1) / FLAT_THREADS;
+  const int blocks = face_blocks + (det2.kind ? 2 : 1) * det_blocks;
+  if (blocks == 0) return cudaSuccess;
   return with_dtype(dtype, [&](auto dt) {
     constexpr int DT = decltype(dt)::value;
-    k_restore_seed<DT><<<grid, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det,
-                                                     det2, seeds);
+    k_restore_seed<DT><<<blocks, FLAT_THREADS, 0, s>>>(F, L, g, fc, tape, stride, scales, ip, det,
+                                                       det2, seeds, face_blocks, det_blocks);
     return cudaGetLastError();
   });
 }

@@ -101,7 +101,7 @@ def optimise(problem: Coupler, theta0: np.ndarray, iters: int = 200, lr: float =
         sched.step()
         with torch.no_grad():
             theta.clamp_(0.0, 1.0)
-        hist.append(float(tdb))
+        hist.append(float(tdb.detach()))
         if log:
             log(it, float(tdb), beta)
     # transmission of the final, fully projected design
