@@ -206,8 +206,10 @@ enum {
                                  (plain loads), 2: fused forward with TMA staging, 3: split
                                  half-steps with TMA staging, 4: TMA half-steps that read one
                                  plane per iteration, 5 (default): the kernels of 4 with two
-                                 x-cells per thread (tile height at least 2); 2 and 3 use the
-                                 TMA reverse of 3, 0 and 1 the plain reverse */
+                                 x-cells per thread (tile height at least 2), 6: one fused
+                                 launch per forward step (H and E half-steps, tile height 4
+                                 or 8) with the reverse of 5; 2 and 3 use the TMA reverse of
+                                 3, 0 and 1 the plain reverse */
   FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8 default, 16); width 32 */
   FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
   FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: every m-th launch of a time loop opens a timed

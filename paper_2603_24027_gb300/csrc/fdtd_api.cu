@@ -590,7 +590,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
   switch (option) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
-      if (value < 0 || value > 5) return fail(h, FDTD_EINVAL, "kernel must be 0..5");
+      if (value < 0 || value > 6) return fail(h, FDTD_EINVAL, "kernel must be 0..6");
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
@@ -708,7 +708,7 @@ static int finish(fdtd_handle* h) {
 // Tile height the half-step kernels run with: the two-cells-per-thread
 // kernels cover two tile rows per warp, so their tiles are at least 2 high.
 static int lag_tile_y(const fdtd_handle* h) {
-  return (h->opt_kernel == 5 && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
+  return ((h->opt_kernel == 5 || h->opt_kernel == 6) && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
 }
 
 // Tile width of the two-cells-per-thread kernels: 40-wide tiles exist for a
@@ -729,6 +729,11 @@ static Det det_of(const fdtd_detector& d) {
 }
 
 static Det det2_of(const fdtd_handle* h) { return det_of(h->det2); }
+
+// Kernels 1, 2 and 6 run the forward step as one ping-pong launch.
+static bool fused_forward(const fdtd_handle* h) {
+  return h->opt_kernel == 1 || h->opt_kernel == 2 || h->opt_kernel == 6;
+}
 
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   StepArgs a;
@@ -856,8 +861,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if ((e = cudaMemsetAsync(h->ws + L.psiF[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream))) return e;
   int r = (h->N - 1) % rec->k;
-  const bool fused = h->opt_kernel == 1 || h->opt_kernel == 2;
+  const bool fused = fused_forward(h);
   const bool tma = h->opt_kernel == 2;
+  const bool ff = h->opt_kernel == 6;
   const bool split_tma = h->opt_kernel == 3;
   const bool lagk = h->opt_kernel == 4 || h->opt_kernel == 5;
   const bool pair = h->opt_kernel == 5;
@@ -881,6 +887,11 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     h->maps_ws = h->ws;
     h->maps_ty = h->opt_tile_y;
   }
+  FFMaps ffmaps[2];
+  for (int b = 0; ff && b < 2; ++b)
+    if ((e = encode_ffwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb),
+                              (const float*)(h->ws + L.psiF[b]), a.g, a.tile_y, &ffmaps[b])))
+      return e;
   int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
@@ -903,8 +914,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       a.F = (float*)(h->ws + L.F[cur]);
       a.psiA = (float*)(h->ws + L.psiF[cur]);
       if ((e = smp.before(FDTD_K_FUSED_FWD))) return e;
-      if ((e = tma ? launch_fwd_tma(h->fmaps[cur], a, Fo, po, h->stream)
-                   : launch_fused_fwd(a, Fo, po, h->stream)))
+      if ((e = ff ? launch_ffwd(ffmaps[cur], a, Fo, po, h->stream)
+               : tma ? launch_fwd_tma(h->fmaps[cur], a, Fo, po, h->stream)
+                     : launch_fused_fwd(a, Fo, po, h->stream)))
         return e;
       if ((e = smp.after(FDTD_K_FUSED_FWD))) return e;
       ++nl;
@@ -976,8 +988,8 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   Det det = a.det;
   const Det det2 = det2_of(h);
   int cur = 0;
-  const bool rlag = h->opt_kernel == 4 || h->opt_kernel == 5;
-  const bool rpair = h->opt_kernel == 5;
+  const bool rlag = h->opt_kernel >= 4;
+  const bool rpair = h->opt_kernel >= 5;
   const bool rtma = h->opt_kernel == 2 || h->opt_kernel == 3;
   SplitMaps rmaps[2];
   LagMaps lrmaps[2];
@@ -1099,7 +1111,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   rc = run_loop(h, rec, 0, enqueue_forward, &nl, h->t0, h->t1);
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = (h->opt_kernel == 1 || h->opt_kernel == 2) ? (h->N & 1) : 0;
+  h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
   h->fwd_rec = *rec;
   return FDTD_OK;
 }
@@ -1412,7 +1424,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
     if (e) return cuda_fail(h, "forward launch", e);
-    h->fwd_buf = (h->opt_kernel == 1 || h->opt_kernel == 2) ? (h->N & 1) : 0;
+    h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
     // objective: per-step slots summed on the host in chunks
     double sum = 0.0, chunk[256];
     for (int n0 = 0; n0 < h->N; n0 += 256) {

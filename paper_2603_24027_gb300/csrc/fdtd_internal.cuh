@@ -245,6 +245,19 @@ cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStrea
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
                            cudaStream_t s);
+
+// Tensor maps of the fused two-cells-per-thread forward: E box 40 x (ty+2)
+// and Ht box 36 x (ty+1) from (x0-4, y0-1), own E and cb boxes 32 x ty, psi
+// boxes 36 x (ty+1) (H side) and 32 x ty (E side); ty is 4 or 8.
+struct alignas(64) FFMaps {
+  CUtensorMap Ew, Hb, Eo, cbo, Ph, Pe;
+};
+cudaError_t encode_ffwd_maps(const float* F, const float* cb, const float* psiA, const Geo& g,
+                             int ty, FFMaps* m);
+// One forward time step: (E^n, Ht^{n-1/2}) in a.F, psi in a.psiA ->
+// (E^{n+1}, Ht^{n+1/2}) in Fo, psi in psiO.
+cudaError_t launch_ffwd(const FFMaps& m, const StepArgs& a, float* Fo, float* psiO,
+                        cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);

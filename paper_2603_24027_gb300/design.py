@@ -103,7 +103,7 @@ def optimise(problem: Coupler, theta0: np.ndarray, iters: int = 200, lr: float =
             theta.clamp_(0.0, 1.0)
         hist.append(float(tdb.detach()))
         if log:
-            log(it, float(tdb), beta)
+            log(it, float(tdb.detach()), beta)
     # transmission of the final, fully projected design
     with torch.no_grad():
         final = float(10.0 * torch.log10(torch.clamp(problem.transmission(theta, beta_max),

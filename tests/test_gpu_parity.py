@@ -74,7 +74,7 @@ SMALL = {
 }
 
 
-KERNELS = [0, 1, 2, 3, 4, 5]   # split plain, fused plain, fused TMA, split TMA, one-plane TMA (1 and 2 cells per thread)
+KERNELS = [0, 1, 2, 3, 4, 5, 6]   # split plain, fused plain, fused TMA, split TMA, one-plane TMA (1 and 2 cells per thread), fused two-cell forward
 
 
 @pytest.mark.parametrize("name", list(SMALL))
