@@ -219,14 +219,16 @@ __global__ void __launch_bounds__(ffwd::L<TY, S>::NT)
         ny_[c] = __fsub_rn(c_hy[c], __fmul_rn(g.S, cy));
         nz_[c] = __fsub_rn(c_hz[c], __fmul_rn(g.S, cz));
       }
-      // cells outside the grid hold zero: the E update reads them as the
-      // zero-padding neighbours of the first row / column
+      // cells outside the grid (the plane below z = 0 included) hold zero: the
+      // E update reads them as the zero-padding neighbours of the first
+      // row / column / plane
       float* T = tiles + (k & 1) * 3 * Y::TP;
-      *reinterpret_cast<float2*>(T + tb_) = make_float2(hv0 ? nx_[0] : 0.f, hv1 ? nx_[1] : 0.f);
+      const bool in0 = hv0 && k >= 0, in1 = hv1 && k >= 0;
+      *reinterpret_cast<float2*>(T + tb_) = make_float2(in0 ? nx_[0] : 0.f, in1 ? nx_[1] : 0.f);
       *reinterpret_cast<float2*>(T + Y::TP + tb_) =
-          make_float2(hv0 ? ny_[0] : 0.f, hv1 ? ny_[1] : 0.f);
+          make_float2(in0 ? ny_[0] : 0.f, in1 ? ny_[1] : 0.f);
       *reinterpret_cast<float2*>(T + 2 * Y::TP + tb_) =
-          make_float2(hv0 ? nz_[0] : 0.f, hv1 ? nz_[1] : 0.f);
+          make_float2(in0 ? nz_[0] : 0.f, in1 ? nz_[1] : 0.f);
       if (wr && (hown0 || hown1)) {
         const long long q = (long long)k * g.plane + hq;
         st2(Hx, q, nx_[0], nx_[1], hown0, hown1);
