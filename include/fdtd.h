@@ -279,6 +279,16 @@ int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code
 int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale, float* d_out,
                 void* cuda_stream);
 
+/* Self-test of the bounded device waits (failure detection without a
+ * fault): one CTA arms an mbarrier for a copy that is never issued and waits
+ * on it with the same bounded wait the TMA pipelines use, giving up after
+ * limit_cycles (> 0) SM clock cycles.  On giving up it ORs the timeout bit
+ * (4) into *d_flag (device, one unsigned, caller-owned and zeroed) and the
+ * call returns FDTD_ETIMEOUT after synchronising the stream, with the CUDA
+ * context still usable.  FDTD_EINVAL for a NULL flag or limit <= 0;
+ * FDTD_ECUDA if the launch fails. */
+int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stream);
+
 /* ------------------------------------------------ no-allocation variant --- */
 
 /* Largest workspace (bytes) fdtd_value_and_grad_noalloc can hold. */

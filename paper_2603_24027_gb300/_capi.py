@@ -100,6 +100,7 @@ _PROTOS = {
                               C.c_void_p]),
     "fdtd_decode": (C.c_int, [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                               C.c_void_p]),
+    "fdtd_selftest_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p]),
     "fdtd_value_and_grad_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                               C.c_double, C.POINTER(C.c_double), C.c_void_p]),
 }

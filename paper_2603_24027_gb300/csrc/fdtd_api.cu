@@ -1329,6 +1329,18 @@ extern "C" int fdtd_objective_history(fdtd_handle* h, double* out) {
   return FDTD_OK;
 }
 
+extern "C" int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stream) {
+  if (!d_flag || limit_cycles <= 0) return FDTD_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = launch_wait_selftest(limit_cycles, d_flag, s);
+  if (e) return FDTD_ECUDA;
+  unsigned flag = 0;
+  if (cudaMemcpyAsync(&flag, d_flag, sizeof flag, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FDTD_ECUDA;
+  return (flag & ERR_TIMEOUT) ? FDTD_ETIMEOUT : FDTD_OK;
+}
+
 extern "C" int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code,
                            float* d_scale, void* cuda_stream) {
   if (dtype < 0 || dtype >= kTapeDtypes || !d_in || !d_code || !d_scale) return FDTD_EINVAL;

@@ -262,6 +262,8 @@ cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const in
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);
 cudaError_t launch_gather(const float* F, Geo g, float* out, cudaStream_t s);
+// One CTA waits (bounded by `limit` cycles) on an mbarrier nothing completes.
+cudaError_t launch_wait_selftest(long long limit, unsigned* flag, cudaStream_t s);
 // Objective of one detector plane for one step, added to *out (FP64).
 cudaError_t launch_monitor(const float* F, Geo g, const Det& d, double* out, cudaStream_t s);
 // FH holds Ht^{n+1/2} (low faces), FE holds E^n (high faces).

@@ -13,6 +13,7 @@
 // kernels need no inter-block ordering.  Blocks are 32 x tile_y columns that
 // march over a z chunk, carrying the z-neighbour plane in registers.
 #include "fdtd_internal.cuh"
+#include "tma.cuh"
 
 namespace fdtd {
 
@@ -434,6 +435,27 @@ cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const in
   if (blocks < 1) blocks = 1;
   k_finalize<<<blocks, 256, 0, s>>>(gacc, cb, g, dlo[0], dlo[1], dlo[2], dX, dY, dZ, scale, out,
                                     err);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------- wait self-test ---
+// An mbarrier armed for 16 transaction bytes that no copy delivers: the
+// bounded wait of the TMA pipelines must give up and report.
+__global__ void k_wait_selftest(long long limit, unsigned* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, 16);
+    if (!mbar_wait(&bar, 0, limit)) atomicOr(flag, ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_wait_selftest(long long limit, unsigned* flag, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit, flag);
   return cudaGetLastError();
 }
 

@@ -382,6 +382,23 @@ def test_group_calls_match_single_calls(F, A):
         np.testing.assert_allclose(g.cpu().numpy(), r["g"], rtol=1e-10, atol=1e-30)
 
 
+def test_bounded_device_wait_reports_a_timeout(F, A):
+    """Failure detection without a fault: a wait that nothing completes gives
+    up after its limit, the host reads FDTD_ETIMEOUT, and the context stays
+    usable for a normal run afterwards."""
+    import ctypes as C
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = A.lib().fdtd_selftest_wait(C.c_void_p(flag.data_ptr()), 20_000_000, None)
+    assert rc == A.FDTD_ETIMEOUT
+    assert int(flag.item()) & 4
+    assert A.lib().fdtd_selftest_wait(C.c_void_p(flag.data_ptr()), 0, None) == A.FDTD_EINVAL
+    assert A.lib().fdtd_selftest_wait(None, 1000, None) == A.FDTD_EINVAL
+    w = SMALL["fd_cube"]()
+    r = gpu_run(F, A, w)
+    L, g = O.gradient(w)
+    assert rel(r["g"], g) < 1e-4
+
+
 def test_error_statuses(F, A):
     import ctypes as C
     w = SMALL["fd_cube"]()
