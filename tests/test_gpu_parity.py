@@ -382,6 +382,63 @@ def test_group_calls_match_single_calls(F, A):
         np.testing.assert_allclose(g.cpu().numpy(), r["g"], rtol=1e-10, atol=1e-30)
 
 
+def _degenerate_cases():
+    cube = I.fd_cube()
+    rb = I.ragged_box(nx=35, ny=17, nz=15, P=3, n_steps=40)
+    P = rb.pml_thickness
+    return {
+        # one time step: a single recorded sample
+        "one_step": cube.replace(n_steps=1, det_index=3),
+        # smallest grid the API accepts: 2P+2 cells per axis (a 2-cell interior)
+        "min_grid": cube.replace(nx=6, ny=6, nz=6, eps=np.ones((6, 6, 6), np.float32),
+                                 design_lo=(2, 2, 2), design_hi=(4, 4, 4), src_pos=(2, 3, 2),
+                                 det_index=3, det_lo=(2, 2), det_hi=(4, 4)),
+        # a one-cell design box and a one-cell detector window
+        "one_cell": rb.replace(design_lo=(P + 4, P + 2, P + 3), design_hi=(P + 5, P + 3, P + 4),
+                               det_lo=(P + 1, P + 1), det_hi=(P + 2, P + 2)),
+    }
+
+
+@pytest.mark.parametrize("name", ["one_step", "min_grid", "one_cell"])
+@pytest.mark.parametrize("kernel", [0, 5])
+def test_degenerate_problems(F, A, name, kernel):
+    w = _degenerate_cases()[name]
+    L, g = O.gradient(w)
+    r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel})
+    assert r["L"] == pytest.approx(L, rel=1e-5, abs=1e-30)
+    if np.abs(g).max() > 0:
+        assert rel(r["g"], g) < 1e-4
+    else:
+        assert np.abs(r["g"]).max() == 0.0
+
+
+@pytest.mark.parametrize("k", [7, 100])
+def test_subsampling_longer_than_the_run(F, A, k):
+    """k >= n_steps keeps only the last step (plus the known zero state) and
+    still matches the oracle's run of the method."""
+    w = I.ragged_box(n_steps=40)
+    r = gpu_run(F, A, w, rec=A.record_cfg("f32", k, "linear"))
+    Lm, gm = O.reverse(w, "f32", k=k, interp="linear")
+    assert r["L"] == pytest.approx(Lm, rel=1e-5)
+    assert rel(r["g"], gm) < 1e-3
+
+
+def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
+    """The 200 x 200 x 100 benchmark grid in the default launch configuration,
+    shortened to 100 steps so that the FP64 oracle computes every output: the
+    forward fields, the objective and the uncompressed gradient."""
+    # an early pulse and the detector inside the design region's x range, so
+    # that the objective and its gradient are not zero after 100 steps
+    w = I.waveguide_mid().replace(n_steps=100, t0_over_tau=0.3, det_index=60)
+    L, g, st = O.gradient(w, want_state=True)
+    assert L != 0.0 and np.abs(g).max() > 0
+    r = gpu_run(F, A, w)
+    eE, eH = field_err(r["fields"], st)
+    assert eE < 1e-5 and eH < 1e-5, (eE, eH)
+    assert r["L"] == pytest.approx(L, rel=1e-5)
+    assert rel(r["g"], g) < 1e-4
+
+
 def test_bounded_device_wait_reports_a_timeout(F, A):
     """Failure detection without a fault: a wait that nothing completes gives
     up after its limit, the host reads FDTD_ETIMEOUT, and the context stays
