@@ -134,11 +134,24 @@ def algorithmic_bytes(w):
     }
 
 
-def record_bytes(w, dtype_bytes):
+def tape_values(w):
+    """Values of one tape sample: two tangential components on six faces."""
     P = w.pml_thickness
     a, b, c = w.nx - 2 * P, w.ny - 2 * P, w.nz - 2 * P
-    vals = 4 * (b * c + a * c + a * b)
-    return vals * (4 + dtype_bytes)
+    return 4 * (b * c + a * c + a * b)
+
+
+def record_bytes(w, dtype_bytes):
+    """One record launch: read every face value (FP32), write its code."""
+    return tape_values(w) * (4 + dtype_bytes)
+
+
+def restore_bytes(w, dtype_bytes, terms):
+    """One restore launch: read `terms` samples' codes per face value, write
+    the FP32 value; plus the detector seed (read E, H; read and write the
+    adjoint) on the detector window."""
+    det = (w.det_hi[0] - w.det_lo[0]) * (w.det_hi[1] - w.det_lo[1])
+    return tape_values(w) * (terms * dtype_bytes + 4) + det * 4 * 12
 
 
 def read_peaks():
@@ -310,15 +323,19 @@ def run_ours(args):
     per_step = {"fwd_h": w.n_steps, "fwd_e": w.n_steps, "rev_e": w.n_steps, "rev_h": w.n_steps,
                 "fused_fwd": w.n_steps, "fused_rev": w.n_steps,
                 "record": -(-w.n_steps // rec.k), "restore_seed": w.n_steps}
+    dtb = {0: 4, 1: 2, 2: 2}.get(rec.dtype, 1)
+    tape_algo = {"record": record_bytes(w, dtb),
+                 "restore_seed": restore_bytes(w, dtb, 2 if rec.interp == 0 else 4)}
     kern = {}
     for name, lst in ktimes.items():
         n = sum(c for _, c in lst)
         avg = sum(ms * c for ms, c in lst) / max(n, 1)
         share = avg * per_step[name] / (total_ms / args.steps)
         d = {"avg_ms": avg, "sampled_launches": n, "share_of_step": share}
-        if name in algo:
-            d["algorithmic_bytes"] = algo[name]
-            d["achieved_gbs"] = algo[name] / (avg / 1e3) / 1e9
+        ab = algo.get(name, tape_algo.get(name))
+        if ab is not None:
+            d["algorithmic_bytes"] = ab
+            d["achieved_gbs"] = ab / (avg / 1e3) / 1e9
         kern[name] = d
     dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["share_of_step"])
     digest = B._digest()
