@@ -357,15 +357,20 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   size_t f6 = al(6 * nc * sizeof(float));
   size_t psb = al(12 * nc * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
+  // the second field and forward-psi buffers exist only for the one-launch
+  // forward kernels, which write the new state next to the old one
+  const bool pingpong = h->opt_kernel == 1 || h->opt_kernel == 2 || h->opt_kernel == 6;
   size_t off = 0;
   L.F[0] = off; off += f6;
-  L.F[1] = off; off += f6;
+  L.F[1] = L.F[0];
+  if (pingpong) { L.F[1] = off; off += f6; }
   L.L[0] = off; off += f6;
-  L.L[1] = off; off += f6;
+  L.L[1] = L.L[0];
   L.cb = off; off += al(nc * sizeof(float));
   L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
   L.psiF[0] = off; off += psb;
-  L.psiF[1] = off; off += psb;
+  L.psiF[1] = L.psiF[0];
+  if (pingpong) { L.psiF[1] = off; off += psb; }
   L.psiL[0] = off; off += psb;
   L.psiL[1] = off; off += psb;
   L.gacc = off; off += al(nd * sizeof(double));
