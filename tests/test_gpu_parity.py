@@ -447,6 +447,22 @@ def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
     same_gradient(r["g"], r0["g"])
 
 
+def test_full_length_benchmark_forward(F, A):
+    """The benchmark workload itself (200 x 200 x 100, 2000 steps, BF16 tape
+    k = 4, default launch configuration) against the FP64 oracle's forward:
+    the objective of every step (the detector plane sampled 2000 times) and
+    the final fields.  After 2000 steps the pulse has left the grid and the
+    final state is a residue of ~1e-3 of the peak field, whose relative error
+    is correspondingly larger than mid-run."""
+    w = I.waveguide_mid()
+    st, obj = O.forward(w)
+    r = gpu_run(F, A, w, rec=A.record_cfg("bf16", 4, "linear"))
+    np.testing.assert_allclose(r["hist"], obj, rtol=0, atol=1e-5 * np.abs(obj).max())
+    assert r["L"] == pytest.approx(obj.sum(), rel=1e-5)
+    eE, eH = field_err(r["fields"], st)
+    assert eE < 1e-2 and eH < 1e-2, (eE, eH)
+
+
 def test_bounded_device_wait_reports_a_timeout(F, A):
     """Failure detection without a fault: a wait that nothing completes gives
     up after its limit, the host reads FDTD_ETIMEOUT, and the context stays
