@@ -628,7 +628,9 @@ __global__ void __launch_bounds__(TW / 2 * TY) k_l2rev_e(const __grid_constant__
                 const float s = lex[c] * c0[c] + ley[c] * c1[c] + lez[c] * c2[c];
                 const long long qd =
                     ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (xc - a.dlo[0]);
-                a.gacc[qd] += (double)s;
+                // one owner per cell: a fire-and-forget reduction in L2 adds
+                // exactly what a load-add-store would, without the load latency
+                atomicAdd(a.gacc + qd, (double)s);
               }
             }
           }
