@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 
@@ -1113,7 +1115,9 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   Geo g = geo_of(h);
   CK(h, launch_prep(d_eps, (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), h->stream));
   int nl = 0;
+  nvtxRangePushA("fdtd forward loop");   // host-side range (enqueue / graph launch)
   rc = run_loop(h, rec, 0, enqueue_forward, &nl, h->t0, h->t1);
+  nvtxRangePop();
   if (rc) return rc;
   h->launches_fwd = nl;
   h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
@@ -1178,7 +1182,9 @@ static int backward_async(fdtd_handle* h, double seed, double seed2) {
   if (rc) return rc;
   CK(h, upload_seeds(h, layout_of(h, &h->fwd_rec), seed, seed2, h->stream));
   int nl = 0;
+  nvtxRangePushA("fdtd backward loop");
   rc = run_loop(h, &h->fwd_rec, 1, enqueue_backward, &nl, h->t2, h->t3);
+  nvtxRangePop();
   if (rc) return rc;
   h->launches_bwd = nl;
   h->have_forward = false;

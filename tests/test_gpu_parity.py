@@ -423,6 +423,28 @@ def test_subsampling_longer_than_the_run(F, A, k):
     assert rel(r["g"], gm) < 1e-3
 
 
+@pytest.mark.parametrize("kernel", [0, 5, 6])
+def test_time_reversal_returns_to_the_initial_state(F, A, kernel):
+    """After the backward run the reconstructed interior state is the zero
+    initial state (E^0 = 0, Ht^{-1/2} = 0) up to the FP32 drift of the
+    reversal (Sec. 1-2: the interior is stepped backwards exactly in exact
+    arithmetic).  The drift is reported relative to the peak field."""
+    w = SMALL["ragged_poynting"]()
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_KERNEL, kernel)
+    eps = torch.from_numpy(w.eps).cuda()
+    sim.forward(eps, A.record_cfg("f32", 1))
+    end = sim.read_fields().cpu().numpy()
+    sim.backward()
+    back = sim.read_fields().cpu().numpy()
+    P = w.pml_thickness
+    interior = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    peak = np.abs(end[interior]).max()
+    drift = np.abs(back[interior]).max() / peak
+    print(f"kernel {kernel}: reversal drift {drift:.2e} of the peak field")
+    assert peak > 0 and drift < 1e-4
+
+
 def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
     """The 200 x 200 x 100 benchmark grid in the default launch configuration,
     shortened to 100 steps so that the FP64 oracle computes every output: the
