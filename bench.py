@@ -338,7 +338,7 @@ def run_ours(args):
             d["achieved_gbs"] = ab / (avg / 1e3) / 1e9
         kern[name] = d
     dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["share_of_step"])
-    digest = B._digest()
+    digest = B.kernel_digest()
     traffic = read_traffic(dom, digest, args.workload)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"],
                 "peak": peak, "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,

@@ -41,6 +41,22 @@ def _digest() -> str:
     return h.hexdigest()[:16]
 
 
+# Device code of the default half-step kernels: the files whose change can
+# change what those kernels move through memory.
+KERNEL_FILES = ["kernels_lag2.cu", "lag_common.cuh", "fdtd_internal.cuh", "tma.cuh"]
+
+
+def kernel_digest() -> str:
+    """Digest of the default kernels' device code and compile flags (keys the
+    recorded DRAM traffic per launch: host-only changes keep it valid)."""
+    h = hashlib.sha256()
+    for name in KERNEL_FILES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "libfdtd_gb300.stamp")
