@@ -6,6 +6,7 @@
 // only its own stream, events and CUDA graphs.  The time loops (hundreds to
 // thousands of launches) are captured once per record configuration and
 // replayed as CUDA graphs.
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -29,7 +30,8 @@ const double kC0 = 299792458.0;
 
 struct Layout {
   size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, obj2, seeds, prof, srcw, tape,
-      scales, err;
+      scales, err, tick;
+  PsiLayout plF, plL;  // layouts of the forward and adjoint auxiliary sets
   size_t total;
   long long stride;   // tape elements per sample
   int J;              // samples
@@ -37,7 +39,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x;
+      tile_x, persistent;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -82,7 +84,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x;
+      opt_prefetch, opt_tile_x, opt_persistent;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -352,12 +354,53 @@ static void interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int
 
 // ---------------------------------------------------------------- layout ---
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+static int rup4(int x) { return (x + 3) & ~3; }
+
+// Auxiliary-set layout.  Full: every axis array spans the grid (the layout
+// of the older kernels, component c of axis a at (4a + c) nc).  Compact
+// (two-cells-per-thread kernels only): the array of axis a holds only the
+// cells of a's two slabs, per axis where the grid is long enough that no
+// staged box reaches both slabs: along x the low part keeps [0, Wlo) and the
+// high slab starts at the 4-aligned cell hs, so that box starts stay on
+// 16-byte boundaries; along y and z the high slab follows the low one.
+static PsiLayout psi_layout(const fdtd_handle* h, bool compact) {
+  PsiLayout pl;
+  const int P = h->P;
+  long long off = 0;
+  for (int a = 0; a < 3; ++a) {
+    PsiAxis& A = pl.ax[a];
+    A.d0 = h->px; A.e0 = h->nx; A.d1 = h->ny; A.d2 = h->nz;
+    A.hs = INT_MAX; A.shift = 0;
+    if (compact && a == 0 && h->nx >= 2 * P + 56) {
+      const int wlo = rup4(P), hs = (h->nx - P) & ~3;
+      A.hs = hs; A.shift = hs - wlo;
+      A.e0 = wlo + (h->nx - hs);
+      A.d0 = rup4(A.e0);
+    } else if (compact && a == 1 && h->ny >= 2 * P + 24) {
+      A.hs = h->ny - P; A.shift = h->ny - 2 * P; A.d1 = 2 * P;
+    } else if (compact && a == 2 && h->nz >= 2 * P + 1) {
+      A.hs = h->nz - P; A.shift = h->nz - 2 * P; A.d2 = 2 * P;
+    }
+    A.ps = (long long)A.d0 * A.d1;
+    A.cs = A.ps * A.d2;
+    A.off = off;
+    off += 4 * A.cs;
+  }
+  pl.total = off;
+  return pl;
+}
 
 static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   Layout L;
   size_t nc = (size_t)h->nz * h->ny * h->px;
   size_t f6 = al(6 * nc * sizeof(float));
-  size_t psb = al(12 * nc * sizeof(float));
+  // the two-cells-per-thread kernels keep their auxiliaries compact: the
+  // forward set when they run the forward (kernel 5), the adjoint sets when
+  // they run the reverse (kernels 5 and 6)
+  L.plF = psi_layout(h, h->opt_kernel == 5);
+  L.plL = psi_layout(h, h->opt_kernel >= 5);
+  size_t psbF = al((size_t)L.plF.total * sizeof(float));
+  size_t psbL = al((size_t)L.plL.total * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
   // the second field and forward-psi buffers exist only for the one-launch
   // forward kernels, which write the new state next to the old one
@@ -370,11 +413,11 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   L.L[1] = L.L[0];
   L.cb = off; off += al(nc * sizeof(float));
   L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
-  L.psiF[0] = off; off += psb;
+  L.psiF[0] = off; off += psbF;
   L.psiF[1] = L.psiF[0];
-  if (pingpong) { L.psiF[1] = off; off += psb; }
-  L.psiL[0] = off; off += psb;
-  L.psiL[1] = off; off += psb;
+  if (pingpong) { L.psiF[1] = off; off += psbF; }
+  L.psiL[0] = off; off += psbL;
+  L.psiL[1] = off; off += psbL;
   L.gacc = off; off += al(nd * sizeof(double));
   L.gout = off; off += al(nd * sizeof(float));
   L.obj = off; off += al((size_t)h->N * sizeof(double));
@@ -383,6 +426,8 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   L.prof = off; off += al(h->prof.size() * sizeof(float));
   L.srcw = off; off += al((h->srcw.size() + 1) * sizeof(float));
   L.err = off; off += 256;
+  // work-unit counters of the persistent half-step launches: two per step
+  L.tick = off; off += al((size_t)2 * h->N * sizeof(int));
   int dt = rec ? rec->dtype : 0;
   int k = rec ? rec->k : 1;
   int eb = code_bytes(dt);
@@ -402,7 +447,6 @@ static Geo geo_of(const fdtd_handle* h) {
   g.plane = (long long)h->ny * h->px;
   g.nc = (long long)h->nz * g.plane;
   g.S = (float)h->S;
-  g.ps_total = 12LL * g.nc;
   g.prof = nullptr;
   return g;
 }
@@ -519,6 +563,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_pdl = 0;
   h->opt_prefetch = 0;
   h->opt_tile_x = 32;
+  h->opt_persistent = 0;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -627,6 +672,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value != 32 && value != 40) return fail(h, FDTD_EINVAL, "tile_x must be 32 or 40");
       h->opt_tile_x = value;
       break;
+    case FDTD_OPT_PERSISTENT: h->opt_persistent = value ? 1 : 0; break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -645,6 +691,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_PDL: *value = h->opt_pdl; break;
     case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
     case FDTD_OPT_TILE_X: *value = h->opt_tile_x; break;
+    case FDTD_OPT_PERSISTENT: *value = h->opt_persistent; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -860,8 +907,9 @@ static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD
 static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
   Layout L = layout_of(h, rec);
   StepArgs a = step_args(h, L);
+  a.pl = L.plF;
   size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
-  size_t psb = (size_t)a.g.ps_total * sizeof(float);
+  size_t psb = (size_t)L.plF.total * sizeof(float);
   cudaError_t e;
   int nl = 0;
   if ((e = cudaMemsetAsync(h->ws + L.F[0], 0, nc6, h->stream))) return e;
@@ -884,7 +932,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (lagk &&
       (e = encode_lag_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
                            (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
-                           a.tile_y, a.tile_x, &lmaps)))
+                           a.tile_y, a.tile_x, L.plF, &lmaps)))
     return e;
   if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
     for (int b = 0; b < 2; ++b)
@@ -899,6 +947,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     if ((e = encode_ffwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb),
                               (const float*)(h->ws + L.psiF[b]), a.g, a.tile_y, &ffmaps[b])))
       return e;
+  // per-launch work-unit counters of the persistent half-steps, zeroed once
+  int* tick = pair && h->opt_persistent ? (int*)(h->ws + L.tick) : nullptr;
+  if (tick && (e = cudaMemsetAsync(tick, 0, 2 * (size_t)h->N * sizeof(int), h->stream))) return e;
   int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
@@ -946,6 +997,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = smp.before(FDTD_K_FWD_H))) return e;
+    a.tickets = tick ? tick + 2 * n : nullptr;
     if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream) : launch_lag(0, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
       return e;
@@ -961,6 +1013,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
     }
     if ((e = smp.before(FDTD_K_FWD_E))) return e;
+    a.tickets = tick ? tick + 2 * n + 1 : nullptr;
     if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream) : launch_lag(1, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
       return e;
@@ -981,8 +1034,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
 static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
   Layout L = layout_of(h, rec);
   StepArgs a = step_args(h, L);
+  a.pl = L.plL;
   size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
-  size_t psb = (size_t)a.g.ps_total * sizeof(float);
+  size_t psb = (size_t)L.plL.total * sizeof(float);
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
   cudaError_t e;
   int nl = 0;
@@ -1007,9 +1061,11 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
       return e;
     if (rlag && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
                                      (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y, a.tile_x,
-                                     &lrmaps[b])))
+                                     L.plL, &lrmaps[b])))
       return e;
   }
+  int* tick = rpair && h->opt_persistent ? (int*)(h->ws + L.tick) : nullptr;
+  if (tick && (e = cudaMemsetAsync(tick, 0, 2 * (size_t)h->N * sizeof(int), h->stream))) return e;
   Sampler smp(h, 1);
   for (int n = h->N - 1; n >= 0; --n) {
     Interp ip;
@@ -1025,12 +1081,14 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = smp.before(FDTD_K_REV_E))) return e;
+    a.tickets = tick ? tick + 2 * n : nullptr;
     if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
                          : launch_lag(2, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_E))) return e;
     if ((e = smp.before(FDTD_K_REV_H))) return e;
+    a.tickets = tick ? tick + 2 * n + 1 : nullptr;
     if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
                          : launch_lag(3, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
@@ -1076,6 +1134,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.pdl = h->opt_pdl;
   key.prefetch = h->opt_prefetch;
   key.tile_x = h->opt_tile_x;
+  key.persistent = h->opt_persistent;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;

@@ -3,9 +3,10 @@
 // Layout in HBM (all float32 unless noted, x fastest, rows padded to px):
 //   fields   F[6][nz][ny][px]       Ex Ey Ez Hx Hy Hz   (E, Ht = eta0 H)
 //   cb       [nz][ny][px]           S / eps_r
-//   psi set  [3 axes][4][nz][ny][px] (convolutional-PML auxiliaries; only the
+//   psi set  per axis [4][nz][ny][px] (convolutional-PML auxiliaries; only the
 //            cells of each axis' absorbing slabs are ever read or written, the
-//            full-grid layout lets the TMA stage them with the field boxes)
+//            full-grid layout lets the TMA stage them with the field boxes);
+//            the two-cells-per-thread kernels use the compact PsiLayout below
 //   profiles [3 axes][6][nmax]      b_E a_E 1/kappa_E b_H a_H 1/kappa_H
 // psi components per axis slab (curl term, sign):
 //   x: 0 (Hy, -dEz/dx) 1 (Hz, +dEy/dx) 2 (Ey, -dHz/dx) 3 (Ez, +dHy/dx)
@@ -31,7 +32,6 @@ struct Geo {
   long long nc;     // nz * plane (one component)
   float S;
   const float* prof;
-  long long ps_total;       // elements per psi set (12 * nc)
 };
 
 // Source region: plane normal `axis` at `index`, cells (u,v) in [u0,u1)x[v0,v1),
@@ -79,6 +79,39 @@ __device__ __forceinline__ long long psi_y(const Geo& g, int c, int i, int j, in
 }
 __device__ __forceinline__ long long psi_z(const Geo& g, int c, int i, int j, int k) {
   return psi_at(g, 2, c, i, j, k);
+}
+
+// Layout of one CPML auxiliary set for the two-cells-per-thread kernels: per
+// axis a (x, y, z) one array of four components [4][d2][d1][d0] that holds
+// either the whole grid (full layout, d0 = px, d1 = ny, d2 = nz) or only the
+// cells of that axis' two slabs (compact layout: the axis coordinate c maps
+// to c below hs and to c - shift from hs on, which packs the high slab right
+// after the low one).
+struct PsiAxis {
+  long long off;   // element offset of the axis array within the set
+  long long cs;    // elements per component (d0 d1 d2)
+  long long ps;    // elements per plane (d0 d1)
+  int d0, d1, d2;  // array extents along x (row pitch), y, z
+  int e0;          // cells along x (<= d0; the rest of a row is padding)
+  int hs, shift;   // coordinate mapping along the axis
+};
+struct PsiLayout {
+  PsiAxis ax[3];
+  long long total;  // elements of the set
+};
+
+__device__ __forceinline__ int psi_map(const PsiAxis& A, int c) {
+  return c >= A.hs ? c - A.shift : c;
+}
+
+// Element index of component c of axis a's auxiliary at cell (x, y, z).
+template <int AX>
+__device__ __forceinline__ long long psi_ix(const PsiLayout& L, int c, int x, int y, int z) {
+  const PsiAxis& A = L.ax[AX];
+  const int xx = AX == 0 ? psi_map(A, x) : x;
+  const int yy = AX == 1 ? psi_map(A, y) : y;
+  const int zz = AX == 2 ? psi_map(A, z) : z;
+  return A.off + c * A.cs + zz * A.ps + (yy * A.d0 + xx);
 }
 
 // Plane membership: p = (i, j, k); (u, v) = the two other axes in increasing order.
@@ -203,6 +236,9 @@ struct StepArgs {
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
   int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
   int tile_x;      // two-cells-per-thread kernels: tile width (32 or 40 cells)
+  PsiLayout pl;    // layout of the auxiliary sets the two-cells-per-thread kernels use
+  int* tickets;    // two-cells-per-thread kernels: work-unit counter of this launch (zeroed
+                   // before it), or null for one unit per CTA of a 3D grid
   unsigned* err;   // device error word (ERR_*)
 };
 
@@ -235,11 +271,14 @@ cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, c
 // Tensor maps of the one-plane-per-iteration kernels for a tw x ty tile:
 // wide (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes,
 // and the psi boxes (tw+4) x ty, tw x (ty+1), tw x ty.
+// Pxw / Pyw / Po view a full-layout set as 12 components (one-cell-per-thread
+// kernels); Q* view the per-axis arrays of `pl` (4 components each): x own
+// and (tw+4) x ty boxes, y own and tw x (ty+1) boxes, z own boxes.
 struct alignas(64) LagMaps {
-  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Pxw, Pyw, Po;
+  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Pxw, Pyw, Po, Qxo, Qxw, Qyo, Qyw, Qzo;
 };
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
-                            const Geo& g, int ty, int tw, LagMaps* m);
+                            const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m);
 cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 // The same half-steps with two x-cells per thread (tile height >= 2).
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);

@@ -138,7 +138,7 @@ def test_options_are_validated(capi, fdtd):
     v = C.c_int()
     for opt, default in [(capi.OPT_KERNEL, 5), (capi.OPT_TILE_Y, 8), (capi.OPT_STAGES, 2),
                          (capi.OPT_USE_GRAPHS, 1), (capi.OPT_TILE_X, 32), (capi.OPT_PDL, 0),
-                         (capi.OPT_PREFETCH, 0)]:
+                         (capi.OPT_PREFETCH, 0), (capi.OPT_PERSISTENT, 0)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
                      (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_ROWS, 3),
@@ -177,3 +177,39 @@ def test_tape_sizes_and_compression_factors(capi, fdtd):
     assert f32 / e4k8 > 31.99
     e4k16 = sim.tape_bytes(capi.record_cfg("e4m3", 16, scaled=True))
     assert f32 / e4k16 > 63.9                        # the paper's 64x at 8 bits, k = 16
+
+
+def test_compact_auxiliary_workspace(capi, fdtd):
+    """The two-cells-per-thread kernels keep each axis' CPML auxiliaries only
+    over that axis' two slabs (x: cells [0, round_up(P, 4)) and from the
+    4-aligned cell round_down(nx - P, 4) on, rows padded to 4; y, z: 2P rows /
+    planes), per axis where the grid is long enough (nx >= 2P + 56,
+    ny >= 2P + 24, nz >= 2P + 1); the one-cell kernels keep the full grid.
+    Three sets (forward + two adjoint) differ; everything else is equal."""
+    al = lambda b: (b + 255) // 256 * 256
+
+    def full(nx, ny, nz):
+        px = (nx + 7) // 8 * 8
+        return al(12 * nz * ny * px * 4)
+
+    # 200 x 200 x 100, P = 12: every axis compact
+    w = I.waveguide_mid()
+    sim = fdtd.Simulation(w)
+    rec = capi.record_cfg("bf16", 4)
+    sim.set_option(capi.OPT_KERNEL, 4)
+    b4 = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_KERNEL, 5)
+    b5 = sim.workspace_bytes(rec)
+    compact = al(4 * (24 * 200 * 100 + 200 * 24 * 100 + 200 * 200 * 24) * 4)
+    assert b4 - b5 == 3 * (full(200, 200, 100) - compact)
+    assert compact / full(200, 200, 100) == pytest.approx(0.16)
+    # 70 x 21 x 19, P = 6: x (rows of 8 + 6 cells, pitch 16) and z (12
+    # planes) compact, y too short (full rows of px = 72)
+    w = I.ragged_box()
+    sim = fdtd.Simulation(w)
+    sim.set_option(capi.OPT_KERNEL, 4)
+    b4 = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_KERNEL, 5)
+    b5 = sim.workspace_bytes(rec)
+    compact = al(4 * (16 * 21 * 19 + 72 * 21 * 19 + 72 * 21 * 12) * 4)
+    assert b4 - b5 == 3 * (full(70, 21, 19) - compact)
