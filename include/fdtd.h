@@ -226,12 +226,9 @@ enum {
                                    next plane's boxes; 0 (default) = off */
   FDTD_OPT_TILE_X = 9,          /* kernel 5 with tile height 8 and 2 or 3 stages: tile width
                                    32 (default) or 40 cells */
-  FDTD_OPT_PERSISTENT = 10      /* kernels 5 and 6 (their two-cells-per-thread half-steps):
-                                   1 = a grid of resident CTAs takes (tile, z chunk) work units
-                                   from a counter and stages a unit's first planes while the
-                                   previous unit finishes; 0 = one unit per CTA of a 3D grid.
-                                   Shapes whose smallest z chunk has fewer planes than the
-                                   ring has stages run with 0 */
+  FDTD_OPT_COMPACT_AUX = 10     /* kernels 5 and 6: 1 (default) = their CPML auxiliaries are
+                                   stored for the slab cells only (per axis, where the grid
+                                   is long enough); 0 = full-grid arrays */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

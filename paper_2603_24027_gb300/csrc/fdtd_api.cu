@@ -30,7 +30,7 @@ const double kC0 = 299792458.0;
 
 struct Layout {
   size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, obj2, seeds, prof, srcw, tape,
-      scales, err, tick;
+      scales, err;
   PsiLayout plF, plL;  // layouts of the forward and adjoint auxiliary sets
   size_t total;
   long long stride;   // tape elements per sample
@@ -39,7 +39,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x, persistent;
+      tile_x, compact;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -84,7 +84,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_persistent;
+      opt_prefetch, opt_tile_x, opt_compact;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -397,8 +397,8 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   // the two-cells-per-thread kernels keep their auxiliaries compact: the
   // forward set when they run the forward (kernel 5), the adjoint sets when
   // they run the reverse (kernels 5 and 6)
-  L.plF = psi_layout(h, h->opt_kernel == 5);
-  L.plL = psi_layout(h, h->opt_kernel >= 5);
+  L.plF = psi_layout(h, h->opt_compact && h->opt_kernel == 5);
+  L.plL = psi_layout(h, h->opt_compact && h->opt_kernel >= 5);
   size_t psbF = al((size_t)L.plF.total * sizeof(float));
   size_t psbL = al((size_t)L.plL.total * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
@@ -426,8 +426,6 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   L.prof = off; off += al(h->prof.size() * sizeof(float));
   L.srcw = off; off += al((h->srcw.size() + 1) * sizeof(float));
   L.err = off; off += 256;
-  // work-unit counters of the persistent half-step launches: two per step
-  L.tick = off; off += al((size_t)2 * h->N * sizeof(int));
   int dt = rec ? rec->dtype : 0;
   int k = rec ? rec->k : 1;
   int eb = code_bytes(dt);
@@ -563,7 +561,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_pdl = 0;
   h->opt_prefetch = 0;
   h->opt_tile_x = 32;
-  h->opt_persistent = 0;
+  h->opt_compact = 1;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -643,6 +641,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
       if (value < 0 || value > 6) return fail(h, FDTD_EINVAL, "kernel must be 0..6");
+      if (value != h->opt_kernel) h->have_forward = false;   // the workspace layout changes
       h->opt_kernel = value;
       break;
     case FDTD_OPT_TILE_Y:
@@ -672,7 +671,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value != 32 && value != 40) return fail(h, FDTD_EINVAL, "tile_x must be 32 or 40");
       h->opt_tile_x = value;
       break;
-    case FDTD_OPT_PERSISTENT: h->opt_persistent = value ? 1 : 0; break;
+    case FDTD_OPT_COMPACT_AUX:
+      if ((value ? 1 : 0) != h->opt_compact) h->have_forward = false;   // layout changes
+      h->opt_compact = value ? 1 : 0;
+      break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -691,7 +693,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_PDL: *value = h->opt_pdl; break;
     case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
     case FDTD_OPT_TILE_X: *value = h->opt_tile_x; break;
-    case FDTD_OPT_PERSISTENT: *value = h->opt_persistent; break;
+    case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -947,9 +949,6 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     if ((e = encode_ffwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb),
                               (const float*)(h->ws + L.psiF[b]), a.g, a.tile_y, &ffmaps[b])))
       return e;
-  // per-launch work-unit counters of the persistent half-steps, zeroed once
-  int* tick = pair && h->opt_persistent ? (int*)(h->ws + L.tick) : nullptr;
-  if (tick && (e = cudaMemsetAsync(tick, 0, 2 * (size_t)h->N * sizeof(int), h->stream))) return e;
   int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
@@ -997,7 +996,6 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = smp.before(FDTD_K_FWD_H))) return e;
-    a.tickets = tick ? tick + 2 * n : nullptr;
     if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream) : launch_lag(0, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
       return e;
@@ -1013,7 +1011,6 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
     }
     if ((e = smp.before(FDTD_K_FWD_E))) return e;
-    a.tickets = tick ? tick + 2 * n + 1 : nullptr;
     if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream) : launch_lag(1, lmaps, a, h->stream))
                   : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
       return e;
@@ -1064,8 +1061,6 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                      L.plL, &lrmaps[b])))
       return e;
   }
-  int* tick = rpair && h->opt_persistent ? (int*)(h->ws + L.tick) : nullptr;
-  if (tick && (e = cudaMemsetAsync(tick, 0, 2 * (size_t)h->N * sizeof(int), h->stream))) return e;
   Sampler smp(h, 1);
   for (int n = h->N - 1; n >= 0; --n) {
     Interp ip;
@@ -1081,14 +1076,12 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = smp.before(FDTD_K_REV_E))) return e;
-    a.tickets = tick ? tick + 2 * n : nullptr;
     if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
                          : launch_lag(2, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_E))) return e;
     if ((e = smp.before(FDTD_K_REV_H))) return e;
-    a.tickets = tick ? tick + 2 * n + 1 : nullptr;
     if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
                          : launch_lag(3, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
@@ -1134,7 +1127,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.pdl = h->opt_pdl;
   key.prefetch = h->opt_prefetch;
   key.tile_x = h->opt_tile_x;
-  key.persistent = h->opt_persistent;
+  key.compact = h->opt_compact;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1237,6 +1230,8 @@ static cudaError_t upload_seeds(fdtd_handle* h, const Layout& L, double seed, do
 
 static int backward_async(fdtd_handle* h, double seed, double seed2) {
   if (!h->have_forward) return fail(h, FDTD_ESTATE, "backward needs a preceding forward");
+  if (layout_of(h, &h->fwd_rec).total > h->ws_bytes)
+    return fail(h, FDTD_ENOMEM, "workspace too small for this record config");
   int rc = begin(h);
   if (rc) return rc;
   CK(h, upload_seeds(h, layout_of(h, &h->fwd_rec), seed, seed2, h->stream));

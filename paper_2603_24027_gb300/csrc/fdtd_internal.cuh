@@ -237,8 +237,6 @@ struct StepArgs {
   int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
   int tile_x;      // two-cells-per-thread kernels: tile width (32 or 40 cells)
   PsiLayout pl;    // layout of the auxiliary sets the two-cells-per-thread kernels use
-  int* tickets;    // two-cells-per-thread kernels: work-unit counter of this launch (zeroed
-                   // before it), or null for one unit per CTA of a 3D grid
   unsigned* err;   // device error word (ERR_*)
 };
 

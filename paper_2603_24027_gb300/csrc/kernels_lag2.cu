@@ -16,11 +16,6 @@
 // increment instead of a modulo per plane.
 #include <cudaTypedefs.h>
 
-#include <algorithm>
-#include <map>
-#include <mutex>
-#include <tuple>
-
 #include "lag_common.cuh"
 
 namespace fdtd {
@@ -104,93 +99,13 @@ __device__ __forceinline__ void psi_box_starts(const PsiLayout& pl, int x0, int 
   *qy0 = y0 + TY + 1 > Yy.hs ? y0 - Yy.shift : y0;
 }
 
-// ------------------------------------------------------------ work units --
-// A work unit is one TW x TY column tile and one z chunk, numbered with x
-// fastest, then y, then the chunk: the order in which the hardware hands out
-// the CTAs of a 3D grid, which keeps z-neighbouring chunks (whose halo planes
-// they share through L2) close in time.  Without a ticket counter every CTA of
-// a 3D grid processes the one unit of its block index.  With one (a.tickets,
-// a counter zeroed before the launch), a grid of resident CTAs processes
-// units until they run out: a CTA's first unit is blockIdx.x, each further
-// one is gridDim.x plus the counter's next value, fetched when the CTA starts
-// its previous unit, so that the ring can stage the next unit's first planes
-// while the current unit finishes.
-struct Units {
-  int ntx, nty, n;
-};
-struct UnitGeo {
-  int x0, y0, k0, k1;  // tile origin, z chunk [k0, k1)
-  int p0, p1;          // planes the kernel stages for the unit
-  int qx0, qy0;        // auxiliary box starts
-  bool txs, tys, tint;
-};
-
-template <int TW, int TY>
-__device__ __forceinline__ Units units_of(const StepArgs& a) {
-  Units U;
-  U.ntx = (a.g.nx + TW - 1) / TW;
-  U.nty = (a.g.ny + TY - 1) / TY;
-  U.n = U.ntx * U.nty * ((a.g.nz + a.zchunk - 1) / a.zchunk);
-  return U;
-}
-
-template <int TW, int TY>
-__device__ __forceinline__ UnitGeo unit_geo(const StepArgs& a, const Units& N, int u) {
-  UnitGeo G;
-  const int t = u / N.ntx;
-  G.x0 = (u - t * N.ntx) * TW;
-  const int bz = t / N.nty;
-  G.y0 = (t - bz * N.nty) * TY;
-  G.k0 = bz * a.zchunk;
-  G.k1 = min(a.g.nz, G.k0 + a.zchunk);
-  psi_box_starts<TW, TY>(a.pl, G.x0, G.y0, &G.qx0, &G.qy0);
-  G.tint = G.x0 + TW - 1 >= a.g.P && G.x0 < a.g.nx - a.g.P && G.y0 + TY - 1 >= a.g.P &&
-           G.y0 < a.g.ny - a.g.P;
-  return G;
-}
-
-__device__ __forceinline__ int first_unit(const StepArgs& a, const Units& N) {
-  return a.tickets ? (int)blockIdx.x
-                   : (int)(blockIdx.x + N.ntx * (blockIdx.y + N.nty * blockIdx.z));
-}
-
-__device__ __forceinline__ int next_unit(const StepArgs& a, const Units& N) {
-  return a.tickets ? (int)gridDim.x + atomicAdd(a.tickets, 1) : N.n;
-}
-
-// Producer cursor of the plane ring (used by thread 0 only): ordinal and id of
-// the unit it stages and the next plane; s_u[ord & 1] holds the id of the
-// CTA's unit of ordinal ord.  The cursor runs at most S planes ahead of the
-// consumers, which stays within the next unit because no unit has fewer
-// than S planes (the host checks this).
-struct Cursor {
-  int ord, u, p, issued;
-};
-
-template <class UG, class Issue>
-__device__ __forceinline__ void produce(Cursor& c, const int* s_u, int n, const UG& ugeo,
-                                        const Issue& issue, unsigned char* st, uint64_t* bar) {
-  if (c.u >= n) return;
-  UnitGeo G = ugeo(c.u);
-  if (c.p > G.p1) {
-    ++c.ord;
-    c.u = s_u[c.ord & 1];
-    if (c.u >= n) return;
-    G = ugeo(c.u);
-    c.p = G.p0;
-  }
-  issue(G, c.p, st, bar);
-  ++c.p;
-  ++c.issued;
-}
-
-// Minimum resident CTAs per SM the register allocation must allow for the
-// default 32 x 8 tiles with two stages: what shared memory allows for the
-// reverse phases (5), seven for the forward half-steps; other shapes leave
-// the allocation to the compiler.
+// Resident CTAs per SM the register allocation must allow for the default
+// 32 x 8 tiles with two stages: eight for the forward half-steps (what their
+// shared memory allows), five for the reverse phases (idem); other shapes
+// leave the allocation to the compiler.
 template <int TY, int S, int TW>
 constexpr int min_ctas(bool fwd) {
-  return (TY == 8 && S == 2 && TW == 32) ? (fwd ? 7 : 5) : 1;
+  return (TY == 8 && S == 2 && TW == 32) ? (fwd ? 8 : 5) : 1;
 }
 
 template <int S>
@@ -223,44 +138,6 @@ __device__ void ring_abort(uint64_t* bars, int stg, uint32_t par, int p, int p1,
   }
 }
 
-// Start the ring: the CTA's first unit goes to s_u[0] and thread 0 stages the
-// first S planes; returns after a barrier, with s_u[0] visible to all.
-template <int S, class UG, class Issue>
-__device__ __forceinline__ void ring_start(const StepArgs& a, const Units& N, int* s_u, Cursor& c,
-                                           const UG& ugeo, const Issue& issue, unsigned char* dsm,
-                                           int stage_bytes, uint64_t* bars) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const int u0 = first_unit(a, N);
-    s_u[0] = u0;
-    s_u[1] = N.n;   // the next unit is fetched later: the prologue stays within unit 0
-    c.ord = 0;
-    c.u = u0;
-    c.p = u0 < N.n ? ugeo(u0).p0 : 0;
-    c.issued = 0;
-    for (int i = 0; i < S; ++i) produce(c, s_u, N.n, ugeo, issue, dsm + i * stage_bytes, bars + i);
-  }
-  __syncthreads();
-}
-
-// A wait gave up: record the timeout and wait, bounded, for the n_out copies
-// issued and not yet consumed (stages stg, stg + 1, ... in ring order) so
-// that no copy lands in shared memory after the CTA has left.
-template <int S>
-__device__ void ring_abort_n(uint64_t* bars, int stg, uint32_t par, int n_out, unsigned* err) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    atomicOr(err, ERR_TIMEOUT);
-    for (int i = 0; i < S && i < n_out; ++i) {
-      int s = stg + i;
-      uint32_t ph = par;
-      if (s >= S) {
-        s -= S;
-        ph ^= 1u;
-      }
-      mbar_wait(&bars[s], ph, kWaitCycles);
-    }
-  }
-}
-
 }  // namespace lag2
 
 using namespace lag2;
@@ -268,395 +145,365 @@ using namespace lag2;
 // =================================================== forward H half-step ===
 template <int TY, int S, int TW>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
-k_l2fwd_h(const __grid_constant__ LagMaps m,
-                                                    StepArgs a) {
+k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LFH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  __shared__ int s_u[2];
-  const Units NU = units_of<TW, TY>(a);
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
-  auto ugeo = [&](int u) {
-    UnitGeo U = unit_geo<TW, TY>(a, NU, u);
-    // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
-    U.p0 = U.k0;
-    U.p1 = U.k1;
-    U.txs = tile_in_slab(U.x0, min(U.x0 + TW - 1, g.nx - 1), g.nx, g.P);
-    U.tys = tile_in_slab(U.y0, min(U.y0 + TY - 1, g.ny - 1), g.ny, g.P);
-    return U;
-  };
-  auto boxes = [&](const UnitGeo& U, int p, auto&& f) {
-    const bool body = p < U.k1;
+  int qx0, qy0;
+  psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
+  auto boxes = [&](int p, auto&& f) {
+    const bool body = p < k1;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    f(Y::E, &m.Fw, U.x0, U.y0, p, 0, 3 * B::P * 4);
-    if (body) f(Y::H, &m.Fo, U.x0, U.y0, p, 3, 3 * B::OP * 4);
-    if (body && U.txs) f(Y::PX, &m.Qxo, U.qx0, U.y0, p, 0, 2 * B::OP * 4);
-    if (body && U.tys) f(Y::PY, &m.Qyo, U.x0, U.qy0, p, 0, 2 * B::OP * 4);
-    if (zs) f(Y::PZ, &m.Qzo, U.x0, U.y0, psi_map(a.pl.ax[2], p), 0, 2 * B::OP * 4);
+    f(Y::E, &m.Fw, x0, y0, p, 0, 3 * B::P * 4);
+    if (body) f(Y::H, &m.Fo, x0, y0, p, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Qxo, qx0, y0, p, 0, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.Qyo, x0, qy0, p, 0, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.Qzo, x0, y0, psi_map(a.pl.ax[2], p), 0, 2 * B::OP * 4);
   };
-  auto issue = [&](const UnitGeo& U, int p, unsigned char* st, uint64_t* bar) {
-    stage_plane([&](int pp, auto&& f) { boxes(U, pp, f); }, p, st, bar,
-                a.prefetch && p + 1 <= U.p1 && p + 1 >= 0 && p + 1 < g.nz);
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= k1 && p + 1 < g.nz);
   };
   pdl_sync();
-  Cursor cur;
-  ring_start<S>(a, NU, s_u, cur, ugeo, issue, dsm, Y::STAGE, bars);
-  int stg = 0, done = 0, ord = 0;
+  if (tid == 0)
+    for (int i = 0; i < S && k0 + i <= k1; ++i) issue(k0 + i, dsm + i * Y::STAGE, bars + i);
+  const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
+  const bool sy = v0 && in_slab(y, g.ny, g.P);
+  float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f;
+  float by = 0.f, ay = 0.f, ky = 1.f;
+  if (sx0) { bx0 = prof(g, 0, PR_BH, x); ax0 = prof(g, 0, PR_AH, x); kx0 = prof(g, 0, PR_KH, x); }
+  if (sx1) { bx1 = prof(g, 0, PR_BH, x + 1); ax1 = prof(g, 0, PR_AH, x + 1); kx1 = prof(g, 0, PR_KH, x + 1); }
+  if (sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
+  const int hb = ty * B::W + 2 * tx;   // own pair in a hi box
+  const int ob = ty * TW + 2 * tx;     // own pair in an own box
+  const long long nc = g.nc;
+  float* const Hx = a.F + 3 * nc;
+  float* const Hy = Hx + nc;
+  float* const Hz = Hy + nc;
+  float* const psi = a.psiA;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;   // plane of the carried pair
+  // carried state of Ht(p-1), per cell of the pair
+  float c_ex[2] = {0.f, 0.f}, c_ey[2] = {0.f, 0.f}, c_t0[2] = {0.f, 0.f}, c_t3[2] = {0.f, 0.f};
+  float c_t4[2] = {0.f, 0.f}, c_t5[2] = {0.f, 0.f}, c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};
+  float c_hz[2] = {0.f, 0.f}, c_pz0[2] = {0.f, 0.f}, c_pz1[2] = {0.f, 0.f};
+  int stg = 0;
   uint32_t par = 0;
   bool ok = true;
-  for (int u = s_u[0]; u < NU.n; u = s_u[++ord & 1]) {
-    const int nxt = tid == 0 ? next_unit(a, NU) : 0;   // the CTA's next unit
-    const UnitGeo U = ugeo(u);
-    const int x0 = U.x0, y0 = U.y0, k0 = U.k0, k1 = U.k1;
-    const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-    const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
-    const bool sy = v0 && in_slab(y, g.ny, g.P);
-    float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f;
-    float by = 0.f, ay = 0.f, ky = 1.f;
-    if (sx0) { bx0 = prof(g, 0, PR_BH, x); ax0 = prof(g, 0, PR_AH, x); kx0 = prof(g, 0, PR_KH, x); }
-    if (sx1) { bx1 = prof(g, 0, PR_BH, x + 1); ax1 = prof(g, 0, PR_AH, x + 1); kx1 = prof(g, 0, PR_KH, x + 1); }
-    if (sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
-    const int hb = ty * B::W + 2 * tx;   // own pair in a hi box
-    const int ob = ty * TW + 2 * tx;     // own pair in an own box
-    const long long nc = g.nc;
-    float* const Hx = a.F + 3 * nc;
-    float* const Hy = Hx + nc;
-    float* const Hz = Hy + nc;
-    float* const psi = a.psiA;
-    long long q = (long long)k0 * g.plane + (long long)y * g.px + x;   // plane of the carried pair
-    // carried state of Ht(p-1), per cell of the pair
-    float c_ex[2] = {0.f, 0.f}, c_ey[2] = {0.f, 0.f}, c_t0[2] = {0.f, 0.f}, c_t3[2] = {0.f, 0.f};
-    float c_t4[2] = {0.f, 0.f}, c_t5[2] = {0.f, 0.f}, c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};
-    float c_hz[2] = {0.f, 0.f}, c_pz0[2] = {0.f, 0.f}, c_pz1[2] = {0.f, 0.f};
-    for (int p = k0; p <= k1; ++p) {
-      unsigned char* st = dsm + stg * Y::STAGE;
-      if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
-      if (!__syncthreads_and(ok)) { ring_abort_n<S>(bars, stg, par, cur.issued - done, a.err); return; }
-      const float* Eb = reinterpret_cast<const float*>(st + Y::E);
-      if (v0) {
-        const float2 ex2 = ld2(Eb, hb), ey2 = ld2(Eb + B::P, hb);
-        const float ex[2] = {ex2.x, ex2.y}, ey[2] = {ey2.x, ey2.y};
-        if (p > k0) {  // finish Ht(p-1) with dEy/dz and dEx/dz
-          const int k = p - 1;
-          float t1[2], t2[2];
-  #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            t1[c] = ey[c] - c_ey[c];
-            t2[c] = ex[c] - c_ex[c];
-          }
-          if (in_slab(k, g.nz, g.P)) {
-            const float bz = prof(g, 2, PR_BH, k), az = prof(g, 2, PR_AH, k), kz = prof(g, 2, PR_KH, k);
-            float s1[2], s2[2];
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              t1[c] = cpml(t1[c], c_pz0[c], bz, az, kz, &s1[c]);
-              t2[c] = cpml(t2[c], c_pz1[c], bz, az, kz, &s2[c]);
-            }
-            const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
-            st2(psi, qz, s1[0], s1[1], true, v1);
-            st2(psi + a.pl.ax[2].cs, qz, s2[0], s2[1], true, v1);
-          }
-          float hx[2], hy[2], hz[2];
-  #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float cx = c_t0[c] - t1[c], cy = t2[c] - c_t3[c], cz = c_t4[c] - c_t5[c];
-            hx[c] = __fsub_rn(c_hx[c], __fmul_rn(g.S, cx));
-            hy[c] = __fsub_rn(c_hy[c], __fmul_rn(g.S, cy));
-            hz[c] = __fsub_rn(c_hz[c], __fmul_rn(g.S, cz));
-          }
-          st2(Hx, q, hx[0], hx[1], true, v1);
-          st2(Hy, q, hy[0], hy[1], true, v1);
-          st2(Hz, q, hz[0], hz[1], true, v1);
-          q += g.plane;
+  for (int p = k0; p <= k1; ++p) {
+    unsigned char* st = dsm + stg * Y::STAGE;
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, k1, a.err); return; }
+    const float* Eb = reinterpret_cast<const float*>(st + Y::E);
+    if (v0) {
+      const float2 ex2 = ld2(Eb, hb), ey2 = ld2(Eb + B::P, hb);
+      const float ex[2] = {ex2.x, ex2.y}, ey[2] = {ey2.x, ey2.y};
+      if (p > k0) {  // finish Ht(p-1) with dEy/dz and dEx/dz
+        const int k = p - 1;
+        float t1[2], t2[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          t1[c] = ey[c] - c_ey[c];
+          t2[c] = ex[c] - c_ex[c];
         }
-        if (p < k1) {  // start Ht(p): x and y derivatives, their psi updates
-          const float2 ez2 = ld2(Eb + 2 * B::P, hb);
-          const float2 ezy = ld2(Eb + 2 * B::P, hb + B::W), exy = ld2(Eb, hb + B::W);
-          const float ezx = Eb[2 * B::P + hb + 2], eyx = Eb[B::P + hb + 2];
-          float t0[2] = {ezy.x - ez2.x, ezy.y - ez2.y};   // dEz/dy
-          float t3[2] = {ez2.y - ez2.x, ezx - ez2.y};     // dEz/dx
-          float t4[2] = {ey[1] - ey[0], eyx - ey[1]};     // dEy/dx
-          float t5[2] = {exy.x - ex[0], exy.y - ex[1]};   // dEx/dy
-          if (sx0 || sx1) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PX);
-            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-            float s3[2] = {0.f, 0.f}, s4[2] = {0.f, 0.f};
-            if (sx0) {
-              t3[0] = cpml(t3[0], p0.x, bx0, ax0, kx0, &s3[0]);
-              t4[0] = cpml(t4[0], p1.x, bx0, ax0, kx0, &s4[0]);
-            }
-            if (sx1) {
-              t3[1] = cpml(t3[1], p0.y, bx1, ax1, kx1, &s3[1]);
-              t4[1] = cpml(t4[1], p1.y, bx1, ax1, kx1, &s4[1]);
-            }
-            const long long qxx = psi_ix<0>(a.pl, 0, x, y, p);
-            st2(psi, qxx, s3[0], s3[1], sx0, sx1);
-            st2(psi + a.pl.ax[0].cs, qxx, s4[0], s4[1], sx0, sx1);
-          }
-          if (sy) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PY);
-            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-            float s0[2], s5[2];
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              t0[c] = cpml(t0[c], q0[c], by, ay, ky, &s0[c]);
-              t5[c] = cpml(t5[c], q1[c], by, ay, ky, &s5[c]);
-            }
-            const long long qyy = psi_ix<1>(a.pl, 0, x, y, p);
-            st2(psi, qyy, s0[0], s0[1], true, v1);
-            st2(psi + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
-          }
-          const float* Ho = reinterpret_cast<const float*>(st + Y::H);
-          const float2 h0 = ld2(Ho, ob), h1 = ld2(Ho + B::OP, ob), h2 = ld2(Ho + 2 * B::OP, ob);
-  #pragma unroll
+        if (in_slab(k, g.nz, g.P)) {
+          const float bz = prof(g, 2, PR_BH, k), az = prof(g, 2, PR_AH, k), kz = prof(g, 2, PR_KH, k);
+          float s1[2], s2[2];
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
-            c_ex[c] = ex[c];
-            c_ey[c] = ey[c];
-            c_t0[c] = t0[c];
-            c_t3[c] = t3[c];
-            c_t4[c] = t4[c];
-            c_t5[c] = t5[c];
+            t1[c] = cpml(t1[c], c_pz0[c], bz, az, kz, &s1[c]);
+            t2[c] = cpml(t2[c], c_pz1[c], bz, az, kz, &s2[c]);
           }
-          c_hx[0] = h0.x; c_hx[1] = h0.y;
-          c_hy[0] = h1.x; c_hy[1] = h1.y;
-          c_hz[0] = h2.x; c_hz[1] = h2.y;
-          if (in_slab(p, g.nz, g.P)) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-            c_pz0[0] = p0.x; c_pz0[1] = p0.y;
-            c_pz1[0] = p1.x; c_pz1[1] = p1.y;
+          const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
+          st2(psi, qz, s1[0], s1[1], true, v1);
+          st2(psi + a.pl.ax[2].cs, qz, s2[0], s2[1], true, v1);
+        }
+        float hx[2], hy[2], hz[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float cx = c_t0[c] - t1[c], cy = t2[c] - c_t3[c], cz = c_t4[c] - c_t5[c];
+          hx[c] = __fsub_rn(c_hx[c], __fmul_rn(g.S, cx));
+          hy[c] = __fsub_rn(c_hy[c], __fmul_rn(g.S, cy));
+          hz[c] = __fsub_rn(c_hz[c], __fmul_rn(g.S, cz));
+        }
+        st2(Hx, q, hx[0], hx[1], true, v1);
+        st2(Hy, q, hy[0], hy[1], true, v1);
+        st2(Hz, q, hz[0], hz[1], true, v1);
+        q += g.plane;
+      }
+      if (p < k1) {  // start Ht(p): x and y derivatives, their psi updates
+        const float2 ez2 = ld2(Eb + 2 * B::P, hb);
+        const float2 ezy = ld2(Eb + 2 * B::P, hb + B::W), exy = ld2(Eb, hb + B::W);
+        const float ezx = Eb[2 * B::P + hb + 2], eyx = Eb[B::P + hb + 2];
+        float t0[2] = {ezy.x - ez2.x, ezy.y - ez2.y};   // dEz/dy
+        float t3[2] = {ez2.y - ez2.x, ezx - ez2.y};     // dEz/dx
+        float t4[2] = {ey[1] - ey[0], eyx - ey[1]};     // dEy/dx
+        float t5[2] = {exy.x - ex[0], exy.y - ex[1]};   // dEx/dy
+        if (sx0 || sx1) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PX);
+          const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+          float s3[2] = {0.f, 0.f}, s4[2] = {0.f, 0.f};
+          if (sx0) {
+            t3[0] = cpml(t3[0], p0.x, bx0, ax0, kx0, &s3[0]);
+            t4[0] = cpml(t4[0], p1.x, bx0, ax0, kx0, &s4[0]);
           }
+          if (sx1) {
+            t3[1] = cpml(t3[1], p0.y, bx1, ax1, kx1, &s3[1]);
+            t4[1] = cpml(t4[1], p1.y, bx1, ax1, kx1, &s4[1]);
+          }
+          const long long qxx = psi_ix<0>(a.pl, 0, x, y, p);
+          st2(psi, qxx, s3[0], s3[1], sx0, sx1);
+          st2(psi + a.pl.ax[0].cs, qxx, s4[0], s4[1], sx0, sx1);
+        }
+        if (sy) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PY);
+          const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+          const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+          float s0[2], s5[2];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            t0[c] = cpml(t0[c], q0[c], by, ay, ky, &s0[c]);
+            t5[c] = cpml(t5[c], q1[c], by, ay, ky, &s5[c]);
+          }
+          const long long qyy = psi_ix<1>(a.pl, 0, x, y, p);
+          st2(psi, qyy, s0[0], s0[1], true, v1);
+          st2(psi + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
+        }
+        const float* Ho = reinterpret_cast<const float*>(st + Y::H);
+        const float2 h0 = ld2(Ho, ob), h1 = ld2(Ho + B::OP, ob), h2 = ld2(Ho + 2 * B::OP, ob);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          c_ex[c] = ex[c];
+          c_ey[c] = ey[c];
+          c_t0[c] = t0[c];
+          c_t3[c] = t3[c];
+          c_t4[c] = t4[c];
+          c_t5[c] = t5[c];
+        }
+        c_hx[0] = h0.x; c_hx[1] = h0.y;
+        c_hy[0] = h1.x; c_hy[1] = h1.y;
+        c_hz[0] = h2.x; c_hz[1] = h2.y;
+        if (in_slab(p, g.nz, g.P)) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PZ);
+          const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+          c_pz0[0] = p0.x; c_pz0[1] = p0.y;
+          c_pz1[0] = p1.x; c_pz1[1] = p1.y;
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        if (p == U.p0) s_u[(ord + 1) & 1] = nxt;
-        produce(cur, s_u, NU.n, ugeo, issue, st, bars + stg);
-      }
-      if (++stg == S) { stg = 0; par ^= 1u; }
-      ++done;
     }
+    __syncthreads();
+    if (tid == 0 && p + S <= k1) issue(p + S, st, bars + stg);
+    if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }
 
 // =================================================== forward E half-step ===
 template <int TY, int S, int TW>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
-k_l2fwd_e(const __grid_constant__ LagMaps m,
-                                                    StepArgs a) {
+k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LFE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  __shared__ int s_u[2];
-  const Units NU = units_of<TW, TY>(a);
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  // plane k0-1 only provides Ht(k0-1) at the own pair
+  const int p0_ = k0 - 1, p1_ = k1 - 1;
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
   double* red = reinterpret_cast<double*>(dsm + S * Y::STAGE + 8 * S + 64);
-  double lsum = 0.0;
-  auto ugeo = [&](int u) {
-    UnitGeo U = unit_geo<TW, TY>(a, NU, u);
-    // plane k0-1 only provides Ht(k0-1) at the own pair
-    U.p0 = U.k0 - 1;
-    U.p1 = U.k1 - 1;
-    U.txs = tile_in_slab(U.x0, min(U.x0 + TW - 1, g.nx - 1), g.nx, g.P);
-    U.tys = tile_in_slab(U.y0, min(U.y0 + TY - 1, g.ny - 1), g.ny, g.P);
-    return U;
-  };
-  auto boxes = [&](const UnitGeo& U, int p, auto&& f) {
-    const bool body = p >= U.k0;
+  int qx0, qy0;
+  psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
+  auto boxes = [&](int p, auto&& f) {
+    const bool body = p >= k0;
     const bool zs = body && in_slab(p, g.nz, g.P);
-    f(Y::H, &m.Fw, U.x0 - 4, U.y0 - 1, p, 3, 3 * B::P * 4);
+    f(Y::H, &m.Fw, x0 - 4, y0 - 1, p, 3, 3 * B::P * 4);
     if (body) {
-      f(Y::E, &m.Fo, U.x0, U.y0, p, 0, 3 * B::OP * 4);
-      f(Y::CB, &m.cbo, U.x0, U.y0, p, 0, B::OP * 4);
+      f(Y::E, &m.Fo, x0, y0, p, 0, 3 * B::OP * 4);
+      f(Y::CB, &m.cbo, x0, y0, p, 0, B::OP * 4);
     }
-    if (body && U.txs) f(Y::PX, &m.Qxo, U.qx0, U.y0, p, 2, 2 * B::OP * 4);
-    if (body && U.tys) f(Y::PY, &m.Qyo, U.x0, U.qy0, p, 2, 2 * B::OP * 4);
-    if (zs) f(Y::PZ, &m.Qzo, U.x0, U.y0, psi_map(a.pl.ax[2], p), 2, 2 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Qxo, qx0, y0, p, 2, 2 * B::OP * 4);
+    if (body && tys) f(Y::PY, &m.Qyo, x0, qy0, p, 2, 2 * B::OP * 4);
+    if (zs) f(Y::PZ, &m.Qzo, x0, y0, psi_map(a.pl.ax[2], p), 2, 2 * B::OP * 4);
   };
-  auto issue = [&](const UnitGeo& U, int p, unsigned char* st, uint64_t* bar) {
-    stage_plane([&](int pp, auto&& f) { boxes(U, pp, f); }, p, st, bar,
-                a.prefetch && p + 1 <= U.p1 && p + 1 >= 0 && p + 1 < g.nz);
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
   };
   pdl_sync();
-  Cursor cur;
-  ring_start<S>(a, NU, s_u, cur, ugeo, issue, dsm, Y::STAGE, bars);
-  int stg = 0, done = 0, ord = 0;
+  if (tid == 0)
+    for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
+  const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
+  const bool sy = v0 && in_slab(y, g.ny, g.P);
+  float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f;
+  float by = 0.f, ay = 0.f, ky = 1.f;
+  if (sx0) { bx0 = prof(g, 0, PR_BE, x); ax0 = prof(g, 0, PR_AE, x); kx0 = prof(g, 0, PR_KE, x); }
+  if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
+  if (sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
+  const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
+  const int ob = ty * TW + 2 * tx;
+  const long long nc = g.nc;
+  float* const Ex = a.F;
+  float* const Ey = Ex + nc;
+  float* const Ez = Ey + nc;
+  float* const psi = a.psiA;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};   // Ht(p-1) at the own pair
+  double lsum = 0.0;
+  int stg = 0;
   uint32_t par = 0;
   bool ok = true;
-  for (int u = s_u[0]; u < NU.n; u = s_u[++ord & 1]) {
-    const int nxt = tid == 0 ? next_unit(a, NU) : 0;   // the CTA's next unit
-    const UnitGeo U = ugeo(u);
-    const int x0 = U.x0, y0 = U.y0, k0 = U.k0;
-    const int p0_ = U.p0, p1_ = U.p1;
-    const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-    const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
-    const bool sy = v0 && in_slab(y, g.ny, g.P);
-    float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f;
-    float by = 0.f, ay = 0.f, ky = 1.f;
-    if (sx0) { bx0 = prof(g, 0, PR_BE, x); ax0 = prof(g, 0, PR_AE, x); kx0 = prof(g, 0, PR_KE, x); }
-    if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
-    if (sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
-    const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
-    const int ob = ty * TW + 2 * tx;
-    const long long nc = g.nc;
-    float* const Ex = a.F;
-    float* const Ey = Ex + nc;
-    float* const Ez = Ey + nc;
-    float* const psi = a.psiA;
-    long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
-    float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};   // Ht(p-1) at the own pair
-    for (int p = p0_; p <= p1_; ++p) {
-      unsigned char* st = dsm + stg * Y::STAGE;
-      if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
-      if (!__syncthreads_and(ok)) { ring_abort_n<S>(bars, stg, par, cur.issued - done, a.err); return; }
-      const float* Hb = reinterpret_cast<const float*>(st + Y::H);
-      if (v0) {
-        const float2 hx2 = ld2(Hb, lb), hy2 = ld2(Hb + B::P, lb), hz2 = ld2(Hb + 2 * B::P, lb);
-        const float hx[2] = {hx2.x, hx2.y}, hy[2] = {hy2.x, hy2.y}, hz[2] = {hz2.x, hz2.y};
-        if (p >= k0) {
-          const int k = p;
-          const float2 hzy = ld2(Hb + 2 * B::P, lb - B::W), hxy = ld2(Hb, lb - B::W);
-          const float hzx = Hb[2 * B::P + lb - 1], hyx = Hb[B::P + lb - 1];
-          const float d6[2] = {hz[0] - hzy.x, hz[1] - hzy.y};      // dHz/dy
-          const float d7[2] = {hy[0] - c_hy[0], hy[1] - c_hy[1]};  // dHy/dz
-          const float d8[2] = {hx[0] - c_hx[0], hx[1] - c_hx[1]};  // dHx/dz
-          const float d9[2] = {hz[0] - hzx, hz[1] - hz[0]};        // dHz/dx
-          const float d10[2] = {hy[0] - hyx, hy[1] - hy[0]};       // dHy/dx
-          const float d11[2] = {hx[0] - hxy.x, hx[1] - hxy.y};     // dHx/dy
-          const bool sz = in_slab(k, g.nz, g.P);
-          float c0[2], c1[2], c2[2];
-          if (!(sx0 || sx1 || sy || sz)) {
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              c0[c] = d6[c] - d7[c];
-              c1[c] = d8[c] - d9[c];
-              c2[c] = d10[c] - d11[c];
-            }
-          } else {
-            float t6[2], t7[2], t8[2], t9[2], t10[2], t11[2];
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              t6[c] = d6[c]; t7[c] = d7[c]; t8[c] = d8[c];
-              t9[c] = d9[c]; t10[c] = d10[c]; t11[c] = d11[c];
-            }
-            if (sx0 || sx1) {
-              const float* P = reinterpret_cast<const float*>(st + Y::PX);
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-              float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
-              if (sx0) {
-                t9[0] = cpml(d9[0], p0.x, bx0, ax0, kx0, &s9[0]);
-                t10[0] = cpml(d10[0], p1.x, bx0, ax0, kx0, &s10[0]);
-              }
-              if (sx1) {
-                t9[1] = cpml(d9[1], p0.y, bx1, ax1, kx1, &s9[1]);
-                t10[1] = cpml(d10[1], p1.y, bx1, ax1, kx1, &s10[1]);
-              }
-              const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
-              st2(psi, qxx, s9[0], s9[1], sx0, sx1);
-              st2(psi + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
-            }
-            if (sy) {
-              const float* P = reinterpret_cast<const float*>(st + Y::PY);
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float s6[2], s11[2];
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                t6[c] = cpml(d6[c], q0[c], by, ay, ky, &s6[c]);
-                t11[c] = cpml(d11[c], q1[c], by, ay, ky, &s11[c]);
-              }
-              const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
-              st2(psi, qyy, s6[0], s6[1], true, v1);
-              st2(psi + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
-            }
-            if (sz) {
-              const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-              const float bz = prof(g, 2, PR_BE, k), az = prof(g, 2, PR_AE, k), kz = prof(g, 2, PR_KE, k);
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float s7[2], s8[2];
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                t7[c] = cpml(d7[c], q0[c], bz, az, kz, &s7[c]);
-                t8[c] = cpml(d8[c], q1[c], bz, az, kz, &s8[c]);
-              }
-              const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
-              st2(psi, qz, s7[0], s7[1], true, v1);
-              st2(psi + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
-            }
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              c0[c] = t6[c] - t7[c];
-              c1[c] = t8[c] - t9[c];
-              c2[c] = t10[c] - t11[c];
-            }
-          }
-          if (a.src.kind) {
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const float w = (c == 0 || v1) ? src_wt(a.src, x + c, y, k) : 0.f;
-              if (w != 0.f) {
-                const float wj = __fmul_rn(w, a.jn);
-                if (a.src.comp == 0) c0[c] = __fsub_rn(c0[c], wj);
-                else if (a.src.comp == 1) c1[c] = __fsub_rn(c1[c], wj);
-                else c2[c] = __fsub_rn(c2[c], wj);
-              }
-            }
-          }
-          const float* Eo = reinterpret_cast<const float*>(st + Y::E);
-          const float2 cb2 = ld2(reinterpret_cast<const float*>(st + Y::CB), ob);
-          const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
-          const float cbv[2] = {cb2.x, cb2.y};
-          const float eo0[2] = {e0.x, e0.y}, eo1[2] = {e1.x, e1.y}, eo2[2] = {e2.x, e2.y};
-          float ex[2], ey[2], ez[2];
-  #pragma unroll
+  for (int p = p0_; p <= p1_; ++p) {
+    unsigned char* st = dsm + stg * Y::STAGE;
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    const float* Hb = reinterpret_cast<const float*>(st + Y::H);
+    if (v0) {
+      const float2 hx2 = ld2(Hb, lb), hy2 = ld2(Hb + B::P, lb), hz2 = ld2(Hb + 2 * B::P, lb);
+      const float hx[2] = {hx2.x, hx2.y}, hy[2] = {hy2.x, hy2.y}, hz[2] = {hz2.x, hz2.y};
+      if (p >= k0) {
+        const int k = p;
+        const float2 hzy = ld2(Hb + 2 * B::P, lb - B::W), hxy = ld2(Hb, lb - B::W);
+        const float hzx = Hb[2 * B::P + lb - 1], hyx = Hb[B::P + lb - 1];
+        const float d6[2] = {hz[0] - hzy.x, hz[1] - hzy.y};      // dHz/dy
+        const float d7[2] = {hy[0] - c_hy[0], hy[1] - c_hy[1]};  // dHy/dz
+        const float d8[2] = {hx[0] - c_hx[0], hx[1] - c_hx[1]};  // dHx/dz
+        const float d9[2] = {hz[0] - hzx, hz[1] - hz[0]};        // dHz/dx
+        const float d10[2] = {hy[0] - hyx, hy[1] - hy[0]};       // dHy/dx
+        const float d11[2] = {hx[0] - hxy.x, hx[1] - hxy.y};     // dHx/dy
+        const bool sz = in_slab(k, g.nz, g.P);
+        float c0[2], c1[2], c2[2];
+        if (!(sx0 || sx1 || sy || sz)) {
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
-            ex[c] = __fadd_rn(eo0[c], __fmul_rn(cbv[c], c0[c]));
-            ey[c] = __fadd_rn(eo1[c], __fmul_rn(cbv[c], c1[c]));
-            ez[c] = __fadd_rn(eo2[c], __fmul_rn(cbv[c], c2[c]));
+            c0[c] = d6[c] - d7[c];
+            c1[c] = d8[c] - d9[c];
+            c2[c] = d10[c] - d11[c];
           }
-          st2(Ex, q, ex[0], ex[1], true, v1);
-          st2(Ey, q, ey[0], ey[1], true, v1);
-          st2(Ez, q, ez[0], ez[1], true, v1);
-          if (a.det.kind) {
-  #pragma unroll
+        } else {
+          float t6[2], t7[2], t8[2], t9[2], t10[2], t11[2];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            t6[c] = d6[c]; t7[c] = d7[c]; t8[c] = d8[c];
+            t9[c] = d9[c]; t10[c] = d10[c]; t11[c] = d11[c];
+          }
+          if (sx0 || sx1) {
+            const float* P = reinterpret_cast<const float*>(st + Y::PX);
+            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+            float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
+            if (sx0) {
+              t9[0] = cpml(d9[0], p0.x, bx0, ax0, kx0, &s9[0]);
+              t10[0] = cpml(d10[0], p1.x, bx0, ax0, kx0, &s10[0]);
+            }
+            if (sx1) {
+              t9[1] = cpml(d9[1], p0.y, bx1, ax1, kx1, &s9[1]);
+              t10[1] = cpml(d10[1], p1.y, bx1, ax1, kx1, &s10[1]);
+            }
+            const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
+            st2(psi, qxx, s9[0], s9[1], sx0, sx1);
+            st2(psi + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
+          }
+          if (sy) {
+            const float* P = reinterpret_cast<const float*>(st + Y::PY);
+            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float s6[2], s11[2];
+#pragma unroll
             for (int c = 0; c < 2; ++c) {
-              int u, v;
-              if ((c == 0 || v1) && on_plane(a.det.axis, a.det.index, a.det.u0, a.det.u1, a.det.v0,
-                                             a.det.v1, x + c, y, k, &u, &v)) {
-                if (a.det.kind == 1) {
-                  lsum += (double)ex[c] * ex[c] + (double)ey[c] * ey[c] + (double)ez[c] * ez[c];
-                } else {
-                  const int ax_ = a.det.axis;
-                  const float Eb_ = ax_ == 0 ? ey[c] : (ax_ == 1 ? ez[c] : ex[c]);
-                  const float Ec2 = ax_ == 0 ? ez[c] : (ax_ == 1 ? ex[c] : ey[c]);
-                  const float Hb2 = ax_ == 0 ? hy[c] : (ax_ == 1 ? hz[c] : hx[c]);
-                  const float Hc2 = ax_ == 0 ? hz[c] : (ax_ == 1 ? hx[c] : hy[c]);
-                  lsum += (double)Eb_ * Hc2 - (double)Ec2 * Hb2;
-                }
+              t6[c] = cpml(d6[c], q0[c], by, ay, ky, &s6[c]);
+              t11[c] = cpml(d11[c], q1[c], by, ay, ky, &s11[c]);
+            }
+            const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
+            st2(psi, qyy, s6[0], s6[1], true, v1);
+            st2(psi + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
+          }
+          if (sz) {
+            const float* P = reinterpret_cast<const float*>(st + Y::PZ);
+            const float bz = prof(g, 2, PR_BE, k), az = prof(g, 2, PR_AE, k), kz = prof(g, 2, PR_KE, k);
+            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float s7[2], s8[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              t7[c] = cpml(d7[c], q0[c], bz, az, kz, &s7[c]);
+              t8[c] = cpml(d8[c], q1[c], bz, az, kz, &s8[c]);
+            }
+            const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
+            st2(psi, qz, s7[0], s7[1], true, v1);
+            st2(psi + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
+          }
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            c0[c] = t6[c] - t7[c];
+            c1[c] = t8[c] - t9[c];
+            c2[c] = t10[c] - t11[c];
+          }
+        }
+        if (a.src.kind) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float w = (c == 0 || v1) ? src_wt(a.src, x + c, y, k) : 0.f;
+            if (w != 0.f) {
+              const float wj = __fmul_rn(w, a.jn);
+              if (a.src.comp == 0) c0[c] = __fsub_rn(c0[c], wj);
+              else if (a.src.comp == 1) c1[c] = __fsub_rn(c1[c], wj);
+              else c2[c] = __fsub_rn(c2[c], wj);
+            }
+          }
+        }
+        const float* Eo = reinterpret_cast<const float*>(st + Y::E);
+        const float2 cb2 = ld2(reinterpret_cast<const float*>(st + Y::CB), ob);
+        const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
+        const float cbv[2] = {cb2.x, cb2.y};
+        const float eo0[2] = {e0.x, e0.y}, eo1[2] = {e1.x, e1.y}, eo2[2] = {e2.x, e2.y};
+        float ex[2], ey[2], ez[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          ex[c] = __fadd_rn(eo0[c], __fmul_rn(cbv[c], c0[c]));
+          ey[c] = __fadd_rn(eo1[c], __fmul_rn(cbv[c], c1[c]));
+          ez[c] = __fadd_rn(eo2[c], __fmul_rn(cbv[c], c2[c]));
+        }
+        st2(Ex, q, ex[0], ex[1], true, v1);
+        st2(Ey, q, ey[0], ey[1], true, v1);
+        st2(Ez, q, ez[0], ez[1], true, v1);
+        if (a.det.kind) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            int u, v;
+            if ((c == 0 || v1) && on_plane(a.det.axis, a.det.index, a.det.u0, a.det.u1, a.det.v0,
+                                           a.det.v1, x + c, y, k, &u, &v)) {
+              if (a.det.kind == 1) {
+                lsum += (double)ex[c] * ex[c] + (double)ey[c] * ey[c] + (double)ez[c] * ez[c];
+              } else {
+                const int ax_ = a.det.axis;
+                const float Eb_ = ax_ == 0 ? ey[c] : (ax_ == 1 ? ez[c] : ex[c]);
+                const float Ec2 = ax_ == 0 ? ez[c] : (ax_ == 1 ? ex[c] : ey[c]);
+                const float Hb2 = ax_ == 0 ? hy[c] : (ax_ == 1 ? hz[c] : hx[c]);
+                const float Hc2 = ax_ == 0 ? hz[c] : (ax_ == 1 ? hx[c] : hy[c]);
+                lsum += (double)Eb_ * Hc2 - (double)Ec2 * Hb2;
               }
             }
           }
-          q += g.plane;
         }
-        c_hx[0] = hx[0]; c_hx[1] = hx[1];
-        c_hy[0] = hy[0]; c_hy[1] = hy[1];
+        q += g.plane;
       }
-      __syncthreads();
-      if (tid == 0) {
-        if (p == U.p0) s_u[(ord + 1) & 1] = nxt;
-        produce(cur, s_u, NU.n, ugeo, issue, st, bars + stg);
-      }
-      if (++stg == S) { stg = 0; par ^= 1u; }
-      ++done;
+      c_hx[0] = hx[0]; c_hx[1] = hx[1];
+      c_hy[0] = hy[0]; c_hy[1] = hy[1];
     }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
+    if (++stg == S) { stg = 0; par ^= 1u; }
   }
   if (a.det.kind) {
     double v = lsum;
@@ -674,587 +521,557 @@ k_l2fwd_e(const __grid_constant__ LagMaps m,
 // ======================================== reverse E phase (+ adjoint H) ===
 template <int TY, int S, int TW>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_e(const __grid_constant__ LagMaps m,
-                                                    StepArgs a) {
+k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LRE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  __shared__ int s_u[2];
-  const Units NU = units_of<TW, TY>(a);
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(x0, min(x0 + TW, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
+  const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  // plane k0-1: Ht(k0-1) at the own pair; planes k0..k1-1: the step proper,
+  // each also finishing lam_H(p-1) with its own z-terms; plane k1 finishes
+  // lam_H(k1-1).
+  const int p0_ = k0 - 1, p1_ = k1;
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
-  auto ugeo = [&](int u) {
-    UnitGeo U = unit_geo<TW, TY>(a, NU, u);
-    // plane k0-1: Ht(k0-1) at the own pair; planes k0..k1-1: the step proper,
-    // each also finishing lam_H(p-1) with its own z-terms; plane k1 finishes
-    // lam_H(k1-1).
-    U.p0 = U.k0 - 1;
-    U.p1 = U.k1;
-    U.txs = tile_in_slab(U.x0, min(U.x0 + TW, g.nx - 1), g.nx, g.P);
-    U.tys = tile_in_slab(U.y0, min(U.y0 + TY, g.ny - 1), g.ny, g.P);
-    return U;
-  };
   // primal data only where the primal runs: interior tiles, planes P..nz-P-1
   // (and plane P-1's Ht for the z difference of plane P)
-  auto primal_of = [&](const UnitGeo& U, int p) { return U.tint && p >= g.P && p < g.nz - g.P; };
-  auto boxes = [&](const UnitGeo& U, int p, auto&& f) {
-    const bool head = p < U.k0, body = p >= U.k0 && p < U.k1, tail = p > U.k0;
+  auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
+  int qx0, qy0;
+  psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
+  auto boxes = [&](int p, auto&& f) {
+    const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (body || tail);
     const bool lam = body || tail;
-    const bool hbox = (head || body) && (primal_of(U, p) || primal_of(U, p + 1));
-    const bool ebox = body && primal_of(U, p);
-    if (hbox) f(Y::H, &m.Fw, U.x0 - 4, U.y0 - 1, p, 3, 3 * B::P * 4);
+    const bool hbox = (head || body) && (primal_plane(p) || primal_plane(p + 1));
+    const bool ebox = body && primal_plane(p);
+    if (hbox) f(Y::H, &m.Fw, x0 - 4, y0 - 1, p, 3, 3 * B::P * 4);
     if (lam) {
-      f(Y::CB, &m.cbw, U.x0, U.y0, p, 0, B::P * 4);
-      f(Y::LE, &m.Lw, U.x0, U.y0, p, 0, 3 * B::P * 4);
+      f(Y::CB, &m.cbw, x0, y0, p, 0, B::P * 4);
+      f(Y::LE, &m.Lw, x0, y0, p, 0, 3 * B::P * 4);
     }
-    if (ebox) f(Y::E, &m.Fo, U.x0, U.y0, p, 0, 3 * B::OP * 4);
-    if (body) f(Y::LH, &m.Lo, U.x0, U.y0, p, 3, 3 * B::OP * 4);
-    if (body && U.txs) f(Y::PX, &m.Qxw, U.qx0, U.y0, p, 2, 2 * B::XP * 4);
-    if (body && U.tys) f(Y::PY, &m.Qyw, U.x0, U.qy0, p, 2, 2 * B::YP * 4);
-    if (zs) f(Y::PZ, &m.Qzo, U.x0, U.y0, psi_map(a.pl.ax[2], p), 2, 2 * B::OP * 4);
+    if (ebox) f(Y::E, &m.Fo, x0, y0, p, 0, 3 * B::OP * 4);
+    if (body) f(Y::LH, &m.Lo, x0, y0, p, 3, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Qxw, qx0, y0, p, 2, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.Qyw, x0, qy0, p, 2, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.Qzo, x0, y0, psi_map(a.pl.ax[2], p), 2, 2 * B::OP * 4);
   };
-  auto issue = [&](const UnitGeo& U, int p, unsigned char* st, uint64_t* bar) {
-    stage_plane([&](int pp, auto&& f) { boxes(U, pp, f); }, p, st, bar,
-                a.prefetch && p + 1 <= U.p1 && p + 1 >= 0 && p + 1 < g.nz);
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
   };
   pdl_sync();
-  Cursor cur;
-  ring_start<S>(a, NU, s_u, cur, ugeo, issue, dsm, Y::STAGE, bars);
-  int stg = 0, done = 0, ord = 0;
+  if (tid == 0)
+    for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
+  // x profiles at x, x+1 (cell 1, also cell 0's +x neighbour) and x+2
+  const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
+  const bool sx2 = v1 && x + 2 < g.nx && in_slab(x + 2, g.nx, g.P);
+  const bool sy = v0 && in_slab(y, g.ny, g.P), sy1 = v0 && y + 1 < g.ny && in_slab(y + 1, g.ny, g.P);
+  float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f, bx2 = 0.f, ax2 = 0.f, kx2 = 1.f;
+  float by = 0.f, ay = 0.f, ky = 1.f, by1 = 0.f, ay1 = 0.f, ky1 = 1.f;
+  if (sx0) { bx0 = prof(g, 0, PR_BE, x); ax0 = prof(g, 0, PR_AE, x); kx0 = prof(g, 0, PR_KE, x); }
+  if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
+  if (sx2) { bx2 = prof(g, 0, PR_BE, x + 2); ax2 = prof(g, 0, PR_AE, x + 2); kx2 = prof(g, 0, PR_KE, x + 2); }
+  if (sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
+  if (sy1) { by1 = prof(g, 1, PR_BE, y + 1); ay1 = prof(g, 1, PR_AE, y + 1); ky1 = prof(g, 1, PR_KE, y + 1); }
+  const bool yin = y >= g.P && y < g.ny - g.P;
+  const bool xyin0 = v0 && yin && x >= g.P && x < g.nx - g.P;
+  const bool xyin1 = v1 && yin && x + 1 >= g.P && x + 1 < g.nx - g.P;
+  const bool dy_ = y >= a.dlo[1] && y < a.dhi[1];
+  const int dX = a.dhi[0] - a.dlo[0], dY = a.dhi[1] - a.dlo[1];
+  const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
+  const int hb = ty * B::W + 2 * tx;             // own pair in a hi box
+  const int ob = ty * TW + 2 * tx;
+  const long long nc = g.nc;
+  float* const Ex = a.F;
+  float* const LHx = a.L + 3 * nc;
+  float* const LHy = LHx + nc;
+  float* const LHz = LHy + nc;
+  float* const lpB = a.psiB;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};   // Ht(p-1) own
+  // partial lam_H(p-1): own value, the -z terms and the completed x / y parts
+  float c_lhx[2] = {0.f, 0.f}, c_lhy[2] = {0.f, 0.f}, c_o8[2] = {0.f, 0.f}, c_o7[2] = {0.f, 0.f};
+  float c_bx[2] = {0.f, 0.f}, c_by[2] = {0.f, 0.f};
+  int stg = 0;
   uint32_t par = 0;
   bool ok = true;
-  for (int u = s_u[0]; u < NU.n; u = s_u[++ord & 1]) {
-    const int nxt = tid == 0 ? next_unit(a, NU) : 0;   // the CTA's next unit
-    const UnitGeo U = ugeo(u);
-    const int x0 = U.x0, y0 = U.y0, k0 = U.k0, k1 = U.k1;
-    const int p0_ = U.p0, p1_ = U.p1;
-    auto primal_plane = [&](int p) { return primal_of(U, p); };
-    const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-    // x profiles at x, x+1 (cell 1, also cell 0's +x neighbour) and x+2
-    const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
-    const bool sx2 = v1 && x + 2 < g.nx && in_slab(x + 2, g.nx, g.P);
-    const bool sy = v0 && in_slab(y, g.ny, g.P), sy1 = v0 && y + 1 < g.ny && in_slab(y + 1, g.ny, g.P);
-    float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f, bx2 = 0.f, ax2 = 0.f, kx2 = 1.f;
-    float by = 0.f, ay = 0.f, ky = 1.f, by1 = 0.f, ay1 = 0.f, ky1 = 1.f;
-    if (sx0) { bx0 = prof(g, 0, PR_BE, x); ax0 = prof(g, 0, PR_AE, x); kx0 = prof(g, 0, PR_KE, x); }
-    if (sx1) { bx1 = prof(g, 0, PR_BE, x + 1); ax1 = prof(g, 0, PR_AE, x + 1); kx1 = prof(g, 0, PR_KE, x + 1); }
-    if (sx2) { bx2 = prof(g, 0, PR_BE, x + 2); ax2 = prof(g, 0, PR_AE, x + 2); kx2 = prof(g, 0, PR_KE, x + 2); }
-    if (sy) { by = prof(g, 1, PR_BE, y); ay = prof(g, 1, PR_AE, y); ky = prof(g, 1, PR_KE, y); }
-    if (sy1) { by1 = prof(g, 1, PR_BE, y + 1); ay1 = prof(g, 1, PR_AE, y + 1); ky1 = prof(g, 1, PR_KE, y + 1); }
-    const bool yin = y >= g.P && y < g.ny - g.P;
-    const bool xyin0 = v0 && yin && x >= g.P && x < g.nx - g.P;
-    const bool xyin1 = v1 && yin && x + 1 >= g.P && x + 1 < g.nx - g.P;
-    const bool dy_ = y >= a.dlo[1] && y < a.dhi[1];
-    const int dX = a.dhi[0] - a.dlo[0], dY = a.dhi[1] - a.dlo[1];
-    const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
-    const int hb = ty * B::W + 2 * tx;             // own pair in a hi box
-    const int ob = ty * TW + 2 * tx;
-    const long long nc = g.nc;
-    float* const Ex = a.F;
-    float* const LHx = a.L + 3 * nc;
-    float* const LHy = LHx + nc;
-    float* const LHz = LHy + nc;
-    float* const lpB = a.psiB;
-    long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
-    float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f};   // Ht(p-1) own
-    // partial lam_H(p-1): own value, the -z terms and the completed x / y parts
-    float c_lhx[2] = {0.f, 0.f}, c_lhy[2] = {0.f, 0.f}, c_o8[2] = {0.f, 0.f}, c_o7[2] = {0.f, 0.f};
-    float c_bx[2] = {0.f, 0.f}, c_by[2] = {0.f, 0.f};
-    for (int p = p0_; p <= p1_; ++p) {
-      unsigned char* st = dsm + stg * Y::STAGE;
-      if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
-      if (!__syncthreads_and(ok)) { ring_abort_n<S>(bars, stg, par, cur.issued - done, a.err); return; }
-      if (v0) {
-        const float* CBb = reinterpret_cast<const float*>(st + Y::CB);
-        const float* LEb = reinterpret_cast<const float*>(st + Y::LE);
-        const float* Hb = reinterpret_cast<const float*>(st + Y::H);
-        if (p >= k0 && p < k1) {
-          const int k = p;
-          const float2 cb2 = ld2(CBb, hb);
-          const float2 lx2 = ld2(LEb, hb), ly2 = ld2(LEb + B::P, hb), lz2 = ld2(LEb + 2 * B::P, hb);
-          const float cbv[2] = {cb2.x, cb2.y};
-          const float lex[2] = {lx2.x, lx2.y}, ley[2] = {ly2.x, ly2.y}, lez[2] = {lz2.x, lz2.y};
-          const bool hv = primal_plane(k) || primal_plane(k + 1);   // H box staged
-          float hx[2] = {0.f, 0.f}, hy[2] = {0.f, 0.f}, hz[2] = {0.f, 0.f};
-          if (hv) {
-            const float2 h0 = ld2(Hb, lb), h1 = ld2(Hb + B::P, lb), h2 = ld2(Hb + 2 * B::P, lb);
-            hx[0] = h0.x; hx[1] = h0.y;
-            hy[0] = h1.x; hy[1] = h1.y;
-            hz[0] = h2.x; hz[1] = h2.y;
-          }
-          // primal inverse E update on the interior, dL/dcb on the design box
-          if (primal_plane(k) && (xyin0 || xyin1)) {
-            const float2 hzy = ld2(Hb + 2 * B::P, lb - B::W), hxy = ld2(Hb, lb - B::W);
-            const float hzx = Hb[2 * B::P + lb - 1], hyx = Hb[B::P + lb - 1];
-            const float d6[2] = {hz[0] - hzy.x, hz[1] - hzy.y}, d7[2] = {hy[0] - c_hy[0], hy[1] - c_hy[1]};
-            const float d8[2] = {hx[0] - c_hx[0], hx[1] - c_hx[1]}, d9[2] = {hz[0] - hzx, hz[1] - hz[0]};
-            const float d10[2] = {hy[0] - hyx, hy[1] - hy[0]}, d11[2] = {hx[0] - hxy.x, hx[1] - hxy.y};
-            float c0[2], c1[2], c2[2];
-  #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              c0[c] = d6[c] - d7[c];
-              c1[c] = d8[c] - d9[c];
-              c2[c] = d10[c] - d11[c];
-            }
-            if (a.src.kind) {
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                const float w = (c == 0 || v1) ? src_wt(a.src, x + c, y, k) : 0.f;
-                if (w != 0.f) {
-                  const float wj = __fmul_rn(w, a.jn);
-                  if (a.src.comp == 0) c0[c] = __fsub_rn(c0[c], wj);
-                  else if (a.src.comp == 1) c1[c] = __fsub_rn(c1[c], wj);
-                  else c2[c] = __fsub_rn(c2[c], wj);
-                }
-              }
-            }
-            const float* Eo = reinterpret_cast<const float*>(st + Y::E);
-            const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
-            st2(Ex, q, __fsub_rn(e0.x, __fmul_rn(cbv[0], c0[0])), __fsub_rn(e0.y, __fmul_rn(cbv[1], c0[1])),
-                xyin0, xyin1);
-            st2(Ex + nc, q, __fsub_rn(e1.x, __fmul_rn(cbv[0], c1[0])),
-                __fsub_rn(e1.y, __fmul_rn(cbv[1], c1[1])), xyin0, xyin1);
-            st2(Ex + 2 * nc, q, __fsub_rn(e2.x, __fmul_rn(cbv[0], c2[0])),
-                __fsub_rn(e2.y, __fmul_rn(cbv[1], c2[1])), xyin0, xyin1);
-            if (dy_ && k >= a.dlo[2] && k < a.dhi[2]) {
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                const int xc = x + c;
-                if ((c == 0 ? xyin0 : xyin1) && xc >= a.dlo[0] && xc < a.dhi[0]) {
-                  const float s = lex[c] * c0[c] + ley[c] * c1[c] + lez[c] * c2[c];
-                  const long long qd =
-                      ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (xc - a.dlo[0]);
-                  // one owner per cell: a fire-and-forget reduction in L2 adds
-                  // exactly what a load-add-store would, without the load latency
-                  atomicAdd(a.gacc + qd, (double)s);
-                }
-              }
-            }
-          }
-          // adjoint of the E half-step, own and +x / +y terms
-          float o6[2], o11[2], o7[2], o8[2], o9[2], o10[2];
-  #pragma unroll
+  for (int p = p0_; p <= p1_; ++p) {
+    unsigned char* st = dsm + stg * Y::STAGE;
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    if (v0) {
+      const float* CBb = reinterpret_cast<const float*>(st + Y::CB);
+      const float* LEb = reinterpret_cast<const float*>(st + Y::LE);
+      const float* Hb = reinterpret_cast<const float*>(st + Y::H);
+      if (p >= k0 && p < k1) {
+        const int k = p;
+        const float2 cb2 = ld2(CBb, hb);
+        const float2 lx2 = ld2(LEb, hb), ly2 = ld2(LEb + B::P, hb), lz2 = ld2(LEb + 2 * B::P, hb);
+        const float cbv[2] = {cb2.x, cb2.y};
+        const float lex[2] = {lx2.x, lx2.y}, ley[2] = {ly2.x, ly2.y}, lez[2] = {lz2.x, lz2.y};
+        const bool hv = primal_plane(k) || primal_plane(k + 1);   // H box staged
+        float hx[2] = {0.f, 0.f}, hy[2] = {0.f, 0.f}, hz[2] = {0.f, 0.f};
+        if (hv) {
+          const float2 h0 = ld2(Hb, lb), h1 = ld2(Hb + B::P, lb), h2 = ld2(Hb + 2 * B::P, lb);
+          hx[0] = h0.x; hx[1] = h0.y;
+          hy[0] = h1.x; hy[1] = h1.y;
+          hz[0] = h2.x; hz[1] = h2.y;
+        }
+        // primal inverse E update on the interior, dL/dcb on the design box
+        if (primal_plane(k) && (xyin0 || xyin1)) {
+          const float2 hzy = ld2(Hb + 2 * B::P, lb - B::W), hxy = ld2(Hb, lb - B::W);
+          const float hzx = Hb[2 * B::P + lb - 1], hyx = Hb[B::P + lb - 1];
+          const float d6[2] = {hz[0] - hzy.x, hz[1] - hzy.y}, d7[2] = {hy[0] - c_hy[0], hy[1] - c_hy[1]};
+          const float d8[2] = {hx[0] - c_hx[0], hx[1] - c_hx[1]}, d9[2] = {hz[0] - hzx, hz[1] - hz[0]};
+          const float d10[2] = {hy[0] - hyx, hy[1] - hy[0]}, d11[2] = {hx[0] - hxy.x, hx[1] - hxy.y};
+          float c0[2], c1[2], c2[2];
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
-            const float wx = cbv[c] * lex[c], wy = cbv[c] * ley[c], wz = cbv[c] * lez[c];
-            o6[c] = wx; o11[c] = -wz; o7[c] = -wx; o8[c] = wy; o9[c] = -wy; o10[c] = wz;
+            c0[c] = d6[c] - d7[c];
+            c1[c] = d8[c] - d9[c];
+            c2[c] = d10[c] - d11[c];
           }
-          float n6[2], n11[2];
-          {
-            const float2 cy2 = ld2(CBb, hb + B::W);
-            const float2 ly = ld2(LEb, hb + B::W), lz = ld2(LEb + 2 * B::P, hb + B::W);
-            n6[0] = cy2.x * ly.x;
-            n6[1] = cy2.y * ly.y;
-            n11[0] = -cy2.x * lz.x;
-            n11[1] = -cy2.y * lz.y;
-          }
-          float n9x, n10x;   // +x terms of cell 1 (from x + 2)
-          {
-            const float c2 = CBb[hb + 2];
-            n9x = -c2 * LEb[B::P + hb + 2];
-            n10x = c2 * LEb[2 * B::P + hb + 2];
-          }
-          if (y + 1 >= g.ny) {
-            n6[0] = 0.f; n6[1] = 0.f; n11[0] = 0.f; n11[1] = 0.f;
-          }
-          if (x + 2 >= g.nx) { n9x = 0.f; n10x = 0.f; }
-          if (sy || sy1) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0)
-            if (sy) {
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::YP, ob);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float s6[2], s11[2];
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                o6[c] = adj(o6[c], q0[c], by, ay, ky, &s6[c]);
-                o11[c] = adj(o11[c], q1[c], by, ay, ky, &s11[c]);
-              }
-              const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
-              st2(lpB, qyy, s6[0], s6[1], true, v1);
-              st2(lpB + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
-            }
-            if (sy1) {
-              const float2 p0 = ld2(P, ob + TW), p1 = ld2(P + B::YP, ob + TW);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float dummy;
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                n6[c] = adj(n6[c], q0[c], by1, ay1, ky1, &dummy);
-                n11[c] = adj(n11[c], q1[c], by1, ay1, ky1, &dummy);
+          if (a.src.kind) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const float w = (c == 0 || v1) ? src_wt(a.src, x + c, y, k) : 0.f;
+              if (w != 0.f) {
+                const float wj = __fmul_rn(w, a.jn);
+                if (a.src.comp == 0) c0[c] = __fsub_rn(c0[c], wj);
+                else if (a.src.comp == 1) c1[c] = __fsub_rn(c1[c], wj);
+                else c2[c] = __fsub_rn(c2[c], wj);
               }
             }
           }
-          if (sx0 || sx1 || sx2) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0, y0)
-            const int xb = ty * B::W + 2 * tx;
-            const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
-            float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
-            if (sx0) {
-              o9[0] = adj(o9[0], p0.x, bx0, ax0, kx0, &s9[0]);
-              o10[0] = adj(o10[0], p1.x, bx0, ax0, kx0, &s10[0]);
-            }
-            if (sx1) {
-              o9[1] = adj(o9[1], p0.y, bx1, ax1, kx1, &s9[1]);
-              o10[1] = adj(o10[1], p1.y, bx1, ax1, kx1, &s10[1]);
-            }
-            const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
-            st2(lpB, qxx, s9[0], s9[1], sx0, sx1);
-            st2(lpB + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
-            if (sx2) {
-              float dummy;
-              n9x = adj(n9x, P[xb + 2], bx2, ax2, kx2, &dummy);
-              n10x = adj(n10x, P[B::XP + xb + 2], bx2, ax2, kx2, &dummy);
+          const float* Eo = reinterpret_cast<const float*>(st + Y::E);
+          const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
+          st2(Ex, q, __fsub_rn(e0.x, __fmul_rn(cbv[0], c0[0])), __fsub_rn(e0.y, __fmul_rn(cbv[1], c0[1])),
+              xyin0, xyin1);
+          st2(Ex + nc, q, __fsub_rn(e1.x, __fmul_rn(cbv[0], c1[0])),
+              __fsub_rn(e1.y, __fmul_rn(cbv[1], c1[1])), xyin0, xyin1);
+          st2(Ex + 2 * nc, q, __fsub_rn(e2.x, __fmul_rn(cbv[0], c2[0])),
+              __fsub_rn(e2.y, __fmul_rn(cbv[1], c2[1])), xyin0, xyin1);
+          if (dy_ && k >= a.dlo[2] && k < a.dhi[2]) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int xc = x + c;
+              if ((c == 0 ? xyin0 : xyin1) && xc >= a.dlo[0] && xc < a.dhi[0]) {
+                const float s = lex[c] * c0[c] + ley[c] * c1[c] + lez[c] * c2[c];
+                const long long qd =
+                    ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (xc - a.dlo[0]);
+                // one owner per cell: a fire-and-forget reduction in L2 adds
+                // exactly what a load-add-store would, without the load latency
+                atomicAdd(a.gacc + qd, (double)s);
+              }
             }
           }
-          // cell 0's +x terms are cell 1's own terms
-          const float n9[2] = {v1 ? o9[1] : 0.f, n9x}, n10[2] = {v1 ? o10[1] : 0.f, n10x};
-          if (in_slab(k, g.nz, g.P)) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-            const float b = prof(g, 2, PR_BE, k), aa = prof(g, 2, PR_AE, k), kv = prof(g, 2, PR_KE, k);
-            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+        }
+        // adjoint of the E half-step, own and +x / +y terms
+        float o6[2], o11[2], o7[2], o8[2], o9[2], o10[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float wx = cbv[c] * lex[c], wy = cbv[c] * ley[c], wz = cbv[c] * lez[c];
+          o6[c] = wx; o11[c] = -wz; o7[c] = -wx; o8[c] = wy; o9[c] = -wy; o10[c] = wz;
+        }
+        float n6[2], n11[2];
+        {
+          const float2 cy2 = ld2(CBb, hb + B::W);
+          const float2 ly = ld2(LEb, hb + B::W), lz = ld2(LEb + 2 * B::P, hb + B::W);
+          n6[0] = cy2.x * ly.x;
+          n6[1] = cy2.y * ly.y;
+          n11[0] = -cy2.x * lz.x;
+          n11[1] = -cy2.y * lz.y;
+        }
+        float n9x, n10x;   // +x terms of cell 1 (from x + 2)
+        {
+          const float c2 = CBb[hb + 2];
+          n9x = -c2 * LEb[B::P + hb + 2];
+          n10x = c2 * LEb[2 * B::P + hb + 2];
+        }
+        if (y + 1 >= g.ny) {
+          n6[0] = 0.f; n6[1] = 0.f; n11[0] = 0.f; n11[1] = 0.f;
+        }
+        if (x + 2 >= g.nx) { n9x = 0.f; n10x = 0.f; }
+        if (sy || sy1) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0)
+          if (sy) {
+            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::YP, ob);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-            float s7[2], s8[2];
-  #pragma unroll
+            float s6[2], s11[2];
+#pragma unroll
             for (int c = 0; c < 2; ++c) {
-              o7[c] = adj(o7[c], q0[c], b, aa, kv, &s7[c]);
-              o8[c] = adj(o8[c], q1[c], b, aa, kv, &s8[c]);
+              o6[c] = adj(o6[c], q0[c], by, ay, ky, &s6[c]);
+              o11[c] = adj(o11[c], q1[c], by, ay, ky, &s11[c]);
             }
-            const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
-            st2(lpB, qz, s7[0], s7[1], true, v1);
-            st2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
+            const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
+            st2(lpB, qyy, s6[0], s6[1], true, v1);
+            st2(lpB + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
           }
-          const float* LHo = reinterpret_cast<const float*>(st + Y::LH);
-          const float2 lh0 = ld2(LHo, ob), lh1 = ld2(LHo + B::OP, ob), lh2 = ld2(LHo + 2 * B::OP, ob);
-          st2(LHz, q, lh2.x + ((o6[0] - n6[0]) + (o9[0] - n9[0])),
-              lh2.y + ((o6[1] - n6[1]) + (o9[1] - n9[1])), true, v1);
-          if (p > k0) {  // finish lam_H(p-1): its +z terms are this plane's o7, o8
-            const long long qm = q - g.plane;
-            st2(LHx, qm, c_lhx[0] + ((c_o8[0] - o8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - o8[1]) + c_bx[1]),
-                true, v1);
-            st2(LHy, qm, c_lhy[0] + ((c_o7[0] - o7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - o7[1]) + c_by[1]),
-                true, v1);
+          if (sy1) {
+            const float2 p0 = ld2(P, ob + TW), p1 = ld2(P + B::YP, ob + TW);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float dummy;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              n6[c] = adj(n6[c], q0[c], by1, ay1, ky1, &dummy);
+              n11[c] = adj(n11[c], q1[c], by1, ay1, ky1, &dummy);
+            }
           }
-          c_lhx[0] = lh0.x; c_lhx[1] = lh0.y;
-          c_lhy[0] = lh1.x; c_lhy[1] = lh1.y;
-  #pragma unroll
+        }
+        if (sx0 || sx1 || sx2) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0, y0)
+          const int xb = ty * B::W + 2 * tx;
+          const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
+          float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
+          if (sx0) {
+            o9[0] = adj(o9[0], p0.x, bx0, ax0, kx0, &s9[0]);
+            o10[0] = adj(o10[0], p1.x, bx0, ax0, kx0, &s10[0]);
+          }
+          if (sx1) {
+            o9[1] = adj(o9[1], p0.y, bx1, ax1, kx1, &s9[1]);
+            o10[1] = adj(o10[1], p1.y, bx1, ax1, kx1, &s10[1]);
+          }
+          const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
+          st2(lpB, qxx, s9[0], s9[1], sx0, sx1);
+          st2(lpB + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
+          if (sx2) {
+            float dummy;
+            n9x = adj(n9x, P[xb + 2], bx2, ax2, kx2, &dummy);
+            n10x = adj(n10x, P[B::XP + xb + 2], bx2, ax2, kx2, &dummy);
+          }
+        }
+        // cell 0's +x terms are cell 1's own terms
+        const float n9[2] = {v1 ? o9[1] : 0.f, n9x}, n10[2] = {v1 ? o10[1] : 0.f, n10x};
+        if (in_slab(k, g.nz, g.P)) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PZ);
+          const float b = prof(g, 2, PR_BE, k), aa = prof(g, 2, PR_AE, k), kv = prof(g, 2, PR_KE, k);
+          const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+          const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+          float s7[2], s8[2];
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
-            c_o8[c] = o8[c];
-            c_o7[c] = o7[c];
-            c_bx[c] = o11[c] - n11[c];
-            c_by[c] = o10[c] - n10[c];
-            c_hx[c] = hx[c];
-            c_hy[c] = hy[c];
+            o7[c] = adj(o7[c], q0[c], b, aa, kv, &s7[c]);
+            o8[c] = adj(o8[c], q1[c], b, aa, kv, &s8[c]);
           }
-          q += g.plane;
-        } else if (p < k0) {
-          if (primal_plane(p) || primal_plane(p + 1)) {
-            const float2 h0 = ld2(Hb, lb), h1 = ld2(Hb + B::P, lb);
-            c_hx[0] = h0.x; c_hx[1] = h0.y;
-            c_hy[0] = h1.x; c_hy[1] = h1.y;
-          }
-        } else {  // p == k1 > k0: finish lam_H(k1-1) with the +z terms of plane k1
-          float n7[2] = {0.f, 0.f}, n8[2] = {0.f, 0.f};
-          if (p < g.nz) {
-            const float2 c2 = ld2(CBb, hb), lx = ld2(LEb, hb), ly = ld2(LEb + B::P, hb);
-            n7[0] = -c2.x * lx.x;
-            n7[1] = -c2.y * lx.y;
-            n8[0] = c2.x * ly.x;
-            n8[1] = c2.y * ly.y;
-            if (in_slab(p, g.nz, g.P)) {
-              const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-              const float b1 = prof(g, 2, PR_BE, p), a1 = prof(g, 2, PR_AE, p), k1v = prof(g, 2, PR_KE, p);
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float dummy;
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                n7[c] = adj(n7[c], q0[c], b1, a1, k1v, &dummy);
-                n8[c] = adj(n8[c], q1[c], b1, a1, k1v, &dummy);
-              }
-            }
-          }
+          const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
+          st2(lpB, qz, s7[0], s7[1], true, v1);
+          st2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
+        }
+        const float* LHo = reinterpret_cast<const float*>(st + Y::LH);
+        const float2 lh0 = ld2(LHo, ob), lh1 = ld2(LHo + B::OP, ob), lh2 = ld2(LHo + 2 * B::OP, ob);
+        st2(LHz, q, lh2.x + ((o6[0] - n6[0]) + (o9[0] - n9[0])),
+            lh2.y + ((o6[1] - n6[1]) + (o9[1] - n9[1])), true, v1);
+        if (p > k0) {  // finish lam_H(p-1): its +z terms are this plane's o7, o8
           const long long qm = q - g.plane;
-          st2(LHx, qm, c_lhx[0] + ((c_o8[0] - n8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - n8[1]) + c_bx[1]),
+          st2(LHx, qm, c_lhx[0] + ((c_o8[0] - o8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - o8[1]) + c_bx[1]),
               true, v1);
-          st2(LHy, qm, c_lhy[0] + ((c_o7[0] - n7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - n7[1]) + c_by[1]),
+          st2(LHy, qm, c_lhy[0] + ((c_o7[0] - o7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - o7[1]) + c_by[1]),
               true, v1);
         }
+        c_lhx[0] = lh0.x; c_lhx[1] = lh0.y;
+        c_lhy[0] = lh1.x; c_lhy[1] = lh1.y;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          c_o8[c] = o8[c];
+          c_o7[c] = o7[c];
+          c_bx[c] = o11[c] - n11[c];
+          c_by[c] = o10[c] - n10[c];
+          c_hx[c] = hx[c];
+          c_hy[c] = hy[c];
+        }
+        q += g.plane;
+      } else if (p < k0) {
+        if (primal_plane(p) || primal_plane(p + 1)) {
+          const float2 h0 = ld2(Hb, lb), h1 = ld2(Hb + B::P, lb);
+          c_hx[0] = h0.x; c_hx[1] = h0.y;
+          c_hy[0] = h1.x; c_hy[1] = h1.y;
+        }
+      } else {  // p == k1 > k0: finish lam_H(k1-1) with the +z terms of plane k1
+        float n7[2] = {0.f, 0.f}, n8[2] = {0.f, 0.f};
+        if (p < g.nz) {
+          const float2 c2 = ld2(CBb, hb), lx = ld2(LEb, hb), ly = ld2(LEb + B::P, hb);
+          n7[0] = -c2.x * lx.x;
+          n7[1] = -c2.y * lx.y;
+          n8[0] = c2.x * ly.x;
+          n8[1] = c2.y * ly.y;
+          if (in_slab(p, g.nz, g.P)) {
+            const float* P = reinterpret_cast<const float*>(st + Y::PZ);
+            const float b1 = prof(g, 2, PR_BE, p), a1 = prof(g, 2, PR_AE, p), k1v = prof(g, 2, PR_KE, p);
+            const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float dummy;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              n7[c] = adj(n7[c], q0[c], b1, a1, k1v, &dummy);
+              n8[c] = adj(n8[c], q1[c], b1, a1, k1v, &dummy);
+            }
+          }
+        }
+        const long long qm = q - g.plane;
+        st2(LHx, qm, c_lhx[0] + ((c_o8[0] - n8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - n8[1]) + c_bx[1]),
+            true, v1);
+        st2(LHy, qm, c_lhy[0] + ((c_o7[0] - n7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - n7[1]) + c_by[1]),
+            true, v1);
       }
-      __syncthreads();
-      if (tid == 0) {
-        if (p == U.p0) s_u[(ord + 1) & 1] = nxt;
-        produce(cur, s_u, NU.n, ugeo, issue, st, bars + stg);
-      }
-      if (++stg == S) { stg = 0; par ^= 1u; }
-      ++done;
     }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
+    if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }
 
 // ======================================== reverse H phase (+ adjoint E) ===
 template <int TY, int S, int TW>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_h(const __grid_constant__ LagMaps m,
-                                                    StepArgs a) {
+k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LRH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  __shared__ int s_u[2];
-  const Units NU = units_of<TW, TY>(a);
+  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
+  const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
+  const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
+  // plane k0-1: lam_H(k0-1) terms for the -z neighbour; planes k0..k1-1: the
+  // step proper; plane p > k0 also finishes the primal Ht(p-1) with E(p).
+  const int p0_ = k0 - 1, p1_ = k1;
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
-  auto ugeo = [&](int u) {
-    UnitGeo U = unit_geo<TW, TY>(a, NU, u);
-    // plane k0-1: lam_H(k0-1) terms for the -z neighbour; planes k0..k1-1: the
-    // step proper; plane p > k0 also finishes the primal Ht(p-1) with E(p).
-    U.p0 = U.k0 - 1;
-    U.p1 = U.k1;
-    U.txs = tile_in_slab(max(U.x0 - 1, 0), min(U.x0 + TW - 1, g.nx - 1), g.nx, g.P);
-    U.tys = tile_in_slab(max(U.y0 - 1, 0), min(U.y0 + TY - 1, g.ny - 1), g.ny, g.P);
-    return U;
-  };
   // primal data only where the primal runs: interior tiles, planes P..nz-P-1
   // (and plane nz-P's E for the z difference of plane nz-P-1)
-  auto primal_of = [&](const UnitGeo& U, int p) { return U.tint && p >= g.P && p < g.nz - g.P; };
-  auto boxes = [&](const UnitGeo& U, int p, auto&& f) {
-    const bool head = p < U.k0, body = p >= U.k0 && p < U.k1, tail = p > U.k0;
+  auto primal_plane = [&](int p) { return tint && p >= g.P && p < g.nz - g.P; };
+  int qx0, qy0;
+  psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
+  auto boxes = [&](int p, auto&& f) {
+    const bool head = p < k0, body = p >= k0 && p < k1, tail = p > k0;
     const bool zs = p >= 0 && p < g.nz && in_slab(p, g.nz, g.P) && (head || body);
-    const bool ebox = (body && primal_of(U, p)) || (tail && primal_of(U, p - 1));
-    const bool hown = body && primal_of(U, p);
-    if (ebox) f(Y::E, &m.Fw, U.x0, U.y0, p, 0, 3 * B::P * 4);
-    if (head || body) f(Y::LH, &m.Lw, U.x0 - 4, U.y0 - 1, p, 3, 3 * B::P * 4);
-    if (hown) f(Y::H, &m.Fo, U.x0, U.y0, p, 3, 3 * B::OP * 4);
-    if (body) f(Y::LE, &m.Lo, U.x0, U.y0, p, 0, 3 * B::OP * 4);
-    if (body && U.txs) f(Y::PX, &m.Qxw, U.qx0 - 4, U.y0, p, 0, 2 * B::XP * 4);
-    if (body && U.tys) f(Y::PY, &m.Qyw, U.x0, U.qy0 - 1, p, 0, 2 * B::YP * 4);
-    if (zs) f(Y::PZ, &m.Qzo, U.x0, U.y0, psi_map(a.pl.ax[2], p), 0, 2 * B::OP * 4);
+    const bool ebox = (body && primal_plane(p)) || (tail && primal_plane(p - 1));
+    const bool hown = body && primal_plane(p);
+    if (ebox) f(Y::E, &m.Fw, x0, y0, p, 0, 3 * B::P * 4);
+    if (head || body) f(Y::LH, &m.Lw, x0 - 4, y0 - 1, p, 3, 3 * B::P * 4);
+    if (hown) f(Y::H, &m.Fo, x0, y0, p, 3, 3 * B::OP * 4);
+    if (body) f(Y::LE, &m.Lo, x0, y0, p, 0, 3 * B::OP * 4);
+    if (body && txs) f(Y::PX, &m.Qxw, qx0 - 4, y0, p, 0, 2 * B::XP * 4);
+    if (body && tys) f(Y::PY, &m.Qyw, x0, qy0 - 1, p, 0, 2 * B::YP * 4);
+    if (zs) f(Y::PZ, &m.Qzo, x0, y0, psi_map(a.pl.ax[2], p), 0, 2 * B::OP * 4);
   };
-  auto issue = [&](const UnitGeo& U, int p, unsigned char* st, uint64_t* bar) {
-    stage_plane([&](int pp, auto&& f) { boxes(U, pp, f); }, p, st, bar,
-                a.prefetch && p + 1 <= U.p1 && p + 1 >= 0 && p + 1 < g.nz);
+  auto issue = [&](int p, unsigned char* st, uint64_t* bar) {
+    stage_plane(boxes, p, st, bar, a.prefetch && p + 1 <= p1_ && p + 1 >= 0 && p + 1 < g.nz);
   };
   pdl_sync();
-  Cursor cur;
-  ring_start<S>(a, NU, s_u, cur, ugeo, issue, dsm, Y::STAGE, bars);
-  int stg = 0, done = 0, ord = 0;
+  if (tid == 0)
+    for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
+  // x profiles at x-1 (cell 0's -x neighbour), x and x+1
+  const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
+  const bool sxm = v0 && x > 0 && in_slab(x - 1, g.nx, g.P);
+  const bool sy = v0 && in_slab(y, g.ny, g.P), sym = v0 && y > 0 && in_slab(y - 1, g.ny, g.P);
+  float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f, bxm = 0.f, axm = 0.f, kxm = 1.f;
+  float by = 0.f, ay = 0.f, ky = 1.f, bym = 0.f, aym = 0.f, kym = 1.f;
+  if (sx0) { bx0 = prof(g, 0, PR_BH, x); ax0 = prof(g, 0, PR_AH, x); kx0 = prof(g, 0, PR_KH, x); }
+  if (sx1) { bx1 = prof(g, 0, PR_BH, x + 1); ax1 = prof(g, 0, PR_AH, x + 1); kx1 = prof(g, 0, PR_KH, x + 1); }
+  if (sxm) { bxm = prof(g, 0, PR_BH, x - 1); axm = prof(g, 0, PR_AH, x - 1); kxm = prof(g, 0, PR_KH, x - 1); }
+  if (sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
+  if (sym) { bym = prof(g, 1, PR_BH, y - 1); aym = prof(g, 1, PR_AH, y - 1); kym = prof(g, 1, PR_KH, y - 1); }
+  const bool yin = y >= g.P && y < g.ny - g.P;
+  const bool xyin0 = v0 && yin && x >= g.P && x < g.nx - g.P;
+  const bool xyin1 = v1 && yin && x + 1 >= g.P && x + 1 < g.nx - g.P;
+  const int lb = (ty + 1) * B::W + 2 * tx + 4;
+  const int hb = ty * B::W + 2 * tx;
+  const int ob = ty * TW + 2 * tx;
+  const float S_ = g.S;
+  const long long nc = g.nc;
+  float* const Hx = a.F + 3 * nc;
+  float* const LEx = a.L;
+  float* const lpB = a.psiB;
+  long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
+  float c_m1[2] = {0.f, 0.f}, c_m2[2] = {0.f, 0.f};   // -z neighbour terms from plane p-1
+  float c_d0[2] = {0.f, 0.f}, c_d3[2] = {0.f, 0.f}, c_d4[2] = {0.f, 0.f}, c_d5[2] = {0.f, 0.f};
+  float c_ex[2] = {0.f, 0.f}, c_ey[2] = {0.f, 0.f};
+  float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f}, c_hz[2] = {0.f, 0.f};
+  bool c_pr0 = false, c_pr1 = false;   // primal Ht(p-1) pending per cell
+  int stg = 0;
   uint32_t par = 0;
   bool ok = true;
-  for (int u = s_u[0]; u < NU.n; u = s_u[++ord & 1]) {
-    const int nxt = tid == 0 ? next_unit(a, NU) : 0;   // the CTA's next unit
-    const UnitGeo U = ugeo(u);
-    const int x0 = U.x0, y0 = U.y0, k0 = U.k0, k1 = U.k1;
-    const int p0_ = U.p0, p1_ = U.p1;
-    auto primal_plane = [&](int p) { return primal_of(U, p); };
-    const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-    // x profiles at x-1 (cell 0's -x neighbour), x and x+1
-    const bool sx0 = v0 && in_slab(x, g.nx, g.P), sx1 = v1 && in_slab(x + 1, g.nx, g.P);
-    const bool sxm = v0 && x > 0 && in_slab(x - 1, g.nx, g.P);
-    const bool sy = v0 && in_slab(y, g.ny, g.P), sym = v0 && y > 0 && in_slab(y - 1, g.ny, g.P);
-    float bx0 = 0.f, ax0 = 0.f, kx0 = 1.f, bx1 = 0.f, ax1 = 0.f, kx1 = 1.f, bxm = 0.f, axm = 0.f, kxm = 1.f;
-    float by = 0.f, ay = 0.f, ky = 1.f, bym = 0.f, aym = 0.f, kym = 1.f;
-    if (sx0) { bx0 = prof(g, 0, PR_BH, x); ax0 = prof(g, 0, PR_AH, x); kx0 = prof(g, 0, PR_KH, x); }
-    if (sx1) { bx1 = prof(g, 0, PR_BH, x + 1); ax1 = prof(g, 0, PR_AH, x + 1); kx1 = prof(g, 0, PR_KH, x + 1); }
-    if (sxm) { bxm = prof(g, 0, PR_BH, x - 1); axm = prof(g, 0, PR_AH, x - 1); kxm = prof(g, 0, PR_KH, x - 1); }
-    if (sy) { by = prof(g, 1, PR_BH, y); ay = prof(g, 1, PR_AH, y); ky = prof(g, 1, PR_KH, y); }
-    if (sym) { bym = prof(g, 1, PR_BH, y - 1); aym = prof(g, 1, PR_AH, y - 1); kym = prof(g, 1, PR_KH, y - 1); }
-    const bool yin = y >= g.P && y < g.ny - g.P;
-    const bool xyin0 = v0 && yin && x >= g.P && x < g.nx - g.P;
-    const bool xyin1 = v1 && yin && x + 1 >= g.P && x + 1 < g.nx - g.P;
-    const int lb = (ty + 1) * B::W + 2 * tx + 4;
-    const int hb = ty * B::W + 2 * tx;
-    const int ob = ty * TW + 2 * tx;
-    const float S_ = g.S;
-    const long long nc = g.nc;
-    float* const Hx = a.F + 3 * nc;
-    float* const LEx = a.L;
-    float* const lpB = a.psiB;
-    long long q = (long long)k0 * g.plane + (long long)y * g.px + x;
-    float c_m1[2] = {0.f, 0.f}, c_m2[2] = {0.f, 0.f};   // -z neighbour terms from plane p-1
-    float c_d0[2] = {0.f, 0.f}, c_d3[2] = {0.f, 0.f}, c_d4[2] = {0.f, 0.f}, c_d5[2] = {0.f, 0.f};
-    float c_ex[2] = {0.f, 0.f}, c_ey[2] = {0.f, 0.f};
-    float c_hx[2] = {0.f, 0.f}, c_hy[2] = {0.f, 0.f}, c_hz[2] = {0.f, 0.f};
-    bool c_pr0 = false, c_pr1 = false;   // primal Ht(p-1) pending per cell
-    for (int p = p0_; p <= p1_; ++p) {
-      unsigned char* st = dsm + stg * Y::STAGE;
-      if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
-      if (!__syncthreads_and(ok)) { ring_abort_n<S>(bars, stg, par, cur.issued - done, a.err); return; }
-      if (v0) {
-        const float* Eb = reinterpret_cast<const float*>(st + Y::E);
-        if (p > k0 && (c_pr0 || c_pr1)) {  // finish the primal Ht(p-1) with dEy/dz, dEx/dz
-          const float2 ex = ld2(Eb, hb), ey = ld2(Eb + B::P, hb);
-          const float d1[2] = {ey.x - c_ey[0], ey.y - c_ey[1]};
-          const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
-          const long long qm = q - g.plane;
-          st2(Hx, qm, __fadd_rn(c_hx[0], __fmul_rn(S_, c_d0[0] - d1[0])),
-              __fadd_rn(c_hx[1], __fmul_rn(S_, c_d0[1] - d1[1])), c_pr0, c_pr1);
-          st2(Hx + nc, qm, __fadd_rn(c_hy[0], __fmul_rn(S_, d2[0] - c_d3[0])),
-              __fadd_rn(c_hy[1], __fmul_rn(S_, d2[1] - c_d3[1])), c_pr0, c_pr1);
-          st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], __fmul_rn(S_, c_d4[0] - c_d5[0])),
-              __fadd_rn(c_hz[1], __fmul_rn(S_, c_d4[1] - c_d5[1])), c_pr0, c_pr1);
+  for (int p = p0_; p <= p1_; ++p) {
+    unsigned char* st = dsm + stg * Y::STAGE;
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    if (v0) {
+      const float* Eb = reinterpret_cast<const float*>(st + Y::E);
+      if (p > k0 && (c_pr0 || c_pr1)) {  // finish the primal Ht(p-1) with dEy/dz, dEx/dz
+        const float2 ex = ld2(Eb, hb), ey = ld2(Eb + B::P, hb);
+        const float d1[2] = {ey.x - c_ey[0], ey.y - c_ey[1]};
+        const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
+        const long long qm = q - g.plane;
+        st2(Hx, qm, __fadd_rn(c_hx[0], __fmul_rn(S_, c_d0[0] - d1[0])),
+            __fadd_rn(c_hx[1], __fmul_rn(S_, c_d0[1] - d1[1])), c_pr0, c_pr1);
+        st2(Hx + nc, qm, __fadd_rn(c_hy[0], __fmul_rn(S_, d2[0] - c_d3[0])),
+            __fadd_rn(c_hy[1], __fmul_rn(S_, d2[1] - c_d3[1])), c_pr0, c_pr1);
+        st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], __fmul_rn(S_, c_d4[0] - c_d5[0])),
+            __fadd_rn(c_hz[1], __fmul_rn(S_, c_d4[1] - c_d5[1])), c_pr0, c_pr1);
+      }
+      const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
+      if (p >= k0 && p < k1) {
+        const int k = p;
+        const bool pp = primal_plane(k);
+        c_pr0 = pp && xyin0;
+        c_pr1 = pp && xyin1;
+        if (c_pr0 || c_pr1) {  // primal Ht(k): x and y derivatives now, z derivatives next plane
+          const float2 ex = ld2(Eb, hb), ey = ld2(Eb + B::P, hb), ez = ld2(Eb + 2 * B::P, hb);
+          const float2 ezy = ld2(Eb + 2 * B::P, hb + B::W), exy = ld2(Eb, hb + B::W);
+          const float ezx = Eb[2 * B::P + hb + 2], eyx = Eb[B::P + hb + 2];
+          const float* Ho = reinterpret_cast<const float*>(st + Y::H);
+          const float2 h0 = ld2(Ho, ob), h1 = ld2(Ho + B::OP, ob), h2 = ld2(Ho + 2 * B::OP, ob);
+          c_d0[0] = ezy.x - ez.x; c_d0[1] = ezy.y - ez.y;
+          c_d3[0] = ez.y - ez.x;  c_d3[1] = ezx - ez.y;
+          c_d4[0] = ey.y - ey.x;  c_d4[1] = eyx - ey.y;
+          c_d5[0] = exy.x - ex.x; c_d5[1] = exy.y - ex.y;
+          c_ex[0] = ex.x; c_ex[1] = ex.y;
+          c_ey[0] = ey.x; c_ey[1] = ey.y;
+          c_hx[0] = h0.x; c_hx[1] = h0.y;
+          c_hy[0] = h1.x; c_hy[1] = h1.y;
+          c_hz[0] = h2.x; c_hz[1] = h2.y;
         }
-        const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
-        if (p >= k0 && p < k1) {
-          const int k = p;
-          const bool pp = primal_plane(k);
-          c_pr0 = pp && xyin0;
-          c_pr1 = pp && xyin1;
-          if (c_pr0 || c_pr1) {  // primal Ht(k): x and y derivatives now, z derivatives next plane
-            const float2 ex = ld2(Eb, hb), ey = ld2(Eb + B::P, hb), ez = ld2(Eb + 2 * B::P, hb);
-            const float2 ezy = ld2(Eb + 2 * B::P, hb + B::W), exy = ld2(Eb, hb + B::W);
-            const float ezx = Eb[2 * B::P + hb + 2], eyx = Eb[B::P + hb + 2];
-            const float* Ho = reinterpret_cast<const float*>(st + Y::H);
-            const float2 h0 = ld2(Ho, ob), h1 = ld2(Ho + B::OP, ob), h2 = ld2(Ho + 2 * B::OP, ob);
-            c_d0[0] = ezy.x - ez.x; c_d0[1] = ezy.y - ez.y;
-            c_d3[0] = ez.y - ez.x;  c_d3[1] = ezx - ez.y;
-            c_d4[0] = ey.y - ey.x;  c_d4[1] = eyx - ey.y;
-            c_d5[0] = exy.x - ex.x; c_d5[1] = exy.y - ex.y;
-            c_ex[0] = ex.x; c_ex[1] = ex.y;
-            c_ey[0] = ey.x; c_ey[1] = ey.y;
-            c_hx[0] = h0.x; c_hx[1] = h0.y;
-            c_hy[0] = h1.x; c_hy[1] = h1.y;
-            c_hz[0] = h2.x; c_hz[1] = h2.y;
+        // adjoint of the H half-step: lam_E += D^T lam_delta, v = -S s lam_H
+        const float2 lx2 = ld2(LHb, lb), ly2 = ld2(LHb + B::P, lb), lz2 = ld2(LHb + 2 * B::P, lb);
+        const float lhx[2] = {lx2.x, lx2.y}, lhy[2] = {ly2.x, ly2.y}, lhz[2] = {lz2.x, lz2.y};
+        float o0[2], o1[2], o2[2], o3[2], o4[2], o5[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          o0[c] = -S_ * lhx[c];
+          o5[c] = S_ * lhz[c];
+          o1[c] = S_ * lhx[c];
+          o2[c] = -S_ * lhy[c];
+          o3[c] = S_ * lhy[c];
+          o4[c] = -S_ * lhz[c];
+        }
+        float m0[2], m5[2];
+        {
+          const float2 lxy = ld2(LHb, lb - B::W), lzy = ld2(LHb + 2 * B::P, lb - B::W);   // -y
+          m0[0] = -S_ * lxy.x; m0[1] = -S_ * lxy.y;
+          m5[0] = S_ * lzy.x;  m5[1] = S_ * lzy.y;
+        }
+        float m3x = S_ * LHb[B::P + lb - 1], m4x = -S_ * LHb[2 * B::P + lb - 1];   // -x of cell 0
+        if (y == 0) { m0[0] = 0.f; m0[1] = 0.f; m5[0] = 0.f; m5[1] = 0.f; }
+        if (x == 0) { m3x = 0.f; m4x = 0.f; }
+        if (sy || sym) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0-1)
+          const int yb = (ty + 1) * TW + 2 * tx;
+          if (sy) {
+            const float2 p0 = ld2(P, yb), p1 = ld2(P + B::YP, yb);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float s4[2], s5[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              o0[c] = adj(o0[c], q0[c], by, ay, ky, &s4[c]);
+              o5[c] = adj(o5[c], q1[c], by, ay, ky, &s5[c]);
+            }
+            const long long qyy = psi_ix<1>(a.pl, 0, x, y, k);
+            st2(lpB, qyy, s4[0], s4[1], true, v1);
+            st2(lpB + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
           }
-          // adjoint of the H half-step: lam_E += D^T lam_delta, v = -S s lam_H
-          const float2 lx2 = ld2(LHb, lb), ly2 = ld2(LHb + B::P, lb), lz2 = ld2(LHb + 2 * B::P, lb);
-          const float lhx[2] = {lx2.x, lx2.y}, lhy[2] = {ly2.x, ly2.y}, lhz[2] = {lz2.x, lz2.y};
-          float o0[2], o1[2], o2[2], o3[2], o4[2], o5[2];
-  #pragma unroll
+          if (sym) {
+            const float2 p0 = ld2(P, yb - TW), p1 = ld2(P + B::YP, yb - TW);
+            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+            float dummy;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              m0[c] = adj(m0[c], q0[c], bym, aym, kym, &dummy);
+              m5[c] = adj(m5[c], q1[c], bym, aym, kym, &dummy);
+            }
+          }
+        }
+        if (sx0 || sx1 || sxm) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0-4, y0)
+          const int xb = ty * B::W + 2 * tx + 4;
+          const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
+          float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
+          if (sx0) {
+            o3[0] = adj(o3[0], p0.x, bx0, ax0, kx0, &s0[0]);
+            o4[0] = adj(o4[0], p1.x, bx0, ax0, kx0, &s1[0]);
+          }
+          if (sx1) {
+            o3[1] = adj(o3[1], p0.y, bx1, ax1, kx1, &s0[1]);
+            o4[1] = adj(o4[1], p1.y, bx1, ax1, kx1, &s1[1]);
+          }
+          const long long qxx = psi_ix<0>(a.pl, 0, x, y, k);
+          st2(lpB, qxx, s0[0], s0[1], sx0, sx1);
+          st2(lpB + a.pl.ax[0].cs, qxx, s1[0], s1[1], sx0, sx1);
+          if (sxm) {
+            float dummy;
+            m3x = adj(m3x, P[xb - 1], bxm, axm, kxm, &dummy);
+            m4x = adj(m4x, P[B::XP + xb - 1], bxm, axm, kxm, &dummy);
+          }
+        }
+        // cell 1's -x terms are cell 0's own terms
+        const float m3[2] = {m3x, o3[0]}, m4[2] = {m4x, o4[0]};
+        if (in_slab(k, g.nz, g.P)) {
+          const float* P = reinterpret_cast<const float*>(st + Y::PZ);
+          const float b = prof(g, 2, PR_BH, k), aa = prof(g, 2, PR_AH, k), kv = prof(g, 2, PR_KH, k);
+          const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
+          const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+          float s8[2], s9[2];
+#pragma unroll
           for (int c = 0; c < 2; ++c) {
-            o0[c] = -S_ * lhx[c];
-            o5[c] = S_ * lhz[c];
-            o1[c] = S_ * lhx[c];
-            o2[c] = -S_ * lhy[c];
-            o3[c] = S_ * lhy[c];
-            o4[c] = -S_ * lhz[c];
+            o1[c] = adj(o1[c], q0[c], b, aa, kv, &s8[c]);
+            o2[c] = adj(o2[c], q1[c], b, aa, kv, &s9[c]);
           }
-          float m0[2], m5[2];
-          {
-            const float2 lxy = ld2(LHb, lb - B::W), lzy = ld2(LHb + 2 * B::P, lb - B::W);   // -y
-            m0[0] = -S_ * lxy.x; m0[1] = -S_ * lxy.y;
-            m5[0] = S_ * lzy.x;  m5[1] = S_ * lzy.y;
-          }
-          float m3x = S_ * LHb[B::P + lb - 1], m4x = -S_ * LHb[2 * B::P + lb - 1];   // -x of cell 0
-          if (y == 0) { m0[0] = 0.f; m0[1] = 0.f; m5[0] = 0.f; m5[1] = 0.f; }
-          if (x == 0) { m3x = 0.f; m4x = 0.f; }
-          if (sy || sym) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PY);   // TW x (TY+1) at (x0, y0-1)
-            const int yb = (ty + 1) * TW + 2 * tx;
-            if (sy) {
-              const float2 p0 = ld2(P, yb), p1 = ld2(P + B::YP, yb);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float s4[2], s5[2];
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                o0[c] = adj(o0[c], q0[c], by, ay, ky, &s4[c]);
-                o5[c] = adj(o5[c], q1[c], by, ay, ky, &s5[c]);
-              }
-              const long long qyy = psi_ix<1>(a.pl, 0, x, y, k);
-              st2(lpB, qyy, s4[0], s4[1], true, v1);
-              st2(lpB + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
-            }
-            if (sym) {
-              const float2 p0 = ld2(P, yb - TW), p1 = ld2(P + B::YP, yb - TW);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float dummy;
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                m0[c] = adj(m0[c], q0[c], bym, aym, kym, &dummy);
-                m5[c] = adj(m5[c], q1[c], bym, aym, kym, &dummy);
-              }
-            }
-          }
-          if (sx0 || sx1 || sxm) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PX);   // (TW+4) x TY at (x0-4, y0)
-            const int xb = ty * B::W + 2 * tx + 4;
-            const float2 p0 = ld2(P, xb), p1 = ld2(P + B::XP, xb);
-            float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
-            if (sx0) {
-              o3[0] = adj(o3[0], p0.x, bx0, ax0, kx0, &s0[0]);
-              o4[0] = adj(o4[0], p1.x, bx0, ax0, kx0, &s1[0]);
-            }
-            if (sx1) {
-              o3[1] = adj(o3[1], p0.y, bx1, ax1, kx1, &s0[1]);
-              o4[1] = adj(o4[1], p1.y, bx1, ax1, kx1, &s1[1]);
-            }
-            const long long qxx = psi_ix<0>(a.pl, 0, x, y, k);
-            st2(lpB, qxx, s0[0], s0[1], sx0, sx1);
-            st2(lpB + a.pl.ax[0].cs, qxx, s1[0], s1[1], sx0, sx1);
-            if (sxm) {
-              float dummy;
-              m3x = adj(m3x, P[xb - 1], bxm, axm, kxm, &dummy);
-              m4x = adj(m4x, P[B::XP + xb - 1], bxm, axm, kxm, &dummy);
-            }
-          }
-          // cell 1's -x terms are cell 0's own terms
-          const float m3[2] = {m3x, o3[0]}, m4[2] = {m4x, o4[0]};
-          if (in_slab(k, g.nz, g.P)) {
+          const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
+          st2(lpB, qz, s8[0], s8[1], true, v1);
+          st2(lpB + a.pl.ax[2].cs, qz, s9[0], s9[1], true, v1);
+        }
+        const float* LEo = reinterpret_cast<const float*>(st + Y::LE);
+        const float2 le0 = ld2(LEo, ob), le1 = ld2(LEo + B::OP, ob), le2 = ld2(LEo + 2 * B::OP, ob);
+        st2(LEx, q, le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
+            le0.y + ((c_m2[1] - o2[1]) + (m5[1] - o5[1])), true, v1);
+        st2(LEx + nc, q, le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
+            le1.y + ((c_m1[1] - o1[1]) + (m4[1] - o4[1])), true, v1);
+        st2(LEx + 2 * nc, q, le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
+            le2.y + ((m0[1] - o0[1]) + (m3[1] - o3[1])), true, v1);
+        // the -z terms plane p+1 needs are this plane's own z-terms
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          c_m1[c] = o1[c];
+          c_m2[c] = o2[c];
+        }
+        q += g.plane;
+      } else if (p < k0) {  // -z terms for plane k0 from plane k0-1
+        float m1n[2] = {0.f, 0.f}, m2n[2] = {0.f, 0.f};
+        if (p >= 0) {
+          const float2 lx2 = ld2(LHb, lb), ly2 = ld2(LHb + B::P, lb);
+          m1n[0] = S_ * lx2.x; m1n[1] = S_ * lx2.y;
+          m2n[0] = -S_ * ly2.x; m2n[1] = -S_ * ly2.y;
+          if (in_slab(p, g.nz, g.P)) {
             const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-            const float b = prof(g, 2, PR_BH, k), aa = prof(g, 2, PR_AH, k), kv = prof(g, 2, PR_KH, k);
+            const float b1 = prof(g, 2, PR_BH, p), a1 = prof(g, 2, PR_AH, p), k1v = prof(g, 2, PR_KH, p);
             const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
             const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-            float s8[2], s9[2];
-  #pragma unroll
+            float dummy;
+#pragma unroll
             for (int c = 0; c < 2; ++c) {
-              o1[c] = adj(o1[c], q0[c], b, aa, kv, &s8[c]);
-              o2[c] = adj(o2[c], q1[c], b, aa, kv, &s9[c]);
+              m1n[c] = adj(m1n[c], q0[c], b1, a1, k1v, &dummy);
+              m2n[c] = adj(m2n[c], q1[c], b1, a1, k1v, &dummy);
             }
-            const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
-            st2(lpB, qz, s8[0], s8[1], true, v1);
-            st2(lpB + a.pl.ax[2].cs, qz, s9[0], s9[1], true, v1);
-          }
-          const float* LEo = reinterpret_cast<const float*>(st + Y::LE);
-          const float2 le0 = ld2(LEo, ob), le1 = ld2(LEo + B::OP, ob), le2 = ld2(LEo + 2 * B::OP, ob);
-          st2(LEx, q, le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
-              le0.y + ((c_m2[1] - o2[1]) + (m5[1] - o5[1])), true, v1);
-          st2(LEx + nc, q, le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
-              le1.y + ((c_m1[1] - o1[1]) + (m4[1] - o4[1])), true, v1);
-          st2(LEx + 2 * nc, q, le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
-              le2.y + ((m0[1] - o0[1]) + (m3[1] - o3[1])), true, v1);
-          // the -z terms plane p+1 needs are this plane's own z-terms
-  #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            c_m1[c] = o1[c];
-            c_m2[c] = o2[c];
-          }
-          q += g.plane;
-        } else if (p < k0) {  // -z terms for plane k0 from plane k0-1
-          float m1n[2] = {0.f, 0.f}, m2n[2] = {0.f, 0.f};
-          if (p >= 0) {
-            const float2 lx2 = ld2(LHb, lb), ly2 = ld2(LHb + B::P, lb);
-            m1n[0] = S_ * lx2.x; m1n[1] = S_ * lx2.y;
-            m2n[0] = -S_ * ly2.x; m2n[1] = -S_ * ly2.y;
-            if (in_slab(p, g.nz, g.P)) {
-              const float* P = reinterpret_cast<const float*>(st + Y::PZ);
-              const float b1 = prof(g, 2, PR_BH, p), a1 = prof(g, 2, PR_AH, p), k1v = prof(g, 2, PR_KH, p);
-              const float2 p0 = ld2(P, ob), p1 = ld2(P + B::OP, ob);
-              const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-              float dummy;
-  #pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                m1n[c] = adj(m1n[c], q0[c], b1, a1, k1v, &dummy);
-                m2n[c] = adj(m2n[c], q1[c], b1, a1, k1v, &dummy);
-              }
-            }
-          }
-  #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            c_m1[c] = m1n[c];
-            c_m2[c] = m2n[c];
           }
         }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          c_m1[c] = m1n[c];
+          c_m2[c] = m2n[c];
+        }
       }
-      __syncthreads();
-      if (tid == 0) {
-        if (p == U.p0) s_u[(ord + 1) & 1] = nxt;
-        produce(cur, s_u, NU.n, ugeo, issue, st, bars + stg);
-      }
-      if (++stg == S) { stg = 0; par ^= 1u; }
-      ++done;
     }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
+    if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }
 
@@ -1267,52 +1084,11 @@ static cudaError_t set_smem_l2(KT kernel, int bytes) {
 // Launch with the programmatic-stream-serialization attribute when a.pdl is
 // set (the kernel then overlaps its launch and prologue with the tail of the
 // previous kernel and waits in pdl_sync()).
-// CTAs of a kernel resident per SM at once, and the SM count (cached per
-// kernel, block size and shared memory).
-static cudaError_t resident_ctas(const void* fn, int threads, int smem, int* occ, int* sms) {
-  static std::mutex mu;
-  static std::map<std::tuple<const void*, int, int, int>, std::pair<int, int>> cache;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e) return e;
-  std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_tuple(fn, threads, smem, dev);
-  auto it = cache.find(key);
-  if (it == cache.end()) {
-    int o = 0, n = 0;
-    if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev))) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, smem))) return e;
-    it = cache.emplace(key, std::make_pair(o, n)).first;
-  }
-  *occ = it->second.first;
-  *sms = it->second.second;
-  return cudaSuccess;
-}
-
-// With a work-unit counter the grid is one CTA per resident slot (occupancy
-// x SMs, at most one per unit), and only when every unit stages at least S
-// planes (the smallest z chunk, plus the one or two planes around it that
-// each kernel stages): the ring's producer then never runs past the next
-// unit.  Otherwise the launch falls back to one unit per CTA of the 3D grid.
 template <class KT>
 static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStream_t s,
-                             const LagMaps& m, const StepArgs& a_in, int S, int extra_planes) {
+                             const LagMaps& m, const StepArgs& a) {
   cudaError_t e = set_smem_l2(kernel, smem);
   if (e) return e;
-  StepArgs a = a_in;
-  if (a.tickets) {
-    const int last = a.g.nz - (int)(grid.z - 1) * a.zchunk;
-    const int lmin = std::min(a.zchunk, last) + extra_planes;
-    int occ = 0, sms = 0;
-    if ((e = resident_ctas((const void*)kernel, (int)(block.x * block.y), smem, &occ, &sms)))
-      return e;
-    const long long units = (long long)grid.x * grid.y * grid.z;
-    if (lmin >= S && occ > 0) {
-      grid = dim3((unsigned)std::min<long long>(units, (long long)occ * sms), 1, 1);
-    } else {
-      a.tickets = nullptr;
-    }
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -1332,10 +1108,10 @@ static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
   dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
   dim3 block(TW / 2, TY);
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S, TW>, grid, block, LFH<TY, S, TW>::smem(), s, m, a, S, 1);
-    case 1: return launch_ex(k_l2fwd_e<TY, S, TW>, grid, block, LFE<TY, S, TW>::smem(), s, m, a, S, 1);
-    case 2: return launch_ex(k_l2rev_e<TY, S, TW>, grid, block, LRE<TY, S, TW>::smem(), s, m, a, S, 2);
-    case 3: return launch_ex(k_l2rev_h<TY, S, TW>, grid, block, LRH<TY, S, TW>::smem(), s, m, a, S, 2);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S, TW>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S, TW>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }
   return cudaErrorInvalidValue;
 }

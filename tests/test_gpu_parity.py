@@ -230,31 +230,6 @@ def test_compact_auxiliaries_match_the_full_grid_layout(F, A, ty, stages, tile_x
     assert r["sim"].workspace_bytes(rec) < base["sim"].workspace_bytes(rec)
 
 
-@pytest.mark.parametrize("kernel", [5, 6])
-@pytest.mark.parametrize("zchunk,stages,ty", [(1, 2, 8), (2, 3, 4), (3, 2, 16), (1, 3, 8),
-                                              (8, 2, 8)])
-def test_persistent_work_units_do_not_change_results(F, A, kernel, zchunk, stages, ty):
-    """Resident CTAs taking (tile, z chunk) units from a counter, the ring
-    staging the next unit's first planes during the current one: bit-equal
-    fields and gradient to one unit per CTA.  With z chunks of 1-3 planes the
-    100 x 100 x 50 grid has 1 400-5 000 units, several per resident CTA;
-    (1, 3) has units of fewer planes than stages (forward: 2 < 3), which run
-    with one unit per CTA."""
-    w = I.waveguide_sweep(n_steps=60)
-    rec = A.record_cfg("bf16", 4, "linear")
-    opts = {A.OPT_KERNEL: kernel, A.OPT_ZCHUNK: zchunk, A.OPT_STAGES: stages,
-            A.OPT_TILE_Y: ty}
-    base = gpu_run(F, A, w, rec=rec, options=dict(opts, **{A.OPT_PERSISTENT: 0}))
-    for graphs in (0, 1):
-        r = gpu_run(F, A, w, rec=rec, options=dict(opts, **{A.OPT_PERSISTENT: 1,
-                                                          A.OPT_USE_GRAPHS: graphs}))
-        np.testing.assert_array_equal(r["fields"], base["fields"])
-        np.testing.assert_array_equal(r["g"], base["g"])
-        # per-step objectives are FP64 sums over CTAs (atomic, any order)
-        np.testing.assert_allclose(r["hist"], base["hist"], rtol=1e-12,
-                                   atol=1e-12 * np.abs(base["hist"]).max())
-
-
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     w = SMALL["ragged_poynting"]()
