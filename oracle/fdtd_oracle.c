@@ -683,6 +683,123 @@ int oracle_quantize_array(int fmt, const double* in, double* out, long n) {
   return 0;
 }
 
+/* ------------------------------------------ block-transform codec ----
+ * Beyond the paper (its Sec. 4 names JPEG-like compression of the tape as
+ * future work): a face component [v][u] is cut into 8 x 8 blocks, cells past
+ * the face edge repeating the last row / column; each block is expanded in
+ * the orthonormal 2D DCT-II basis
+ *     B_uv(x, y) = c_u c_v cos((2x+1) u pi/16) cos((2y+1) v pi/16),
+ *     c_0 = sqrt(1/8), c_u = sqrt(2/8) otherwise,
+ * and only the first K coefficients in diagonal order (u + v ascending, then
+ * v ascending) are kept, each as an int8 code round(C / s) with the block
+ * scale s = max(max|C| / 127, 2^-126) (1 for an all-zero block).
+ * This is a quantised code decided in floating point, so it is computed in
+ * the precision the CUDA path uses: float32, the basis rounded to float from
+ * the double product, every sum an fmaf chain in a fixed order (cells row by
+ * row for a coefficient; kept coefficients in order for a value), then one
+ * float multiply by s.  (The cross-check against an FP64 DCT is a test.)
+ */
+static void bdct_uv(int i, int* u, int* v) {
+  int n = 0;
+  for (int d = 0; d <= 14; ++d)
+    for (int vv = 0; vv <= d && vv <= 7; ++vv) {
+      int uu = d - vv;
+      if (uu > 7) continue;
+      if (n++ == i) { *u = uu; *v = vv; return; }
+    }
+  *u = 0; *v = 0;
+}
+
+/* beta[i*64 + y*8 + x] = B_{u_i v_i}(x, y) as float. */
+void oracle_bdct_basis(float* beta) {
+  for (int i = 0; i < 64; ++i) {
+    int u, v; bdct_uv(i, &u, &v);
+    for (int y = 0; y < 8; ++y)
+      for (int x = 0; x < 8; ++x) {
+        double cu = u == 0 ? sqrt(1.0 / 8.0) : 0.5, cv = v == 0 ? sqrt(1.0 / 8.0) : 0.5;
+        double du = cu * cos((2 * x + 1) * u * 3.14159265358979323846 / 16.0);
+        double dv = cv * cos((2 * y + 1) * v * 3.14159265358979323846 / 16.0);
+        beta[i * 64 + y * 8 + x] = (float)(du * dv);
+      }
+  }
+}
+
+/* in [nv][nu] -> codes [nblocks][K] and scales [nblocks], blocks row-major. */
+int oracle_bdct_encode(const float* in, int nu, int nv, int K, signed char* codes, float* scales) {
+  if (nu < 1 || nv < 1 || K < 1 || K > 64) return -1;
+  float beta[64 * 64];
+  oracle_bdct_basis(beta);
+  int nbu = (nu + 7) / 8, nbv = (nv + 7) / 8;
+  for (int bv = 0; bv < nbv; ++bv)
+    for (int bu = 0; bu < nbu; ++bu) {
+      float X[64], C[64];
+      for (int y = 0; y < 8; ++y)
+        for (int x = 0; x < 8; ++x) {
+          int vv = bv * 8 + y < nv ? bv * 8 + y : nv - 1;
+          int uu = bu * 8 + x < nu ? bu * 8 + x : nu - 1;
+          X[y * 8 + x] = in[(size_t)vv * nu + uu];
+        }
+      float amax = 0.0f;
+      for (int i = 0; i < K; ++i) {
+        float c = 0.0f;
+        for (int t = 0; t < 64; ++t) c = fmaf(X[t], beta[i * 64 + t], c);
+        C[i] = c;
+        if (fabsf(c) > amax) amax = fabsf(c);
+      }
+      float s = 1.0f;
+      if (amax > 0.0f) {
+        s = amax / 127.0f;
+        if (s < 1.17549435e-38f) s = 1.17549435e-38f;
+      }
+      size_t b = (size_t)bv * nbu + bu;
+      for (int i = 0; i < K; ++i) {
+        float q = rintf(C[i] / s);
+        if (q > 127.0f) q = 127.0f;
+        if (q < -127.0f) q = -127.0f;
+        codes[b * K + i] = (signed char)(int)q;
+      }
+      scales[b] = s;
+    }
+  return 0;
+}
+
+int oracle_bdct_decode(const signed char* codes, const float* scales, int nu, int nv, int K,
+                       float* out) {
+  if (nu < 1 || nv < 1 || K < 1 || K > 64) return -1;
+  float beta[64 * 64];
+  oracle_bdct_basis(beta);
+  int nbu = (nu + 7) / 8;
+  for (int vv = 0; vv < nv; ++vv)
+    for (int uu = 0; uu < nu; ++uu) {
+      size_t b = (size_t)(vv / 8) * nbu + uu / 8;
+      int t = (vv % 8) * 8 + uu % 8;
+      float acc = 0.0f;
+      for (int i = 0; i < K; ++i) acc = fmaf((float)codes[b * K + i], beta[i * 64 + t], acc);
+      out[(size_t)vv * nu + uu] = acc * scales[b];
+    }
+  return 0;
+}
+
+/* Apply the codec to one face sample in place ([comp][v][u], float32 values
+ * as the CUDA path records them). */
+static int bdct_face(double* v, int nu, int nv, int K) {
+  size_t n = (size_t)nu * nv;
+  int nb = ((nu + 7) / 8) * ((nv + 7) / 8);
+  float* x = (float*)malloc(n * sizeof(float));
+  float* y = (float*)malloc(n * sizeof(float));
+  signed char* codes = (signed char*)malloc((size_t)nb * K);
+  float* sc = (float*)malloc((size_t)nb * sizeof(float));
+  if (!x || !y || !codes || !sc) { free(x); free(y); free(codes); free(sc); return -2; }
+  for (int t = 0; t < 2; ++t) {
+    for (size_t i = 0; i < n; ++i) x[i] = (float)v[t * n + i];
+    oracle_bdct_encode(x, nu, nv, K, codes, sc);
+    oracle_bdct_decode(codes, sc, nu, nv, K, y);
+    for (size_t i = 0; i < n; ++i) v[t * n + i] = y[i];
+  }
+  free(x); free(y); free(codes); free(sc);
+  return 0;
+}
+
 /* ------------------------------------------------- interpolation ----
  * Value at time q of a series known at increasing knots t[0..nk-1].
  * kind 0: linear between the bracketing knots (Sec. 2).
@@ -868,8 +985,9 @@ int oracle_unstep(const ocfg* c, const double* eps, double* st, int n) {
  * the forward run, so any use of a value the method does not have shows up.
  * fmt < 0 keeps the samples unquantised (exact FP64).
  */
-int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k, int interp,
-                   double seed, double* grad, double* obj, double* tape_values_out) {
+int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int coeffs, int k,
+                      int interp, double seed, double* grad, double* obj,
+                      double* tape_values_out) {
   size_t N = ncell(c);
   int T = c->n_steps;
   if (k < 1 || T < 1 || c->P < 1) return -1;
@@ -909,10 +1027,21 @@ int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k,
     e_update(&x, eps, st, n);
     L += objective(c, st);
   }
-  if (fmt >= 0)
+  if (fmt == 9) {   /* block-transform codec, K = coeffs (0: 10) */
+    for (int j = 0; j < J; ++j)
+      for (int f = 0; f < 6; ++f) {
+        int ua, va, nu, nv; face_dims(c, f, &ua, &va, &nu, &nv);
+        if (bdct_face(tape + (size_t)j * ns + foff[f], nu, nv, coeffs ? coeffs : 10)) {
+          free(st); free(lam); free(tmp); free(dE); free(tape); free(tk); free(pv); free(fb);
+          ctx_free(&x);
+          return -2;
+        }
+      }
+  } else if (fmt >= 0) {
     for (int j = 0; j < J; ++j)
       for (int f = 0; f < 6; ++f)
         encode_face(fmt, scaled, tape + (size_t)j * ns + foff[f], foff[f + 1] - foff[f], NULL);
+  }
   if (tape_values_out) memcpy(tape_values_out, tape, (size_t)J * ns * sizeof(double));
 
   /* keep only what the method has: the interior of E and Ht */
@@ -974,4 +1103,9 @@ int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k,
   free(st); free(lam); free(tmp); free(dE); free(tape); free(tk); free(pv); free(fb);
   ctx_free(&x);
   return 0;
+}
+
+int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k, int interp,
+                   double seed, double* grad, double* obj, double* tape_values_out) {
+  return oracle_reverse_ex(c, eps, fmt, scaled, 0, k, interp, seed, grad, obj, tape_values_out);
 }

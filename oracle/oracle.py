@@ -18,9 +18,17 @@ C0 = 299792458.0
 NF = 18
 # Tape formats.  "e4m3" is the OCP / hardware float8 e4m3fn (max 448); the
 # other 8-bit formats are the ones compared in Sec. 4 (Fig. 3); "e4m3ieee" is
-# the IEEE-style float8 e4m3 with infinities (max 240).
+# the IEEE-style float8 e4m3 with infinities (max 240); "bdct<K>" is the 8 x 8
+# block-transform codec keeping K coefficients per block ("bdct": K = 10).
 FMT = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4, "e5m2fnuz": 5,
-       "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8, "none": -1}
+       "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8, "bdct": 9, "none": -1}
+
+
+def _fmt(fmt: str):
+    """(format id, coefficients) of a format name."""
+    if fmt.startswith("bdct"):
+        return 9, (int(fmt[4:]) if len(fmt) > 4 else 10)
+    return FMT[fmt], 0
 
 
 class OCfg(C.Structure):
@@ -63,6 +71,13 @@ def lib():
         L.oracle_gradient2.argtypes = [cp, dp, C.c_double, C.c_double, dp, dp, dp]
         L.oracle_reverse.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      dp, dp, dp]
+        L.oracle_reverse_ex.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_double, dp, dp, dp]
+        fp = C.POINTER(C.c_float)
+        bp = C.POINTER(C.c_byte)
+        L.oracle_bdct_basis.argtypes = [fp]
+        L.oracle_bdct_encode.argtypes = [fp, C.c_int, C.c_int, C.c_int, bp, fp]
+        L.oracle_bdct_decode.argtypes = [bp, fp, C.c_int, C.c_int, C.c_int, fp]
         L.oracle_quantize_array.argtypes = [C.c_int, dp, dp, C.c_long]
         L.oracle_format_max.argtypes = [C.c_int]
         L.oracle_format_max.restype = C.c_double
@@ -229,10 +244,41 @@ def reverse(w, fmt: str = "none", scaled: bool = False, k: int = 1, interp: str 
     tape = None
     if want_tape:
         tape = np.zeros((n_samples(c.n_steps, k), sample_values(w, **kw)))
-    _check(lib().oracle_reverse(C.byref(c), _dp(_eps(w)), FMT[fmt], int(scaled), k,
-                                0 if interp == "linear" else 1, seed, _dp(g), _dp(obj),
-                                _dp(tape) if want_tape else None))
+    fid, coeffs = _fmt(fmt)
+    _check(lib().oracle_reverse_ex(C.byref(c), _dp(_eps(w)), fid, int(scaled), coeffs, k,
+                                   0 if interp == "linear" else 1, seed, _dp(g), _dp(obj),
+                                   _dp(tape) if want_tape else None))
     return (float(obj[0]), g, tape) if want_tape else (float(obj[0]), g)
+
+
+def bdct_basis() -> np.ndarray:
+    """float32 [64 coefficients in diagonal order][8 y][8 x]."""
+    b = np.zeros(64 * 64, np.float32)
+    lib().oracle_bdct_basis(b.ctypes.data_as(C.POINTER(C.c_float)))
+    return b.reshape(64, 8, 8)
+
+
+def bdct_encode(plane, K: int):
+    """float32 plane [nv][nu] -> (int8 codes [nblocks][K], float32 scales)."""
+    x = np.ascontiguousarray(plane, dtype=np.float32)
+    nv, nu = x.shape
+    nb = ((nu + 7) // 8) * ((nv + 7) // 8)
+    codes = np.zeros((nb, K), np.int8)
+    scales = np.zeros(nb, np.float32)
+    _check(lib().oracle_bdct_encode(x.ctypes.data_as(C.POINTER(C.c_float)), nu, nv, K,
+                                    codes.ctypes.data_as(C.POINTER(C.c_byte)),
+                                    scales.ctypes.data_as(C.POINTER(C.c_float))))
+    return codes, scales
+
+
+def bdct_decode(codes, scales, nu: int, nv: int) -> np.ndarray:
+    codes = np.ascontiguousarray(codes, dtype=np.int8)
+    scales = np.ascontiguousarray(scales, dtype=np.float32)
+    out = np.zeros((nv, nu), np.float32)
+    _check(lib().oracle_bdct_decode(codes.ctypes.data_as(C.POINTER(C.c_byte)),
+                                    scales.ctypes.data_as(C.POINTER(C.c_float)), nu, nv,
+                                    codes.shape[1], out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out
 
 
 def quantize(fmt: str, x) -> np.ndarray:

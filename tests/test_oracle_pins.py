@@ -534,3 +534,125 @@ def test_sine_at_136_steps_per_period(k):
     cub = np.abs(O.interp_series("cubic", t, p, q) - np.sin(w * q))[inner].max()
     # cubic's edge shrinks as sampling approaches Nyquist (4.25 samples/period at k = 32)
     assert cub < (0.2 if k <= 16 else 0.5) * lin
+
+
+# ------------------------------------------------ block-transform codec ---
+# The tape codec beyond the paper (Sec. 4 names JPEG-like tape compression as
+# future work): 8 x 8 orthonormal DCT-II, first K coefficients in diagonal
+# order, int8 codes with one float32 scale per block.
+
+def _dct_order():
+    return [(d - v, v) for d in range(15) for v in range(d + 1) if d - v <= 7 and v <= 7]
+
+
+def test_bdct_basis_is_the_orthonormal_dct_in_diagonal_order():
+    """Rows of the basis are orthonormal (to float32 rounding) and row i is
+    the outer product of the 1D DCT-II vectors of (u_i, v_i), the diagonal
+    order u + v ascending then v ascending; checked against scipy's DCT."""
+    from scipy.fft import dct
+    b = O.bdct_basis().astype(np.float64)
+    m = b.reshape(64, 64)
+    assert np.abs(m @ m.T - np.eye(64)).max() < 2e-7
+    d = dct(np.eye(8), type=2, norm="ortho", axis=0)      # d[u, x]
+    order = _dct_order()
+    assert order[:10] == [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (3, 0), (2, 1), (1, 2),
+                          (0, 3)]
+    for i, (u, v) in enumerate(order):
+        np.testing.assert_allclose(b[i], np.outer(d[v], d[u]), rtol=0, atol=1e-7)
+
+
+def test_bdct_coefficients_match_scipy_dctn():
+    """All 64 coefficients kept: codes * scale are the 2D DCT-II coefficients
+    of the block (scipy.fft.dctn, orthonormal, FP64) to within half a code
+    step, the largest code is +-127, and decoding reproduces the block to
+    within the accumulated half steps."""
+    from scipy.fft import dctn
+    rng = np.random.default_rng(4)
+    order = _dct_order()
+    for trial in range(20):
+        x = (rng.standard_normal((8, 8)) * 10.0 ** rng.uniform(-6, 3)).astype(np.float32)
+        codes, s = O.bdct_encode(x, 64)
+        C = dctn(x.astype(np.float64), type=2, norm="ortho")   # C[v, u]
+        ref = np.array([C[v, u] for (u, v) in order])
+        got = codes[0].astype(np.float64) * s[0]
+        assert np.abs(got - ref).max() <= 0.5 * s[0] * (1 + 1e-5) + 1e-6 * np.abs(ref).max()
+        assert np.abs(codes[0]).max() == 127
+        assert s[0] == np.float32(np.float32(np.abs(ref).max()) / np.float32(127.0)) or \
+            abs(s[0] - np.abs(ref).max() / 127) <= 1e-6 * s[0]
+        y = O.bdct_decode(codes, s, 8, 8)
+        # each decoded cell carries at most 64 half-step errors, each weighted
+        # by |B_i(cell)| <= 1/4
+        assert np.abs(y - x).max() <= 64 * 0.25 * 0.5 * s[0] * 1.01
+
+
+def test_bdct_single_basis_function_and_constant_blocks():
+    """A block equal to a * B_j (j < K) codes to +-127 at j and 0 elsewhere;
+    a constant block c has the single coefficient 8c (DC) and decodes to c to
+    within one code step; an all-zero block has scale 1 and zero codes."""
+    b = O.bdct_basis()
+    for j in (0, 1, 2, 4, 9):
+        for a in (3.5, -0.02):
+            codes, s = O.bdct_encode(a * b[j], 10)
+            assert codes[0, j] == (127 if a > 0 else -127)
+            assert np.abs(np.delete(codes[0], j)).max() == 0
+            assert s[0] == pytest.approx(abs(a) / 127, rel=1e-6)
+    x = np.full((8, 8), 0.7, np.float32)
+    codes, s = O.bdct_encode(x, 6)
+    assert codes[0, 0] == 127 and np.abs(codes[0, 1:]).max() == 0
+    assert s[0] == pytest.approx(8 * 0.7 / 127, rel=1e-6)
+    np.testing.assert_allclose(O.bdct_decode(codes, s, 8, 8), x, rtol=0, atol=s[0] / 8)
+    codes, s = O.bdct_encode(np.zeros((8, 8), np.float32), 10)
+    assert s[0] == 1.0 and not codes.any()
+
+
+def test_bdct_ragged_faces_repeat_the_edge():
+    """Cells past the face edge repeat the last row / column: an 11 x 5 face
+    codes exactly like the 16 x 8 face padded by edge replication, and the
+    decoded face is the padded one's decode, cropped."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((5, 11)).astype(np.float32)
+    xp = np.pad(x, ((0, 3), (0, 5)), mode="edge")
+    for K in (1, 10, 64):
+        c, s = O.bdct_encode(x, K)
+        cp, sp = O.bdct_encode(xp, K)
+        np.testing.assert_array_equal(c, cp)
+        np.testing.assert_array_equal(s, sp)
+        np.testing.assert_array_equal(O.bdct_decode(c, s, 11, 5),
+                                      O.bdct_decode(cp, sp, 16, 8)[:5, :11])
+
+
+def test_bdct_keeps_smooth_fields_and_drops_fine_detail():
+    """Zonal truncation: a long-wavelength field (period 40 cells, as the
+    boundary fields of the 20 nm waveguide) keeps its shape when only the
+    first K coefficients are kept (FP64 with scipy's DCT: max error 5 % of the
+    amplitude at K = 10, < 2 % at K = 21); the codec's error stays within that
+    truncation error plus the quantisation bound 0.5 s sum_i |B_i(cell)| per
+    cell.  A block of the highest frequency (u = v = 7) alone is removed
+    (down to the float32 rounding of the kept coefficients)."""
+    from scipy.fft import dctn, idctn
+    yy, xx = np.mgrid[0:32, 0:48]
+    smooth = np.sin(2 * np.pi * (xx / 40.0 + yy / 55.0)).astype(np.float32)
+    errs = {}
+    for K in (10, 21):
+        keep = np.zeros((8, 8), bool)
+        for (u, v) in _dct_order()[:K]:
+            keep[v, u] = True
+        trunc = np.zeros((32, 48))
+        for by in range(4):
+            for bx in range(6):
+                blk = smooth[8 * by:8 * by + 8, 8 * bx:8 * bx + 8].astype(np.float64)
+                C = dctn(blk, type=2, norm="ortho")
+                trunc[8 * by:8 * by + 8, 8 * bx:8 * bx + 8] = idctn(np.where(keep, C, 0.0),
+                                                                    type=2, norm="ortho")
+        terr = np.abs(trunc - smooth)
+        errs[K] = terr.max()
+        c, s = O.bdct_encode(smooth, K)
+        y = O.bdct_decode(c, s, 48, 32)
+        wsum = np.abs(O.bdct_basis()[:K]).sum(axis=0)            # [8 y][8 x]
+        bound = (0.5 * s.reshape(4, 6)[:, None, :, None] * wsum[None, :, None, :]).reshape(32, 48)
+        assert np.all(np.abs(y - smooth) <= terr + bound * 1.001 + 1e-6)
+    assert errs[21] < 0.02 < errs[10] < 0.06
+    hf = np.tile(5.0 * O.bdct_basis()[63], (4, 6))
+    c, s = O.bdct_encode(hf, 10)
+    # what is left is the float32 rounding of the kept coefficients (~1e-7)
+    assert np.abs(O.bdct_decode(c, s, 48, 32)).max() < 1e-5
