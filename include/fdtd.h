@@ -107,11 +107,22 @@ typedef struct {
  *   E4M3_IEEE   4,3,7,  240     E3M4     3,4,3,  15.5
  * "fnuz": no infinities, no negative zero, NaN = 0x80; the IEEE-like ones
  * reserve the all-ones exponent for infinities and NaNs.  All encodings round
- * to nearest, ties to even, and saturate to the largest finite value. */
+ * to nearest, ties to even, and saturate to the largest finite value.
+ *
+ * BDCT (9) is a block-transform codec beyond the paper (its Sec. 4 names
+ * JPEG-like compression of the tape as future work): every face component
+ * [v][u] is cut into 8 x 8 blocks (cells past the face edge repeat the last
+ * row / column), each block is transformed with the orthonormal 2D DCT-II,
+ * and the first `coeffs` coefficients in diagonal order (u + v ascending,
+ * then v ascending) are kept as int8 codes round(C / s), s = max(max|C| /
+ * 127, 2^-126) (1 for an all-zero block), with s stored as float32 per block.
+ * All of it in float32 with a fixed operation order (fmaf over the block's
+ * cells row by row, then over the kept coefficients in order), so that an
+ * independent implementation reproduces the codes bit for bit. */
 enum {
   FDTD_TAPE_F32 = 0, FDTD_TAPE_BF16 = 1, FDTD_TAPE_F16 = 2, FDTD_TAPE_E4M3 = 3,
   FDTD_TAPE_E4M3B11FNUZ = 4, FDTD_TAPE_E5M2FNUZ = 5, FDTD_TAPE_E4M3FNUZ = 6,
-  FDTD_TAPE_E4M3_IEEE = 7, FDTD_TAPE_E3M4 = 8
+  FDTD_TAPE_E4M3_IEEE = 7, FDTD_TAPE_E3M4 = 8, FDTD_TAPE_BDCT = 9
 };
 enum { FDTD_INTERP_LINEAR = 0, FDTD_INTERP_CUBIC = 1 };
 
@@ -120,12 +131,16 @@ enum { FDTD_INTERP_LINEAR = 0, FDTD_INTERP_CUBIC = 1 };
  * interpolation used to restore the steps in between.  scaled = 1 stores a
  * per-face, per-sample FP32 scale max(absmax/format_max, 2^-126) (1 when the
  * face is all zero; F16 and the 8-bit types only); values are converted back
- * to FP32 before any arithmetic. */
+ * to FP32 before any arithmetic.  coeffs: BDCT only, coefficients kept per
+ * 8 x 8 block (1..64; 0 = 10, the diagonals u + v <= 3); must be 0 for the
+ * other types.  A BDCT sample holds int8 codes [face][comp][block][coeffs]
+ * (zero-padded to 16 bytes), then float32 scales [face][comp][block]. */
 typedef struct {
   int dtype;
   int k;
   int interp;
   int scaled;
+  int coeffs;
 } fdtd_record_cfg;
 
 /* Plan a problem.  Host only: touches no device.  dx in metres, dt in
@@ -281,6 +296,21 @@ int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, void* d_code
                 void* cuda_stream);
 int fdtd_decode(int dtype, const void* d_code, size_t n, const float* d_scale, float* d_out,
                 void* cuda_stream);
+
+/* BDCT codec on one raw device plane, for tests: d_in float32 [nv][nu]
+ * (nu, nv >= 1) -> d_codes int8 [nblocks][coeffs] and d_scales float32
+ * [nblocks], nblocks = ceil(nu/8) ceil(nv/8) in row-major block order; decode
+ * writes the reconstructed [nv][nu] plane.  coeffs in 1..64 (FDTD_EINVAL
+ * otherwise).  Asynchronous on cuda_stream. */
+int fdtd_bdct_encode(const float* d_in, int nu, int nv, int coeffs, signed char* d_codes,
+                     float* d_scales, void* cuda_stream);
+int fdtd_bdct_decode(const signed char* d_codes, const float* d_scales, int nu, int nv, int coeffs,
+                     float* d_out, void* cuda_stream);
+/* The BDCT basis table (host, no device use): out[i*64 + y*8 + x] = the
+ * float32 value of basis function i (diagonal order) at cell (x, y).  The
+ * first BDCT use on a device uploads this table synchronously, so it must
+ * not happen while the caller's stream is being captured. */
+int fdtd_bdct_basis(float* out);
 
 /* Self-test of the bounded device waits (failure detection without a
  * fault): one CTA arms an mbarrier for a copy that is never issued and waits

@@ -17,9 +17,12 @@ FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ESTATE, FDTD_ETIMEOUT, FDTD_
 STATUS_NAMES = {0: "FDTD_OK", -1: "FDTD_EINVAL", -2: "FDTD_ENOMEM", -3: "FDTD_ECUDA",
                 -4: "FDTD_ESTATE", -5: "FDTD_ETIMEOUT", -6: "FDTD_ENONFINITE"}
 # Tape element types: "e4m3" (alias "e4m3fn") is the hardware OCP float8; the
-# other 8-bit names are the formats of Sec. 4, "e4m3ieee" the IEEE-style e4m3.
+# other 8-bit names are the formats of Sec. 4, "e4m3ieee" the IEEE-style e4m3;
+# "bdct" is the 8 x 8 block-transform codec ("bdct<K>" keeps K coefficients per
+# block, plain "bdct" 10).
 TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4, "e5m2fnuz": 5,
-        "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8}
+        "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8, "bdct": 9}
+BDCT_DEFAULT_COEFFS = 10
 INTERP = {"linear": 0, "cubic": 1}
 OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS, OPT_STAGES, OPT_PDL, \
     OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX = range(11)
@@ -51,7 +54,8 @@ class Detector(C.Structure):
 
 
 class RecordCfg(C.Structure):
-    _fields_ = [("dtype", C.c_int), ("k", C.c_int), ("interp", C.c_int), ("scaled", C.c_int)]
+    _fields_ = [("dtype", C.c_int), ("k", C.c_int), ("interp", C.c_int), ("scaled", C.c_int),
+                ("coeffs", C.c_int)]
 
 
 class FdtdError(RuntimeError):
@@ -100,6 +104,11 @@ _PROTOS = {
                               C.c_void_p]),
     "fdtd_decode": (C.c_int, [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                               C.c_void_p]),
+    "fdtd_bdct_encode": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
+    "fdtd_bdct_decode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                   C.c_void_p]),
+    "fdtd_bdct_basis": (C.c_int, [C.c_void_p]),
     "fdtd_selftest_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p]),
     "fdtd_value_and_grad_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                               C.c_double, C.POINTER(C.c_double), C.c_void_p]),
@@ -129,7 +138,12 @@ def check(status: int, handle=None) -> None:
 
 def record_cfg(dtype: str = "f32", k: int = 1, interp: str = "linear", scaled=None) -> RecordCfg:
     """Tape configuration; scaled defaults to per-face scales for f16 and the
-    hardware e4m3 (the paper's 8-bit formats default to unscaled, as in Sec. 4)."""
+    hardware e4m3 (the paper's 8-bit formats default to unscaled, as in Sec. 4).
+    "bdct<K>" selects the block-transform codec with K coefficients per block."""
+    coeffs = 0
+    if dtype.startswith("bdct"):
+        coeffs = int(dtype[4:]) if len(dtype) > 4 else BDCT_DEFAULT_COEFFS
+        dtype = "bdct"
     if scaled is None:
         scaled = dtype in ("f16", "e4m3", "e4m3fn")
-    return RecordCfg(TAPE[dtype], int(k), INTERP[interp], int(bool(scaled)))
+    return RecordCfg(TAPE[dtype], int(k), INTERP[interp], int(bool(scaled)), coeffs)

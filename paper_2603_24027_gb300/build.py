@@ -18,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libfdtd_gb300.so")
 SOURCES = ["kernels_step.cu", "kernels_fused.cu", "kernels_tma.cu", "kernels_split_tma.cu",
-           "kernels_lag.cu", "kernels_lag2.cu", "kernels_ffwd.cu", "kernels_tape.cu", "fdtd_api.cu"]
+           "kernels_lag.cu", "kernels_lag2.cu", "kernels_ffwd.cu", "kernels_tape.cu",
+           "kernels_bdct.cu", "fdtd_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE]

@@ -20,6 +20,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/fdtd.h"
+#include "bdct.cuh"
 #include "fdtd_internal.cuh"
 
 using namespace fdtd;
@@ -250,6 +251,23 @@ static int n_samples(int N, int k) {
   return (N - 1 - r) / k + 1;
 }
 
+static bool valid_dtype(int dt) { return (dt >= 0 && dt < kTapeDtypes) || dt == kTapeBdct; }
+// coeffs: 0..64 for BDCT (0 = the default), 0 for every other type.
+static bool coeffs_ok(const fdtd_record_cfg* rec) {
+  return rec->dtype == kTapeBdct ? rec->coeffs >= 0 && rec->coeffs <= 64 : rec->coeffs == 0;
+}
+static int bdct_coeffs(const fdtd_record_cfg* rec) {
+  return rec->coeffs ? rec->coeffs : kBdctDefaultCoeffs;
+}
+
+// Bytes of one tape sample (padded to 16) and the element size its offsets
+// count in.
+static long long sample_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec) {
+  if (rec && rec->dtype == kTapeBdct) return bdct_layout(h->faces, bdct_coeffs(rec)).sample_bytes;
+  const int eb = code_bytes(rec ? rec->dtype : 0);
+  return (sample_elems(h) * eb + 15) / 16 * 16;
+}
+
 // ---------------------------------------------------------- interpolation ---
 // Knots of the recorded series in step units: samples at r + j k and the
 // known zero initial state (Ht^{-1/2} at -1; E^0 at 0 unless 0 is a sample).
@@ -428,9 +446,8 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   L.err = off; off += 256;
   int dt = rec ? rec->dtype : 0;
   int k = rec ? rec->k : 1;
-  int eb = code_bytes(dt);
-  long long se = sample_elems(h);
-  long long stride = ((se * eb + 15) / 16) * 16 / eb;
+  int eb = dt == kTapeBdct ? 1 : code_bytes(dt);
+  long long stride = sample_bytes(h, rec) / eb;
   L.stride = stride;
   L.J = n_samples(h->N, k);
   L.tape = off; off += al((size_t)L.J * stride * eb);
@@ -451,12 +468,13 @@ static Geo geo_of(const fdtd_handle* h) {
 
 static int check_rec(fdtd_handle* h, const fdtd_record_cfg* rec) {
   if (!rec) return fail(h, FDTD_EINVAL, "record config is NULL");
-  if (rec->dtype < 0 || rec->dtype >= kTapeDtypes) return fail(h, FDTD_EINVAL, "unknown tape dtype");
+  if (!valid_dtype(rec->dtype)) return fail(h, FDTD_EINVAL, "unknown tape dtype");
   if (rec->k < 1) return fail(h, FDTD_EINVAL, "k must be >= 1");
   if (rec->interp != FDTD_INTERP_LINEAR && rec->interp != FDTD_INTERP_CUBIC)
     return fail(h, FDTD_EINVAL, "unknown interpolation");
-  if (rec->scaled && rec->dtype < 2)
-    return fail(h, FDTD_EINVAL, "per-face scale applies to F16 and E4M3 only");
+  if (rec->scaled && (rec->dtype < 2 || rec->dtype == kTapeBdct))
+    return fail(h, FDTD_EINVAL, "per-face scale applies to F16 and the 8-bit types only");
+  if (!coeffs_ok(rec)) return fail(h, FDTD_EINVAL, "coeffs: 0..64 for BDCT, 0 otherwise");
   return FDTD_OK;
 }
 
@@ -607,17 +625,23 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
 extern "C" int fdtd_workspace_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec,
                                     size_t* bytes) {
   if (!h || !bytes) return FDTD_EINVAL;
-  if (rec && (rec->k < 1 || rec->dtype < 0 || rec->dtype >= kTapeDtypes)) return FDTD_EINVAL;
+  if (rec && (rec->k < 1 || !valid_dtype(rec->dtype) || !coeffs_ok(rec))) return FDTD_EINVAL;
   *bytes = layout_of(h, rec).total;
   return FDTD_OK;
 }
 
 extern "C" int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes) {
-  if (!h || !bytes || !rec || rec->k < 1 || rec->dtype < 0 || rec->dtype >= kTapeDtypes)
+  if (!h || !bytes || !rec || rec->k < 1 || !valid_dtype(rec->dtype) || !coeffs_ok(rec))
     return FDTD_EINVAL;
   size_t J = n_samples(h->N, rec->k);
-  size_t b = J * (size_t)sample_elems(h) * code_bytes(rec->dtype);
-  if (rec->scaled) b += J * 6 * sizeof(float);
+  size_t b;
+  if (rec->dtype == kTapeBdct) {   // codes and per-block scales, unpadded
+    const BdctLayout bl = bdct_layout(h->faces, bdct_coeffs(rec));
+    b = J * (size_t)bl.bstart[6] * (bl.K + sizeof(float));
+  } else {
+    b = J * (size_t)sample_elems(h) * code_bytes(rec->dtype);
+    if (rec->scaled) b += J * 6 * sizeof(float);
+  }
   *bytes = b;
   return FDTD_OK;
 }
@@ -954,7 +978,15 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   a.psiA = (float*)(h->ws + L.psiF[0]);
   char* tape = h->ws + L.tape;
   float* scales = (float*)(h->ws + L.scales);
-  int eb = code_bytes(rec->dtype);
+  const bool bdct = rec->dtype == kTapeBdct;
+  const int eb = bdct ? 1 : code_bytes(rec->dtype);
+  const BdctLayout bl = bdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
+  auto record = [&](const float* FH, const float* FE, int j) {
+    void* smp = tape + (size_t)j * L.stride * eb;
+    return bdct ? launch_record_bdct(FH, FE, a.g, h->faces, bl, smp, h->stream)
+                : launch_record(rec->dtype, rec->scaled, FH, FE, a.g, h->faces, smp,
+                                scales + (size_t)j * 6, h->stream);
+  };
   const Det det2 = det2_of(h);
   if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
     return e;
@@ -979,10 +1011,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       ++nl;
       if (rec_now) {
         if ((e = smp.before(FDTD_K_RECORD))) return e;
-        if ((e = launch_record(rec->dtype, rec->scaled, Fo, a.F, a.g, h->faces,
-                               tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
-                               h->stream)))
-          return e;
+        if ((e = record(Fo, a.F, j))) return e;
         if ((e = smp.after(FDTD_K_RECORD))) return e;
         ++nl;
       }
@@ -1003,10 +1032,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     ++nl;
     if (rec_now) {
       if ((e = smp.before(FDTD_K_RECORD))) return e;
-      if ((e = launch_record(rec->dtype, rec->scaled, a.F, a.F, a.g, h->faces,
-                             tape + (size_t)j * L.stride * eb, scales + (size_t)j * 6,
-                             h->stream)))
-        return e;
+      if ((e = record(a.F, a.F, j))) return e;
       if ((e = smp.after(FDTD_K_RECORD))) return e;
       ++nl;
     }
@@ -1061,15 +1087,21 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                      L.plL, &lrmaps[b])))
       return e;
   }
+  const BdctLayout bl =
+      rec->dtype == kTapeBdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
   Sampler smp(h, 1);
   for (int n = h->N - 1; n >= 0; --n) {
     Interp ip;
     interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
     if ((e = smp.before(FDTD_K_RESTORE))) return e;
-    if ((e = launch_restore_seed(rec->dtype, a.F, a.L, a.g, h->faces, h->ws + L.tape, L.stride,
-                                 (const float*)(h->ws + L.scales), ip, det, det2,
-                                 (const double*)(h->ws + L.seeds), h->stream)))
+    if ((e = rec->dtype == kTapeBdct
+                 ? launch_restore_seed_bdct(a.F, a.L, a.g, h->faces, bl, h->ws + L.tape, L.stride,
+                                            ip, det, det2, (const double*)(h->ws + L.seeds),
+                                            h->stream)
+                 : launch_restore_seed(rec->dtype, a.F, a.L, a.g, h->faces, h->ws + L.tape,
+                                       L.stride, (const float*)(h->ws + L.scales), ip, det, det2,
+                                       (const double*)(h->ws + L.seeds), h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_RESTORE))) return e;
     a.jn = h->wave[n];
@@ -1165,6 +1197,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   h->have_forward = false;
   CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, h->stream));
   Geo g = geo_of(h);
+  if (rec->dtype == kTapeBdct) CK(h, bdct_ensure_basis());
   CK(h, launch_prep(d_eps, (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), h->stream));
   int nl = 0;
   nvtxRangePushA("fdtd forward loop");   // host-side range (enqueue / graph launch)
@@ -1411,6 +1444,34 @@ extern "C" int fdtd_encode(int dtype, int scaled, const float* d_in, size_t n, v
   if (dtype < 0 || dtype >= kTapeDtypes || !d_in || !d_code || !d_scale) return FDTD_EINVAL;
   if (scaled && dtype < 2) return FDTD_EINVAL;
   cudaError_t e = launch_encode(dtype, scaled, d_in, n, d_code, d_scale, (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
+}
+
+extern "C" int fdtd_bdct_encode(const float* d_in, int nu, int nv, int coeffs,
+                                signed char* d_codes, float* d_scales, void* cuda_stream) {
+  if (!d_in || !d_codes || !d_scales || nu < 1 || nv < 1 || coeffs < 1 || coeffs > 64)
+    return FDTD_EINVAL;
+  cudaError_t e = bdct_ensure_basis();
+  if (e == cudaSuccess)
+    e = launch_bdct_encode(d_in, nu, nv, coeffs, d_codes, d_scales, (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
+}
+
+extern "C" int fdtd_bdct_basis(float* out) {
+  if (!out) return FDTD_EINVAL;
+  bdct_basis_host(out);
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_bdct_decode(const signed char* d_codes, const float* d_scales, int nu, int nv,
+                                int coeffs, float* d_out, void* cuda_stream) {
+  if (!d_codes || !d_scales || !d_out || nu < 1 || nv < 1 || coeffs < 1 || coeffs > 64)
+    return FDTD_EINVAL;
+  cudaError_t e = bdct_ensure_basis();
+  if (e == cudaSuccess)
+    e = launch_bdct_decode(d_codes, d_scales, nu, nv, coeffs, d_out, (cudaStream_t)cuda_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA;
 }

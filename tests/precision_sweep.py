@@ -16,6 +16,10 @@ forward does not depend on the tape).
 type unscaled (float32, float16, bfloat16 and the five 8-bit formats
 e4m3b11fnuz, e5m2fnuz, e4m3fnuz, e4m3 (IEEE-style) and e3m4) for k in
 {1, 2, 4, 8, 16, 32} with linear interpolation.
+
+--block-codec runs the block-transform tape (beyond the paper: 8 x 8 DCT
+blocks keeping K = 6, 10, 15 or 21 coefficients, int8 codes) for k in
+{1, 4, 8, 16} with cubic interpolation, beside FP32 and scaled E4M3.
 """
 from __future__ import annotations
 
@@ -35,6 +39,8 @@ KS = [1, 2, 4, 8, 16]
 INTERPS = ["linear", "cubic"]
 PAPER_DTYPES = ["f32", "f16", "bf16", "e4m3b11fnuz", "e5m2fnuz", "e4m3fnuz", "e4m3ieee", "e3m4"]
 PAPER_KS = [1, 2, 4, 8, 16, 32]
+BDCT_DTYPES = ["f32", "e4m3", "bdct6", "bdct10", "bdct15", "bdct21"]
+BDCT_KS = [1, 4, 8, 16]
 
 
 def rel(a, b):
@@ -75,7 +81,9 @@ def run_seed(seed: int, n_steps: int, dtypes=DTYPES, ks=KS, interps=INTERPS, sca
     for dt in dtypes:
         for k in ks:
             for interp in interps:
-                if dt == "f32" and k == 1 and interp == "cubic":
+                if dt == "f32" and k == 1 and interp == "cubic" and base is None:
+                    interp = "linear"   # the FP32 k = 1 baseline comes first
+                elif dt == "f32" and k == 1 and interp == "cubic":
                     continue
                 rec = A.record_cfg(dt, k, interp, scaled=scaled)
                 L = sim.forward(eps, rec)
@@ -119,6 +127,7 @@ def main():
     p.add_argument("--md", default=None)
     p.add_argument("--paper-formats", action="store_true")
     p.add_argument("--no-oracle", action="store_true")
+    p.add_argument("--block-codec", action="store_true")
     a = p.parse_args()
     from paper_2603_24027_gb300 import build as B
     from oracle import build as OB
@@ -129,6 +138,9 @@ def main():
         if a.paper_formats:
             r, t = run_seed(s, a.steps, dtypes=PAPER_DTYPES, ks=PAPER_KS, interps=["linear"],
                             scaled=False, oracle=not a.no_oracle)
+        elif a.block_codec:
+            r, t = run_seed(s, a.steps, dtypes=BDCT_DTYPES, ks=BDCT_KS, interps=["cubic"],
+                            oracle=not a.no_oracle)
         else:
             r, t = run_seed(s, a.steps, oracle=not a.no_oracle)
         base = r[0]

@@ -213,3 +213,34 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     b5 = sim.workspace_bytes(rec)
     compact = al(4 * (16 * 21 * 19 + 72 * 21 * 19 + 72 * 21 * 12) * 4)
     assert b4 - b5 == 3 * (full(70, 21, 19) - compact)
+
+
+def test_bdct_basis_and_tape_sizes(capi, fdtd):
+    """The block-transform codec: the library's basis table equals the
+    oracle's bit for bit (both computed on the host from the DCT-II
+    definition); tape bytes = samples x blocks x (K codes + 4-byte scale),
+    blocks = 2 components x ceil(nu/8) ceil(nv/8) per face; coeffs is
+    validated (1..64 for BDCT, 0 = 10; 0 for the other types)."""
+    import ctypes as C
+    from oracle import oracle as O
+    beta = np.zeros(64 * 64, np.float32)
+    assert capi.lib().fdtd_bdct_basis(C.c_void_p(beta.ctypes.data)) == capi.FDTD_OK
+    np.testing.assert_array_equal(beta.reshape(64, 8, 8), O.bdct_basis())
+    w = I.waveguide_mid()                            # faces 176x76 (x, y) and 176x176 (z)
+    sim = fdtd.Simulation(w)
+    blocks = 2 * 2 * (22 * 10 + 22 * 10 + 22 * 22)
+    assert blocks == 3696
+    for K, name in ((10, "bdct"), (6, "bdct6"), (21, "bdct21")):
+        rec = capi.record_cfg(name, 8)
+        assert rec.coeffs == K
+        assert sim.tape_bytes(rec) == 250 * blocks * (K + 4)
+    f32 = sim.tape_bytes(capi.record_cfg("f32", 1))
+    assert f32 / sim.tape_bytes(capi.record_cfg("bdct10", 1)) > 17.8
+    lib = capi.lib()
+    n = C.c_size_t()
+    for dt, k, coeffs in ((9, 1, 65), (9, 1, -1), (1, 1, 10)):
+        rec = capi.RecordCfg(dt, k, 0, 0, coeffs)
+        assert lib.fdtd_workspace_bytes(sim.h, C.byref(rec), C.byref(n)) == capi.FDTD_EINVAL
+    rec = capi.RecordCfg(9, 1, 0, 1, 10)           # no per-face scale for BDCT
+    out = C.c_double()
+    assert lib.fdtd_forward(sim.h, C.c_void_p(1), C.byref(rec), C.byref(out)) == capi.FDTD_EINVAL

@@ -352,6 +352,53 @@ def test_paper_fp8_tape_matches_oracle_method(F, A, fmt, k):
     assert cos(r["g"], g) > 0.999
 
 
+@pytest.mark.parametrize("K", [1, 6, 10, 21, 64])
+def test_bdct_codec_is_bit_exact_against_oracle(F, A, K):
+    """Block-transform codec on raw planes (ragged sizes, values over many
+    decades, all-zero and constant blocks): codes, scales and decoded values
+    equal the oracle's float32 implementation bit for bit."""
+    import ctypes as C
+    rng = np.random.default_rng(K)
+    for nv, nu in [(1, 1), (8, 8), (5, 11), (76, 176), (129, 37)]:
+        x = (rng.standard_normal((nv, nu)) * np.exp(rng.uniform(-20, 3, (nv, nu))))
+        x = x.astype(np.float32)
+        if nu >= 16 and nv >= 16:
+            x[:8, :8] = 0.0                    # an all-zero block
+            x[8:16, 8:16] = 0.25               # a constant block
+        nb = ((nu + 7) // 8) * ((nv + 7) // 8)
+        xd = torch.from_numpy(x).cuda()
+        codes = torch.zeros((nb, K), dtype=torch.int8, device="cuda")
+        scales = torch.zeros(nb, dtype=torch.float32, device="cuda")
+        out = torch.zeros((nv, nu), dtype=torch.float32, device="cuda")
+        A.check(A.lib().fdtd_bdct_encode(C.c_void_p(xd.data_ptr()), nu, nv, K,
+                                         C.c_void_p(codes.data_ptr()),
+                                         C.c_void_p(scales.data_ptr()), None))
+        A.check(A.lib().fdtd_bdct_decode(C.c_void_p(codes.data_ptr()),
+                                         C.c_void_p(scales.data_ptr()), nu, nv, K,
+                                         C.c_void_p(out.data_ptr()), None))
+        oc, osc = O.bdct_encode(x, K)
+        np.testing.assert_array_equal(codes.cpu().numpy(), oc)
+        np.testing.assert_array_equal(scales.cpu().numpy(), osc)
+        np.testing.assert_array_equal(out.cpu().numpy(), O.bdct_decode(oc, osc, nu, nv))
+
+
+@pytest.mark.parametrize("name,k,interp", [("bdct10", 2, "cubic"), ("bdct21", 1, "linear"),
+                                           ("bdct6", 4, "cubic")])
+def test_bdct_tape_matches_oracle_method(F, A, name, k, interp):
+    """Gradient with the block-transform tape against the oracle's run of the
+    method with the same codec (its quantisation decisions are taken on the
+    oracle's own FP64 fields rounded to float32, so a few codes may differ
+    by one step: soft parity), for the default and the one-cell kernels."""
+    w = I.ragged_box(n_steps=120)
+    rec = A.record_cfg(name, k, interp)
+    L, g = O.reverse(w, name, k=k, interp=interp)
+    for kernel in (5, 0):
+        r = gpu_run(F, A, w, rec=rec, options={A.OPT_KERNEL: kernel})
+        assert r["L"] == pytest.approx(L, rel=1e-5)
+        assert rel(r["g"], g) < 2e-2
+        assert cos(r["g"], g) > 0.999
+
+
 def test_autograd_function_against_central_differences(F, A):
     """FDTDGrad's backward vs central differences of its own forward (FP32
     fields, FP64 objective).  Along the gradient direction the derivative is
