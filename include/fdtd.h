@@ -241,9 +241,16 @@ enum {
                                    next plane's boxes; 0 (default) = off */
   FDTD_OPT_TILE_X = 9,          /* kernel 5 with tile height 8 and 2 or 3 stages: tile width
                                    32 (default) or 40 cells */
-  FDTD_OPT_COMPACT_AUX = 10     /* kernels 5 and 6: 1 (default) = their CPML auxiliaries are
+  FDTD_OPT_COMPACT_AUX = 10,    /* kernels 5 and 6: 1 (default) = their CPML auxiliaries are
                                    stored for the slab cells only (per axis, where the grid
                                    is long enough); 0 = full-grid arrays */
+  FDTD_OPT_EXACT_REVERSAL = 11  /* kernel 5: q in 8..30 rounds every field increment of the
+                                   leapfrog to a multiple of 2^-q, so that the fields stay on
+                                   that grid and, while |E|, |Ht| < 2^(24-q), every float32
+                                   update is exact and the time-reversed interior retraces
+                                   the forward run bit for bit (with an FP32 k = 1 tape);
+                                   0 (default) = plain float32 increments.  Other kernels
+                                   with q != 0: FDTD_EINVAL at fdtd_forward */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -40,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x, compact;
+      tile_x, compact, exact;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -85,7 +85,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_compact;
+      opt_prefetch, opt_tile_x, opt_compact, opt_exact;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -580,6 +580,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_prefetch = 0;
   h->opt_tile_x = 32;
   h->opt_compact = 1;
+  h->opt_exact = 0;
   h->maps_ws = nullptr;
   h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
@@ -699,6 +700,12 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if ((value ? 1 : 0) != h->opt_compact) h->have_forward = false;   // layout changes
       h->opt_compact = value ? 1 : 0;
       break;
+    case FDTD_OPT_EXACT_REVERSAL:
+      if (value != 0 && (value < 8 || value > 30))
+        return fail(h, FDTD_EINVAL, "exact reversal: q must be 0 or 8..30");
+      if (value != h->opt_exact) h->have_forward = false;   // the backward must match it
+      h->opt_exact = value;
+      break;
     default: return fail(h, FDTD_EINVAL, "unknown option");
   }
   return FDTD_OK;
@@ -718,6 +725,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
     case FDTD_OPT_TILE_X: *value = h->opt_tile_x; break;
     case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
+    case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -836,6 +844,9 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.pdl = h->opt_pdl;
   a.prefetch = h->opt_prefetch;
   a.tile_x = lag_tile_x(h);
+  a.xq = h->opt_exact;
+  a.xs = h->opt_exact ? ldexpf(1.0f, h->opt_exact) : 1.0f;
+  a.xi = h->opt_exact ? ldexpf(1.0f, -h->opt_exact) : 1.0f;
   a.zchunk = h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
   a.err = (unsigned*)(h->ws + L.err);
   return a;
@@ -1160,6 +1171,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.prefetch = h->opt_prefetch;
   key.tile_x = h->opt_tile_x;
   key.compact = h->opt_compact;
+  key.exact = h->opt_exact;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1189,6 +1201,8 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   int rc = check_rec(h, rec);
   if (rc) return rc;
   if (!d_eps) return fail(h, FDTD_EINVAL, "eps is NULL");
+  if (h->opt_exact && h->opt_kernel != 5)
+    return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 only");
   Layout L = layout_of(h, rec);
   if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
   if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this record config");

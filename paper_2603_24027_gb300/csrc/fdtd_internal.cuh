@@ -100,6 +100,15 @@ struct PsiLayout {
   long long total;  // elements of the set
 };
 
+// Exact reversal: the field increment d rounded to the grid of multiples of
+// 2^-xq.  Fields that start on the grid (zero) and move by grid increments
+// stay on it, and while |field| < 2^(24-xq) the float32 sum of two grid
+// values is exact, so the reverse step (field - the same increment) restores
+// the previous value bit for bit.  Scaling by a power of two is exact.
+__device__ __forceinline__ float grid_inc(float d, int xq, float xs, float xi) {
+  return xq ? __fmul_rn(rintf(__fmul_rn(d, xs)), xi) : d;
+}
+
 __device__ __forceinline__ int psi_map(const PsiAxis& A, int c) {
   return c >= A.hs ? c - A.shift : c;
 }
@@ -237,6 +246,8 @@ struct StepArgs {
   int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
   int tile_x;      // two-cells-per-thread kernels: tile width (32 or 40 cells)
   PsiLayout pl;    // layout of the auxiliary sets the two-cells-per-thread kernels use
+  int xq;          // exact reversal: increments rounded to multiples of 2^-xq (0 = off)
+  float xs, xi;    // 2^xq, 2^-xq
   unsigned* err;   // device error word (ERR_*)
 };
 

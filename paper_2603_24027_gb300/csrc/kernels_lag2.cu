@@ -230,9 +230,9 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const float cx = c_t0[c] - t1[c], cy = t2[c] - c_t3[c], cz = c_t4[c] - c_t5[c];
-          hx[c] = __fsub_rn(c_hx[c], __fmul_rn(g.S, cx));
-          hy[c] = __fsub_rn(c_hy[c], __fmul_rn(g.S, cy));
-          hz[c] = __fsub_rn(c_hz[c], __fmul_rn(g.S, cz));
+          hx[c] = __fsub_rn(c_hx[c], grid_inc(__fmul_rn(g.S, cx), a.xq, a.xs, a.xi));
+          hy[c] = __fsub_rn(c_hy[c], grid_inc(__fmul_rn(g.S, cy), a.xq, a.xs, a.xi));
+          hz[c] = __fsub_rn(c_hz[c], grid_inc(__fmul_rn(g.S, cz), a.xq, a.xs, a.xi));
         }
         st2(Hx, q, hx[0], hx[1], true, v1);
         st2(Hy, q, hy[0], hy[1], true, v1);
@@ -470,9 +470,9 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
         float ex[2], ey[2], ez[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          ex[c] = __fadd_rn(eo0[c], __fmul_rn(cbv[c], c0[c]));
-          ey[c] = __fadd_rn(eo1[c], __fmul_rn(cbv[c], c1[c]));
-          ez[c] = __fadd_rn(eo2[c], __fmul_rn(cbv[c], c2[c]));
+          ex[c] = __fadd_rn(eo0[c], grid_inc(__fmul_rn(cbv[c], c0[c]), a.xq, a.xs, a.xi));
+          ey[c] = __fadd_rn(eo1[c], grid_inc(__fmul_rn(cbv[c], c1[c]), a.xq, a.xs, a.xi));
+          ez[c] = __fadd_rn(eo2[c], grid_inc(__fmul_rn(cbv[c], c2[c]), a.xq, a.xs, a.xi));
         }
         st2(Ex, q, ex[0], ex[1], true, v1);
         st2(Ey, q, ey[0], ey[1], true, v1);
@@ -650,12 +650,15 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
           }
           const float* Eo = reinterpret_cast<const float*>(st + Y::E);
           const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
-          st2(Ex, q, __fsub_rn(e0.x, __fmul_rn(cbv[0], c0[0])), __fsub_rn(e0.y, __fmul_rn(cbv[1], c0[1])),
+          auto inc = [&](float cbc, float cc) {
+            return grid_inc(__fmul_rn(cbc, cc), a.xq, a.xs, a.xi);
+          };
+          st2(Ex, q, __fsub_rn(e0.x, inc(cbv[0], c0[0])), __fsub_rn(e0.y, inc(cbv[1], c0[1])),
               xyin0, xyin1);
-          st2(Ex + nc, q, __fsub_rn(e1.x, __fmul_rn(cbv[0], c1[0])),
-              __fsub_rn(e1.y, __fmul_rn(cbv[1], c1[1])), xyin0, xyin1);
-          st2(Ex + 2 * nc, q, __fsub_rn(e2.x, __fmul_rn(cbv[0], c2[0])),
-              __fsub_rn(e2.y, __fmul_rn(cbv[1], c2[1])), xyin0, xyin1);
+          st2(Ex + nc, q, __fsub_rn(e1.x, inc(cbv[0], c1[0])), __fsub_rn(e1.y, inc(cbv[1], c1[1])),
+              xyin0, xyin1);
+          st2(Ex + 2 * nc, q, __fsub_rn(e2.x, inc(cbv[0], c2[0])),
+              __fsub_rn(e2.y, inc(cbv[1], c2[1])), xyin0, xyin1);
           if (dy_ && k >= a.dlo[2] && k < a.dhi[2]) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -911,12 +914,13 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
         const float d1[2] = {ey.x - c_ey[0], ey.y - c_ey[1]};
         const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
         const long long qm = q - g.plane;
-        st2(Hx, qm, __fadd_rn(c_hx[0], __fmul_rn(S_, c_d0[0] - d1[0])),
-            __fadd_rn(c_hx[1], __fmul_rn(S_, c_d0[1] - d1[1])), c_pr0, c_pr1);
-        st2(Hx + nc, qm, __fadd_rn(c_hy[0], __fmul_rn(S_, d2[0] - c_d3[0])),
-            __fadd_rn(c_hy[1], __fmul_rn(S_, d2[1] - c_d3[1])), c_pr0, c_pr1);
-        st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], __fmul_rn(S_, c_d4[0] - c_d5[0])),
-            __fadd_rn(c_hz[1], __fmul_rn(S_, c_d4[1] - c_d5[1])), c_pr0, c_pr1);
+        auto inc = [&](float cc) { return grid_inc(__fmul_rn(S_, cc), a.xq, a.xs, a.xi); };
+        st2(Hx, qm, __fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
+            __fadd_rn(c_hx[1], inc(c_d0[1] - d1[1])), c_pr0, c_pr1);
+        st2(Hx + nc, qm, __fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
+            __fadd_rn(c_hy[1], inc(d2[1] - c_d3[1])), c_pr0, c_pr1);
+        st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], inc(c_d4[0] - c_d5[0])),
+            __fadd_rn(c_hz[1], inc(c_d4[1] - c_d5[1])), c_pr0, c_pr1);
       }
       const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
       if (p >= k0 && p < k1) {

@@ -244,3 +244,21 @@ def test_bdct_basis_and_tape_sizes(capi, fdtd):
     rec = capi.RecordCfg(9, 1, 0, 1, 10)           # no per-face scale for BDCT
     out = C.c_double()
     assert lib.fdtd_forward(sim.h, C.c_void_p(1), C.byref(rec), C.byref(out)) == capi.FDTD_EINVAL
+
+
+def test_exact_reversal_option_is_validated(capi, fdtd):
+    """Grid exponent q: 0 (off) or 8..30; only kernel 5 rounds its increments,
+    so a forward with another kernel and q != 0 is refused before any device
+    work."""
+    import ctypes as C
+    sim = fdtd.Simulation(I.fd_cube())
+    lib = capi.lib()
+    for q in (7, 31, -1):
+        assert lib.fdtd_set_option(sim.h, capi.OPT_EXACT_REVERSAL, q) == capi.FDTD_EINVAL
+    assert lib.fdtd_set_option(sim.h, capi.OPT_EXACT_REVERSAL, 22) == capi.FDTD_OK
+    v = C.c_int()
+    assert lib.fdtd_get_option(sim.h, capi.OPT_EXACT_REVERSAL, C.byref(v)) == 0 and v.value == 22
+    assert lib.fdtd_set_option(sim.h, capi.OPT_KERNEL, 0) == capi.FDTD_OK
+    out = C.c_double()
+    rc = lib.fdtd_forward(sim.h, C.c_void_p(1), C.byref(capi.record_cfg()), C.byref(out))
+    assert rc == capi.FDTD_EINVAL
