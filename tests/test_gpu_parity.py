@@ -399,6 +399,22 @@ def test_bdct_tape_matches_oracle_method(F, A, name, k, interp):
         assert cos(r["g"], g) > 0.999
 
 
+def test_bdct_coefficient_counts_are_not_mixed_up_by_cached_graphs(F, A):
+    """One handle running the block codec with K = 6, then K = 21 (captured
+    time-loop graphs are keyed by K too): the K = 21 results equal a fresh
+    handle's bit for bit and differ from K = 6."""
+    w = I.ragged_box(n_steps=60)
+    eps = torch.from_numpy(w.eps).cuda()
+    sim = F.Simulation(w)
+    out = {}
+    for name in ("bdct6", "bdct21"):
+        sim.forward(eps, A.record_cfg(name, 2, "cubic"))
+        out[name] = sim.backward().cpu().numpy()
+    fresh = gpu_run(F, A, w, rec=A.record_cfg("bdct21", 2, "cubic"))
+    np.testing.assert_array_equal(out["bdct21"], fresh["g"])
+    assert not np.array_equal(out["bdct6"], out["bdct21"])
+
+
 def test_autograd_function_against_central_differences(F, A):
     """FDTDGrad's backward vs central differences of its own forward (FP32
     fields, FP64 objective).  Along the gradient direction the derivative is
