@@ -250,7 +250,8 @@ enum {
                                    update is exact and the time-reversed interior retraces
                                    the forward run bit for bit (with an FP32 k = 1 tape);
                                    0 (default) = plain float32 increments.  Other kernels
-                                   with q != 0: FDTD_EINVAL at fdtd_forward */
+                                   or tile shapes than kernel 5's defaults (32 x 8 tiles,
+                                   2 stages) with q != 0: FDTD_EINVAL at fdtd_forward */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -1202,8 +1202,9 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   int rc = check_rec(h, rec);
   if (rc) return rc;
   if (!d_eps) return fail(h, FDTD_EINVAL, "eps is NULL");
-  if (h->opt_exact && h->opt_kernel != 5)
-    return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 only");
+  if (h->opt_exact && (h->opt_kernel != 5 || h->opt_tile_y != 8 || h->opt_stages != 2 ||
+                       lag_tile_x(h) != 32))
+    return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 with its default tiles");
   Layout L = layout_of(h, rec);
   if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
   if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this record config");

@@ -99,6 +99,13 @@ __device__ __forceinline__ void psi_box_starts(const PsiLayout& pl, int x0, int 
   *qy0 = y0 + TY + 1 > Yy.hs ? y0 - Yy.shift : y0;
 }
 
+// A field increment of the leapfrog; EX (exact reversal) rounds it to the
+// grid of multiples of 2^-xq (see grid_inc), compiled in only where used.
+template <bool EX>
+__device__ __forceinline__ float inc_of(float d, const StepArgs& a) {
+  return EX ? grid_inc(d, 1, a.xs, a.xi) : d;
+}
+
 // Resident CTAs per SM the register allocation must allow for the default
 // 32 x 8 tiles with two stages: eight for the forward half-steps (what their
 // shared memory allows), five for the reverse phases (idem); other shapes
@@ -143,7 +150,7 @@ __device__ void ring_abort(uint64_t* bars, int stg, uint32_t par, int p, int p1,
 using namespace lag2;
 
 // =================================================== forward H half-step ===
-template <int TY, int S, int TW>
+template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
 k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -230,9 +237,9 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const float cx = c_t0[c] - t1[c], cy = t2[c] - c_t3[c], cz = c_t4[c] - c_t5[c];
-          hx[c] = __fsub_rn(c_hx[c], grid_inc(__fmul_rn(g.S, cx), a.xq, a.xs, a.xi));
-          hy[c] = __fsub_rn(c_hy[c], grid_inc(__fmul_rn(g.S, cy), a.xq, a.xs, a.xi));
-          hz[c] = __fsub_rn(c_hz[c], grid_inc(__fmul_rn(g.S, cz), a.xq, a.xs, a.xi));
+          hx[c] = __fsub_rn(c_hx[c], inc_of<EX>(__fmul_rn(g.S, cx), a));
+          hy[c] = __fsub_rn(c_hy[c], inc_of<EX>(__fmul_rn(g.S, cy), a));
+          hz[c] = __fsub_rn(c_hz[c], inc_of<EX>(__fmul_rn(g.S, cz), a));
         }
         st2(Hx, q, hx[0], hx[1], true, v1);
         st2(Hy, q, hy[0], hy[1], true, v1);
@@ -306,7 +313,7 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // =================================================== forward E half-step ===
-template <int TY, int S, int TW>
+template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
 k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -470,9 +477,9 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
         float ex[2], ey[2], ez[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          ex[c] = __fadd_rn(eo0[c], grid_inc(__fmul_rn(cbv[c], c0[c]), a.xq, a.xs, a.xi));
-          ey[c] = __fadd_rn(eo1[c], grid_inc(__fmul_rn(cbv[c], c1[c]), a.xq, a.xs, a.xi));
-          ez[c] = __fadd_rn(eo2[c], grid_inc(__fmul_rn(cbv[c], c2[c]), a.xq, a.xs, a.xi));
+          ex[c] = __fadd_rn(eo0[c], inc_of<EX>(__fmul_rn(cbv[c], c0[c]), a));
+          ey[c] = __fadd_rn(eo1[c], inc_of<EX>(__fmul_rn(cbv[c], c1[c]), a));
+          ez[c] = __fadd_rn(eo2[c], inc_of<EX>(__fmul_rn(cbv[c], c2[c]), a));
         }
         st2(Ex, q, ex[0], ex[1], true, v1);
         st2(Ey, q, ey[0], ey[1], true, v1);
@@ -519,7 +526,7 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // ======================================== reverse E phase (+ adjoint H) ===
-template <int TY, int S, int TW>
+template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
 k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -651,7 +658,7 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
           const float* Eo = reinterpret_cast<const float*>(st + Y::E);
           const float2 e0 = ld2(Eo, ob), e1 = ld2(Eo + B::OP, ob), e2 = ld2(Eo + 2 * B::OP, ob);
           auto inc = [&](float cbc, float cc) {
-            return grid_inc(__fmul_rn(cbc, cc), a.xq, a.xs, a.xi);
+            return inc_of<EX>(__fmul_rn(cbc, cc), a);
           };
           st2(Ex, q, __fsub_rn(e0.x, inc(cbv[0], c0[0])), __fsub_rn(e0.y, inc(cbv[1], c0[1])),
               xyin0, xyin1);
@@ -829,7 +836,7 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // ======================================== reverse H phase (+ adjoint E) ===
-template <int TY, int S, int TW>
+template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
 k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -914,7 +921,7 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
         const float d1[2] = {ey.x - c_ey[0], ey.y - c_ey[1]};
         const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
         const long long qm = q - g.plane;
-        auto inc = [&](float cc) { return grid_inc(__fmul_rn(S_, cc), a.xq, a.xs, a.xi); };
+        auto inc = [&](float cc) { return inc_of<EX>(__fmul_rn(S_, cc), a); };
         st2(Hx, qm, __fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
             __fadd_rn(c_hx[1], inc(c_d0[1] - d1[1])), c_pr0, c_pr1);
         st2(Hx + nc, qm, __fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
@@ -1106,26 +1113,30 @@ static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStr
   return cudaLaunchKernelEx(&cfg, kernel, m, a);
 }
 
-template <int TY, int S, int TW = 32>
+template <int TY, int S, int TW = 32, bool EX = false>
 static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   static_assert((TW / 2 * TY) % 32 == 0, "a CTA is a whole number of warps");
   dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
   dim3 block(TW / 2, TY);
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S, TW>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
-    case 1: return launch_ex(k_l2fwd_e<TY, S, TW>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
-    case 2: return launch_ex(k_l2rev_e<TY, S, TW>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
-    case 3: return launch_ex(k_l2rev_h<TY, S, TW>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }
   return cudaErrorInvalidValue;
 }
 
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
-// A warp covers two tile rows, so tile heights start at 2 (the caller runs
+// Exact reversal (a.xq != 0) runs 32 x 8 tiles with two stages.  A warp covers two tile rows, so tile heights start at 2 (the caller runs
 // a requested height of 1 as 2).  Stage counts 2 and 4 are built for tile
 // heights 2, 4 and 8; height 16 runs with 3.
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   const int S = a.stages;
+  if (a.xq) {   // exact reversal: built for the default shape only
+    if (a.tile_y != 8 || S != 2 || a.tile_x != 32) return cudaErrorInvalidValue;
+    return launch_lag2_t<8, 2, 32, true>(which, m, a, s);
+  }
   if (a.tile_x == 40) {   // 40-wide tiles: tile height 8 only (whole warps), 2 or 3 stages
     if (a.tile_y != 8) return cudaErrorInvalidValue;
     return S == 3 ? launch_lag2_t<8, 3, 40>(which, m, a, s) : launch_lag2_t<8, 2, 40>(which, m, a, s);
