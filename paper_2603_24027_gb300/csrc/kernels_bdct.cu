@@ -1,12 +1,12 @@
 // kernels_bdct.cu -- block-transform tape codec (tape type 9): record,
 // restore and raw-plane entry points.  The codec is defined in bdct.cuh.
 //
-// Record: one thread per (face, component, 8 x 8 block): the block's 64
-// values are loaded once (x faces are strided in memory, but a sample is
-// recorded only every k steps and covers the surface only), the K kept
-// coefficients are formed twice (once for the block's absmax, once to
-// quantise; both passes evaluate the same fmaf chain, so they agree), and
-// the codes and the scale are written.  Restore: one thread per recorded
+// Record: one warp per (face, component, 8 x 8 block): the lanes stage the
+// block's 64 values in shared memory (x faces are strided in memory, but a
+// sample is recorded only every k steps and covers the surface only), lane i
+// forms coefficient i (and i + 32) as the codec's sequential fmaf chain over
+// the 64 cells, the block's absmax is a warp max (exact in any order), and
+// each lane quantises its own coefficients.  Restore: one thread per recorded
 // value, decoding its block's K codes for each of the (up to four) time
 // samples of the interpolation; the basis values of a warp's 32 cells lie in
 // one 32-byte sector per coefficient.
@@ -23,6 +23,7 @@ static constexpr int BDCT_THREADS = 256;
 static constexpr float kBdctMinScale = 1.17549435e-38f;   // 2^-126
 
 __device__ float g_bdct_beta[64 * 64];
+__device__ float g_bdct_beta_t[64 * 64];   // transposed: [cell][coefficient]
 
 // ------------------------------------------------------------ host side ---
 void bdct_order_host(int i, int* u, int* v) {
@@ -80,36 +81,48 @@ cudaError_t bdct_ensure_basis() {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return cudaSuccess;
-  float beta[64 * 64];
+  float beta[64 * 64], beta_t[64 * 64];
   bdct_basis_host(beta);
+  for (int i = 0; i < 64; ++i)
+    for (int t = 0; t < 64; ++t) beta_t[t * 64 + i] = beta[i * 64 + t];
   if ((e = cudaMemcpyToSymbol(g_bdct_beta, beta, sizeof beta))) return e;
+  if ((e = cudaMemcpyToSymbol(g_bdct_beta_t, beta_t, sizeof beta_t))) return e;
   done[dev] = true;
   return cudaSuccess;
 }
 
 // ---------------------------------------------------------- device side ---
-// Quantise the block X (64 values, row-major) to K codes and a scale.
-__device__ __forceinline__ void bdct_encode_block(const float (&X)[64], int K,
-                                                  signed char* __restrict__ codes,
-                                                  float* __restrict__ scale) {
+// Quantise one block with a warp: X (64 values, row-major, shared memory,
+// visible to the warp) -> K codes and the scale.  Lane i owns coefficients i
+// and i + 32.
+__device__ __forceinline__ void bdct_encode_block_warp(const float* X, int K, int lane,
+                                                       signed char* __restrict__ codes,
+                                                       float* __restrict__ scale) {
+  float c[2] = {0.f, 0.f};
   float amax = 0.f;
-  for (int i = 0; i < K; ++i) {
-    const float* __restrict__ b = g_bdct_beta + i * 64;
-    float c = 0.f;
 #pragma unroll
-    for (int t = 0; t < 64; ++t) c = __fmaf_rn(X[t], __ldg(b + t), c);
-    amax = fmaxf(amax, fabsf(c));
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    if (i < K) {
+      float acc = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < 64; ++t) acc = __fmaf_rn(X[t], __ldg(g_bdct_beta_t + t * 64 + i), acc);
+      c[h] = acc;
+      amax = fmaxf(amax, fabsf(acc));
+    }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const float s = amax > 0.f ? fmaxf(__fdiv_rn(amax, 127.0f), kBdctMinScale) : 1.0f;
-  for (int i = 0; i < K; ++i) {
-    const float* __restrict__ b = g_bdct_beta + i * 64;
-    float c = 0.f;
 #pragma unroll
-    for (int t = 0; t < 64; ++t) c = __fmaf_rn(X[t], __ldg(b + t), c);
-    const float q = fminf(fmaxf(rintf(__fdiv_rn(c, s)), -127.f), 127.f);
-    codes[i] = (signed char)(int)q;
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    if (i < K) {
+      const float q = fminf(fmaxf(rintf(__fdiv_rn(c[h], s)), -127.f), 127.f);
+      codes[i] = (signed char)(int)q;
+    }
   }
-  *scale = s;
+  if (lane == 0) *scale = s;
 }
 
 // Value of cell t (y * 8 + x) of a block from its K codes and scale.
@@ -121,13 +134,17 @@ __device__ __forceinline__ float bdct_decode_cell(const signed char* __restrict_
   return __fmul_rn(acc, s);
 }
 
+static constexpr int BDCT_WARPS = BDCT_THREADS / 32;
+
 __global__ void __launch_bounds__(BDCT_THREADS) k_record_bdct(const float* __restrict__ FH,
                                                               const float* __restrict__ FE, Geo g,
                                                               const __grid_constant__ Faces fc,
                                                               const __grid_constant__ BdctLayout bl,
                                                               unsigned char* __restrict__ sample) {
-  const int b = blockIdx.x * BDCT_THREADS + threadIdx.x;
-  if (b >= bl.bstart[6]) return;
+  __shared__ float Xs[BDCT_WARPS][64];
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+  const int b = blockIdx.x * BDCT_WARPS + wv;
+  if (b >= bl.bstart[6]) return;   // whole warps
   int f = 0;
 #pragma unroll
   for (int t = 1; t < 6; ++t) f += b >= bl.bstart[t];
@@ -138,27 +155,25 @@ __global__ void __launch_bounds__(BDCT_THREADS) k_record_bdct(const float* __res
   const int blk = rb - comp_t * nb;
   const int bv = blk / bl.nbu[f], bu = blk - bv * bl.nbu[f];
   const float* __restrict__ F = (f & 1) ? FE : FH;
-  float X[64];
 #pragma unroll
-  for (int y = 0; y < 8; ++y) {
-    const int v = min(bv * 8 + y, fd.nv - 1);
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-      const int u = min(bu * 8 + x, fd.nu - 1);
-      int comp;
-      const long long q = face_value_cell(g, fd, (comp_t * fd.nv + v) * fd.nu + u, &comp);
-      X[y * 8 + x] = F[comp * g.nc + q];
-    }
+  for (int h = 0; h < 2; ++h) {
+    const int t = lane + 32 * h, y = t >> 3, x = t & 7;
+    const int v = min(bv * 8 + y, fd.nv - 1), u = min(bu * 8 + x, fd.nu - 1);
+    int comp;
+    const long long q = face_value_cell(g, fd, (comp_t * fd.nv + v) * fd.nu + u, &comp);
+    Xs[wv][t] = F[comp * g.nc + q];
   }
-  bdct_encode_block(X, bl.K, reinterpret_cast<signed char*>(sample) + (long long)b * bl.K,
-                    reinterpret_cast<float*>(sample + bl.code_bytes) + b);
+  __syncwarp();
+  bdct_encode_block_warp(Xs[wv], bl.K, lane,
+                         reinterpret_cast<signed char*>(sample) + (long long)b * bl.K,
+                         reinterpret_cast<float*>(sample + bl.code_bytes) + b);
 }
 
 cudaError_t launch_record_bdct(const float* FH, const float* FE, Geo g, const Faces& fc,
                                const BdctLayout& bl, void* tape_sample, cudaStream_t s) {
   const int nb = bl.bstart[6];
   if (nb == 0) return cudaSuccess;
-  k_record_bdct<<<(nb + BDCT_THREADS - 1) / BDCT_THREADS, BDCT_THREADS, 0, s>>>(
+  k_record_bdct<<<(nb + BDCT_WARPS - 1) / BDCT_WARPS, BDCT_THREADS, 0, s>>>(
       FH, FE, g, fc, bl, reinterpret_cast<unsigned char*>(tape_sample));
   return cudaGetLastError();
 }
@@ -227,18 +242,20 @@ __global__ void __launch_bounds__(BDCT_THREADS) k_bdct_encode(const float* __res
                                                               int nv, int K,
                                                               signed char* __restrict__ codes,
                                                               float* __restrict__ scales) {
+  __shared__ float Xs[BDCT_WARPS][64];
+  const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
   const int nbu = (nu + 7) / 8, nbv = (nv + 7) / 8;
-  const int b = blockIdx.x * BDCT_THREADS + threadIdx.x;
-  if (b >= nbu * nbv) return;
+  const int b = blockIdx.x * BDCT_WARPS + wv;
+  if (b >= nbu * nbv) return;   // whole warps
   const int bv = b / nbu, bu = b - bv * nbu;
-  float X[64];
 #pragma unroll
-  for (int y = 0; y < 8; ++y) {
-    const int v = min(bv * 8 + y, nv - 1);
-#pragma unroll
-    for (int x = 0; x < 8; ++x) X[y * 8 + x] = in[(long long)v * nu + min(bu * 8 + x, nu - 1)];
+  for (int h = 0; h < 2; ++h) {
+    const int t = lane + 32 * h, y = t >> 3, x = t & 7;
+    const int v = min(bv * 8 + y, nv - 1), u = min(bu * 8 + x, nu - 1);
+    Xs[wv][t] = in[(long long)v * nu + u];
   }
-  bdct_encode_block(X, K, codes + (long long)b * K, scales + b);
+  __syncwarp();
+  bdct_encode_block_warp(Xs[wv], K, lane, codes + (long long)b * K, scales + b);
 }
 
 __global__ void __launch_bounds__(BDCT_THREADS) k_bdct_decode(const signed char* __restrict__ codes,
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(BDCT_THREADS) k_bdct_decode(const signed char*
 cudaError_t launch_bdct_encode(const float* in, int nu, int nv, int K, signed char* codes,
                                float* scales, cudaStream_t s) {
   const long long nb = (long long)((nu + 7) / 8) * ((nv + 7) / 8);
-  k_bdct_encode<<<(unsigned)((nb + BDCT_THREADS - 1) / BDCT_THREADS), BDCT_THREADS, 0, s>>>(
+  k_bdct_encode<<<(unsigned)((nb + BDCT_WARPS - 1) / BDCT_WARPS), BDCT_THREADS, 0, s>>>(
       in, nu, nv, K, codes, scales);
   return cudaGetLastError();
 }
