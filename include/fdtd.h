@@ -244,7 +244,7 @@ enum {
   FDTD_OPT_COMPACT_AUX = 10,    /* kernels 5 and 6: 1 (default) = their CPML auxiliaries are
                                    stored for the slab cells only (per axis, where the grid
                                    is long enough); 0 = full-grid arrays */
-  FDTD_OPT_EXACT_REVERSAL = 11  /* kernel 5: q in 8..30 rounds every field increment of the
+  FDTD_OPT_EXACT_REVERSAL = 11, /* kernel 5: q in 8..30 rounds every field increment of the
                                    leapfrog to a multiple of 2^-q, so that the fields stay on
                                    that grid and, while |E|, |Ht| < 2^(24-q), every float32
                                    update is exact and the time-reversed interior retraces
@@ -252,6 +252,9 @@ enum {
                                    0 (default) = plain float32 increments.  Other kernels
                                    or tile shapes than kernel 5's defaults (32 x 8 tiles,
                                    2 stages) with q != 0: FDTD_EINVAL at fdtd_forward */
+  FDTD_OPT_ZCHUNK_FWD = 12      /* kernel 5: z planes per CTA of the forward half-steps
+                                   (default 8; 0 = the whole column); FDTD_OPT_ZCHUNK then
+                                   sets the reverse phases (and every other kernel) */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -40,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs;
+      tile_x, compact, exact, coeffs, zchunk_fwd;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -85,7 +85,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_compact, opt_exact;
+      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -573,6 +573,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_kernel = 5;
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
+  h->opt_zchunk_fwd = 8;
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
@@ -700,6 +701,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if ((value ? 1 : 0) != h->opt_compact) h->have_forward = false;   // layout changes
       h->opt_compact = value ? 1 : 0;
       break;
+    case FDTD_OPT_ZCHUNK_FWD:
+      if (value < 0) return fail(h, FDTD_EINVAL, "zchunk must be >= 0");
+      h->opt_zchunk_fwd = value;
+      break;
     case FDTD_OPT_EXACT_REVERSAL:
       if (value != 0 && (value < 8 || value > 30))
         return fail(h, FDTD_EINVAL, "exact reversal: q must be 0 or 8..30");
@@ -726,6 +731,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_TILE_X: *value = h->opt_tile_x; break;
     case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
     case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
+    case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -945,6 +951,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   Layout L = layout_of(h, rec);
   StepArgs a = step_args(h, L);
   a.pl = L.plF;
+  if (h->opt_kernel == 5) a.zchunk = h->opt_zchunk_fwd > 0 ? h->opt_zchunk_fwd : h->nz;
   size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
   size_t psb = (size_t)L.plF.total * sizeof(float);
   cudaError_t e;
@@ -1173,6 +1180,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.compact = h->opt_compact;
   key.exact = h->opt_exact;
   key.coeffs = rec->coeffs;
+  key.zchunk_fwd = h->opt_zchunk_fwd;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;

@@ -156,6 +156,7 @@ def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y, rows, stages)
     base = gpu_run(F, A, w)
     for kernel in KERNELS:
         r = gpu_run(F, A, w, options={A.OPT_KERNEL: kernel, A.OPT_ZCHUNK: zchunk,
+                                      A.OPT_ZCHUNK_FWD: (zchunk + 5) % 17,
                                       A.OPT_TILE_Y: tile_y, A.OPT_ROWS: rows,
                                       A.OPT_STAGES: stages})
         np.testing.assert_array_equal(r["fields"], base["fields"])
