@@ -49,12 +49,14 @@ KERNEL_FILES = ["kernels_lag2.cu", "lag_common.cuh", "fdtd_internal.cuh", "tma.c
 
 def kernel_digest() -> str:
     """Digest of the default kernels' device code and compile flags (keys the
-    recorded DRAM traffic per launch: host-only changes keep it valid)."""
+    recorded DRAM traffic per launch: host-only changes keep it valid).  The
+    include path is left out, so that copies of the tree at other paths (and
+    machines) agree."""
     h = hashlib.sha256()
     for name in KERNEL_FILES:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + [x for x in FLAGS if not x.startswith("-I")]).encode())
     return h.hexdigest()[:16]
 
 
