@@ -252,14 +252,9 @@ enum {
                                    0 (default) = plain float32 increments.  Other kernels
                                    or tile shapes than kernel 5's defaults (32 x 8 tiles,
                                    2 stages) with q != 0: FDTD_EINVAL at fdtd_forward */
-  FDTD_OPT_ZCHUNK_FWD = 12,     /* kernel 5: z planes per CTA of the forward half-steps
+  FDTD_OPT_ZCHUNK_FWD = 12      /* kernel 5: z planes per CTA of the forward half-steps
                                    (default 8; 0 = the whole column); FDTD_OPT_ZCHUNK then
                                    sets the reverse phases (and every other kernel) */
-  FDTD_OPT_FUSED_RESTORE = 13   /* kernels 5 and 6: 1 = the reverse phases carry the tape
-                                   restore and the objective seeds of the reverse step (extra
-                                   CTAs restore the interface faces, the tile CTAs seed their
-                                   own detector cells), so a reverse step is two launches
-                                   instead of three; 0 (default) = a restore launch per step */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -44,8 +44,7 @@ def _digest() -> str:
 
 # Device code of the default half-step kernels: the files whose change can
 # change what those kernels move through memory.
-KERNEL_FILES = ["kernels_lag2.cu", "lag_common.cuh", "fdtd_internal.cuh", "tma.cuh",
-                "restore_fused.cuh", "tape_common.cuh", "bdct.cuh"]
+KERNEL_FILES = ["kernels_lag2.cu", "lag_common.cuh", "fdtd_internal.cuh", "tma.cuh"]
 
 
 def kernel_digest() -> str:

@@ -41,8 +41,6 @@ BdctLayout bdct_layout(const Faces& fc, int K);
 // Upload the basis table to the device once per device (host-synchronous;
 // call outside stream capture).
 cudaError_t bdct_ensure_basis();
-// Device address of the basis table (after bdct_ensure_basis; host call).
-cudaError_t bdct_basis_device(const float** out);
 
 cudaError_t launch_record_bdct(const float* FH, const float* FE, Geo g, const Faces& fc,
                                const BdctLayout& bl, void* tape_sample, cudaStream_t s);

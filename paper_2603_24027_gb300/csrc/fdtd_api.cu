@@ -21,7 +21,6 @@
 
 #include "../../include/fdtd.h"
 #include "bdct.cuh"
-#include "restore_fused.cuh"
 #include "fdtd_internal.cuh"
 
 using namespace fdtd;
@@ -41,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs, zchunk_fwd, fused_restore;
+      tile_x, compact, exact, coeffs, zchunk_fwd;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -86,8 +85,7 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_fused_restore;
-  const float* bdct_beta_dev;   // device address of the block codec's basis table
+      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -576,8 +574,6 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_zchunk_fwd = 8;
-  h->opt_fused_restore = 0;
-  h->bdct_beta_dev = nullptr;
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
@@ -709,7 +705,6 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < 0) return fail(h, FDTD_EINVAL, "zchunk must be >= 0");
       h->opt_zchunk_fwd = value;
       break;
-    case FDTD_OPT_FUSED_RESTORE: h->opt_fused_restore = value ? 1 : 0; break;
     case FDTD_OPT_EXACT_REVERSAL:
       if (value != 0 && (value < 8 || value > 30))
         return fail(h, FDTD_EINVAL, "exact reversal: q must be 0 or 8..30");
@@ -737,7 +732,6 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
     case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
     case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
-    case FDTD_OPT_FUSED_RESTORE: *value = h->opt_fused_restore; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -1113,49 +1107,11 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   }
   const BdctLayout bl =
       rec->dtype == kTapeBdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
-  // the reverse phases of kernels 5 and 6 may carry the restore and seeds
-  const bool fuse = rpair && h->opt_fused_restore;
-  FusedRestore fr0{};
-  if (fuse) {
-    fr0.dtype = rec->dtype;
-    fr0.tape = (const unsigned char*)(h->ws + L.tape);
-    fr0.stride = L.stride * (rec->dtype == kTapeBdct ? 1 : code_bytes(rec->dtype));
-    fr0.scales = (const float*)(h->ws + L.scales);
-    fr0.beta = h->bdct_beta_dev;
-    fr0.fc = h->faces;
-    fr0.bl = bl;
-    fr0.det = det;
-    fr0.det2 = det2;
-    fr0.seeds = (const double*)(h->ws + L.seeds);
-    // face-restoring CTAs: about four values per thread of a 32 x tile_y-cell tile CTA
-    const int* st6 = h->faces.start;
-    const long long vals = std::max<long long>(st6[1] - st6[0] + st6[3] - st6[2] + st6[5] - st6[4],
-                                               st6[2] - st6[1] + st6[4] - st6[3] + st6[6] - st6[5]);
-    const long long per_plane = (long long)((h->nx + a.tile_x - 1) / a.tile_x) *
-                                ((h->ny + a.tile_y - 1) / a.tile_y) * (a.tile_x / 2 * a.tile_y) * 4;
-    fr0.extra_z = (int)std::max<long long>(1, (vals + per_plane - 1) / per_plane);
-  }
   Sampler smp(h, 1);
   for (int n = h->N - 1; n >= 0; --n) {
     Interp ip;
     interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
-    FusedRestore fre = fr0, frh = fr0;
-    if (fuse) {
-      // E phase of step n: E^n on the high faces and the lam_H seeds of step n
-      // (step N-1 has its own restore launch); H phase of step n: Ht^{n-1/2}
-      // on the low faces and the lam_E seeds of step n-1
-      fre.faces = n < h->N - 1 ? 2 : 0;
-      fre.seed = n < h->N - 1 ? 2 : 0;
-      fre.ip = ip;
-      frh.faces = n > 0 ? 1 : 0;
-      frh.seed = n > 0 ? 1 : 0;
-      if (n > 0) {
-        interp_weights(h, rec, n - 1, 0, frh.ip.slot[0], frh.ip.w[0]);
-        interp_weights(h, rec, n - 1, 1, frh.ip.slot[1], frh.ip.w[1]);
-      }
-    }
-    if (!fuse || n == h->N - 1) {
     if ((e = smp.before(FDTD_K_RESTORE))) return e;
     if ((e = rec->dtype == kTapeBdct
                  ? launch_restore_seed_bdct(a.F, a.L, a.g, h->faces, bl, h->ws + L.tape, L.stride,
@@ -1166,24 +1122,23 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
                                        (const double*)(h->ws + L.seeds), h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_RESTORE))) return e;
-    }
     a.jn = h->wave[n];
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
     if ((e = smp.before(FDTD_K_REV_E))) return e;
-    if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream, &fre)
+    if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
                          : launch_lag(2, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_E))) return e;
     if ((e = smp.before(FDTD_K_REV_H))) return e;
-    if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream, &frh)
+    if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
                          : launch_lag(3, lrmaps[cur], a, h->stream))
               : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_H))) return e;
     cur ^= 1;
-    nl += fuse && n < h->N - 1 ? 2 : 3;
+    nl += 3;
   }
   *launches = nl;
   return cudaSuccess;
@@ -1226,7 +1181,6 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.exact = h->opt_exact;
   key.coeffs = rec->coeffs;
   key.zchunk_fwd = h->opt_zchunk_fwd;
-  key.fused_restore = h->opt_fused_restore;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1338,10 +1292,6 @@ static int backward_async(fdtd_handle* h, double seed, double seed2) {
   int rc = begin(h);
   if (rc) return rc;
   CK(h, upload_seeds(h, layout_of(h, &h->fwd_rec), seed, seed2, h->stream));
-  if (h->fwd_rec.dtype == kTapeBdct && !h->bdct_beta_dev) {   // outside any capture
-    CK(h, bdct_ensure_basis());
-    CK(h, bdct_basis_device(&h->bdct_beta_dev));
-  }
   int nl = 0;
   nvtxRangePushA("fdtd backward loop");
   rc = run_loop(h, &h->fwd_rec, 1, enqueue_backward, &nl, h->t2, h->t3);

@@ -290,10 +290,7 @@ cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, con
                             const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m);
 cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 // The same half-steps with two x-cells per thread (tile height >= 2).
-struct FusedRestore;
-// fr: tape restore and seeds carried by a reverse-phase launch (null: none).
-cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s,
-                        const FusedRestore* fr = nullptr);
+cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
                            cudaStream_t s);
 

@@ -91,13 +91,6 @@ cudaError_t bdct_ensure_basis() {
   return cudaSuccess;
 }
 
-cudaError_t bdct_basis_device(const float** out) {
-  void* ptr = nullptr;
-  cudaError_t e = cudaGetSymbolAddress(&ptr, g_bdct_beta);
-  *out = static_cast<const float*>(ptr);
-  return e;
-}
-
 // ---------------------------------------------------------- device side ---
 // Quantise one block with a warp: X (64 values, row-major, shared memory,
 // visible to the warp) -> K codes and the scale.  Lane i owns coefficients i

@@ -17,7 +17,6 @@
 #include <cudaTypedefs.h>
 
 #include "lag_common.cuh"
-#include "restore_fused.cuh"
 
 namespace fdtd {
 
@@ -98,22 +97,6 @@ __device__ __forceinline__ void psi_box_starts(const PsiLayout& pl, int x0, int 
   const PsiAxis& Yy = pl.ax[1];
   *qx0 = x0 + TW + 4 > X.hs ? x0 - X.shift : x0;
   *qy0 = y0 + TY + 1 > Yy.hs ? y0 - Yy.shift : y0;
-}
-
-// Seeds of a flux detector normal to `axis` (b, c the next axes cyclically):
-// l = E_b Ht_c - E_c Ht_b per cell, so lam_H_c += s E_b, lam_H_b -= s E_c and
-// lam_E_b += s Ht_c, lam_E_c -= s Ht_b.
-__device__ __forceinline__ void seed_flux_h(float& lx, float& ly, float& lz, float ex, float ey,
-                                            float ez, int axis, float s) {
-  if (axis == 0) { lz += s * ey; ly -= s * ez; }
-  else if (axis == 1) { lx += s * ez; lz -= s * ex; }
-  else { ly += s * ex; lx -= s * ey; }
-}
-__device__ __forceinline__ void seed_flux_e(float& lx, float& ly, float& lz, float hx, float hy,
-                                            float hz, int axis, float s) {
-  if (axis == 0) { ly += s * hz; lz -= s * hy; }
-  else if (axis == 1) { lz += s * hx; lx -= s * hz; }
-  else { lx += s * hy; ly -= s * hx; }
 }
 
 // A field increment of the leapfrog; EX (exact reversal) rounds it to the
@@ -545,21 +528,12 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
 // ======================================== reverse E phase (+ adjoint H) ===
 template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__ FusedRestore R) {
+k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LRE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  {   // CTAs past the z chunks restore interface faces (see restore_fused.cuh)
-    const int nch = (g.nz + a.zchunk - 1) / a.zchunk;
-    if ((int)blockIdx.z >= nch) {
-      if (R.faces)
-        fr_faces(R, g, a.F, ((blockIdx.z - nch) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
-                 R.extra_z * gridDim.x * gridDim.y);
-      return;
-    }
-  }
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
@@ -799,24 +773,7 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__
           st2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
         }
         const float* LHo = reinterpret_cast<const float*>(st + Y::LH);
-        float2 lh0 = ld2(LHo, ob), lh1 = ld2(LHo + B::OP, ob), lh2 = ld2(LHo + 2 * B::OP, ob);
-        if (R.seed == 2) {   // lam_H += s dl/dHt on the flux detectors' own cells (E^{n+1} here)
-          const float* Eo = reinterpret_cast<const float*>(st + Y::E);
-#pragma unroll
-          for (int w = 0; w < 2; ++w) {
-            const Det& d = w ? R.det2 : R.det;
-            if (d.kind != 2) continue;
-            const float sd = (float)R.seeds[w];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              if ((c == 0 || v1) && det_hit(d, x + c, y, k)) {
-                const float ex = Eo[ob + c], ey = Eo[B::OP + ob + c], ez = Eo[2 * B::OP + ob + c];
-                if (c == 0) seed_flux_h(lh0.x, lh1.x, lh2.x, ex, ey, ez, d.axis, sd);
-                else seed_flux_h(lh0.y, lh1.y, lh2.y, ex, ey, ez, d.axis, sd);
-              }
-            }
-          }
-        }
+        const float2 lh0 = ld2(LHo, ob), lh1 = ld2(LHo + B::OP, ob), lh2 = ld2(LHo + 2 * B::OP, ob);
         st2(LHz, q, lh2.x + ((o6[0] - n6[0]) + (o9[0] - n9[0])),
             lh2.y + ((o6[1] - n6[1]) + (o9[1] - n9[1])), true, v1);
         if (p > k0) {  // finish lam_H(p-1): its +z terms are this plane's o7, o8
@@ -881,21 +838,12 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__
 // ======================================== reverse H phase (+ adjoint E) ===
 template <int TY, int S, int TW, bool EX>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__ FusedRestore R) {
+k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
   typedef LRH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  {   // CTAs past the z chunks restore interface faces (see restore_fused.cuh)
-    const int nch = (g.nz + a.zchunk - 1) / a.zchunk;
-    if ((int)blockIdx.z >= nch) {
-      if (R.faces)
-        fr_faces(R, g, a.F, ((blockIdx.z - nch) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x,
-                 R.extra_z * gridDim.x * gridDim.y);
-      return;
-    }
-  }
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
@@ -974,34 +922,12 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__
         const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
         const long long qm = q - g.plane;
         auto inc = [&](float cc) { return inc_of<EX>(__fmul_rn(S_, cc), a); };
-        const float hxn[2] = {__fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
-                              __fadd_rn(c_hx[1], inc(c_d0[1] - d1[1]))};
-        const float hyn[2] = {__fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
-                              __fadd_rn(c_hy[1], inc(d2[1] - c_d3[1]))};
-        const float hzn[2] = {__fadd_rn(c_hz[0], inc(c_d4[0] - c_d5[0])),
-                              __fadd_rn(c_hz[1], inc(c_d4[1] - c_d5[1]))};
-        st2(Hx, qm, hxn[0], hxn[1], c_pr0, c_pr1);
-        st2(Hx + nc, qm, hyn[0], hyn[1], c_pr0, c_pr1);
-        st2(Hx + 2 * nc, qm, hzn[0], hzn[1], c_pr0, c_pr1);
-        if (R.seed == 1) {   // lam_E += s dl/dE on the flux detectors' own cells: Ht^{n+1/2}
-#pragma unroll              // of plane p-1 is complete only now, so lam_E(p-1) is updated again
-          for (int w = 0; w < 2; ++w) {
-            const Det& d = w ? R.det2 : R.det;
-            if (d.kind != 2) continue;
-            const float sd = (float)R.seeds[w];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              if ((c == 0 ? c_pr0 : c_pr1) && det_hit(d, x + c, y, p - 1)) {
-                float* l = LEx + qm + c;
-                float lx = l[0], ly = l[nc], lz = l[2 * nc];
-                seed_flux_e(lx, ly, lz, hxn[c], hyn[c], hzn[c], d.axis, sd);
-                l[0] = lx;
-                l[nc] = ly;
-                l[2 * nc] = lz;
-              }
-            }
-          }
-        }
+        st2(Hx, qm, __fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
+            __fadd_rn(c_hx[1], inc(c_d0[1] - d1[1])), c_pr0, c_pr1);
+        st2(Hx + nc, qm, __fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
+            __fadd_rn(c_hy[1], inc(d2[1] - c_d3[1])), c_pr0, c_pr1);
+        st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], inc(c_d4[0] - c_d5[0])),
+            __fadd_rn(c_hz[1], inc(c_d4[1] - c_d5[1])), c_pr0, c_pr1);
       }
       const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
       if (p >= k0 && p < k1) {
@@ -1115,34 +1041,12 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a, const __grid_constant__
         }
         const float* LEo = reinterpret_cast<const float*>(st + Y::LE);
         const float2 le0 = ld2(LEo, ob), le1 = ld2(LEo + B::OP, ob), le2 = ld2(LEo + 2 * B::OP, ob);
-        float2 nl0 = make_float2(le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
-                                 le0.y + ((c_m2[1] - o2[1]) + (m5[1] - o5[1])));
-        float2 nl1 = make_float2(le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
-                                 le1.y + ((c_m1[1] - o1[1]) + (m4[1] - o4[1])));
-        float2 nl2 = make_float2(le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
-                                 le2.y + ((m0[1] - o0[1]) + (m3[1] - o3[1])));
-        if (R.seed == 1) {   // lam_E += s dl/dE on the |E|^2 detectors' own cells (E^{n+1} here)
-#pragma unroll
-          for (int w = 0; w < 2; ++w) {
-            const Det& d = w ? R.det2 : R.det;
-            if (d.kind != 1) continue;
-            const float sd = (float)R.seeds[w];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              if ((c == 0 || v1) && det_hit(d, x + c, y, k)) {
-                const float ex = Eb[hb + c], ey = Eb[B::P + hb + c], ez = Eb[2 * B::P + hb + c];
-                if (c == 0) {
-                  nl0.x += sd * (2.0f * ex); nl1.x += sd * (2.0f * ey); nl2.x += sd * (2.0f * ez);
-                } else {
-                  nl0.y += sd * (2.0f * ex); nl1.y += sd * (2.0f * ey); nl2.y += sd * (2.0f * ez);
-                }
-              }
-            }
-          }
-        }
-        st2(LEx, q, nl0.x, nl0.y, true, v1);
-        st2(LEx + nc, q, nl1.x, nl1.y, true, v1);
-        st2(LEx + 2 * nc, q, nl2.x, nl2.y, true, v1);
+        st2(LEx, q, le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
+            le0.y + ((c_m2[1] - o2[1]) + (m5[1] - o5[1])), true, v1);
+        st2(LEx + nc, q, le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
+            le1.y + ((c_m1[1] - o1[1]) + (m4[1] - o4[1])), true, v1);
+        st2(LEx + 2 * nc, q, le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
+            le2.y + ((m0[1] - o0[1]) + (m3[1] - o3[1])), true, v1);
         // the -z terms plane p+1 needs are this plane's own z-terms
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -1191,9 +1095,9 @@ static cudaError_t set_smem_l2(KT kernel, int bytes) {
 // Launch with the programmatic-stream-serialization attribute when a.pdl is
 // set (the kernel then overlaps its launch and prologue with the tail of the
 // previous kernel and waits in pdl_sync()).
-template <class KT, class... Args>
+template <class KT>
 static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStream_t s,
-                             const StepArgs& a, const Args&... args) {
+                             const LagMaps& m, const StepArgs& a) {
   cudaError_t e = set_smem_l2(kernel, smem);
   if (e) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1206,23 +1110,19 @@ static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStr
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = a.pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
+  return cudaLaunchKernelEx(&cfg, kernel, m, a);
 }
 
 template <int TY, int S, int TW = 32, bool EX = false>
-static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
-                                 const FusedRestore& R, cudaStream_t s) {
+static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   static_assert((TW / 2 * TY) % 32 == 0, "a CTA is a whole number of warps");
   dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
   dim3 block(TW / 2, TY);
-  dim3 rgrid(grid.x, grid.y, grid.z + (R.faces ? R.extra_z : 0));
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX>, grid, block, LFH<TY, S, TW>::smem(), s, a, m, a);
-    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX>, grid, block, LFE<TY, S, TW>::smem(), s, a, m, a);
-    case 2:
-      return launch_ex(k_l2rev_e<TY, S, TW, EX>, rgrid, block, LRE<TY, S, TW>::smem(), s, a, m, a, R);
-    case 3:
-      return launch_ex(k_l2rev_h<TY, S, TW, EX>, rgrid, block, LRH<TY, S, TW>::smem(), s, a, m, a, R);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -1231,27 +1131,24 @@ static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
 // Exact reversal (a.xq != 0) runs 32 x 8 tiles with two stages.  A warp covers two tile rows, so tile heights start at 2 (the caller runs
 // a requested height of 1 as 2).  Stage counts 2 and 4 are built for tile
 // heights 2, 4 and 8; height 16 runs with 3.
-cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s,
-                        const FusedRestore* fr) {
-  const FusedRestore none{};
-  const FusedRestore& R = fr ? *fr : none;
+cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   const int S = a.stages;
   if (a.xq) {   // exact reversal: built for the default shape only
     if (a.tile_y != 8 || S != 2 || a.tile_x != 32) return cudaErrorInvalidValue;
-    return launch_lag2_t<8, 2, 32, true>(which, m, a, R, s);
+    return launch_lag2_t<8, 2, 32, true>(which, m, a, s);
   }
   if (a.tile_x == 40) {   // 40-wide tiles: tile height 8 only (whole warps), 2 or 3 stages
     if (a.tile_y != 8) return cudaErrorInvalidValue;
-    return S == 3 ? launch_lag2_t<8, 3, 40>(which, m, a, R, s) : launch_lag2_t<8, 2, 40>(which, m, a, R, s);
+    return S == 3 ? launch_lag2_t<8, 3, 40>(which, m, a, s) : launch_lag2_t<8, 2, 40>(which, m, a, s);
   }
   switch (a.tile_y) {
-    case 2: return S == 2 ? launch_lag2_t<2, 2>(which, m, a, R, s)
-                 : S == 4 ? launch_lag2_t<2, 4>(which, m, a, R, s) : launch_lag2_t<2, 3>(which, m, a, R, s);
-    case 4: return S == 2 ? launch_lag2_t<4, 2>(which, m, a, R, s)
-                 : S == 4 ? launch_lag2_t<4, 4>(which, m, a, R, s) : launch_lag2_t<4, 3>(which, m, a, R, s);
-    case 8: return S == 2 ? launch_lag2_t<8, 2>(which, m, a, R, s)
-                 : S == 4 ? launch_lag2_t<8, 4>(which, m, a, R, s) : launch_lag2_t<8, 3>(which, m, a, R, s);
-    case 16: return launch_lag2_t<16, 3>(which, m, a, R, s);
+    case 2: return S == 2 ? launch_lag2_t<2, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag2_t<2, 4>(which, m, a, s) : launch_lag2_t<2, 3>(which, m, a, s);
+    case 4: return S == 2 ? launch_lag2_t<4, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag2_t<4, 4>(which, m, a, s) : launch_lag2_t<4, 3>(which, m, a, s);
+    case 8: return S == 2 ? launch_lag2_t<8, 2>(which, m, a, s)
+                 : S == 4 ? launch_lag2_t<8, 4>(which, m, a, s) : launch_lag2_t<8, 3>(which, m, a, s);
+    case 16: return launch_lag2_t<16, 3>(which, m, a, s);
   }
   return cudaErrorInvalidValue;
 }

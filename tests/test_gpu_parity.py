@@ -231,53 +231,6 @@ def test_compact_auxiliaries_match_the_full_grid_layout(F, A, ty, stages, tile_x
     assert r["sim"].workspace_bytes(rec) < base["sim"].workspace_bytes(rec)
 
 
-@pytest.mark.parametrize("kernel", [5, 6])
-@pytest.mark.parametrize("name,tape", [("ragged_poynting", "bf16:2:linear"),
-                                       ("ragged_e2_point", "f32:1:linear"),
-                                       ("ragged_poynting", "e4m3:3:cubic"),
-                                       ("ragged_e2_point", "e4m3b11fnuz:2:linear"),
-                                       ("ragged_poynting", "bdct10:2:cubic"),
-                                       ("coupler2", "bf16:4:linear")])
-def test_fused_restore_matches_the_restore_launch(F, A, kernel, name, tape):
-    """The reverse phases carrying the tape restore and the objective seeds
-    (extra CTAs restore the faces, tile CTAs seed their own detector cells)
-    against a restore launch per step: the same fields bit for bit and the
-    same gradient, for both detector kinds, two detectors, every kind of
-    tape, with and without captured graphs."""
-    if name == "coupler2":
-        w = I.coupler_small(n_steps=70)
-    else:
-        w = SMALL[name]()
-    dt, k, interp = tape.split(":")
-    rec = A.record_cfg(dt, int(k), interp)
-    eps = torch.from_numpy(w.eps).cuda()
-    out = {}
-    for fused in (0, 1):
-        for graphs in (0, 1):
-            sim = F.Simulation(w)
-            for o, v in {A.OPT_KERNEL: kernel, A.OPT_FUSED_RESTORE: fused,
-                         A.OPT_USE_GRAPHS: graphs}.items():
-                sim.set_option(o, v)
-            sim.forward(eps, rec)
-            g = sim.backward(0.7, seed2=-1.3 if name == "coupler2" else 0.0).cpu().numpy()
-            out[(fused, graphs)] = (sim.read_fields().cpu().numpy(), g)
-    base_f, base_g = out[(0, 1)]
-    for key, (f, g) in out.items():
-        np.testing.assert_array_equal(f, base_f)
-        same_gradient(g, base_g)
-
-
-@pytest.mark.parametrize("zchunk,ty,stages", [(1, 4, 3), (5, 16, 3), (3, 2, 4)])
-def test_fused_restore_with_launch_shapes(F, A, zchunk, ty, stages):
-    w = SMALL["ragged_poynting"]()
-    rec = A.record_cfg("bf16", 2, "linear")
-    base = gpu_run(F, A, w, rec=rec)
-    r = gpu_run(F, A, w, rec=rec, options={A.OPT_FUSED_RESTORE: 1, A.OPT_ZCHUNK: zchunk,
-                                           A.OPT_TILE_Y: ty, A.OPT_STAGES: stages})
-    np.testing.assert_array_equal(r["fields"], base["fields"])
-    same_gradient(r["g"], base["g"])
-
-
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     w = SMALL["ragged_poynting"]()
