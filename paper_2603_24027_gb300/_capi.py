@@ -10,7 +10,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfdtd_gb300.so")
+# FDTD_BOUNDS_CHECKED=1 loads the bounds-checked test build instead.
+LIB_PATH = os.path.join(HERE, "libfdtd_gb300_checked.so" if os.environ.get("FDTD_BOUNDS_CHECKED")
+                        else "libfdtd_gb300.so")
 
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ESTATE, FDTD_ETIMEOUT, FDTD_ENONFINITE = (
     0, -1, -2, -3, -4, -5, -6)

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libfdtd_gb300.so")
+# Bounds-checked variant for tests (-DFDTD_BOUNDS_CHECK): every store of the
+# default kernels checks that it lands in a buffer the launch may write.
+LIB_CHECKED = os.path.join(HERE, "libfdtd_gb300_checked.so")
 SOURCES = ["kernels_step.cu", "kernels_fused.cu", "kernels_tma.cu", "kernels_split_tma.cu",
            "kernels_lag.cu", "kernels_lag2.cu", "kernels_ffwd.cu", "kernels_tape.cu",
            "kernels_bdct.cu", "fdtd_api.cu"]
@@ -60,17 +63,20 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "libfdtd_gb300.stamp")
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    out = LIB_CHECKED if checked else LIB
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    extra = list(extra) + (["-DFDTD_BOUNDS_CHECK"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
+    stamp = os.path.join(bdir, "libfdtd_gb300.stamp")
     dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(out) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == dig:
-                return LIB
+                return out
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -81,15 +87,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = out + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     with open(stamp, "w") as f:
         f.write(dig)
-    return LIB
+    return out
 
 
 if __name__ == "__main__":

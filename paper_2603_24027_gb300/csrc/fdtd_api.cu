@@ -1254,6 +1254,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   if (rc) return rc;
   if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
   if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
+  if (err & ERR_BOUNDS) return fail(h, FDTD_ECUDA, "bounds check: a store fell outside its buffers");
   double s = 0.0;
   for (double v : h->obj_hist) s += v;
   if (!isfinite(s)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
@@ -1315,6 +1316,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
+  if (err & ERR_BOUNDS) return fail(h, FDTD_ECUDA, "bounds check: a store fell outside its buffers");
   if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
   return FDTD_OK;
 }

@@ -24,7 +24,7 @@
 namespace fdtd {
 
 enum { PR_BE = 0, PR_AE = 1, PR_KE = 2, PR_BH = 3, PR_AH = 4, PR_KH = 5 };
-enum { ERR_EPS = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u, ERR_LAUNCH = 8u };
+enum { ERR_EPS = 1u, ERR_NONFINITE = 2u, ERR_TIMEOUT = 4u, ERR_LAUNCH = 8u, ERR_BOUNDS = 16u };
 
 struct Geo {
   int nx, ny, nz, px, P, nmax;

@@ -38,6 +38,27 @@ __device__ __forceinline__ void st2(float* p, long long q, float u, float v, boo
   }
 }
 
+#ifdef FDTD_BOUNDS_CHECK
+// Bounds-checked test build: a store must land in the fields, the adjoint
+// fields or one of the two auxiliary sets of the launch, else it is skipped
+// and the error word records ERR_BOUNDS.
+__device__ __forceinline__ bool in_buf(const float* p, const float* base, long long n) {
+  return base && p >= base && p < base + n;
+}
+__device__ __forceinline__ bool store_ok(const StepArgs& a, const float* p) {
+  const long long n6 = 6 * a.g.nc;
+  if (in_buf(p, a.F, n6) || in_buf(p, a.L, n6) || in_buf(p, a.psiA, a.pl.total) ||
+      in_buf(p, a.psiB, a.pl.total))
+    return true;
+  atomicOr(a.err, ERR_BOUNDS);
+  return false;
+}
+#define ST2(p, q, u, v, f0, f1) \
+  st2(p, q, u, v, (f0) && store_ok(a, (p) + (q)), (f1) && store_ok(a, (p) + (q) + 1))
+#else
+#define ST2(p, q, u, v, f0, f1) st2(p, q, u, v, f0, f1)
+#endif
+
 // Forward CPML recursion of one derivative d (Eq. 5 form): the updated psi
 // goes to *s, the stretched derivative is returned.
 __device__ __forceinline__ float cpml(float d, float psi_old, float b, float a, float kv, float* s) {
@@ -230,8 +251,8 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
             t2[c] = cpml(t2[c], c_pz1[c], bz, az, kz, &s2[c]);
           }
           const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
-          st2(psi, qz, s1[0], s1[1], true, v1);
-          st2(psi + a.pl.ax[2].cs, qz, s2[0], s2[1], true, v1);
+          ST2(psi, qz, s1[0], s1[1], true, v1);
+          ST2(psi + a.pl.ax[2].cs, qz, s2[0], s2[1], true, v1);
         }
         float hx[2], hy[2], hz[2];
 #pragma unroll
@@ -241,9 +262,9 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
           hy[c] = __fsub_rn(c_hy[c], inc_of<EX>(__fmul_rn(g.S, cy), a));
           hz[c] = __fsub_rn(c_hz[c], inc_of<EX>(__fmul_rn(g.S, cz), a));
         }
-        st2(Hx, q, hx[0], hx[1], true, v1);
-        st2(Hy, q, hy[0], hy[1], true, v1);
-        st2(Hz, q, hz[0], hz[1], true, v1);
+        ST2(Hx, q, hx[0], hx[1], true, v1);
+        ST2(Hy, q, hy[0], hy[1], true, v1);
+        ST2(Hz, q, hz[0], hz[1], true, v1);
         q += g.plane;
       }
       if (p < k1) {  // start Ht(p): x and y derivatives, their psi updates
@@ -267,8 +288,8 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
             t4[1] = cpml(t4[1], p1.y, bx1, ax1, kx1, &s4[1]);
           }
           const long long qxx = psi_ix<0>(a.pl, 0, x, y, p);
-          st2(psi, qxx, s3[0], s3[1], sx0, sx1);
-          st2(psi + a.pl.ax[0].cs, qxx, s4[0], s4[1], sx0, sx1);
+          ST2(psi, qxx, s3[0], s3[1], sx0, sx1);
+          ST2(psi + a.pl.ax[0].cs, qxx, s4[0], s4[1], sx0, sx1);
         }
         if (sy) {
           const float* P = reinterpret_cast<const float*>(st + Y::PY);
@@ -281,8 +302,8 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
             t5[c] = cpml(t5[c], q1[c], by, ay, ky, &s5[c]);
           }
           const long long qyy = psi_ix<1>(a.pl, 0, x, y, p);
-          st2(psi, qyy, s0[0], s0[1], true, v1);
-          st2(psi + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
+          ST2(psi, qyy, s0[0], s0[1], true, v1);
+          ST2(psi + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
         }
         const float* Ho = reinterpret_cast<const float*>(st + Y::H);
         const float2 h0 = ld2(Ho, ob), h1 = ld2(Ho + B::OP, ob), h2 = ld2(Ho + 2 * B::OP, ob);
@@ -418,8 +439,8 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
               t10[1] = cpml(d10[1], p1.y, bx1, ax1, kx1, &s10[1]);
             }
             const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
-            st2(psi, qxx, s9[0], s9[1], sx0, sx1);
-            st2(psi + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
+            ST2(psi, qxx, s9[0], s9[1], sx0, sx1);
+            ST2(psi + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
           }
           if (sy) {
             const float* P = reinterpret_cast<const float*>(st + Y::PY);
@@ -432,8 +453,8 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
               t11[c] = cpml(d11[c], q1[c], by, ay, ky, &s11[c]);
             }
             const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
-            st2(psi, qyy, s6[0], s6[1], true, v1);
-            st2(psi + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
+            ST2(psi, qyy, s6[0], s6[1], true, v1);
+            ST2(psi + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
           }
           if (sz) {
             const float* P = reinterpret_cast<const float*>(st + Y::PZ);
@@ -447,8 +468,8 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
               t8[c] = cpml(d8[c], q1[c], bz, az, kz, &s8[c]);
             }
             const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
-            st2(psi, qz, s7[0], s7[1], true, v1);
-            st2(psi + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
+            ST2(psi, qz, s7[0], s7[1], true, v1);
+            ST2(psi + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
           }
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
@@ -481,9 +502,9 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
           ey[c] = __fadd_rn(eo1[c], inc_of<EX>(__fmul_rn(cbv[c], c1[c]), a));
           ez[c] = __fadd_rn(eo2[c], inc_of<EX>(__fmul_rn(cbv[c], c2[c]), a));
         }
-        st2(Ex, q, ex[0], ex[1], true, v1);
-        st2(Ey, q, ey[0], ey[1], true, v1);
-        st2(Ez, q, ez[0], ez[1], true, v1);
+        ST2(Ex, q, ex[0], ex[1], true, v1);
+        ST2(Ey, q, ey[0], ey[1], true, v1);
+        ST2(Ez, q, ez[0], ez[1], true, v1);
         if (a.det.kind) {
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
@@ -660,11 +681,11 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
           auto inc = [&](float cbc, float cc) {
             return inc_of<EX>(__fmul_rn(cbc, cc), a);
           };
-          st2(Ex, q, __fsub_rn(e0.x, inc(cbv[0], c0[0])), __fsub_rn(e0.y, inc(cbv[1], c0[1])),
+          ST2(Ex, q, __fsub_rn(e0.x, inc(cbv[0], c0[0])), __fsub_rn(e0.y, inc(cbv[1], c0[1])),
               xyin0, xyin1);
-          st2(Ex + nc, q, __fsub_rn(e1.x, inc(cbv[0], c1[0])), __fsub_rn(e1.y, inc(cbv[1], c1[1])),
+          ST2(Ex + nc, q, __fsub_rn(e1.x, inc(cbv[0], c1[0])), __fsub_rn(e1.y, inc(cbv[1], c1[1])),
               xyin0, xyin1);
-          st2(Ex + 2 * nc, q, __fsub_rn(e2.x, inc(cbv[0], c2[0])),
+          ST2(Ex + 2 * nc, q, __fsub_rn(e2.x, inc(cbv[0], c2[0])),
               __fsub_rn(e2.y, inc(cbv[1], c2[1])), xyin0, xyin1);
           if (dy_ && k >= a.dlo[2] && k < a.dhi[2]) {
 #pragma unroll
@@ -676,6 +697,12 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
                     ((long long)(k - a.dlo[2]) * dY + (y - a.dlo[1])) * dX + (xc - a.dlo[0]);
                 // one owner per cell: a fire-and-forget reduction in L2 adds
                 // exactly what a load-add-store would, without the load latency
+#ifdef FDTD_BOUNDS_CHECK
+                if (qd < 0 || qd >= (long long)dX * dY * (a.dhi[2] - a.dlo[2])) {
+                  atomicOr(a.err, ERR_BOUNDS);
+                  continue;
+                }
+#endif
                 atomicAdd(a.gacc + qd, (double)s);
               }
             }
@@ -719,8 +746,8 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
               o11[c] = adj(o11[c], q1[c], by, ay, ky, &s11[c]);
             }
             const long long qyy = psi_ix<1>(a.pl, 2, x, y, k);
-            st2(lpB, qyy, s6[0], s6[1], true, v1);
-            st2(lpB + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
+            ST2(lpB, qyy, s6[0], s6[1], true, v1);
+            ST2(lpB + a.pl.ax[1].cs, qyy, s11[0], s11[1], true, v1);
           }
           if (sy1) {
             const float2 p0 = ld2(P, ob + TW), p1 = ld2(P + B::YP, ob + TW);
@@ -747,8 +774,8 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
             o10[1] = adj(o10[1], p1.y, bx1, ax1, kx1, &s10[1]);
           }
           const long long qxx = psi_ix<0>(a.pl, 2, x, y, k);
-          st2(lpB, qxx, s9[0], s9[1], sx0, sx1);
-          st2(lpB + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
+          ST2(lpB, qxx, s9[0], s9[1], sx0, sx1);
+          ST2(lpB + a.pl.ax[0].cs, qxx, s10[0], s10[1], sx0, sx1);
           if (sx2) {
             float dummy;
             n9x = adj(n9x, P[xb + 2], bx2, ax2, kx2, &dummy);
@@ -769,18 +796,18 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
             o8[c] = adj(o8[c], q1[c], b, aa, kv, &s8[c]);
           }
           const long long qz = psi_ix<2>(a.pl, 2, x, y, k);
-          st2(lpB, qz, s7[0], s7[1], true, v1);
-          st2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
+          ST2(lpB, qz, s7[0], s7[1], true, v1);
+          ST2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], true, v1);
         }
         const float* LHo = reinterpret_cast<const float*>(st + Y::LH);
         const float2 lh0 = ld2(LHo, ob), lh1 = ld2(LHo + B::OP, ob), lh2 = ld2(LHo + 2 * B::OP, ob);
-        st2(LHz, q, lh2.x + ((o6[0] - n6[0]) + (o9[0] - n9[0])),
+        ST2(LHz, q, lh2.x + ((o6[0] - n6[0]) + (o9[0] - n9[0])),
             lh2.y + ((o6[1] - n6[1]) + (o9[1] - n9[1])), true, v1);
         if (p > k0) {  // finish lam_H(p-1): its +z terms are this plane's o7, o8
           const long long qm = q - g.plane;
-          st2(LHx, qm, c_lhx[0] + ((c_o8[0] - o8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - o8[1]) + c_bx[1]),
+          ST2(LHx, qm, c_lhx[0] + ((c_o8[0] - o8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - o8[1]) + c_bx[1]),
               true, v1);
-          st2(LHy, qm, c_lhy[0] + ((c_o7[0] - o7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - o7[1]) + c_by[1]),
+          ST2(LHy, qm, c_lhy[0] + ((c_o7[0] - o7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - o7[1]) + c_by[1]),
               true, v1);
         }
         c_lhx[0] = lh0.x; c_lhx[1] = lh0.y;
@@ -823,9 +850,9 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
           }
         }
         const long long qm = q - g.plane;
-        st2(LHx, qm, c_lhx[0] + ((c_o8[0] - n8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - n8[1]) + c_bx[1]),
+        ST2(LHx, qm, c_lhx[0] + ((c_o8[0] - n8[0]) + c_bx[0]), c_lhx[1] + ((c_o8[1] - n8[1]) + c_bx[1]),
             true, v1);
-        st2(LHy, qm, c_lhy[0] + ((c_o7[0] - n7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - n7[1]) + c_by[1]),
+        ST2(LHy, qm, c_lhy[0] + ((c_o7[0] - n7[0]) + c_by[0]), c_lhy[1] + ((c_o7[1] - n7[1]) + c_by[1]),
             true, v1);
       }
     }
@@ -922,11 +949,11 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
         const float d2[2] = {ex.x - c_ex[0], ex.y - c_ex[1]};
         const long long qm = q - g.plane;
         auto inc = [&](float cc) { return inc_of<EX>(__fmul_rn(S_, cc), a); };
-        st2(Hx, qm, __fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
+        ST2(Hx, qm, __fadd_rn(c_hx[0], inc(c_d0[0] - d1[0])),
             __fadd_rn(c_hx[1], inc(c_d0[1] - d1[1])), c_pr0, c_pr1);
-        st2(Hx + nc, qm, __fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
+        ST2(Hx + nc, qm, __fadd_rn(c_hy[0], inc(d2[0] - c_d3[0])),
             __fadd_rn(c_hy[1], inc(d2[1] - c_d3[1])), c_pr0, c_pr1);
-        st2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], inc(c_d4[0] - c_d5[0])),
+        ST2(Hx + 2 * nc, qm, __fadd_rn(c_hz[0], inc(c_d4[0] - c_d5[0])),
             __fadd_rn(c_hz[1], inc(c_d4[1] - c_d5[1])), c_pr0, c_pr1);
       }
       const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
@@ -986,8 +1013,8 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
               o5[c] = adj(o5[c], q1[c], by, ay, ky, &s5[c]);
             }
             const long long qyy = psi_ix<1>(a.pl, 0, x, y, k);
-            st2(lpB, qyy, s4[0], s4[1], true, v1);
-            st2(lpB + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
+            ST2(lpB, qyy, s4[0], s4[1], true, v1);
+            ST2(lpB + a.pl.ax[1].cs, qyy, s5[0], s5[1], true, v1);
           }
           if (sym) {
             const float2 p0 = ld2(P, yb - TW), p1 = ld2(P + B::YP, yb - TW);
@@ -1014,8 +1041,8 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
             o4[1] = adj(o4[1], p1.y, bx1, ax1, kx1, &s1[1]);
           }
           const long long qxx = psi_ix<0>(a.pl, 0, x, y, k);
-          st2(lpB, qxx, s0[0], s0[1], sx0, sx1);
-          st2(lpB + a.pl.ax[0].cs, qxx, s1[0], s1[1], sx0, sx1);
+          ST2(lpB, qxx, s0[0], s0[1], sx0, sx1);
+          ST2(lpB + a.pl.ax[0].cs, qxx, s1[0], s1[1], sx0, sx1);
           if (sxm) {
             float dummy;
             m3x = adj(m3x, P[xb - 1], bxm, axm, kxm, &dummy);
@@ -1036,16 +1063,16 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
             o2[c] = adj(o2[c], q1[c], b, aa, kv, &s9[c]);
           }
           const long long qz = psi_ix<2>(a.pl, 0, x, y, k);
-          st2(lpB, qz, s8[0], s8[1], true, v1);
-          st2(lpB + a.pl.ax[2].cs, qz, s9[0], s9[1], true, v1);
+          ST2(lpB, qz, s8[0], s8[1], true, v1);
+          ST2(lpB + a.pl.ax[2].cs, qz, s9[0], s9[1], true, v1);
         }
         const float* LEo = reinterpret_cast<const float*>(st + Y::LE);
         const float2 le0 = ld2(LEo, ob), le1 = ld2(LEo + B::OP, ob), le2 = ld2(LEo + 2 * B::OP, ob);
-        st2(LEx, q, le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
+        ST2(LEx, q, le0.x + ((c_m2[0] - o2[0]) + (m5[0] - o5[0])),
             le0.y + ((c_m2[1] - o2[1]) + (m5[1] - o5[1])), true, v1);
-        st2(LEx + nc, q, le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
+        ST2(LEx + nc, q, le1.x + ((c_m1[0] - o1[0]) + (m4[0] - o4[0])),
             le1.y + ((c_m1[1] - o1[1]) + (m4[1] - o4[1])), true, v1);
-        st2(LEx + 2 * nc, q, le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
+        ST2(LEx + 2 * nc, q, le2.x + ((m0[0] - o0[0]) + (m3[0] - o3[0])),
             le2.y + ((m0[1] - o0[1]) + (m3[1] - o3[1])), true, v1);
         // the -z terms plane p+1 needs are this plane's own z-terms
 #pragma unroll
