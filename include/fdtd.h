@@ -295,6 +295,21 @@ int fdtd_source_waveform(const fdtd_handle* h, float* out);
 int fdtd_interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int step, int field,
                         int* slot, float* weight);
 
+/* Checkpoint of a forward run (the state fdtd_backward consumes): the final
+ * fields, the coefficients cb, the boundary tape with its scales and the
+ * per-step objectives, with a header naming the problem and record config.
+ * fdtd_state_bytes: size of the blob for the last forward (host only;
+ * FDTD_ESTATE without one).  fdtd_save_state: copies it into host memory
+ * (bytes >= fdtd_state_bytes, else FDTD_EINVAL); the handle keeps its state.
+ * fdtd_load_state: makes a handle of the same problem (grid, PML, steps,
+ * second detector) ready for fdtd_backward as if it had run that forward;
+ * its bound workspace must fit the saved record config.  Errors: FDTD_EINVAL
+ * for a blob of another problem or a bad header, FDTD_ESTATE without a
+ * workspace, FDTD_ENOMEM if it is too small. */
+int fdtd_state_bytes(const fdtd_handle* h, size_t* bytes);
+int fdtd_save_state(fdtd_handle* h, void* host_buf, size_t bytes);
+int fdtd_load_state(fdtd_handle* h, const void* host_buf, size_t bytes);
+
 /* Copy the current E, Ht (6 x [nz][ny][nx] float32) into d_out (device). */
 int fdtd_read_fields(fdtd_handle* h, float* d_out);
 /* Per-step objective l_n of the last forward (host, n_steps doubles). */

@@ -1435,6 +1435,113 @@ extern "C" int fdtd_kernel_timing(const fdtd_handle* h, int kind, float* avg_ms,
   return FDTD_OK;
 }
 
+// --------------------------------------------------------- checkpoint ---
+namespace {
+struct StateHeader {
+  char magic[8];
+  int nx, ny, nz, P, N, det2_kind;
+  fdtd_record_cfg rec;
+  int pad;
+  long long nc, tape_bytes;
+  double obj2_sum;
+};
+const char kStateMagic[8] = {'F', 'D', 'T', 'D', 'S', 'T', '0', '1'};
+
+// Device regions of a forward's state for record config rec: fields, cb,
+// tape, scales, objectives, second objectives (bytes each).
+void state_regions(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t sz[6]) {
+  const Layout L = layout_of(h, rec);
+  const size_t nc = (size_t)h->nz * h->ny * h->px;
+  const int eb = rec->dtype == kTapeBdct ? 1 : code_bytes(rec->dtype);
+  sz[0] = 6 * nc * sizeof(float);
+  sz[1] = nc * sizeof(float);
+  sz[2] = (size_t)L.J * L.stride * eb;
+  sz[3] = (size_t)L.J * 6 * sizeof(float);
+  sz[4] = (size_t)h->N * sizeof(double);
+  sz[5] = (size_t)h->N * sizeof(double);
+}
+}  // namespace
+
+extern "C" int fdtd_state_bytes(const fdtd_handle* h, size_t* bytes) {
+  if (!h || !bytes) return FDTD_EINVAL;
+  if (!h->have_forward) return FDTD_ESTATE;
+  size_t sz[6];
+  state_regions(h, &h->fwd_rec, sz);
+  *bytes = sizeof(StateHeader) + sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5];
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_save_state(fdtd_handle* h, void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return FDTD_EINVAL;
+  size_t need = 0;
+  if (fdtd_state_bytes(h, &need)) return fail(h, FDTD_ESTATE, "no forward state to save");
+  if (bytes < need) return fail(h, FDTD_EINVAL, "state buffer too small");
+  int rc = begin(h);
+  if (rc) return rc;
+  const Layout L = layout_of(h, &h->fwd_rec);
+  size_t sz[6];
+  state_regions(h, &h->fwd_rec, sz);
+  StateHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kStateMagic, 8);
+  hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.P = h->P; hd.N = h->N;
+  hd.det2_kind = h->det2.kind;
+  hd.rec = h->fwd_rec;
+  hd.nc = (long long)h->nz * h->ny * h->px;
+  hd.tape_bytes = (long long)sz[2];
+  hd.obj2_sum = h->obj2_sum;
+  char* out = (char*)host_buf;
+  memcpy(out, &hd, sizeof hd);
+  out += sizeof hd;
+  const size_t src[6] = {L.F[h->fwd_buf], L.cb, L.tape, L.scales, L.obj, L.obj2};
+  for (int i = 0; i < 6; ++i) {
+    if (i == 4) {   // the host copy of the per-step objectives
+      memcpy(out, h->obj_hist.data(), sz[4]);
+    } else if (sz[i]) {
+      CK(h, cudaMemcpyAsync(out, h->ws + src[i], sz[i], cudaMemcpyDeviceToHost, h->stream));
+    }
+    out += sz[i];
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return finish(h);
+}
+
+extern "C" int fdtd_load_state(fdtd_handle* h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < sizeof(StateHeader)) return FDTD_EINVAL;
+  StateHeader hd;
+  memcpy(&hd, host_buf, sizeof hd);
+  if (memcmp(hd.magic, kStateMagic, 8) != 0) return fail(h, FDTD_EINVAL, "not a state blob");
+  if (hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.P != h->P || hd.N != h->N ||
+      hd.det2_kind != h->det2.kind || hd.nc != (long long)h->nz * h->ny * h->px)
+    return fail(h, FDTD_EINVAL, "state of another problem");
+  int rc = check_rec(h, &hd.rec);
+  if (rc) return rc;
+  size_t sz[6];
+  state_regions(h, &hd.rec, sz);
+  if ((long long)sz[2] != hd.tape_bytes ||
+      bytes < sizeof hd + sz[0] + sz[1] + sz[2] + sz[3] + sz[4] + sz[5])
+    return fail(h, FDTD_EINVAL, "state blob truncated or inconsistent");
+  if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+  const Layout L = layout_of(h, &hd.rec);
+  if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this state");
+  rc = begin(h);
+  if (rc) return rc;
+  const char* in = (const char*)host_buf + sizeof hd;
+  const size_t dst[6] = {L.F[0], L.cb, L.tape, L.scales, L.obj, L.obj2};
+  h->obj_hist.assign(h->N, 0.0);
+  for (int i = 0; i < 6; ++i) {
+    if (i == 4) memcpy(h->obj_hist.data(), in, sz[4]);
+    if (sz[i]) CK(h, cudaMemcpyAsync(h->ws + dst[i], in, sz[i], cudaMemcpyHostToDevice, h->stream));
+    in += sz[i];
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->fwd_rec = hd.rec;
+  h->fwd_buf = 0;
+  h->obj2_sum = hd.obj2_sum;
+  h->have_forward = true;
+  return finish(h);
+}
+
 extern "C" int fdtd_read_fields(fdtd_handle* h, float* d_out) {
   if (!h || !d_out) return FDTD_EINVAL;
   if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");

@@ -133,6 +133,26 @@ class Simulation:
                                          C.byref(out)))
         return out.value
 
+    # --------------------------------------------------------- checkpoint --
+    def save_state(self) -> "np.ndarray":
+        """The last forward's state (fields, cb, tape, objectives) as a host
+        byte array that load_state restores, in this or another handle of the
+        same problem."""
+        import numpy as np
+        n = C.c_size_t()
+        self._check(A.lib().fdtd_state_bytes(self.h, C.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._check(A.lib().fdtd_save_state(self.h, C.c_void_p(buf.ctypes.data), n.value))
+        return buf
+
+    def load_state(self, buf, rec) -> None:
+        """Make this handle ready for backward() from a saved forward state
+        (rec: the record config it was saved with, for the workspace size)."""
+        import numpy as np
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self.ensure_workspace(rec)
+        self._check(A.lib().fdtd_load_state(self.h, C.c_void_p(buf.ctypes.data), buf.size))
+
     def backward(self, seed: float = 1.0, out: Optional[torch.Tensor] = None,
                  seed2: Optional[float] = None) -> torch.Tensor:
         """d(seed L + seed2 M)/d(eps) over the design box, float32 [dz][dy][dx]

@@ -264,3 +264,21 @@ def test_exact_reversal_option_is_validated(capi, fdtd):
     out = C.c_double()
     rc = lib.fdtd_forward(sim.h, C.c_void_p(1), C.byref(capi.record_cfg()), C.byref(out))
     assert rc == capi.FDTD_EINVAL
+
+
+def test_checkpoint_header_is_validated(capi, fdtd):
+    """fdtd_state_bytes needs a forward; fdtd_load_state refuses a blob that
+    is not a state or belongs to another problem before touching the device."""
+    import ctypes as C
+    lib = capi.lib()
+    sim = fdtd.Simulation(I.fd_cube())
+    n = C.c_size_t()
+    assert lib.fdtd_state_bytes(sim.h, C.byref(n)) == capi.FDTD_ESTATE
+    junk = np.zeros(4096, np.uint8)
+    assert lib.fdtd_load_state(sim.h, C.c_void_p(junk.ctypes.data), junk.size) == capi.FDTD_EINVAL
+    # a header of an 8^3 problem with other step count
+    hdr = np.zeros(4096, np.uint8)
+    hdr[:8] = np.frombuffer(b"FDTDST01", np.uint8)
+    ints = hdr[8:8 + 24].view(np.int32)
+    ints[:] = [8, 8, 8, 2, 61, 0]
+    assert lib.fdtd_load_state(sim.h, C.c_void_p(hdr.ctypes.data), hdr.size) == capi.FDTD_EINVAL

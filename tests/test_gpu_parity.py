@@ -231,6 +231,29 @@ def test_compact_auxiliaries_match_the_full_grid_layout(F, A, ty, stages, tile_x
     assert r["sim"].workspace_bytes(rec) < base["sim"].workspace_bytes(rec)
 
 
+@pytest.mark.parametrize("kernel,tape", [(5, "bf16:4:linear"), (6, "bdct10:2:cubic"),
+                                         (0, "e4m3:2:cubic")])
+def test_checkpoint_resumes_the_backward_in_another_handle(F, A, kernel, tape):
+    """Forward in one handle, save its state to host memory, load it into a
+    fresh handle of the same problem: the fresh handle's backward gives the
+    original's gradient and objectives bit for bit."""
+    w = SMALL["ragged_poynting"]()
+    dt, k, interp = tape.split(":")
+    rec = A.record_cfg(dt, int(k), interp)
+    eps = torch.from_numpy(w.eps).cuda()
+    a = F.Simulation(w)
+    a.set_option(A.OPT_KERNEL, kernel)
+    a.forward(eps, rec)
+    blob = a.save_state()
+    ga = a.backward().cpu().numpy()
+    b = F.Simulation(w)
+    b.set_option(A.OPT_KERNEL, kernel)
+    b.load_state(blob, rec)
+    np.testing.assert_array_equal(b.objective_history(), a.objective_history())
+    gb = b.backward().cpu().numpy()
+    np.testing.assert_array_equal(gb, ga)
+
+
 @pytest.mark.parametrize("graphs", [0, 1])
 def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     w = SMALL["ragged_poynting"]()
