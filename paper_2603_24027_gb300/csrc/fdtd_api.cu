@@ -1526,6 +1526,7 @@ extern "C" int fdtd_load_state(fdtd_handle* h, const void* host_buf, size_t byte
   if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this state");
   rc = begin(h);
   if (rc) return rc;
+  CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, h->stream));   // as a forward leaves it
   const char* in = (const char*)host_buf + sizeof hd;
   const size_t dst[6] = {L.F[0], L.cb, L.tape, L.scales, L.obj, L.obj2};
   h->obj_hist.assign(h->N, 0.0);
