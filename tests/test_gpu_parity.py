@@ -612,6 +612,30 @@ def test_exact_reversal_on_the_benchmark_grid(F, A):
     assert err < rounding_bound(w, q)
 
 
+def test_large_grid_properties_at_full_size(F, A):
+    """The 600 x 600 x 300 grid (108 M cells, 16-cell CPML) in the default
+    launch configuration, 80 steps of an early pulse with the BF16 k = 4
+    tape of the benchmark: the compact auxiliary layout gives the same fields
+    bit for bit and the same gradient as the full-grid layout in less memory,
+    and with exact reversal (FP32 k = 1 tape) the interior returns to zero
+    bit for bit."""
+    w = I.waveguide_large(n_steps=80).replace(t0_over_tau=0.3, det_index=60)
+    rec = A.record_cfg("bf16", 4, "linear")
+    a = gpu_run(F, A, w, rec=rec)
+    b = gpu_run(F, A, w, rec=rec, options={A.OPT_COMPACT_AUX: 0})
+    np.testing.assert_array_equal(a["fields"], b["fields"])
+    assert np.abs(a["g"]).max() > 0
+    same_gradient(a["g"], b["g"])
+    assert a["sim"].workspace_bytes(rec) < b["sim"].workspace_bytes(rec)
+    del a, b
+    r = gpu_run(F, A, w, options={A.OPT_EXACT_REVERSAL: 22})
+    back = r["sim"].read_fields().cpu().numpy()
+    P = w.pml_thickness
+    interior = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    assert np.abs(r["fields"][interior]).max() > 0
+    assert not np.any(back[interior])
+
+
 def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
     """The 200 x 200 x 100 benchmark grid in the default launch configuration,
     shortened to 100 steps so that the FP64 oracle computes every output: the
