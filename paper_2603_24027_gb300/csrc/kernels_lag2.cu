@@ -136,30 +136,15 @@ constexpr int min_ctas(bool fwd) {
   return (TY == 8 && S == 2 && TW == 32) ? (fwd ? 8 : 5) : 1;
 }
 
-// The ring's barriers after the S stages: "full" barriers 0..S-1 complete
-// when a stage's copies have landed; "empty" barriers S..2S-1 when every warp
-// of the CTA has finished reading the stage, after which the producer (thread
-// 0) may fill it again.  No CTA-wide barrier is needed per plane.
 template <int S>
 __device__ __forceinline__ uint64_t* ring_init(unsigned char* dsm, int stage_bytes) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + S * stage_bytes);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const int warps = (blockDim.x * blockDim.y + 31) / 32;
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&bars[s], 1);
-      mbar_init(&bars[S + s], warps);
-    }
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
   }
   __syncthreads();
   return bars;
-}
-
-// The warp is done with the stage: one arrival (its lane 0, tid = linear
-// thread index) on the stage's empty barrier.
-__device__ __forceinline__ void ring_release(uint64_t* bars, int S_, int stg, int tid) {
-  __syncwarp();
-  if ((tid & 31) == 0) mbar_arrive(bars + S_ + stg);
 }
 
 // A wait for plane p (stage stg, parity par) gave up: record the timeout and
@@ -240,9 +225,11 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   float c_hz[2] = {0.f, 0.f}, c_pz0[2] = {0.f, 0.f}, c_pz1[2] = {0.f, 0.f};
   int stg = 0;
   uint32_t par = 0;
+  bool ok = true;
   for (int p = k0; p <= k1; ++p) {
     unsigned char* st = dsm + stg * Y::STAGE;
-    if (!mbar_wait(bars + stg, par, kWaitCycles)) { ring_abort<S>(bars, stg, par, p, k1, a.err); return; }
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, k1, a.err); return; }
     const float* Eb = reinterpret_cast<const float*>(st + Y::E);
     if (v0) {
       const float2 ex2 = ld2(Eb, hb), ey2 = ld2(Eb + B::P, hb);
@@ -340,15 +327,8 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
         }
       }
     }
-    ring_release(bars, S, stg, tid);
-    if (tid == 0 && p + S <= k1) {   // refill the stage once every warp is done with it
-      if (!mbar_wait(bars + S + stg, par, kWaitCycles)) {   // planes p+1 .. p+S-1 are in flight
-        const int ns = stg + 1 == S ? 0 : stg + 1;
-        ring_abort<S>(bars, ns, ns ? par : par ^ 1u, p + 1, min(k1, p + S - 1), a.err);
-        return;
-      }
-      issue(p + S, st, bars + stg);
-    }
+    __syncthreads();
+    if (tid == 0 && p + S <= k1) issue(p + S, st, bars + stg);
     if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }
@@ -371,6 +351,7 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   // plane k0-1 only provides Ht(k0-1) at the own pair
   const int p0_ = k0 - 1, p1_ = k1 - 1;
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);
+  double* red = reinterpret_cast<double*>(dsm + S * Y::STAGE + 8 * S + 64);
   int qx0, qy0;
   psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
   auto boxes = [&](int p, auto&& f) {
@@ -410,9 +391,11 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   double lsum = 0.0;
   int stg = 0;
   uint32_t par = 0;
+  bool ok = true;
   for (int p = p0_; p <= p1_; ++p) {
     unsigned char* st = dsm + stg * Y::STAGE;
-    if (!mbar_wait(bars + stg, par, kWaitCycles)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
     const float* Hb = reinterpret_cast<const float*>(st + Y::H);
     if (v0) {
       const float2 hx2 = ld2(Hb, lb), hy2 = ld2(Hb + B::P, lb), hz2 = ld2(Hb + 2 * B::P, lb);
@@ -546,21 +529,20 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
       c_hx[0] = hx[0]; c_hx[1] = hx[1];
       c_hy[0] = hy[0]; c_hy[1] = hy[1];
     }
-    ring_release(bars, S, stg, tid);
-    if (tid == 0 && p + S <= p1_) {   // refill the stage once every warp is done with it
-      if (!mbar_wait(bars + S + stg, par, kWaitCycles)) {   // planes p+1 .. p+S-1 are in flight
-        const int ns = stg + 1 == S ? 0 : stg + 1;
-        ring_abort<S>(bars, ns, ns ? par : par ^ 1u, p + 1, min(p1_, p + S - 1), a.err);
-        return;
-      }
-      issue(p + S, st, bars + stg);
-    }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
     if (++stg == S) { stg = 0; par ^= 1u; }
   }
-  if (a.det.kind) {   // one FP64 reduction per warp (no CTA-wide barrier after the ring)
+  if (a.det.kind) {
     double v = lsum;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0 && v != 0.0) atomicAdd(a.obj, v);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int wv = 0; wv < (TW / 2 * TY) / 32; ++wv) t += red[wv];
+      if (t != 0.0) atomicAdd(a.obj, t);
+    }
   }
 }
 
@@ -645,9 +627,11 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
   float c_bx[2] = {0.f, 0.f}, c_by[2] = {0.f, 0.f};
   int stg = 0;
   uint32_t par = 0;
+  bool ok = true;
   for (int p = p0_; p <= p1_; ++p) {
     unsigned char* st = dsm + stg * Y::STAGE;
-    if (!mbar_wait(bars + stg, par, kWaitCycles)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
     if (v0) {
       const float* CBb = reinterpret_cast<const float*>(st + Y::CB);
       const float* LEb = reinterpret_cast<const float*>(st + Y::LE);
@@ -872,15 +856,8 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
             true, v1);
       }
     }
-    ring_release(bars, S, stg, tid);
-    if (tid == 0 && p + S <= p1_) {   // refill the stage once every warp is done with it
-      if (!mbar_wait(bars + S + stg, par, kWaitCycles)) {   // planes p+1 .. p+S-1 are in flight
-        const int ns = stg + 1 == S ? 0 : stg + 1;
-        ring_abort<S>(bars, ns, ns ? par : par ^ 1u, p + 1, min(p1_, p + S - 1), a.err);
-        return;
-      }
-      issue(p + S, st, bars + stg);
-    }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
     if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }
@@ -959,9 +936,11 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
   bool c_pr0 = false, c_pr1 = false;   // primal Ht(p-1) pending per cell
   int stg = 0;
   uint32_t par = 0;
+  bool ok = true;
   for (int p = p0_; p <= p1_; ++p) {
     unsigned char* st = dsm + stg * Y::STAGE;
-    if (!mbar_wait(bars + stg, par, kWaitCycles)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
+    if (!mbar_wait(bars + stg, par, kWaitCycles)) ok = false;
+    if (!__syncthreads_and(ok)) { ring_abort<S>(bars, stg, par, p, p1_, a.err); return; }
     if (v0) {
       const float* Eb = reinterpret_cast<const float*>(st + Y::E);
       if (p > k0 && (c_pr0 || c_pr1)) {  // finish the primal Ht(p-1) with dEy/dz, dEx/dz
@@ -1128,15 +1107,8 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
         }
       }
     }
-    ring_release(bars, S, stg, tid);
-    if (tid == 0 && p + S <= p1_) {   // refill the stage once every warp is done with it
-      if (!mbar_wait(bars + S + stg, par, kWaitCycles)) {   // planes p+1 .. p+S-1 are in flight
-        const int ns = stg + 1 == S ? 0 : stg + 1;
-        ring_abort<S>(bars, ns, ns ? par : par ^ 1u, p + 1, min(p1_, p + S - 1), a.err);
-        return;
-      }
-      issue(p + S, st, bars + stg);
-    }
+    __syncthreads();
+    if (tid == 0 && p + S <= p1_) issue(p + S, st, bars + stg);
     if (++stg == S) { stg = 0; par ^= 1u; }
   }
 }

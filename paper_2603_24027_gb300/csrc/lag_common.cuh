@@ -102,7 +102,7 @@ struct LFH {
   static constexpr int PY = PX + r128(2 * g_::OP * 4);
   static constexpr int PZ = PY + r128(2 * g_::OP * 4);
   static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 16 * S; }
+  static int smem() { return S * STAGE + 8 * S; }
 };
 
 // Forward E half-step: Ht lo box, E and cb own, psi_E own boxes; a small
@@ -117,7 +117,7 @@ struct LFE {
   static constexpr int PY = PX + r128(2 * g_::OP * 4);
   static constexpr int PZ = PY + r128(2 * g_::OP * 4);
   static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 16 * S + 256; }
+  static int smem() { return S * STAGE + 8 * S + 256; }
 };
 
 // Reverse E phase: Ht lo box, E own, cb and lam_E hi boxes, lam_H own,
@@ -134,7 +134,7 @@ struct LRE {
   static constexpr int PY = PX + r128(2 * g_::XP * 4);         // lam_psi_E y: 32 x (TY+1) at (x0, y0)
   static constexpr int PZ = PY + r128(2 * g_::YP * 4);         // lam_psi_E z: own
   static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 16 * S; }
+  static int smem() { return S * STAGE + 8 * S; }
 };
 
 // Reverse H phase: E hi box, Ht own, lam_H lo box, lam_E own, lam_psi_H
@@ -150,7 +150,7 @@ struct LRH {
   static constexpr int PY = PX + r128(2 * g_::XP * 4);         // lam_psi_H y: 32 x (TY+1) at (x0, y0-1)
   static constexpr int PZ = PY + r128(2 * g_::YP * 4);         // lam_psi_H z: own
   static constexpr int STAGE = PZ + r128(2 * g_::OP * 4);
-  static int smem() { return S * STAGE + 16 * S; }
+  static int smem() { return S * STAGE + 8 * S; }
 };
 
 }  // namespace fdtd
