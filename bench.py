@@ -356,6 +356,9 @@ def run_ours(args):
                    "design_box": list(w.design_shape[::-1]),
                    "parallelism": f"replicas x{ws}", "l2": "flushed before every timed step",
                    "fwd_ms": statistics.median(fwd_ms), "bwd_ms": statistics.median(bwd_ms),
+                   # forward-only and reverse-only rates (cells x steps / phase time)
+                   "fwd_gcell_updates_per_s": w.n_cells * w.n_steps / statistics.median(fwd_ms) / 1e6,
+                   "bwd_gcell_updates_per_s": w.n_cells * w.n_steps / statistics.median(bwd_ms) / 1e6,
                    "wall_s": wall},
         "gpu_launches": gpu_launches,
         "roofline": roofline,
