@@ -656,3 +656,21 @@ def test_bdct_keeps_smooth_fields_and_drops_fine_detail():
     c, s = O.bdct_encode(hf, 10)
     # what is left is the float32 rounding of the kept coefficients (~1e-7)
     assert np.abs(O.bdct_decode(c, s, 48, 32)).max() < 1e-5
+
+
+def test_bdct_single_coefficient_is_the_block_mean():
+    """K = 1 keeps the DC term only: C_0 = 8 mean(block), coded as +-127 with
+    s = |C_0| / 127, so every decoded cell is C_0 / 8 = the block mean (to
+    float32 rounding); on a ragged plane the mean is over the block with its
+    edge cells repeated."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((13, 21)).astype(np.float32)
+    codes, s = O.bdct_encode(x, 1)
+    y = O.bdct_decode(codes, s, 21, 13)
+    xp = np.pad(x.astype(np.float64), ((0, 3), (0, 3)), mode="edge")
+    for bv in range(2):
+        for bu in range(3):
+            m = xp[8 * bv:8 * bv + 8, 8 * bu:8 * bu + 8].mean()
+            blk = y[8 * bv:min(8 * bv + 8, 13), 8 * bu:min(8 * bu + 8, 21)]
+            np.testing.assert_allclose(blk, m, rtol=1e-5, atol=1e-6)
+            assert abs(codes[bv * 3 + bu, 0]) == 127
