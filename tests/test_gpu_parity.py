@@ -254,13 +254,14 @@ def test_checkpoint_resumes_the_backward_in_another_handle(F, A, kernel, tape):
     np.testing.assert_array_equal(gb, ga)
 
 
-@pytest.mark.parametrize("nx,ny,nz,tile_x", [(70, 38, 15, 32), (69, 37, 14, 32), (70, 38, 15, 40),
-                                             (71, 39, 16, 40)])
+@pytest.mark.parametrize("nx,ny,nz,tile_x", [(70, 38, 16, 32), (69, 37, 16, 32), (70, 38, 17, 40),
+                                             (69, 39, 16, 40)])
 def test_compact_auxiliaries_at_the_eligibility_thresholds(F, A, nx, ny, nz, tile_x):
-    """7-cell CPML: x is compacted from nx = 2P + 56 = 70, y from ny = 2P + 24 =
-    38, z from nz = 2P + 1 = 15; one cell less keeps the axis full.  Grids
-    at and just below each threshold, 32- and 40-wide tiles: the fields equal
-    the full-grid layout's bit for bit and the gradient agrees."""
+    """7-cell CPML: x is compacted from nx = 2P + 56 = 70 and y from ny = 2P +
+    24 = 38, one cell less keeps the axis full (z from 2P + 1, below the
+    smallest valid grid, 2P + 2).  Grids at and just below each threshold,
+    32- and 40-wide tiles: the fields equal the full-grid layout's bit for
+    bit and the gradient agrees."""
     w = I.ragged_box(nx=nx, ny=ny, nz=nz, P=7, n_steps=50)
     rec = A.record_cfg("bf16", 2, "linear")
     opts = {A.OPT_TILE_X: tile_x, A.OPT_STAGES: 2}
