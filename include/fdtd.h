@@ -253,8 +253,10 @@ enum {
                                    or tile shapes than kernel 5's defaults (32 x 8 tiles,
                                    2 stages) with q != 0: FDTD_EINVAL at fdtd_forward */
   FDTD_OPT_ZCHUNK_FWD = 12      /* kernel 5: z planes per CTA of the forward half-steps
-                                   (default 8; 0 = the whole column); FDTD_OPT_ZCHUNK then
-                                   sets the reverse phases (and every other kernel) */
+                                   (0 = the whole column; -1, the default: 16 when that grid
+                                   of CTAs fits in about one wave of resident CTAs, else
+                                   FDTD_OPT_ZCHUNK); FDTD_OPT_ZCHUNK sets the reverse phases
+                                   (and every other kernel) */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

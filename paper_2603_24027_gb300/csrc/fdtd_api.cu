@@ -573,7 +573,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_kernel = 5;
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
-  h->opt_zchunk_fwd = 8;
+  h->opt_zchunk_fwd = -1;
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
@@ -702,7 +702,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       h->opt_compact = value ? 1 : 0;
       break;
     case FDTD_OPT_ZCHUNK_FWD:
-      if (value < 0) return fail(h, FDTD_EINVAL, "zchunk must be >= 0");
+      if (value < -1) return fail(h, FDTD_EINVAL, "forward zchunk must be >= -1");
       h->opt_zchunk_fwd = value;
       break;
     case FDTD_OPT_EXACT_REVERSAL:
@@ -823,6 +823,28 @@ static Det det_of(const fdtd_detector& d) {
 }
 
 static Det det2_of(const fdtd_handle* h) { return det_of(h->det2); }
+
+// z chunk of kernel 5's forward half-steps.  Automatic (-1): 16 planes when
+// the 16-plane grid of CTAs fits in about one wave of resident CTAs (8 per SM
+// for these kernels), else the reverse phases' chunk: on small grids the
+// longer chunks halve the halo planes and the ramps without adding a second
+// wave (measured: 3 % faster forward on 200 x 200 x 100, 1 % slower on
+// 600 x 600 x 300 where the rule keeps 8).
+static int forward_zchunk(const fdtd_handle* h, const StepArgs& a) {
+  if (h->opt_zchunk_fwd == 0) return h->nz;
+  if (h->opt_zchunk_fwd > 0) return h->opt_zchunk_fwd;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      sms = n;
+  }
+  const long long tiles = (long long)((h->nx + a.tile_x - 1) / a.tile_x) *
+                          ((h->ny + a.tile_y - 1) / a.tile_y);
+  const long long units16 = tiles * ((h->nz + 15) / 16);
+  return sms > 0 && units16 * 20 <= 8LL * sms * 21 ? 16 : a.zchunk;
+}
 
 // Kernels 1, 2 and 6 run the forward step as one ping-pong launch.
 static bool fused_forward(const fdtd_handle* h) {
@@ -951,7 +973,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   Layout L = layout_of(h, rec);
   StepArgs a = step_args(h, L);
   a.pl = L.plF;
-  if (h->opt_kernel == 5) a.zchunk = h->opt_zchunk_fwd > 0 ? h->opt_zchunk_fwd : h->nz;
+  if (h->opt_kernel == 5) a.zchunk = forward_zchunk(h, a);
   size_t nc6 = 6 * (size_t)a.g.nc * sizeof(float);
   size_t psb = (size_t)L.plF.total * sizeof(float);
   cudaError_t e;

@@ -33,7 +33,8 @@ def main(argv=None):
     p.add_argument("--prefetch", type=int, default=0)
     p.add_argument("--tile-x", type=int, default=32)
     p.add_argument("--compact", type=int, default=1)
-    p.add_argument("--zchunk-fwd", type=int, default=-1, help="-1: same as --zchunk")
+    p.add_argument("--zchunk-fwd", type=int, default=-2,
+                   help="-2: same as --zchunk, -1: the library's automatic choice")
     p.add_argument("--tape", default="bf16:4:linear")
     p.add_argument("--pml", type=int, default=0)
     p.add_argument("--warmup", type=int, default=0)
@@ -63,7 +64,7 @@ def main(argv=None):
     sim.set_option(A.OPT_PREFETCH, a.prefetch)
     sim.set_option(A.OPT_TILE_X, a.tile_x)
     sim.set_option(A.OPT_COMPACT_AUX, a.compact)
-    sim.set_option(A.OPT_ZCHUNK_FWD, a.zchunk if a.zchunk_fwd < 0 else a.zchunk_fwd)
+    sim.set_option(A.OPT_ZCHUNK_FWD, a.zchunk if a.zchunk_fwd == -2 else a.zchunk_fwd)
     sim.set_option(A.OPT_SAMPLE_EVERY, a.sample_every)
     sim.set_option(A.OPT_USE_GRAPHS, 0 if a.no_graphs else 1)
     eps = torch.from_numpy(w.eps).cuda()
