@@ -252,11 +252,25 @@ enum {
                                    0 (default) = plain float32 increments.  Other kernels
                                    or tile shapes than kernel 5's defaults (32 x 8 tiles,
                                    2 stages) with q != 0: FDTD_EINVAL at fdtd_forward */
-  FDTD_OPT_ZCHUNK_FWD = 12      /* kernel 5: z planes per CTA of the forward half-steps
-                                   (0 = the whole column; -1, the default: 16 when that grid
-                                   of CTAs fits in about one wave of resident CTAs, else
+  FDTD_OPT_ZCHUNK_FWD = 12,     /* kernel 5: z planes per CTA of the forward half-steps
+                                   (0 = the whole column; -1, the default: FDTD_OPT_ZCHUNK
+                                   when the forward runs in z groups, as it does by default;
+                                   with one launch per half-step, 16 when that grid of CTAs
+                                   fits in about one wave of resident CTAs, else
                                    FDTD_OPT_ZCHUNK); FDTD_OPT_ZCHUNK sets the reverse phases
                                    (and every other kernel) */
+  FDTD_OPT_ZGROUPS = 13         /* kernel 5: G in 0..16; G > 1 splits every half-step launch
+                                   into G launches over consecutive ranges of its z chunks,
+                                   each on its own stream and waiting only for the
+                                   neighbouring ranges of the half-step before, so that
+                                   one half-step's tail overlaps the next one's start
+                                   (tape, restore and monitor launches join all ranges);
+                                   results are unchanged.  0 (default) = automatic: 4 in
+                                   the forward, 3 in the reverse; 1 = one launch per
+                                   half-step.  Sampled kernel timing
+                                   (FDTD_OPT_SAMPLE_EVERY) records only loops that run
+                                   with one launch per half-step; the no-allocation entry
+                                   point always runs that way */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);

@@ -40,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs, zchunk_fwd;
+      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -85,7 +85,13 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd;
+      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
+  // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
+  // three events (the last launch of an even / odd phase, the join), plus the
+  // fork event
+  std::vector<cudaStream_t> zs;
+  std::vector<cudaEvent_t> zev;
+  cudaEvent_t zfork;
   // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
   FwdMaps fmaps[2];
   char* maps_ws;
@@ -108,6 +114,7 @@ struct fdtd_handle {
   std::string err;
 };
 
+static const int kMaxZGroups = 16;
 static std::string g_create_error;
 
 static int fail(fdtd_handle* h, int code, const std::string& msg) {
@@ -574,6 +581,8 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_zchunk_fwd = -1;
+  h->opt_zgroups = 0;
+  h->zfork = nullptr;
   h->opt_sample = 0;
   h->opt_rows = 1;
   h->opt_stages = 2;
@@ -618,6 +627,9 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
     cudaEventDestroy(h->ev_in); cudaEventDestroy(h->ev_out);
     cudaEventDestroy(h->t0); cudaEventDestroy(h->t1);
     cudaEventDestroy(h->t2); cudaEventDestroy(h->t3);
+    for (cudaEvent_t ev : h->zev) cudaEventDestroy(ev);
+    for (cudaStream_t st : h->zs) cudaStreamDestroy(st);
+    if (h->zfork) cudaEventDestroy(h->zfork);
     cudaStreamDestroy(h->stream);
   }
   delete h;
@@ -705,6 +717,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < -1) return fail(h, FDTD_EINVAL, "forward zchunk must be >= -1");
       h->opt_zchunk_fwd = value;
       break;
+    case FDTD_OPT_ZGROUPS:
+      if (value < 0 || value > kMaxZGroups) return fail(h, FDTD_EINVAL, "zgroups must be 0..16");
+      h->opt_zgroups = value;
+      break;
     case FDTD_OPT_EXACT_REVERSAL:
       if (value != 0 && (value < 8 || value > 30))
         return fail(h, FDTD_EINVAL, "exact reversal: q must be 0 or 8..30");
@@ -732,6 +748,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
     case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
     case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
+    case FDTD_OPT_ZGROUPS: *value = h->opt_zgroups; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -824,15 +841,28 @@ static Det det_of(const fdtd_detector& d) {
 
 static Det det2_of(const fdtd_handle* h) { return det_of(h->det2); }
 
-// z chunk of kernel 5's forward half-steps.  Automatic (-1): 16 planes when
-// the 16-plane grid of CTAs fits in about one wave of resident CTAs (8 per SM
-// for these kernels), else the reverse phases' chunk: on small grids the
-// longer chunks halve the halo planes and the ramps without adding a second
-// wave (measured: 3 % faster forward on 200 x 200 x 100, 1 % slower on
+// z groups of kernel 5's half-steps in direction dir (0 forward, 1 reverse).
+// Automatic (0): 4 in the forward and 3 in the reverse, the fastest counts on
+// both 200 x 200 x 100 and 600 x 600 x 300 (the reverse phases join at every
+// step's restore, so only two phases overlap there).
+static int zgroups_of(const fdtd_handle* h, int dir) {
+  if (h->opt_kernel != 5) return 1;
+  if (h->opt_zgroups > 0) return h->opt_zgroups;
+  return dir == 0 ? 4 : 3;
+}
+
+// z chunk of kernel 5's forward half-steps.  Automatic (-1): with z groups
+// the reverse phases' chunk (8 planes by default: 7 % faster than one launch
+// per half-step on 200 x 200 x 100); without, 16 planes when the 16-plane
+// grid of CTAs fits in about one wave of resident CTAs (8 per SM for these
+// kernels), else the reverse phases' chunk: on small grids the longer chunks
+// halve the halo planes and the ramps without adding a second wave
+// (measured: 3 % faster forward on 200 x 200 x 100, 1 % slower on
 // 600 x 600 x 300 where the rule keeps 8).
 static int forward_zchunk(const fdtd_handle* h, const StepArgs& a) {
   if (h->opt_zchunk_fwd == 0) return h->nz;
   if (h->opt_zchunk_fwd > 0) return h->opt_zchunk_fwd;
+  if (zgroups_of(h, 0) > 1) return a.zchunk;
   static int sms = 0;
   if (!sms) {
     int dev = 0, n = 0;
@@ -964,6 +994,83 @@ static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
   }
 }
 
+// z-group scheduling of the two-cells-per-thread half-steps (FDTD_OPT_ZGROUPS):
+// each half-step launch is split into G launches over consecutive ranges of its
+// z chunks, group g on its own stream.  A half-step reads what the previous one
+// wrote at most one plane beyond its own cells, and a chunk range spans at least
+// one plane, so group g of a phase waits only for groups g - 1 and g + 1 of the
+// phase before (and for its own through stream order); the tail of one phase
+// then overlaps the start of the next.  Launches that read or write whole faces
+// (tape record and restore, the second detector's monitor) run on the main
+// stream between a join of all groups and a fork.
+struct ZGroups {
+  fdtd_handle* h;
+  int G = 1, nch = 1, par = 0;
+  bool forked = false, prev = false;
+  ZGroups(fdtd_handle* h_, bool on, int dir, const StepArgs& a) : h(h_) {
+    nch = (a.g.nz + a.zchunk - 1) / a.zchunk;
+    const int want = zgroups_of(h, dir);
+    if (on && want > 1 && (int)h->zs.size() >= want) G = std::min(want, nch);
+  }
+  bool active() const { return G > 1; }
+  cudaEvent_t ev(int slot, int g) const { return h->zev[(size_t)g * 3 + slot]; }
+  cudaError_t fork() {
+    if (!active()) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(h->zfork, h->stream);
+    for (int g = 0; !e && g < G; ++g) e = cudaStreamWaitEvent(h->zs[g], h->zfork, 0);
+    forked = true;
+    prev = false;
+    return e;
+  }
+  cudaError_t join() {
+    if (!active() || !forked) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; !e && g < G; ++g) {
+      e = cudaEventRecord(ev(2, g), h->zs[g]);
+      if (!e) e = cudaStreamWaitEvent(h->stream, ev(2, g), 0);
+    }
+    forked = false;
+    return e;
+  }
+  template <class Launch>
+  cudaError_t phase(Launch launch, StepArgs a) {
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < G; ++g) {
+      cudaStream_t st = h->zs[g];
+      if (prev && g > 0 && (e = cudaStreamWaitEvent(st, ev(par ^ 1, g - 1), 0))) return e;
+      if (prev && g + 1 < G && (e = cudaStreamWaitEvent(st, ev(par ^ 1, g + 1), 0))) return e;
+      a.zc0 = (int)((long long)g * nch / G);
+      a.zc1 = (int)((long long)(g + 1) * nch / G);
+      if ((e = launch(a, st))) return e;
+      if ((e = cudaEventRecord(ev(par, g), st))) return e;
+    }
+    par ^= 1;
+    prev = true;
+    return e;
+  }
+};
+
+// Streams and events of the z-group scheduling of direction dir (created as
+// needed, outside a capture).
+static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
+  const int want = zgroups_of(h, dir);
+  if (want <= 1 || (int)h->zs.size() >= want) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (!h->zfork) e = cudaEventCreateWithFlags(&h->zfork, cudaEventDisableTiming);
+  while (!e && (int)h->zs.size() < want) {
+    cudaStream_t st;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e) break;
+    h->zs.push_back(st);
+    for (int i = 0; !e && i < 3; ++i) {
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (!e) h->zev.push_back(ev);
+    }
+  }
+  return e;
+}
+
 static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_FUSED_FWD,
                                 FDTD_K_MONITOR};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_FUSED_REV};
@@ -1031,6 +1138,9 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
     return e;
   Sampler smp(h, 0);
+  ZGroups zg(h, pair && !fused, 0, a);
+  if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
+  if ((e = zg.fork())) return e;
   for (int n = 0; n < h->N; ++n) {
     a.jn = h->wave[n];
     a.obj = (double*)(h->ws + L.obj) + n;
@@ -1065,30 +1175,51 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
       continue;
     }
     if ((e = smp.before(FDTD_K_FWD_H))) return e;
-    if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream) : launch_lag(0, lmaps, a, h->stream))
-                  : split_tma ? launch_split_tma(0, smaps, a, h->stream) : launch_fwd_h(a, h->stream)))
+    if (zg.active()) {
+      if ((e = zg.phase([&](const StepArgs& b, cudaStream_t st) {
+             return launch_lag2(0, lmaps, b, st); }, a)))
+        return e;
+      nl += zg.G - 1;
+    } else if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream)
+                                 : launch_lag(0, lmaps, a, h->stream))
+                         : split_tma ? launch_split_tma(0, smaps, a, h->stream)
+                                     : launch_fwd_h(a, h->stream))) {
       return e;
+    }
     if ((e = smp.after(FDTD_K_FWD_H))) return e;
     ++nl;
     if (rec_now) {
+      if ((e = zg.join())) return e;
       if ((e = smp.before(FDTD_K_RECORD))) return e;
       if ((e = record(a.F, a.F, j))) return e;
       if ((e = smp.after(FDTD_K_RECORD))) return e;
+      if ((e = zg.fork())) return e;
       ++nl;
     }
     if ((e = smp.before(FDTD_K_FWD_E))) return e;
-    if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream) : launch_lag(1, lmaps, a, h->stream))
-                  : split_tma ? launch_split_tma(1, smaps, a, h->stream) : launch_fwd_e(a, h->stream)))
+    if (zg.active()) {
+      if ((e = zg.phase([&](const StepArgs& b, cudaStream_t st) {
+             return launch_lag2(1, lmaps, b, st); }, a)))
+        return e;
+      nl += zg.G - 1;
+    } else if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream)
+                                 : launch_lag(1, lmaps, a, h->stream))
+                         : split_tma ? launch_split_tma(1, smaps, a, h->stream)
+                                     : launch_fwd_e(a, h->stream))) {
       return e;
+    }
     if ((e = smp.after(FDTD_K_FWD_E))) return e;
     ++nl;
     if (det2.kind) {
+      if ((e = zg.join())) return e;
       if ((e = smp.before(FDTD_K_MONITOR))) return e;
       if ((e = launch_monitor(a.F, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream))) return e;
       if ((e = smp.after(FDTD_K_MONITOR))) return e;
+      if ((e = zg.fork())) return e;
       ++nl;
     }
   }
+  if ((e = zg.join())) return e;
   h->fwd_buf = cur;
   *launches = nl;
   return cudaSuccess;
@@ -1130,7 +1261,10 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   const BdctLayout bl =
       rec->dtype == kTapeBdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
   Sampler smp(h, 1);
+  ZGroups zg(h, rlag && rpair, 1, a);
+  if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
   for (int n = h->N - 1; n >= 0; --n) {
+    if ((e = zg.join())) return e;
     Interp ip;
     interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
@@ -1147,6 +1281,19 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.jn = h->wave[n];
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
+    if (zg.active()) {
+      const LagMaps& m = lrmaps[cur];
+      if ((e = zg.fork())) return e;
+      if ((e = zg.phase([&](const StepArgs& b, cudaStream_t st) {
+             return launch_lag2(2, m, b, st); }, a)))
+        return e;
+      if ((e = zg.phase([&](const StepArgs& b, cudaStream_t st) {
+             return launch_lag2(3, m, b, st); }, a)))
+        return e;
+      cur ^= 1;
+      nl += 1 + 2 * zg.G;
+      continue;
+    }
     if ((e = smp.before(FDTD_K_REV_E))) return e;
     if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
                          : launch_lag(2, lrmaps[cur], a, h->stream))
@@ -1162,6 +1309,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     cur ^= 1;
     nl += 3;
   }
+  if ((e = zg.join())) return e;
   *launches = nl;
   return cudaSuccess;
 }
@@ -1181,6 +1329,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
         h->spool[dir][e].push_back(ev);
       }
   }
+  CK(h, ensure_zgroups(h, dir));
   if (!h->opt_graphs) {
     CK(h, cudaEventRecord(ta, h->stream));
     cudaError_t e = fn(h, rec, launches);
@@ -1203,6 +1352,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.exact = h->opt_exact;
   key.coeffs = rec->coeffs;
   key.zchunk_fwd = h->opt_zchunk_fwd;
+  key.zgroups = h->opt_zgroups;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1685,16 +1835,17 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
   if (rc) return rc;
 
   // Run the usual time loops on the caller's stream with the scratch as the
-  // workspace: direct launches (no graph), no sampling events.
+  // workspace: direct launches (no graph), no sampling events, one stream.
   char* ws0 = h->ws;
   size_t b0 = h->ws_bytes;
   bool up0 = h->tables_uploaded;
   cudaStream_t s0 = h->stream;
-  int samp0 = h->opt_sample;
+  int samp0 = h->opt_sample, zg0 = h->opt_zgroups;   // no side streams here
   h->ws = (char*)scratch;
   h->ws_bytes = FDTD_NOALLOC_SCRATCH_BYTES;
   h->stream = h->user_stream;
   h->opt_sample = 0;
+  h->opt_zgroups = 1;
   h->have_forward = false;
   auto restore = [&]() {
     h->ws = ws0;
@@ -1702,6 +1853,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     h->tables_uploaded = up0;
     h->stream = s0;
     h->opt_sample = samp0;
+    h->opt_zgroups = zg0;
     h->have_forward = false;
   };
   auto run = [&]() -> int {

@@ -239,6 +239,7 @@ struct StepArgs {
   double* obj;     // per-step objective slot
   float jn;        // J waveform value of this step
   int zchunk;
+  int zc0, zc1;     // two-cells-per-thread kernels: z chunks [zc0, zc1) of this launch (zc1 = 0: to the last)
   int tile_y;
   int rows;        // tile rows per thread (TMA half-step kernels)
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)

@@ -182,7 +182,7 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
@@ -345,7 +345,7 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane k0-1 only provides Ht(k0-1) at the own pair
@@ -558,7 +558,7 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
   const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
@@ -874,7 +874,7 @@ k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
   const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = blockIdx.z * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
@@ -1143,7 +1143,10 @@ static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStr
 template <int TY, int S, int TW = 32, bool EX = false>
 static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   static_assert((TW / 2 * TY) % 32 == 0, "a CTA is a whole number of warps");
-  dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
+  const int nch = (a.g.nz + a.zchunk - 1) / a.zchunk;
+  const int zc1 = a.zc1 > 0 ? min(a.zc1, nch) : nch;
+  if (a.zc0 < 0 || a.zc0 >= zc1) return cudaErrorInvalidValue;
+  dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, zc1 - a.zc0);
   dim3 block(TW / 2, TY);
   switch (which) {
     case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);

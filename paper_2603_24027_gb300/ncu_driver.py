@@ -35,6 +35,8 @@ def main(argv=None):
     p.add_argument("--compact", type=int, default=1)
     p.add_argument("--zchunk-fwd", type=int, default=-2,
                    help="-2: same as --zchunk, -1: the library's automatic choice")
+    p.add_argument("--zgroups", type=int, default=1,
+                   help="split each half-step launch into this many z-chunk ranges")
     p.add_argument("--tape", default="bf16:4:linear")
     p.add_argument("--pml", type=int, default=0)
     p.add_argument("--warmup", type=int, default=0)
@@ -65,6 +67,7 @@ def main(argv=None):
     sim.set_option(A.OPT_TILE_X, a.tile_x)
     sim.set_option(A.OPT_COMPACT_AUX, a.compact)
     sim.set_option(A.OPT_ZCHUNK_FWD, a.zchunk if a.zchunk_fwd == -2 else a.zchunk_fwd)
+    sim.set_option(A.OPT_ZGROUPS, a.zgroups)
     sim.set_option(A.OPT_SAMPLE_EVERY, a.sample_every)
     sim.set_option(A.OPT_USE_GRAPHS, 0 if a.no_graphs else 1)
     eps = torch.from_numpy(w.eps).cuda()
@@ -73,7 +76,7 @@ def main(argv=None):
         g = sim.backward(1.0)
     torch.cuda.synchronize()
     out = dict(workload=w.name, steps=w.n_steps, pml=w.pml_thickness, kernel=a.kernel,
-               tile_y=a.tile_y, zchunk=a.zchunk, rows=a.rows, stages=a.stages, pdl=a.pdl, prefetch=a.prefetch, tile_x=a.tile_x, compact=a.compact, zchunk_fwd=a.zchunk_fwd, L=L, grad_l1=float(g.abs().sum()),
+               tile_y=a.tile_y, zchunk=a.zchunk, rows=a.rows, stages=a.stages, pdl=a.pdl, prefetch=a.prefetch, tile_x=a.tile_x, compact=a.compact, zchunk_fwd=a.zchunk_fwd, zgroups=a.zgroups, L=L, grad_l1=float(g.abs().sum()),
                timing=sim.last_timing(), kernels=sim.kernel_timing())
     print(json.dumps(out))
 

@@ -139,13 +139,14 @@ def test_options_are_validated(capi, fdtd):
     for opt, default in [(capi.OPT_KERNEL, 5), (capi.OPT_TILE_Y, 8), (capi.OPT_STAGES, 2),
                          (capi.OPT_USE_GRAPHS, 1), (capi.OPT_TILE_X, 32), (capi.OPT_PDL, 0),
                          (capi.OPT_PREFETCH, 0), (capi.OPT_COMPACT_AUX, 1),
-                         (capi.OPT_EXACT_REVERSAL, 0), (capi.OPT_ZCHUNK_FWD, -1)]:
+                         (capi.OPT_EXACT_REVERSAL, 0), (capi.OPT_ZCHUNK_FWD, -1),
+                         (capi.OPT_ZGROUPS, 0)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
                      (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_ROWS, 3),
                      (capi.OPT_ZCHUNK, -1), (capi.OPT_TILE_X, 0), (capi.OPT_TILE_X, 36),
                      (capi.OPT_ZCHUNK_FWD, -2), (capi.OPT_EXACT_REVERSAL, 5),
-                     (99, 1)]:
+                     (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (99, 1)]:
         assert lib.fdtd_set_option(sim.h, opt, val) == capi.FDTD_EINVAL
     assert lib.fdtd_set_option(sim.h, capi.OPT_STAGES, 4) == capi.FDTD_OK
     assert lib.fdtd_get_option(sim.h, capi.OPT_STAGES, C.byref(v)) == capi.FDTD_OK and v.value == 4

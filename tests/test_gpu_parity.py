@@ -163,6 +163,39 @@ def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y, rows, stages)
         same_gradient(r["g"], base["g"])
 
 
+@pytest.mark.parametrize("zgroups,zchunk,zfwd,tape,graphs", [
+    (2, 4, -1, "bf16:2", 1), (0, 3, -1, "f16:2", 0), (3, 2, 3, "f32:1", 1), (5, 1, 2, "bf16:3", 0),
+    (16, 4, 4, "e4m3:2", 1), (4, 8, 0, "bdct:2", 1)])
+def test_zgroups_do_not_change_results(F, A, zgroups, zchunk, zfwd, tape, graphs):
+    """Split half-step launches over z-chunk ranges on their own streams (the
+    scheduling only changes which launches may overlap): the same fields bit for
+    bit, the same gradient, including more groups than z chunks (16 on the
+    whole-column forward) and tape samples (record joins every group)."""
+    w = SMALL["ragged_poynting"]()
+    dt, k = tape.split(":")
+    rec = A.record_cfg(dt, int(k))
+    opts = {A.OPT_ZCHUNK: zchunk, A.OPT_ZCHUNK_FWD: zfwd, A.OPT_USE_GRAPHS: graphs}
+    base = gpu_run(F, A, w, rec=rec, options={**opts, A.OPT_ZGROUPS: 1})
+    r = gpu_run(F, A, w, rec=rec, options={**opts, A.OPT_ZGROUPS: zgroups})
+    np.testing.assert_array_equal(r["fields"], base["fields"])
+    np.testing.assert_allclose(r["hist"], base["hist"], rtol=1e-12, atol=1e-300)
+    same_gradient(r["g"], base["g"])
+    if tape == "f32:1":
+        L, g = O.gradient(w)
+        assert rel(r["g"], g) < 1e-4
+
+
+def test_zgroups_benchmark_grid_matches_single_launches(F, A):
+    """The 200 x 200 x 100 waveguide (400 steps, BF16 k = 4): the default z
+    groups leave the forward fields bit for bit and the gradient unchanged."""
+    w = I.waveguide().replace(n_steps=400)
+    rec = A.record_cfg("bf16", 4)
+    base = gpu_run(F, A, w, rec=rec, options={A.OPT_ZGROUPS: 1})
+    r = gpu_run(F, A, w, rec=rec)   # automatic: 4 groups forward, 3 reverse
+    np.testing.assert_array_equal(r["fields"], base["fields"])
+    same_gradient(r["g"], base["g"])
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16", "e4m3"])
 @pytest.mark.parametrize("scaled", [False, True])
 def test_codec_is_bit_exact_against_torch_casts(F, A, dtype, scaled):
@@ -289,8 +322,9 @@ def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
     add up to the measured loop times, and sampling does not change results."""
     w = I.waveguide_sweep(n_steps=200)
     rec = A.record_cfg("bf16", 4, "linear")
-    base = gpu_run(F, A, w, rec=rec)
-    r = gpu_run(F, A, w, rec=rec, options={A.OPT_SAMPLE_EVERY: 7})
+    one = {A.OPT_ZGROUPS: 1}   # sampling records loops with one launch per half-step
+    base = gpu_run(F, A, w, rec=rec, options=one)
+    r = gpu_run(F, A, w, rec=rec, options={**one, A.OPT_SAMPLE_EVERY: 7})
     np.testing.assert_array_equal(r["fields"], base["fields"])
     np.testing.assert_array_equal(r["g"], base["g"])
     sim = r["sim"]
