@@ -354,6 +354,14 @@ int fdtd_bdct_decode(const signed char* d_codes, const float* d_scales, int nu, 
  * not happen while the caller's stream is being captured. */
 int fdtd_bdct_basis(float* out);
 
+/* The z-chunk ranges of the z-group schedule (FDTD_OPT_ZGROUPS; host only,
+ * no device use): nch >= 1 z chunks split into min(G, nch) groups, G >= 1;
+ * group g covers chunks [lo[g], hi[g]) (lo, hi: caller arrays of at least
+ * min(G, nch) ints).  Returns the group count, or FDTD_EINVAL.  In the
+ * schedule, group g of a half-step waits for groups g - 1 and g + 1 of the
+ * half-step before (and for its own through stream order). */
+int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi);
+
 /* Self-test of the bounded device waits (failure detection without a
  * fault): one CTA arms an mbarrier for a copy that is never issued and waits
  * on it with the same bounded wait the TMA pipelines use, giving up after

@@ -115,6 +115,7 @@ _PROTOS = {
     "fdtd_state_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "fdtd_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "fdtd_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "fdtd_zgroup_ranges": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_selftest_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p]),
     "fdtd_value_and_grad_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                               C.c_double, C.POINTER(C.c_double), C.c_void_p]),

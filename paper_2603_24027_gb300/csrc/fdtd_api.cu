@@ -1003,6 +1003,13 @@ static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
 // then overlaps the start of the next.  Launches that read or write whole faces
 // (tape record and restore, the second detector's monitor) run on the main
 // stream between a join of all groups and a fork.
+// Chunks [lo, hi) of group g when nch z chunks are split into G <= nch groups
+// (every range non-empty).
+static void zgroup_range(int nch, int G, int g, int* lo, int* hi) {
+  *lo = (int)((long long)g * nch / G);
+  *hi = (int)((long long)(g + 1) * nch / G);
+}
+
 struct ZGroups {
   fdtd_handle* h;
   int G = 1, nch = 1, par = 0;
@@ -1039,8 +1046,7 @@ struct ZGroups {
       cudaStream_t st = h->zs[g];
       if (prev && g > 0 && (e = cudaStreamWaitEvent(st, ev(par ^ 1, g - 1), 0))) return e;
       if (prev && g + 1 < G && (e = cudaStreamWaitEvent(st, ev(par ^ 1, g + 1), 0))) return e;
-      a.zc0 = (int)((long long)g * nch / G);
-      a.zc1 = (int)((long long)(g + 1) * nch / G);
+      zgroup_range(nch, G, g, &a.zc0, &a.zc1);
       if ((e = launch(a, st))) return e;
       if ((e = cudaEventRecord(ev(par, g), st))) return e;
     }
@@ -1731,6 +1737,13 @@ extern "C" int fdtd_objective_history(fdtd_handle* h, double* out) {
   if ((int)h->obj_hist.size() != h->N) return fail(h, FDTD_ESTATE, "no forward run yet");
   memcpy(out, h->obj_hist.data(), h->N * sizeof(double));
   return FDTD_OK;
+}
+
+extern "C" int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi) {
+  if (nch < 1 || G < 1 || !lo || !hi) return FDTD_EINVAL;
+  const int n = std::min(G, nch);
+  for (int g = 0; g < n; ++g) zgroup_range(nch, n, g, &lo[g], &hi[g]);
+  return n;
 }
 
 extern "C" int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stream) {
