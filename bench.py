@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--sample-every", type=int, default=50)
     p.add_argument("--zgroups", type=int, default=0,
                    help="z groups per half-step (0: the library's automatic choice)")
+    p.add_argument("--autotune", action="store_true",
+                   help="tune the launch shapes first (autotune.tune, cached per GPU type)")
     p.add_argument("--cpu-sample-steps", type=int, default=24)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true")
@@ -279,6 +281,10 @@ def run_ours(args):
     sim.set_option(A.OPT_ZGROUPS, args.zgroups)
     eps = torch.from_numpy(w.eps).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tuned = None
+    if args.autotune:
+        from paper_2603_24027_gb300 import autotune
+        tuned = autotune.tune(sim, eps, rec)
 
     def barrier():
         if ws > 1:
@@ -322,6 +328,7 @@ def run_ours(args):
     # launch has no duration of its own there; the per-kernel costs come from a
     # sampled pass of the same steps with one launch per half-step (CUDA events
     # on the library stream, pair-minus-single intervals) right after them.
+    zgroups_timed = sim.get_option(A.OPT_ZGROUPS)
     sim.set_option(A.OPT_ZGROUPS, 1)
     sim.set_option(A.OPT_SAMPLE_EVERY, args.sample_every)
     step(sim, rec)                                 # capture the sampled graphs
@@ -335,7 +342,7 @@ def run_ours(args):
         for name, (ms, n) in sim.kernel_timing().items():
             ktimes.setdefault(name, []).append((ms, n))
     torch.cuda.synchronize()
-    sim.set_option(A.OPT_ZGROUPS, args.zgroups)
+    sim.set_option(A.OPT_ZGROUPS, zgroups_timed)
     sim.set_option(A.OPT_SAMPLE_EVERY, 0)
     one_step_ms = statistics.median(one_ms)
     algo = algorithmic_bytes(w)
@@ -382,6 +389,8 @@ def run_ours(args):
                    "design_box": list(w.design_shape[::-1]),
                    "parallelism": f"replicas x{ws}", "l2": "flushed before every timed step",
                    "zgroups": args.zgroups or "automatic (4 forward, 3 reverse)",
+                   "autotuned": None if tuned is None else
+                   {"options": tuned["options"], "cached": tuned["cached"]},
                    "fwd_ms": statistics.median(fwd_ms), "bwd_ms": statistics.median(bwd_ms),
                    "one_launch_per_half_step_ms": one_step_ms,
                    # forward-only and reverse-only rates (cells x steps / phase time)
