@@ -158,3 +158,46 @@ def test_unreadable_cache_is_empty(tmp_path):
     assert T.load_cache(str(tmp_path / "missing.json")) == {}
     T.save_entry(str(p), "k", {"options": {}})
     assert T.load_cache(str(p)) == {"k": {"options": {}}}
+
+
+def test_gpu_timing_wrapper_drives_a_trial_copy(tmp_path, monkeypatch):
+    """gpu_measure's own logic with the simulation class and the device
+    synchronisation replaced by fakes: the trial copy is shortened, inherits
+    the handle's fixed options, receives each candidate, and its loop times
+    (median of reps, after one untimed run) become the search's costs."""
+    import torch
+    from paper_2603_24027_gb300 import fdtd
+
+    made = []
+
+    class TrialSim(FakeSim):
+        def __init__(self, w, device=None):
+            super().__init__(w)
+            self.device, self.runs = device, 0
+            made.append(self)
+
+        def forward(self, eps, rec):
+            self.runs += 1
+
+        def backward(self, seed):
+            pass
+
+        def last_timing(self):
+            # forward cost falls with more z groups; the first (untimed) run is slow
+            g = self.opts[A.OPT_ZGROUPS]
+            slow = 100.0 if self.runs % 3 == 1 else 0.0
+            return {"fwd_ms": 10.0 - 0.5 * g + slow, "bwd_ms": 20.0}
+
+    monkeypatch.setattr(fdtd, "Simulation", TrialSim)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    w = I.ragged_box().replace(n_steps=500)
+    sim = FakeSim(w, opts={A.OPT_USE_GRAPHS: 1, A.OPT_ROWS: 1, A.OPT_PDL: 0,
+                           A.OPT_PREFETCH: 0, A.OPT_TILE_X: 40, A.OPT_COMPACT_AUX: 1})
+    eps = torch.zeros(1)
+    r = T.tune(sim, eps, A.record_cfg("bf16", 4), cache=str(tmp_path / "t.json"),
+               trial_steps=50, reps=2, gpu_name="GB300", max_passes=1)
+    (trial,) = made
+    assert trial.w.n_steps == 50 and trial.device == eps.device
+    assert trial.opts[A.OPT_TILE_X] == 40 and trial.opts[A.OPT_KERNEL] == 5
+    assert r["options"]["zgroups"] == 8 and sim.get_option(A.OPT_ZGROUPS) == 8
+    assert r["seconds"] == pytest.approx((10.0 - 4.0 + 20.0) / 1e3)
