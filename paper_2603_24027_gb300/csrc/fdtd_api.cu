@@ -994,6 +994,13 @@ static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
   }
 }
 
+// Chunks [lo, hi) of group g when nch z chunks are split into G <= nch groups
+// (every range non-empty).
+static void zgroup_range(int nch, int G, int g, int* lo, int* hi) {
+  *lo = (int)((long long)g * nch / G);
+  *hi = (int)((long long)(g + 1) * nch / G);
+}
+
 // z-group scheduling of the two-cells-per-thread half-steps (FDTD_OPT_ZGROUPS):
 // each half-step launch is split into G launches over consecutive ranges of its
 // z chunks, group g on its own stream.  A half-step reads what the previous one
@@ -1003,13 +1010,6 @@ static void collect_samples(fdtd_handle* h, int dir, const int* kinds, int nk) {
 // then overlaps the start of the next.  Launches that read or write whole faces
 // (tape record and restore, the second detector's monitor) run on the main
 // stream between a join of all groups and a fork.
-// Chunks [lo, hi) of group g when nch z chunks are split into G <= nch groups
-// (every range non-empty).
-static void zgroup_range(int nch, int G, int g, int* lo, int* hi) {
-  *lo = (int)((long long)g * nch / G);
-  *hi = (int)((long long)(g + 1) * nch / G);
-}
-
 struct ZGroups {
   fdtd_handle* h;
   int G = 1, nch = 1, par = 0;
@@ -1017,7 +1017,9 @@ struct ZGroups {
   ZGroups(fdtd_handle* h_, bool on, int dir, const StepArgs& a) : h(h_) {
     nch = (a.g.nz + a.zchunk - 1) / a.zchunk;
     const int want = zgroups_of(h, dir);
-    if (on && want > 1 && (int)h->zs.size() >= want) G = std::min(want, nch);
+    if (on && want > 1 && h->zfork && (int)h->zs.size() >= want &&
+        h->zev.size() >= 3 * h->zs.size())
+      G = std::min(want, nch);
   }
   bool active() const { return G > 1; }
   cudaEvent_t ev(int slot, int g) const { return h->zev[(size_t)g * 3 + slot]; }
@@ -1064,15 +1066,20 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
   cudaError_t e = cudaSuccess;
   if (!h->zfork) e = cudaEventCreateWithFlags(&h->zfork, cudaEventDisableTiming);
   while (!e && (int)h->zs.size() < want) {
+    // a stream joins the pool only with its three events
     cudaStream_t st;
+    cudaEvent_t evs[3] = {nullptr, nullptr, nullptr};
     e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e) break;
-    h->zs.push_back(st);
-    for (int i = 0; !e && i < 3; ++i) {
-      cudaEvent_t ev;
-      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (!e) h->zev.push_back(ev);
+    for (int i = 0; !e && i < 3; ++i) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+    if (e) {
+      for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+      cudaStreamDestroy(st);
+      break;
     }
+    h->zs.push_back(st);
+    h->zev.insert(h->zev.end(), evs, evs + 3);
   }
   return e;
 }
