@@ -6,7 +6,9 @@ single-kernel captures) and launch-shape sweeps.
 
 Runs one forward + backward (after one warm-up pair when --warmup 1) and
 prints the objective and per-kernel sampled timings.  --pml overrides the
-CPML thickness, to separate interior and absorbing-layer cost.
+CPML thickness, to separate interior and absorbing-layer cost.  It runs one
+launch per half-step unless --zgroups says otherwise (0: the library's
+automatic z groups), so that a captured launch covers the whole grid.
 """
 from __future__ import annotations
 
