@@ -217,21 +217,18 @@ int fdtd_backward2(fdtd_handle* h, double seed, double seed2, float* d_grad_eps)
 
 enum {
   FDTD_OPT_USE_GRAPHS = 0,    /* 1 (default): replay the time loop as a CUDA graph */
-  FDTD_OPT_KERNEL = 1,        /* 0: split half-steps (plain loads), 1: fused 2.5D forward
-                                 (plain loads), 2: fused forward with TMA staging, 3: split
-                                 half-steps with TMA staging, 4: TMA half-steps that read one
-                                 plane per iteration, 5 (default): the kernels of 4 with two
-                                 x-cells per thread (tile height at least 2), 6: one fused
-                                 launch per forward step (H and E half-steps, tile height 4
-                                 or 8) with the reverse of 5; 2 and 3 use the TMA reverse of
-                                 3, 0 and 1 the plain reverse */
+  FDTD_OPT_KERNEL = 1,        /* 5 (default): half-steps that stage one z plane per iteration
+                                 in shared memory with TMA box loads (two x-cells per thread,
+                                 tile height at least 2); 0: the same half-steps with plain
+                                 global loads, one cell per thread (an independent
+                                 cross-check; the tiling, staging and z-group options do not
+                                 apply to it).  Other values: FDTD_EINVAL */
   FDTD_OPT_TILE_Y = 2,        /* CTA tile height in cells (1, 2, 4, 8 default, 16); width 32 */
   FDTD_OPT_ZCHUNK = 3,        /* z planes per CTA (0 = whole column) */
   FDTD_OPT_SAMPLE_EVERY = 4,  /* m > 0: every m-th launch of a time loop opens a timed
                                  interval (CUDA events on the library's stream), see
                                  fdtd_kernel_timing (0 = off) */
-  FDTD_OPT_ROWS_PER_THREAD = 5, /* TMA half-step kernels: tile rows per thread (1 default, 2) */
-  FDTD_OPT_STAGES = 6,          /* one-plane kernels (4, 5): planes staged per CTA (2
+  FDTD_OPT_STAGES = 6,          /* kernel 5: planes staged per CTA (2
                                    default, 3, 4): stages - 1 planes are in flight while one
                                    is computed */
   FDTD_OPT_PDL = 7,             /* kernel 5: 1 = launch as a programmatic dependent of the
@@ -241,7 +238,7 @@ enum {
                                    next plane's boxes; 0 (default) = off */
   FDTD_OPT_TILE_X = 9,          /* kernel 5 with tile height 8 and 2 or 3 stages: tile width
                                    32 (default) or 40 cells */
-  FDTD_OPT_COMPACT_AUX = 10,    /* kernels 5 and 6: 1 (default) = their CPML auxiliaries are
+  FDTD_OPT_COMPACT_AUX = 10,    /* kernel 5: 1 (default) = its CPML auxiliaries are
                                    stored for the slab cells only (per axis, where the grid
                                    is long enough); 0 = full-grid arrays */
   FDTD_OPT_EXACT_REVERSAL = 11, /* kernel 5: q in 8..30 rounds every field increment of the

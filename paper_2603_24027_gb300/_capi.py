@@ -26,9 +26,9 @@ TAPE = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3, "e4m3fn": 3, "e4m3b11fnuz": 4,
         "e4m3fnuz": 6, "e4m3ieee": 7, "e3m4": 8, "bdct": 9}
 BDCT_DEFAULT_COEFFS = 10
 INTERP = {"linear": 0, "cubic": 1}
-OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY, OPT_ROWS, OPT_STAGES, OPT_PDL, \
-    OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX, OPT_EXACT_REVERSAL, OPT_ZCHUNK_FWD, \
-    OPT_ZGROUPS = range(14)
+OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY = range(5)
+OPT_STAGES, OPT_PDL, OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX, OPT_EXACT_REVERSAL, \
+    OPT_ZCHUNK_FWD, OPT_ZGROUPS = range(6, 14)
 K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV, K_MONITOR = \
     range(9)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "fused_fwd",

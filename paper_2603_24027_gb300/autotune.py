@@ -150,7 +150,7 @@ def gpu_measure(sim, eps, rec, trial_steps: int = 200, reps: int = 3):
     w = sim.w.replace(n_steps=max(1, min(sim.w.n_steps, trial_steps)))
     trial = fdtd.Simulation(w, device=eps.device)
     tuned = set(OPTION_IDS.values())
-    fixed = [A.OPT_KERNEL, A.OPT_USE_GRAPHS, A.OPT_ROWS, A.OPT_PDL, A.OPT_PREFETCH,
+    fixed = [A.OPT_KERNEL, A.OPT_USE_GRAPHS, A.OPT_PDL, A.OPT_PREFETCH,
              A.OPT_TILE_X, A.OPT_COMPACT_AUX, A.OPT_EXACT_REVERSAL]
     for oid in fixed:
         if oid not in tuned:

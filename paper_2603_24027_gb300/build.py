@@ -20,8 +20,7 @@ LIB = os.path.join(HERE, "libfdtd_gb300.so")
 # Bounds-checked variant for tests (-DFDTD_BOUNDS_CHECK): every store of the
 # default kernels checks that it lands in a buffer the launch may write.
 LIB_CHECKED = os.path.join(HERE, "libfdtd_gb300_checked.so")
-SOURCES = ["kernels_step.cu", "kernels_fused.cu", "kernels_tma.cu", "kernels_split_tma.cu",
-           "kernels_lag.cu", "kernels_lag2.cu", "kernels_ffwd.cu", "kernels_tape.cu",
+SOURCES = ["kernels_step.cu", "kernels_lag2.cu", "tensor_maps.cu", "kernels_tape.cu",
            "kernels_bdct.cu", "fdtd_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

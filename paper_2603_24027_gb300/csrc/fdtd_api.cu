@@ -39,7 +39,7 @@ struct Layout {
 };
 
 struct GraphKey {
-  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, rows, stages, pdl, prefetch,
+  int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, stages, pdl, prefetch,
       tile_x, compact, exact, coeffs, zchunk_fwd, zgroups;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
@@ -84,7 +84,7 @@ struct fdtd_handle {
   int fwd_buf;                // field buffer holding the state after forward
   fdtd_record_cfg fwd_rec;
 
-  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_rows, opt_stages, opt_pdl,
+  int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_stages, opt_pdl,
       opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
   // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
   // three events (the last launch of an even / odd phase, the join), plus the
@@ -92,10 +92,6 @@ struct fdtd_handle {
   std::vector<cudaStream_t> zs;
   std::vector<cudaEvent_t> zev;
   cudaEvent_t zfork;
-  // tensor maps of the TMA kernels, per field buffer (valid for maps_ws / maps_ty)
-  FwdMaps fmaps[2];
-  char* maps_ws;
-  int maps_ty;
   // sampled kernel timing (see Sampler): per direction a pool of start / end
   // events and the intervals the last enqueued or replayed loop recorded
   std::vector<cudaEvent_t> spool[2][2];
@@ -419,28 +415,21 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   Layout L;
   size_t nc = (size_t)h->nz * h->ny * h->px;
   size_t f6 = al(6 * nc * sizeof(float));
-  // the two-cells-per-thread kernels keep their auxiliaries compact: the
-  // forward set when they run the forward (kernel 5), the adjoint sets when
-  // they run the reverse (kernels 5 and 6)
+  // the staged kernels (5) keep their auxiliaries compact
   L.plF = psi_layout(h, h->opt_compact && h->opt_kernel == 5);
-  L.plL = psi_layout(h, h->opt_compact && h->opt_kernel >= 5);
+  L.plL = psi_layout(h, h->opt_compact && h->opt_kernel == 5);
   size_t psbF = al((size_t)L.plF.total * sizeof(float));
   size_t psbL = al((size_t)L.plL.total * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
-  // the second field and forward-psi buffers exist only for the one-launch
-  // forward kernels, which write the new state next to the old one
-  const bool pingpong = h->opt_kernel == 1 || h->opt_kernel == 2 || h->opt_kernel == 6;
   size_t off = 0;
   L.F[0] = off; off += f6;
   L.F[1] = L.F[0];
-  if (pingpong) { L.F[1] = off; off += f6; }
   L.L[0] = off; off += f6;
   L.L[1] = L.L[0];
   L.cb = off; off += al(nc * sizeof(float));
   L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
   L.psiF[0] = off; off += psbF;
   L.psiF[1] = L.psiF[0];
-  if (pingpong) { L.psiF[1] = off; off += psbF; }
   L.psiL[0] = off; off += psbL;
   L.psiL[1] = off; off += psbL;
   L.gacc = off; off += al(nd * sizeof(double));
@@ -584,15 +573,12 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_zgroups = 0;
   h->zfork = nullptr;
   h->opt_sample = 0;
-  h->opt_rows = 1;
   h->opt_stages = 2;
   h->opt_pdl = 0;
   h->opt_prefetch = 0;
   h->opt_tile_x = 32;
   h->opt_compact = 1;
   h->opt_exact = 0;
-  h->maps_ws = nullptr;
-  h->maps_ty = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
     h->savg[q] = 0.f;
     h->scount[q] = 0;
@@ -678,7 +664,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
   switch (option) {
     case FDTD_OPT_USE_GRAPHS: h->opt_graphs = value ? 1 : 0; break;
     case FDTD_OPT_KERNEL:
-      if (value < 0 || value > 6) return fail(h, FDTD_EINVAL, "kernel must be 0..6");
+      if (value != 0 && value != 5) return fail(h, FDTD_EINVAL, "kernel must be 0 or 5");
       if (value != h->opt_kernel) h->have_forward = false;   // the workspace layout changes
       h->opt_kernel = value;
       break;
@@ -694,10 +680,6 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
     case FDTD_OPT_SAMPLE_EVERY:
       if (value < 0) return fail(h, FDTD_EINVAL, "sample interval must be >= 0");
       h->opt_sample = value;
-      break;
-    case FDTD_OPT_ROWS_PER_THREAD:
-      if (value != 1 && value != 2) return fail(h, FDTD_EINVAL, "rows per thread must be 1 or 2");
-      h->opt_rows = value;
       break;
     case FDTD_OPT_STAGES:
       if (value < 2 || value > 4) return fail(h, FDTD_EINVAL, "stages must be 2, 3 or 4");
@@ -740,7 +722,6 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_TILE_Y: *value = h->opt_tile_y; break;
     case FDTD_OPT_ZCHUNK: *value = h->opt_zchunk; break;
     case FDTD_OPT_SAMPLE_EVERY: *value = h->opt_sample; break;
-    case FDTD_OPT_ROWS_PER_THREAD: *value = h->opt_rows; break;
     case FDTD_OPT_STAGES: *value = h->opt_stages; break;
     case FDTD_OPT_PDL: *value = h->opt_pdl; break;
     case FDTD_OPT_PREFETCH: *value = h->opt_prefetch; break;
@@ -816,10 +797,10 @@ static int finish(fdtd_handle* h) {
   return FDTD_OK;
 }
 
-// Tile height the half-step kernels run with: the two-cells-per-thread
-// kernels cover two tile rows per warp, so their tiles are at least 2 high.
+// Tile height the staged kernels run with: they cover two tile rows per
+// warp, so their tiles are at least 2 high.
 static int lag_tile_y(const fdtd_handle* h) {
-  return ((h->opt_kernel == 5 || h->opt_kernel == 6) && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
+  return (h->opt_kernel == 5 && h->opt_tile_y < 2) ? 2 : h->opt_tile_y;
 }
 
 // Tile width of the two-cells-per-thread kernels: 40-wide tiles exist for a
@@ -876,11 +857,6 @@ static int forward_zchunk(const fdtd_handle* h, const StepArgs& a) {
   return sms > 0 && units16 * 20 <= 8LL * sms * 21 ? 16 : a.zchunk;
 }
 
-// Kernels 1, 2 and 6 run the forward step as one ping-pong launch.
-static bool fused_forward(const fdtd_handle* h) {
-  return h->opt_kernel == 1 || h->opt_kernel == 2 || h->opt_kernel == 6;
-}
-
 static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   StepArgs a;
   memset(&a, 0, sizeof a);
@@ -897,7 +873,6 @@ static StepArgs step_args(const fdtd_handle* h, const Layout& L) {
   a.src.w = (const float*)(h->ws + L.srcw);
   a.det = det_of(h->det);
   a.tile_y = lag_tile_y(h);
-  a.rows = h->opt_rows;
   a.stages = h->opt_stages;
   a.pdl = h->opt_pdl;
   a.prefetch = h->opt_prefetch;
@@ -1084,8 +1059,7 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
   return e;
 }
 
-static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_FUSED_FWD,
-                                FDTD_K_MONITOR};
+static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_FUSED_REV};
 
 // Enqueue the forward time loop on h->stream (capturable).
@@ -1102,38 +1076,13 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if ((e = cudaMemsetAsync(h->ws + L.psiF[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream))) return e;
   int r = (h->N - 1) % rec->k;
-  const bool fused = fused_forward(h);
-  const bool tma = h->opt_kernel == 2;
-  const bool ff = h->opt_kernel == 6;
-  const bool split_tma = h->opt_kernel == 3;
-  const bool lagk = h->opt_kernel == 4 || h->opt_kernel == 5;
   const bool pair = h->opt_kernel == 5;
-  SplitMaps smaps;
-  if (split_tma &&
-      (e = encode_split_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
-                             (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
-                             h->opt_tile_y, &smaps)))
-    return e;
   LagMaps lmaps;
-  if (lagk &&
+  if (pair &&
       (e = encode_lag_maps((const float*)(h->ws + L.F[0]), (const float*)(h->ws + L.F[0]),
                            (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiF[0]), a.g,
                            a.tile_y, a.tile_x, L.plF, &lmaps)))
     return e;
-  if (tma && (h->maps_ws != h->ws || h->maps_ty != h->opt_tile_y)) {
-    for (int b = 0; b < 2; ++b)
-      if ((e = encode_fwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb), a.g,
-                               h->opt_tile_y, &h->fmaps[b])))
-        return e;
-    h->maps_ws = h->ws;
-    h->maps_ty = h->opt_tile_y;
-  }
-  FFMaps ffmaps[2];
-  for (int b = 0; ff && b < 2; ++b)
-    if ((e = encode_ffwd_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.cb),
-                              (const float*)(h->ws + L.psiF[b]), a.g, a.tile_y, &ffmaps[b])))
-      return e;
-  int cur = 0;
   a.F = (float*)(h->ws + L.F[0]);
   a.psiA = (float*)(h->ws + L.psiF[0]);
   char* tape = h->ws + L.tape;
@@ -1151,7 +1100,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
     return e;
   Sampler smp(h, 0);
-  ZGroups zg(h, pair && !fused, 0, a);
+  ZGroups zg(h, pair, 0, a);
   if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
   if ((e = zg.fork())) return e;
   for (int n = 0; n < h->N; ++n) {
@@ -1159,44 +1108,13 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     a.obj = (double*)(h->ws + L.obj) + n;
     const bool rec_now = n >= r && (n - r) % rec->k == 0;
     const int j = rec_now ? (n - r) / rec->k : 0;
-    if (fused) {
-      // one pass: (E^n, Ht^{n-1/2}) in F[cur] -> (E^{n+1}, Ht^{n+1/2}) in F[cur^1]
-      float* Fo = (float*)(h->ws + L.F[cur ^ 1]);
-      float* po = (float*)(h->ws + L.psiF[cur ^ 1]);
-      a.F = (float*)(h->ws + L.F[cur]);
-      a.psiA = (float*)(h->ws + L.psiF[cur]);
-      if ((e = smp.before(FDTD_K_FUSED_FWD))) return e;
-      if ((e = ff ? launch_ffwd(ffmaps[cur], a, Fo, po, h->stream)
-               : tma ? launch_fwd_tma(h->fmaps[cur], a, Fo, po, h->stream)
-                     : launch_fused_fwd(a, Fo, po, h->stream)))
-        return e;
-      if ((e = smp.after(FDTD_K_FUSED_FWD))) return e;
-      ++nl;
-      if (rec_now) {
-        if ((e = smp.before(FDTD_K_RECORD))) return e;
-        if ((e = record(Fo, a.F, j))) return e;
-        if ((e = smp.after(FDTD_K_RECORD))) return e;
-        ++nl;
-      }
-      if (det2.kind) {
-        if ((e = smp.before(FDTD_K_MONITOR))) return e;
-        if ((e = launch_monitor(Fo, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream))) return e;
-        if ((e = smp.after(FDTD_K_MONITOR))) return e;
-        ++nl;
-      }
-      cur ^= 1;
-      continue;
-    }
     if ((e = smp.before(FDTD_K_FWD_H))) return e;
     if (zg.active()) {
       if ((e = zg.phase([&](const StepArgs& b, cudaStream_t st) {
              return launch_lag2(0, lmaps, b, st); }, a)))
         return e;
       nl += zg.G - 1;
-    } else if ((e = lagk ? (pair ? launch_lag2(0, lmaps, a, h->stream)
-                                 : launch_lag(0, lmaps, a, h->stream))
-                         : split_tma ? launch_split_tma(0, smaps, a, h->stream)
-                                     : launch_fwd_h(a, h->stream))) {
+    } else if ((e = pair ? launch_lag2(0, lmaps, a, h->stream) : launch_fwd_h(a, h->stream))) {
       return e;
     }
     if ((e = smp.after(FDTD_K_FWD_H))) return e;
@@ -1215,10 +1133,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
              return launch_lag2(1, lmaps, b, st); }, a)))
         return e;
       nl += zg.G - 1;
-    } else if ((e = lagk ? (pair ? launch_lag2(1, lmaps, a, h->stream)
-                                 : launch_lag(1, lmaps, a, h->stream))
-                         : split_tma ? launch_split_tma(1, smaps, a, h->stream)
-                                     : launch_fwd_e(a, h->stream))) {
+    } else if ((e = pair ? launch_lag2(1, lmaps, a, h->stream) : launch_fwd_e(a, h->stream))) {
       return e;
     }
     if ((e = smp.after(FDTD_K_FWD_E))) return e;
@@ -1233,7 +1148,7 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     }
   }
   if ((e = zg.join())) return e;
-  h->fwd_buf = cur;
+  h->fwd_buf = 0;
   *launches = nl;
   return cudaSuccess;
 }
@@ -1256,25 +1171,17 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   Det det = a.det;
   const Det det2 = det2_of(h);
   int cur = 0;
-  const bool rlag = h->opt_kernel >= 4;
-  const bool rpair = h->opt_kernel >= 5;
-  const bool rtma = h->opt_kernel == 2 || h->opt_kernel == 3;
-  SplitMaps rmaps[2];
+  const bool rpair = h->opt_kernel == 5;
   LagMaps lrmaps[2];
-  for (int b = 0; b < 2; ++b) {
-    if (rtma && (e = encode_split_maps(a.F, a.L, (const float*)(h->ws + L.cb),
-                                       (const float*)(h->ws + L.psiL[b]), a.g, h->opt_tile_y,
-                                       &rmaps[b])))
+  for (int b = 0; b < 2; ++b)
+    if (rpair && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
+                                      (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y, a.tile_x,
+                                      L.plL, &lrmaps[b])))
       return e;
-    if (rlag && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
-                                     (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y, a.tile_x,
-                                     L.plL, &lrmaps[b])))
-      return e;
-  }
   const BdctLayout bl =
       rec->dtype == kTapeBdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
   Sampler smp(h, 1);
-  ZGroups zg(h, rlag && rpair, 1, a);
+  ZGroups zg(h, rpair, 1, a);
   if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
   for (int n = h->N - 1; n >= 0; --n) {
     if ((e = zg.join())) return e;
@@ -1308,15 +1215,11 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
       continue;
     }
     if ((e = smp.before(FDTD_K_REV_E))) return e;
-    if ((e = rlag ? (rpair ? launch_lag2(2, lrmaps[cur], a, h->stream)
-                         : launch_lag(2, lrmaps[cur], a, h->stream))
-              : rtma ? launch_split_tma(2, rmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
+    if ((e = rpair ? launch_lag2(2, lrmaps[cur], a, h->stream) : launch_rev_e(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_E))) return e;
     if ((e = smp.before(FDTD_K_REV_H))) return e;
-    if ((e = rlag ? (rpair ? launch_lag2(3, lrmaps[cur], a, h->stream)
-                         : launch_lag(3, lrmaps[cur], a, h->stream))
-              : rtma ? launch_split_tma(3, rmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
+    if ((e = rpair ? launch_lag2(3, lrmaps[cur], a, h->stream) : launch_rev_h(a, h->stream)))
       return e;
     if ((e = smp.after(FDTD_K_REV_H))) return e;
     cur ^= 1;
@@ -1356,7 +1259,6 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.scaled = rec->scaled; key.kernel = h->opt_kernel; key.tile_y = h->opt_tile_y;
   key.zchunk = h->opt_zchunk;
   key.sample = h->opt_sample;
-  key.rows = h->opt_rows;
   key.stages = h->opt_stages;
   key.pdl = h->opt_pdl;
   key.prefetch = h->opt_prefetch;
@@ -1414,7 +1316,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   nvtxRangePop();
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
+  h->fwd_buf = 0;
   h->fwd_rec = *rec;
   return FDTD_OK;
 }
@@ -1434,7 +1336,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   h->obj2_sum = 0.0;
   for (double v : m) h->obj2_sum += v;
   CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
-  collect_samples(h, 0, kFwdKinds, 5);
+  collect_samples(h, 0, kFwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
   if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
@@ -1890,7 +1792,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
     if (e) return cuda_fail(h, "forward launch", e);
-    h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
+    h->fwd_buf = 0;
     // objective: per-step slots summed on the host in chunks
     double sum = 0.0, chunk[256];
     for (int n0 = 0; n0 < h->N; n0 += 256) {

@@ -229,7 +229,7 @@ struct StepArgs {
   Geo g;
   float* F;        // fields
   float* cb;
-  float* psiA;     // psi set read (and written in place by the split forward)
+  float* psiA;     // psi set read (and written in place by the forward)
   float* psiB;     // psi set written (ping-pong)
   float* L;        // adjoint fields (6 components, same layout as F)
   double* gacc;    // FP64 design-box accumulator [dz][dy][dx]
@@ -241,7 +241,6 @@ struct StepArgs {
   int zchunk;
   int zc0, zc1;     // two-cells-per-thread kernels: z chunks [zc0, zc1) of this launch (zc1 = 0: to the last)
   int tile_y;
-  int rows;        // tile rows per thread (TMA half-step kernels)
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
   int prefetch;    // two-cells-per-thread kernels: warm L2 with the plane after the one staged
@@ -252,61 +251,26 @@ struct StepArgs {
   unsigned* err;   // device error word (ERR_*)
 };
 
-// Tensor maps of the TMA kernels: E and Ht boxes of one field buffer and the
-// cb box, each a 4D (x, y, z, component) view.
-struct alignas(64) FwdMaps {
-  CUtensorMap E, H, cb;
-};
-
 cudaError_t launch_prep(const float* eps, float* cb, Geo g, unsigned* err, cudaStream_t s);
+// Plain-load half-steps (kernel 0, the independent cross-check of the staged
+// kernels): one cell per thread, every neighbour read from global memory.
 cudaError_t launch_fwd_h(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fwd_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
-cudaError_t launch_fused_fwd(const StepArgs& a, float* Fout, float* psiOut, cudaStream_t s);
-cudaError_t launch_fused_rev(const StepArgs& a, float* Fout, float* Lout, cudaStream_t s);
-cudaError_t encode_fwd_maps(const float* F, const float* cb, const Geo& g, int ty, FwdMaps* m);
 
-// Tensor maps of the TMA half-step kernels: "h" = halo box {40, ty+2} at
-// (x0-4, y0-1), "o" = own box {32, ty} at (x0, y0), over the field buffer F,
-// the adjoint buffer L, cb and the psi set read by the kernel.
-struct alignas(64) SplitMaps {
-  CUtensorMap Fh, Fo, Lh, Lo, cbh, cbo, Ph, Po;
-};
-cudaError_t encode_split_maps(const float* F, const float* L, const float* cb, const float* psiA,
-                              const Geo& g, int ty, SplitMaps* m);
-// which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
-cudaError_t launch_split_tma(int which, const SplitMaps& m, const StepArgs& a, cudaStream_t s);
-
-// Tensor maps of the one-plane-per-iteration kernels for a tw x ty tile:
-// wide (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes,
-// and the psi boxes (tw+4) x ty, tw x (ty+1), tw x ty.
-// Pxw / Pyw / Po view a full-layout set as 12 components (one-cell-per-thread
-// kernels); Q* view the per-axis arrays of `pl` (4 components each): x own
+// Tensor maps of the plane-staging kernels for a tw x ty tile: wide
+// (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes;
+// Q* view the per-axis auxiliary arrays of `pl` (4 components each): x own
 // and (tw+4) x ty boxes, y own and tw x (ty+1) boxes, z own boxes.
 struct alignas(64) LagMaps {
-  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Pxw, Pyw, Po, Qxo, Qxw, Qyo, Qyw, Qzo;
+  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Qxo, Qxw, Qyo, Qyw, Qzo;
 };
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
                             const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m);
-cudaError_t launch_lag(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
-// The same half-steps with two x-cells per thread (tile height >= 2).
+// Staged half-steps, two x-cells per thread (kernel 5; tile height >= 2).
+// which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
-cudaError_t launch_fwd_tma(const FwdMaps& m, const StepArgs& a, float* Fo, float* psiO,
-                           cudaStream_t s);
-
-// Tensor maps of the fused two-cells-per-thread forward: E box 40 x (ty+2)
-// and Ht box 36 x (ty+1) from (x0-4, y0-1), own E and cb boxes 32 x ty, psi
-// boxes 36 x (ty+1) (H side) and 32 x ty (E side); ty is 4 or 8.
-struct alignas(64) FFMaps {
-  CUtensorMap Ew, Hb, Eo, cbo, Ph, Pe;
-};
-cudaError_t encode_ffwd_maps(const float* F, const float* cb, const float* psiA, const Geo& g,
-                             int ty, FFMaps* m);
-// One forward time step: (E^n, Ht^{n-1/2}) in a.F, psi in a.psiA ->
-// (E^{n+1}, Ht^{n+1/2}) in Fo, psi in psiO.
-cudaError_t launch_ffwd(const FFMaps& m, const StepArgs& a, float* Fo, float* psiO,
-                        cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);

@@ -136,7 +136,7 @@ def test_tune_leaves_other_kernels_and_exact_shapes_alone(tmp_path):
 
     def boom(o):
         raise AssertionError("kernels other than 5 are not tuned")
-    sim = FakeSim(opts={A.OPT_KERNEL: 4})
+    sim = FakeSim(opts={A.OPT_KERNEL: 0})
     r = T.tune(sim, None, rec, cache=path, measure=boom, gpu_name="GB300")
     assert r["options"] == {} and r["trials"] == 0
 
@@ -191,7 +191,7 @@ def test_gpu_timing_wrapper_drives_a_trial_copy(tmp_path, monkeypatch):
     monkeypatch.setattr(fdtd, "Simulation", TrialSim)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     w = I.ragged_box().replace(n_steps=500)
-    sim = FakeSim(w, opts={A.OPT_USE_GRAPHS: 1, A.OPT_ROWS: 1, A.OPT_PDL: 0,
+    sim = FakeSim(w, opts={A.OPT_USE_GRAPHS: 1, A.OPT_PDL: 0,
                            A.OPT_PREFETCH: 0, A.OPT_TILE_X: 40, A.OPT_COMPACT_AUX: 1})
     eps = torch.zeros(1)
     r = T.tune(sim, eps, A.record_cfg("bf16", 4), cache=str(tmp_path / "t.json"),

@@ -143,7 +143,8 @@ def test_options_are_validated(capi, fdtd):
                          (capi.OPT_ZGROUPS, 0)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
-                     (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_ROWS, 3),
+                     (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_KERNEL, 4),
+                     (capi.OPT_KERNEL, 6), (5, 1),
                      (capi.OPT_ZCHUNK, -1), (capi.OPT_TILE_X, 0), (capi.OPT_TILE_X, 36),
                      (capi.OPT_ZCHUNK_FWD, -2), (capi.OPT_EXACT_REVERSAL, 5),
                      (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (99, 1)]:
@@ -183,11 +184,11 @@ def test_tape_sizes_and_compression_factors(capi, fdtd):
 
 
 def test_compact_auxiliary_workspace(capi, fdtd):
-    """The two-cells-per-thread kernels keep each axis' CPML auxiliaries only
+    """The staged kernels keep each axis' CPML auxiliaries only
     over that axis' two slabs (x: cells [0, round_up(P, 4)) and from the
     4-aligned cell round_down(nx - P, 4) on, rows padded to 4; y, z: 2P rows /
     planes), per axis where the grid is long enough (nx >= 2P + 56,
-    ny >= 2P + 24, nz >= 2P + 1); the one-cell kernels keep the full grid.
+    ny >= 2P + 24, nz >= 2P + 1); the plain-load kernels keep the full grid.
     Three sets (forward + two adjoint) differ; everything else is equal."""
     al = lambda b: (b + 255) // 256 * 256
 
@@ -199,7 +200,7 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     w = I.waveguide_mid()
     sim = fdtd.Simulation(w)
     rec = capi.record_cfg("bf16", 4)
-    sim.set_option(capi.OPT_KERNEL, 4)
+    sim.set_option(capi.OPT_KERNEL, 0)
     b4 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_KERNEL, 5)
     b5 = sim.workspace_bytes(rec)
@@ -210,7 +211,7 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     # planes) compact, y too short (full rows of px = 72)
     w = I.ragged_box()
     sim = fdtd.Simulation(w)
-    sim.set_option(capi.OPT_KERNEL, 4)
+    sim.set_option(capi.OPT_KERNEL, 0)
     b4 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_KERNEL, 5)
     b5 = sim.workspace_bytes(rec)

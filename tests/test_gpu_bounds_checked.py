@@ -37,10 +37,8 @@ for name, w in grids.items():
     ref = {"f32:1:linear": O.gradient(w)[1],
            "bdct10:2:cubic": O.reverse(w, "bdct10", k=2, interp="cubic")[1]}
     eps = torch.from_numpy(w.eps).cuda()
-    for kernel in (5, 6):
+    for kernel in (5,):
         for opts in shapes:
-            if kernel == 6 and A.OPT_EXACT_REVERSAL in opts:
-                continue
             for tape in ("f32:1:linear", "bdct10:2:cubic"):
                 sim = F.Simulation(w)
                 sim.set_option(A.OPT_KERNEL, kernel)

@@ -42,7 +42,7 @@ def _noalloc(A, sim, eps, rec, seed, out):
     return obj.value, out.cpu().numpy().copy()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [0, 5])
 @pytest.mark.parametrize("tape", [("f32", 1, "linear"), ("bf16", 4, "cubic"), ("e4m3", 2, "linear"),
                                   ("bdct10", 2, "cubic")])
 def test_noalloc_matches_workspace_path_on_two_calls(mods, kernel, tape):
