@@ -256,7 +256,7 @@ enum {
                                    fits in about one wave of resident CTAs, else
                                    FDTD_OPT_ZCHUNK); FDTD_OPT_ZCHUNK sets the reverse phases
                                    (and every other kernel) */
-  FDTD_OPT_ZGROUPS = 13         /* kernel 5: G in 0..16; G > 1 splits every half-step launch
+  FDTD_OPT_ZGROUPS = 13,        /* kernel 5: G in 0..16; G > 1 splits every half-step launch
                                    into G launches over consecutive ranges of its z chunks,
                                    each on its own stream and waiting only for the
                                    neighbouring ranges of the half-step before, so that
@@ -268,6 +268,14 @@ enum {
                                    (FDTD_OPT_SAMPLE_EVERY) records only loops that run
                                    with one launch per half-step; the no-allocation entry
                                    point always runs that way */
+  FDTD_OPT_INJECT_WAIT_TIMEOUT = 14 /* failure-detection test hook: L > 0 makes every backward
+                                   (fdtd_backward, fdtd_backward2, the group and no-allocation
+                                   calls) start with one bounded device wait that nothing
+                                   completes; it gives up after L SM cycles and sets the
+                                   timeout bit of the device error word, so the call returns
+                                   FDTD_ETIMEOUT with the CUDA context usable.  0 (default) =
+                                   off.  Injects no fault: the wait is the same bounded wait
+                                   as fdtd_selftest_wait */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);
@@ -369,6 +377,17 @@ int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi);
  * FDTD_ECUDA if the launch fails. */
 int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stream);
 
+/* The status a call returns for a device error word (host only, no device
+ * use).  The kernels OR these bits into a word the host reads after each
+ * run: 1 eps invalid (non-finite or < 1) -> FDTD_ENONFINITE; 4 a bounded
+ * wait gave up -> FDTD_ETIMEOUT; 16 a bounds-checked store was dropped (the
+ * checked test build) -> FDTD_ECUDA; 2 a non-finite gradient ->
+ * FDTD_ENONFINITE; any other bit -> FDTD_ECUDA; 0 -> FDTD_OK.  With several
+ * bits set the first in that order decides.  Every entry point that runs the
+ * kernels (forward, backward, the group and no-allocation calls) maps the
+ * word through this one rule. */
+int fdtd_status_of_error_word(unsigned err_word);
+
 /* ------------------------------------------------ no-allocation variant --- */
 
 /* Largest workspace (bytes) fdtd_value_and_grad_noalloc can hold. */
@@ -391,7 +410,11 @@ int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stre
  * (device, float32 design box).  Work is queued on the handle's stream and
  * the call blocks until done.  The first call on a device looks up the
  * scratch array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture begins.  The call
+ * current, and the first call with a BDCT tape uploads the codec's basis
+ * table (cudaMemcpyToSymbol, as any first BDCT use does); make those first
+ * calls before any stream capture begins.  Device errors map to statuses as
+ * in fdtd_status_of_error_word, after the forward and after the backward;
+ * options are validated as for fdtd_forward (FDTD_EINVAL).  The call
  * itself calls no cudaMalloc / cudaFree, creates no stream, event or graph,
  * and clears every part of the scratch it reads before using it.  All calls
  * on a device share the one array, so calls that overlap on the GPU (from

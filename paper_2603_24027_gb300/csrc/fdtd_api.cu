@@ -40,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups;
+      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -86,6 +86,7 @@ struct fdtd_handle {
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_stages, opt_pdl,
       opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
+  int opt_inject_wait;        // FDTD_OPT_INJECT_WAIT_TIMEOUT (SM cycles; 0 = off)
   // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
   // three events (the last launch of an even / odd phase, the join), plus the
   // fork event
@@ -579,6 +580,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_tile_x = 32;
   h->opt_compact = 1;
   h->opt_exact = 0;
+  h->opt_inject_wait = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
     h->savg[q] = 0.f;
     h->scount[q] = 0;
@@ -703,6 +705,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < 0 || value > kMaxZGroups) return fail(h, FDTD_EINVAL, "zgroups must be 0..16");
       h->opt_zgroups = value;
       break;
+    case FDTD_OPT_INJECT_WAIT_TIMEOUT:
+      if (value < 0) return fail(h, FDTD_EINVAL, "injected wait limit must be >= 0");
+      h->opt_inject_wait = value;
+      break;
     case FDTD_OPT_EXACT_REVERSAL:
       if (value != 0 && (value < 8 || value > 30))
         return fail(h, FDTD_EINVAL, "exact reversal: q must be 0 or 8..30");
@@ -730,6 +736,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
     case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
     case FDTD_OPT_ZGROUPS: *value = h->opt_zgroups; break;
+    case FDTD_OPT_INJECT_WAIT_TIMEOUT: *value = h->opt_inject_wait; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -1166,6 +1173,11 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   if ((e = cudaMemsetAsync(h->ws + L.psiL[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.psiL[1], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.gacc, 0, nd * sizeof(double), h->stream))) return e;
+  // failure-detection test hook: one bounded device wait that nothing
+  // completes gives up after the set limit and sets the timeout bit
+  if (h->opt_inject_wait > 0 &&
+      (e = launch_wait_selftest(h->opt_inject_wait, (unsigned*)(h->ws + L.err), h->stream)))
+    return e;
   a.F = (float*)(h->ws + L.F[h->fwd_buf]);
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
@@ -1268,6 +1280,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.coeffs = rec->coeffs;
   key.zchunk_fwd = h->opt_zchunk_fwd;
   key.zgroups = h->opt_zgroups;
+  key.inject_wait = h->opt_inject_wait;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1293,13 +1306,48 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   return FDTD_OK;
 }
 
+// ------------------------------------------------- device error word ---
+// Status of a device error word (ERR_* bits), most specific first: an eps
+// that failed validation, a bounded wait that gave up, a checked store that
+// was dropped, a non-finite result.
+static int err_status(unsigned err, const char** msg) {
+  if (err & ERR_EPS) { *msg = "eps must be finite and >= 1"; return FDTD_ENONFINITE; }
+  if (err & ERR_TIMEOUT) { *msg = "a device wait gave up (TMA pipeline)"; return FDTD_ETIMEOUT; }
+  if (err & ERR_BOUNDS) {
+    *msg = "bounds check: a store fell outside its buffers";
+    return FDTD_ECUDA;
+  }
+  if (err & ERR_NONFINITE) { *msg = "a result is not finite"; return FDTD_ENONFINITE; }
+  if (err) { *msg = "unknown device error bits"; return FDTD_ECUDA; }
+  *msg = "";
+  return FDTD_OK;
+}
+
+static int check_err(fdtd_handle* h, unsigned err) {
+  const char* msg = nullptr;
+  const int rc = err_status(err, &msg);
+  return rc ? fail(h, rc, msg) : FDTD_OK;
+}
+
+extern "C" int fdtd_status_of_error_word(unsigned err_word) {
+  const char* msg = nullptr;
+  return err_status(err_word, &msg);
+}
+
+// Options that only some kernels implement, checked before a forward.
+static int check_kernel_options(fdtd_handle* h) {
+  if (h->opt_exact && (h->opt_kernel != 5 || h->opt_tile_y != 8 || h->opt_stages != 2 ||
+                       lag_tile_x(h) != 32))
+    return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 with its default tiles");
+  return FDTD_OK;
+}
+
 static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec) {
   int rc = check_rec(h, rec);
   if (rc) return rc;
   if (!d_eps) return fail(h, FDTD_EINVAL, "eps is NULL");
-  if (h->opt_exact && (h->opt_kernel != 5 || h->opt_tile_y != 8 || h->opt_stages != 2 ||
-                       lag_tile_x(h) != 32))
-    return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 with its default tiles");
+  rc = check_kernel_options(h);
+  if (rc) return rc;
   Layout L = layout_of(h, rec);
   if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
   if (L.total > h->ws_bytes) return fail(h, FDTD_ENOMEM, "workspace too small for this record config");
@@ -1339,9 +1387,8 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   collect_samples(h, 0, kFwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
-  if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
-  if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
-  if (err & ERR_BOUNDS) return fail(h, FDTD_ECUDA, "bounds check: a store fell outside its buffers");
+  rc = check_err(h, err);
+  if (rc) return rc;
   double s = 0.0;
   for (double v : h->obj_hist) s += v;
   if (!isfinite(s)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
@@ -1402,10 +1449,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   collect_samples(h, 1, kBwdKinds, 4);
   int rc = finish(h);
   if (rc) return rc;
-  if (err & ERR_TIMEOUT) return fail(h, FDTD_ETIMEOUT, "a device wait gave up (TMA pipeline)");
-  if (err & ERR_BOUNDS) return fail(h, FDTD_ECUDA, "bounds check: a store fell outside its buffers");
-  if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
-  return FDTD_OK;
+  return check_err(h, err);
 }
 
 extern "C" int fdtd_backward(fdtd_handle* h, double seed, float* d_grad_eps) {
@@ -1744,6 +1788,8 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
   int rc = check_rec(h, rec);
   if (rc) return rc;
   if (!d_eps || !d_grad) return fail(h, FDTD_EINVAL, "NULL device buffer");
+  rc = check_kernel_options(h);
+  if (rc) return rc;
   Layout L = layout_of(h, rec);
   if (L.total > FDTD_NOALLOC_SCRATCH_BYTES) {
     char buf[256];
@@ -1788,6 +1834,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
                             cudaMemcpyHostToDevice, s));
     CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, s));
     Geo g = geo_of(h);
+    if (rec->dtype == kTapeBdct) CK(h, bdct_ensure_basis());
     CK(h, launch_prep(d_eps, (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), s));
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
@@ -1805,7 +1852,8 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     unsigned err = 0;
     CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
-    if (err & ERR_EPS) return fail(h, FDTD_ENONFINITE, "eps must be finite and >= 1");
+    int rc2 = check_err(h, err);
+    if (rc2) return rc2;
     if (!isfinite(sum)) return fail(h, FDTD_ENONFINITE, "objective is not finite");
     CK(h, upload_seeds(h, L, seed, 0.0, s));
     e = enqueue_backward(h, rec, &nl);
@@ -1814,7 +1862,8 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
                           h->dlo, h->dhi, h->seed_scale, d_grad, (unsigned*)(h->ws + L.err), s));
     CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
-    if (err & ERR_NONFINITE) return fail(h, FDTD_ENONFINITE, "gradient is not finite");
+    rc2 = check_err(h, err);
+    if (rc2) return rc2;
     if (objective) *objective = sum;
     return FDTD_OK;
   };

@@ -284,3 +284,49 @@ def test_checkpoint_header_is_validated(capi, fdtd):
     ints = hdr[8:8 + 24].view(np.int32)
     ints[:] = [8, 8, 8, 2, 61, 0]
     assert lib.fdtd_load_state(sim.h, C.c_void_p(hdr.ctypes.data), hdr.size) == capi.FDTD_EINVAL
+
+
+def test_error_word_maps_to_one_status(capi):
+    """The device error word (bits the kernels OR in) maps to the status every
+    entry point returns, through one rule: eps invalid (1) -> ENONFINITE,
+    wait gave up (4) -> ETIMEOUT, dropped checked store (16) -> ECUDA,
+    non-finite gradient (2) -> ENONFINITE, any other bit -> ECUDA; the first
+    in that order wins."""
+    f = capi.lib().fdtd_status_of_error_word
+    assert f(0) == capi.FDTD_OK
+    assert f(1) == capi.FDTD_ENONFINITE
+    assert f(2) == capi.FDTD_ENONFINITE
+    assert f(4) == capi.FDTD_ETIMEOUT
+    assert f(16) == capi.FDTD_ECUDA
+    assert f(8) == capi.FDTD_ECUDA and f(1 << 31) == capi.FDTD_ECUDA
+    assert f(4 | 2) == capi.FDTD_ETIMEOUT          # a timed-out run's result is not trusted
+    assert f(16 | 2) == capi.FDTD_ECUDA
+    assert f(1 | 4 | 16) == capi.FDTD_ENONFINITE     # invalid input is reported first
+    assert f(4 | 16) == capi.FDTD_ETIMEOUT
+
+
+def test_noalloc_validates_options_like_the_forward(capi, fdtd):
+    """Exact reversal is built into kernel 5 only: the no-allocation call
+    refuses it with kernel 0 as fdtd_forward does, before any device work."""
+    lib = capi.lib()
+    sim = fdtd.Simulation(I.fd_cube())
+    assert lib.fdtd_set_option(sim.h, capi.OPT_EXACT_REVERSAL, 22) == capi.FDTD_OK
+    assert lib.fdtd_set_option(sim.h, capi.OPT_KERNEL, 0) == capi.FDTD_OK
+    obj = C.c_double()
+    rc = lib.fdtd_value_and_grad_noalloc(sim.h, C.c_void_p(256), C.byref(capi.record_cfg()), 1.0,
+                                         C.byref(obj), C.c_void_p(512))
+    assert rc == capi.FDTD_EINVAL
+    assert "exact reversal" in lib.fdtd_last_error(sim.h).decode()
+    rc = lib.fdtd_forward(sim.h, C.c_void_p(256), C.byref(capi.record_cfg()), C.byref(obj))
+    assert rc == capi.FDTD_EINVAL
+
+
+def test_inject_wait_option_is_validated(capi, fdtd):
+    lib = capi.lib()
+    sim = fdtd.Simulation(I.fd_cube())
+    v = C.c_int()
+    assert lib.fdtd_get_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, C.byref(v)) == 0 and v.value == 0
+    assert lib.fdtd_set_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, -1) == capi.FDTD_EINVAL
+    assert lib.fdtd_set_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, 100000) == capi.FDTD_OK
+    assert lib.fdtd_get_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, C.byref(v)) == 0
+    assert v.value == 100000
