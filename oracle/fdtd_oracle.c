@@ -908,6 +908,11 @@ static void encode_face(int fmt, int scaled, double* v, size_t n, double* scale_
   if (scale_out) *scale_out = scale;
 }
 
+/* Public: the face encoder on one array (for its tests). */
+void oracle_encode_face(int fmt, int scaled, double* v, size_t n, double* scale_out) {
+  encode_face(fmt, scaled, v, n, scale_out);
+}
+
 /* Inverse interior updates: E^n from (E^{n+1}, Ht^{n+1/2}), then Ht^{n-1/2}
  * from (Ht^{n+1/2}, E^n).  Only cells of I are written; the interior has
  * kappa = 1 and no psi, so the curls are the plain lossless ones.
@@ -985,10 +990,11 @@ int oracle_unstep(const ocfg* c, const double* eps, double* st, int n) {
  * the forward run, so any use of a value the method does not have shows up.
  * fmt < 0 keeps the samples unquantised (exact FP64).
  */
-int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int coeffs, int k,
-                      int interp, double seed, double* grad, double* obj,
-                      double* tape_values_out) {
+int oracle_reverse2(const ocfg* c, const double* eps, int fmt, int scaled, int coeffs, int k,
+                    int interp, double seed, double seed2, double* grad, double* obj2,
+                    double* tape_values_out) {
   size_t N = ncell(c);
+  const ocfg c2 = second_detector(c);
   int T = c->n_steps;
   if (k < 1 || T < 1 || c->P < 1) return -1;
   int r = (T - 1) % k;
@@ -1015,7 +1021,7 @@ int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int
   for (int f = 0; f < 6; ++f) foff[f + 1] = foff[f] + face_values(c, f);
 
   /* forward with recording */
-  double L = 0.0;
+  double L = 0.0, M = 0.0;
   for (int n = 0; n < T; ++n) {
     int sample = n >= r && (n - r) % k == 0;
     int j = (n - r) / k;
@@ -1026,6 +1032,7 @@ int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int
       for (int f = 0; f < 6; f += 2) face_io(c, f, st, tape + (size_t)j * ns + foff[f], 0);
     e_update(&x, eps, st, n);
     L += objective(c, st);
+    if (c->det2_kind) M += objective(&c2, st);
   }
   if (fmt == 9) {   /* block-transform codec, K = coeffs (0: 10) */
     for (int j = 0; j < J; ++j)
@@ -1072,7 +1079,9 @@ int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int
       }
       face_io(c, f, st, fb + foff[f], 1);
     }
+    /* both detectors' adjoint sources, from the reconstructed (E^{n+1}, Ht^{n+1/2}) */
     objective_seed(c, st, seed, lam);
+    if (c->det2_kind) objective_seed(&c2, st, seed2, lam);
     inverse_e(&x, eps, st, n, dE);
     for (int kk = 0; kk < dZ; ++kk)
       for (int jj = 0; jj < dY; ++jj)
@@ -1099,10 +1108,23 @@ int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int
     inverse_h(&x, st);
     adj_h_transpose(&x, lam, tmp);
   }
-  if (obj) *obj = L;
+  if (obj2) { obj2[0] = L; obj2[1] = M; }
   free(st); free(lam); free(tmp); free(dE); free(tape); free(tk); free(pv); free(fb);
   ctx_free(&x);
   return 0;
+}
+
+/* The method for the first detector's objective alone (second detector ignored). */
+int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int coeffs, int k,
+                      int interp, double seed, double* grad, double* obj,
+                      double* tape_values_out) {
+  ocfg one = *c;
+  one.det2_kind = 0;
+  double o2[2];
+  int rc = oracle_reverse2(&one, eps, fmt, scaled, coeffs, k, interp, seed, 0.0, grad, o2,
+                           tape_values_out);
+  if (obj) *obj = o2[0];
+  return rc;
 }
 
 int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k, int interp,

@@ -75,6 +75,9 @@ def lib():
                                         C.c_double, dp, dp, dp]
         fp = C.POINTER(C.c_float)
         bp = C.POINTER(C.c_byte)
+        L.oracle_reverse2.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_double, C.c_double, dp, dp, dp]
+        L.oracle_encode_face.argtypes = [C.c_int, C.c_int, dp, C.c_size_t, dp]
         L.oracle_bdct_basis.argtypes = [fp]
         L.oracle_bdct_encode.argtypes = [fp, C.c_int, C.c_int, C.c_int, bp, fp]
         L.oracle_bdct_decode.argtypes = [bp, fp, C.c_int, C.c_int, C.c_int, fp]
@@ -249,6 +252,30 @@ def reverse(w, fmt: str = "none", scaled: bool = False, k: int = 1, interp: str 
                                    0 if interp == "linear" else 1, seed, _dp(g), _dp(obj),
                                    _dp(tape) if want_tape else None))
     return (float(obj[0]), g, tape) if want_tape else (float(obj[0]), g)
+
+
+def reverse2(w, fmt: str = "none", scaled: bool = False, k: int = 1, interp: str = "linear",
+             seed: float = 1.0, seed2: float = 0.0, **kw):
+    """The method in FP64 for seed * L + seed2 * M (M: the workload's second
+    detector), both detectors seeded from the reconstructed fields in the same
+    time-reversed run.  Returns (L, M, grad)."""
+    c = make_cfg(w, **kw)
+    g = np.zeros(w.design_shape)
+    obj = np.zeros(2)
+    fid, coeffs = _fmt(fmt)
+    _check(lib().oracle_reverse2(C.byref(c), _dp(_eps(w)), fid, int(scaled), coeffs, k,
+                                 0 if interp == "linear" else 1, seed, seed2, _dp(g), _dp(obj),
+                                 None))
+    return float(obj[0]), float(obj[1]), g
+
+
+def encode_face(fmt: str, values, scaled: bool = True):
+    """The tape encoder on one face sample: quantised values (FP64) and the
+    scale it used."""
+    v = np.ascontiguousarray(values, dtype=np.float64).ravel().copy()
+    sc = np.zeros(1)
+    lib().oracle_encode_face(FMT[fmt], int(scaled), _dp(v), v.size, _dp(sc))
+    return v, float(sc[0])
 
 
 def bdct_basis() -> np.ndarray:

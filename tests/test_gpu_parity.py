@@ -357,16 +357,24 @@ def test_two_detector_gradient_matches_oracle(F, A, kernel):
     assert rel(g, gr) < 1e-4
 
 
-def test_two_detector_compressed_tape_and_seed_errors(F, A):
+@pytest.mark.parametrize("tape", ["bf16:4:linear", "e4m3:2:cubic"])
+def test_two_detector_compressed_tape_and_seed_errors(F, A, tape):
+    """Both detectors seeded through a compressed tape (the transmission ratio
+    of Sec. 4) against the oracle's FP64 run of the same method with the same
+    tape settings and seeds: soft parity (a quantiser may round FP32 and FP64
+    inputs to neighbouring codes)."""
     w = I.coupler_small(n_steps=110)
-    Lr, Mr, gr = O.gradient2(w, 1.0, -2.0)
+    dt, k, interp = tape.split(":")
+    scaled = dt == "e4m3"
+    Lm, Mm, gm = O.reverse2(w, dt, scaled=scaled, k=int(k), interp=interp, seed=1.0, seed2=-2.0)
     sim = F.Simulation(w)
     eps = torch.from_numpy(w.eps).cuda()
-    sim.forward(eps, A.record_cfg("bf16", 4, "linear"))
+    L = sim.forward(eps, A.record_cfg(dt, int(k), interp))
+    M = sim.objectives()[1]
+    assert L == pytest.approx(Lm, rel=1e-5) and M == pytest.approx(Mm, rel=1e-5)
     g = sim.backward(1.0, seed2=-2.0).cpu().numpy()
-    # against the exact gradient: the k = 4 subsampling error of this short,
-    # fast-varying run (the oracle's FP64 run of the method reaches 0.998)
-    assert cos(g, gr) > 0.995
+    assert cos(g, gm) > 0.999
+    assert rel(g, gm) < 2e-2
     # seed2 without a second detector is a state error
     w1 = w.replace(det2_kind=0)
     sim1 = F.Simulation(w1)
@@ -688,26 +696,40 @@ def test_large_grid_properties_at_full_size(F, A):
 
 
 def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
-    """The 200 x 200 x 100 benchmark grid in the default launch configuration,
-    shortened to 100 steps so that the FP64 oracle computes every output: the
-    forward fields, the objective and the uncompressed gradient."""
-    # an early pulse and the detector inside the design region's x range, so
-    # that the objective and its gradient are not zero after 100 steps
-    w = I.waveguide_mid().replace(n_steps=100, t0_over_tau=0.3, det_index=60)
+    """The 200 x 200 x 100 benchmark grid with its own source (the Gaussian
+    pulse centred at 3 tau) in the default launch configuration, shortened to
+    700 steps and with the detector moved into the design region's x range
+    (x = 60), so that the FP64 oracle computes every output and both L and
+    dL/d(eps) are non-zero (79 % of the design cells above 1e-6 of the
+    maximum): forward fields, objective and the uncompressed-tape gradient at
+    the stated tolerances."""
+    w = I.waveguide_mid().replace(n_steps=700, det_index=60)
     L, g, st = O.gradient(w, want_state=True)
     assert L != 0.0 and np.abs(g).max() > 0
     r = gpu_run(F, A, w)
     eE, eH = field_err(r["fields"], st)
     assert eE < 1e-5 and eH < 1e-5, (eE, eH)
     assert r["L"] == pytest.approx(L, rel=1e-5)
-    # The source switched on at 0.3 tau drives content up to the grid's
-    # Nyquist limit, which FP32 time reversal over 100 steps reproduces to
-    # ~2e-4 (the smooth pulses of the other tests reach 1e-7): the bound is
-    # set accordingly, and the plain split kernels, an independent variant,
-    # must agree with the default kernels to rounding.
-    assert rel(r["g"], g) < 1e-3
+    assert rel(r["g"], g) < 1e-4, rel(r["g"], g)
     r0 = gpu_run(F, A, w, options={A.OPT_KERNEL: 0})
     np.testing.assert_array_equal(r0["fields"], r["fields"])
+    same_gradient(r["g"], r0["g"])
+
+
+def test_reversal_drift_report_with_an_abruptly_switched_source(F, A):
+    """Drift report, not parity: a source switched on at 0.3 tau (not the
+    benchmark's pulse) drives content up to the grid's Nyquist limit, where
+    float32 time reversal of 100 steps reproduces the gradient only to ~2e-4
+    (printed).  The bound checked is that drift's order; the plain-load
+    kernels, an independent variant, agree with the default ones to
+    rounding."""
+    w = I.waveguide_mid().replace(n_steps=100, t0_over_tau=0.3, det_index=60)
+    L, g = O.gradient(w)
+    r = gpu_run(F, A, w)
+    drift = rel(r["g"], g)
+    print(f"reversal drift, abrupt source, 100 steps: gradient rel. error {drift:.2e}")
+    assert drift < 1e-3
+    r0 = gpu_run(F, A, w, options={A.OPT_KERNEL: 0})
     same_gradient(r["g"], r0["g"])
 
 

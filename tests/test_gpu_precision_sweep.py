@@ -3,6 +3,7 @@ one seed, a few tape configurations, checked against the FP64 oracle."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -60,3 +61,32 @@ def test_paper_format_grid_ordering():
     assert c[("e3m4", 1)] < 0.99
     comp = {(r["dtype"], r["k"]): r["compression"] for r in rows}
     assert comp[("e4m3b11fnuz", 16)] == pytest.approx(64.0)
+
+
+@pytest.mark.parametrize("tape", ["bf16:4:linear", "e4m3:8:cubic"])
+def test_compressed_tape_parity_against_the_oracle_method_at_sweep_size(tape):
+    """The 100 x 100 x 50 waveguide, 2000 steps (the size the precision sweep
+    is quoted on), compressed tapes against the FP64 oracle's run of the same
+    method (same format, scale rule, k and interpolation): relative L2 error
+    below 2e-2 and cosine above 0.999 (soft parity: a quantiser may round the
+    FP32 and FP64 face values to neighbouring codes)."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from oracle import oracle as O
+    from paper_2603_24027_gb300 import _capi as A
+    from paper_2603_24027_gb300 import build as B
+    from paper_2603_24027_gb300 import fdtd
+    from paper_2603_24027_gb300 import inputs as I
+    B.build()
+    w = I.waveguide_sweep(seed=0, n_steps=2000)
+    dt, k, interp = tape.split(":")
+    Lm, gm = O.reverse(w, dt, scaled=dt == "e4m3", k=int(k), interp=interp)
+    sim = fdtd.Simulation(w)
+    eps = torch.from_numpy(w.eps).cuda()
+    L = sim.forward(eps, A.record_cfg(dt, int(k), interp))
+    g = sim.backward(1.0).cpu().numpy().astype(np.float64)
+    assert L == pytest.approx(Lm, rel=1e-5)
+    c = float(g.ravel() @ gm.ravel() / (np.linalg.norm(g) * np.linalg.norm(gm)))
+    e = float(np.linalg.norm(g - gm) / np.linalg.norm(gm))
+    print(f"{tape}: cosine {c:.7f}, rel. error {e:.2e} against the oracle's method run")
+    assert c > 0.999 and e < 2e-2, (c, e)

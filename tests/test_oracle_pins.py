@@ -674,3 +674,118 @@ def test_bdct_single_coefficient_is_the_block_mean():
             blk = y[8 * bv:min(8 * bv + 8, 13), 8 * bu:min(8 * bu + 8, 21)]
             np.testing.assert_allclose(blk, m, rtol=1e-5, atol=1e-6)
             assert abs(codes[bv * 3 + bu, 0]) == 127
+
+
+# -------------------------------------- per-face scaled tape encoder ---------
+
+MANT = {"e4m3": 3, "f16": 10}
+MIN_SUB = {"e4m3": 2.0 ** -9, "f16": 2.0 ** -24}
+
+
+@pytest.mark.parametrize("fmt", ["e4m3", "f16"])
+def test_scaled_face_encoder_properties(fmt):
+    """The per-face scale of the reduced bit-width tape (Sec. 2; the scale
+    reading of BASELINE's FP8 tape): the face's largest magnitude maps onto the
+    format's largest finite value and comes back exactly; every value is
+    within half a step of the format at the face's scale; scaling a face by a
+    power of two scales its code values by the same power (the scale absorbs
+    the exponent, where the unscaled format would flush or saturate); an
+    all-zero face keeps scale 1; the scale never drops below 2^-126."""
+    rng = np.random.default_rng(31)
+    fmax = O.format_max(fmt)
+    v = rng.standard_normal(3000) * 10.0 ** rng.uniform(-6, 0, 3000) * 3.7e-2
+    q, s = O.encode_face(fmt, v)
+    amax = np.abs(v).max()
+    assert np.abs(q).max() == pytest.approx(amax, rel=1e-15)
+    assert s == pytest.approx(amax / fmax, rel=1e-15)
+    bound = amax * 2.0 ** -(MANT[fmt] + 1) + s * MIN_SUB[fmt] / 2
+    assert np.all(np.abs(q - v) <= bound * (1 + 1e-12))
+    # relative precision of the format for values near the face's maximum
+    big = np.abs(v) > amax / 2
+    assert np.all(np.abs(q - v)[big] <= np.abs(v[big]) * 2.0 ** -MANT[fmt] * (1 + 1e-12))
+    for e in (-100, -20, 30):
+        q2, s2 = O.encode_face(fmt, v * 2.0 ** e)
+        np.testing.assert_array_equal(q2, q * 2.0 ** e)
+        assert s2 == s * 2.0 ** e
+    # far below the format's range: the unscaled format loses the face, the
+    # scaled one keeps what it kept at the original scale
+    qu, su = O.encode_face(fmt, v * 2.0 ** -40, scaled=False)
+    assert su == 1.0 and np.count_nonzero(qu) < np.count_nonzero(q) // 10
+    z, sz = O.encode_face(fmt, np.zeros(64))
+    assert sz == 1.0 and not z.any()
+    # a face whose absmax / fmax is below 2^-126 gets the floor scale
+    _, sf = O.encode_face(fmt, np.full(8, fmax * 2.0 ** -140))
+    assert sf == 2.0 ** -126
+
+
+def _face_slices(w):
+    """Offsets of the six faces in one tape sample: face f = 2 axis + high,
+    two tangential components of the interior cross-section each."""
+    P = w.pml_thickness
+    dims = (w.nx, w.ny, w.nz)
+    out, off = [], 0
+    for f in range(6):
+        a = f // 2
+        ua, va = (1 if a == 0 else 0), (1 if a == 2 else 2)
+        n = 2 * (dims[ua] - 2 * P) * (dims[va] - 2 * P)
+        out.append(slice(off, off + n))
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("fmt", ["e4m3", "f16"])
+def test_method_tape_is_scaled_per_face_and_sample(fmt):
+    """The method's recorded tape with a scaled format equals, face by face and
+    sample by sample, the exact samples divided by that face's own scale
+    max(absmax / format_max, 2^-126) (1 for an all-zero face), quantised and
+    multiplied back.  The faces of one sample have very different magnitudes
+    here, so a scale shared across a sample, a missing floor or a multiply in
+    place of the divide would change the codes."""
+    w = I.ragged_box(nx=16, ny=13, nz=12, P=3, n_steps=60)
+    _, _, raw = O.reverse(w, "none", k=1, want_tape=True)
+    _, _, tq = O.reverse(w, fmt, scaled=True, k=1, want_tape=True)
+    fmax = O.format_max(fmt)
+    faces = _face_slices(w)
+    spread, zero_faces = 0.0, 0
+    for j in range(raw.shape[0]):
+        amaxes = []
+        for sl in faces:
+            r = raw[j, sl]
+            amax = np.abs(r).max()
+            amaxes.append(amax)
+            s = max(amax / fmax, 2.0 ** -126) if amax > 0 else 1.0
+            zero_faces += amax == 0
+            np.testing.assert_array_equal(tq[j, sl], O.quantize(fmt, r / s) * s)
+        nz = [a for a in amaxes if a > 0]
+        if len(nz) > 1:
+            spread = max(spread, max(nz) / min(nz))
+    assert spread > 100 and zero_faces > 0
+
+
+# ------------------------------------------ two detectors in the method -----
+
+def test_two_detector_method_with_exact_samples_equals_stored_history():
+    """Both detectors seeded in the same time-reversed run (the transmission
+    ratio of Sec. 4): with exact samples at every step it reproduces the
+    stored-history gradient of s L + s2 M, and L, M themselves."""
+    w = I.coupler_small(n_steps=70)
+    s1, s2 = 0.7, -1.3
+    L, M, g = O.gradient2(w, s1, s2)
+    L2, M2, g2 = O.reverse2(w, "none", k=1, seed=s1, seed2=s2)
+    assert L2 == pytest.approx(L, rel=1e-14) and M2 == pytest.approx(M, rel=1e-14)
+    assert np.isfinite(g2).all()
+    assert np.linalg.norm(g2 - g) <= 1e-11 * np.linalg.norm(g)
+
+
+def test_two_detector_method_is_linear_in_the_seeds_for_a_compressed_tape():
+    """The tape does not depend on the seeds and the adjoint is linear: the
+    method's gradient of s L + s2 M with a compressed tape equals s times its
+    gradient of L plus s2 times its gradient of M (the second detector made
+    the only one) from the same tape."""
+    w = I.coupler_small(n_steps=70)
+    s1, s2 = 0.7, -1.3
+    _, _, g = O.reverse2(w, "e4m3", scaled=True, k=2, interp="cubic", seed=s1, seed2=s2)
+    _, g1 = O.reverse(w, "e4m3", scaled=True, k=2, interp="cubic")
+    _, gm = O.reverse(_swap_detectors(w), "e4m3", scaled=True, k=2, interp="cubic")
+    np.testing.assert_allclose(g, s1 * g1 + s2 * gm, rtol=0, atol=1e-12 * np.abs(g).max())
+    assert np.abs(gm).max() > 1e-3 * np.abs(g1).max()
