@@ -1,30 +1,49 @@
 """Benchmark: gradient throughput of the time-reversible FDTD on one or more GPUs.
 
-One step = one forward run (n_steps leapfrog steps recording the compressed
-boundary tape) plus one backward run (time-reversed interior, tape restore,
-adjoint, dL/d(eps)) of the waveguide workload: 200 x 200 x 100 cells at
-20 nm, 12-cell CPML, 2000 steps, BF16 tape every 4th step with linear
-interpolation.  Metric: cell-updates per second of the whole gradient,
-nx*ny*nz*n_steps / (T_forward + T_backward), cells including the CPML.
+One step = one gradient: a forward run (n_steps leapfrog steps recording the
+compressed boundary tape) plus a backward run (time-reversed interior, tape
+restore, adjoint, dL/d(eps)) of the workload, through the public host-buffer
+call fdtd_value_and_grad_host.  Default workload: the large waveguide, 600 x
+600 x 300 cells at 10 nm, 16-cell CPML, 10000 steps, FP8 E4M3 tape with a
+per-face scale, every 8th step, linear interpolation (32x smaller than the
+FP32 tape of every step).
+
+Metric: cell-updates per second of the whole gradient,
+nx*ny*nz*n_steps / T, cells including the CPML.
+  value: T = device time of each call between its input copy and its output
+         copy (CUDA events on the library's stream; eps already in HBM);
+  e2e:   T = wall time of the same calls, host copies included.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload waveguide200|waveguide600|batched64] [--n-steps N]
+                  [--workload waveguide600|waveguide200|batched64] [--n-steps N]
+                  [--tape dtype:k:interp] [--no-compare]
+  python bench.py --profile-run [--workload ...] [--n-steps N] [launch options]
 
 N > 1 runs under torchrun: every rank computes its own design (independent
 problems, no data-path collective) and rank 0 prints one JSON line.
---impl reference times the FP64 CPU oracle on the host cores instead.
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+time-truncated sample of the same workload.
 
-Other workloads (not the default line): waveguide600 = 600 x 600 x 300 cells
-at 10 nm, 16-cell CPML (10000 steps unless --n-steps); batched64 = 64
-independent vacuum cubes of 32..128 cells with 600..1500 steps each, run
-concurrently through the group calls (one step = one group forward + one
-group backward of all 64).
+Roofline: the algorithmic bytes of a forward time step (52 B per cell, +32 B
+per CPML axis of the cell) and of a reverse time step (100 B per interior
+cell, 52 B per CPML cell, +32 B per CPML axis, +16 B per design cell), plus
+the tape's codes, over the measured time of one step of that phase; the
+reverse phase is the dominant one.  The per-kernel breakdown comes from a
+sampled pass with one launch per half-step on a shortened copy of the
+workload (same grid, same per-launch work).
+
+--profile-run: one short forward + backward for profilers (ncu launch lists,
+single-kernel captures) and launch-shape sweeps; prints the timings.
+
+Other workloads: waveguide200 = 200 x 200 x 100 cells at 20 nm, 12-cell CPML,
+2000 steps; batched64 = 64 independent vacuum cubes of 32..128 cells with
+600..1500 steps each, run concurrently through the group calls (one step =
+one group forward + one group backward of all 64).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -39,29 +58,53 @@ import numpy as np  # noqa: E402
 
 METRIC = "fwd+reverse grad Gcell-updates/s & HBM roofline %; tape bytes at stated grad err"
 UNIT = "Gcell-updates/s"
+DEFAULT_TAPE = {"waveguide600": "e4m3:8:linear", "waveguide200": "e4m3:8:linear",
+                "batched64": "bf16:4:linear"}
+CPU_SAMPLE_STEPS = {"waveguide600": 2, "waveguide200": 24, "batched64": 24}
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--tape", default="bf16:4:linear")
+    p.add_argument("--workload", default="waveguide600",
+                   choices=["waveguide600", "waveguide200", "batched64"])
+    p.add_argument("--n-steps", type=int, default=0, help="override the workload's step count")
+    p.add_argument("--tape", default="", help="dtype:k:interp (default per workload)")
     p.add_argument("--compare-tape", default="f32:1:linear")
-    p.add_argument("--kernel", type=int, default=-1, help="0 split, 1 fused, -1 library default")
-    p.add_argument("--sample-every", type=int, default=50)
+    p.add_argument("--no-compare", action="store_true")
+    p.add_argument("--compare-steps", type=int, default=1)
+    p.add_argument("--kernel", type=int, default=-1, help="0 plain loads, 5 staged, -1 default")
     p.add_argument("--zgroups", type=int, default=0,
                    help="z groups per half-step (0: the library's automatic choice)")
     p.add_argument("--autotune", action="store_true",
                    help="tune the launch shapes first (autotune.tune, cached per GPU type)")
-    p.add_argument("--cpu-sample-steps", type=int, default=24)
+    p.add_argument("--sample-steps", type=int, default=400,
+                   help="time steps of the sampled per-kernel pass")
+    p.add_argument("--sample-every", type=int, default=50)
+    p.add_argument("--cpu-sample-steps", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-compare", action="store_true")
-    p.add_argument("--workload", default="waveguide200",
-                   choices=["waveguide200", "waveguide600", "batched64"])
-    p.add_argument("--n-steps", type=int, default=0, help="override the workload's step count")
-    return p.parse_args()
+    # --profile-run and its launch options
+    p.add_argument("--profile-run", action="store_true")
+    p.add_argument("--tile-y", type=int, default=0)
+    p.add_argument("--tile-x", type=int, default=0)
+    p.add_argument("--zchunk", type=int, default=0)
+    p.add_argument("--zchunk-fwd", type=int, default=-2,
+                   help="-2: library default, -1: automatic")
+    p.add_argument("--stages", type=int, default=0)
+    p.add_argument("--pdl", type=int, default=-1)
+    p.add_argument("--prefetch", type=int, default=-1)
+    p.add_argument("--compact", type=int, default=-1)
+    p.add_argument("--pml", type=int, default=0, help="profile run: CPML thickness override")
+    p.add_argument("--no-graphs", action="store_true")
+    a = p.parse_args(argv)
+    if not a.tape:
+        a.tape = DEFAULT_TAPE[a.workload]
+    if not a.cpu_sample_steps:
+        a.cpu_sample_steps = CPU_SAMPLE_STEPS[a.workload]
+    return a
 
 
 def dist_env():
@@ -89,7 +132,7 @@ def job_rate(ws: int, cell_updates: int, steps: int, seconds: float) -> float:
     return ws * cell_updates * steps / seconds / 1e9
 
 
-def workload(rank: int, n_steps=None, name: str = "waveguide200"):
+def workload(rank: int, n_steps=None, name: str = "waveguide600"):
     from paper_2603_24027_gb300 import inputs as I
     w = I.waveguide_large(seed=rank) if name == "waveguide600" else I.waveguide_mid(seed=rank)
     return w if not n_steps else w.replace(n_steps=n_steps)
@@ -114,30 +157,6 @@ def cell_classes(w):
                 slab_axes=int(slabs.sum()), cells=w.n_cells)
 
 
-def algorithmic_bytes(w):
-    """Minimum HBM bytes per launch of each kernel kind (FP32 = 4 B, FP64 accumulator 8 B).
-    Split kernels move one field family per launch; fused kernels read the
-    state once and write it once (ping-pong)."""
-    c = cell_classes(w)
-    n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
-    npml = n - ni
-    return {
-        # read E,H; write H (36 B); CPML: 2 psi read + 2 written per slab axis
-        "fwd_h": 36 * n + 16 * sa,
-        # read H,E,cb; write E (40 B); CPML as above
-        "fwd_e": 40 * n + 16 * sa,
-        # interior: read H,E,cb,lamE,lamH, write E,lamH (76 B); others 40 B; design 16 B
-        "rev_e": 76 * ni + 40 * npml + 16 * nd + 16 * sa,
-        # interior: read E,H,lamH,lamE, write H,lamE (72 B); others 36 B
-        "rev_h": 72 * ni + 36 * npml + 16 * sa,
-        # read E,H,cb, write E,H (52 B); 4 psi read + 4 written per slab axis
-        "fused_fwd": 52 * n + 32 * sa,
-        # interior: primal 12+12... read E,H,lamE,lamH,cb, write E,H,lamE,lamH (100 B);
-        # CPML-side cells adjoint only (52 B); design +16 B; psi 32 B per slab axis
-        "fused_rev": 100 * ni + 52 * npml + 16 * nd + 32 * sa,
-    }
-
-
 def tape_values(w):
     """Values of one tape sample: two tangential components on six faces."""
     P = w.pml_thickness
@@ -145,17 +164,52 @@ def tape_values(w):
     return 4 * (b * c + a * c + a * b)
 
 
-def record_bytes(w, dtype_bytes):
-    """One record launch: read every face value (FP32), write its code."""
-    return tape_values(w) * (4 + dtype_bytes)
+def code_bytes(spec: str) -> float:
+    dt = spec.split(":")[0]
+    if dt == "f32":
+        return 4.0
+    if dt in ("bf16", "f16"):
+        return 2.0
+    if dt.startswith("bdct"):
+        K = int(dt[4:]) if len(dt) > 4 else 10
+        return (K + 4) / 64.0
+    return 1.0
 
 
-def restore_bytes(w, dtype_bytes, terms):
-    """One restore launch: read `terms` samples' codes per face value, write
-    the FP32 value; plus the detector seed (read E, H; read and write the
-    adjoint) on the detector window."""
-    det = (w.det_hi[0] - w.det_lo[0]) * (w.det_hi[1] - w.det_lo[1])
-    return tape_values(w) * (terms * dtype_bytes + 4) + det * 4 * 12
+def phase_bytes(w, tape: str):
+    """Algorithmic HBM bytes of one forward and one reverse time step (FP32 =
+    4 B): forward 52 B per cell (read E, Ht, cb; write E, Ht) + 32 B per CPML
+    axis of the cell (4 auxiliaries read and written); reverse 100 B per
+    interior cell (read E, Ht, lamE, lamH, cb; write all four), 52 B per CPML
+    cell (adjoint only), + 32 B per CPML axis, + 16 B per design cell (FP64
+    accumulator read and write).  The tape adds one sample's codes every k-th
+    forward step and, per reverse step, the codes of the samples the
+    interpolation reads (2 linear, 4 cubic) and the restored FP32 values."""
+    c = cell_classes(w)
+    n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
+    _, k, interp = tape.split(":")
+    tv, cbytes = tape_values(w), code_bytes(tape)
+    terms = 2 if interp == "linear" else 4
+    fwd = 52 * n + 32 * sa + tv * (4 + cbytes) / int(k)
+    rev = 100 * ni + 52 * (n - ni) + 32 * sa + 16 * nd + tv * (terms * cbytes + 4)
+    return {"forward": fwd, "reverse": rev}
+
+
+def kernel_bytes(w):
+    """Per-launch bytes each split half-step kernel moves itself (its own
+    reads and writes), for the per-kernel breakdown only: the split reverse
+    reads E, Ht and the adjoint in both of its launches."""
+    c = cell_classes(w)
+    n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
+    npml = n - ni
+    return {"fwd_h": 36 * n + 16 * sa, "fwd_e": 40 * n + 16 * sa,
+            "rev_e": 76 * ni + 40 * npml + 16 * nd + 16 * sa,
+            "rev_h": 72 * ni + 36 * npml + 16 * sa,
+            "fused_rev": 100 * ni + 52 * npml + 16 * nd + 32 * sa}
+
+
+PHASE_KERNELS = {"forward": ["fwd_h", "fwd_e", "record"],
+                 "reverse": ["restore_seed", "rev_e", "rev_h", "fused_rev"]}
 
 
 def read_peaks():
@@ -168,17 +222,19 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def read_traffic(kernel: str, digest: str, workload: str = "waveguide200"):
-    """ncu DRAM bytes per launch recorded for this kernel build, or None."""
+def read_traffic(digest: str, workload: str):
+    """ncu DRAM bytes per launch recorded for this kernel build:
+    {kernel kind: bytes}, from profiles/traffic.txt."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
     if not os.path.exists(path):
-        return None
+        return out
     with open(path) as f:
         for line in f:
             parts = line.split("#", 1)[0].split()
-            if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest and parts[2] == workload:
-                return float(parts[3])
-    return None
+            if len(parts) >= 4 and parts[1] == digest and parts[2] == workload:
+                out[parts[0]] = float(parts[3])
+    return out
 
 
 # -------------------------------------------------------------- clocks ---
@@ -258,6 +314,69 @@ def tape_cfg(A, spec: str):
     return A.record_cfg(dt, int(k), interp)
 
 
+def apply_options(A, sim, args):
+    """Launch options given on the command line (unset ones keep the
+    library's defaults)."""
+    if args.kernel >= 0:
+        sim.set_option(A.OPT_KERNEL, args.kernel)
+    sim.set_option(A.OPT_ZGROUPS, args.zgroups)
+    for val, opt in ((args.tile_y, A.OPT_TILE_Y), (args.tile_x, A.OPT_TILE_X),
+                     (args.zchunk, A.OPT_ZCHUNK), (args.stages, A.OPT_STAGES)):
+        if val > 0:
+            sim.set_option(opt, val)
+    for val, opt in ((args.pdl, A.OPT_PDL), (args.prefetch, A.OPT_PREFETCH),
+                     (args.compact, A.OPT_COMPACT_AUX)):
+        if val >= 0:
+            sim.set_option(opt, val)
+    if args.zchunk_fwd != -2:
+        sim.set_option(A.OPT_ZCHUNK_FWD, args.zchunk_fwd)
+    if args.no_graphs:
+        sim.set_option(A.OPT_USE_GRAPHS, 0)
+
+
+def sampled_breakdown(A, fdtd, args, w, rec, dev, flush):
+    """Per-kernel in-loop costs from a pass with one launch per half-step on
+    the workload shortened to --sample-steps time steps (same grid, same work
+    per launch): CUDA events on the library's stream around sampled launches
+    (pair-minus-single intervals, see fdtd_kernel_timing)."""
+    import torch
+    ws_ = w.replace(n_steps=max(1, min(w.n_steps, args.sample_steps)))
+    sim = fdtd.Simulation(ws_, device=dev)
+    apply_options(A, sim, args)
+    sim.set_option(A.OPT_ZGROUPS, 1)
+    sim.set_option(A.OPT_SAMPLE_EVERY, args.sample_every)
+    eps = torch.from_numpy(ws_.eps).to(dev)
+    sim.forward(eps, rec)                   # capture the sampled graphs
+    sim.backward(1.0)
+    torch.cuda.synchronize()
+    ktimes, loop_ms = {}, []
+    for _ in range(2):
+        flush.random_(0, 255)
+        sim.forward(eps, rec)
+        sim.backward(1.0)
+        t = sim.last_timing()
+        loop_ms.append(t["fwd_ms"] + t["bwd_ms"])
+        for name, (ms, n) in sim.kernel_timing().items():
+            ktimes.setdefault(name, []).append((ms, n))
+    torch.cuda.synchronize()
+    per_step = {"fwd_h": 1.0, "fwd_e": 1.0, "rev_e": 1.0, "rev_h": 1.0, "fused_rev": 1.0,
+                "restore_seed": 1.0, "record": 1.0 / rec.k}
+    kb = kernel_bytes(w)
+    step_ms = statistics.median(loop_ms) / ws_.n_steps
+    kern = {}
+    for name, lst in ktimes.items():
+        n = sum(c for _, c in lst)
+        avg = sum(ms * c for ms, c in lst) / max(n, 1)
+        d = {"avg_ms": avg, "sampled_launches": n,
+             "share_of_step": avg * per_step.get(name, 1.0) / step_ms}
+        if name in kb:
+            d["own_bytes"] = kb[name]
+            d["own_gbs"] = kb[name] / (avg / 1e3) / 1e9
+        kern[name] = d
+    del sim
+    return kern, {"n_steps": ws_.n_steps, "ms_per_time_step": step_ms}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -276,109 +395,83 @@ def run_ours(args):
     w = workload(rank, args.n_steps, args.workload)
     rec = tape_cfg(A, args.tape)
     sim = fdtd.Simulation(w, device=dev)
-    if args.kernel >= 0:
-        sim.set_option(A.OPT_KERNEL, args.kernel)
-    sim.set_option(A.OPT_ZGROUPS, args.zgroups)
-    eps = torch.from_numpy(w.eps).to(dev)
+    apply_options(A, sim, args)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tuned = None
     if args.autotune:
         from paper_2603_24027_gb300 import autotune
-        tuned = autotune.tune(sim, eps, rec)
+        tuned = autotune.tune(sim, torch.from_numpy(w.eps).to(dev), rec)
+    eps_h = torch.from_numpy(w.eps).pin_memory()
+    grad_h = torch.empty(w.design_shape, dtype=torch.float32).pin_memory()
 
     def barrier():
         if ws > 1:
             dist.barrier()
 
-    def step(s, r):
-        s.forward(eps, r)
-        return s.backward(1.0)
-
     for _ in range(max(3, args.warmup)):
-        step(sim, rec)
+        sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    fwd_ms, bwd_ms = [], []
+    dev_ms, wall_s, fwd_ms, bwd_ms = [], [], [], []
     barrier()
     torch.cuda.synchronize()
-    wall0 = time.perf_counter()
     with ClockSampler(gpu_index_for_smi(local)) as clk:
-        for i in range(args.steps):
+        for _ in range(args.steps):
             flush.random_(0, 255)              # evict L2 (129 MB) before each timed step
-            starts[i].record()
-            g = step(sim, rec)
-            ends[i].record()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L, _ = sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
+            wall_s.append(time.perf_counter() - t0)
+            dev_ms.append(sim.last_host_call_ms())
             t = sim.last_timing()
             fwd_ms.append(t["fwd_ms"])
             bwd_ms.append(t["bwd_ms"])
-        torch.cuda.synchronize()
     barrier()
-    wall = time.perf_counter() - wall0
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = max_over_ranks(sum(step_ms), ws, dev)
-    launches = sim.last_timing()
-    gpu_launches = (launches["fwd_launches"] + launches["bwd_launches"] + 2) * args.steps
+    assert np.isfinite(L) and np.isfinite(grad_h.numpy()).all()
+    g_main = grad_h.clone()
+    total_ms = max_over_ranks(sum(dev_ms), ws, dev)
+    total_wall = max_over_ranks(sum(wall_s), ws, dev)
+    t = sim.last_timing()
+    gpu_launches = (t["fwd_launches"] + t["bwd_launches"] + 2) * args.steps
     cell_updates = w.n_cells * w.n_steps
     value = job_rate(ws, cell_updates, args.steps, total_ms / 1e3)
 
-    # Per-kernel live timing.  The timed steps run the default schedule, whose
-    # half-steps are split into z groups on several streams that overlap, so a
-    # launch has no duration of its own there; the per-kernel costs come from a
-    # sampled pass of the same steps with one launch per half-step (CUDA events
-    # on the library stream, pair-minus-single intervals) right after them.
-    zgroups_timed = sim.get_option(A.OPT_ZGROUPS)
-    sim.set_option(A.OPT_ZGROUPS, 1)
-    sim.set_option(A.OPT_SAMPLE_EVERY, args.sample_every)
-    step(sim, rec)                                 # capture the sampled graphs
-    torch.cuda.synchronize()
-    ktimes, one_ms = {}, []
-    for i in range(max(2, min(args.steps, 4))):
-        flush.random_(0, 255)
-        step(sim, rec)
-        t = sim.last_timing()
-        one_ms.append(t["fwd_ms"] + t["bwd_ms"])
-        for name, (ms, n) in sim.kernel_timing().items():
-            ktimes.setdefault(name, []).append((ms, n))
-    torch.cuda.synchronize()
-    sim.set_option(A.OPT_ZGROUPS, zgroups_timed)
-    sim.set_option(A.OPT_SAMPLE_EVERY, 0)
-    one_step_ms = statistics.median(one_ms)
-    algo = algorithmic_bytes(w)
+    # roofline of the two phases: algorithmic bytes of one time step over the
+    # measured time of one step of that phase (the loops' CUDA events)
     peak, peak_kind = read_peaks()
-    per_step = {"fwd_h": w.n_steps, "fwd_e": w.n_steps, "rev_e": w.n_steps, "rev_h": w.n_steps,
-                "fused_fwd": w.n_steps, "fused_rev": w.n_steps,
-                "record": -(-w.n_steps // rec.k), "restore_seed": w.n_steps}
-    dtb = {0: 4, 1: 2, 2: 2}.get(rec.dtype, 1)
-    tape_algo = {"record": record_bytes(w, dtb),
-                 "restore_seed": restore_bytes(w, dtb, 2 if rec.interp == 0 else 4)}
-    kern = {}
-    for name, lst in ktimes.items():
-        n = sum(c for _, c in lst)
-        avg = sum(ms * c for ms, c in lst) / max(n, 1)
-        share = avg * per_step[name] / one_step_ms
-        d = {"avg_ms": avg, "sampled_launches": n, "share_of_step": share}
-        ab = algo.get(name, tape_algo.get(name))
-        if ab is not None:
-            d["algorithmic_bytes"] = ab
-            d["achieved_gbs"] = ab / (avg / 1e3) / 1e9
-        kern[name] = d
-    dom = max((k for k in kern if k in algo), key=lambda k: kern[k]["share_of_step"])
+    pb = phase_bytes(w, args.tape)
+    f_ms = statistics.median(fwd_ms) / w.n_steps
+    r_ms = statistics.median(bwd_ms) / w.n_steps
     digest = B.kernel_digest()
-    traffic = read_traffic(dom, digest, args.workload)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"],
-                "peak": peak, "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
-                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+    traffic = read_traffic(digest, args.workload)
+    kern, sampled = sampled_breakdown(A, fdtd, args, w, rec, dev, flush)
+    per_launch = {"record": 1.0 / rec.k}
+    phases = {}
+    for ph, ms in (("forward", f_ms), ("reverse", r_ms)):
+        ach = pb[ph] / (ms / 1e3) / 1e9
+        # ncu DRAM bytes of one time step of the phase: set only when every
+        # kernel the phase launched has a capture for the current kernel code
+        kinds = [k for k in PHASE_KERNELS[ph] if k in kern]
+        tr = (sum(traffic[k] * per_launch.get(k, 1.0) for k in kinds)
+              if kinds and all(k in traffic for k in kinds) else None)
+        phases[ph] = {"algorithmic_bytes_per_time_step": pb[ph], "ms_per_time_step": ms,
+                      "achieved": ach, "frac": ach / peak, "traffic": tr,
+                      "kernels": kinds}
+    dom = max(phases, key=lambda p: phases[p]["ms_per_time_step"])
+    roofline = {"bound": "hbm", "kernel": f"{dom} phase (one time step)",
+                "achieved": phases[dom]["achieved"], "peak": peak, "unit": "GB/s",
+                "frac": phases[dom]["frac"], "traffic": phases[dom]["traffic"],
+                "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": algo[dom],
-                "launch_timing": "sampled pass with one launch per half-step, after the timed steps"}
-    # the whole step: every kernel's algorithmic bytes over the timed step time
-    step_bytes = sum(kern[k]["algorithmic_bytes"] * per_step[k] for k in kern
-                     if "algorithmic_bytes" in kern[k])
-    roofline["step_achieved"] = step_bytes / (total_ms / args.steps / 1e3) / 1e9
-    roofline["step_frac"] = roofline["step_achieved"] / peak
+                "timing": "CUDA events on the library stream around each timed step's time "
+                          "loops; per time step = loop time / n_steps",
+                "kernel_digest": digest, "phases": phases,
+                "breakdown": {"kernels": kern, "sampled_pass": sampled}}
+    whole = (pb["forward"] + pb["reverse"]) * w.n_steps / (total_ms / args.steps / 1e3) / 1e9
+    roofline["gradient_achieved"] = whole
+    roofline["gradient_frac"] = whole / peak
 
+    tape_bytes = sim.tape_bytes(rec)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -387,69 +480,52 @@ def run_ours(args):
         "config": {"workload": w.name, "cells": w.n_cells, "n_steps": w.n_steps,
                    "pml": w.pml_thickness, "tape": args.tape,
                    "design_box": list(w.design_shape[::-1]),
-                   "parallelism": f"replicas x{ws}", "l2": "flushed before every timed step",
-                   "zgroups": args.zgroups or "automatic (4 forward, 3 reverse)",
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "state larger than L2; L2 also flushed before every timed step",
+                   "zgroups": args.zgroups or "automatic",
                    "autotuned": None if tuned is None else
                    {"options": tuned["options"], "cached": tuned["cached"]},
                    "fwd_ms": statistics.median(fwd_ms), "bwd_ms": statistics.median(bwd_ms),
-                   "one_launch_per_half_step_ms": one_step_ms,
-                   # forward-only and reverse-only rates (cells x steps / phase time)
-                   "fwd_gcell_updates_per_s": w.n_cells * w.n_steps / statistics.median(fwd_ms) / 1e6,
-                   "bwd_gcell_updates_per_s": w.n_cells * w.n_steps / statistics.median(bwd_ms) / 1e6,
-                   "wall_s": wall},
+                   "fwd_gcell_updates_per_s": cell_updates / statistics.median(fwd_ms) / 1e6,
+                   "bwd_gcell_updates_per_s": cell_updates / statistics.median(bwd_ms) / 1e6,
+                   "timed_through": "fdtd_value_and_grad_host (value: device part; e2e: wall)"},
         "gpu_launches": gpu_launches,
         "roofline": roofline,
-        "kernels": kern,
         "clocks": clk.summary(),
-        "tape_bytes": sim.tape_bytes(rec),
+        "tape_bytes": tape_bytes,
+        "tape_reduction_vs_f32_k1": sim.tape_bytes(tape_cfg(A, "f32:1:linear")) / tape_bytes,
     }
+    nd = int(np.prod(w.design_shape))
+    out["e2e"] = {"value": job_rate(ws, cell_updates, args.steps, total_wall), "unit": UNIT,
+                  "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
+    del sim
 
-    # the same code with the uncompressed FP32 tape, and gradient agreement
+    # the same code with the uncompressed FP32 tape: speed and gradient agreement
     if not args.no_compare:
         rec32 = tape_cfg(A, args.compare_tape)
         sim32 = fdtd.Simulation(w, device=dev)
-        if args.kernel >= 0:
-            sim32.set_option(A.OPT_KERNEL, args.kernel)
-        for _ in range(2):
-            g32 = step(sim32, rec32)
-        torch.cuda.synchronize()
-        ts = []
-        for i in range(args.steps):
+        apply_options(A, sim32, args)
+        g32 = torch.empty(w.design_shape, dtype=torch.float32).pin_memory()
+        sim32.value_and_grad_host(eps_h, rec32, 1.0, g32)
+        ts, tw = [], []
+        for _ in range(max(1, args.compare_steps)):
             flush.random_(0, 255)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            g32 = step(sim32, rec32)
-            b.record()
             torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        v32 = cell_updates / (sum(ts) / args.steps / 1e3) / 1e9
-        g64, g3264 = g.double(), g32.double()
-        cosv = float((g64 * g3264).sum() / (g64.norm() * g3264.norm()))
-        relv = float((g64 - g3264).norm() / g3264.norm())
-        out["compare"] = {"tape": args.compare_tape, "value": v32,
+            t0 = time.perf_counter()
+            sim32.value_and_grad_host(eps_h, rec32, 1.0, g32)
+            tw.append(time.perf_counter() - t0)
+            ts.append(sim32.last_host_call_ms())
+        v32 = cell_updates / (sum(ts) / len(ts) / 1e3) / 1e9
+        e32 = cell_updates / (sum(tw) / len(tw)) / 1e9
+        a64, b64 = g_main.double(), g32.double()
+        out["compare"] = {"tape": args.compare_tape, "value": v32, "e2e": e32,
                           "tape_bytes": sim32.tape_bytes(rec32),
-                          "tape_reduction": sim32.tape_bytes(rec32) / sim.tape_bytes(rec),
+                          "tape_reduction": sim32.tape_bytes(rec32) / tape_bytes,
                           "speedup_vs_compare": value / ws / v32,
-                          "grad_cosine": cosv, "grad_rel_err": relv}
+                          "e2e_speedup_vs_compare": out["e2e"]["value"] / ws / e32,
+                          "grad_cosine": float((a64 * b64).sum() / (a64.norm() * b64.norm())),
+                          "grad_rel_err": float((a64 - b64).norm() / b64.norm())}
         del sim32
-
-    # end to end through the public host-buffer call
-    eps_h = torch.from_numpy(w.eps).pin_memory()
-    grad_h = torch.empty(w.design_shape, dtype=torch.float32).pin_memory()
-    sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
-    barrier()
-    torch.cuda.synchronize()
-    te = []
-    for i in range(args.steps):
-        flush.random_(0, 255)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.value_and_grad_host(eps_h, rec, 1.0, grad_h)
-        te.append(time.perf_counter() - t0)
-    e2e_t = max_over_ranks(sum(te), ws, dev)
-    nd = int(np.prod(w.design_shape))
-    out["e2e"] = {"value": job_rate(ws, cell_updates, args.steps, e2e_t), "unit": UNIT,
-                  "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps, args.workload)
@@ -459,9 +535,43 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------- profile run ---
+
+def run_profile(args):
+    """One short forward + backward with the given launch options (one launch
+    per half-step unless --zgroups says otherwise), for profilers."""
+    import torch
+    from paper_2603_24027_gb300 import _capi as A
+    from paper_2603_24027_gb300 import build as B
+    from paper_2603_24027_gb300 import fdtd
+    from paper_2603_24027_gb300 import inputs as I
+
+    B.build()
+    w = I.CONFIGS[args.workload]().replace(n_steps=args.n_steps or 12)
+    if args.pml:
+        w = w.replace(pml_thickness=args.pml)
+    rec = tape_cfg(A, args.tape)
+    sim = fdtd.Simulation(w)
+    if args.zgroups == 0:
+        args.zgroups = 1
+    apply_options(A, sim, args)
+    sim.set_option(A.OPT_SAMPLE_EVERY, args.sample_every if args.sample_every != 50 else 0)
+    eps = torch.from_numpy(w.eps).cuda()
+    for _ in range(min(args.warmup, 1) + 1):
+        L = sim.forward(eps, rec)
+        g = sim.backward(1.0)
+    torch.cuda.synchronize()
+    opts = {name: sim.get_option(getattr(A, name)) for name in
+            ("OPT_KERNEL", "OPT_TILE_Y", "OPT_TILE_X", "OPT_ZCHUNK", "OPT_ZCHUNK_FWD",
+             "OPT_STAGES", "OPT_ZGROUPS", "OPT_COMPACT_AUX", "OPT_PDL", "OPT_PREFETCH")}
+    print(json.dumps(dict(workload=w.name, n_steps=w.n_steps, pml=w.pml_thickness,
+                          tape=args.tape, options=opts, L=L, grad_l1=float(g.abs().sum()),
+                          timing=sim.last_timing(), kernels=sim.kernel_timing())))
+
+
 # ------------------------------------------------------------- oracle ---
 
-def oracle_step(n_steps: int, name: str = "waveguide200"):
+def oracle_step(n_steps: int, name: str):
     from oracle import oracle as O
     w = workload(0, n_steps=n_steps, name=name)
     t0 = time.perf_counter()
@@ -469,12 +579,10 @@ def oracle_step(n_steps: int, name: str = "waveguide200"):
     return time.perf_counter() - t0, w
 
 
-def cpu_baseline(n_steps: int, name: str = "waveguide200"):
+def cpu_baseline(n_steps: int, name: str):
     from oracle import build as ob
     from oracle import oracle as O
     ob.build()
-    if name == "waveguide600":          # 27x the cells: keep the sample at a similar CPU time
-        n_steps = max(2, n_steps // 12)
     dt, w = oracle_step(n_steps, name)
     return {"value": w.n_cells * w.n_steps / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle",
@@ -491,10 +599,10 @@ def run_reference(args):
     ob.build()
     n = args.cpu_sample_steps
     for _ in range(max(3, args.warmup)):
-        oracle_step(max(2, n // 4))
+        oracle_step(max(1, n // 2), args.workload)
     ts = []
     for _ in range(args.steps):
-        dt, w = oracle_step(n)
+        dt, w = oracle_step(n, args.workload)
         ts.append(dt)
     value = w.n_cells * n * len(ts) / sum(ts) / 1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -504,8 +612,8 @@ def run_reference(args):
            "config": {"workload": w.name, "cells": w.n_cells, "n_steps_sample": n},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
                             "kind": "oracle",
-                            "sample": f"each step: FP64 oracle gradient of the 200x200x100 "
-                                      f"workload over {n} steps"},
+                            "sample": f"each step: FP64 oracle gradient of the "
+                                      f"{w.nx}x{w.ny}x{w.nz} workload over {n} steps"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -531,7 +639,7 @@ def run_batched(args):
     rec = tape_cfg(A, args.tape)
     sims = [fdtd.Simulation(w, device=dev) for w in wl]
     for s in sims:
-        s.set_option(A.OPT_ZGROUPS, args.zgroups)
+        apply_options(A, s, args)
     eps = [torch.from_numpy(w.eps).to(dev) for w in wl]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -557,11 +665,11 @@ def run_batched(args):
     total_ms = max_over_ranks(sum(ts), ws, dev)
     cell_updates = sum(w.n_cells * w.n_steps for w in wl)
     value = job_rate(ws, cell_updates, args.steps, total_ms / 1e3)
-    # aggregate algorithmic bytes of one step (all problems, all launches)
+    # aggregate algorithmic bytes of one step (all problems, both phases)
     byts = 0
     for w in wl:
-        ab = algorithmic_bytes(w)
-        byts += w.n_steps * (ab["fwd_h"] + ab["fwd_e"] + ab["rev_e"] + ab["rev_h"])
+        pb = phase_bytes(w, args.tape)
+        byts += w.n_steps * (pb["forward"] + pb["reverse"])
     peak, peak_kind = read_peaks()
     achieved = byts / (total_ms / args.steps / 1e3) / 1e9
     launches = sum(s.last_timing()["fwd_launches"] + s.last_timing()["bwd_launches"] + 2
@@ -596,10 +704,10 @@ def run_batched(args):
                    "parallelism": f"replicas x{ws}, 64 concurrent problems",
                    "l2": "flushed before every timed step"},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "all kernels, aggregate over 64 concurrent problems",
+        "roofline": {"bound": "hbm", "kernel": "whole gradient, all 64 concurrent problems",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"
+                     "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "algorithmic_bytes_per_step": byts},
         "clocks": clk.summary(),
@@ -615,7 +723,9 @@ def run_batched(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_run:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64":
         run_batched(args)

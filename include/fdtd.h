@@ -302,6 +302,13 @@ int fdtd_kernel_timing(const fdtd_handle* h, int kind, float* avg_ms, int* sampl
 int fdtd_last_timing(const fdtd_handle* h, float* fwd_ms, float* bwd_ms, int* fwd_launches,
                      int* bwd_launches);
 
+/* Device time (CUDA events on the library's stream, milliseconds) of the
+ * last successful fdtd_value_and_grad_host between the end of its input
+ * copy and the start of its output copy: eps -> cb, the forward and
+ * backward time loops, the host waits between them and the gradient
+ * finalisation; 0 before the first such call. */
+int fdtd_last_host_call_ms(const fdtd_handle* h, float* device_ms);
+
 /* ------------------------------------------------ introspection --------- */
 
 /* Host copies of the plan's tables (no device needed).  which: 0 b_E,

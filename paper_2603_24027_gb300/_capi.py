@@ -95,6 +95,7 @@ _PROTOS = {
     "fdtd_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "fdtd_last_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fdtd_last_host_call_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "fdtd_kernel_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float),
                                      C.POINTER(C.c_int)]),
     "fdtd_pml_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),

@@ -101,7 +101,8 @@ struct fdtd_handle {
   int scount[FDTD_K_KINDS];
 
   cudaStream_t stream;
-  cudaEvent_t ev_in, ev_out, t0, t1, t2, t3;
+  cudaEvent_t ev_in, ev_out, t0, t1, t2, t3, t4, t5;
+  float host_call_ms;         // device part of the last fdtd_value_and_grad_host
   bool cuda_ready;
   std::map<GraphKey, GraphEntry> graphs;
   int launches_fwd, launches_bwd;
@@ -588,6 +589,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->cuda_ready = false;
   h->launches_fwd = h->launches_bwd = 0;
   h->fwd_ms = h->bwd_ms = 0.f;
+  h->host_call_ms = 0.f;
   build_profiles(h);
   build_source(h);
   build_faces(h);
@@ -615,6 +617,7 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
     cudaEventDestroy(h->ev_in); cudaEventDestroy(h->ev_out);
     cudaEventDestroy(h->t0); cudaEventDestroy(h->t1);
     cudaEventDestroy(h->t2); cudaEventDestroy(h->t3);
+    cudaEventDestroy(h->t4); cudaEventDestroy(h->t5);
     for (cudaEvent_t ev : h->zev) cudaEventDestroy(ev);
     for (cudaStream_t st : h->zs) cudaStreamDestroy(st);
     if (h->zfork) cudaEventDestroy(h->zfork);
@@ -775,6 +778,8 @@ static int ensure_cuda(fdtd_handle* h) {
   CK(h, cudaEventCreate(&h->t1));
   CK(h, cudaEventCreate(&h->t2));
   CK(h, cudaEventCreate(&h->t3));
+  CK(h, cudaEventCreate(&h->t4));
+  CK(h, cudaEventCreate(&h->t5));
   h->cuda_ready = true;
   return FDTD_OK;
 }
@@ -1508,15 +1513,18 @@ extern "C" int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps,
   CK(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0));
   CK(h, cudaMemcpyAsync(h->ws + L.eps, h_eps, n * sizeof(float), cudaMemcpyHostToDevice,
                         h->stream));
+  CK(h, cudaEventRecord(h->t4, h->stream));   // device part: after the input copy ...
   rc = fdtd_forward(h, (const float*)(h->ws + L.eps), rec, objective);
   if (rc) return rc;
   rc = backward_async(h, seed, 0.0);
   if (rc) return rc;
   rc = backward_finish(h, (float*)(h->ws + L.gout));
   if (rc) return rc;
+  CK(h, cudaEventRecord(h->t5, h->stream));   // ... up to the output copy
   CK(h, cudaMemcpyAsync(h_grad, h->ws + L.gout, nd * sizeof(float), cudaMemcpyDeviceToHost,
                         h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaEventElapsedTime(&h->host_call_ms, h->t4, h->t5));
   return FDTD_OK;
 }
 
@@ -1556,6 +1564,12 @@ extern "C" int fdtd_last_timing(const fdtd_handle* h, float* fwd_ms, float* bwd_
   if (bwd_ms) *bwd_ms = h->bwd_ms;
   if (fwd_launches) *fwd_launches = h->launches_fwd;
   if (bwd_launches) *bwd_launches = h->launches_bwd;
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_last_host_call_ms(const fdtd_handle* h, float* device_ms) {
+  if (!h || !device_ms) return FDTD_EINVAL;
+  *device_ms = h->host_call_ms;
   return FDTD_OK;
 }
 

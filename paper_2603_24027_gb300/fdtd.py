@@ -203,6 +203,13 @@ class Simulation:
                                              C.byref(lb)))
         return dict(fwd_ms=f.value, bwd_ms=b.value, fwd_launches=lf.value, bwd_launches=lb.value)
 
+    def last_host_call_ms(self) -> float:
+        """Device time of the last value_and_grad_host between its input and
+        output copies (ms)."""
+        ms = C.c_float()
+        self._check(A.lib().fdtd_last_host_call_ms(self.h, C.byref(ms)))
+        return ms.value
+
     def kernel_timing(self):
         """{kernel name: (average ms, sampled launches)} of the last runs."""
         out = {}
