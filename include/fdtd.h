@@ -268,7 +268,7 @@ enum {
                                    (FDTD_OPT_SAMPLE_EVERY) records only loops that run
                                    with one launch per half-step; the no-allocation entry
                                    point always runs that way */
-  FDTD_OPT_INJECT_WAIT_TIMEOUT = 14 /* failure-detection test hook: L > 0 makes every backward
+  FDTD_OPT_INJECT_WAIT_TIMEOUT = 14, /* failure-detection test hook: L > 0 makes every backward
                                    (fdtd_backward, fdtd_backward2, the group and no-allocation
                                    calls) start with one bounded device wait that nothing
                                    completes; it gives up after L SM cycles and sets the
@@ -276,6 +276,19 @@ enum {
                                    FDTD_ETIMEOUT with the CUDA context usable.  0 (default) =
                                    off.  Injects no fault: the wait is the same bounded wait
                                    as fdtd_selftest_wait */
+  FDTD_OPT_REVERSE = 15         /* kernel 5: how a reverse time step runs.  0 (default) =
+                                   automatic: fused with 32 x 8 tiles, else split; 1 = split:
+                                   a reverse E phase and a reverse H phase, each updating the
+                                   primal and the adjoint fields in place; 2 = fused: one
+                                   launch for the primal fields (both inverse half-steps,
+                                   interior cells, with dL/d(eps) accumulated) and one for the
+                                   adjoint fields (both transposed half-steps, every cell),
+                                   each reading every field once and writing it once into
+                                   the other buffer of a ping-pong pair (the workspace holds
+                                   a second field and adjoint buffer); FDTD_EINVAL at
+                                   fdtd_forward with other tiles.  Results agree with the
+                                   split phases: primal fields bit for bit, gradients to
+                                   rounding */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);
@@ -283,7 +296,7 @@ int fdtd_get_option(const fdtd_handle* h, int option, int* value);
 /* Kernel kinds for fdtd_kernel_timing. */
 enum {
   FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
-  FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_FUSED_FWD = 6, FDTD_K_FUSED_REV = 7,
+  FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_REV_PRIMAL = 6, FDTD_K_REV_ADJOINT = 7,
   FDTD_K_MONITOR = 8, FDTD_K_KINDS = 9
 };
 /* Average in-loop cost (ms) per launch of one kernel kind in the last
@@ -373,6 +386,20 @@ int fdtd_bdct_basis(float* out);
  * schedule, group g of a half-step waits for groups g - 1 and g + 1 of the
  * half-step before (and for its own through stream order). */
 int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi);
+
+/* The (tile x, tile y, z chunk) units of the three launches of a fused
+ * reverse step (FDTD_OPT_REVERSE), 32 x 8 tiles and zchunk planes (0 = the
+ * whole column) on an nx x ny x nz grid with P CPML cells (host only, no
+ * device use).  counts[0..2] receive the unit counts of the primal launch
+ * (every unit with an interior cell), of the adjoint launch without CPML
+ * terms (units whose cells and neighbours x0-1 .. x0+32, y0-1 .. y0+8, planes
+ * k0-1 .. k1 are all interior) and of the adjoint launch with CPML (all other
+ * units).  With units != NULL the units follow as int triples in that order
+ * (counts[0] + counts[1] + counts[2] triples, at most max_units triples,
+ * else FDTD_EINVAL).  The two adjoint lists together cover every unit of the
+ * grid exactly once. */
+int fdtd_reverse_units(int nx, int ny, int nz, int P, int zchunk, int* counts, int* units,
+                       int max_units);
 
 /* Self-test of the bounded device waits (failure detection without a
  * fault): one CTA arms an mbarrier for a copy that is never issued and waits

@@ -28,11 +28,11 @@ BDCT_DEFAULT_COEFFS = 10
 INTERP = {"linear": 0, "cubic": 1}
 OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY = range(5)
 OPT_STAGES, OPT_PDL, OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX, OPT_EXACT_REVERSAL, \
-    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT = range(6, 15)
-K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_FUSED_FWD, K_FUSED_REV, K_MONITOR = \
+    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT, OPT_REVERSE = range(6, 16)
+K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_REV_PRIMAL, K_REV_ADJOINT, K_MONITOR = \
     range(9)
-KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "fused_fwd",
-                "fused_rev", "monitor"]
+KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "rev_primal",
+                "rev_adjoint", "monitor"]
 
 
 class Grid(C.Structure):
@@ -119,6 +119,8 @@ _PROTOS = {
     "fdtd_zgroup_ranges": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_selftest_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p]),
     "fdtd_status_of_error_word": (C.c_int, [C.c_uint]),
+    "fdtd_reverse_units": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(C.c_int), C.c_void_p, C.c_int]),
     "fdtd_value_and_grad_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                               C.c_double, C.POINTER(C.c_double), C.c_void_p]),
 }

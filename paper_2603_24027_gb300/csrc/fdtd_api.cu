@@ -40,7 +40,7 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait;
+      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait, reverse;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -87,6 +87,7 @@ struct fdtd_handle {
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_stages, opt_pdl,
       opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
   int opt_inject_wait;        // FDTD_OPT_INJECT_WAIT_TIMEOUT (SM cycles; 0 = off)
+  int opt_reverse;            // FDTD_OPT_REVERSE: 0 automatic, 1 split phases, 2 fused
   // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
   // three events (the last launch of an even / odd phase, the join), plus the
   // fork event
@@ -375,6 +376,16 @@ static void interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int
   }
 }
 
+// The reverse step of kernel 5 runs as two fused launches (primal and
+// adjoint, kernels_rev_fused.cu) unless FDTD_OPT_REVERSE asks for the split
+// phases; the fused kernels are built for 32 x 8 tiles.
+static bool fused_reverse(const fdtd_handle* h) {
+  if (h->opt_kernel != 5 || h->opt_reverse == 1) return false;
+  const int ty = h->opt_tile_y < 2 ? 2 : h->opt_tile_y;
+  const int tx = (ty == 8 && h->opt_stages <= 3 && h->opt_tile_x == 40) ? 40 : 32;
+  return ty == 8 && tx == 32;
+}
+
 // ---------------------------------------------------------------- layout ---
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 static int rup4(int x) { return (x + 3) & ~3; }
@@ -423,11 +434,16 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   size_t psbF = al((size_t)L.plF.total * sizeof(float));
   size_t psbL = al((size_t)L.plL.total * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
+  // the fused reverse step writes the new fields and adjoint fields next to
+  // the old ones (ping-pong pairs)
+  const bool pingpong = fused_reverse(h);
   size_t off = 0;
   L.F[0] = off; off += f6;
   L.F[1] = L.F[0];
+  if (pingpong) { L.F[1] = off; off += f6; }
   L.L[0] = off; off += f6;
   L.L[1] = L.L[0];
+  if (pingpong) { L.L[1] = off; off += f6; }
   L.cb = off; off += al(nc * sizeof(float));
   L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
   L.psiF[0] = off; off += psbF;
@@ -582,6 +598,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_compact = 1;
   h->opt_exact = 0;
   h->opt_inject_wait = 0;
+  h->opt_reverse = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
     h->savg[q] = 0.f;
     h->scount[q] = 0;
@@ -708,6 +725,11 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < 0 || value > kMaxZGroups) return fail(h, FDTD_EINVAL, "zgroups must be 0..16");
       h->opt_zgroups = value;
       break;
+    case FDTD_OPT_REVERSE:
+      if (value < 0 || value > 2) return fail(h, FDTD_EINVAL, "reverse must be 0, 1 or 2");
+      if (value != h->opt_reverse) h->have_forward = false;   // the workspace layout changes
+      h->opt_reverse = value;
+      break;
     case FDTD_OPT_INJECT_WAIT_TIMEOUT:
       if (value < 0) return fail(h, FDTD_EINVAL, "injected wait limit must be >= 0");
       h->opt_inject_wait = value;
@@ -740,6 +762,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
     case FDTD_OPT_ZGROUPS: *value = h->opt_zgroups; break;
     case FDTD_OPT_INJECT_WAIT_TIMEOUT: *value = h->opt_inject_wait; break;
+    case FDTD_OPT_REVERSE: *value = h->opt_reverse; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -1072,7 +1095,8 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
 }
 
 static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR};
-static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_FUSED_REV};
+static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_REV_PRIMAL,
+                                FDTD_K_REV_ADJOINT};
 
 // Enqueue the forward time loop on h->stream (capturable).
 static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
@@ -1188,12 +1212,27 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   Det det = a.det;
   const Det det2 = det2_of(h);
   int cur = 0;
-  const bool rpair = h->opt_kernel == 5;
+  const bool fused = fused_reverse(h);
+  const bool rpair = h->opt_kernel == 5 && !fused;
   LagMaps lrmaps[2];
   for (int b = 0; b < 2; ++b)
     if (rpair && (e = encode_lag_maps(a.F, a.L, (const float*)(h->ws + L.cb),
                                       (const float*)(h->ws + L.psiL[b]), a.g, a.tile_y, a.tile_x,
                                       L.plL, &lrmaps[b])))
+      return e;
+  // fused reverse step: buffer cur of the fields, the adjoint fields and the
+  // auxiliaries is read, buffer cur ^ 1 written (the forward's state is in
+  // buffer 0)
+  RevMaps rmaps[2];
+  const RevUnits U = rev_units(a.g, a.zchunk);
+  // the adjoint launches run on a side stream unless kernel timing is being
+  // sampled or one launch per half-step is asked for (FDTD_OPT_ZGROUPS = 1)
+  const bool conc = fused && h->opt_sample == 0 && h->opt_zgroups != 1 && !h->zs.empty() &&
+                    h->zev.size() >= 3;
+  for (int b = 0; fused && b < 2; ++b)
+    if ((e = encode_rev_maps((const float*)(h->ws + L.F[b]), (const float*)(h->ws + L.L[b]),
+                             (const float*)(h->ws + L.cb), (const float*)(h->ws + L.psiL[b]), a.g,
+                             L.plL, &rmaps[b])))
       return e;
   const BdctLayout bl =
       rec->dtype == kTapeBdct ? bdct_layout(h->faces, bdct_coeffs(rec)) : BdctLayout{};
@@ -1202,6 +1241,12 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
   for (int n = h->N - 1; n >= 0; --n) {
     if ((e = zg.join())) return e;
+    if (fused) {
+      a.F = (float*)(h->ws + L.F[cur]);
+      a.L = (float*)(h->ws + L.L[cur]);
+      a.Fn = (float*)(h->ws + L.F[cur ^ 1]);
+      a.Ln = (float*)(h->ws + L.L[cur ^ 1]);
+    }
     Interp ip;
     interp_weights(h, rec, n, 0, ip.slot[0], ip.w[0]);
     interp_weights(h, rec, n, 1, ip.slot[1], ip.w[1]);
@@ -1218,6 +1263,30 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
     a.jn = h->wave[n];
     a.psiA = (float*)(h->ws + L.psiL[cur]);
     a.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
+    if (fused) {
+      // the primal and the adjoint launches of a step are independent: with
+      // a side stream the adjoint runs beside the primal, and the next
+      // step's restore waits for both
+      cudaStream_t side = conc ? h->zs[0] : h->stream;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[0], h->stream))) return e;
+        if ((e = cudaStreamWaitEvent(side, h->zev[0], 0))) return e;
+      }
+      if ((e = smp.before(FDTD_K_REV_PRIMAL))) return e;
+      if ((e = launch_rev_fused(0, rmaps[cur], a, U, h->stream))) return e;
+      if ((e = smp.after(FDTD_K_REV_PRIMAL))) return e;
+      if ((e = smp.before(FDTD_K_REV_ADJOINT))) return e;
+      if ((e = launch_rev_fused(1, rmaps[cur], a, U, side))) return e;
+      if ((e = launch_rev_fused(2, rmaps[cur], a, U, side))) return e;
+      if ((e = smp.after(FDTD_K_REV_ADJOINT))) return e;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[1], side))) return e;
+        if ((e = cudaStreamWaitEvent(h->stream, h->zev[1], 0))) return e;
+      }
+      cur ^= 1;
+      nl += 4;
+      continue;
+    }
     if (zg.active()) {
       const LagMaps& m = lrmaps[cur];
       if ((e = zg.fork())) return e;
@@ -1286,6 +1355,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.zchunk_fwd = h->opt_zchunk_fwd;
   key.zgroups = h->opt_zgroups;
   key.inject_wait = h->opt_inject_wait;
+  key.reverse = h->opt_reverse;
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1344,6 +1414,8 @@ static int check_kernel_options(fdtd_handle* h) {
   if (h->opt_exact && (h->opt_kernel != 5 || h->opt_tile_y != 8 || h->opt_stages != 2 ||
                        lag_tile_x(h) != 32))
     return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 with its default tiles");
+  if (h->opt_reverse == 2 && !fused_reverse(h))
+    return fail(h, FDTD_EINVAL, "the fused reverse step is built into kernel 5 with 32 x 8 tiles");
   return FDTD_OK;
 }
 
@@ -1439,6 +1511,9 @@ static int backward_async(fdtd_handle* h, double seed, double seed2) {
   if (rc) return rc;
   h->launches_bwd = nl;
   h->have_forward = false;
+  // the fused reverse step leaves the reconstructed fields in the buffer of
+  // the last step's output
+  h->fwd_buf = fused_reverse(h) ? (h->N & 1) : 0;
   return FDTD_OK;
 }
 
@@ -1451,7 +1526,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaEventElapsedTime(&h->bwd_ms, h->t2, h->t3));
-  collect_samples(h, 1, kBwdKinds, 4);
+  collect_samples(h, 1, kBwdKinds, 5);
   int rc = finish(h);
   if (rc) return rc;
   return check_err(h, err);
@@ -1711,6 +1786,38 @@ extern "C" int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi) {
   const int n = std::min(G, nch);
   for (int g = 0; g < n; ++g) zgroup_range(nch, n, g, &lo[g], &hi[g]);
   return n;
+}
+
+extern "C" int fdtd_reverse_units(int nx, int ny, int nz, int P, int zchunk, int* counts,
+                                  int* units, int max_units) {
+  if (nx < 1 || ny < 1 || nz < 1 || P < 0 || zchunk < 0 || !counts) return FDTD_EINVAL;
+  Geo g;
+  memset(&g, 0, sizeof g);
+  g.nx = nx; g.ny = ny; g.nz = nz; g.P = P;
+  const RevUnits U = rev_units(g, zchunk);
+  const long long np = (long long)(U.px1 - U.px0) * (U.py1 - U.py0) * (U.pz1 - U.pz0);
+  const long long ni = (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0) * (U.iz1 - U.iz0);
+  const long long nall = (long long)U.ntx * U.nty * U.nzc;
+  if (np > INT_MAX || nall > INT_MAX) return FDTD_EINVAL;
+  counts[0] = (int)np;
+  counts[1] = (int)ni;
+  counts[2] = (int)(nall - ni);
+  if (!units) return FDTD_OK;
+  const long long n = np + nall;
+  if (n > max_units) return FDTD_EINVAL;
+  int* o = units;
+  for (int z = U.pz0; z < U.pz1; ++z)
+    for (int y = U.py0; y < U.py1; ++y)
+      for (int x = U.px0; x < U.px1; ++x) { *o++ = x; *o++ = y; *o++ = z; }
+  for (int z = U.iz0; z < U.iz1; ++z)
+    for (int y = U.iy0; y < U.iy1; ++y)
+      for (int x = U.ix0; x < U.ix1; ++x) { *o++ = x; *o++ = y; *o++ = z; }
+  for (long long u = 0; u < nall - ni; ++u) {
+    int tx, ty, cz;
+    rev_unit_of(U, u, &tx, &ty, &cz);
+    *o++ = tx; *o++ = ty; *o++ = cz;
+  }
+  return FDTD_OK;
 }
 
 extern "C" int fdtd_selftest_wait(unsigned* d_flag, long long limit_cycles, void* cuda_stream) {

@@ -232,6 +232,8 @@ struct StepArgs {
   float* psiA;     // psi set read (and written in place by the forward)
   float* psiB;     // psi set written (ping-pong)
   float* L;        // adjoint fields (6 components, same layout as F)
+  float* Fn;       // fused reverse step: fields written (the other buffer of a ping-pong pair)
+  float* Ln;       // fused reverse step: adjoint fields written
   double* gacc;    // FP64 design-box accumulator [dz][dy][dx]
   int dlo[3], dhi[3];
   Src src;
@@ -240,6 +242,7 @@ struct StepArgs {
   float jn;        // J waveform value of this step
   int zchunk;
   int zc0, zc1;     // two-cells-per-thread kernels: z chunks [zc0, zc1) of this launch (zc1 = 0: to the last)
+  int t0x, t0y;     // fused reverse step: first tile of a launch along x and y
   int tile_y;
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
@@ -271,6 +274,34 @@ cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, con
 // Staged half-steps, two x-cells per thread (kernel 5; tile height >= 2).
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
+// The fused reverse step (kernels_rev_fused.cu): tensor maps of 32 x 8
+// tiles over the current field, adjoint and auxiliary buffers (boxes: F40 /
+// cb40 / L40 (TW+8) x (TY+2), F36 / cb36 / L36 (TW+4) x (TY+1), Qx40
+// (TW+8) x (TY+1), Qy36 (TW+4) x (TY+2), Qz36 (TW+4) x (TY+1), Qxw (TW+4) x
+// TY, Qyw TW x (TY+1), Qzo TW x TY).
+struct alignas(64) RevMaps {
+  CUtensorMap F40, F36, cb36, cb40, L40, L36, Qx40, Qy36, Qz36, Qxw, Qyw, Qzo;
+};
+cudaError_t encode_rev_maps(const float* F, const float* L, const float* cb, const float* psiA,
+                            const Geo& g, const PsiLayout& pl, RevMaps* m);
+// Tiles (32 x 8) and z chunks of the three launches of a fused reverse step:
+// the primal one covers the tiles [px0, px1) x [py0, py1) and chunks
+// [pz0, pz1) holding interior cells; the adjoint one without CPML terms the
+// box [ix0, ix1) x [iy0, iy1) x [iz0, iz1) of units whose every evaluated
+// term lies in the interior; the adjoint one with CPML every other unit of
+// the ntx x nty x nzc grid.
+struct RevUnits {
+  int ntx, nty, nzc;
+  int px0, px1, py0, py1, pz0, pz1;
+  int ix0, ix1, iy0, iy1, iz0, iz1;
+};
+RevUnits rev_units(const Geo& g, int zchunk);
+void rev_unit_of(const RevUnits& U, long long u, int* tx, int* ty, int* cz);
+// which: 0 primal (E^n, Ht^{n-1/2}, dL/dcb), 1 adjoint over the CPML-free
+// units, 2 adjoint over the CPML units.  Reads a.F, a.L, a.psiA; writes
+// a.Fn, a.Ln, a.psiB, a.gacc.
+cudaError_t launch_rev_fused(int which, const RevMaps& m, const StepArgs& a, const RevUnits& U,
+                             cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,
                             cudaStream_t s);

@@ -20,154 +20,6 @@
 
 namespace fdtd {
 
-namespace lag2 {
-
-__device__ __forceinline__ float2 ld2(const float* b, int i) {
-  return *reinterpret_cast<const float2*>(b + i);
-}
-
-// Store the pair (u, v) at element offset q (q even, 8-byte aligned because
-// the row pitch is a multiple of 8): one 8-byte store when both cells are
-// written, else the flagged one.
-__device__ __forceinline__ void st2(float* p, long long q, float u, float v, bool f0, bool f1) {
-  if (f0 && f1) {
-    *reinterpret_cast<float2*>(p + q) = make_float2(u, v);
-  } else {
-    if (f0) p[q] = u;
-    if (f1) p[q + 1] = v;
-  }
-}
-
-#ifdef FDTD_BOUNDS_CHECK
-// Bounds-checked test build: a store must land in the fields, the adjoint
-// fields or one of the two auxiliary sets of the launch, else it is skipped
-// and the error word records ERR_BOUNDS.
-__device__ __forceinline__ bool in_buf(const float* p, const float* base, long long n) {
-  return base && p >= base && p < base + n;
-}
-__device__ __forceinline__ bool store_ok(const StepArgs& a, const float* p) {
-  const long long n6 = 6 * a.g.nc;
-  if (in_buf(p, a.F, n6) || in_buf(p, a.L, n6) || in_buf(p, a.psiA, a.pl.total) ||
-      in_buf(p, a.psiB, a.pl.total))
-    return true;
-  atomicOr(a.err, ERR_BOUNDS);
-  return false;
-}
-#define ST2(p, q, u, v, f0, f1) \
-  st2(p, q, u, v, (f0) && store_ok(a, (p) + (q)), (f1) && store_ok(a, (p) + (q) + 1))
-#else
-#define ST2(p, q, u, v, f0, f1) st2(p, q, u, v, f0, f1)
-#endif
-
-// Forward CPML recursion of one derivative d (Eq. 5 form): the updated psi
-// goes to *s, the stretched derivative is returned.
-__device__ __forceinline__ float cpml(float d, float psi_old, float b, float a, float kv, float* s) {
-  const float t = __fmaf_rn(b, psi_old, __fmul_rn(a, d));
-  *s = t;
-  return __fmaf_rn(kv, d, t);
-}
-
-// Adjoint of the recursion: returns the curl term with the CPML response;
-// the adjoint auxiliary for the next (earlier) step goes to *out.
-__device__ __forceinline__ float adj(float v, float lpsi, float b, float a, float kv, float* out) {
-  const float mu = lpsi + v;
-  *out = b * mu;
-  return kv * v + a * mu;
-}
-
-// Programmatic dependent launch: wait until the previous kernel in the stream
-// has completed and its writes are visible (nothing before this point reads
-// or writes data another kernel touches), then allow the next kernel's CTAs
-// to start their own prologue as this grid's CTAs retire.  Without a
-// programmatic dependency both are no-ops.
-__device__ __forceinline__ void pdl_sync() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Stage plane p: boxes(p, f) calls f(stage offset, tensor map, x, y, z,
-// component, bytes) for every box the kernel needs of plane p (z is p, or its
-// row in a compact auxiliary array).  The barrier expects the sum of the
-// boxes' bytes, then every box is loaded; with prefetch, plane p + 1's boxes
-// are also warmed in L2 so that their own load, one iteration later, finds
-// them closer (only planes inside [0, nz) and the ring).
-template <class Boxes>
-__device__ __forceinline__ void stage_plane(const Boxes& boxes, int p, unsigned char* st,
-                                            uint64_t* bar, bool prefetch_next) {
-  uint32_t bytes = 0;
-  boxes(p, [&](int, const CUtensorMap*, int, int, int, int, uint32_t b) { bytes += b; });
-  mbar_expect_tx(bar, bytes);
-  boxes(p, [&](int off, const CUtensorMap* mp, int x, int y, int z, int c, uint32_t) {
-    tma_load_4d(st + off, mp, bar, x, y, z, c);
-  });
-  if (prefetch_next)
-    boxes(p + 1, [&](int, const CUtensorMap* mp, int x, int y, int z, int c, uint32_t) {
-      tma_prefetch_l2_4d(mp, x, y, z, c);
-    });
-}
-
-// Start coordinates of a tile's boxes in the per-axis auxiliary arrays: a
-// tile whose boxes reach the mapped (high) part of the axis uses the mapped
-// start, so that its slab cells land where the array holds them (its other
-// cells are not slab cells and never read their auxiliaries).  TW + 4 / TY + 1
-// cover the widest box of any kernel.
-template <int TW, int TY>
-__device__ __forceinline__ void psi_box_starts(const PsiLayout& pl, int x0, int y0, int* qx0,
-                                               int* qy0) {
-  const PsiAxis& X = pl.ax[0];
-  const PsiAxis& Yy = pl.ax[1];
-  *qx0 = x0 + TW + 4 > X.hs ? x0 - X.shift : x0;
-  *qy0 = y0 + TY + 1 > Yy.hs ? y0 - Yy.shift : y0;
-}
-
-// A field increment of the leapfrog; EX (exact reversal) rounds it to the
-// grid of multiples of 2^-xq (see grid_inc), compiled in only where used.
-template <bool EX>
-__device__ __forceinline__ float inc_of(float d, const StepArgs& a) {
-  return EX ? grid_inc(d, 1, a.xs, a.xi) : d;
-}
-
-// Resident CTAs per SM the register allocation must allow for the default
-// 32 x 8 tiles with two stages: eight for the forward half-steps (what their
-// shared memory allows), five for the reverse phases (idem); other shapes
-// leave the allocation to the compiler.
-template <int TY, int S, int TW>
-constexpr int min_ctas(bool fwd) {
-  return (TY == 8 && S == 2 && TW == 32) ? (fwd ? 8 : 5) : 1;
-}
-
-template <int S>
-__device__ __forceinline__ uint64_t* ring_init(unsigned char* dsm, int stage_bytes) {
-  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + S * stage_bytes);
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  return bars;
-}
-
-// A wait for plane p (stage stg, parity par) gave up: record the timeout and
-// wait, bounded, for the copies still in flight (planes p .. min(p1, p+S-1))
-// so that no copy lands in shared memory after the CTA has left.
-template <int S>
-__device__ void ring_abort(uint64_t* bars, int stg, uint32_t par, int p, int p1, unsigned* err) {
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    atomicOr(err, ERR_TIMEOUT);
-    for (int i = 0; i < S && p + i <= p1; ++i) {
-      int s = stg + i;
-      uint32_t ph = par;
-      if (s >= S) {
-        s -= S;
-        ph ^= 1u;
-      }
-      mbar_wait(&bars[s], ph, kWaitCycles);
-    }
-  }
-}
-
-}  // namespace lag2
-
 using namespace lag2;
 
 // =================================================== forward H half-step ===

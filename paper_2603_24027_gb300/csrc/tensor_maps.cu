@@ -73,4 +73,23 @@ cudaError_t encode_lag_maps(const float* F, const float* Lm, const float* cb, co
   return cudaSuccess;
 }
 
+cudaError_t encode_rev_maps(const float* F, const float* Lm, const float* cb, const float* psiA,
+                            const Geo& g, const PsiLayout& pl, RevMaps* m) {
+  const int tw = 32, ty = 8;
+  *m = RevMaps{};
+  cudaError_t e;
+  if ((e = enc3(&m->F40, F, g, 6, tw + 8, ty + 2, 3))) return e;
+  if ((e = enc3(&m->F36, F, g, 6, tw + 4, ty + 1, 3))) return e;
+  if ((e = enc3(&m->cb36, cb, g, 1, tw + 4, ty + 1, 1))) return e;
+  if ((e = enc3(&m->cb40, cb, g, 1, tw + 8, ty + 2, 1))) return e;
+  if ((e = enc3(&m->L40, Lm, g, 6, tw + 8, ty + 2, 3))) return e;
+  if ((e = enc3(&m->L36, Lm, g, 6, tw + 4, ty + 1, 3))) return e;
+  if ((e = enc_axis(&m->Qx40, psiA, pl.ax[0], tw + 8, ty + 1))) return e;
+  if ((e = enc_axis(&m->Qy36, psiA, pl.ax[1], tw + 4, ty + 2))) return e;
+  if ((e = enc_axis(&m->Qz36, psiA, pl.ax[2], tw + 4, ty + 1))) return e;
+  if ((e = enc_axis(&m->Qxw, psiA, pl.ax[0], tw + 4, ty))) return e;
+  if ((e = enc_axis(&m->Qyw, psiA, pl.ax[1], tw, ty + 1))) return e;
+  return enc_axis(&m->Qzo, psiA, pl.ax[2], tw, ty);
+}
+
 }  // namespace fdtd

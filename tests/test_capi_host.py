@@ -140,14 +140,16 @@ def test_options_are_validated(capi, fdtd):
                          (capi.OPT_USE_GRAPHS, 1), (capi.OPT_TILE_X, 32), (capi.OPT_PDL, 0),
                          (capi.OPT_PREFETCH, 0), (capi.OPT_COMPACT_AUX, 1),
                          (capi.OPT_EXACT_REVERSAL, 0), (capi.OPT_ZCHUNK_FWD, -1),
-                         (capi.OPT_ZGROUPS, 0)]:
+                         (capi.OPT_ZGROUPS, 0), (capi.OPT_REVERSE, 0),
+                         (capi.OPT_INJECT_WAIT_TIMEOUT, 0)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
                      (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_KERNEL, 4),
                      (capi.OPT_KERNEL, 6), (5, 1),
                      (capi.OPT_ZCHUNK, -1), (capi.OPT_TILE_X, 0), (capi.OPT_TILE_X, 36),
                      (capi.OPT_ZCHUNK_FWD, -2), (capi.OPT_EXACT_REVERSAL, 5),
-                     (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (99, 1)]:
+                     (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (capi.OPT_REVERSE, 3),
+                     (capi.OPT_REVERSE, -1), (99, 1)]:
         assert lib.fdtd_set_option(sim.h, opt, val) == capi.FDTD_EINVAL
     assert lib.fdtd_set_option(sim.h, capi.OPT_STAGES, 4) == capi.FDTD_OK
     assert lib.fdtd_get_option(sim.h, capi.OPT_STAGES, C.byref(v)) == capi.FDTD_OK and v.value == 4
@@ -189,7 +191,9 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     4-aligned cell round_down(nx - P, 4) on, rows padded to 4; y, z: 2P rows /
     planes), per axis where the grid is long enough (nx >= 2P + 56,
     ny >= 2P + 24, nz >= 2P + 1); the plain-load kernels keep the full grid.
-    Three sets (forward + two adjoint) differ; everything else is equal."""
+    Three sets (forward + two adjoint) differ; with the fused reverse step
+    (the default) kernel 5 also holds a second field and adjoint buffer
+    (ping-pong pairs, 2 x 6 components); everything else is equal."""
     al = lambda b: (b + 255) // 256 * 256
 
     def full(nx, ny, nz):
@@ -204,8 +208,11 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     b4 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_KERNEL, 5)
     b5 = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_REVERSE, 1)
+    b5s = sim.workspace_bytes(rec)
     compact = al(4 * (24 * 200 * 100 + 200 * 24 * 100 + 200 * 200 * 24) * 4)
-    assert b4 - b5 == 3 * (full(200, 200, 100) - compact)
+    assert b4 - b5s == 3 * (full(200, 200, 100) - compact)
+    assert b5 - b5s == 2 * al(6 * 100 * 200 * 200 * 4)
     assert compact / full(200, 200, 100) == pytest.approx(0.16)
     # 70 x 21 x 19, P = 6: x (rows of 8 + 6 cells, pitch 16) and z (12
     # planes) compact, y too short (full rows of px = 72)
@@ -214,6 +221,7 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     sim.set_option(capi.OPT_KERNEL, 0)
     b4 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_KERNEL, 5)
+    sim.set_option(capi.OPT_REVERSE, 1)
     b5 = sim.workspace_bytes(rec)
     compact = al(4 * (16 * 21 * 19 + 72 * 21 * 19 + 72 * 21 * 12) * 4)
     assert b4 - b5 == 3 * (full(70, 21, 19) - compact)
@@ -330,3 +338,51 @@ def test_inject_wait_option_is_validated(capi, fdtd):
     assert lib.fdtd_set_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, 100000) == capi.FDTD_OK
     assert lib.fdtd_get_option(sim.h, capi.OPT_INJECT_WAIT_TIMEOUT, C.byref(v)) == 0
     assert v.value == 100000
+
+
+@pytest.mark.parametrize("nx,ny,nz,P,zc", [(70, 21, 19, 6, 8), (86, 50, 30, 7, 8), (86, 50, 30, 7, 3),
+                                          (200, 200, 100, 12, 8), (120, 77, 41, 9, 0),
+                                          (600, 600, 300, 16, 8), (20, 18, 17, 8, 5),
+                                          (130, 40, 60, 5, 7)])
+def test_fused_reverse_units_partition(capi, nx, ny, nz, P, zc):
+    """The fused reverse step's launches (32 x 8 tiles, zc-plane chunks):
+    the primal launch covers exactly the units that hold an interior cell;
+    the adjoint launch without CPML terms exactly the units whose evaluated
+    cells x0-1 .. x0+32, y0-1 .. y0+8 and planes k0-1 .. k1 all lie in the
+    interior (so no CPML term is skipped); the adjoint launch with CPML every
+    other unit, each once."""
+    lib = capi.lib()
+    counts = (C.c_int * 3)()
+    assert lib.fdtd_reverse_units(nx, ny, nz, P, zc, counts, None, 0) == capi.FDTD_OK
+    n = sum(counts)
+    buf = np.zeros((n, 3), np.int32)
+    assert lib.fdtd_reverse_units(nx, ny, nz, P, zc, counts, buf.ctypes.data, n - 1) == capi.FDTD_EINVAL
+    assert lib.fdtd_reverse_units(nx, ny, nz, P, zc, counts, buf.ctypes.data, n) == capi.FDTD_OK
+    prim = buf[:counts[0]]
+    inner = buf[counts[0]:counts[0] + counts[1]]
+    ring = buf[counts[0] + counts[1]:]
+    z = zc if zc > 0 else nz
+    ntx, nty, nzc = -(-nx // 32), -(-ny // 8), -(-nz // z)
+
+    def interior(lo, hi, nn):           # every cell of [lo, hi] is interior
+        return lo >= P and hi <= nn - P - 1
+
+    want_p, want_i = set(), set()
+    for cz in range(nzc):
+        k0, k1 = cz * z, min(nz, cz * z + z)
+        for ty in range(nty):
+            for tx in range(ntx):
+                x0, y0 = 32 * tx, 8 * ty
+                has = (max(x0, P) < min(x0 + 32, nx - P) and max(y0, P) < min(y0 + 8, ny - P)
+                       and max(k0, P) < min(k1, nz - P))
+                if has:
+                    want_p.add((tx, ty, cz))
+                if (interior(x0 - 1, x0 + 32, nx) and interior(y0 - 1, y0 + 8, ny)
+                        and interior(k0 - 1, k1, nz)):
+                    want_i.add((tx, ty, cz))
+    assert len(prim) == len(want_p) and set(map(tuple, prim)) == want_p
+    assert len(inner) == len(want_i) and set(map(tuple, inner)) == want_i
+    allu = {(tx, ty, cz) for cz in range(nzc) for ty in range(nty) for tx in range(ntx)}
+    ring_set = set(map(tuple, ring))
+    assert len(ring_set) == len(ring)               # each once
+    assert ring_set == allu - want_i

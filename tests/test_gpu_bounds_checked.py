@@ -1,5 +1,6 @@
 """Bounds-checked build (-DFDTD_BOUNDS_CHECK) of the library: every store of
-the default two-cells-per-thread kernels checks that it lands in the
+the default two-cells-per-thread kernels (and of the fused reverse step,
+into the other buffer of each ping-pong pair) checks that it lands in the
 fields, the adjoint fields or an auxiliary set of its launch, and the
 gacc reduction that it stays in the design box; a stray store is skipped
 and reported (FDTD_ECUDA).  compute-sanitizer is closed on this machine, so
@@ -27,11 +28,14 @@ grids = {
     "ragged86": I.ragged_box(nx=86, ny=50, nz=30, P=7, n_steps=60),
     "ragged45": I.ragged_box(nx=45, ny=27, nz=23, P=5, n_steps=60, det_kind=I.OBJ_E2_PLANE,
                              src_kind=I.SRC_POINT),
+    "interior150": I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=50),
 }
 shapes = [dict(), {A.OPT_TILE_Y: 2, A.OPT_STAGES: 4, A.OPT_ZCHUNK: 1},
           {A.OPT_TILE_Y: 4, A.OPT_STAGES: 3, A.OPT_ZCHUNK: 3},
           {A.OPT_TILE_Y: 16, A.OPT_ZCHUNK: 5}, {A.OPT_TILE_X: 40, A.OPT_STAGES: 3},
-          {A.OPT_EXACT_REVERSAL: 22}, {A.OPT_COMPACT_AUX: 0}]
+          {A.OPT_EXACT_REVERSAL: 22}, {A.OPT_COMPACT_AUX: 0}, {A.OPT_REVERSE: 1},
+          {A.OPT_REVERSE: 1, A.OPT_EXACT_REVERSAL: 22}, {A.OPT_ZCHUNK: 3},
+          {A.OPT_ZCHUNK: 1, A.OPT_COMPACT_AUX: 0}]
 n = 0
 for name, w in grids.items():
     ref = {"f32:1:linear": O.gradient(w)[1],

@@ -161,6 +161,120 @@ def test_launch_shapes_do_not_change_results(F, A, zchunk, tile_y, stages):
         same_gradient(r["g"], base["g"])
 
 
+FUSED_GRIDS = {
+    "ragged_poynting": lambda: I.ragged_box(),
+    "ragged_e2_point": lambda: I.ragged_box(nx=45, ny=27, nz=23, P=5, n_steps=90,
+                                            det_kind=I.OBJ_E2_PLANE, src_kind=I.SRC_POINT),
+    # CPML-free adjoint units exist and the CPML units take every branch of
+    # their enumeration (chunks below / above, rows below / above, columns
+    # left / right); 86 x 50 x 30 compacts all three auxiliary axes
+    "interior_units": lambda: I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=70),
+    "compact86": lambda: I.ragged_box(nx=86, ny=50, nz=30, P=7, n_steps=60),
+}
+
+
+def run_both_ways(F, A, w, rec, reverse, options=None):
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_REVERSE, reverse)
+    for k, v in (options or {}).items():
+        sim.set_option(k, v)
+    eps = torch.from_numpy(np.ascontiguousarray(w.eps)).cuda()
+    L = sim.forward(eps, rec)
+    g = sim.backward(1.0).cpu().numpy()
+    back = sim.read_fields().cpu().numpy()
+    return L, g, back
+
+
+@pytest.mark.parametrize("name", list(FUSED_GRIDS))
+@pytest.mark.parametrize("tape", ["f32:1:linear", "bf16:4:cubic", "e4m3:2:linear", "bdct10:2:cubic"])
+def test_fused_reverse_step_matches_the_split_phases(F, A, name, tape):
+    """The fused reverse step (a primal and an adjoint launch per step, each
+    reading every field once into the other buffer of a ping-pong pair)
+    against the split phases: the reconstructed interior fields after the
+    whole backward run bit for bit (the primal half-steps repeat the same
+    rounded operations), the gradient to the adjoint sums' rounding."""
+    w = FUSED_GRIDS[name]()
+    dt, k, interp = tape.split(":")
+    rec = A.record_cfg(dt, int(k), interp)
+    Ls, gs, bs = run_both_ways(F, A, w, rec, 1)
+    Lf, gf, bf = run_both_ways(F, A, w, rec, 2)
+    assert Lf == pytest.approx(Ls, rel=1e-12)   # FP64 atomic sums across CTAs
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    np.testing.assert_array_equal(bf[inner], bs[inner])
+    assert np.abs(gs).max() > 0
+    same_gradient(gf, gs)
+
+
+def test_fused_reverse_step_with_exact_reversal_returns_to_zero(F, A):
+    """Exact reversal through the fused primal kernel: the interior returns to
+    the zero initial state bit for bit, and the gradient agrees with the split
+    phases' exact-reversal run."""
+    w = FUSED_GRIDS["interior_units"]()
+    rec = A.record_cfg("f32", 1)
+    opts = {A.OPT_EXACT_REVERSAL: 22}
+    _, gs, _ = run_both_ways(F, A, w, rec, 1, opts)
+    _, gf, bf = run_both_ways(F, A, w, rec, 2, opts)
+    P = w.pml_thickness
+    assert not np.any(bf[:, P:w.nz - P, P:w.ny - P, P:w.nx - P])
+    same_gradient(gf, gs)
+
+
+@pytest.mark.parametrize("reverse", [1, 2])
+def test_exact_reversal_on_a_grid_of_many_waves(F, A, reverse):
+    """300 x 120 x 80 cells, 200 steps, exact reversal: every one of the many
+    waves of CTAs must read each staged plane only after its copy landed and
+    refill a stage only after every thread's reads of it are ordered before
+    the copy (a proxy fence between the shared-memory reads and the TMA
+    write); any stale or early read leaves the interior off zero."""
+    w = I.ragged_box(nx=300, ny=120, nz=80, P=8, n_steps=200)
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_REVERSE, reverse)
+    sim.set_option(A.OPT_EXACT_REVERSAL, 22)
+    eps = torch.from_numpy(w.eps).cuda()
+    sim.forward(eps, A.record_cfg("f32", 1))
+    fwd = sim.read_fields().cpu().numpy()
+    sim.backward(1.0)
+    back = sim.read_fields().cpu().numpy()
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    assert np.abs(fwd[inner]).max() > 1e-3
+    assert not np.any(back[inner])
+
+
+@pytest.mark.parametrize("zchunk", [1, 3, 0])
+def test_fused_reverse_step_chunks_and_two_detectors(F, A, zchunk):
+    """z chunks of 1 and 3 planes and whole columns (every chunk boundary
+    passes the lag planes between CTAs), and a second detector seeded in the
+    same run: the fused step against the oracle's exact gradient."""
+    w = I.coupler_small(n_steps=70)
+    L, M, g = O.gradient2(w, 0.7, -1.3)
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_REVERSE, 2)
+    sim.set_option(A.OPT_ZCHUNK, zchunk)
+    eps = torch.from_numpy(w.eps).cuda()
+    sim.forward(eps, A.record_cfg("f32", 1))
+    gf = sim.backward(0.7, seed2=-1.3).cpu().numpy()
+    assert rel(gf, g) < 1e-4
+
+
+def test_fused_reverse_step_needs_its_tiles(F, A):
+    """FDTD_OPT_REVERSE = 2 with other tiles than 32 x 8 is refused at the
+    forward; automatic (0) falls back to the split phases there."""
+    w = SMALL["fd_cube"]()
+    eps = torch.from_numpy(w.eps).cuda()
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_REVERSE, 2)
+    sim.set_option(A.OPT_TILE_Y, 4)
+    with pytest.raises(A.FdtdError) as e:
+        sim.forward(eps, A.record_cfg("f32", 1))
+    assert e.value.status == A.FDTD_EINVAL
+    sim.set_option(A.OPT_REVERSE, 0)
+    sim.forward(eps, A.record_cfg("f32", 1))
+    L, g = O.gradient(w)
+    assert rel(sim.backward(1.0).cpu().numpy(), g) < 1e-4
+
+
 @pytest.mark.parametrize("zgroups,zchunk,zfwd,tape,graphs", [
     (2, 4, -1, "bf16:2", 1), (0, 3, -1, "f16:2", 0), (3, 2, 3, "f32:1", 1), (5, 1, 2, "bf16:3", 0),
     (16, 4, 4, "e4m3:2", 1), (4, 8, 0, "bdct:2", 1)])
@@ -314,13 +428,16 @@ def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     assert a["L"] == b["L"]
 
 
-def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
+@pytest.mark.parametrize("reverse,kinds", [(1, ("rev_e", "rev_h")), (2, ("rev_primal", "rev_adjoint"))])
+def test_sampled_kernel_timing_accounts_for_the_loop(F, A, reverse, kinds):
     """Differential in-loop timing (pair of launches minus single launch):
     every kernel kind gets a positive cost, the costs times the launch counts
-    add up to the measured loop times, and sampling does not change results."""
+    add up to the measured loop times, and sampling does not change results;
+    for the split reverse phases and for the fused reverse step (whose
+    adjoint kind covers its two launches)."""
     w = I.waveguide_sweep(n_steps=200)
     rec = A.record_cfg("bf16", 4, "linear")
-    one = {A.OPT_ZGROUPS: 1}   # sampling records loops with one launch per half-step
+    one = {A.OPT_ZGROUPS: 1, A.OPT_REVERSE: reverse}   # sampling records one launch per half-step
     base = gpu_run(F, A, w, rec=rec, options=one)
     r = gpu_run(F, A, w, rec=rec, options={**one, A.OPT_SAMPLE_EVERY: 7})
     np.testing.assert_array_equal(r["fields"], base["fields"])
@@ -329,11 +446,11 @@ def test_sampled_kernel_timing_accounts_for_the_loop(F, A):
     sim.forward(torch.from_numpy(w.eps).cuda(), rec)   # warm graphs, then measure
     sim.backward(1.0)
     kt, t = sim.kernel_timing(), sim.last_timing()
-    for name in ("fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h"):
+    for name in ("fwd_h", "fwd_e", "record", "restore_seed") + kinds:
         assert name in kt and kt[name][0] > 0 and kt[name][1] >= 1, (name, kt)
     n, nrec = w.n_steps, -(-w.n_steps // 4)
     fwd = n * (kt["fwd_h"][0] + kt["fwd_e"][0]) + nrec * kt["record"][0]
-    bwd = n * (kt["restore_seed"][0] + kt["rev_e"][0] + kt["rev_h"][0])
+    bwd = n * (kt["restore_seed"][0] + kt[kinds[0]][0] + kt[kinds[1]][0])
     assert 0.7 < fwd / t["fwd_ms"] < 1.3, (fwd, t)
     assert 0.7 < bwd / t["bwd_ms"] < 1.3, (bwd, t)
 
