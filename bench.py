@@ -77,6 +77,8 @@ def parse(argv=None):
     p.add_argument("--no-compare", action="store_true")
     p.add_argument("--compare-steps", type=int, default=1)
     p.add_argument("--kernel", type=int, default=-1, help="0 plain loads, 5 staged, -1 default")
+    p.add_argument("--reverse", type=int, default=-1,
+                   help="reverse step: 1 split phases, 2 fused, -1 the library's choice")
     p.add_argument("--zgroups", type=int, default=0,
                    help="z groups per half-step (0: the library's automatic choice)")
     p.add_argument("--autotune", action="store_true",
@@ -198,18 +200,19 @@ def phase_bytes(w, tape: str):
 def kernel_bytes(w):
     """Per-launch bytes each split half-step kernel moves itself (its own
     reads and writes), for the per-kernel breakdown only: the split reverse
-    reads E, Ht and the adjoint in both of its launches."""
+    reads E, Ht and the adjoint in both of its launches.  (The fused
+    reverse's launches are accounted as the reverse phase.)"""
     c = cell_classes(w)
     n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
     npml = n - ni
     return {"fwd_h": 36 * n + 16 * sa, "fwd_e": 40 * n + 16 * sa,
             "rev_e": 76 * ni + 40 * npml + 16 * nd + 16 * sa,
-            "rev_h": 72 * ni + 36 * npml + 16 * sa,
-            "fused_rev": 100 * ni + 52 * npml + 16 * nd + 32 * sa}
+            "rev_h": 72 * ni + 36 * npml + 16 * sa}
 
 
 PHASE_KERNELS = {"forward": ["fwd_h", "fwd_e", "record"],
-                 "reverse": ["restore_seed", "rev_e", "rev_h", "fused_rev"]}
+                 "reverse": ["restore_seed", "rev_e", "rev_h", "rev_primal", "rev_adjoint",
+                             "rev_adjoint_cpml"]}
 
 
 def read_peaks():
@@ -319,6 +322,8 @@ def apply_options(A, sim, args):
     library's defaults)."""
     if args.kernel >= 0:
         sim.set_option(A.OPT_KERNEL, args.kernel)
+    if args.reverse >= 0:
+        sim.set_option(A.OPT_REVERSE, args.reverse)
     sim.set_option(A.OPT_ZGROUPS, args.zgroups)
     for val, opt in ((args.tile_y, A.OPT_TILE_Y), (args.tile_x, A.OPT_TILE_X),
                      (args.zchunk, A.OPT_ZCHUNK), (args.stages, A.OPT_STAGES)):
@@ -359,8 +364,7 @@ def sampled_breakdown(A, fdtd, args, w, rec, dev, flush):
         for name, (ms, n) in sim.kernel_timing().items():
             ktimes.setdefault(name, []).append((ms, n))
     torch.cuda.synchronize()
-    per_step = {"fwd_h": 1.0, "fwd_e": 1.0, "rev_e": 1.0, "rev_h": 1.0, "fused_rev": 1.0,
-                "restore_seed": 1.0, "record": 1.0 / rec.k}
+    per_step = {"record": 1.0 / rec.k}
     kb = kernel_bytes(w)
     step_ms = statistics.median(loop_ms) / ws_.n_steps
     kern = {}
@@ -563,7 +567,8 @@ def run_profile(args):
     torch.cuda.synchronize()
     opts = {name: sim.get_option(getattr(A, name)) for name in
             ("OPT_KERNEL", "OPT_TILE_Y", "OPT_TILE_X", "OPT_ZCHUNK", "OPT_ZCHUNK_FWD",
-             "OPT_STAGES", "OPT_ZGROUPS", "OPT_COMPACT_AUX", "OPT_PDL", "OPT_PREFETCH")}
+             "OPT_STAGES", "OPT_ZGROUPS", "OPT_COMPACT_AUX", "OPT_PDL", "OPT_PREFETCH",
+             "OPT_REVERSE")}
     print(json.dumps(dict(workload=w.name, n_steps=w.n_steps, pml=w.pml_thickness,
                           tape=args.tape, options=opts, L=L, grad_l1=float(g.abs().sum()),
                           timing=sim.last_timing(), kernels=sim.kernel_timing())))

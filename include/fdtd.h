@@ -277,7 +277,9 @@ enum {
                                    off.  Injects no fault: the wait is the same bounded wait
                                    as fdtd_selftest_wait */
   FDTD_OPT_REVERSE = 15         /* kernel 5: how a reverse time step runs.  0 (default) =
-                                   automatic: fused with 32 x 8 tiles, else split; 1 = split:
+                                   automatic: fused with 32 x 8 tiles when at most half of
+                                   the (tile, z chunk) units carry CPML terms (see
+                                   fdtd_reverse_units), else split; 1 = split:
                                    a reverse E phase and a reverse H phase, each updating the
                                    primal and the adjoint fields in place; 2 = fused: one
                                    launch for the primal fields (both inverse half-steps,
@@ -297,7 +299,7 @@ int fdtd_get_option(const fdtd_handle* h, int option, int* value);
 enum {
   FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
   FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_REV_PRIMAL = 6, FDTD_K_REV_ADJOINT = 7,
-  FDTD_K_MONITOR = 8, FDTD_K_KINDS = 9
+  FDTD_K_MONITOR = 8, FDTD_K_REV_ADJOINT_CPML = 9, FDTD_K_KINDS = 10
 };
 /* Average in-loop cost (ms) per launch of one kernel kind in the last
  * forward + backward, and the number of samples it rests on

@@ -379,11 +379,23 @@ static void interp_weights(const fdtd_handle* h, const fdtd_record_cfg* rec, int
 // The reverse step of kernel 5 runs as two fused launches (primal and
 // adjoint, kernels_rev_fused.cu) unless FDTD_OPT_REVERSE asks for the split
 // phases; the fused kernels are built for 32 x 8 tiles.
+// Automatic (0): fused where at most half of the (tile, chunk) units carry
+// CPML terms, which its adjoint evaluates in a heavier variant (measured on
+// GB300: the reverse 11 % faster than split on 600 x 600 x 300 with 31 % of
+// the units in the CPML, 28 % slower on 200 x 200 x 100 with 70 %).
 static bool fused_reverse(const fdtd_handle* h) {
   if (h->opt_kernel != 5 || h->opt_reverse == 1) return false;
   const int ty = h->opt_tile_y < 2 ? 2 : h->opt_tile_y;
   const int tx = (ty == 8 && h->opt_stages <= 3 && h->opt_tile_x == 40) ? 40 : 32;
-  return ty == 8 && tx == 32;
+  if (ty != 8 || tx != 32) return false;
+  if (h->opt_reverse == 2) return true;
+  Geo g;
+  memset(&g, 0, sizeof g);
+  g.nx = h->nx; g.ny = h->ny; g.nz = h->nz; g.P = h->P;
+  const RevUnits U = rev_units(g, h->opt_zchunk > 0 ? h->opt_zchunk : h->nz);
+  const long long all = (long long)U.ntx * U.nty * U.nzc;
+  const long long cpml = all - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0) * (U.iz1 - U.iz0);
+  return 2 * cpml <= all;
 }
 
 // ---------------------------------------------------------------- layout ---
@@ -950,9 +962,28 @@ struct Sampler {
     }
     return cudaEventRecordWithFlags(pool[slot], h->stream, cudaEventRecordExternal);
   }
+  // A fixed integer hash of the launch index picks the sampled launches (one
+  // in m on average) and the interval type, so that every kind is sampled
+  // both alone and after each of its predecessors whatever the number of
+  // launches per time step (a plain every-m-th choice with alternating types
+  // misses kinds when m shares a factor with it).
+  static uint32_t mix(uint64_t v) {
+    v ^= v >> 33;
+    v *= 0xff51afd7ed558ccdULL;
+    v ^= v >> 33;
+    v *= 0xc4ceb9fe1a85ec53ULL;
+    v ^= v >> 33;
+    return (uint32_t)v;
+  }
   cudaError_t before(int kind) {
-    if (m <= 0 || open >= 0 || i % m) return cudaSuccess;
-    open_type = (int)((i / m) & 1);
+    if (m <= 0 || open >= 0) return cudaSuccess;
+    const uint32_t hsh = mix((uint64_t)i);
+    if (hsh % (uint32_t)m) return cudaSuccess;
+    // no interval beyond the events created before the capture
+    if (h->splan[dir].size() >= h->spool[dir][0].size() ||
+        h->splan[dir].size() >= h->spool[dir][1].size())
+      return cudaSuccess;
+    open_type = (int)((hsh >> 24) & 1);
     h->splan[dir].push_back(SampleEntry{-1, kind, kind});
     open = (int)h->splan[dir].size() - 1;
     end_at = i + open_type;
@@ -1096,7 +1127,7 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
 
 static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_REV_PRIMAL,
-                                FDTD_K_REV_ADJOINT};
+                                FDTD_K_REV_ADJOINT, FDTD_K_REV_ADJOINT_CPML};
 
 // Enqueue the forward time loop on h->stream (capturable).
 static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, int* launches) {
@@ -1277,8 +1308,10 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
       if ((e = smp.after(FDTD_K_REV_PRIMAL))) return e;
       if ((e = smp.before(FDTD_K_REV_ADJOINT))) return e;
       if ((e = launch_rev_fused(1, rmaps[cur], a, U, side))) return e;
-      if ((e = launch_rev_fused(2, rmaps[cur], a, U, side))) return e;
       if ((e = smp.after(FDTD_K_REV_ADJOINT))) return e;
+      if ((e = smp.before(FDTD_K_REV_ADJOINT_CPML))) return e;
+      if ((e = launch_rev_fused(2, rmaps[cur], a, U, side))) return e;
+      if ((e = smp.after(FDTD_K_REV_ADJOINT_CPML))) return e;
       if (conc) {
         if ((e = cudaEventRecord(h->zev[1], side))) return e;
         if ((e = cudaStreamWaitEvent(h->stream, h->zev[1], 0))) return e;
@@ -1323,7 +1356,10 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
                     int* launches, cudaEvent_t ta, cudaEvent_t tb) {
   // events for the sampled intervals exist before a capture starts
   if (h->opt_sample > 0) {
-    const size_t need = (size_t)(3LL * h->N / h->opt_sample) + 4;
+    // at most four sampled units per time step (restore, primal, two adjoint
+    // launches; forward: two half-steps, record, monitor), one in m sampled
+    // on average: room for twice that
+    const size_t need = (size_t)(8LL * h->N / h->opt_sample) + 16;
     for (int e = 0; e < 2; ++e)
       while (h->spool[dir][e].size() < need) {
         cudaEvent_t ev;
@@ -1526,7 +1562,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaEventElapsedTime(&h->bwd_ms, h->t2, h->t3));
-  collect_samples(h, 1, kBwdKinds, 5);
+  collect_samples(h, 1, kBwdKinds, 6);
   int rc = finish(h);
   if (rc) return rc;
   return check_err(h, err);

@@ -192,8 +192,8 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     planes), per axis where the grid is long enough (nx >= 2P + 56,
     ny >= 2P + 24, nz >= 2P + 1); the plain-load kernels keep the full grid.
     Three sets (forward + two adjoint) differ; with the fused reverse step
-    (the default) kernel 5 also holds a second field and adjoint buffer
-    (ping-pong pairs, 2 x 6 components); everything else is equal."""
+    kernel 5 also holds a second field and adjoint buffer (ping-pong pairs,
+    2 x 6 components); everything else is equal."""
     al = lambda b: (b + 255) // 256 * 256
 
     def full(nx, ny, nz):
@@ -207,9 +207,12 @@ def test_compact_auxiliary_workspace(capi, fdtd):
     sim.set_option(capi.OPT_KERNEL, 0)
     b4 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_KERNEL, 5)
+    sim.set_option(capi.OPT_REVERSE, 2)
     b5 = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_REVERSE, 1)
     b5s = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_REVERSE, 0)   # automatic: split here (70 % of the units in the CPML)
+    assert sim.workspace_bytes(rec) == b5s
     compact = al(4 * (24 * 200 * 100 + 200 * 24 * 100 + 200 * 200 * 24) * 4)
     assert b4 - b5s == 3 * (full(200, 200, 100) - compact)
     assert b5 - b5s == 2 * al(6 * 100 * 200 * 200 * 4)
@@ -386,3 +389,21 @@ def test_fused_reverse_units_partition(capi, nx, ny, nz, P, zc):
     ring_set = set(map(tuple, ring))
     assert len(ring_set) == len(ring)               # each once
     assert ring_set == allu - want_i
+
+
+def test_automatic_reverse_follows_the_cpml_share(capi, fdtd):
+    """FDTD_OPT_REVERSE = 0 takes the fused reverse step (and its second field
+    and adjoint buffers) where at most half of the (tile, chunk) units carry
+    CPML terms: the 600 x 600 x 300 grid (31 %), not the 200 x 200 x 100 one
+    (70 %)."""
+    lib = capi.lib()
+    counts = (C.c_int * 3)()
+    for w, fused in ((I.waveguide_large(n_steps=10), True), (I.waveguide_mid(), False)):
+        assert lib.fdtd_reverse_units(w.nx, w.ny, w.nz, w.pml_thickness, 8, counts, None, 0) == 0
+        share = counts[2] / (counts[1] + counts[2])
+        assert (share <= 0.5) == fused, share
+        sim = fdtd.Simulation(w)
+        rec = capi.record_cfg("e4m3", 8)
+        auto = sim.workspace_bytes(rec)
+        sim.set_option(capi.OPT_REVERSE, 2 if fused else 1)
+        assert sim.workspace_bytes(rec) == auto

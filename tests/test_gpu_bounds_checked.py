@@ -33,9 +33,10 @@ grids = {
 shapes = [dict(), {A.OPT_TILE_Y: 2, A.OPT_STAGES: 4, A.OPT_ZCHUNK: 1},
           {A.OPT_TILE_Y: 4, A.OPT_STAGES: 3, A.OPT_ZCHUNK: 3},
           {A.OPT_TILE_Y: 16, A.OPT_ZCHUNK: 5}, {A.OPT_TILE_X: 40, A.OPT_STAGES: 3},
-          {A.OPT_EXACT_REVERSAL: 22}, {A.OPT_COMPACT_AUX: 0}, {A.OPT_REVERSE: 1},
-          {A.OPT_REVERSE: 1, A.OPT_EXACT_REVERSAL: 22}, {A.OPT_ZCHUNK: 3},
-          {A.OPT_ZCHUNK: 1, A.OPT_COMPACT_AUX: 0}]
+          {A.OPT_EXACT_REVERSAL: 22}, {A.OPT_COMPACT_AUX: 0}, {A.OPT_REVERSE: 2},
+          {A.OPT_REVERSE: 2, A.OPT_EXACT_REVERSAL: 22}, {A.OPT_REVERSE: 2, A.OPT_ZCHUNK: 3},
+          {A.OPT_REVERSE: 2, A.OPT_ZCHUNK: 1, A.OPT_COMPACT_AUX: 0},
+          {A.OPT_REVERSE: 1, A.OPT_ZCHUNK: 3}]
 n = 0
 for name, w in grids.items():
     ref = {"f32:1:linear": O.gradient(w)[1],

@@ -428,13 +428,14 @@ def test_dependent_launch_and_l2_prefetch_do_not_change_results(F, A, graphs):
     assert a["L"] == b["L"]
 
 
-@pytest.mark.parametrize("reverse,kinds", [(1, ("rev_e", "rev_h")), (2, ("rev_primal", "rev_adjoint"))])
+@pytest.mark.parametrize("reverse,kinds", [(1, ("rev_e", "rev_h")),
+                                           (2, ("rev_primal", "rev_adjoint", "rev_adjoint_cpml"))])
 def test_sampled_kernel_timing_accounts_for_the_loop(F, A, reverse, kinds):
     """Differential in-loop timing (pair of launches minus single launch):
     every kernel kind gets a positive cost, the costs times the launch counts
     add up to the measured loop times, and sampling does not change results;
-    for the split reverse phases and for the fused reverse step (whose
-    adjoint kind covers its two launches)."""
+    for the split reverse phases and for the fused reverse step (its primal
+    launch and its two adjoint launches)."""
     w = I.waveguide_sweep(n_steps=200)
     rec = A.record_cfg("bf16", 4, "linear")
     one = {A.OPT_ZGROUPS: 1, A.OPT_REVERSE: reverse}   # sampling records one launch per half-step
@@ -450,7 +451,7 @@ def test_sampled_kernel_timing_accounts_for_the_loop(F, A, reverse, kinds):
         assert name in kt and kt[name][0] > 0 and kt[name][1] >= 1, (name, kt)
     n, nrec = w.n_steps, -(-w.n_steps // 4)
     fwd = n * (kt["fwd_h"][0] + kt["fwd_e"][0]) + nrec * kt["record"][0]
-    bwd = n * (kt["restore_seed"][0] + kt[kinds[0]][0] + kt[kinds[1]][0])
+    bwd = n * (kt["restore_seed"][0] + sum(kt[k][0] for k in kinds))
     assert 0.7 < fwd / t["fwd_ms"] < 1.3, (fwd, t)
     assert 0.7 < bwd / t["bwd_ms"] < 1.3, (bwd, t)
 

@@ -46,10 +46,10 @@ def _noalloc(A, sim, eps, rec, seed, out):
     return obj.value, out.cpu().numpy().copy()
 
 
-@pytest.mark.parametrize("kernel", [0, 5])
+@pytest.mark.parametrize("kernel,reverse", [(0, 0), (5, 1), (5, 2)])
 @pytest.mark.parametrize("tape", [("f32", 1, "linear"), ("bf16", 4, "cubic"), ("e4m3", 2, "linear"),
                                   ("bdct10", 2, "cubic")])
-def test_noalloc_matches_workspace_path_on_two_calls(mods, kernel, tape):
+def test_noalloc_matches_workspace_path_on_two_calls(mods, kernel, reverse, tape):
     A, F = mods
     w = I.ragged_box(n_steps=90)
     rec = A.record_cfg(*tape)
@@ -57,11 +57,13 @@ def test_noalloc_matches_workspace_path_on_two_calls(mods, kernel, tape):
     # reference: the workspace entry points
     ref = F.Simulation(w)
     ref.set_option(A.OPT_KERNEL, kernel)
+    ref.set_option(A.OPT_REVERSE, reverse)
     L_ref = ref.forward(eps, rec)
     g_ref = ref.backward(0.5).cpu().numpy()
     # two calls in a row through the no-allocation entry point
     sim = F.Simulation(w)
     sim.set_option(A.OPT_KERNEL, kernel)
+    sim.set_option(A.OPT_REVERSE, reverse)
     out = torch.full(w.design_shape, float("nan"), device="cuda")
     for _ in range(2):
         L, g = _noalloc(A, sim, eps, rec, 0.5, out)
