@@ -1311,13 +1311,14 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
       if ((e = smp.after(FDTD_K_REV_ADJOINT))) return e;
       if ((e = smp.before(FDTD_K_REV_ADJOINT_CPML))) return e;
       if ((e = launch_rev_fused(2, rmaps[cur], a, U, side))) return e;
+      if ((e = launch_rev_fused(3, rmaps[cur], a, U, side))) return e;
       if ((e = smp.after(FDTD_K_REV_ADJOINT_CPML))) return e;
       if (conc) {
         if ((e = cudaEventRecord(h->zev[1], side))) return e;
         if ((e = cudaStreamWaitEvent(h->stream, h->zev[1], 0))) return e;
       }
       cur ^= 1;
-      nl += 4;
+      nl += 5;
       continue;
     }
     if (zg.active()) {
@@ -1848,11 +1849,20 @@ extern "C" int fdtd_reverse_units(int nx, int ny, int nz, int P, int zchunk, int
   for (int z = U.iz0; z < U.iz1; ++z)
     for (int y = U.iy0; y < U.iy1; ++y)
       for (int x = U.ix0; x < U.ix1; ++x) { *o++ = x; *o++ = y; *o++ = z; }
-  for (long long u = 0; u < nall - ni; ++u) {
+  for (int z = 0; z < U.nzc - (U.iz1 - U.iz0); ++z)
+    for (int y = 0; y < U.iy1 - U.iy0; ++y)
+      for (int x = 0; x < U.ix1 - U.ix0; ++x) {
+        int tx, ty, cz;
+        rev_zonly_unit(U, x, y, z, &tx, &ty, &cz);
+        *o++ = tx; *o++ = ty; *o++ = cz;
+      }
+  const long long nring = rev_ring_tiles(U) * U.nzc;
+  for (long long u = 0; u < nring; ++u) {
     int tx, ty, cz;
-    rev_unit_of(U, u, &tx, &ty, &cz);
+    rev_ring_unit(U, u, &tx, &ty, &cz);
     *o++ = tx; *o++ = ty; *o++ = cz;
   }
+  if (o != units + 3 * n) return FDTD_ECUDA;
   return FDTD_OK;
 }
 

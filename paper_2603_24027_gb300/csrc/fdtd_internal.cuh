@@ -296,10 +296,15 @@ struct RevUnits {
   int ix0, ix1, iy0, iy1, iz0, iz1;
 };
 RevUnits rev_units(const Geo& g, int zchunk);
-void rev_unit_of(const RevUnits& U, long long u, int* tx, int* ty, int* cz);
+// The CPML units split into z-only units (tiles inside [ix0, ix1) x
+// [iy0, iy1), chunks outside [iz0, iz1)) and ring units (every other tile,
+// every chunk); the launches' unit enumerations, for the host and tests.
+void rev_zonly_unit(const RevUnits& U, int bx, int by, int bz, int* tx, int* ty, int* cz);
+void rev_ring_unit(const RevUnits& U, long long u, int* tx, int* ty, int* cz);
+long long rev_ring_tiles(const RevUnits& U);
 // which: 0 primal (E^n, Ht^{n-1/2}, dL/dcb), 1 adjoint over the CPML-free
-// units, 2 adjoint over the CPML units.  Reads a.F, a.L, a.psiA; writes
-// a.Fn, a.Ln, a.psiB, a.gacc.
+// units, 2 adjoint over the z-only units, 3 adjoint over the ring units.
+// Reads a.F, a.L, a.psiA; writes a.Fn, a.Ln, a.psiB, a.gacc.
 cudaError_t launch_rev_fused(int which, const RevMaps& m, const StepArgs& a, const RevUnits& U,
                              cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,

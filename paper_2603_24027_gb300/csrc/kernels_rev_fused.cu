@@ -64,15 +64,18 @@ struct PL {
 };
 
 // Stage layout of the adjoint kernel: cb and lam_E boxes (TW+8) x (TY+2) at
-// (x0-4, y0-1), lam_H box (TW+4) x (TY+1) at (x0-4, y0-1); with CPML (PML),
-// the adjoint auxiliaries of the E half-step at plane p (x: (TW+8) x (TY+1)
+// (x0-4, y0-1), lam_H box (TW+4) x (TY+1) at (x0-4, y0-1); with CPML terms
+// (by MODE below), the adjoint auxiliaries of the E half-step at plane p (x: (TW+8) x (TY+1)
 // at (x0-4, y0-1); y: (TW+4) x (TY+2) at (x0-4, y0-1); z: (TW+4) x (TY+1) at
 // (x0-4, y0-1)) and of the H half-step at plane p-1 (x: (TW+4) x TY at
 // (x0-4, y0); y: TW x (TY+1) at (x0, y0-1); z: TW x TY at (x0, y0)).  The
 // stages' mbarriers follow the S stages; then lam_H' of plane p-1 on the
 // tile and its -x / -y halo, [3][TY+1][TW+4] at (x0-4, y0-1).
-template <int TY, int S, int TW, bool PML>
+// MODE 0: no CPML term in the unit; 1: z CPML terms only (tiles inside the
+// x / y interior, chunks touching a z slab); 2: every axis (the x / y ring).
+template <int TY, int S, int TW, int MODE>
 struct AL {
+  static constexpr bool PXY = MODE == 2, PZ = MODE >= 1;
   static constexpr int WW = TW + 8, WR = TY + 2, WP = WW * WR;
   static constexpr int HW = TW + 4, HR = TY + 1, HP = HW * HR;
   static constexpr int EXP = (TW + 8) * (TY + 1), EYP = (TW + 4) * (TY + 2), EZP = HP;
@@ -81,12 +84,12 @@ struct AL {
   static constexpr int LE = CB + r128(WP * 4);
   static constexpr int LH = LE + r128(3 * WP * 4);
   static constexpr int PEX = LH + r128(3 * HP * 4);
-  static constexpr int PEY = PEX + (PML ? r128(2 * EXP * 4) : 0);
-  static constexpr int PEZ = PEY + (PML ? r128(2 * EYP * 4) : 0);
-  static constexpr int PHX = PEZ + (PML ? r128(2 * EZP * 4) : 0);
-  static constexpr int PHY = PHX + (PML ? r128(2 * HXP * 4) : 0);
-  static constexpr int PHZ = PHY + (PML ? r128(2 * HYP * 4) : 0);
-  static constexpr int STAGE = PHZ + (PML ? r128(2 * HZP * 4) : 0);
+  static constexpr int PEY = PEX + (PXY ? r128(2 * EXP * 4) : 0);
+  static constexpr int PEZ = PEY + (PXY ? r128(2 * EYP * 4) : 0);
+  static constexpr int PHX = PEZ + (PZ ? r128(2 * EZP * 4) : 0);
+  static constexpr int PHY = PHX + (PXY ? r128(2 * HXP * 4) : 0);
+  static constexpr int PHZ = PHY + (PXY ? r128(2 * HYP * 4) : 0);
+  static constexpr int STAGE = PHZ + (PZ ? r128(2 * HZP * 4) : 0);
   static constexpr int BARS = S * STAGE;
   static constexpr int SL = r128(BARS + 8 * S);
   static int smem() { return SL + 3 * HP * 4; }
@@ -95,36 +98,33 @@ struct AL {
 // ring_init puts the barriers at S * STAGE: the exchange arrays come after them
 static_assert(PL<8, 3, 32>::BARS == 3 * PL<8, 3, 32>::STAGE &&
               PL<8, 3, 32>::SE >= PL<8, 3, 32>::BARS + 8 * 3, "SE after the barriers");
-static_assert(AL<8, 3, 32, false>::SL >= AL<8, 3, 32, false>::BARS + 8 * 3, "SL after the barriers");
-static_assert(AL<8, 2, 32, true>::SL >= AL<8, 2, 32, true>::BARS + 8 * 2, "SL after the barriers");
+static_assert(AL<8, 3, 32, 0>::SL >= AL<8, 3, 32, 0>::BARS + 8 * 3, "SL after the barriers");
+static_assert(AL<8, 3, 32, 1>::SL >= AL<8, 3, 32, 1>::BARS + 8 * 3, "SL after the barriers");
+static_assert(AL<8, 2, 32, 2>::SL >= AL<8, 2, 32, 2>::BARS + 8 * 2, "SL after the barriers");
 
 // Resident CTAs per SM the register allocation must allow (what the shared
 // memory of the default shapes allows).
-template <int S, bool PML>
-constexpr int adj_ctas() { return PML ? 4 : 5; }
+template <int S, int MODE>
+constexpr int adj_ctas() { return MODE == 2 ? 4 : (MODE == 1 ? 4 : 5); }
 
-// Tile and chunk of this CTA.  Primal and CPML-free adjoint launches: a 3D
-// grid offset by (t0x, t0y, zc0).  Adjoint launch over the CPML units: a 1D
-// grid over every (tile, chunk) outside the CPML-free box [ix0, ix1) x
-// [iy0, iy1) x [iz0, iz1): first the chunks outside [iz0, iz1) with every
-// tile, then the chunks inside it with the tiles outside [ix0, ix1) x
-// [iy0, iy1) (rows below, rows above, then the left and right columns of the
-// rows in between).
-__host__ __device__ inline void unit_of(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
-  const long long NT = (long long)U.ntx * U.nty;
-  const int nzin = U.iz1 - U.iz0;
-  const long long nzs = U.nzc - nzin;
-  if (u < NT * nzs) {
-    const int c = (int)(u / NT), t = (int)(u % NT);
-    *cz = c < U.iz0 ? c : U.iz1 + (c - U.iz0);
-    *tx = t % U.ntx;
-    *ty = t / U.ntx;
-    return;
-  }
-  const long long ring = NT - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0);
-  long long v = u - NT * nzs;
-  *cz = U.iz0 + (int)(v / ring);
-  long long r = v % ring;
+// Tile and chunk of a unit.  Primal and CPML-free adjoint launches: a 3D
+// grid offset by (t0x, t0y, zc0).  z-only units (MODE 1): a 3D grid over the
+// tiles [ix0, ix1) x [iy0, iy1) and the chunks outside [iz0, iz1) (below,
+// then above).  Ring units (MODE 2): a 1D grid over every chunk times the
+// tiles outside [ix0, ix1) x [iy0, iy1) (rows below, rows above, then the
+// left and right columns of the rows in between).
+__host__ __device__ inline int zonly_chunk(const RevUnits& U, int c) {
+  return c < U.iz0 ? c : U.iz1 + (c - U.iz0);
+}
+
+__host__ __device__ inline long long ring_tiles(const RevUnits& U) {
+  return (long long)U.ntx * U.nty - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0);
+}
+
+__host__ __device__ inline void ring_unit(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
+  const long long ring = ring_tiles(U);
+  *cz = (int)(u / ring);
+  long long r = u % ring;
   const long long below = (long long)U.ntx * U.iy0;
   if (r < below) {
     *ty = (int)(r / U.ntx);
@@ -346,20 +346,21 @@ k_rev_primal(const __grid_constant__ RevMaps m, StepArgs a) {
 }
 
 // ============================================================= adjoint ===
-template <int TY, int S, int TW, bool PML>
-__global__ void __launch_bounds__(TW / 2 * (TY + 2), (adj_ctas<S, PML>()))
+template <int TY, int S, int TW, int MODE>
+__global__ void __launch_bounds__(TW / 2 * (TY + 2), (adj_ctas<S, MODE>()))
 k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
-  typedef AL<TY, S, TW, PML> Y;
+  typedef AL<TY, S, TW, MODE> Y;
+  constexpr bool PXY = Y::PXY, PZ = Y::PZ;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
   int tix, tiy, cz;
-  if (PML) {
-    unit_of(U, blockIdx.x, &tix, &tiy, &cz);
+  if (MODE == 2) {
+    ring_unit(U, blockIdx.x, &tix, &tiy, &cz);
   } else {
     tix = blockIdx.x + a.t0x;
     tiy = blockIdx.y + a.t0y;
-    cz = blockIdx.z + a.zc0;
+    cz = MODE == 1 ? zonly_chunk(U, blockIdx.z) : blockIdx.z + a.zc0;
   }
   const int x0 = tix * TW, y0 = tiy * TY;
   const int k0 = cz * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
@@ -379,7 +380,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);   // at Y::BARS
   int qx0 = x0, qy0 = y0;
   bool txs = false, tys = false, txh = false, tyh = false;
-  if (PML) {
+  if (PXY) {
     psi_box_starts<TW, TY>(a.pl, x0, y0, &qx0, &qy0);
     txs = tile_in_slab(max(x0 - 2, 0), min(x0 + TW, g.nx - 1), g.nx, g.P);
     tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY, g.ny - 1), g.ny, g.P);
@@ -389,20 +390,22 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
   auto inz = [&](int p) { return p >= 0 && p < g.nz; };
   auto boxes = [&](int p, auto&& f) {
     const bool tail = p == k1;
-    if (!inz(p) && !(PML && inz(p - 1) && p - 1 >= k0 - 1)) return;
+    if (!inz(p) && !(PZ && inz(p - 1) && p - 1 >= k0 - 1)) return;
     if (inz(p)) {
       f(Y::CB, &m.cb40, x0 - 4, y0 - 1, p, 0, Y::WP * 4);
       f(Y::LE, &m.L40, x0 - 4, y0 - 1, p, 0, 3 * Y::WP * 4);
       if (!tail) f(Y::LH, &m.L36, x0 - 4, y0 - 1, p, 3, 3 * Y::HP * 4);
     }
-    if (PML) {
+    const int pm = p - 1;
+    if (PXY) {
       if (inz(p) && !tail && txs) f(Y::PEX, &m.Qx40, qx0 - 4, y0 - 1, p, 2, 2 * Y::EXP * 4);
       if (inz(p) && !tail && tys) f(Y::PEY, &m.Qy36, x0 - 4, qy0 - 1, p, 2, 2 * Y::EYP * 4);
-      if (inz(p) && in_slab(p, g.nz, g.P))
-        f(Y::PEZ, &m.Qz36, x0 - 4, y0 - 1, psi_map(a.pl.ax[2], p), 2, 2 * Y::EZP * 4);
-      const int pm = p - 1;
       if (pm >= k0 && txh) f(Y::PHX, &m.Qxw, qx0 - 4, y0, pm, 0, 2 * Y::HXP * 4);
       if (pm >= k0 && tyh) f(Y::PHY, &m.Qyw, x0, qy0 - 1, pm, 0, 2 * Y::HYP * 4);
+    }
+    if (PZ) {
+      if (inz(p) && in_slab(p, g.nz, g.P))
+        f(Y::PEZ, &m.Qz36, x0 - 4, y0 - 1, psi_map(a.pl.ax[2], p), 2, 2 * Y::EZP * 4);
       if (pm >= k0 - 1 && inz(pm) && in_slab(pm, g.nz, g.P))
         f(Y::PHZ, &m.Qzo, x0, y0, psi_map(a.pl.ax[2], pm), 0, 2 * Y::HZP * 4);
     }
@@ -412,11 +415,11 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
   };
   if (tid == 0)
     for (int i = 0; i < S && p0_ + i <= p1_; ++i) issue(p0_ + i, dsm + i * Y::STAGE, bars + i);
-  // CPML profiles (PML units only): E side at x, x+1, x+2 and y, y+1; H side
+  // x / y CPML profiles (ring units only): E side at x, x+1, x+2 and y, y+1; H side
   // at x-1, x, x+1 and y-1, y
   bool sx0 = false, sx1 = false, sx2 = false, sy = false, sy1 = false;
   bool hx0 = false, hx1 = false, hxm = false, hy = false, hym = false;
-  if (PML) {
+  if (PXY) {
     sx0 = ok0 && in_slab(x, g.nx, g.P);
     sx1 = ok1 && in_slab(x + 1, g.nx, g.P);
     sx2 = ok1 && x + 2 < g.nx && in_slab(x + 2, g.nx, g.P);
@@ -454,7 +457,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
     const float* LEb = reinterpret_cast<const float*>(st + Y::LE);
     const float* LHb = reinterpret_cast<const float*>(st + Y::LH);
     const bool head = p < k0, tail = p == k1;
-    const bool zs = PML && inz(p) && in_slab(p, g.nz, g.P);
+    const bool zs = PZ && inz(p) && in_slab(p, g.nz, g.P);
     float fx[2] = {0.f, 0.f}, fy[2] = {0.f, 0.f};   // lam_Hx', lam_Hy' of plane p-1
     float own_le[3][2];                              // lam_E(p) at the pair
     // ---- transpose of the E half-step: lam_H' ----
@@ -489,7 +492,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             n10x = c2 * LEb[2 * Y::WP + wb + 2];
           }
         }
-        if (PML) {
+        if (PXY) {
           if (sy || sy1) {
             const float* P = reinterpret_cast<const float*>(st + Y::PEY);   // (TW+4) x (TY+2) at (x0-4, y0-1)
             const int yb = (y - y0 + 1) * (TW + 4) + (x - x0 + 4);
@@ -610,7 +613,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
           n7[1] = -c2.y * lx.y;
           n8[0] = c2.x * ly.x;
           n8[1] = c2.y * ly.y;
-          if (PML && zs) {
+          if (zs) {
             const float* P = reinterpret_cast<const float*>(st + Y::PEZ);
             const float b1 = prof(g, 2, PR_BE, p), a1 = prof(g, 2, PR_AE, p), k1v = prof(g, 2, PR_KE, p);
             const float2 p0 = ld2(P, lb), p1 = ld2(P + Y::EZP, lb);
@@ -665,8 +668,8 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
         if (y == 0) { m0[0] = 0.f; m0[1] = 0.f; m5[0] = 0.f; m5[1] = 0.f; }
         if (x == 0) { m3x = 0.f; m4x = 0.f; }
         const int pm = p - 1;
-        if (PML) {
-          if (hy || hym) {
+        {
+          if (PXY && (hy || hym)) {
             const float* P = reinterpret_cast<const float*>(st + Y::PHY);   // TW x (TY+1) at (x0, y0-1)
             const int yb = (y - y0 + 1) * TW + (x - x0);
             if (hy) {
@@ -696,7 +699,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               }
             }
           }
-          if (hx0 || hx1 || hxm) {
+          if (PXY && (hx0 || hx1 || hxm)) {
             const float* P = reinterpret_cast<const float*>(st + Y::PHX);   // (TW+4) x TY at (x0-4, y0)
             const int xb = (y - y0) * (TW + 4) + (x - x0 + 4);
             const float2 p0 = ld2(P, xb), p1 = ld2(P + Y::HXP, xb);
@@ -723,7 +726,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               m4x = adj(m4x, P[Y::HXP + xb - 1], b, aa, kk, &dummy);
             }
           }
-          if (in_slab(pm, g.nz, g.P)) {
+          if (PZ && in_slab(pm, g.nz, g.P)) {
             const float* P = reinterpret_cast<const float*>(st + Y::PHZ);   // TW x TY at (x0, y0)
             const int zb = (y - y0) * TW + (x - x0);
             const float b = prof(g, 2, PR_BH, pm), aa = prof(g, 2, PR_AH, pm), kv = prof(g, 2, PR_KH, pm);
@@ -764,7 +767,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             m1n[c] = S_ * fx[c];
             m2n[c] = -S_ * fy[c];
           }
-          if (PML && in_slab(pm, g.nz, g.P)) {
+          if (PZ && in_slab(pm, g.nz, g.P)) {
             const float* P = reinterpret_cast<const float*>(st + Y::PHZ);
             const int zb = (y - y0) * TW + (x - x0);
             const float b1 = prof(g, 2, PR_BH, pm), a1 = prof(g, 2, PR_AH, pm), k1v = prof(g, 2, PR_KH, pm);
@@ -821,11 +824,11 @@ static cudaError_t launch_rev_fused_t(int which, const RevMaps& m, const StepArg
         return launch_rf(k_rev_primal<TY, 3, TW, true>, grid, block, PL<TY, 3, TW>::smem(), s, m, a);
       return launch_rf(k_rev_primal<TY, 3, TW, false>, grid, block, PL<TY, 3, TW>::smem(), s, m, a);
     case 1:
-      return launch_rf(k_rev_adjoint<TY, 3, TW, false>, grid, block,
-                       AL<TY, 3, TW, false>::smem(), s, m, a, U);
+      return launch_rf(k_rev_adjoint<TY, 3, TW, 0>, grid, block, AL<TY, 3, TW, 0>::smem(), s, m, a, U);
     case 2:
-      return launch_rf(k_rev_adjoint<TY, 2, TW, true>, grid, block, AL<TY, 2, TW, true>::smem(), s,
-                       m, a, U);
+      return launch_rf(k_rev_adjoint<TY, 3, TW, 1>, grid, block, AL<TY, 3, TW, 1>::smem(), s, m, a, U);
+    case 3:
+      return launch_rf(k_rev_adjoint<TY, 2, TW, 2>, grid, block, AL<TY, 2, TW, 2>::smem(), s, m, a, U);
   }
   return cudaErrorInvalidValue;
 }
@@ -833,21 +836,30 @@ static cudaError_t launch_rev_fused_t(int which, const RevMaps& m, const StepArg
 cudaError_t launch_rev_fused(int which, const RevMaps& m, const StepArgs& a, const RevUnits& U,
                              cudaStream_t s) {
   const int TW = 32, TY = 8;
-  dim3 grid;
-  if (which == 0) {
-    grid = dim3(U.px1 - U.px0, U.py1 - U.py0, U.pz1 - U.pz0);
-  } else if (which == 1) {
-    grid = dim3(U.ix1 - U.ix0, U.iy1 - U.iy0, U.iz1 - U.iz0);
-  } else {
-    const long long n = (long long)U.ntx * U.nty * U.nzc -
-                        (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0) * (U.iz1 - U.iz0);
-    grid = dim3((unsigned)n, 1, 1);
+  if (a.tile_y != TY || a.tile_x != TW) return cudaErrorInvalidValue;
+  dim3 grid(0, 0, 0);
+  StepArgs b = a;
+  const int nzin = U.iz1 - U.iz0;
+  switch (which) {
+    case 0:
+      grid = dim3(U.px1 - U.px0, U.py1 - U.py0, U.pz1 - U.pz0);
+      b.t0x = U.px0; b.t0y = U.py0; b.zc0 = U.pz0;
+      break;
+    case 1:
+      grid = dim3(U.ix1 - U.ix0, U.iy1 - U.iy0, nzin);
+      b.t0x = U.ix0; b.t0y = U.iy0; b.zc0 = U.iz0;
+      break;
+    case 2:
+      grid = dim3(U.ix1 - U.ix0, U.iy1 - U.iy0, U.nzc - nzin);
+      b.t0x = U.ix0; b.t0y = U.iy0; b.zc0 = 0;
+      break;
+    case 3:
+      grid = dim3((unsigned)(ring_tiles(U) * U.nzc), 1, 1);
+      break;
+    default:
+      return cudaErrorInvalidValue;
   }
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  StepArgs b = a;
-  if (which == 0) { b.t0x = U.px0; b.t0y = U.py0; b.zc0 = U.pz0; }
-  if (which == 1) { b.t0x = U.ix0; b.t0y = U.iy0; b.zc0 = U.iz0; }
-  if (a.tile_y != TY || a.tile_x != TW) return cudaErrorInvalidValue;
   return launch_rev_fused_t<8>(which, m, b, U, grid, s);
 }
 
@@ -883,8 +895,16 @@ RevUnits rev_units(const Geo& g, int zchunk) {
   return U;
 }
 
-void rev_unit_of(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
-  unit_of(U, u, tx, ty, cz);
+void rev_zonly_unit(const RevUnits& U, int bx, int by, int bz, int* tx, int* ty, int* cz) {
+  *tx = bx + U.ix0;
+  *ty = by + U.iy0;
+  *cz = zonly_chunk(U, bz);
 }
+
+void rev_ring_unit(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
+  ring_unit(U, u, tx, ty, cz);
+}
+
+long long rev_ring_tiles(const RevUnits& U) { return ring_tiles(U); }
 
 }  // namespace fdtd
