@@ -143,8 +143,10 @@ typedef struct {
   int coeffs;
 } fdtd_record_cfg;
 
-/* Plan a problem.  Host only: touches no device.  dx in metres, dt in
- * seconds with c dt / dx <= 1/sqrt(3).  n_steps >= 1.  design box
+/* Plan a problem (Sec. 2, Fig. 2: a simulation volume surrounded by PML on
+ * every face, a source, a detector and a design region; the time step obeys
+ * the CFL bound of Eq. 1).  Host only: touches no device.  dx in metres, dt
+ * in seconds with c dt / dx <= 1/sqrt(3).  n_steps >= 1.  design box
  * [lo, hi) inside the interior.  cuda_stream: the caller's stream (NULL =
  * legacy default stream); all work is ordered after work already queued
  * there, and later work queued there sees the results.
@@ -164,16 +166,22 @@ int fdtd_bind_workspace(fdtd_handle* h, void* dptr, size_t bytes);
 /* Bytes of the compressed boundary tape alone (samples + scales). */
 int fdtd_tape_bytes(const fdtd_handle* h, const fdtd_record_cfg* rec, size_t* bytes);
 
-/* Forward run: n_steps leapfrog steps from zero fields with eps (device,
- * float32 [nz][ny][nx], every value finite and >= 1), recording the
- * boundary tape; writes L to *objective (host).  Blocks until done.
- * Keeps the final state for fdtd_backward. */
+/* Forward run (Sec. 2: the forward simulation records the field values at
+ * the interface slices between the simulation volume and the PML, converted
+ * to the tape's bit-width and kept every k-th step): n_steps leapfrog steps
+ * from zero fields with eps (device, float32 [nz][ny][nx], every value
+ * finite and >= 1), recording the boundary tape; writes L to *objective
+ * (host).  Blocks until done.  Keeps the final state for fdtd_backward. */
 int fdtd_forward(fdtd_handle* h, const float* d_eps, const fdtd_record_cfg* rec,
                  double* objective);
 
-/* Backward run: seed * dL/d(eps) over the design box into d_grad_eps
- * (device, float32 [dz][dy][dx]).  Needs a preceding fdtd_forward; consumes
- * its state (FDTD_ESTATE otherwise).  Blocks until done. */
+/* Backward run (Sec. 2: the time-reversed simulation, with the recorded
+ * values converted back to float32, interpolated in time and injected at
+ * the interface slices, which act as sources; the adjoint runs alongside and
+ * gives the gradient, Sec. 1): seed * dL/d(eps) over the design box into
+ * d_grad_eps (device, float32 [dz][dy][dx]).  Needs a preceding
+ * fdtd_forward; consumes its state (FDTD_ESTATE otherwise).  Blocks until
+ * done. */
 int fdtd_backward(fdtd_handle* h, double seed, float* d_grad_eps);
 
 /* Both directions with HOST buffers (end-to-end path): copies h_eps to the
