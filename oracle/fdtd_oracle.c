@@ -15,7 +15,10 @@
  *     interface slices between the simulation volume and the PML, compressed
  *     by reduced bit-width and by keeping every k-th step; then run the
  *     time-reversed simulation with those slices injected back (linear or
- *     cubic interpolation in time) together with the adjoint.
+ *     cubic interpolation in time) together with the adjoint;
+ *   - the method's single operations (half-steps, their inverses and
+ *     transposes, the objective and its seed, one face's interface layer),
+ *     exported for tests that run the method piece by piece.
  *
  * Discretisation (the paper assumes a standard FDTD and cites the textbook):
  *   E and Ht = eta0*H; Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2),
@@ -971,6 +974,22 @@ int oracle_unstep(const ocfg* c, const double* eps, double* st, int n) {
   return 0;
 }
 
+/* grad += -sum_e lam_E[e] * dE[e] / eps on the design box [dz][dy][dx]
+ * (dE = E^{n+1} - E^n = cb * (curl Ht - J): the adjoint's share of step n). */
+static void grad_accumulate(const ocfg* c, const double* eps, const double* lam,
+                            const double* dE, double* grad) {
+  size_t N = ncell(c);
+  int dX = c->dhi[0] - c->dlo[0], dY = c->dhi[1] - c->dlo[1], dZ = c->dhi[2] - c->dlo[2];
+  for (int kk = 0; kk < dZ; ++kk)
+    for (int jj = 0; jj < dY; ++jj)
+      for (int ii = 0; ii < dX; ++ii) {
+        size_t q = idx(c, c->dlo[0] + ii, c->dlo[1] + jj, c->dlo[2] + kk);
+        double s = 0.0;
+        for (int e = 0; e < 3; ++e) s += lam[e * N + q] * dE[e * N + q];
+        grad[((size_t)kk * dY + jj) * dX + ii] += -s / eps[q];
+      }
+}
+
 /* ------------------------------------------------ the method, FP64 ----
  * Forward N steps recording the interface slices at the sample steps
  * s_j = r + j k (r = (N-1) mod k, so the last step is always a sample),
@@ -1083,14 +1102,7 @@ int oracle_reverse2(const ocfg* c, const double* eps, int fmt, int scaled, int c
     objective_seed(c, st, seed, lam);
     if (c->det2_kind) objective_seed(&c2, st, seed2, lam);
     inverse_e(&x, eps, st, n, dE);
-    for (int kk = 0; kk < dZ; ++kk)
-      for (int jj = 0; jj < dY; ++jj)
-        for (int ii = 0; ii < dX; ++ii) {
-          size_t q = idx(c, c->dlo[0] + ii, c->dlo[1] + jj, c->dlo[2] + kk);
-          double s = 0.0;
-          for (int e = 0; e < 3; ++e) s += lam[e * N + q] * dE[e * N + q];
-          grad[((size_t)kk * dY + jj) * dX + ii] += -s / eps[q];
-        }
+    grad_accumulate(c, eps, lam, dE, grad);
     adj_e_transpose(&x, eps, lam, tmp);
     /* restore E^n: knots 0 (zero, unless s_0 == 0) and s_j */
     nk = 0;
@@ -1130,4 +1142,53 @@ int oracle_reverse_ex(const ocfg* c, const double* eps, int fmt, int scaled, int
 int oracle_reverse(const ocfg* c, const double* eps, int fmt, int scaled, int k, int interp,
                    double seed, double* grad, double* obj, double* tape_values_out) {
   return oracle_reverse_ex(c, eps, fmt, scaled, 0, k, interp, seed, grad, obj, tape_values_out);
+}
+
+/* ---------------------------------------- the method's pieces, exported ----
+ * Single operations of the method above on the full grid, for tests that run
+ * it piece by piece (for instance split into z slabs, each holding only its
+ * own planes).  st and lam: NF arrays of ncell doubles.
+ *   op 0: H half-step of the forward (st);
+ *   op 1: E half-step of step n (st);
+ *   op 2: inverse E half-step of step n on the interior (st); dE (3 ncell,
+ *         optional) receives E^{n+1} - E^n there;
+ *   op 3: inverse H half-step on the interior (st);
+ *   op 4: transpose of the E half-step (lam; tmp: 6 ncell doubles);
+ *   op 5: transpose of the H half-step (lam; tmp);
+ *   op 6: grad += -lam_E . dE / eps on the design box (lam, dE, grad).
+ */
+int oracle_op(const ocfg* c, const double* eps, int op, int n, double* st, double* lam,
+              double* tmp, double* dE, double* grad) {
+  octx x;
+  if (op < 0 || op > 6) return -1;
+  if (ctx_init(&x, c)) { ctx_free(&x); return -2; }
+  switch (op) {
+    case 0: h_update(&x, st); break;
+    case 1: e_update(&x, eps, st, n); break;
+    case 2: inverse_e(&x, eps, st, n, dE); break;
+    case 3: inverse_h(&x, st); break;
+    case 4: adj_e_transpose(&x, eps, lam, tmp); break;
+    case 5: adj_h_transpose(&x, lam, tmp); break;
+    default: grad_accumulate(c, eps, lam, dE, grad); break;
+  }
+  ctx_free(&x);
+  return 0;
+}
+
+/* l_n of the detector from the state (E^{n+1}, Ht^{n+1/2}). */
+double oracle_objective(const ocfg* c, const double* st) {
+  return c->det_kind ? objective(c, st) : 0.0;
+}
+
+/* lam += seed * dl_n / d(E^{n+1}, Ht^{n+1/2}) on the detector. */
+void oracle_objective_seed(const ocfg* c, const double* st, double seed, double* lam) {
+  if (c->det_kind) objective_seed(c, st, seed, lam);
+}
+
+/* Face f's interface layer: dir 0 copies state -> buf, dir 1 buf -> state
+ * (values [tangential comp][v][u], the tape's order). */
+int oracle_face_io(const ocfg* c, int f, double* st, double* buf, int dir) {
+  if (f < 0 || f > 5 || c->P < 1) return -1;
+  face_io(c, f, st, buf, dir);
+  return 0;
 }

@@ -78,6 +78,11 @@ def lib():
         L.oracle_reverse2.argtypes = [cp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_double, C.c_double, dp, dp, dp]
         L.oracle_encode_face.argtypes = [C.c_int, C.c_int, dp, C.c_size_t, dp]
+        L.oracle_op.argtypes = [cp, dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+        L.oracle_objective.argtypes = [cp, dp]
+        L.oracle_objective.restype = C.c_double
+        L.oracle_objective_seed.argtypes = [cp, dp, C.c_double, dp]
+        L.oracle_face_io.argtypes = [cp, C.c_int, dp, dp, C.c_int]
         L.oracle_bdct_basis.argtypes = [fp]
         L.oracle_bdct_encode.argtypes = [fp, C.c_int, C.c_int, C.c_int, bp, fp]
         L.oracle_bdct_decode.argtypes = [bp, fp, C.c_int, C.c_int, C.c_int, fp]
@@ -267,6 +272,37 @@ def reverse2(w, fmt: str = "none", scaled: bool = False, k: int = 1, interp: str
                                  0 if interp == "linear" else 1, seed, seed2, _dp(g), _dp(obj),
                                  None))
     return float(obj[0]), float(obj[1]), g
+
+
+OPS = {"forward_h": 0, "forward_e": 1, "inverse_e": 2, "inverse_h": 3, "adjoint_e": 4,
+       "adjoint_h": 5, "grad": 6}
+
+
+def op(w, name: str, n: int = 0, state=None, lam=None, tmp=None, dE=None, grad=None, **kw):
+    """One operation of the method on the full grid, in place (see
+    oracle_op): forward_h / forward_e / inverse_e (dE optional) / inverse_h
+    on `state`; adjoint_e / adjoint_h on `lam` (tmp: 6 x ncell scratch);
+    grad (lam, dE, grad over the design box)."""
+    c = make_cfg(w, **kw)
+    ptr = lambda a: None if a is None else _dp(a)  # noqa: E731
+    _check(lib().oracle_op(C.byref(c), _dp(_eps(w)), OPS[name], n, ptr(state), ptr(lam),
+                           ptr(tmp), ptr(dE), ptr(grad)))
+
+
+def objective(w, state, **kw) -> float:
+    """l_n of the workload's detector from (E^{n+1}, Ht^{n+1/2})."""
+    return float(lib().oracle_objective(C.byref(make_cfg(w, **kw)), _dp(state)))
+
+
+def objective_seed(w, state, seed: float, lam, **kw) -> None:
+    lib().oracle_objective_seed(C.byref(make_cfg(w, **kw)), _dp(state), seed, _dp(lam))
+
+
+def face_io(w, f: int, state, buf, to_state: bool = False, **kw) -> None:
+    """Copy face f's interface layer out of (or, to_state, into) the state;
+    buf: 2 * nu * nv doubles [comp][v][u]."""
+    _check(lib().oracle_face_io(C.byref(make_cfg(w, **kw)), f, _dp(state), _dp(buf),
+                                int(to_state)))
 
 
 def encode_face(fmt: str, values, scaled: bool = True):
