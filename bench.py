@@ -79,6 +79,8 @@ def parse(argv=None):
     p.add_argument("--kernel", type=int, default=-1, help="0 plain loads, 5 staged, -1 default")
     p.add_argument("--reverse", type=int, default=-1,
                    help="reverse step: 1 split phases, 2 fused, -1 the library's choice")
+    p.add_argument("--forward", type=int, default=-1,
+                   help="forward step: 1 split half-steps, 2 fused, -1 the library's choice")
     p.add_argument("--zgroups", type=int, default=0,
                    help="z groups per half-step (0: the library's automatic choice)")
     p.add_argument("--autotune", action="store_true",
@@ -200,8 +202,8 @@ def phase_bytes(w, tape: str):
 def kernel_bytes(w):
     """Per-launch bytes each split half-step kernel moves itself (its own
     reads and writes), for the per-kernel breakdown only: the split reverse
-    reads E, Ht and the adjoint in both of its launches.  (The fused
-    reverse's launches are accounted as the reverse phase.)"""
+    reads E, Ht and the adjoint in both of its launches.  (The fused steps'
+    launches are accounted as their phase.)"""
     c = cell_classes(w)
     n, ni, nd, sa = c["cells"], c["interior"], c["design"], c["slab_axes"]
     npml = n - ni
@@ -210,7 +212,7 @@ def kernel_bytes(w):
             "rev_h": 72 * ni + 36 * npml + 16 * sa}
 
 
-PHASE_KERNELS = {"forward": ["fwd_h", "fwd_e", "record"],
+PHASE_KERNELS = {"forward": ["fwd_fused", "fwd_h", "fwd_e", "record"],
                  "reverse": ["restore_seed", "rev_e", "rev_h", "rev_primal", "rev_adjoint",
                              "rev_adjoint_cpml"]}
 
@@ -324,6 +326,8 @@ def apply_options(A, sim, args):
         sim.set_option(A.OPT_KERNEL, args.kernel)
     if args.reverse >= 0:
         sim.set_option(A.OPT_REVERSE, args.reverse)
+    if args.forward >= 0:
+        sim.set_option(A.OPT_FORWARD, args.forward)
     sim.set_option(A.OPT_ZGROUPS, args.zgroups)
     for val, opt in ((args.tile_y, A.OPT_TILE_Y), (args.tile_x, A.OPT_TILE_X),
                      (args.zchunk, A.OPT_ZCHUNK), (args.stages, A.OPT_STAGES)):
@@ -366,6 +370,8 @@ def sampled_breakdown(A, fdtd, args, w, rec, dev, flush):
     torch.cuda.synchronize()
     per_step = {"record": 1.0 / rec.k}
     kb = kernel_bytes(w)
+    if "fwd_fused" in ktimes:   # the split half-steps ran only the fused step's CPML units
+        kb = {k: v for k, v in kb.items() if k not in ("fwd_h", "fwd_e")}
     step_ms = statistics.median(loop_ms) / ws_.n_steps
     kern = {}
     for name, lst in ktimes.items():
@@ -376,6 +382,8 @@ def sampled_breakdown(A, fdtd, args, w, rec, dev, flush):
         if name in kb:
             d["own_bytes"] = kb[name]
             d["own_gbs"] = kb[name] / (avg / 1e3) / 1e9
+        if name in ("fwd_h", "fwd_e") and "fwd_fused" in ktimes:
+            d["units"] = "the CPML units of the fused forward step"
         kern[name] = d
     del sim
     return kern, {"n_steps": ws_.n_steps, "ms_per_time_step": step_ms}
@@ -568,7 +576,7 @@ def run_profile(args):
     opts = {name: sim.get_option(getattr(A, name)) for name in
             ("OPT_KERNEL", "OPT_TILE_Y", "OPT_TILE_X", "OPT_ZCHUNK", "OPT_ZCHUNK_FWD",
              "OPT_STAGES", "OPT_ZGROUPS", "OPT_COMPACT_AUX", "OPT_PDL", "OPT_PREFETCH",
-             "OPT_REVERSE")}
+             "OPT_REVERSE", "OPT_FORWARD")}
     print(json.dumps(dict(workload=w.name, n_steps=w.n_steps, pml=w.pml_thickness,
                           tape=args.tape, options=opts, L=L, grad_l1=float(g.abs().sum()),
                           timing=sim.last_timing(), kernels=sim.kernel_timing())))

@@ -284,7 +284,7 @@ enum {
                                    FDTD_ETIMEOUT with the CUDA context usable.  0 (default) =
                                    off.  Injects no fault: the wait is the same bounded wait
                                    as fdtd_selftest_wait */
-  FDTD_OPT_REVERSE = 15         /* kernel 5: how a reverse time step runs.  0 (default) =
+  FDTD_OPT_REVERSE = 15,        /* kernel 5: how a reverse time step runs.  0 (default) =
                                    automatic: fused with 32 x 8 tiles when at most half of
                                    the (tile, z chunk) units carry CPML terms (see
                                    fdtd_reverse_units), else split; 1 = split:
@@ -299,6 +299,19 @@ enum {
                                    fdtd_forward with other tiles.  Results agree with the
                                    split phases: primal fields bit for bit, gradients to
                                    rounding */
+  FDTD_OPT_FORWARD = 16         /* kernel 5: how a forward time step runs.  0 (default) =
+                                   automatic: fused where it can run (below) and at most
+                                   half of the (tile, z chunk) units carry CPML terms, else
+                                   split; 1 = split: an H and an E half-step launch, each
+                                   updating the fields in place; 2 = fused: the units
+                                   without a CPML term (fdtd_reverse_units' CPML-free box)
+                                   run both half-steps in one launch that reads every field
+                                   once and writes it once into the other buffer of a
+                                   ping-pong pair, and the other units run the split
+                                   half-steps from and into the same pair.  Needs 32 x 8
+                                   tiles, such units, and the source and the detector
+                                   outside them; else FDTD_EINVAL at fdtd_forward.  The
+                                   fields are bit-identical to the split half-steps' */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);
@@ -307,7 +320,7 @@ int fdtd_get_option(const fdtd_handle* h, int option, int* value);
 enum {
   FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
   FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_REV_PRIMAL = 6, FDTD_K_REV_ADJOINT = 7,
-  FDTD_K_MONITOR = 8, FDTD_K_REV_ADJOINT_CPML = 9, FDTD_K_KINDS = 10
+  FDTD_K_MONITOR = 8, FDTD_K_REV_ADJOINT_CPML = 9, FDTD_K_FWD_FUSED = 10, FDTD_K_KINDS = 11
 };
 /* Average in-loop cost (ms) per launch of one kernel kind in the last
  * forward + backward, and the number of samples it rests on

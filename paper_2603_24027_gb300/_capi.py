@@ -28,11 +28,11 @@ BDCT_DEFAULT_COEFFS = 10
 INTERP = {"linear": 0, "cubic": 1}
 OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY = range(5)
 OPT_STAGES, OPT_PDL, OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX, OPT_EXACT_REVERSAL, \
-    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT, OPT_REVERSE = range(6, 16)
+    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT, OPT_REVERSE, OPT_FORWARD = range(6, 17)
 K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_REV_PRIMAL, K_REV_ADJOINT, K_MONITOR, \
-    K_REV_ADJOINT_CPML = range(10)
+    K_REV_ADJOINT_CPML, K_FWD_FUSED = range(11)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "rev_primal",
-                "rev_adjoint", "monitor", "rev_adjoint_cpml"]
+                "rev_adjoint", "monitor", "rev_adjoint_cpml", "fwd_fused"]
 
 
 class Grid(C.Structure):

@@ -40,7 +40,8 @@ struct Layout {
 
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, stages, pdl, prefetch,
-      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait, reverse;
+      tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait, reverse, forward,
+      start_buf;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -88,6 +89,7 @@ struct fdtd_handle {
       opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
   int opt_inject_wait;        // FDTD_OPT_INJECT_WAIT_TIMEOUT (SM cycles; 0 = off)
   int opt_reverse;            // FDTD_OPT_REVERSE: 0 automatic, 1 split phases, 2 fused
+  int opt_forward;            // FDTD_OPT_FORWARD: 0 automatic, 1 split half-steps, 2 fused
   // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
   // three events (the last launch of an even / odd phase, the join), plus the
   // fork event
@@ -398,6 +400,53 @@ static bool fused_reverse(const fdtd_handle* h) {
   return 2 * cpml <= all;
 }
 
+// Planes per z chunk of a fused forward step (the unit grid of its launches).
+static int fused_forward_zchunk(const fdtd_handle* h) {
+  if (h->opt_zchunk_fwd > 0) return h->opt_zchunk_fwd;
+  return h->opt_zchunk > 0 ? h->opt_zchunk : h->nz;
+}
+
+// Does the plane region (normal `axis` at `index`, [u0, u1) x [v0, v1) in the
+// other two axes, increasing axis order) meet the cell box [lo, hi)?
+static bool plane_meets(int axis, int index, int u0, int u1, int v0, int v1, const int lo[3],
+                        const int hi[3]) {
+  const int ua = axis == 0 ? 1 : 0, va = axis == 2 ? 1 : 2;
+  return index >= lo[axis] && index < hi[axis] && u0 < hi[ua] && u1 > lo[ua] && v0 < hi[va] &&
+         v1 > lo[va];
+}
+
+// The forward step of kernel 5 runs the units without a CPML term as one
+// fused launch (both half-steps, kernels_fwd_fused.cu) and the other units
+// with the split half-steps, unless FDTD_OPT_FORWARD asks for the split
+// half-steps everywhere.  It needs 32 x 8 tiles, such units, and the source
+// and the detector outside them (the split E half-step adds the source and
+// sums the objective).  Automatic (0): as the reverse step, fused where at
+// most half of the units carry CPML terms.
+static bool fused_forward(const fdtd_handle* h) {
+  if (h->opt_kernel != 5 || h->opt_forward == 1) return false;
+  const int ty = h->opt_tile_y < 2 ? 2 : h->opt_tile_y;
+  const int tx = (ty == 8 && h->opt_stages <= 3 && h->opt_tile_x == 40) ? 40 : 32;
+  if (ty != 8 || tx != 32) return false;
+  Geo g;
+  memset(&g, 0, sizeof g);
+  g.nx = h->nx; g.ny = h->ny; g.nz = h->nz; g.P = h->P;
+  const int zc = fused_forward_zchunk(h);
+  const RevUnits U = rev_units(g, zc);
+  if (U.ix1 <= U.ix0 || U.iy1 <= U.iy0 || U.iz1 <= U.iz0) return false;
+  const int lo[3] = {U.ix0 * 32, U.iy0 * 8, U.iz0 * zc};
+  const int hi[3] = {U.ix1 * 32, U.iy1 * 8, std::min(U.iz1 * zc, h->nz)};
+  if (h->src.kind && plane_meets(h->src_axis, h->src_index, h->src_u0, h->src_u1, h->src_v0,
+                                 h->src_v1, lo, hi))
+    return false;
+  if (h->det.kind && plane_meets(h->det.axis, h->det.index, h->det.lo[0], h->det.hi[0],
+                                 h->det.lo[1], h->det.hi[1], lo, hi))
+    return false;
+  if (h->opt_forward == 2) return true;
+  const long long all = (long long)U.ntx * U.nty * U.nzc;
+  const long long cpml = all - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0) * (U.iz1 - U.iz0);
+  return 2 * cpml <= all;
+}
+
 // ---------------------------------------------------------------- layout ---
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 static int rup4(int x) { return (x + 3) & ~3; }
@@ -446,16 +495,16 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   size_t psbF = al((size_t)L.plF.total * sizeof(float));
   size_t psbL = al((size_t)L.plL.total * sizeof(float));
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
-  // the fused reverse step writes the new fields and adjoint fields next to
-  // the old ones (ping-pong pairs)
-  const bool pingpong = fused_reverse(h);
+  // the fused steps write the new fields (and, in reverse, adjoint fields)
+  // next to the old ones (ping-pong pairs)
+  const bool rev2 = fused_reverse(h), fwd2 = fused_forward(h);
   size_t off = 0;
   L.F[0] = off; off += f6;
   L.F[1] = L.F[0];
-  if (pingpong) { L.F[1] = off; off += f6; }
+  if (rev2 || fwd2) { L.F[1] = off; off += f6; }
   L.L[0] = off; off += f6;
   L.L[1] = L.L[0];
-  if (pingpong) { L.L[1] = off; off += f6; }
+  if (rev2) { L.L[1] = off; off += f6; }
   L.cb = off; off += al(nc * sizeof(float));
   L.eps = off; off += al((size_t)h->nx * h->ny * h->nz * sizeof(float));
   L.psiF[0] = off; off += psbF;
@@ -611,6 +660,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_exact = 0;
   h->opt_inject_wait = 0;
   h->opt_reverse = 0;
+  h->opt_forward = 0;
   for (int q = 0; q < FDTD_K_KINDS; ++q) {
     h->savg[q] = 0.f;
     h->scount[q] = 0;
@@ -742,6 +792,11 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value != h->opt_reverse) h->have_forward = false;   // the workspace layout changes
       h->opt_reverse = value;
       break;
+    case FDTD_OPT_FORWARD:
+      if (value < 0 || value > 2) return fail(h, FDTD_EINVAL, "forward must be 0, 1 or 2");
+      if (value != h->opt_forward) h->have_forward = false;   // the workspace layout changes
+      h->opt_forward = value;
+      break;
     case FDTD_OPT_INJECT_WAIT_TIMEOUT:
       if (value < 0) return fail(h, FDTD_EINVAL, "injected wait limit must be >= 0");
       h->opt_inject_wait = value;
@@ -775,6 +830,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_ZGROUPS: *value = h->opt_zgroups; break;
     case FDTD_OPT_INJECT_WAIT_TIMEOUT: *value = h->opt_inject_wait; break;
     case FDTD_OPT_REVERSE: *value = h->opt_reverse; break;
+    case FDTD_OPT_FORWARD: *value = h->opt_forward; break;
     default: return FDTD_EINVAL;
   }
   return FDTD_OK;
@@ -1125,7 +1181,8 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
   return e;
 }
 
-static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR};
+static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR,
+                                FDTD_K_FWD_FUSED};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_REV_PRIMAL,
                                 FDTD_K_REV_ADJOINT, FDTD_K_REV_ADJOINT_CPML};
 
@@ -1167,6 +1224,79 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
     return e;
   Sampler smp(h, 0);
+  if (fused_forward(h)) {
+    // fused forward step: the CPML-free units in one launch on the main
+    // stream, the split H half-step of the other units beside it on a side
+    // stream, then their split E half-step; buffer cur of the fields is read
+    // and buffer cur ^ 1 written (the auxiliaries stay in place)
+    a.zchunk = fused_forward_zchunk(h);
+    const RevUnits U = rev_units(a.g, a.zchunk);
+    RevMaps fm[2];
+    LagMaps lh[2], le[2];
+    for (int b = 0; b < 2; ++b) {
+      const float* Fb = (const float*)(h->ws + L.F[b]);
+      const float* Fo = (const float*)(h->ws + L.F[b ^ 1]);
+      const float* cbp = (const float*)(h->ws + L.cb);
+      const float* ps = (const float*)(h->ws + L.psiF[0]);
+      if ((e = encode_rev_maps(Fb, Fb, cbp, ps, a.g, L.plF, &fm[b]))) return e;
+      if ((e = encode_lag_maps(Fb, Fb, cbp, ps, a.g, 8, 32, L.plF, &lh[b]))) return e;
+      if ((e = encode_lag_maps(Fb, Fb, cbp, ps, a.g, 8, 32, L.plF, &le[b], Fo))) return e;
+    }
+    const bool conc = h->opt_sample == 0 && h->opt_zgroups != 1 && !h->zs.empty() &&
+                      h->zev.size() >= 3;
+    int cur = 0;
+    for (int n = 0; n < h->N; ++n) {
+      a.jn = h->wave[n];
+      a.obj = (double*)(h->ws + L.obj) + n;
+      a.F = (float*)(h->ws + L.F[cur]);
+      a.Fn = (float*)(h->ws + L.F[cur ^ 1]);
+      const bool rec_now = n >= r && (n - r) % rec->k == 0;
+      const int j = rec_now ? (n - r) / rec->k : 0;
+      cudaStream_t side = conc ? h->zs[0] : h->stream;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[0], h->stream))) return e;
+        if ((e = cudaStreamWaitEvent(side, h->zev[0], 0))) return e;
+      }
+      StepArgs b = a;
+      b.U = U;
+      if ((e = smp.before(FDTD_K_FWD_FUSED))) return e;
+      if ((e = launch_fwd_fused(fm[cur], a, U, h->stream))) return e;
+      if ((e = smp.after(FDTD_K_FWD_FUSED))) return e;
+      if ((e = smp.before(FDTD_K_FWD_H))) return e;
+      for (int um = 1; um <= 2; ++um) {
+        b.umode = um;
+        if ((e = launch_lag2(0, lh[cur], b, side))) return e;
+      }
+      if ((e = smp.after(FDTD_K_FWD_H))) return e;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[1], side))) return e;
+        if ((e = cudaStreamWaitEvent(h->stream, h->zev[1], 0))) return e;
+      }
+      if ((e = smp.before(FDTD_K_FWD_E))) return e;
+      for (int um = 1; um <= 2; ++um) {
+        b.umode = um;
+        if ((e = launch_lag2(1, le[cur], b, h->stream))) return e;
+      }
+      if ((e = smp.after(FDTD_K_FWD_E))) return e;
+      nl += 5;
+      if (rec_now) {   // E^n is still in buffer cur, Ht^{n+1/2} now in cur ^ 1
+        if ((e = smp.before(FDTD_K_RECORD))) return e;
+        if ((e = record(a.Fn, a.F, j))) return e;
+        if ((e = smp.after(FDTD_K_RECORD))) return e;
+        ++nl;
+      }
+      if (det2.kind) {
+        if ((e = smp.before(FDTD_K_MONITOR))) return e;
+        if ((e = launch_monitor(a.Fn, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream)))
+          return e;
+        if ((e = smp.after(FDTD_K_MONITOR))) return e;
+        ++nl;
+      }
+      cur ^= 1;
+    }
+    *launches = nl;
+    return cudaSuccess;
+  }
   ZGroups zg(h, pair, 0, a);
   if (zg.active()) smp.m = 0;   // launches of a phase overlap: no per-kind intervals
   if ((e = zg.fork())) return e;
@@ -1215,7 +1345,6 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
     }
   }
   if ((e = zg.join())) return e;
-  h->fwd_buf = 0;
   *launches = nl;
   return cudaSuccess;
 }
@@ -1229,7 +1358,10 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
   cudaError_t e;
   int nl = 0;
-  if ((e = cudaMemsetAsync(h->ws + L.L[0], 0, nc6, h->stream))) return e;
+  // the adjoint starts at zero in the buffer the first step reads: the fused
+  // reverse step starts in the forward's buffer, the split phases work in 0
+  const int lam0 = fused_reverse(h) ? h->fwd_buf : 0;
+  if ((e = cudaMemsetAsync(h->ws + L.L[lam0], 0, nc6, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.psiL[0], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.psiL[1], 0, psb, h->stream))) return e;
   if ((e = cudaMemsetAsync(h->ws + L.gacc, 0, nd * sizeof(double), h->stream))) return e;
@@ -1242,7 +1374,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
   a.L = (float*)(h->ws + L.L[0]);
   Det det = a.det;
   const Det det2 = det2_of(h);
-  int cur = 0;
+  int cur = h->fwd_buf;   // the forward's final state
   const bool fused = fused_reverse(h);
   const bool rpair = h->opt_kernel == 5 && !fused;
   LagMaps lrmaps[2];
@@ -1253,7 +1385,7 @@ static cudaError_t enqueue_backward(fdtd_handle* h, const fdtd_record_cfg* rec, 
       return e;
   // fused reverse step: buffer cur of the fields, the adjoint fields and the
   // auxiliaries is read, buffer cur ^ 1 written (the forward's state is in
-  // buffer 0)
+  // buffer fwd_buf; the adjoint starts in buffer fwd_buf too)
   RevMaps rmaps[2];
   const RevUnits U = rev_units(a.g, a.zchunk);
   // the adjoint launches run on a side stream unless kernel timing is being
@@ -1393,6 +1525,8 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.zgroups = h->opt_zgroups;
   key.inject_wait = h->opt_inject_wait;
   key.reverse = h->opt_reverse;
+  key.forward = h->opt_forward;
+  key.start_buf = dir == 1 ? h->fwd_buf : 0;   // the backward starts from the forward's buffer
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph;
@@ -1453,6 +1587,10 @@ static int check_kernel_options(fdtd_handle* h) {
     return fail(h, FDTD_EINVAL, "exact reversal is built into kernel 5 with its default tiles");
   if (h->opt_reverse == 2 && !fused_reverse(h))
     return fail(h, FDTD_EINVAL, "the fused reverse step is built into kernel 5 with 32 x 8 tiles");
+  if (h->opt_forward == 2 && !fused_forward(h))
+    return fail(h, FDTD_EINVAL,
+                "the fused forward step needs kernel 5, 32 x 8 tiles, CPML-free units and the "
+                "source and detector outside them");
   return FDTD_OK;
 }
 
@@ -1478,7 +1616,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   nvtxRangePop();
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = 0;
+  h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;   // a fused forward ends in buffer N mod 2
   h->fwd_rec = *rec;
   return FDTD_OK;
 }
@@ -1498,7 +1636,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   h->obj2_sum = 0.0;
   for (double v : m) h->obj2_sum += v;
   CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
-  collect_samples(h, 0, kFwdKinds, 4);
+  collect_samples(h, 0, kFwdKinds, 5);
   int rc = finish(h);
   if (rc) return rc;
   rc = check_err(h, err);
@@ -1550,7 +1688,7 @@ static int backward_async(fdtd_handle* h, double seed, double seed2) {
   h->have_forward = false;
   // the fused reverse step leaves the reconstructed fields in the buffer of
   // the last step's output
-  h->fwd_buf = fused_reverse(h) ? (h->N & 1) : 0;
+  if (fused_reverse(h)) h->fwd_buf ^= h->N & 1;
   return FDTD_OK;
 }
 
@@ -2006,7 +2144,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
     if (e) return cuda_fail(h, "forward launch", e);
-    h->fwd_buf = 0;
+    h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
     // objective: per-step slots summed on the host in chunks
     double sum = 0.0, chunk[256];
     for (int n0 = 0; n0 < h->N; n0 += 256) {

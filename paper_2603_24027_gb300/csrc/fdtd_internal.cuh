@@ -223,6 +223,54 @@ template <> struct Code<8> : Soft8<3, 4, 3, true, 31, 2> {};       // e3m4 (IEEE
 constexpr int kTapeDtypes = 9;
 inline int code_bytes(int dt) { return dt == 0 ? 4 : (dt <= 2 ? 2 : 1); }
 
+// Units (32 x 8 tile, z chunk) of the staged kernels: ntx x nty tiles and nzc
+// chunks.  [px0, px1) x [py0, py1) x [pz0, pz1): the units holding interior
+// cells; [ix0, ix1) x [iy0, iy1) x [iz0, iz1): the units whose every cell
+// and every neighbour one cell away (x in [x0-1, x0+32], y in [y0-1, y0+8],
+// z in [k0-1, k1]) lies in the interior, i.e. without a CPML term.  The
+// other units split into z-only units (tiles inside [ix0, ix1) x [iy0, iy1),
+// chunks outside [iz0, iz1)) and ring units (every other tile, every chunk).
+struct RevUnits {
+  int ntx, nty, nzc;
+  int px0, px1, py0, py1, pz0, pz1;
+  int ix0, ix1, iy0, iy1, iz0, iz1;
+};
+
+// The chunk of z-only unit c (grid z index): below [iz0, iz1), then above.
+__host__ __device__ inline int zonly_chunk(const RevUnits& U, int c) {
+  return c < U.iz0 ? c : U.iz1 + (c - U.iz0);
+}
+
+__host__ __device__ inline long long ring_tiles(const RevUnits& U) {
+  return (long long)U.ntx * U.nty - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0);
+}
+
+// Ring unit u: chunk u / ring_tiles, then the tile: rows below [iy0, iy1),
+// rows above, then the left and right columns of the rows in between.
+__host__ __device__ inline void ring_unit(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
+  const long long ring = ring_tiles(U);
+  *cz = (int)(u / ring);
+  long long r = u % ring;
+  const long long below = (long long)U.ntx * U.iy0;
+  if (r < below) {
+    *ty = (int)(r / U.ntx);
+    *tx = (int)(r % U.ntx);
+    return;
+  }
+  r -= below;
+  const long long above = (long long)U.ntx * (U.nty - U.iy1);
+  if (r < above) {
+    *ty = U.iy1 + (int)(r / U.ntx);
+    *tx = (int)(r % U.ntx);
+    return;
+  }
+  r -= above;
+  const int w = U.ix0 + (U.ntx - U.ix1);
+  *ty = U.iy0 + (int)(r / w);
+  const int c = (int)(r % w);
+  *tx = c < U.ix0 ? c : U.ix1 + (c - U.ix0);
+}
+
 // ------------------------------------------------------------ launchers ----
 // Implemented in kernels_step.cu / kernels_tape.cu; return cudaGetLastError().
 struct StepArgs {
@@ -232,7 +280,8 @@ struct StepArgs {
   float* psiA;     // psi set read (and written in place by the forward)
   float* psiB;     // psi set written (ping-pong)
   float* L;        // adjoint fields (6 components, same layout as F)
-  float* Fn;       // fused reverse step: fields written (the other buffer of a ping-pong pair)
+  float* Fn;       // fused steps: fields written (the other buffer of a ping-pong pair);
+                   // the forward half-steps write here when set, else in place
   float* Ln;       // fused reverse step: adjoint fields written
   double* gacc;    // FP64 design-box accumulator [dz][dy][dx]
   int dlo[3], dhi[3];
@@ -243,6 +292,9 @@ struct StepArgs {
   int zchunk;
   int zc0, zc1;     // two-cells-per-thread kernels: z chunks [zc0, zc1) of this launch (zc1 = 0: to the last)
   int t0x, t0y;     // fused reverse step: first tile of a launch along x and y
+  int umode;        // forward half-steps (32 x 8 tiles): 0 every unit of the grid (offset
+                    // by zc0), 1 the z-only units of U, 2 the ring units of U
+  RevUnits U;
   int tile_y;
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
@@ -269,18 +321,22 @@ cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
 struct alignas(64) LagMaps {
   CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Qxo, Qxw, Qyo, Qyw, Qzo;
 };
+// Fwide (optional): the field buffer of the wide boxes Fw (the forward E
+// half-step of a fused forward reads Ht^{n+1/2} from the buffer being written).
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
-                            const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m);
+                            const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m,
+                            const float* Fwide = nullptr);
 // Staged half-steps, two x-cells per thread (kernel 5; tile height >= 2).
 // which: 0 forward H, 1 forward E, 2 reverse E phase, 3 reverse H phase.
 cudaError_t launch_lag2(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s);
-// The fused reverse step (kernels_rev_fused.cu): tensor maps of 32 x 8
-// tiles over the current field, adjoint and auxiliary buffers (boxes: F40 /
-// cb40 / L40 (TW+8) x (TY+2), F36 / cb36 / L36 (TW+4) x (TY+1), Qx40
+// The fused steps (kernels_rev_fused.cu, kernels_fwd_fused.cu): tensor maps
+// of 32 x 8 tiles over the current field, adjoint and auxiliary buffers
+// (boxes: F40 / cb40 / L40 (TW+8) x (TY+2), F36 / cb36 / L36 (TW+4) x
+// (TY+1), cb32 TW x TY, Qx40
 // (TW+8) x (TY+1), Qy36 (TW+4) x (TY+2), Qz36 (TW+4) x (TY+1), Qxw (TW+4) x
 // TY, Qyw TW x (TY+1), Qzo TW x TY).
 struct alignas(64) RevMaps {
-  CUtensorMap F40, F36, cb36, cb40, L40, L36, Qx40, Qy36, Qz36, Qxw, Qyw, Qzo;
+  CUtensorMap F40, F36, cb36, cb40, cb32, L40, L36, Qx40, Qy36, Qz36, Qxw, Qyw, Qzo;
 };
 cudaError_t encode_rev_maps(const float* F, const float* L, const float* cb, const float* psiA,
                             const Geo& g, const PsiLayout& pl, RevMaps* m);
@@ -290,11 +346,6 @@ cudaError_t encode_rev_maps(const float* F, const float* L, const float* cb, con
 // box [ix0, ix1) x [iy0, iy1) x [iz0, iz1) of units whose every evaluated
 // term lies in the interior; the adjoint one with CPML every other unit of
 // the ntx x nty x nzc grid.
-struct RevUnits {
-  int ntx, nty, nzc;
-  int px0, px1, py0, py1, pz0, pz1;
-  int ix0, ix1, iy0, iy1, iz0, iz1;
-};
 RevUnits rev_units(const Geo& g, int zchunk);
 // The CPML units split into z-only units (tiles inside [ix0, ix1) x
 // [iy0, iy1), chunks outside [iz0, iz1)) and ring units (every other tile,
@@ -306,6 +357,11 @@ long long rev_ring_tiles(const RevUnits& U);
 // units, 2 adjoint over the z-only units, 3 adjoint over the ring units.
 // Reads a.F, a.L, a.psiA; writes a.Fn, a.Ln, a.psiB, a.gacc.
 cudaError_t launch_rev_fused(int which, const RevMaps& m, const StepArgs& a, const RevUnits& U,
+                             cudaStream_t s);
+// The fused forward step (kernels_fwd_fused.cu) over the units [ix0, ix1) x
+// [iy0, iy1) x [iz0, iz1) of U (none may hold a source or detector cell):
+// reads a.F (E^n, Ht^{n-1/2}) and cb, writes a.Fn (E^{n+1}, Ht^{n+1/2}).
+cudaError_t launch_fwd_fused(const RevMaps& m, const StepArgs& a, const RevUnits& U,
                              cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,

@@ -22,8 +22,29 @@ namespace fdtd {
 
 using namespace lag2;
 
+// The unit (tile, z chunk) of this CTA of a forward half-step: every unit of
+// the grid (chunks offset by zc0), or, in the UM instantiations, the z-only
+// (umode 1) or ring (umode 2) units of a fused forward step, whose CPML-free
+// units run k_fwd_fused.
+template <bool UM>
+__device__ __forceinline__ void fwd_unit(const StepArgs& a, int* tix, int* tiy, int* cz) {
+  if (UM && a.umode == 2) {
+    ring_unit(a.U, blockIdx.x, tix, tiy, cz);
+  } else if (UM) {
+    *tix = blockIdx.x + a.U.ix0;
+    *tiy = blockIdx.y + a.U.iy0;
+    *cz = zonly_chunk(a.U, blockIdx.z);
+  } else {
+    *tix = blockIdx.x;
+    *tiy = blockIdx.y;
+    *cz = blockIdx.z + a.zc0;
+  }
+}
+
 // =================================================== forward H half-step ===
-template <int TY, int S, int TW, bool EX>
+// UM: a fused forward step's CPML units (unit decode by a.umode, Ht^{n+1/2}
+// written to a.Fn); else every unit, in place.
+template <int TY, int S, int TW, bool EX, bool UM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
 k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -31,10 +52,12 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  int tix, tiy, cz;
+  fwd_unit<UM>(a, &tix, &tiy, &cz);
+  const int x0 = tix * TW, y0 = tiy * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = cz * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane p < k1 starts Ht(p); plane p > k0 finishes Ht(p-1) (needs E(p))
@@ -66,7 +89,7 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
   const int hb = ty * B::W + 2 * tx;   // own pair in a hi box
   const int ob = ty * TW + 2 * tx;     // own pair in an own box
   const long long nc = g.nc;
-  float* const Hx = a.F + 3 * nc;
+  float* const Hx = (UM ? a.Fn : a.F) + 3 * nc;   // Ht^{n+1/2}: in place, or the other buffer
   float* const Hy = Hx + nc;
   float* const Hz = Hy + nc;
   float* const psi = a.psiA;
@@ -186,7 +209,9 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // =================================================== forward E half-step ===
-template <int TY, int S, int TW, bool EX>
+// UM: as in the H half-step (E^{n+1} written to a.Fn, Ht^{n+1/2} read from
+// the buffer the tensor map Fw views).
+template <int TY, int S, int TW, bool EX, bool UM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
 k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   typedef G<TY, TW> B;
@@ -194,10 +219,12 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  int tix, tiy, cz;
+  fwd_unit<UM>(a, &tix, &tiy, &cz);
+  const int x0 = tix * TW, y0 = tiy * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = cz * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   // plane k0-1 only provides Ht(k0-1) at the own pair
@@ -234,7 +261,7 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
   const int lb = (ty + 1) * B::W + 2 * tx + 4;   // own pair in a lo box
   const int ob = ty * TW + 2 * tx;
   const long long nc = g.nc;
-  float* const Ex = a.F;
+  float* const Ex = UM ? a.Fn : a.F;   // E^{n+1}: in place, or the other buffer
   float* const Ey = Ex + nc;
   float* const Ez = Ey + nc;
   float* const psi = a.psiA;
@@ -999,10 +1026,25 @@ static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
   const int zc1 = a.zc1 > 0 ? min(a.zc1, nch) : nch;
   if (a.zc0 < 0 || a.zc0 >= zc1) return cudaErrorInvalidValue;
   dim3 grid((a.g.nx + TW - 1) / TW, (a.g.ny + TY - 1) / TY, zc1 - a.zc0);
+  if (a.umode) {   // the forward half-steps over the CPML units of a fused forward step
+    if (which > 1 || TY != 8 || TW != 32 || a.U.nzc != nch) return cudaErrorInvalidValue;
+    const RevUnits& U = a.U;
+    grid = a.umode == 1 ? dim3(U.ix1 - U.ix0, U.iy1 - U.iy0, U.nzc - (U.iz1 - U.iz0))
+                        : dim3((unsigned)(ring_tiles(U) * U.nzc), 1, 1);
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+  }
   dim3 block(TW / 2, TY);
+  if constexpr (TY == 8 && TW == 32) {
+    if (a.umode) {
+      if (!a.Fn) return cudaErrorInvalidValue;
+      if (which == 0)
+        return launch_ex(k_l2fwd_h<TY, S, TW, EX, true>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+      return launch_ex(k_l2fwd_e<TY, S, TW, EX, true>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    }
+  }
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
-    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX, false>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX, false>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
     case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
     case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }

@@ -109,41 +109,9 @@ constexpr int adj_ctas() { return MODE == 2 ? 4 : (MODE == 1 ? 4 : 5); }
 
 // Tile and chunk of a unit.  Primal and CPML-free adjoint launches: a 3D
 // grid offset by (t0x, t0y, zc0).  z-only units (MODE 1): a 3D grid over the
-// tiles [ix0, ix1) x [iy0, iy1) and the chunks outside [iz0, iz1) (below,
-// then above).  Ring units (MODE 2): a 1D grid over every chunk times the
-// tiles outside [ix0, ix1) x [iy0, iy1) (rows below, rows above, then the
-// left and right columns of the rows in between).
-__host__ __device__ inline int zonly_chunk(const RevUnits& U, int c) {
-  return c < U.iz0 ? c : U.iz1 + (c - U.iz0);
-}
-
-__host__ __device__ inline long long ring_tiles(const RevUnits& U) {
-  return (long long)U.ntx * U.nty - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0);
-}
-
-__host__ __device__ inline void ring_unit(const RevUnits& U, long long u, int* tx, int* ty, int* cz) {
-  const long long ring = ring_tiles(U);
-  *cz = (int)(u / ring);
-  long long r = u % ring;
-  const long long below = (long long)U.ntx * U.iy0;
-  if (r < below) {
-    *ty = (int)(r / U.ntx);
-    *tx = (int)(r % U.ntx);
-    return;
-  }
-  r -= below;
-  const long long above = (long long)U.ntx * (U.nty - U.iy1);
-  if (r < above) {
-    *ty = U.iy1 + (int)(r / U.ntx);
-    *tx = (int)(r % U.ntx);
-    return;
-  }
-  r -= above;
-  const int w = U.ix0 + (U.ntx - U.ix1);
-  *ty = U.iy0 + (int)(r / w);
-  const int c = (int)(r % w);
-  *tx = c < U.ix0 ? c : U.ix1 + (c - U.ix0);
-}
+// tiles [ix0, ix1) x [iy0, iy1) and the chunks outside [iz0, iz1)
+// (zonly_chunk).  Ring units (MODE 2): a 1D grid over every chunk times the
+// ring tiles (ring_unit).
 
 }  // namespace revf
 
@@ -554,22 +522,22 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               n10x = adj(n10x, P[Y::EXP + xb + 2], b, aa, kk, &dummy);
             }
           }
-          if (zs) {
-            const float* P = reinterpret_cast<const float*>(st + Y::PEZ);   // (TW+4) x (TY+1) at (x0-4, y0-1)
-            const float b = prof(g, 2, PR_BE, p), aa = prof(g, 2, PR_AE, p), kv = prof(g, 2, PR_KE, p);
-            const float2 p0 = ld2(P, lb), p1 = ld2(P + Y::EZP, lb);
-            const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
-            float s7[2], s8[2];
+        }
+        if (zs) {   // z-only and ring units
+          const float* P = reinterpret_cast<const float*>(st + Y::PEZ);   // (TW+4) x (TY+1) at (x0-4, y0-1)
+          const float b = prof(g, 2, PR_BE, p), aa = prof(g, 2, PR_AE, p), kv = prof(g, 2, PR_KE, p);
+          const float2 p0 = ld2(P, lb), p1 = ld2(P + Y::EZP, lb);
+          const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
+          float s7[2], s8[2];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              o7[c] = adj(o7[c], q0[c], b, aa, kv, &s7[c]);
-              o8[c] = adj(o8[c], q1[c], b, aa, kv, &s8[c]);
-            }
-            if (!head && (v0 || v1)) {
-              const long long qz = psi_ix<2>(a.pl, 2, x, y, p);
-              ST2(lpB, qz, s7[0], s7[1], v0, v1);
-              ST2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], v0, v1);
-            }
+          for (int c = 0; c < 2; ++c) {
+            o7[c] = adj(o7[c], q0[c], b, aa, kv, &s7[c]);
+            o8[c] = adj(o8[c], q1[c], b, aa, kv, &s8[c]);
+          }
+          if (!head && (v0 || v1)) {
+            const long long qz = psi_ix<2>(a.pl, 2, x, y, p);
+            ST2(lpB, qz, s7[0], s7[1], v0, v1);
+            ST2(lpB + a.pl.ax[2].cs, qz, s8[0], s8[1], v0, v1);
           }
         }
         // cell 0's +x terms are cell 1's own terms

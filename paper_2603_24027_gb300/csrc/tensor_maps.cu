@@ -55,7 +55,8 @@ static cudaError_t enc_axis(CUtensorMap* m, const float* set, const PsiAxis& A, 
 }
 
 cudaError_t encode_lag_maps(const float* F, const float* Lm, const float* cb, const float* psiA,
-                            const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m) {
+                            const Geo& g, int ty, int tw, const PsiLayout& pl, LagMaps* m,
+                            const float* Fwide) {
   *m = LagMaps{};
   cudaError_t e;
   const int w = tw + 4;
@@ -64,7 +65,7 @@ cudaError_t encode_lag_maps(const float* F, const float* Lm, const float* cb, co
   if ((e = enc_axis(&m->Qyo, psiA, pl.ax[1], tw, ty))) return e;
   if ((e = enc_axis(&m->Qyw, psiA, pl.ax[1], tw, ty + 1))) return e;
   if ((e = enc_axis(&m->Qzo, psiA, pl.ax[2], tw, ty))) return e;
-  if ((e = enc3(&m->Fw, F, g, 6, w, ty + 1, 3))) return e;
+  if ((e = enc3(&m->Fw, Fwide ? Fwide : F, g, 6, w, ty + 1, 3))) return e;
   if ((e = enc3(&m->Fo, F, g, 6, tw, ty, 3))) return e;
   if ((e = enc3(&m->Lw, Lm, g, 6, w, ty + 1, 3))) return e;
   if ((e = enc3(&m->Lo, Lm, g, 6, tw, ty, 3))) return e;
@@ -82,6 +83,7 @@ cudaError_t encode_rev_maps(const float* F, const float* Lm, const float* cb, co
   if ((e = enc3(&m->F36, F, g, 6, tw + 4, ty + 1, 3))) return e;
   if ((e = enc3(&m->cb36, cb, g, 1, tw + 4, ty + 1, 1))) return e;
   if ((e = enc3(&m->cb40, cb, g, 1, tw + 8, ty + 2, 1))) return e;
+  if ((e = enc3(&m->cb32, cb, g, 1, tw, ty, 1))) return e;
   if ((e = enc3(&m->L40, Lm, g, 6, tw + 8, ty + 2, 3))) return e;
   if ((e = enc3(&m->L36, Lm, g, 6, tw + 4, ty + 1, 3))) return e;
   if ((e = enc_axis(&m->Qx40, psiA, pl.ax[0], tw + 8, ty + 1))) return e;

@@ -141,7 +141,7 @@ def test_options_are_validated(capi, fdtd):
                          (capi.OPT_PREFETCH, 0), (capi.OPT_COMPACT_AUX, 1),
                          (capi.OPT_EXACT_REVERSAL, 0), (capi.OPT_ZCHUNK_FWD, -1),
                          (capi.OPT_ZGROUPS, 0), (capi.OPT_REVERSE, 0),
-                         (capi.OPT_INJECT_WAIT_TIMEOUT, 0)]:
+                         (capi.OPT_INJECT_WAIT_TIMEOUT, 0), (capi.OPT_FORWARD, 0)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
                      (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_KERNEL, 4),
@@ -149,7 +149,8 @@ def test_options_are_validated(capi, fdtd):
                      (capi.OPT_ZCHUNK, -1), (capi.OPT_TILE_X, 0), (capi.OPT_TILE_X, 36),
                      (capi.OPT_ZCHUNK_FWD, -2), (capi.OPT_EXACT_REVERSAL, 5),
                      (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (capi.OPT_REVERSE, 3),
-                     (capi.OPT_REVERSE, -1), (99, 1)]:
+                     (capi.OPT_REVERSE, -1), (capi.OPT_FORWARD, 3), (capi.OPT_FORWARD, -1),
+                     (99, 1)]:
         assert lib.fdtd_set_option(sim.h, opt, val) == capi.FDTD_EINVAL
     assert lib.fdtd_set_option(sim.h, capi.OPT_STAGES, 4) == capi.FDTD_OK
     assert lib.fdtd_get_option(sim.h, capi.OPT_STAGES, C.byref(v)) == capi.FDTD_OK and v.value == 4
@@ -407,3 +408,33 @@ def test_automatic_reverse_follows_the_cpml_share(capi, fdtd):
         auto = sim.workspace_bytes(rec)
         sim.set_option(capi.OPT_REVERSE, 2 if fused else 1)
         assert sim.workspace_bytes(rec) == auto
+
+
+def test_fused_forward_workspace_and_automatic_choice(capi, fdtd):
+    """The fused forward step needs the second field buffer only (its
+    auxiliaries stay in place); FDTD_OPT_FORWARD = 0 takes it on the 600 x
+    600 x 300 grid (31 % of the units in the CPML, source and detector in the
+    ring) and not on the 200 x 200 x 100 one (70 %)."""
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    rec = capi.record_cfg("e4m3", 8)
+    w = I.waveguide_large(n_steps=10)
+    f6 = al(6 * w.nz * w.ny * ((w.nx + 7) // 8 * 8) * 4)
+    sim = fdtd.Simulation(w)
+    sim.set_option(capi.OPT_REVERSE, 1)
+    sim.set_option(capi.OPT_FORWARD, 1)
+    split = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_FORWARD, 2)
+    assert sim.workspace_bytes(rec) - split == f6
+    sim.set_option(capi.OPT_FORWARD, 0)
+    assert sim.workspace_bytes(rec) - split == f6
+    sim.set_option(capi.OPT_REVERSE, 2)
+    assert sim.workspace_bytes(rec) - split == 2 * f6   # the reverse adds the adjoint's pair
+    w = I.waveguide_mid()
+    sim = fdtd.Simulation(w)
+    sim.set_option(capi.OPT_REVERSE, 1)
+    sim.set_option(capi.OPT_FORWARD, 1)
+    split = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_FORWARD, 0)
+    assert sim.workspace_bytes(rec) == split

@@ -170,6 +170,11 @@ FUSED_GRIDS = {
     # left / right); 86 x 50 x 30 compacts all three auxiliary axes
     "interior_units": lambda: I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=70),
     "compact86": lambda: I.ragged_box(nx=86, ny=50, nz=30, P=7, n_steps=60),
+    # a point source next to the low z-CPML inside the z-only units and an
+    # |E|^2 detector nine cells above it: the z-CPML terms of the adjoint
+    # there carry a large share of the gradient
+    "zcpml_point": lambda: I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=120,
+                                        det_kind=I.OBJ_E2_PLANE, src_kind=I.SRC_POINT),
 }
 
 
@@ -218,6 +223,121 @@ def test_fused_reverse_step_with_exact_reversal_returns_to_zero(F, A):
     P = w.pml_thickness
     assert not np.any(bf[:, P:w.nz - P, P:w.ny - P, P:w.nx - P])
     same_gradient(gf, gs)
+
+
+def test_fused_reverse_step_with_z_cpml_units_matches_the_oracle(F, A):
+    """The fused reverse step against the exact discrete gradient where the
+    z-only units' CPML terms matter (a point source in them): every unit
+    variant of the adjoint must carry its CPML terms, and a missing one
+    leaves the gradient far off (and, over thousands of steps, unbounded)."""
+    w = FUSED_GRIDS["zcpml_point"]()
+    L, g = O.gradient(w)
+    Lf, gf, _ = run_both_ways(F, A, w, A.record_cfg("f32", 1), 2)
+    assert Lf == pytest.approx(L, rel=1e-5)
+    assert rel(gf, g) < 1e-4
+
+
+def test_fused_reverse_step_stays_bounded_over_many_steps(F, A):
+    """2000 steps on the grid above: the fused step's gradient stays within
+    rounding of the split phases' (an adjoint CPML term left out grows
+    without bound over such runs)."""
+    w = FUSED_GRIDS["zcpml_point"]().replace(n_steps=2000)
+    rec = A.record_cfg("e4m3", 8, "linear")
+    _, gs, _ = run_both_ways(F, A, w, rec, 1)
+    _, gf, _ = run_both_ways(F, A, w, rec, 2)
+    assert np.all(np.isfinite(gf))
+    assert rel(gf, gs) < 1e-5
+
+
+# ------------------------------------------------ the fused forward step --
+
+def run_forward_way(F, A, w, rec, forward, reverse, options=None):
+    """(L, fields after the forward, gradient, fields after the backward)."""
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_FORWARD, forward)
+    sim.set_option(A.OPT_REVERSE, reverse)
+    for k, v in (options or {}).items():
+        sim.set_option(k, v)
+    eps = torch.from_numpy(np.ascontiguousarray(w.eps)).cuda()
+    L = sim.forward(eps, rec)
+    fwd = sim.read_fields().cpu().numpy()
+    g = sim.backward(1.0).cpu().numpy()
+    back = sim.read_fields().cpu().numpy()
+    return L, fwd, g, back
+
+
+FWD_GRIDS = {
+    "interior_units": FUSED_GRIDS["interior_units"],
+    # a point source next to the low z-CPML; the Poynting detector (x = 17)
+    # and the source lie outside the CPML-free units, as the fused forward needs
+    "point_near_zcpml": lambda: I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=120,
+                                             src_kind=I.SRC_POINT),
+    # odd step count: the forward ends in the second buffer of the pair
+    "odd_steps": lambda: I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=71),
+    "compact_large": lambda: I.ragged_box(nx=200, ny=90, nz=56, P=8, n_steps=50),
+}
+
+
+@pytest.mark.parametrize("name", list(FWD_GRIDS))
+@pytest.mark.parametrize("tape", ["f32:1:linear", "bf16:4:cubic", "e4m3:2:linear"])
+@pytest.mark.parametrize("reverse", [1, 2])
+def test_fused_forward_step_matches_the_split_half_steps(F, A, name, tape, reverse):
+    """The fused forward step (CPML-free units in one launch, the others in
+    the split half-steps, all into the other buffer of a ping-pong pair)
+    against the split half-steps in place: the fields after the forward and
+    after the backward bit for bit (the same rounded operations per cell),
+    the objective to the FP64 sums' order, the gradient to the adjoint sums'
+    rounding; with both reverse modes, which start from the forward's buffer."""
+    w = FWD_GRIDS[name]()
+    dt, k, interp = tape.split(":")
+    rec = A.record_cfg(dt, int(k), interp)
+    Ls, fs, gs, bs = run_forward_way(F, A, w, rec, 1, reverse)
+    Lf, ff, gf, bf = run_forward_way(F, A, w, rec, 2, reverse)
+    assert np.abs(fs).max() > 0
+    np.testing.assert_array_equal(ff, fs)
+    assert Lf == pytest.approx(Ls, rel=1e-12)
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    np.testing.assert_array_equal(bf[inner], bs[inner])
+    same_gradient(gf, gs)
+
+
+@pytest.mark.parametrize("n_steps", [70, 71])
+def test_fused_forward_and_reverse_with_exact_reversal_return_to_zero(F, A, n_steps):
+    """Exact reversal with both fused steps: the interior returns to zero bit
+    for bit from either buffer of the pair, and the gradient (of the scheme
+    with increments on the 2^-22 grid) matches the split kernels' run of the
+    same scheme."""
+    w = FWD_GRIDS["point_near_zcpml"]().replace(n_steps=n_steps)
+    rec = A.record_cfg("f32", 1)
+    opts = {A.OPT_EXACT_REVERSAL: 22}
+    _, fwd, g, back = run_forward_way(F, A, w, rec, 2, 2, opts)
+    _, fs, gs, _ = run_forward_way(F, A, w, rec, 1, 1, opts)
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    assert np.abs(fwd[inner]).max() > 1e-3
+    np.testing.assert_array_equal(fwd, fs)
+    assert not np.any(back[inner])
+    same_gradient(g, gs)
+
+
+def test_fused_forward_needs_the_source_outside_its_units(F, A):
+    """A source inside the CPML-free units: FDTD_OPT_FORWARD = 2 is refused at
+    the forward, automatic (0) runs the split half-steps, and the gradient
+    matches the oracle."""
+    w = I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=120, src_kind=I.SRC_POINT)
+    w = w.replace(src_pos=(40, 30, 20))   # tile 1, chunk 2: a CPML-free unit
+    eps = torch.from_numpy(w.eps).cuda()
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_FORWARD, 2)
+    with pytest.raises(A.FdtdError) as e:
+        sim.forward(eps, A.record_cfg("f32", 1))
+    assert e.value.status == A.FDTD_EINVAL
+    sim.set_option(A.OPT_FORWARD, 0)
+    sim.forward(eps, A.record_cfg("f32", 1))
+    _, g = O.gradient(w)
+    assert np.abs(g).max() > 0
+    assert rel(sim.backward(1.0).cpu().numpy(), g) < 1e-4
 
 
 @pytest.mark.parametrize("reverse", [1, 2])
