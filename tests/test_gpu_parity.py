@@ -954,6 +954,40 @@ def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
     same_gradient(r["g"], r0["g"])
 
 
+def test_largest_grid_in_the_bench_configuration(F, A):
+    """600 x 600 x 300 cells, 10 000 steps, the E4M3 tape every 8th step: the
+    bench's line, with the library's default steps (fused forward and fused
+    reverse), against the split half-steps and phases.  The oracle cannot run
+    this grid, so properties that hold at any size stand in: forward fields
+    bit for bit, the objective to the FP64 sums' order, the gradient finite
+    and within 1e-5 of the split kernels' over a run long enough for an
+    adjoint term left out to grow without bound."""
+    w = I.waveguide_large(n_steps=10000)
+    rec = A.record_cfg("e4m3", 8, "linear")
+    Lf, ff, gf, _ = run_forward_way(F, A, w, rec, 0, 0)
+    torch.cuda.empty_cache()
+    Ls, fs, gs, _ = run_forward_way(F, A, w, rec, 1, 1)
+    torch.cuda.empty_cache()
+    assert np.abs(fs).max() > 0 and np.abs(gs).max() > 0
+    np.testing.assert_array_equal(ff, fs)
+    assert Lf == pytest.approx(Ls, rel=1e-12)
+    assert np.all(np.isfinite(gf))
+    assert rel(gf, gs) < 1e-5
+
+
+def test_largest_grid_exact_reversal_returns_to_zero(F, A):
+    """The same grid, 300 steps, exact reversal through the default steps:
+    the interior returns to the zero initial state bit for bit."""
+    w = I.waveguide_large(n_steps=300)
+    _, fwd, _, back = run_forward_way(F, A, w, A.record_cfg("f32", 1), 0, 0,
+                                      {A.OPT_EXACT_REVERSAL: 22})
+    torch.cuda.empty_cache()
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    assert np.abs(fwd[inner]).max() > 0
+    assert not np.any(back[inner])
+
+
 def test_reversal_drift_report_with_an_abruptly_switched_source(F, A):
     """Drift report, not parity: a source switched on at 0.3 tau (not the
     benchmark's pulse) drives content up to the grid's Nyquist limit, where
