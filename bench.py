@@ -32,6 +32,11 @@ reverse phase is the dominant one.  The per-kernel breakdown comes from a
 sampled pass with one launch per half-step on a shortened copy of the
 workload (same grid, same per-launch work).
 
+capacity: the workspace of one problem with this tape and with the
+comparison tape, and how many such problems fit side by side in the GPU's
+memory (where tape compression pays on one GPU: the FP32 tape of every step
+bounds the batch, not the speed).
+
 --profile-run: one short forward + backward for profilers (ncu launch lists,
 single-kernel captures) and launch-shape sweeps; prints the timings.
 
@@ -507,6 +512,11 @@ def run_ours(args):
         "tape_bytes": tape_bytes,
         "tape_reduction_vs_f32_k1": sim.tape_bytes(tape_cfg(A, "f32:1:linear")) / tape_bytes,
     }
+    # what the tape buys on one GPU: how many such problems fit side by side
+    dev_bytes = torch.cuda.get_device_properties(dev).total_memory
+    ws_bytes = sim.workspace_bytes(rec)
+    out["capacity"] = {"device_bytes": dev_bytes, "workspace_bytes": ws_bytes,
+                       "problems_per_gpu": dev_bytes // ws_bytes}
     nd = int(np.prod(w.design_shape))
     out["e2e"] = {"value": job_rate(ws, cell_updates, args.steps, total_wall), "unit": UNIT,
                   "h2d_bytes_per_step": w.n_cells * 4, "d2h_bytes_per_step": nd * 4 + 8}
@@ -530,6 +540,9 @@ def run_ours(args):
         v32 = cell_updates / (sum(ts) / len(ts) / 1e3) / 1e9
         e32 = cell_updates / (sum(tw) / len(tw)) / 1e9
         a64, b64 = g_main.double(), g32.double()
+        ws32 = sim32.workspace_bytes(rec32)
+        out["capacity"].update(compare_workspace_bytes=ws32,
+                               compare_problems_per_gpu=dev_bytes // ws32)
         out["compare"] = {"tape": args.compare_tape, "value": v32, "e2e": e32,
                           "tape_bytes": sim32.tape_bytes(rec32),
                           "tape_reduction": sim32.tape_bytes(rec32) / tape_bytes,
