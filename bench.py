@@ -43,7 +43,9 @@ single-kernel captures) and launch-shape sweeps; prints the timings.
 Other workloads: waveguide200 = 200 x 200 x 100 cells at 20 nm, 12-cell CPML,
 2000 steps; batched64 = 64 independent vacuum cubes of 32..128 cells with
 600..1500 steps each, run concurrently through the group calls (one step =
-one group forward + one group backward of all 64).
+one group forward + one group backward of all 64); the line also reports
+the same designs through the batched calls, one launch per half-step over
+all of them (one_launch_per_half_step).
 """
 from __future__ import annotations
 
@@ -719,6 +721,26 @@ def run_batched(args):
         te.append(time.perf_counter() - t0)
     assert all(np.isfinite(objs))
     e2e_t = max_over_ranks(sum(te), ws, dev)
+
+    # the same designs in one launch per half-step over all of them
+    # (fdtd_batch_forward / backward): measured beside the concurrent loops
+    def bstep():
+        fdtd.group_forward(sims, eps, rec, batched=True)
+        return fdtd.group_backward(sims, batched=True)
+
+    for _ in range(2):
+        bstep()
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(args.steps):
+        flush.random_(0, 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        bstep()
+        b.record()
+        torch.cuda.synchronize()
+        tb.append(a.elapsed_time(b))
+    batched_ms = max_over_ranks(sum(tb), ws, dev)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -740,6 +762,11 @@ def run_batched(args):
         "e2e": {"value": job_rate(ws, cell_updates, args.steps, e2e_t), "unit": UNIT,
                 "h2d_bytes_per_step": sum(w.n_cells * 4 for w in wl),
                 "d2h_bytes_per_step": sum(int(np.prod(w.design_shape)) * 4 + 8 for w in wl)},
+        "one_launch_per_half_step": {
+            "value": job_rate(ws, cell_updates, args.steps, batched_ms / 1e3), "unit": UNIT,
+            "ms_per_step": batched_ms / args.steps,
+            "launches_per_step": sims[0].last_timing()["fwd_launches"]
+            + sims[0].last_timing()["bwd_launches"]},
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

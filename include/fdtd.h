@@ -191,10 +191,34 @@ int fdtd_value_and_grad_host(fdtd_handle* h, const float* h_eps, const fdtd_reco
                              double seed, double* objective, float* h_grad);
 
 /* Batched designs: n independent handles (each with its own workspace)
- * processed together; objs[i] / d_grads[i] as in fdtd_forward/backward. */
+ * processed together; objs[i] / d_grads[i] as in fdtd_forward/backward.
+ * Each handle runs its own time loop (a CUDA graph on its own stream); all
+ * are enqueued before any is awaited, so they run concurrently. */
 int fdtd_group_forward(fdtd_handle* const* hs, int n, const float* const* d_eps,
                        const fdtd_record_cfg* rec, double* objs);
 int fdtd_group_backward(fdtd_handle* const* hs, int n, const double* seeds,
+                        float* const* d_grads);
+
+/* Batched designs in one launch per half-step: the same results as the
+ * group calls (fields and gradients equal to each handle's own run; the
+ * objectives to the order of their FP64 sums), but every forward half-step
+ * of every design runs as ONE launch over a list of (design, tile, z chunk)
+ * units, and likewise the record, the restore and the reverse phases, each
+ * CTA reading its design's own arguments and tensor maps from tables in
+ * device memory.  Designs are taken in descending order of step count: at
+ * forward step s (reverse iteration t) the designs with more than s (t)
+ * steps run, design d at its step s (N_d - 1 - t).  The loops are captured
+ * once into CUDA graphs; the plan (tables and graphs, allocated by the
+ * library with cudaMalloc, outside the time loops) belongs to hs[0] and is
+ * rebuilt when the list, a workspace or an option changes; it is freed with
+ * hs[0].  Every handle must run kernel 5's split steps (FDTD_OPT_FORWARD and
+ * FDTD_OPT_REVERSE resolving to 1) with 32 x 8 tiles and two stages, one
+ * detector, no exact reversal, and an unscaled tape format; else
+ * FDTD_EINVAL.  fdtd_batch_backward needs the handles' forwards to come
+ * from one fdtd_batch_forward (or with one record config). */
+int fdtd_batch_forward(fdtd_handle* const* hs, int n, const float* const* d_eps,
+                       const fdtd_record_cfg* rec, double* objs);
+int fdtd_batch_backward(fdtd_handle* const* hs, int n, const double* seeds,
                         float* const* d_grads);
 
 /* Last error message of h, or of the last failed fdtd_create when h is NULL. */

@@ -89,6 +89,10 @@ _PROTOS = {
                                      C.POINTER(RecordCfg), C.POINTER(C.c_double)]),
     "fdtd_group_backward": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_void_p)]),
+    "fdtd_batch_forward": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                     C.POINTER(RecordCfg), C.POINTER(C.c_double)]),
+    "fdtd_batch_backward": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_void_p)]),
     "fdtd_last_error": (C.c_char_p, [C.c_void_p]),
     "fdtd_destroy": (C.c_int, [C.c_void_p]),
     "fdtd_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),

@@ -60,6 +60,8 @@ struct GraphEntry {
   std::vector<SampleEntry> plan;   // intervals the graph's event nodes record
 };
 
+struct BatchPlan;
+
 struct fdtd_handle {
   int nx, ny, nz, px, P, N, nmax;
   double S, dx, dt;
@@ -112,8 +114,11 @@ struct fdtd_handle {
   float fwd_ms, bwd_ms;
   std::vector<double> obj_hist;
   double obj2_sum;            // second detector's objective of the last forward
+  BatchPlan* batch;           // batched-designs plan led by this handle (fdtd_batch_*)
   std::string err;
 };
+
+static void drop_batch(fdtd_handle* h);
 
 static const int kMaxZGroups = 16;
 static std::string g_create_error;
@@ -700,6 +705,7 @@ extern "C" int fdtd_destroy(fdtd_handle* h) {
     for (cudaEvent_t ev : h->zev) cudaEventDestroy(ev);
     for (cudaStream_t st : h->zs) cudaStreamDestroy(st);
     if (h->zfork) cudaEventDestroy(h->zfork);
+    drop_batch(h);
     cudaStreamDestroy(h->stream);
   }
   delete h;
@@ -1802,6 +1808,389 @@ extern "C" int fdtd_group_backward(fdtd_handle* const* hs, int n, const double* 
   }
   for (int i = 0; i < n; ++i) {
     int rc = backward_finish(hs[i], d_grads[i]);
+    if (rc) return rc;
+  }
+  return FDTD_OK;
+}
+
+// --------------------------------------------------- batched designs ----
+// fdtd_batch_forward / fdtd_batch_backward: the split half-steps of every
+// design run as one launch per half-step over a list of (design, tile x,
+// tile y, z chunk) units, and the record and restore of every design as one
+// launch per step; each CTA reads its design's own step arguments and tensor
+// maps from tables in device memory.  Designs are ordered by descending step
+// count, so the designs still running at a forward step, or at a reverse
+// iteration t (design d runs its step N_d - 1 - t), are a prefix of the list
+// and of the units.  The loops are captured once into two CUDA graphs; the
+// plan (tables, graphs, stream) belongs to the first handle of the list and
+// is rebuilt when the list, a workspace, an option or the record config
+// changes.  The per-cell arithmetic is the split kernels', so fields and
+// gradients equal those of the same designs run one by one.
+struct BatchPlan {
+  std::vector<size_t> sig;            // what the tables and graphs were built for
+  char* dev = nullptr;                // device tables (owned)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int launches[2] = {0, 0};
+};
+
+static void drop_batch(fdtd_handle* h) {
+  BatchPlan* b = h->batch;
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& x : b->exec)
+    if (x) cudaGraphExecDestroy(x);
+  if (b->dev) cudaFree(b->dev);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  h->batch = nullptr;
+}
+
+// The batched path runs the split half-steps and phases of kernel 5 with
+// 32 x 8 tiles and two stages, one detector, no exact reversal, and an
+// unscaled tape format (one thread per recorded value).
+static int batch_check(fdtd_handle* const* hs, int n, const fdtd_record_cfg* rec) {
+  if (!hs || n < 1 || !rec) return FDTD_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    fdtd_handle* h = hs[i];
+    if (!h) return FDTD_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return fail(h, FDTD_EINVAL, "a handle appears twice in the batch");
+    int rc = check_rec(h, rec);
+    if (rc) return rc;
+    if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
+    if (layout_of(h, rec).total > h->ws_bytes)
+      return fail(h, FDTD_ENOMEM, "workspace too small for this record config");
+    if (h->opt_kernel != 5 || fused_forward(h) || fused_reverse(h) || lag_tile_y(h) != 8 ||
+        lag_tile_x(h) != 32 || h->opt_stages != 2 || h->opt_exact || h->det2.kind ||
+        h->opt_inject_wait)
+      return fail(h, FDTD_EINVAL,
+                  "batched designs run kernel 5's split steps with 32 x 8 tiles, two stages, "
+                  "one detector and no exact reversal");
+  }
+  if (rec->dtype == kTapeBdct || (rec->scaled && rec->dtype >= 2))
+    return fail(hs[0], FDTD_EINVAL, "batched designs record unscaled tape formats only");
+  return FDTD_OK;
+}
+
+static std::vector<size_t> batch_signature(fdtd_handle* const* hs, int n,
+                                           const fdtd_record_cfg* rec) {
+  std::vector<size_t> s = {(size_t)n, (size_t)rec->dtype, (size_t)rec->k, (size_t)rec->interp,
+                           (size_t)rec->scaled, (size_t)rec->coeffs};
+  for (int i = 0; i < n; ++i) {
+    const fdtd_handle* h = hs[i];
+    const size_t v[] = {(size_t)h, (size_t)h->ws, h->ws_bytes, (size_t)h->nx, (size_t)h->ny,
+                        (size_t)h->nz, (size_t)h->P, (size_t)h->N, (size_t)h->opt_zchunk,
+                        (size_t)(h->opt_zchunk_fwd + 1), (size_t)h->opt_zgroups,
+                        (size_t)h->opt_compact, (size_t)h->opt_graphs};
+    s.insert(s.end(), v, v + sizeof v / sizeof v[0]);
+  }
+  return s;
+}
+
+// Device copy of a host table at an aligned offset of the plan's memory.
+template <class T>
+static size_t batch_put(std::vector<std::pair<size_t, std::vector<char>>>& parts, size_t& off,
+                        const std::vector<T>& v) {
+  const size_t at = off;
+  std::vector<char> bytes(v.size() * sizeof(T));
+  if (!v.empty()) memcpy(bytes.data(), v.data(), bytes.size());
+  off = al(off + bytes.size());
+  parts.emplace_back(at, std::move(bytes));
+  return at;
+}
+
+// Build, or reuse, the plan of this batch: the tables and the two captured loops.
+static int batch_plan(fdtd_handle* const* hs, int n, const fdtd_record_cfg* rec,
+                      BatchPlan** out) {
+  fdtd_handle* h0 = hs[0];
+  std::vector<size_t> sig = batch_signature(hs, n, rec);
+  if (h0->batch && h0->batch->sig == sig) {
+    *out = h0->batch;
+    return FDTD_OK;
+  }
+  drop_batch(h0);
+  int rc = ensure_cuda(h0);
+  if (rc) return rc;
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hs[a]->N > hs[b]->N; });
+  const int maxN = hs[ord[0]]->N;
+  auto active = [&](int s) {   // designs with more than s steps: a prefix of ord
+    int c = 0;
+    while (c < n && hs[ord[c]]->N > s) ++c;
+    return c;
+  };
+  std::vector<LagMaps> maps(3 * (size_t)n);   // [d] forward; [n + 2d + b] reverse, aux set b
+  std::vector<int4> uf, ur;
+  std::vector<int> cf(n + 1, 0), cr(n + 1, 0);
+  std::vector<StepArgs> bf(n), br(n);
+  int rec_blocks = 0, res_blocks = 0;
+  for (int d = 0; d < n; ++d) {
+    fdtd_handle* h = hs[ord[d]];
+    const Layout L = layout_of(h, rec);
+    float* F0 = (float*)(h->ws + L.F[0]);
+    float* L0 = (float*)(h->ws + L.L[0]);
+    const float* cbp = (const float*)(h->ws + L.cb);
+    StepArgs a = step_args(h, L);
+    a.pl = L.plF;
+    a.zchunk = forward_zchunk(h, a);
+    a.F = F0;
+    a.psiA = (float*)(h->ws + L.psiF[0]);
+    a.bmap = d;
+    CK(h0, encode_lag_maps(F0, F0, cbp, a.psiA, a.g, 8, 32, L.plF, &maps[d]));
+    const int ntx = (h->nx + 31) / 32, nty = (h->ny + 7) / 8;
+    for (int z = 0; z < (h->nz + a.zchunk - 1) / a.zchunk; ++z)
+      for (int y = 0; y < nty; ++y)
+        for (int x = 0; x < ntx; ++x) uf.push_back(make_int4(d, x, y, z));
+    cf[d + 1] = (int)uf.size();
+    bf[d] = a;
+    StepArgs b = step_args(h, L);
+    b.pl = L.plL;
+    b.F = F0;
+    b.L = L0;
+    for (int k = 0; k < 2; ++k)
+      CK(h0, encode_lag_maps(F0, L0, cbp, (const float*)(h->ws + L.psiL[k]), b.g, 8, 32, L.plL,
+                             &maps[n + 2 * d + k]));
+    for (int z = 0; z < (h->nz + b.zchunk - 1) / b.zchunk; ++z)
+      for (int y = 0; y < nty; ++y)
+        for (int x = 0; x < ntx; ++x) ur.push_back(make_int4(d, x, y, z));
+    cr[d + 1] = (int)ur.size();
+    br[d] = b;
+    rec_blocks = std::max(rec_blocks, record_flat_blocks(h->faces));
+    int fb, db;
+    restore_blocks(h->faces, b.det, det2_of(h), &fb, &db);
+    res_blocks = std::max(res_blocks, fb + db);
+  }
+  // per step: every running design's own arguments; record and restore jobs
+  std::vector<StepArgs> af((size_t)maxN * n), ar((size_t)maxN * n);
+  memset(af.data(), 0, af.size() * sizeof(StepArgs));
+  memset(ar.data(), 0, ar.size() * sizeof(StepArgs));
+  std::vector<RecordJob> rj;
+  std::vector<int> roff(maxN + 1, 0);
+  std::vector<RestoreJob> sj((size_t)maxN * n);
+  memset(sj.data(), 0, sj.size() * sizeof(RestoreJob));
+  const int eb = code_bytes(rec->dtype);
+  for (int s = 0; s < maxN; ++s) {
+    const int A = active(s);
+    for (int d = 0; d < A; ++d) {
+      fdtd_handle* h = hs[ord[d]];
+      const Layout L = layout_of(h, rec);
+      StepArgs a = bf[d];
+      a.jn = h->wave[s];
+      a.obj = (double*)(h->ws + L.obj) + s;
+      af[(size_t)s * n + d] = a;
+      const int r = (h->N - 1) % rec->k;
+      if (s >= r && (s - r) % rec->k == 0) {
+        const int j = (s - r) / rec->k;
+        RecordJob J;
+        memset(&J, 0, sizeof J);
+        J.FH = J.FE = a.F;
+        J.g = a.g;
+        J.fc = h->faces;
+        J.sample = h->ws + L.tape + (size_t)j * L.stride * eb;
+        J.scale_slot = (float*)(h->ws + L.scales) + (size_t)j * 6;
+        rj.push_back(J);
+      }
+      // reverse iteration s: design d runs its step N_d - 1 - s
+      const int nd = h->N - 1 - s, cur = s & 1;
+      StepArgs b = br[d];
+      b.jn = h->wave[nd];
+      b.psiA = (float*)(h->ws + L.psiL[cur]);
+      b.psiB = (float*)(h->ws + L.psiL[cur ^ 1]);
+      b.bmap = n + 2 * d + cur;
+      ar[(size_t)s * n + d] = b;
+      RestoreJob& R = sj[(size_t)s * n + d];
+      R.F = b.F;
+      R.L = b.L;
+      R.g = b.g;
+      R.fc = h->faces;
+      R.tape = h->ws + L.tape;
+      R.stride = L.stride;
+      R.scales = (const float*)(h->ws + L.scales);
+      interp_weights(h, rec, nd, 0, R.ip.slot[0], R.ip.w[0]);
+      interp_weights(h, rec, nd, 1, R.ip.slot[1], R.ip.w[1]);
+      R.det = b.det;
+      R.det2 = det2_of(h);
+      R.seeds = (const double*)(h->ws + L.seeds);
+      restore_blocks(R.fc, R.det, R.det2, &R.face_blocks, &R.det_blocks);
+    }
+    roff[s + 1] = (int)rj.size();
+  }
+  // one device allocation for the tables (once per plan, outside the loops)
+  std::vector<std::pair<size_t, std::vector<char>>> parts;
+  size_t off = 0;
+  const size_t o_maps = batch_put(parts, off, maps), o_uf = batch_put(parts, off, uf);
+  const size_t o_ur = batch_put(parts, off, ur), o_af = batch_put(parts, off, af);
+  const size_t o_ar = batch_put(parts, off, ar), o_rj = batch_put(parts, off, rj);
+  const size_t o_sj = batch_put(parts, off, sj);
+  BatchPlan* B = new (std::nothrow) BatchPlan();
+  if (!B) return fail(h0, FDTD_ENOMEM, "batch plan");
+  h0->batch = B;
+  if (cudaMalloc(&B->dev, off) != cudaSuccess) {
+    drop_batch(h0);
+    return fail(h0, FDTD_ENOMEM, "no device memory for the batch tables");
+  }
+  for (auto& p : parts)
+    if (!p.second.empty())
+      CK(h0, cudaMemcpy(B->dev + p.first, p.second.data(), p.second.size(), cudaMemcpyHostToDevice));
+  CK(h0, cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
+  CK(h0, cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
+  StepArgs la;   // the launch's own arguments: the lists of this launch
+  memset(&la, 0, sizeof la);
+  la.tile_y = 8;
+  la.tile_x = 32;
+  la.stages = 2;
+  la.bmaps = (const LagMaps*)(B->dev + o_maps);
+  LagMaps none;
+  memset(&none, 0, sizeof none);
+  const int dtype = rec->dtype;
+  for (int dir = 0; dir < 2; ++dir) {
+    CK(h0, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int nl = 0;
+    for (int s = 0; s < maxN && !e; ++s) {
+      const int A = active(s);
+      if (dir == 0) {
+        la.bunits = (const int4*)(B->dev + o_uf);
+        la.bargs = (const StepArgs*)(B->dev + o_af) + (size_t)s * n;
+        la.bcount = cf[A];
+        e = launch_lag2(0, none, la, B->stream);
+        if (!e && roff[s + 1] > roff[s]) {
+          e = launch_record_batch(dtype, (const RecordJob*)(B->dev + o_rj) + roff[s],
+                                  roff[s + 1] - roff[s], rec_blocks, B->stream);
+          ++nl;
+        }
+        if (!e) e = launch_lag2(1, none, la, B->stream);
+      } else {
+        e = launch_restore_seed_batch(dtype, (const RestoreJob*)(B->dev + o_sj) + (size_t)s * n, A,
+                                      res_blocks, B->stream);
+        la.bunits = (const int4*)(B->dev + o_ur);
+        la.bargs = (const StepArgs*)(B->dev + o_ar) + (size_t)s * n;
+        la.bcount = cr[A];
+        if (!e) e = launch_lag2(2, none, la, B->stream);
+        if (!e) e = launch_lag2(3, none, la, B->stream);
+        ++nl;
+      }
+      nl += 2;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(B->stream, &graph);
+    if (e || e2) {
+      if (graph) cudaGraphDestroy(graph);
+      drop_batch(h0);
+      return cuda_fail(h0, "batched loop capture", e ? e : e2);
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&B->exec[dir], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3) {
+      drop_batch(h0);
+      return cuda_fail(h0, "batched loop instantiate", e3);
+    }
+    B->launches[dir] = nl;
+  }
+  B->sig = sig;
+  *out = B;
+  return FDTD_OK;
+}
+
+// The batched loop of direction dir (0 forward, 1 backward) after every
+// design's own launches, each design's stream after it.
+static int batch_run(fdtd_handle* const* hs, int n, BatchPlan* B, int dir) {
+  for (int i = 0; i < n; ++i) {
+    CK(hs[i], cudaEventRecord(hs[i]->ev_out, hs[i]->stream));
+    CK(hs[i], cudaStreamWaitEvent(B->stream, hs[i]->ev_out, 0));
+  }
+  for (int i = 0; i < n; ++i) CK(hs[i], cudaEventRecord(dir ? hs[i]->t2 : hs[i]->t0, B->stream));
+  CK(hs[0], cudaGraphLaunch(B->exec[dir], B->stream));
+  for (int i = 0; i < n; ++i) CK(hs[i], cudaEventRecord(dir ? hs[i]->t3 : hs[i]->t1, B->stream));
+  CK(hs[0], cudaEventRecord(B->ev, B->stream));
+  for (int i = 0; i < n; ++i) CK(hs[i], cudaStreamWaitEvent(hs[i]->stream, B->ev, 0));
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_batch_forward(fdtd_handle* const* hs, int n, const float* const* d_eps,
+                                  const fdtd_record_cfg* rec, double* objs) {
+  if (!hs || n < 1 || !d_eps || !rec || !objs) return FDTD_EINVAL;
+  int rc = batch_check(hs, n, rec);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (!d_eps[i]) return fail(hs[i], FDTD_EINVAL, "eps is NULL");
+    rc = check_kernel_options(hs[i]);
+    if (rc) return rc;
+  }
+  BatchPlan* B = nullptr;
+  rc = batch_plan(hs, n, rec, &B);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {   // each design's own start, on its stream
+    fdtd_handle* h = hs[i];
+    rc = begin(h);
+    if (rc) return rc;
+    h->have_forward = false;
+    const Layout L = layout_of(h, rec);
+    const Geo g = geo_of(h);
+    CK(h, cudaMemsetAsync(h->ws + L.err, 0, 256, h->stream));
+    CK(h, launch_prep(d_eps[i], (float*)(h->ws + L.cb), g, (unsigned*)(h->ws + L.err), h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.F[0], 0, 6 * (size_t)g.nc * sizeof(float), h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.psiF[0], 0, (size_t)L.plF.total * sizeof(float), h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.obj, 0, h->N * sizeof(double), h->stream));
+  }
+  rc = batch_run(hs, n, B, 0);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    hs[i]->launches_fwd = B->launches[0];
+    hs[i]->fwd_buf = 0;
+    hs[i]->fwd_rec = *rec;
+  }
+  for (int i = 0; i < n; ++i) {
+    rc = forward_finish(hs[i], &objs[i]);
+    if (rc) return rc;
+  }
+  return FDTD_OK;
+}
+
+extern "C" int fdtd_batch_backward(fdtd_handle* const* hs, int n, const double* seeds,
+                                   float* const* d_grads) {
+  if (!hs || n < 1 || !seeds || !d_grads || !hs[0]) return FDTD_EINVAL;
+  const fdtd_record_cfg rec = hs[0]->fwd_rec;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return FDTD_EINVAL;
+    if (!hs[i]->have_forward)
+      return fail(hs[i], FDTD_ESTATE, "backward needs a preceding forward");
+    if (memcmp(&hs[i]->fwd_rec, &rec, sizeof rec))
+      return fail(hs[i], FDTD_EINVAL, "the batch's forwards used different record configs");
+    if (!d_grads[i]) return fail(hs[i], FDTD_EINVAL, "gradient buffer is NULL");
+  }
+  int rc = batch_check(hs, n, &rec);
+  if (rc) return rc;
+  BatchPlan* B = nullptr;
+  rc = batch_plan(hs, n, &rec, &B);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    fdtd_handle* h = hs[i];
+    rc = begin(h);
+    if (rc) return rc;
+    const Layout L = layout_of(h, &rec);
+    const size_t nc6 = 6 * (size_t)h->nz * h->ny * h->px * sizeof(float);
+    const size_t psb = (size_t)L.plL.total * sizeof(float);
+    const size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) *
+                      (h->dhi[2] - h->dlo[2]);
+    CK(h, upload_seeds(h, L, seeds[i], 0.0, h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.L[0], 0, nc6, h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.psiL[0], 0, psb, h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.psiL[1], 0, psb, h->stream));
+    CK(h, cudaMemsetAsync(h->ws + L.gacc, 0, nd * sizeof(double), h->stream));
+  }
+  rc = batch_run(hs, n, B, 1);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    hs[i]->launches_bwd = B->launches[1];
+    hs[i]->have_forward = false;
+  }
+  for (int i = 0; i < n; ++i) {
+    rc = backward_finish(hs[i], d_grads[i]);
     if (rc) return rc;
   }
   return FDTD_OK;

@@ -273,6 +273,13 @@ __host__ __device__ inline void ring_unit(const RevUnits& U, long long u, int* t
 
 // ------------------------------------------------------------ launchers ----
 // Implemented in kernels_step.cu / kernels_tape.cu; return cudaGetLastError().
+// Tensor maps of the plane-staging kernels for a tw x ty tile: wide
+// (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes;
+// Q* view the per-axis auxiliary arrays of `pl` (4 components each): x own
+// and (tw+4) x ty boxes, y own and tw x (ty+1) boxes, z own boxes.
+struct alignas(64) LagMaps {
+  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Qxo, Qxw, Qyo, Qyw, Qzo;
+};
 struct StepArgs {
   Geo g;
   float* F;        // fields
@@ -295,6 +302,14 @@ struct StepArgs {
   int umode;        // forward half-steps (32 x 8 tiles): 0 every unit of the grid (offset
                     // by zc0), 1 the z-only units of U, 2 the ring units of U
   RevUnits U;
+  // batched designs (the BM kernel instantiations): CTA b runs unit bunits[b]
+  // = (design, tile x, tile y, z chunk) of design bargs[design] (that
+  // design's own arguments for this step) with the tensor maps bmaps[bmap]
+  const int4* bunits;
+  const StepArgs* bargs;
+  const LagMaps* bmaps;
+  int bmap;
+  int bcount;       // units of a batched launch (its CTAs)
   int tile_y;
   int stages;      // ring stages of the one-plane kernels (2, 3 or 4)
   int pdl;         // launch the two-cells-per-thread kernels as programmatic dependents
@@ -314,13 +329,6 @@ cudaError_t launch_fwd_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_e(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_rev_h(const StepArgs& a, cudaStream_t s);
 
-// Tensor maps of the plane-staging kernels for a tw x ty tile: wide
-// (tw+4) x (ty+1) boxes (own and one neighbour side), own tw x ty boxes;
-// Q* view the per-axis auxiliary arrays of `pl` (4 components each): x own
-// and (tw+4) x ty boxes, y own and tw x (ty+1) boxes, z own boxes.
-struct alignas(64) LagMaps {
-  CUtensorMap Fw, Fo, Lw, Lo, cbw, cbo, Qxo, Qxw, Qyo, Qyw, Qzo;
-};
 // Fwide (optional): the field buffer of the wide boxes Fw (the forward E
 // half-step of a fused forward reads Ht^{n+1/2} from the buffer being written).
 cudaError_t encode_lag_maps(const float* F, const float* L, const float* cb, const float* psiA,
@@ -379,6 +387,36 @@ cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Face
                                 const void* tape, long long sample_stride, const float* scales,
                                 const Interp& ip, const Det& det, const Det& det2,
                                 const double* seeds, cudaStream_t s);
+// Batched designs: the record (unscaled formats) and restore launches of
+// several designs in one launch, one job per design (lists in device memory).
+struct RecordJob {
+  const float* FH;
+  const float* FE;
+  Geo g;
+  Faces fc;
+  void* sample;
+  float* scale_slot;
+};
+struct RestoreJob {
+  float* F;
+  float* L;
+  Geo g;
+  Faces fc;
+  const void* tape;
+  long long stride;
+  const float* scales;
+  Interp ip;
+  Det det, det2;
+  const double* seeds;
+  int face_blocks, det_blocks;
+};
+cudaError_t launch_record_batch(int dtype, const RecordJob* jobs, int njobs, int max_blocks,
+                                cudaStream_t s);
+cudaError_t launch_restore_seed_batch(int dtype, const RestoreJob* jobs, int njobs,
+                                      int max_blocks, cudaStream_t s);
+void restore_blocks(const Faces& fc, const Det& det, const Det& det2, int* face_blocks,
+                    int* det_blocks);
+int record_flat_blocks(const Faces& fc);
 cudaError_t launch_encode(int dtype, int scaled, const float* in, size_t n, void* code,
                           float* scale, cudaStream_t s);
 cudaError_t launch_decode(int dtype, const void* code, size_t n, const float* scale, float* out,

@@ -22,13 +22,35 @@ namespace fdtd {
 
 using namespace lag2;
 
+// Batched designs (BM): this CTA's unit (design, tile x, tile y, chunk), and
+// the design's own step arguments and tensor maps in global memory; else the
+// launch's own.
+template <bool BM>
+__device__ __forceinline__ int4 batch_unit(const StepArgs& a_) {
+  return BM ? a_.bunits[blockIdx.x] : make_int4(0, 0, 0, 0);
+}
+
+// Batched designs: the thread that issues the CTA's copies acquires the
+// design's tensor maps (in global memory) before its first copy.
+template <bool BM>
+__device__ __forceinline__ void batch_maps_acquire(const LagMaps& m) {
+  if (BM && threadIdx.x == 0 && threadIdx.y == 0) {
+    const CUtensorMap* t = &m.Fw;
+    for (int i = 0; i < (int)(sizeof(LagMaps) / sizeof(CUtensorMap)); ++i) tensormap_acquire(t + i);
+  }
+}
+
 // The unit (tile, z chunk) of this CTA of a forward half-step: every unit of
 // the grid (chunks offset by zc0), or, in the UM instantiations, the z-only
 // (umode 1) or ring (umode 2) units of a fused forward step, whose CPML-free
 // units run k_fwd_fused.
-template <bool UM>
-__device__ __forceinline__ void fwd_unit(const StepArgs& a, int* tix, int* tiy, int* cz) {
-  if (UM && a.umode == 2) {
+template <bool UM, bool BM>
+__device__ __forceinline__ void fwd_unit(const StepArgs& a, int4 bu, int* tix, int* tiy, int* cz) {
+  if (BM) {
+    *tix = bu.y;
+    *tiy = bu.z;
+    *cz = bu.w;
+  } else if (UM && a.umode == 2) {
     ring_unit(a.U, blockIdx.x, tix, tiy, cz);
   } else if (UM) {
     *tix = blockIdx.x + a.U.ix0;
@@ -44,16 +66,20 @@ __device__ __forceinline__ void fwd_unit(const StepArgs& a, int* tix, int* tiy, 
 // =================================================== forward H half-step ===
 // UM: a fused forward step's CPML units (unit decode by a.umode, Ht^{n+1/2}
 // written to a.Fn); else every unit, in place.
-template <int TY, int S, int TW, bool EX, bool UM>
+template <int TY, int S, int TW, bool EX, bool UM, bool BM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
-k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
+k_l2fwd_h(const __grid_constant__ LagMaps m_, StepArgs a_) {
+  const int4 bu = batch_unit<BM>(a_);
+  const StepArgs& a = BM ? a_.bargs[bu.x] : a_;
+  const LagMaps& m = BM ? a_.bmaps[a.bmap] : m_;
+  batch_maps_acquire<BM>(m);
   typedef G<TY, TW> B;
   typedef LFH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
   int tix, tiy, cz;
-  fwd_unit<UM>(a, &tix, &tiy, &cz);
+  fwd_unit<UM, BM>(a, bu, &tix, &tiy, &cz);
   const int x0 = tix * TW, y0 = tiy * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
@@ -211,16 +237,20 @@ k_l2fwd_h(const __grid_constant__ LagMaps m, StepArgs a) {
 // =================================================== forward E half-step ===
 // UM: as in the H half-step (E^{n+1} written to a.Fn, Ht^{n+1/2} read from
 // the buffer the tensor map Fw views).
-template <int TY, int S, int TW, bool EX, bool UM>
+template <int TY, int S, int TW, bool EX, bool UM, bool BM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(true)))
-k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
+k_l2fwd_e(const __grid_constant__ LagMaps m_, StepArgs a_) {
+  const int4 bu = batch_unit<BM>(a_);
+  const StepArgs& a = BM ? a_.bargs[bu.x] : a_;
+  const LagMaps& m = BM ? a_.bmaps[a.bmap] : m_;
+  batch_maps_acquire<BM>(m);
   typedef G<TY, TW> B;
   typedef LFE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
   int tix, tiy, cz;
-  fwd_unit<UM>(a, &tix, &tiy, &cz);
+  fwd_unit<UM, BM>(a, bu, &tix, &tiy, &cz);
   const int x0 = tix * TW, y0 = tiy * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
@@ -426,18 +456,22 @@ k_l2fwd_e(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // ======================================== reverse E phase (+ adjoint H) ===
-template <int TY, int S, int TW, bool EX>
+template <int TY, int S, int TW, bool EX, bool BM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
+k_l2rev_e(const __grid_constant__ LagMaps m_, StepArgs a_) {
+  const int4 bu = batch_unit<BM>(a_);
+  const StepArgs& a = BM ? a_.bargs[bu.x] : a_;
+  const LagMaps& m = BM ? a_.bmaps[a.bmap] : m_;
+  batch_maps_acquire<BM>(m);
   typedef G<TY, TW> B;
   typedef LRE<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x0 = (BM ? bu.y : (int)blockIdx.x) * TW, y0 = (BM ? bu.z : (int)blockIdx.y) * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (BM ? bu.w : (int)blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(x0, min(x0 + TW, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(y0, min(y0 + TY, g.ny - 1), g.ny, g.P);
   const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
@@ -742,18 +776,22 @@ k_l2rev_e(const __grid_constant__ LagMaps m, StepArgs a) {
 }
 
 // ======================================== reverse H phase (+ adjoint E) ===
-template <int TY, int S, int TW, bool EX>
+template <int TY, int S, int TW, bool EX, bool BM>
 __global__ void __launch_bounds__(TW / 2 * TY, (min_ctas<TY, S, TW>(false)))
-k_l2rev_h(const __grid_constant__ LagMaps m, StepArgs a) {
+k_l2rev_h(const __grid_constant__ LagMaps m_, StepArgs a_) {
+  const int4 bu = batch_unit<BM>(a_);
+  const StepArgs& a = BM ? a_.bargs[bu.x] : a_;
+  const LagMaps& m = BM ? a_.bmaps[a.bmap] : m_;
+  batch_maps_acquire<BM>(m);
   typedef G<TY, TW> B;
   typedef LRH<TY, S, TW> Y;
   extern __shared__ __align__(128) unsigned char dsm[];
   const Geo& g = a.g;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * (TW / 2) + tx;
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TY;
+  const int x0 = (BM ? bu.y : (int)blockIdx.x) * TW, y0 = (BM ? bu.z : (int)blockIdx.y) * TY;
   const int x = x0 + 2 * tx, y = y0 + ty;
   const bool v0 = x < g.nx && y < g.ny, v1 = v0 && x + 1 < g.nx;
-  const int k0 = (blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
+  const int k0 = (BM ? bu.w : (int)blockIdx.z + a.zc0) * a.zchunk, k1 = min(g.nz, k0 + a.zchunk);
   const bool txs = tile_in_slab(max(x0 - 1, 0), min(x0 + TW - 1, g.nx - 1), g.nx, g.P);
   const bool tys = tile_in_slab(max(y0 - 1, 0), min(y0 + TY - 1, g.ny - 1), g.ny, g.P);
   const bool tint = x0 + TW - 1 >= g.P && x0 < g.nx - g.P && y0 + TY - 1 >= g.P && y0 < g.ny - g.P;
@@ -1022,6 +1060,20 @@ static cudaError_t launch_ex(KT kernel, dim3 grid, dim3 block, int smem, cudaStr
 template <int TY, int S, int TW = 32, bool EX = false>
 static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a, cudaStream_t s) {
   static_assert((TW / 2 * TY) % 32 == 0, "a CTA is a whole number of warps");
+  if constexpr (TY == 8 && TW == 32 && S == 2 && !EX) {
+    if (a.bunits) {   // batched designs: one CTA per listed unit
+      if (a.bcount <= 0) return cudaSuccess;
+      const dim3 bg((unsigned)a.bcount, 1, 1), blk(TW / 2, TY);
+      switch (which) {
+        case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX, false, true>, bg, blk, LFH<TY, S, TW>::smem(), s, m, a);
+        case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX, false, true>, bg, blk, LFE<TY, S, TW>::smem(), s, m, a);
+        case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX, true>, bg, blk, LRE<TY, S, TW>::smem(), s, m, a);
+        case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX, true>, bg, blk, LRH<TY, S, TW>::smem(), s, m, a);
+      }
+      return cudaErrorInvalidValue;
+    }
+  }
+  if (a.bunits) return cudaErrorInvalidValue;   // batched designs: 32 x 8 tiles, two stages
   const int nch = (a.g.nz + a.zchunk - 1) / a.zchunk;
   const int zc1 = a.zc1 > 0 ? min(a.zc1, nch) : nch;
   if (a.zc0 < 0 || a.zc0 >= zc1) return cudaErrorInvalidValue;
@@ -1038,15 +1090,15 @@ static cudaError_t launch_lag2_t(int which, const LagMaps& m, const StepArgs& a,
     if (a.umode) {
       if (!a.Fn) return cudaErrorInvalidValue;
       if (which == 0)
-        return launch_ex(k_l2fwd_h<TY, S, TW, EX, true>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
-      return launch_ex(k_l2fwd_e<TY, S, TW, EX, true>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+        return launch_ex(k_l2fwd_h<TY, S, TW, EX, true, false>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+      return launch_ex(k_l2fwd_e<TY, S, TW, EX, true, false>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
     }
   }
   switch (which) {
-    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX, false>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
-    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX, false>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
-    case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
-    case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
+    case 0: return launch_ex(k_l2fwd_h<TY, S, TW, EX, false, false>, grid, block, LFH<TY, S, TW>::smem(), s, m, a);
+    case 1: return launch_ex(k_l2fwd_e<TY, S, TW, EX, false, false>, grid, block, LFE<TY, S, TW>::smem(), s, m, a);
+    case 2: return launch_ex(k_l2rev_e<TY, S, TW, EX, false>, grid, block, LRE<TY, S, TW>::smem(), s, m, a);
+    case 3: return launch_ex(k_l2rev_h<TY, S, TW, EX, false>, grid, block, LRH<TY, S, TW>::smem(), s, m, a);
   }
   return cudaErrorInvalidValue;
 }

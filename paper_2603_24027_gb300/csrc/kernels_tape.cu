@@ -55,11 +55,10 @@ static constexpr int FLAT_THREADS = 256;  // one thread per value otherwise
 
 // Unscaled formats: one thread per recorded value, grid (value blocks, face).
 template <int DT>
-__global__ void __launch_bounds__(FLAT_THREADS) k_record_flat(const float* __restrict__ FH,
-                                                              const float* __restrict__ FE, Geo g,
-                                                              const __grid_constant__ Faces fc,
-                                                              void* __restrict__ tape_sample,
-                                                              float* scale_slot) {
+__device__ __forceinline__ void record_flat_body(const float* __restrict__ FH,
+                                                 const float* __restrict__ FE, const Geo& g,
+                                                 const Faces& fc, void* __restrict__ tape_sample,
+                                                 float* scale_slot) {
   typedef typename Code<DT>::T T;
   const int f = blockIdx.y;
   const FaceDesc& fd = fc.f[f];
@@ -71,6 +70,22 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_record_flat(const float* __res
   int comp;
   const long long q = face_value_cell(g, fd, r, &comp);
   reinterpret_cast<T*>(tape_sample)[fd.off + r] = Code<DT>::enc(F[comp * g.nc + q]);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(FLAT_THREADS) k_record_flat(const float* __restrict__ FH,
+                                                              const float* __restrict__ FE, Geo g,
+                                                              const __grid_constant__ Faces fc,
+                                                              void* __restrict__ tape_sample,
+                                                              float* scale_slot) {
+  record_flat_body<DT>(FH, FE, g, fc, tape_sample, scale_slot);
+}
+
+// Batched designs: the same for the job blockIdx.z of a list.
+template <int DT>
+__global__ void __launch_bounds__(FLAT_THREADS) k_record_flat_batch(const RecordJob* __restrict__ jobs) {
+  const RecordJob& j = jobs[blockIdx.z];
+  record_flat_body<DT>(j.FH, j.FE, j.g, j.fc, j.sample, j.scale_slot);
 }
 
 // Scaled formats: one cluster of FACE_CLUSTER CTAs per face (blockIdx.y); the
@@ -172,16 +187,14 @@ cudaError_t launch_record(int dtype, int scaled, const float* FH, const float* F
 // dl_n/d(E^{n+1}, Ht^{n+1/2}) for the detector, seeds[1] * dm_n/d(...) for
 // the second one.
 template <int DT>
-__global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict__ F,
-                                                               float* __restrict__ L, Geo g,
-                                                               const __grid_constant__ Faces fc,
-                                                               const void* __restrict__ tape,
-                                                               long long stride,
-                                                               const float* __restrict__ scales,
-                                                               const __grid_constant__ Interp ip,
-                                                               Det det, Det det2,
-                                                               const double* __restrict__ seeds,
-                                                               int face_blocks, int det_blocks) {
+__device__ __forceinline__ void restore_seed_body(float* __restrict__ F, float* __restrict__ L,
+                                                  const Geo& g, const Faces& fc,
+                                                  const void* __restrict__ tape, long long stride,
+                                                  const float* __restrict__ scales,
+                                                  const Interp& ip, const Det& det,
+                                                  const Det& det2,
+                                                  const double* __restrict__ seeds,
+                                                  int face_blocks, int det_blocks) {
   typedef typename Code<DT>::T T;
   if ((int)blockIdx.x < face_blocks) {
     const int r = blockIdx.x * FLAT_THREADS + threadIdx.x;
@@ -211,6 +224,31 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict
   seed_detectors(F, L, g, det, det2, seeds, blockIdx.x - face_blocks, det_blocks);
 }
 
+template <int DT>
+__global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed(float* __restrict__ F,
+                                                               float* __restrict__ L, Geo g,
+                                                               const __grid_constant__ Faces fc,
+                                                               const void* __restrict__ tape,
+                                                               long long stride,
+                                                               const float* __restrict__ scales,
+                                                               const __grid_constant__ Interp ip,
+                                                               Det det, Det det2,
+                                                               const double* __restrict__ seeds,
+                                                               int face_blocks, int det_blocks) {
+  restore_seed_body<DT>(F, L, g, fc, tape, stride, scales, ip, det, det2, seeds, face_blocks,
+                        det_blocks);
+}
+
+// Batched designs: the same for the job blockIdx.y of a list (blocks past the
+// job's own face and detector blocks return).
+template <int DT>
+__global__ void __launch_bounds__(FLAT_THREADS) k_restore_seed_batch(const RestoreJob* __restrict__ jobs) {
+  const RestoreJob& j = jobs[blockIdx.y];
+  if ((int)blockIdx.x >= j.face_blocks + (j.det2.kind ? 2 : 1) * j.det_blocks) return;
+  restore_seed_body<DT>(j.F, j.L, j.g, j.fc, j.tape, j.stride, j.scales, j.ip, j.det, j.det2,
+                        j.seeds, j.face_blocks, j.det_blocks);
+}
+
 cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Faces& fc,
                                 const void* tape, long long stride, const float* scales,
                                 const Interp& ip, const Det& det, const Det& det2,
@@ -227,6 +265,43 @@ cudaError_t launch_restore_seed(int dtype, float* F, float* L, Geo g, const Face
                                                        det2, seeds, face_blocks, det_blocks);
     return cudaGetLastError();
   });
+}
+
+// Batched designs: njobs jobs of a list in device memory, max_blocks value
+// blocks (record: per face; restore: faces and detectors) for the largest.
+cudaError_t launch_record_batch(int dtype, const RecordJob* jobs, int njobs, int max_blocks,
+                                cudaStream_t s) {
+  if (njobs <= 0 || max_blocks <= 0) return cudaSuccess;
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    k_record_flat_batch<DT><<<dim3(max_blocks, 6, njobs), FLAT_THREADS, 0, s>>>(jobs);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_restore_seed_batch(int dtype, const RestoreJob* jobs, int njobs,
+                                      int max_blocks, cudaStream_t s) {
+  if (njobs <= 0 || max_blocks <= 0) return cudaSuccess;
+  return with_dtype(dtype, [&](auto dt) {
+    constexpr int DT = decltype(dt)::value;
+    k_restore_seed_batch<DT><<<dim3(max_blocks, njobs), FLAT_THREADS, 0, s>>>(jobs);
+    return cudaGetLastError();
+  });
+}
+
+// The value and detector blocks of one restore launch (as launch_restore_seed counts them).
+void restore_blocks(const Faces& fc, const Det& det, const Det& det2, int* face_blocks,
+                    int* det_blocks) {
+  *face_blocks = (fc.start[6] + FLAT_THREADS - 1) / FLAT_THREADS;
+  int dmax = det.kind ? (det.u1 - det.u0) * (det.v1 - det.v0) : 0;
+  if (det2.kind) dmax = max(dmax, (det2.u1 - det2.u0) * (det2.v1 - det2.v0));
+  *det_blocks = (dmax + FLAT_THREADS - 1) / FLAT_THREADS;
+}
+
+int record_flat_blocks(const Faces& fc) {
+  int m = 0;
+  for (int f = 0; f < 6; ++f) m = max(m, (2 * fc.f[f].nu * fc.f[f].nv + FLAT_THREADS - 1) / FLAT_THREADS);
+  return m;
 }
 
 // -------------------------------------------------------- raw codec ------

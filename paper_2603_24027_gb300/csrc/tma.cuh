@@ -87,6 +87,15 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// A tensor map in global memory (the batched designs' tables, written by a
+// host copy): order the generic-proxy view of its 128 bytes before this
+// thread's tensor-map-proxy uses of it (the TMA copies that name it).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
+
 // Default bound for one wait: ~2 s at 2 GHz.
 constexpr long long kWaitCycles = 4000000000LL;
 

@@ -239,18 +239,33 @@ class Simulation:
         return list(slot), list(wt)
 
 
-def group_forward(sims, eps_list, rec):
+def _first_error(sims, status):
+    """Raise for a failed group call with the message of the handle that set one."""
+    for s in sims:
+        msg = A.lib().fdtd_last_error(s.h)
+        if msg:
+            raise A.FdtdError(status, msg.decode())
+    A.check(status)
+
+
+def group_forward(sims, eps_list, rec, batched: bool = False):
+    """Forward runs of several designs together: concurrent time loops
+    (fdtd_group_forward), or with batched=True one launch per half-step over
+    all designs (fdtd_batch_forward)."""
     n = len(sims)
     hs = (C.c_void_p * n)(*[s.h.value for s in sims])
     for s, e in zip(sims, eps_list):
         s.ensure_workspace(rec, e.device)
     eps = (C.c_void_p * n)(*[e.data_ptr() for e in eps_list])
     objs = (C.c_double * n)()
-    A.check(A.lib().fdtd_group_forward(hs, n, eps, C.byref(rec), objs))
+    fn = A.lib().fdtd_batch_forward if batched else A.lib().fdtd_group_forward
+    st = fn(hs, n, eps, C.byref(rec), objs)
+    if st != A.FDTD_OK:
+        _first_error(sims, st)
     return list(objs)
 
 
-def group_backward(sims, seeds=None, outs=None):
+def group_backward(sims, seeds=None, outs=None, batched: bool = False):
     n = len(sims)
     hs = (C.c_void_p * n)(*[s.h.value for s in sims])
     seeds = [1.0] * n if seeds is None else seeds
@@ -258,7 +273,10 @@ def group_backward(sims, seeds=None, outs=None):
         outs = [torch.empty(s.design_shape, dtype=torch.float32, device=s._ws.device) for s in sims]
     sd = (C.c_double * n)(*seeds)
     gp = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
-    A.check(A.lib().fdtd_group_backward(hs, n, sd, gp))
+    fn = A.lib().fdtd_batch_backward if batched else A.lib().fdtd_group_backward
+    st = fn(hs, n, sd, gp)
+    if st != A.FDTD_OK:
+        _first_error(sims, st)
     return outs
 
 
