@@ -438,3 +438,38 @@ def test_fused_forward_workspace_and_automatic_choice(capi, fdtd):
     split = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_FORWARD, 0)
     assert sim.workspace_bytes(rec) == split
+
+
+def test_batched_designs_validate_before_any_device_work(capi, fdtd):
+    """fdtd_batch_forward / fdtd_batch_backward check their arguments, the
+    handles' options and the tape format on the host, before the plan's
+    device tables or any launch (handles bound to a placeholder workspace
+    address, which nothing dereferences on these paths)."""
+    lib = capi.lib()
+    wl = I.batched_cubes(n_sims=3, seed=5, sizes=(32, 40), steps=(20, 30))
+    sims = [fdtd.Simulation(w) for w in wl]
+    base = 1 << 40
+    for i, s in enumerate(sims):
+        assert lib.fdtd_bind_workspace(s.h, C.c_void_p(base + i * (1 << 32)), 1 << 31) == 0
+    n = len(sims)
+    hs = (C.c_void_p * n)(*[s.h.value for s in sims])
+    eps = (C.c_void_p * n)(*[base] * n)
+    objs = (C.c_double * n)()
+    bf16 = capi.record_cfg("bf16", 4)
+    assert lib.fdtd_batch_forward(hs, 0, eps, C.byref(bf16), objs) == capi.FDTD_EINVAL
+    assert lib.fdtd_batch_forward(None, n, eps, C.byref(bf16), objs) == capi.FDTD_EINVAL
+    twice = (C.c_void_p * 2)(sims[0].h.value, sims[0].h.value)
+    assert lib.fdtd_batch_forward(twice, 2, eps, C.byref(bf16), objs) == capi.FDTD_EINVAL
+    scaled = capi.record_cfg("e4m3", 2, scaled=True)
+    assert lib.fdtd_batch_forward(hs, n, eps, C.byref(scaled), objs) == capi.FDTD_EINVAL
+    assert b"unscaled" in lib.fdtd_last_error(sims[0].h)
+    sims[2].set_option(capi.OPT_EXACT_REVERSAL, 22)
+    assert lib.fdtd_batch_forward(hs, n, eps, C.byref(bf16), objs) == capi.FDTD_EINVAL
+    assert b"split steps" in lib.fdtd_last_error(sims[2].h)
+    sims[2].set_option(capi.OPT_EXACT_REVERSAL, 0)
+    sims[1].set_option(capi.OPT_REVERSE, 2)
+    assert lib.fdtd_batch_forward(hs, n, eps, C.byref(bf16), objs) == capi.FDTD_EINVAL
+    sims[1].set_option(capi.OPT_REVERSE, 1)
+    seeds = (C.c_double * n)(*[1.0] * n)
+    grads = (C.c_void_p * n)(*[base] * n)
+    assert lib.fdtd_batch_backward(hs, n, seeds, grads) == capi.FDTD_ESTATE
