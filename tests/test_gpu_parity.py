@@ -975,6 +975,38 @@ def test_largest_grid_in_the_bench_configuration(F, A):
     assert rel(gf, gs) < 1e-5
 
 
+def test_largest_grid_against_the_oracle_near_the_source(F, A):
+    """All 108 M cells of the 600 x 600 x 300 grid in the bench's launch
+    configuration (fused forward and fused reverse, FP32 tape of every step),
+    against the FP64 oracle: the Poynting detector moved to x = 28 and the
+    design box to x in [21, 28) around the strip, between the source plane
+    (x = 20) and the detector, so that L and dL/d(eps) are non-zero within
+    120 steps.  Both stay outside the CPML-free units, as the fused forward
+    needs.  Fields after the forward within 1e-5, the objective within 1e-5,
+    the gradient within 1e-4."""
+    w = I.waveguide_large(n_steps=120)
+    P, yc, zc = w.pml_thickness, w.ny // 2, w.nz // 2
+    w = w.replace(det_index=28, design_lo=(21, yc - 16, zc - 11), design_hi=(28, yc + 16, zc + 11))
+    L, g, st = O.gradient(w, want_state=True)
+    assert L != 0.0 and np.abs(g).max() > 0
+    sim = F.Simulation(w)
+    for opt in (A.OPT_FORWARD, A.OPT_REVERSE):
+        assert sim.get_option(opt) == 0
+    eps = torch.from_numpy(w.eps).cuda()
+    Lg = sim.forward(eps, A.record_cfg("f32", 1))
+    assert sim.last_timing()["fwd_launches"] == 6 * w.n_steps   # fused: 5 launches + the record
+    fields = sim.read_fields().cpu().numpy()
+    eE, eH = field_err(fields, st)
+    del st
+    assert eE < 1e-5 and eH < 1e-5, (eE, eH)
+    assert Lg == pytest.approx(L, rel=1e-5)
+    gg = sim.backward(1.0).cpu().numpy()
+    assert sim.last_timing()["bwd_launches"] == 5 * w.n_steps   # fused: restore, primal, 3 adjoint
+    assert rel(gg, g) < 1e-4, rel(gg, g)
+    del sim
+    torch.cuda.empty_cache()
+
+
 def test_largest_grid_exact_reversal_returns_to_zero(F, A):
     """The same grid, 300 steps, exact reversal through the default steps:
     the interior returns to the zero initial state bit for bit."""
