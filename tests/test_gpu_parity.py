@@ -1007,6 +1007,27 @@ def test_largest_grid_against_the_oracle_near_the_source(F, A):
     torch.cuda.empty_cache()
 
 
+def test_largest_grid_compressed_tape_against_the_oracle_method(F, A):
+    """The same full-size case with the bench's tape (E4M3 with per-face
+    scales, every 8th step, linear): the GPU gradient against the oracle's
+    FP64 run of the method with the same quantiser and interpolation, at the
+    compressed-tape bar (relative L2 2e-2, cosine 0.999)."""
+    w = I.waveguide_large(n_steps=120)
+    yc, zc = w.ny // 2, w.nz // 2
+    w = w.replace(det_index=28, design_lo=(21, yc - 16, zc - 11), design_hi=(28, yc + 16, zc + 11))
+    Lm, gm = O.reverse(w, fmt="e4m3", scaled=True, k=8, interp="linear")
+    assert np.abs(gm).max() > 0
+    sim = F.Simulation(w)
+    eps = torch.from_numpy(w.eps).cuda()
+    Lg = sim.forward(eps, A.record_cfg("e4m3", 8, "linear"))
+    gg = sim.backward(1.0).cpu().numpy()
+    assert Lg == pytest.approx(Lm, rel=1e-5)
+    assert rel(gg, gm) < 2e-2, rel(gg, gm)
+    assert cos(gg, gm) > 0.999
+    del sim
+    torch.cuda.empty_cache()
+
+
 def test_largest_grid_exact_reversal_returns_to_zero(F, A):
     """The same grid, 300 steps, exact reversal through the default steps:
     the interior returns to the zero initial state bit for bit."""
