@@ -611,11 +611,13 @@ def cpu_baseline(n_steps: int, name: str):
     from oracle import build as ob
     from oracle import oracle as O
     ob.build()
+    oracle_step(max(1, n_steps // 2), name)   # warm-up, as the reference arm does
     dt, w = oracle_step(n_steps, name)
     return {"value": w.n_cells * w.n_steps / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle",
             "sample": f"FP64 oracle gradient (forward + stored-history adjoint) of the same "
-                      f"{w.nx}x{w.ny}x{w.nz} workload truncated to {n_steps} steps; {dt:.1f} s"}
+                      f"{w.nx}x{w.ny}x{w.nz} workload truncated to {n_steps} steps, after one "
+                      f"warm-up run; {dt:.1f} s"}
 
 
 def run_reference(args):
