@@ -92,7 +92,9 @@ struct AL {
   static constexpr int STAGE = PHZ + (PZ ? r128(2 * HZP * 4) : 0);
   static constexpr int BARS = S * STAGE;
   static constexpr int SL = r128(BARS + 8 * S);
-  static int smem() { return SL + 3 * HP * 4; }
+  // ring units: the x / y CPML profiles of the tile's cells and halo
+  static constexpr int SP = SL + r128(3 * HP * 4), SPXN = TW + 8, SPYN = TY + 4;
+  static int smem() { return PXY ? SP + 6 * (SPXN + SPYN) * 4 : SL + 3 * HP * 4; }
 };
 
 // ring_init puts the barriers at S * STAGE: the exchange arrays come after them
@@ -345,6 +347,24 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
   const bool ok1 = task && rowok && x + 1 >= 0 && x + 1 < g.nx;
   const bool v0 = mainT && ok0, v1 = mainT && ok1;   // cells this thread stores
   const int p0_ = k0 - 1, p1_ = k1;
+  // ring units: the x / y CPML profiles the tile's cells and halo read,
+  // staged once (they do not change along z), [6][TW+8] from x0-4 and
+  // [6][TY+4] from y0-2
+  float* SPX = reinterpret_cast<float*>(dsm + Y::SP);
+  float* SPY = SPX + 6 * Y::SPXN;
+  auto spx = [&](int w, int xx) { return SPX[w * Y::SPXN + xx - x0 + 4]; };
+  auto spy = [&](int w, int yy) { return SPY[w * Y::SPYN + yy - y0 + 2]; };
+  if (PXY) {
+    const int nt = (TW / 2) * (TY + 2);
+    for (int i = tid; i < 6 * Y::SPXN; i += nt) {
+      const int w = i / Y::SPXN, xi = x0 - 4 + i % Y::SPXN;
+      SPX[i] = (xi >= 0 && xi < g.nx) ? prof(g, 0, w, xi) : 0.f;
+    }
+    for (int i = tid; i < 6 * Y::SPYN; i += nt) {
+      const int w = i / Y::SPYN, yi = y0 - 2 + i % Y::SPYN;
+      SPY[i] = (yi >= 0 && yi < g.ny) ? prof(g, 1, w, yi) : 0.f;
+    }
+  }
   uint64_t* bars = ring_init<S>(dsm, Y::STAGE);   // at Y::BARS
   int qx0 = x0, qy0 = y0;
   bool txs = false, tys = false, txh = false, tyh = false;
@@ -465,7 +485,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             const float* P = reinterpret_cast<const float*>(st + Y::PEY);   // (TW+4) x (TY+2) at (x0-4, y0-1)
             const int yb = (y - y0 + 1) * (TW + 4) + (x - x0 + 4);
             if (sy) {
-              const float by = prof(g, 1, PR_BE, y), ay = prof(g, 1, PR_AE, y), ky = prof(g, 1, PR_KE, y);
+              const float by = spy(PR_BE, y), ay = spy(PR_AE, y), ky = spy(PR_KE, y);
               const float2 p0 = ld2(P, yb), p1 = ld2(P + Y::EYP, yb);
               const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
               float s6[2], s11[2];
@@ -481,8 +501,8 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               }
             }
             if (sy1) {
-              const float by1 = prof(g, 1, PR_BE, y + 1), ay1 = prof(g, 1, PR_AE, y + 1),
-                          ky1 = prof(g, 1, PR_KE, y + 1);
+              const float by1 = spy(PR_BE, y + 1), ay1 = spy(PR_AE, y + 1),
+                          ky1 = spy(PR_KE, y + 1);
               const float2 p0 = ld2(P, yb + TW + 4), p1 = ld2(P + Y::EYP, yb + TW + 4);
               const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
               float dummy;
@@ -499,13 +519,13 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             const float2 p0 = ld2(P, xb), p1 = ld2(P + Y::EXP, xb);
             float s9[2] = {0.f, 0.f}, s10[2] = {0.f, 0.f};
             if (sx0) {
-              const float b = prof(g, 0, PR_BE, x), aa = prof(g, 0, PR_AE, x), kk = prof(g, 0, PR_KE, x);
+              const float b = spx(PR_BE, x), aa = spx(PR_AE, x), kk = spx(PR_KE, x);
               o9[0] = adj(o9[0], p0.x, b, aa, kk, &s9[0]);
               o10[0] = adj(o10[0], p1.x, b, aa, kk, &s10[0]);
             }
             if (sx1) {
-              const float b = prof(g, 0, PR_BE, x + 1), aa = prof(g, 0, PR_AE, x + 1),
-                          kk = prof(g, 0, PR_KE, x + 1);
+              const float b = spx(PR_BE, x + 1), aa = spx(PR_AE, x + 1),
+                          kk = spx(PR_KE, x + 1);
               o9[1] = adj(o9[1], p0.y, b, aa, kk, &s9[1]);
               o10[1] = adj(o10[1], p1.y, b, aa, kk, &s10[1]);
             }
@@ -515,8 +535,8 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               ST2(lpB + a.pl.ax[0].cs, qxx, s10[0], s10[1], v0 && sx0, v1 && sx1);
             }
             if (sx2) {
-              const float b = prof(g, 0, PR_BE, x + 2), aa = prof(g, 0, PR_AE, x + 2),
-                          kk = prof(g, 0, PR_KE, x + 2);
+              const float b = spx(PR_BE, x + 2), aa = spx(PR_AE, x + 2),
+                          kk = spx(PR_KE, x + 2);
               float dummy;
               n9x = adj(n9x, P[xb + 2], b, aa, kk, &dummy);
               n10x = adj(n10x, P[Y::EXP + xb + 2], b, aa, kk, &dummy);
@@ -641,7 +661,7 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             const float* P = reinterpret_cast<const float*>(st + Y::PHY);   // TW x (TY+1) at (x0, y0-1)
             const int yb = (y - y0 + 1) * TW + (x - x0);
             if (hy) {
-              const float by = prof(g, 1, PR_BH, y), ay = prof(g, 1, PR_AH, y), ky = prof(g, 1, PR_KH, y);
+              const float by = spy(PR_BH, y), ay = spy(PR_AH, y), ky = spy(PR_KH, y);
               const float2 p0 = ld2(P, yb), p1 = ld2(P + Y::HYP, yb);
               const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
               float s4[2], s5[2];
@@ -655,8 +675,8 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
               ST2(lpB + a.pl.ax[1].cs, qyy, s5[0], s5[1], v0, v1);
             }
             if (hym) {
-              const float bym = prof(g, 1, PR_BH, y - 1), aym = prof(g, 1, PR_AH, y - 1),
-                          kym = prof(g, 1, PR_KH, y - 1);
+              const float bym = spy(PR_BH, y - 1), aym = spy(PR_AH, y - 1),
+                          kym = spy(PR_KH, y - 1);
               const float2 p0 = ld2(P, yb - TW), p1 = ld2(P + Y::HYP, yb - TW);
               const float q0[2] = {p0.x, p0.y}, q1[2] = {p1.x, p1.y};
               float dummy;
@@ -673,13 +693,13 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             const float2 p0 = ld2(P, xb), p1 = ld2(P + Y::HXP, xb);
             float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f};
             if (hx0) {
-              const float b = prof(g, 0, PR_BH, x), aa = prof(g, 0, PR_AH, x), kk = prof(g, 0, PR_KH, x);
+              const float b = spx(PR_BH, x), aa = spx(PR_AH, x), kk = spx(PR_KH, x);
               o3[0] = adj(o3[0], p0.x, b, aa, kk, &s0[0]);
               o4[0] = adj(o4[0], p1.x, b, aa, kk, &s1[0]);
             }
             if (hx1) {
-              const float b = prof(g, 0, PR_BH, x + 1), aa = prof(g, 0, PR_AH, x + 1),
-                          kk = prof(g, 0, PR_KH, x + 1);
+              const float b = spx(PR_BH, x + 1), aa = spx(PR_AH, x + 1),
+                          kk = spx(PR_KH, x + 1);
               o3[1] = adj(o3[1], p0.y, b, aa, kk, &s0[1]);
               o4[1] = adj(o4[1], p1.y, b, aa, kk, &s1[1]);
             }
@@ -687,8 +707,8 @@ k_rev_adjoint(const __grid_constant__ RevMaps m, StepArgs a, RevUnits U) {
             ST2(lpB, qxx, s0[0], s0[1], hx0, hx1);
             ST2(lpB + a.pl.ax[0].cs, qxx, s1[0], s1[1], hx0, hx1);
             if (hxm) {
-              const float b = prof(g, 0, PR_BH, x - 1), aa = prof(g, 0, PR_AH, x - 1),
-                          kk = prof(g, 0, PR_KH, x - 1);
+              const float b = spx(PR_BH, x - 1), aa = spx(PR_AH, x - 1),
+                          kk = spx(PR_KH, x - 1);
               float dummy;
               m3x = adj(m3x, P[xb - 1], b, aa, kk, &dummy);
               m4x = adj(m4x, P[Y::HXP + xb - 1], b, aa, kk, &dummy);
