@@ -35,8 +35,8 @@ schedule of half-steps and exchanges of one forward and one reverse step,
 and the exchange itself over torch.distributed point-to-point messages
 (NCCL for CUDA tensors, gloo for CPU tensors).  The per-rank device engine
 (the staged kernels on a slab with two ghost planes and a z-CPML on the
-owned global faces only) is not part of the library: every run of it so
-far has had one GPU.
+owned global faces only) is not part of the library, which drives one GPU
+per process and no device-side halo path.
 """
 from __future__ import annotations
 

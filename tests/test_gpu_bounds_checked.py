@@ -4,7 +4,7 @@ into the other buffer of each ping-pong pair) checks that it lands in the
 fields, the adjoint fields or an auxiliary set of its launch, and the
 gacc reduction that it stays in the design box; a stray store is skipped
 and reported (FDTD_ECUDA).  compute-sanitizer is closed on this machine, so
-this build stands in for it: it runs the index arithmetic of the compact
+this library build stands in for it: it runs the index arithmetic of the compact
 auxiliary layout, the tile shapes, z chunks and ragged grids in a separate
 process and checks that no store strays and the gradients stay those of
 the FP64 oracle."""

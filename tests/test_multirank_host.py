@@ -1,6 +1,6 @@
 """Host logic of the multi-GPU benchmark path, on CPU with two gloo ranks.
 
-The gradient workload does not shard across GPUs in this build: N GPUs run N
+The gradient workload does not shard across GPUs in the library: N GPUs run N
 independent replicas (one seeded design per rank, no data-path collective),
 timed by the slowest rank.  These tests run the benchmark's rank helpers
 under a real two-process gloo group: the max-over-ranks reduction, the

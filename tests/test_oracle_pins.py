@@ -685,7 +685,7 @@ MIN_SUB = {"e4m3": 2.0 ** -9, "f16": 2.0 ** -24}
 @pytest.mark.parametrize("fmt", ["e4m3", "f16"])
 def test_scaled_face_encoder_properties(fmt):
     """The per-face scale of the reduced bit-width tape (Sec. 2; the scale
-    reading of BASELINE's FP8 tape): the face's largest magnitude maps onto the
+    reading of the benchmark's FP8 tape): the face's largest magnitude maps onto the
     format's largest finite value and comes back exactly; every value is
     within half a step of the format at the face's scale; scaling a face by a
     power of two scales its code values by the same power (the scale absorbs
