@@ -323,10 +323,11 @@ enum {
                                    fdtd_forward with other tiles.  Results agree with the
                                    split phases: primal fields bit for bit, gradients to
                                    rounding */
-  FDTD_OPT_FORWARD = 16         /* kernel 5: how a forward time step runs.  0 (default) =
-                                   automatic: fused where it can run (below) and at most
-                                   half of the (tile, z chunk) units carry CPML terms, else
-                                   split; 1 = split: an H and an E half-step launch, each
+  FDTD_OPT_FORWARD = 16,        /* kernel 5: how a forward time step runs.  0 (default) =
+                                   automatic: where at most half of the (tile, z chunk)
+                                   units carry CPML terms, two steps per pass (3) where it
+                                   can run (below), else fused where it can run; split
+                                   elsewhere; 1 = split: an H and an E half-step launch, each
                                    updating the fields in place; 2 = fused: the units
                                    without a CPML term (fdtd_reverse_units' CPML-free box)
                                    run both half-steps in one launch that reads every field
@@ -335,7 +336,27 @@ enum {
                                    half-steps from and into the same pair.  Needs 32 x 8
                                    tiles, such units, and the source and the detector
                                    outside them; else FDTD_EINVAL at fdtd_forward.  The
-                                   fields are bit-identical to the split half-steps' */
+                                   fields are bit-identical to the split half-steps'; 3 =
+                                   two steps per pass (temporal blocking, not part of the
+                                   paper's method): the deep units (fdtd_deep_units: no
+                                   CPML term on their cells or a two-cell halo) run time
+                                   steps n and n + 1 in one launch that reads E^n,
+                                   Ht^{n-1/2} and cb once and writes E^{n+2}, Ht^{n+3/2}
+                                   once into the other buffer of the pair, plus the
+                                   intermediate level on the one-cell frame of the deep
+                                   box into a third field buffer; the other units run the
+                                   split half-steps one step at a time through that
+                                   buffer.  Needs 32 x 8 tiles, deep units, and the source
+                                   and the detectors two cells or more away from them;
+                                   else FDTD_EINVAL at fdtd_forward.  An odd step count
+                                   runs its first step as split half-steps over every
+                                   unit.  The fields and the tape are bit-identical to
+                                   the split half-steps' */
+  FDTD_OPT_ZCHUNK_FWD2 = 17     /* kernel 5 with FDTD_OPT_FORWARD = 3: z planes per CTA of
+                                   the two-step pass (-1 or 0, the default: four chunks of
+                                   the other units' split half-steps, whose chunks are
+                                   FDTD_OPT_ZCHUNK_FWD planes if > 0, else FDTD_OPT_ZCHUNK);
+                                   a chunk streams two planes below and one above it */
 };
 int fdtd_set_option(fdtd_handle* h, int option, int value);
 int fdtd_get_option(const fdtd_handle* h, int option, int* value);
@@ -344,7 +365,8 @@ int fdtd_get_option(const fdtd_handle* h, int option, int* value);
 enum {
   FDTD_K_FWD_H = 0, FDTD_K_FWD_E = 1, FDTD_K_RECORD = 2, FDTD_K_RESTORE = 3,
   FDTD_K_REV_E = 4, FDTD_K_REV_H = 5, FDTD_K_REV_PRIMAL = 6, FDTD_K_REV_ADJOINT = 7,
-  FDTD_K_MONITOR = 8, FDTD_K_REV_ADJOINT_CPML = 9, FDTD_K_FWD_FUSED = 10, FDTD_K_KINDS = 11
+  FDTD_K_MONITOR = 8, FDTD_K_REV_ADJOINT_CPML = 9, FDTD_K_FWD_FUSED = 10,
+  FDTD_K_FWD_2STEP = 11, FDTD_K_KINDS = 12
 };
 /* Average in-loop cost (ms) per launch of one kernel kind in the last
  * forward + backward, and the number of samples it rests on
@@ -447,6 +469,16 @@ int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi);
  * grid exactly once. */
 int fdtd_reverse_units(int nx, int ny, int nz, int P, int zchunk, int* counts, int* units,
                        int max_units);
+
+/* The deep units of the two-step forward (FDTD_OPT_FORWARD = 3) for an
+ * nx x ny x nz grid with a P-cell CPML and split z chunks of zchunk planes:
+ * box[0..5] = ix0, ix1, iy0, iy1, iz0, iz1, the tiles [ix0, ix1) x [iy0,
+ * iy1) (x0 = 32 ix, y0 = 8 iy) and whole chunks [iz0, iz1) (planes [k0, k1))
+ * for which the cells x in [x0 - 2, x0 + 34), y in [y0 - 2, y0 + 9), z in
+ * [k0 - 2, k1] (where a two-step pass evaluates the intermediate level) all
+ * lie in the interior [P, n - P) of every axis.  All zero when there are
+ * none.  Host only; FDTD_EINVAL on NULL or non-positive sizes. */
+int fdtd_deep_units(int nx, int ny, int nz, int P, int zchunk, int* box);
 
 /* Self-test of the bounded device waits (failure detection without a
  * fault): one CTA arms an mbarrier for a copy that is never issued and waits

@@ -28,11 +28,12 @@ BDCT_DEFAULT_COEFFS = 10
 INTERP = {"linear": 0, "cubic": 1}
 OPT_USE_GRAPHS, OPT_KERNEL, OPT_TILE_Y, OPT_ZCHUNK, OPT_SAMPLE_EVERY = range(5)
 OPT_STAGES, OPT_PDL, OPT_PREFETCH, OPT_TILE_X, OPT_COMPACT_AUX, OPT_EXACT_REVERSAL, \
-    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT, OPT_REVERSE, OPT_FORWARD = range(6, 17)
+    OPT_ZCHUNK_FWD, OPT_ZGROUPS, OPT_INJECT_WAIT_TIMEOUT, OPT_REVERSE, OPT_FORWARD, \
+    OPT_ZCHUNK_FWD2 = range(6, 18)
 K_FWD_H, K_FWD_E, K_RECORD, K_RESTORE, K_REV_E, K_REV_H, K_REV_PRIMAL, K_REV_ADJOINT, K_MONITOR, \
-    K_REV_ADJOINT_CPML, K_FWD_FUSED = range(11)
+    K_REV_ADJOINT_CPML, K_FWD_FUSED, K_FWD_2STEP = range(12)
 KERNEL_NAMES = ["fwd_h", "fwd_e", "record", "restore_seed", "rev_e", "rev_h", "rev_primal",
-                "rev_adjoint", "monitor", "rev_adjoint_cpml", "fwd_fused"]
+                "rev_adjoint", "monitor", "rev_adjoint_cpml", "fwd_fused", "fwd_2step"]
 
 
 class Grid(C.Structure):
@@ -125,6 +126,8 @@ _PROTOS = {
     "fdtd_status_of_error_word": (C.c_int, [C.c_uint]),
     "fdtd_reverse_units": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                      C.POINTER(C.c_int), C.c_void_p, C.c_int]),
+    "fdtd_deep_units": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(C.c_int)]),
     "fdtd_value_and_grad_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(RecordCfg),
                                               C.c_double, C.POINTER(C.c_double), C.c_void_p]),
 }

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libfdtd_gb300.so")
 # default kernels checks that it lands in a buffer the launch may write.
 LIB_CHECKED = os.path.join(HERE, "libfdtd_gb300_checked.so")
 SOURCES = ["kernels_step.cu", "kernels_lag2.cu", "kernels_rev_fused.cu", "kernels_fwd_fused.cu",
-           "tensor_maps.cu", "kernels_tape.cu", "kernels_bdct.cu", "fdtd_api.cu"]
+           "kernels_fwd_2step.cu", "tensor_maps.cu", "kernels_tape.cu", "kernels_bdct.cu", "fdtd_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE]
@@ -46,8 +46,8 @@ def _digest() -> str:
 
 # Device code of the default half-step kernels: the files whose change can
 # change what those kernels move through memory.
-KERNEL_FILES = ["kernels_lag2.cu", "kernels_rev_fused.cu", "kernels_fwd_fused.cu", "lag_common.cuh",
-                "fdtd_internal.cuh", "tma.cuh"]
+KERNEL_FILES = ["kernels_lag2.cu", "kernels_rev_fused.cu", "kernels_fwd_fused.cu",
+                "kernels_fwd_2step.cu", "lag_common.cuh", "fdtd_internal.cuh", "tma.cuh"]
 
 
 def kernel_digest() -> str:

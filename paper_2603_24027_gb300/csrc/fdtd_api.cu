@@ -30,7 +30,7 @@ namespace {
 const double kC0 = 299792458.0;
 
 struct Layout {
-  size_t F[2], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, obj2, seeds, prof, srcw, tape,
+  size_t F[3], L[2], cb, eps, psiF[2], psiL[2], gacc, gout, obj, obj2, seeds, prof, srcw, tape,
       scales, err;
   PsiLayout plF, plL;  // layouts of the forward and adjoint auxiliary sets
   size_t total;
@@ -41,7 +41,7 @@ struct Layout {
 struct GraphKey {
   int dir, dtype, k, interp, scaled, kernel, tile_y, zchunk, sample, stages, pdl, prefetch,
       tile_x, compact, exact, coeffs, zchunk_fwd, zgroups, inject_wait, reverse, forward,
-      start_buf;
+      zchunk_fwd2, start_buf;
   bool operator<(const GraphKey& o) const {
     return memcmp(this, &o, sizeof(GraphKey)) < 0;
   }
@@ -88,10 +88,12 @@ struct fdtd_handle {
   fdtd_record_cfg fwd_rec;
 
   int opt_graphs, opt_kernel, opt_tile_y, opt_zchunk, opt_sample, opt_stages, opt_pdl,
-      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups;
+      opt_prefetch, opt_tile_x, opt_compact, opt_exact, opt_zchunk_fwd, opt_zgroups,
+      opt_zchunk_fwd2;
   int opt_inject_wait;        // FDTD_OPT_INJECT_WAIT_TIMEOUT (SM cycles; 0 = off)
   int opt_reverse;            // FDTD_OPT_REVERSE: 0 automatic, 1 split phases, 2 fused
-  int opt_forward;            // FDTD_OPT_FORWARD: 0 automatic, 1 split half-steps, 2 fused
+  int opt_forward;            // FDTD_OPT_FORWARD: 0 automatic, 1 split half-steps, 2 fused,
+                              // 3 two steps per pass
   // z-group scheduling (FDTD_OPT_ZGROUPS): one stream per group, and per group
   // three events (the last launch of an even / odd phase, the join), plus the
   // fork event
@@ -426,9 +428,13 @@ static bool plane_meets(int axis, int index, int u0, int u1, int v0, int v1, con
 // half-steps everywhere.  It needs 32 x 8 tiles, such units, and the source
 // and the detector outside them (the split E half-step adds the source and
 // sums the objective).  Automatic (0): as the reverse step, fused where at
-// most half of the units carry CPML terms.
+// most half of the units carry CPML terms, unless the two-step pass (below)
+// runs there.
+static bool two_step_forward(const fdtd_handle* h);
+
 static bool fused_forward(const fdtd_handle* h) {
-  if (h->opt_kernel != 5 || h->opt_forward == 1) return false;
+  if (h->opt_kernel != 5 || h->opt_forward == 1 || h->opt_forward == 3) return false;
+  if (h->opt_forward == 0 && two_step_forward(h)) return false;   // automatic: two steps per pass
   const int ty = h->opt_tile_y < 2 ? 2 : h->opt_tile_y;
   const int tx = (ty == 8 && h->opt_stages <= 3 && h->opt_tile_x == 40) ? 40 : 32;
   if (ty != 8 || tx != 32) return false;
@@ -450,6 +456,53 @@ static bool fused_forward(const fdtd_handle* h) {
   const long long all = (long long)U.ntx * U.nty * U.nzc;
   const long long cpml = all - (long long)(U.ix1 - U.ix0) * (U.iy1 - U.iy0) * (U.iz1 - U.iz0);
   return 2 * cpml <= all;
+}
+
+// Two time steps per pass (kernels_fwd_2step.cu, FDTD_OPT_FORWARD = 3): the
+// deep units run steps n and n + 1 in one launch, the other units the split
+// half-steps one step at a time through a third field buffer.  Needs kernel
+// 5 with 32 x 8 tiles, deep units, and the source and the detectors at least
+// two cells away from the deep box (the pass evaluates the intermediate
+// level on a two-cell halo and adds no source term, sums no objective).
+// Automatic (0): where the fused step would run (at most half of the units
+// carry CPML terms), which it beats on 600 x 600 x 300 (1055 against 1166 us
+// per forward step); on 200 x 200 x 100 it is slower than the split
+// half-steps (92 against 59 us), as the fused step is.
+static bool two_step_forward(const fdtd_handle* h) {
+  if (h->opt_kernel != 5 || (h->opt_forward != 3 && h->opt_forward != 0)) return false;
+  const int ty = h->opt_tile_y < 2 ? 2 : h->opt_tile_y;
+  const int tx = (ty == 8 && h->opt_stages <= 3 && h->opt_tile_x == 40) ? 40 : 32;
+  if (ty != 8 || tx != 32) return false;
+  Geo g;
+  memset(&g, 0, sizeof g);
+  g.nx = h->nx; g.ny = h->ny; g.nz = h->nz; g.P = h->P;
+  const int zc = fused_forward_zchunk(h);
+  const RevUnits U = deep_units(g, zc);
+  if (U.ix1 <= U.ix0 || U.iy1 <= U.iy0 || U.iz1 <= U.iz0) return false;
+  const int lo[3] = {U.ix0 * 32 - 2, U.iy0 * 8 - 2, U.iz0 * zc - 2};
+  const int hi[3] = {U.ix1 * 32 + 2, U.iy1 * 8 + 2, std::min(U.iz1 * zc, h->nz) + 2};
+  if (h->src.kind && plane_meets(h->src_axis, h->src_index, h->src_u0, h->src_u1, h->src_v0,
+                                 h->src_v1, lo, hi))
+    return false;
+  if (h->det.kind && plane_meets(h->det.axis, h->det.index, h->det.lo[0], h->det.hi[0],
+                                 h->det.lo[1], h->det.hi[1], lo, hi))
+    return false;
+  if (h->det2.kind && plane_meets(h->det2.axis, h->det2.index, h->det2.lo[0], h->det2.hi[0],
+                                  h->det2.lo[1], h->det2.hi[1], lo, hi))
+    return false;
+  if (h->opt_forward == 3) return true;
+  const RevUnits R = rev_units(g, zc);
+  const long long all = (long long)R.ntx * R.nty * R.nzc;
+  const long long cpml = all - (long long)(R.ix1 - R.ix0) * (R.iy1 - R.iy0) * (R.iz1 - R.iz0);
+  return R.ix1 > R.ix0 && 2 * cpml <= all;
+}
+
+// The field buffer holding the state after a forward: the fused step flips
+// the pair every step, the two-step pass every pair of steps (and its split
+// first step, for an odd count, once).
+static int forward_end_buf(const fdtd_handle* h) {
+  if (two_step_forward(h)) return ((h->N + 1) / 2) & 1;
+  return fused_forward(h) ? (h->N & 1) : 0;
 }
 
 // ---------------------------------------------------------------- layout ---
@@ -502,11 +555,13 @@ static Layout layout_of(const fdtd_handle* h, const fdtd_record_cfg* rec) {
   size_t nd = (size_t)(h->dhi[0] - h->dlo[0]) * (h->dhi[1] - h->dlo[1]) * (h->dhi[2] - h->dlo[2]);
   // the fused steps write the new fields (and, in reverse, adjoint fields)
   // next to the old ones (ping-pong pairs)
-  const bool rev2 = fused_reverse(h), fwd2 = fused_forward(h);
+  const bool rev2 = fused_reverse(h), fwd2 = fused_forward(h), two = two_step_forward(h);
   size_t off = 0;
   L.F[0] = off; off += f6;
   L.F[1] = L.F[0];
-  if (rev2 || fwd2) { L.F[1] = off; off += f6; }
+  if (rev2 || fwd2 || two) { L.F[1] = off; off += f6; }
+  L.F[2] = L.F[0];
+  if (two) { L.F[2] = off; off += f6; }   // the two-step pass's intermediate level
   L.L[0] = off; off += f6;
   L.L[1] = L.L[0];
   if (rev2) { L.L[1] = off; off += f6; }
@@ -654,6 +709,7 @@ extern "C" int fdtd_create(const fdtd_grid* grid, double dx, double dt, const fd
   h->opt_tile_y = 8;
   h->opt_zchunk = 8;
   h->opt_zchunk_fwd = -1;
+  h->opt_zchunk_fwd2 = -1;
   h->opt_zgroups = 0;
   h->zfork = nullptr;
   h->opt_sample = 0;
@@ -789,6 +845,10 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       if (value < -1) return fail(h, FDTD_EINVAL, "forward zchunk must be >= -1");
       h->opt_zchunk_fwd = value;
       break;
+    case FDTD_OPT_ZCHUNK_FWD2:
+      if (value < -1) return fail(h, FDTD_EINVAL, "two-step zchunk must be >= -1");
+      h->opt_zchunk_fwd2 = value;
+      break;
     case FDTD_OPT_ZGROUPS:
       if (value < 0 || value > kMaxZGroups) return fail(h, FDTD_EINVAL, "zgroups must be 0..16");
       h->opt_zgroups = value;
@@ -799,7 +859,7 @@ extern "C" int fdtd_set_option(fdtd_handle* h, int option, int value) {
       h->opt_reverse = value;
       break;
     case FDTD_OPT_FORWARD:
-      if (value < 0 || value > 2) return fail(h, FDTD_EINVAL, "forward must be 0, 1 or 2");
+      if (value < 0 || value > 3) return fail(h, FDTD_EINVAL, "forward must be 0, 1, 2 or 3");
       if (value != h->opt_forward) h->have_forward = false;   // the workspace layout changes
       h->opt_forward = value;
       break;
@@ -833,6 +893,7 @@ extern "C" int fdtd_get_option(const fdtd_handle* h, int option, int* value) {
     case FDTD_OPT_COMPACT_AUX: *value = h->opt_compact; break;
     case FDTD_OPT_EXACT_REVERSAL: *value = h->opt_exact; break;
     case FDTD_OPT_ZCHUNK_FWD: *value = h->opt_zchunk_fwd; break;
+    case FDTD_OPT_ZCHUNK_FWD2: *value = h->opt_zchunk_fwd2; break;
     case FDTD_OPT_ZGROUPS: *value = h->opt_zgroups; break;
     case FDTD_OPT_INJECT_WAIT_TIMEOUT: *value = h->opt_inject_wait; break;
     case FDTD_OPT_REVERSE: *value = h->opt_reverse; break;
@@ -1188,7 +1249,7 @@ static cudaError_t ensure_zgroups(fdtd_handle* h, int dir) {
 }
 
 static const int kFwdKinds[] = {FDTD_K_FWD_H, FDTD_K_FWD_E, FDTD_K_RECORD, FDTD_K_MONITOR,
-                                FDTD_K_FWD_FUSED};
+                                FDTD_K_FWD_FUSED, FDTD_K_FWD_2STEP};
 static const int kBwdKinds[] = {FDTD_K_RESTORE, FDTD_K_REV_E, FDTD_K_REV_H, FDTD_K_REV_PRIMAL,
                                 FDTD_K_REV_ADJOINT, FDTD_K_REV_ADJOINT_CPML};
 
@@ -1230,6 +1291,117 @@ static cudaError_t enqueue_forward(fdtd_handle* h, const fdtd_record_cfg* rec, i
   if (det2.kind && (e = cudaMemsetAsync(h->ws + L.obj2, 0, h->N * sizeof(double), h->stream)))
     return e;
   Sampler smp(h, 0);
+  if (two_step_forward(h)) {
+    // two steps per pass: steps n, n + 1 of the deep units in one launch on
+    // the main stream (buffer cur -> cur ^ 1, the intermediate level's frame
+    // -> buffer 2), the split H half-step of step n over the other units
+    // beside it on a side stream (cur -> 2), then their split E half-step of
+    // step n (cur -> 2) and both half-steps of step n + 1 (2 -> cur ^ 1); the
+    // auxiliaries stay in place.  An odd count runs step 0 as split
+    // half-steps over every unit (cur -> cur ^ 1).
+    const int zcs = fused_forward_zchunk(h);
+    a.zchunk = zcs;
+    const RevUnits D = deep_units(a.g, zcs);
+    RevUnits all = D;   // no deep box: the ring decode covers every unit
+    all.ix0 = all.ix1 = all.iy0 = all.iy1 = all.iz0 = all.iz1 = 0;
+    const int zdeep = h->opt_zchunk_fwd2 > 0 ? h->opt_zchunk_fwd2 : 4 * zcs;
+    const float* Fb[3];
+    for (int b = 0; b < 3; ++b) Fb[b] = (const float*)(h->ws + L.F[b]);
+    const float* cbp = (const float*)(h->ws + L.cb);
+    const float* ps = (const float*)(h->ws + L.psiF[0]);
+    Fwd2Maps dm[2];
+    LagMaps lh[3], le[3][3];   // le[i][o]: E of buffer i, Ht^{n+1/2} of buffer o
+    for (int b = 0; b < 3; ++b) {
+      if (b < 2 && (e = encode_fwd2_maps(Fb[b], cbp, a.g, &dm[b]))) return e;
+      if ((e = encode_lag_maps(Fb[b], Fb[b], cbp, ps, a.g, 8, 32, L.plF, &lh[b]))) return e;
+      for (int o = 0; o < 3; ++o)
+        if (o != b && (e = encode_lag_maps(Fb[b], Fb[b], cbp, ps, a.g, 8, 32, L.plF, &le[b][o],
+                                           Fb[o])))
+          return e;
+    }
+    const bool conc = h->opt_sample == 0 && h->opt_zgroups != 1 && !h->zs.empty() &&
+                      h->zev.size() >= 3;
+    // one split time step over the units of U (umode 1 and 2) from buffer i
+    // into buffer o, with its record and second detector
+    auto split_step = [&](int n, int i, int o, const RevUnits& U, cudaStream_t hs,
+                          bool h_done) -> cudaError_t {
+      StepArgs b = a;
+      b.U = U;
+      b.zchunk = zcs;
+      b.jn = h->wave[n];
+      b.obj = (double*)(h->ws + L.obj) + n;
+      b.F = (float*)(h->ws + L.F[i]);
+      b.Fn = (float*)(h->ws + L.F[o]);
+      cudaError_t e2;
+      if (!h_done) {
+        if ((e2 = smp.before(FDTD_K_FWD_H))) return e2;
+        for (int um = 1; um <= 2; ++um) {
+          b.umode = um;
+          if ((e2 = launch_lag2(0, lh[i], b, hs))) return e2;
+        }
+        if ((e2 = smp.after(FDTD_K_FWD_H))) return e2;
+        nl += 2;
+        return cudaSuccess;
+      }
+      if ((e2 = smp.before(FDTD_K_FWD_E))) return e2;
+      for (int um = 1; um <= 2; ++um) {
+        b.umode = um;
+        if ((e2 = launch_lag2(1, le[i][o], b, h->stream))) return e2;
+      }
+      if ((e2 = smp.after(FDTD_K_FWD_E))) return e2;
+      nl += 2;
+      const bool rec_now = n >= r && (n - r) % rec->k == 0;
+      if (rec_now) {   // E^n in buffer i, Ht^{n+1/2} in buffer o
+        if ((e2 = smp.before(FDTD_K_RECORD))) return e2;
+        if ((e2 = record(b.Fn, b.F, (n - r) / rec->k))) return e2;
+        if ((e2 = smp.after(FDTD_K_RECORD))) return e2;
+        ++nl;
+      }
+      if (det2.kind) {
+        if ((e2 = smp.before(FDTD_K_MONITOR))) return e2;
+        if ((e2 = launch_monitor(b.Fn, a.g, det2, (double*)(h->ws + L.obj2) + n, h->stream)))
+          return e2;
+        if ((e2 = smp.after(FDTD_K_MONITOR))) return e2;
+        ++nl;
+      }
+      return cudaSuccess;
+    };
+    int cur = 0, n = 0;
+    if (h->N & 1) {
+      if ((e = split_step(0, cur, cur ^ 1, all, h->stream, false))) return e;
+      if ((e = split_step(0, cur, cur ^ 1, all, h->stream, true))) return e;
+      cur ^= 1;
+      n = 1;
+    }
+    for (; n + 1 < h->N; n += 2) {
+      cudaStream_t side = conc ? h->zs[0] : h->stream;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[0], h->stream))) return e;
+        if ((e = cudaStreamWaitEvent(side, h->zev[0], 0))) return e;
+      }
+      StepArgs b = a;
+      b.F = (float*)(h->ws + L.F[cur]);
+      b.Fn = (float*)(h->ws + L.F[cur ^ 1]);
+      b.Fm = (float*)(h->ws + L.F[2]);
+      b.zcs = zcs;
+      b.zchunk = zdeep;
+      if ((e = smp.before(FDTD_K_FWD_2STEP))) return e;
+      if ((e = launch_fwd_2step(dm[cur], b, D, h->stream))) return e;
+      if ((e = smp.after(FDTD_K_FWD_2STEP))) return e;
+      ++nl;
+      if ((e = split_step(n, cur, 2, D, side, false))) return e;
+      if (conc) {
+        if ((e = cudaEventRecord(h->zev[1], side))) return e;
+        if ((e = cudaStreamWaitEvent(h->stream, h->zev[1], 0))) return e;
+      }
+      if ((e = split_step(n, cur, 2, D, h->stream, true))) return e;
+      if ((e = split_step(n + 1, 2, cur ^ 1, D, h->stream, false))) return e;
+      if ((e = split_step(n + 1, 2, cur ^ 1, D, h->stream, true))) return e;
+      cur ^= 1;
+    }
+    *launches = nl;
+    return cudaSuccess;
+  }
   if (fused_forward(h)) {
     // fused forward step: the CPML-free units in one launch on the main
     // stream, the split H half-step of the other units beside it on a side
@@ -1532,6 +1704,7 @@ static int run_loop(fdtd_handle* h, const fdtd_record_cfg* rec, int dir, Enqueue
   key.inject_wait = h->opt_inject_wait;
   key.reverse = h->opt_reverse;
   key.forward = h->opt_forward;
+  key.zchunk_fwd2 = h->opt_zchunk_fwd2;
   key.start_buf = dir == 1 ? h->fwd_buf : 0;   // the backward starts from the forward's buffer
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
@@ -1597,6 +1770,10 @@ static int check_kernel_options(fdtd_handle* h) {
     return fail(h, FDTD_EINVAL,
                 "the fused forward step needs kernel 5, 32 x 8 tiles, CPML-free units and the "
                 "source and detector outside them");
+  if (h->opt_forward == 3 && !two_step_forward(h))
+    return fail(h, FDTD_EINVAL,
+                "the two-step forward needs kernel 5, 32 x 8 tiles, deep units and the source "
+                "and detectors two cells or more away from them");
   return FDTD_OK;
 }
 
@@ -1622,7 +1799,7 @@ static int forward_async(fdtd_handle* h, const float* d_eps, const fdtd_record_c
   nvtxRangePop();
   if (rc) return rc;
   h->launches_fwd = nl;
-  h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;   // a fused forward ends in buffer N mod 2
+  h->fwd_buf = forward_end_buf(h);
   h->fwd_rec = *rec;
   return FDTD_OK;
 }
@@ -1642,7 +1819,7 @@ static int forward_finish(fdtd_handle* h, double* objective) {
   h->obj2_sum = 0.0;
   for (double v : m) h->obj2_sum += v;
   CK(h, cudaEventElapsedTime(&h->fwd_ms, h->t0, h->t1));
-  collect_samples(h, 0, kFwdKinds, 5);
+  collect_samples(h, 0, kFwdKinds, (int)(sizeof kFwdKinds / sizeof kFwdKinds[0]));
   int rc = finish(h);
   if (rc) return rc;
   rc = check_err(h, err);
@@ -1707,7 +1884,7 @@ static int backward_finish(fdtd_handle* h, float* d_grad) {
   CK(h, cudaMemcpyAsync(&err, h->ws + L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaEventElapsedTime(&h->bwd_ms, h->t2, h->t3));
-  collect_samples(h, 1, kBwdKinds, 6);
+  collect_samples(h, 1, kBwdKinds, (int)(sizeof kBwdKinds / sizeof kBwdKinds[0]));
   int rc = finish(h);
   if (rc) return rc;
   return check_err(h, err);
@@ -1863,9 +2040,9 @@ static int batch_check(fdtd_handle* const* hs, int n, const fdtd_record_cfg* rec
     if (!h->ws) return fail(h, FDTD_ESTATE, "no workspace bound");
     if (layout_of(h, rec).total > h->ws_bytes)
       return fail(h, FDTD_ENOMEM, "workspace too small for this record config");
-    if (h->opt_kernel != 5 || fused_forward(h) || fused_reverse(h) || lag_tile_y(h) != 8 ||
-        lag_tile_x(h) != 32 || h->opt_stages != 2 || h->opt_exact || h->det2.kind ||
-        h->opt_inject_wait)
+    if (h->opt_kernel != 5 || fused_forward(h) || h->opt_forward == 3 || two_step_forward(h) ||
+        fused_reverse(h) || lag_tile_y(h) != 8 || lag_tile_x(h) != 32 || h->opt_stages != 2 ||
+        h->opt_exact || h->det2.kind || h->opt_inject_wait)
       return fail(h, FDTD_EINVAL,
                   "batched designs run kernel 5's split steps with 32 x 8 tiles, two stages, "
                   "one detector and no exact reversal");
@@ -2352,6 +2529,17 @@ extern "C" int fdtd_zgroup_ranges(int nch, int G, int* lo, int* hi) {
   return n;
 }
 
+extern "C" int fdtd_deep_units(int nx, int ny, int nz, int P, int zchunk, int* box) {
+  if (nx < 1 || ny < 1 || nz < 1 || P < 0 || zchunk < 1 || !box) return FDTD_EINVAL;
+  Geo g;
+  memset(&g, 0, sizeof g);
+  g.nx = nx; g.ny = ny; g.nz = nz; g.P = P;
+  const RevUnits U = deep_units(g, zchunk);
+  const int v[6] = {U.ix0, U.ix1, U.iy0, U.iy1, U.iz0, U.iz1};
+  for (int i = 0; i < 6; ++i) box[i] = v[i];
+  return FDTD_OK;
+}
+
 extern "C" int fdtd_reverse_units(int nx, int ny, int nz, int P, int zchunk, int* counts,
                                   int* units, int max_units) {
   if (nx < 1 || ny < 1 || nz < 1 || P < 0 || zchunk < 0 || !counts) return FDTD_EINVAL;
@@ -2533,7 +2721,7 @@ extern "C" int fdtd_value_and_grad_noalloc(fdtd_handle* h, const float* d_eps,
     int nl = 0;
     cudaError_t e = enqueue_forward(h, rec, &nl);
     if (e) return cuda_fail(h, "forward launch", e);
-    h->fwd_buf = fused_forward(h) ? (h->N & 1) : 0;
+    h->fwd_buf = forward_end_buf(h);
     // objective: per-step slots summed on the host in chunks
     double sum = 0.0, chunk[256];
     for (int n0 = 0; n0 < h->N; n0 += 256) {

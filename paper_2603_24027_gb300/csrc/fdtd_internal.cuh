@@ -290,6 +290,7 @@ struct StepArgs {
   float* Fn;       // fused steps: fields written (the other buffer of a ping-pong pair);
                    // the forward half-steps write here when set, else in place
   float* Ln;       // fused reverse step: adjoint fields written
+  float* Fm;       // two-step forward: the intermediate time level (frame of the deep box)
   double* gacc;    // FP64 design-box accumulator [dz][dy][dx]
   int dlo[3], dhi[3];
   Src src;
@@ -298,6 +299,7 @@ struct StepArgs {
   float jn;        // J waveform value of this step
   int zchunk;
   int zc0, zc1;     // two-cells-per-thread kernels: z chunks [zc0, zc1) of this launch (zc1 = 0: to the last)
+  int zcs;          // two-step forward: planes per z chunk of U (the split half-steps' chunks)
   int t0x, t0y;     // fused reverse step: first tile of a launch along x and y
   int umode;        // forward half-steps (32 x 8 tiles): 0 every unit of the grid (offset
                     // by zc0), 1 the z-only units of U, 2 the ring units of U
@@ -370,6 +372,24 @@ cudaError_t launch_rev_fused(int which, const RevMaps& m, const StepArgs& a, con
 // [iy0, iy1) x [iz0, iz1) of U (none may hold a source or detector cell):
 // reads a.F (E^n, Ht^{n-1/2}) and cb, writes a.Fn (E^{n+1}, Ht^{n+1/2}).
 cudaError_t launch_fwd_fused(const RevMaps& m, const StepArgs& a, const RevUnits& U,
+                             cudaStream_t s);
+// Two forward time steps per pass (kernels_fwd_2step.cu): tensor maps over
+// the fields (boxes 40 x 12, 3 components) and cb (40 x 10).
+struct alignas(64) Fwd2Maps {
+  CUtensorMap F4012, cb40;
+};
+cudaError_t encode_fwd2_maps(const float* F, const float* cb, const Geo& g, Fwd2Maps* m);
+// The deep units of a grid for split z chunks of zcs planes: the tiles and
+// full chunks ([ix0, ix1) x [iy0, iy1) x [iz0, iz1) of the ntx x nty x nzc
+// grid of rev_units) on whose cells and two-cell halo a two-step pass
+// evaluates no CPML term; the other units are U's z-only and ring units.
+RevUnits deep_units(const Geo& g, int zcs);
+// Steps n and n + 1 over the deep units U (chunks of a.zchunk planes, U's
+// chunks of a.zcs planes; none may come within two cells of a source or
+// detector cell): reads a.F (E^n, Ht^{n-1/2}) and cb, writes a.Fn (E^{n+2},
+// Ht^{n+3/2}) and, on the one-cell frame of the deep box, a.Fm (E^{n+1},
+// Ht^{n+1/2}).
+cudaError_t launch_fwd_2step(const Fwd2Maps& m, const StepArgs& a, const RevUnits& U,
                              cudaStream_t s);
 cudaError_t launch_finalize(const double* gacc, const float* cb, Geo g, const int* dlo,
                             const int* dhi, double scale, float* out, unsigned* err,

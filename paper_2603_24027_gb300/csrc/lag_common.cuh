@@ -121,6 +121,7 @@ __device__ __forceinline__ bool in_buf(const float* p, const float* base, long l
 __device__ __forceinline__ bool store_ok(const StepArgs& a, const float* p) {
   const long long n6 = 6 * a.g.nc;
   if (in_buf(p, a.F, n6) || in_buf(p, a.L, n6) || in_buf(p, a.Fn, n6) || in_buf(p, a.Ln, n6) ||
+      in_buf(p, a.Fm, n6) ||
       in_buf(p, a.psiA, a.pl.total) || in_buf(p, a.psiB, a.pl.total))
     return true;
   atomicOr(a.err, ERR_BOUNDS);

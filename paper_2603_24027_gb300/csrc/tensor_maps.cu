@@ -94,4 +94,11 @@ cudaError_t encode_rev_maps(const float* F, const float* Lm, const float* cb, co
   return enc_axis(&m->Qzo, psiA, pl.ax[2], tw, ty);
 }
 
+cudaError_t encode_fwd2_maps(const float* F, const float* cb, const Geo& g, Fwd2Maps* m) {
+  *m = Fwd2Maps{};
+  cudaError_t e;
+  if ((e = enc3(&m->F4012, F, g, 6, 40, 12, 3))) return e;
+  return enc3(&m->cb40, cb, g, 1, 40, 10, 1);
+}
+
 }  // namespace fdtd

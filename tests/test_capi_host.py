@@ -141,7 +141,8 @@ def test_options_are_validated(capi, fdtd):
                          (capi.OPT_PREFETCH, 0), (capi.OPT_COMPACT_AUX, 1),
                          (capi.OPT_EXACT_REVERSAL, 0), (capi.OPT_ZCHUNK_FWD, -1),
                          (capi.OPT_ZGROUPS, 0), (capi.OPT_REVERSE, 0),
-                         (capi.OPT_INJECT_WAIT_TIMEOUT, 0), (capi.OPT_FORWARD, 0)]:
+                         (capi.OPT_INJECT_WAIT_TIMEOUT, 0), (capi.OPT_FORWARD, 0),
+                         (capi.OPT_ZCHUNK_FWD2, -1)]:
         assert lib.fdtd_get_option(sim.h, opt, C.byref(v)) == capi.FDTD_OK and v.value == default
     for opt, val in [(capi.OPT_KERNEL, 7), (capi.OPT_KERNEL, -1), (capi.OPT_TILE_Y, 3),
                      (capi.OPT_STAGES, 1), (capi.OPT_STAGES, 5), (capi.OPT_KERNEL, 4),
@@ -149,7 +150,8 @@ def test_options_are_validated(capi, fdtd):
                      (capi.OPT_ZCHUNK, -1), (capi.OPT_TILE_X, 0), (capi.OPT_TILE_X, 36),
                      (capi.OPT_ZCHUNK_FWD, -2), (capi.OPT_EXACT_REVERSAL, 5),
                      (capi.OPT_ZGROUPS, -1), (capi.OPT_ZGROUPS, 17), (capi.OPT_REVERSE, 3),
-                     (capi.OPT_REVERSE, -1), (capi.OPT_FORWARD, 3), (capi.OPT_FORWARD, -1),
+                     (capi.OPT_REVERSE, -1), (capi.OPT_FORWARD, 4), (capi.OPT_FORWARD, -1),
+                     (capi.OPT_ZCHUNK_FWD2, -2),
                      (99, 1)]:
         assert lib.fdtd_set_option(sim.h, opt, val) == capi.FDTD_EINVAL
     assert lib.fdtd_set_option(sim.h, capi.OPT_STAGES, 4) == capi.FDTD_OK
@@ -344,6 +346,67 @@ def test_inject_wait_option_is_validated(capi, fdtd):
     assert v.value == 100000
 
 
+@pytest.mark.parametrize("nx,ny,nz,P,zc", [(150, 60, 40, 6, 8), (200, 90, 56, 8, 8),
+                                          (170, 75, 61, 7, 4), (200, 200, 100, 12, 8),
+                                          (600, 600, 300, 16, 8), (73, 33, 33, 8, 8),
+                                          (74, 33, 33, 8, 8), (70, 21, 19, 6, 8),
+                                          (130, 40, 60, 5, 7), (66, 34, 34, 1, 1)])
+def test_deep_units_against_brute_force(capi, nx, ny, nz, P, zc):
+    """The two-step forward's deep units: every 32 x 8 tile and whole zc-plane
+    chunk whose cells x0-2 .. x0+33, y0-2 .. y0+8 and planes k0-2 .. k1 (where
+    the pass evaluates the intermediate level) all lie in the interior, and
+    no other; per axis the qualifying tiles form one run, so the units are
+    the box the library reports (all zero when an axis has none)."""
+    lib = capi.lib()
+    box = (C.c_int * 6)()
+    assert lib.fdtd_deep_units(nx, ny, nz, P, zc, box) == capi.FDTD_OK
+
+    def inside(lo, hi_incl, n):
+        return lo >= P and hi_incl <= n - P - 1
+
+    xs = [t for t in range(-(-nx // 32)) if inside(32 * t - 2, 32 * t + 33, nx)]
+    ys = [t for t in range(-(-ny // 8)) if inside(8 * t - 2, 8 * t + 8, ny)]
+    zs = [c for c in range(-(-nz // zc)) if (c + 1) * zc <= nz and
+          inside(c * zc - 2, (c + 1) * zc, nz)]
+    want = [0] * 6
+    if xs and ys and zs:
+        for run in (xs, ys, zs):
+            assert run == list(range(run[0], run[-1] + 1))
+        want = [xs[0], xs[-1] + 1, ys[0], ys[-1] + 1, zs[0], zs[-1] + 1]
+    assert list(box) == want
+    assert lib.fdtd_deep_units(nx, ny, nz, P, 0, box) == capi.FDTD_EINVAL
+    assert lib.fdtd_deep_units(nx, ny, nz, P, zc, None) == capi.FDTD_EINVAL
+
+
+def test_two_step_forward_workspace(capi, fdtd):
+    """FDTD_OPT_FORWARD = 3 holds three field buffers (the pair and the
+    intermediate level); with the fused reverse the pair is shared."""
+    def al(x):
+        return (x + 255) // 256 * 256
+
+    rec = capi.record_cfg("e4m3", 8)
+    w = I.waveguide_large(n_steps=10)
+    f6 = al(6 * w.nz * w.ny * ((w.nx + 7) // 8 * 8) * 4)
+    sim = fdtd.Simulation(w)
+    sim.set_option(capi.OPT_REVERSE, 1)
+    sim.set_option(capi.OPT_FORWARD, 1)
+    split = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_FORWARD, 3)
+    assert sim.workspace_bytes(rec) - split == 2 * f6
+    sim.set_option(capi.OPT_REVERSE, 2)
+    assert sim.workspace_bytes(rec) - split == 3 * f6
+    sim.set_option(capi.OPT_FORWARD, 3)
+    sim.set_option(capi.OPT_ZCHUNK_FWD2, 5)
+    assert sim.workspace_bytes(rec) - split == 3 * f6
+    # a grid without deep units gets no third buffer (and is refused at the forward)
+    sim = fdtd.Simulation(I.ragged_box())
+    sim.set_option(capi.OPT_REVERSE, 1)
+    sim.set_option(capi.OPT_FORWARD, 1)
+    split = sim.workspace_bytes(rec)
+    sim.set_option(capi.OPT_FORWARD, 3)
+    assert sim.workspace_bytes(rec) == split
+
+
 @pytest.mark.parametrize("nx,ny,nz,P,zc", [(70, 21, 19, 6, 8), (86, 50, 30, 7, 8), (86, 50, 30, 7, 3),
                                           (200, 200, 100, 12, 8), (120, 77, 41, 9, 0),
                                           (600, 600, 300, 16, 8), (20, 18, 17, 8, 5),
@@ -412,9 +475,10 @@ def test_automatic_reverse_follows_the_cpml_share(capi, fdtd):
 
 def test_fused_forward_workspace_and_automatic_choice(capi, fdtd):
     """The fused forward step needs the second field buffer only (its
-    auxiliaries stay in place); FDTD_OPT_FORWARD = 0 takes it on the 600 x
-    600 x 300 grid (31 % of the units in the CPML, source and detector in the
-    ring) and not on the 200 x 200 x 100 one (70 %)."""
+    auxiliaries stay in place); FDTD_OPT_FORWARD = 0 takes the two-step pass
+    (second and third buffer) on the 600 x 600 x 300 grid (31 % of the units
+    in the CPML, source and detector in the ring) and neither it nor the
+    fused step on the 200 x 200 x 100 one (70 %)."""
     def al(x):
         return (x + 255) // 256 * 256
 
@@ -427,10 +491,11 @@ def test_fused_forward_workspace_and_automatic_choice(capi, fdtd):
     split = sim.workspace_bytes(rec)
     sim.set_option(capi.OPT_FORWARD, 2)
     assert sim.workspace_bytes(rec) - split == f6
-    sim.set_option(capi.OPT_FORWARD, 0)
-    assert sim.workspace_bytes(rec) - split == f6
     sim.set_option(capi.OPT_REVERSE, 2)
     assert sim.workspace_bytes(rec) - split == 2 * f6   # the reverse adds the adjoint's pair
+    sim.set_option(capi.OPT_REVERSE, 1)
+    sim.set_option(capi.OPT_FORWARD, 0)   # automatic: two steps per pass (a third buffer)
+    assert sim.workspace_bytes(rec) - split == 2 * f6
     w = I.waveguide_mid()
     sim = fdtd.Simulation(w)
     sim.set_option(capi.OPT_REVERSE, 1)

@@ -37,13 +37,18 @@ shapes = [dict(), {A.OPT_TILE_Y: 2, A.OPT_STAGES: 4, A.OPT_ZCHUNK: 1},
           {A.OPT_REVERSE: 2, A.OPT_EXACT_REVERSAL: 22}, {A.OPT_REVERSE: 2, A.OPT_ZCHUNK: 3},
           {A.OPT_REVERSE: 2, A.OPT_ZCHUNK: 1, A.OPT_COMPACT_AUX: 0},
           {A.OPT_REVERSE: 1, A.OPT_ZCHUNK: 3}]
+# the two-step forward (its pass writes the pair's other buffer and the
+# intermediate buffer's frame) on the grid with deep units
+deep = {"interior150": [{A.OPT_FORWARD: 3}, {A.OPT_FORWARD: 3, A.OPT_REVERSE: 2},
+                        {A.OPT_FORWARD: 3, A.OPT_EXACT_REVERSAL: 22},
+                        {A.OPT_FORWARD: 3, A.OPT_ZCHUNK_FWD: 4, A.OPT_ZCHUNK_FWD2: 5}]}
 n = 0
 for name, w in grids.items():
     ref = {"f32:1:linear": O.gradient(w)[1],
            "bdct10:2:cubic": O.reverse(w, "bdct10", k=2, interp="cubic")[1]}
     eps = torch.from_numpy(w.eps).cuda()
     for kernel in (5,):
-        for opts in shapes:
+        for opts in shapes + deep.get(name, []):
             for tape in ("f32:1:linear", "bdct10:2:cubic"):
                 sim = F.Simulation(w)
                 sim.set_option(A.OPT_KERNEL, kernel)

@@ -340,6 +340,101 @@ def test_fused_forward_needs_the_source_outside_its_units(F, A):
     assert rel(sim.backward(1.0).cpu().numpy(), g) < 1e-4
 
 
+# grids with deep units for the two-step forward (source and detectors two
+# cells or more away from them); "ragged_chunks" cuts the deep z range into
+# 5-plane chunks of the pass over 4-plane chunks of the split half-steps
+FWD2_GRIDS = {
+    "interior_units": (FUSED_GRIDS["interior_units"], {}),
+    "odd_steps": (FWD_GRIDS["odd_steps"], {}),
+    "compact_large": (FWD_GRIDS["compact_large"], {}),
+    "ragged_chunks": (lambda: I.ragged_box(nx=170, ny=75, nz=61, P=7, n_steps=33),
+                      {"zf": 4, "zf2": 5}),
+}
+
+
+def fwd2_opts(A, extra):
+    o = {}
+    if "zf" in extra:
+        o[A.OPT_ZCHUNK_FWD] = extra["zf"]
+    if "zf2" in extra:
+        o[A.OPT_ZCHUNK_FWD2] = extra["zf2"]
+    return o
+
+
+@pytest.mark.parametrize("name", list(FWD2_GRIDS))
+@pytest.mark.parametrize("tape", ["f32:1:linear", "bf16:3:cubic", "e4m3:2:linear"])
+@pytest.mark.parametrize("reverse", [1, 2])
+def test_two_step_forward_matches_the_split_half_steps(F, A, name, tape, reverse):
+    """Two time steps per pass over the deep units (the other units in split
+    half-steps through the intermediate buffer) against the split half-steps
+    in place: the fields after the forward and after the backward bit for
+    bit, the objective to the FP64 sums' order, the gradient to the adjoint
+    sums' rounding (so the tape, sampled at the pass's first and second step
+    alike, is the same); odd step counts run their first step split."""
+    make, extra = FWD2_GRIDS[name]
+    w = make()
+    dt, k, interp = tape.split(":")
+    rec = A.record_cfg(dt, int(k), interp)
+    opts = fwd2_opts(A, extra)
+    Ls, fs, gs, bs = run_forward_way(F, A, w, rec, 1, reverse, opts)
+    Lt, ft, gt, bt = run_forward_way(F, A, w, rec, 3, reverse, opts)
+    assert np.abs(fs).max() > 0
+    np.testing.assert_array_equal(ft, fs)
+    assert Lt == pytest.approx(Ls, rel=1e-12)
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    np.testing.assert_array_equal(bt[inner], bs[inner])
+    same_gradient(gt, gs)
+
+
+@pytest.mark.parametrize("n_steps", [70, 71])
+def test_two_step_forward_with_exact_reversal_returns_to_zero(F, A, n_steps):
+    """Exact reversal after a two-step forward: the fields equal the split
+    kernels' run of the same scheme bit for bit, and the fused reverse brings
+    the interior back to zero bit for bit from either buffer."""
+    w = FWD2_GRIDS["interior_units"][0]().replace(n_steps=n_steps)
+    rec = A.record_cfg("f32", 1)
+    opts = {A.OPT_EXACT_REVERSAL: 22}
+    _, fwd, g, back = run_forward_way(F, A, w, rec, 3, 2, opts)
+    _, fs, gs, _ = run_forward_way(F, A, w, rec, 1, 1, opts)
+    P = w.pml_thickness
+    inner = (slice(None), slice(P, w.nz - P), slice(P, w.ny - P), slice(P, w.nx - P))
+    assert np.abs(fwd[inner]).max() > 1e-3
+    np.testing.assert_array_equal(fwd, fs)
+    assert not np.any(back[inner])
+    same_gradient(g, gs)
+
+
+def test_two_step_forward_matches_the_oracle(F, A):
+    """FP32 tape of every step after a two-step forward: the gradient within
+    1e-4 of the exact discrete gradient, the objective within 1e-5."""
+    w = FWD2_GRIDS["interior_units"][0]().replace(n_steps=121)
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_FORWARD, 3)
+    eps = torch.from_numpy(w.eps).cuda()
+    L = sim.forward(eps, A.record_cfg("f32", 1))
+    g = sim.backward(1.0).cpu().numpy()
+    Lo, go = O.gradient(w)
+    assert np.abs(go).max() > 0
+    assert L == pytest.approx(Lo, rel=1e-5)
+    assert rel(g, go) < 1e-4
+
+
+def test_two_step_forward_needs_the_source_away_from_its_units(F, A):
+    """A point source inside the deep units: FDTD_OPT_FORWARD = 3 is refused
+    at the forward and the handle stays usable."""
+    w = I.ragged_box(nx=150, ny=60, nz=40, P=6, n_steps=40, src_kind=I.SRC_POINT)
+    w = w.replace(src_pos=(60, 30, 20))
+    eps = torch.from_numpy(w.eps).cuda()
+    sim = F.Simulation(w)
+    sim.set_option(A.OPT_FORWARD, 3)
+    with pytest.raises(A.FdtdError) as e:
+        sim.forward(eps, A.record_cfg("f32", 1))
+    assert e.value.status == A.FDTD_EINVAL
+    sim.set_option(A.OPT_FORWARD, 1)
+    assert np.isfinite(sim.forward(eps, A.record_cfg("f32", 1)))
+
+
 @pytest.mark.parametrize("reverse", [1, 2])
 def test_exact_reversal_on_a_grid_of_many_waves(F, A, reverse):
     """300 x 120 x 80 cells, 200 steps, exact reversal: every one of the many
@@ -956,8 +1051,8 @@ def test_full_size_waveguide_in_the_benchmark_configuration(F, A):
 
 def test_largest_grid_in_the_bench_configuration(F, A):
     """600 x 600 x 300 cells, 10 000 steps, the E4M3 tape every 8th step: the
-    bench's line, with the library's default steps (fused forward and fused
-    reverse), against the split half-steps and phases.  The oracle cannot run
+    bench's line, with the library's default steps (two time steps per pass
+    forward, fused reverse), against the split half-steps and phases.  The oracle cannot run
     this grid, so properties that hold at any size stand in: forward fields
     bit for bit, the objective to the FP64 sums' order, the gradient finite
     and within 1e-5 of the split kernels' over a run long enough for an
@@ -977,12 +1072,12 @@ def test_largest_grid_in_the_bench_configuration(F, A):
 
 def test_largest_grid_against_the_oracle_near_the_source(F, A):
     """All 108 M cells of the 600 x 600 x 300 grid in the bench's launch
-    configuration (fused forward and fused reverse, FP32 tape of every step),
-    against the FP64 oracle: the Poynting detector moved to x = 28 and the
-    design box to x in [21, 28) around the strip, between the source plane
-    (x = 20) and the detector, so that L and dL/d(eps) are non-zero within
-    120 steps.  Both stay outside the CPML-free units, as the fused forward
-    needs.  Fields after the forward within 1e-5, the objective within 1e-5,
+    configuration (two time steps per pass forward, fused reverse, FP32
+    tape of every step), against the FP64 oracle: the Poynting detector moved
+    to x = 28 and the design box to x in [21, 28) around the strip, between
+    the source plane (x = 20) and the detector, so that L and dL/d(eps) are
+    non-zero within 120 steps.  Source and detector stay two cells or more
+    away from the deep units (x >= 32), as the two-step pass needs.  Fields after the forward within 1e-5, the objective within 1e-5,
     the gradient within 1e-4."""
     w = I.waveguide_large(n_steps=120)
     P, yc, zc = w.pml_thickness, w.ny // 2, w.nz // 2
@@ -994,7 +1089,8 @@ def test_largest_grid_against_the_oracle_near_the_source(F, A):
         assert sim.get_option(opt) == 0
     eps = torch.from_numpy(w.eps).cuda()
     Lg = sim.forward(eps, A.record_cfg("f32", 1))
-    assert sim.last_timing()["fwd_launches"] == 6 * w.n_steps   # fused: 5 launches + the record
+    # per pair of steps: the pass, 2 x 4 split launches over the other units, 2 records
+    assert sim.last_timing()["fwd_launches"] == 11 * w.n_steps // 2
     fields = sim.read_fields().cpu().numpy()
     eE, eH = field_err(fields, st)
     del st
