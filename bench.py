@@ -489,7 +489,8 @@ def run_ours(args):
         if "fwd_2step" in kinds:
             phases[ph]["note"] = ("two time steps per pass over the deep units: one time "
                                   "step's algorithmic bytes over the time per step is an "
-                                  "effective bandwidth (the pass moves half of them)")
+                                  "effective bandwidth (the pass moves the deep units' "
+                                  "bytes once per two time steps)")
     dom = max(phases, key=lambda p: phases[p]["ms_per_time_step"])
     roofline = {"bound": "hbm", "kernel": f"{dom} phase (one time step)",
                 "achieved": phases[dom]["achieved"], "peak": peak, "unit": "GB/s",

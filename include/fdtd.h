@@ -353,8 +353,8 @@ enum {
                                    unit.  The fields and the tape are bit-identical to
                                    the split half-steps' */
   FDTD_OPT_ZCHUNK_FWD2 = 17     /* kernel 5 with FDTD_OPT_FORWARD = 3: z planes per CTA of
-                                   the two-step pass (-1 or 0, the default: four chunks of
-                                   the other units' split half-steps, whose chunks are
+                                   the two-step pass (-1 or 0, the default: sixteen chunks
+                                   of the other units' split half-steps, whose chunks are
                                    FDTD_OPT_ZCHUNK_FWD planes if > 0, else FDTD_OPT_ZCHUNK);
                                    a chunk streams two planes below and one above it */
 };
