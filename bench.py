@@ -28,7 +28,10 @@ Roofline: the algorithmic bytes of a forward time step (52 B per cell, +32 B
 per CPML axis of the cell) and of a reverse time step (100 B per interior
 cell, 52 B per CPML cell, +32 B per CPML axis, +16 B per design cell), plus
 the tape's codes, over the measured time of one step of that phase; the
-reverse phase is the dominant one.  The per-kernel breakdown comes from a
+reverse phase is the dominant one.  Where the forward runs two time steps per
+pass over the deep units (the library's choice on the large grid), its
+fraction is an effective one: those units' fields cross DRAM once per two
+steps.  The per-kernel breakdown comes from a
 sampled pass with one launch per half-step on a shortened copy of the
 workload (same grid, same per-launch work).
 

@@ -465,7 +465,7 @@ static bool fused_forward(const fdtd_handle* h) {
 // two cells away from the deep box (the pass evaluates the intermediate
 // level on a two-cell halo and adds no source term, sums no objective).
 // Automatic (0): where the fused step would run (at most half of the units
-// carry CPML terms), which it beats on 600 x 600 x 300 (1055 against 1166 us
+// carry CPML terms), which it beats on 600 x 600 x 300 (1028 against 1166 us
 // per forward step); on 200 x 200 x 100 it is slower than the split
 // half-steps (92 against 59 us), as the fused step is.
 static bool two_step_forward(const fdtd_handle* h) {
