@@ -2,8 +2,9 @@
 
 How fast a gradient runs depends on launch options that leave its results
 unchanged: the tile height and ring stages of the one-plane kernels, the z
-chunk of the reverse phases and of the forward half-steps, and the number of
-z groups each half-step is split into.  The library's defaults come from
+chunk of the reverse phases, of the forward half-steps and of the two-step
+forward pass (a no-op where that pass does not run), and the number of z
+groups each half-step is split into.  The library's defaults come from
 sweeps on two waveguide grids; other grids may prefer other values.  `tune`
 times candidate settings on a shortened copy of the problem itself (same
 grid, CPML, source, detector, design box, tape and kernel; fewer time steps),
@@ -35,6 +36,7 @@ SPACE: List[Tuple[str, int, Sequence[int]]] = [
     ("zgroups", A.OPT_ZGROUPS, (0, 1, 3, 4, 6, 8)),
     ("zchunk", A.OPT_ZCHUNK, (8, 4, 6, 10, 16)),
     ("zchunk_fwd", A.OPT_ZCHUNK_FWD, (-1, 8, 16, 4)),
+    ("zchunk_fwd2", A.OPT_ZCHUNK_FWD2, (-1, 64, 256)),
     ("tile_y", A.OPT_TILE_Y, (8, 4, 16, 2)),
     ("stages", A.OPT_STAGES, (2, 3, 4)),
 ]
@@ -91,6 +93,8 @@ def valid(options: Dict[str, int]) -> bool:
     if ty == 16 and s != 3:
         return False
     if options.get("zchunk", 8) < 0 or options.get("zchunk_fwd", -1) < -1:
+        return False
+    if options.get("zchunk_fwd2", -1) < -1:
         return False
     return 0 <= options.get("zgroups", 0) <= 16
 

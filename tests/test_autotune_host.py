@@ -8,7 +8,8 @@ from paper_2603_24027_gb300 import _capi as A
 from paper_2603_24027_gb300 import autotune as T
 from paper_2603_24027_gb300 import inputs as I
 
-START = {"zgroups": 0, "zchunk": 8, "zchunk_fwd": -1, "tile_y": 8, "stages": 2}
+START = {"zgroups": 0, "zchunk": 8, "zchunk_fwd": -1, "zchunk_fwd2": -1, "tile_y": 8,
+         "stages": 2}
 
 
 class FakeSim:
@@ -17,7 +18,8 @@ class FakeSim:
     def __init__(self, w=None, opts=None):
         self.w = w or I.ragged_box()
         self.opts = {A.OPT_KERNEL: 5, A.OPT_ZGROUPS: 0, A.OPT_ZCHUNK: 8, A.OPT_ZCHUNK_FWD: -1,
-                     A.OPT_TILE_Y: 8, A.OPT_STAGES: 2, A.OPT_EXACT_REVERSAL: 0}
+                     A.OPT_ZCHUNK_FWD2: -1, A.OPT_TILE_Y: 8, A.OPT_STAGES: 2,
+                     A.OPT_EXACT_REVERSAL: 0}
         self.opts.update(opts or {})
 
     def get_option(self, oid):
@@ -48,7 +50,8 @@ class Counter:
 
 
 def test_search_reaches_a_separable_minimum_and_times_each_setting_once():
-    target = {"zgroups": 3, "zchunk": 6, "zchunk_fwd": 8, "tile_y": 4, "stages": 3}
+    target = {"zgroups": 3, "zchunk": 6, "zchunk_fwd": 8, "zchunk_fwd2": 64, "tile_y": 4,
+              "stages": 3}
     m = Counter(separable(target))
     best, t, tried = T.search(m, START)
     assert best == target
@@ -104,7 +107,8 @@ def test_cache_key_separates_what_changes_the_best_shape():
 def test_tune_applies_caches_and_reuses(tmp_path):
     path = str(tmp_path / "sub" / "tune.json")
     rec = A.record_cfg("bf16", 4)
-    target = {"zgroups": 4, "zchunk": 10, "zchunk_fwd": 16, "tile_y": 8, "stages": 2}
+    target = {"zgroups": 4, "zchunk": 10, "zchunk_fwd": 16, "zchunk_fwd2": -1, "tile_y": 8,
+              "stages": 2}
     sim = FakeSim()
     r = T.tune(sim, None, rec, cache=path, measure=separable(target), gpu_name="GB300")
     assert not r["cached"] and r["options"] == target
@@ -147,7 +151,7 @@ def test_tune_leaves_other_kernels_and_exact_shapes_alone(tmp_path):
         return 1.0 - 0.1 * (o.get("zgroups") == 3)
     sim = FakeSim(opts={A.OPT_EXACT_REVERSAL: 16})
     r = T.tune(sim, None, rec, cache=path, measure=cost, gpu_name="GB300")
-    assert all(s == {"zgroups", "zchunk", "zchunk_fwd"} for s in seen)
+    assert all(s == {"zgroups", "zchunk", "zchunk_fwd", "zchunk_fwd2"} for s in seen)
     assert r["options"]["zgroups"] == 3 and sim.get_option(A.OPT_TILE_Y) == 8
 
 
