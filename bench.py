@@ -520,6 +520,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}",
                    "l2": "state larger than L2; L2 also flushed before every timed step",
                    "zgroups": args.zgroups or "automatic",
+                   "forward_step": ("two steps per pass over the deep units" if "fwd_2step" in kern
+                                    else "fused" if "fwd_fused" in kern else "split"),
+                   "reverse_step": "fused" if "rev_primal" in kern else "split",
                    "autotuned": None if tuned is None else
                    {"options": tuned["options"], "cached": tuned["cached"]},
                    "fwd_ms": statistics.median(fwd_ms), "bwd_ms": statistics.median(bwd_ms),
